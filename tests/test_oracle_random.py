@@ -1,0 +1,86 @@
+"""Pins of the oracle's random streams (no GPU): Philox4x32-10 against the
+published known-answer vectors, the Maxwell-Juettner reinjection sampler
+against textbook moments and its exact distribution, and the probabilistic
+escape draw against its binomial law.  The leaky box (Sec. 4.1) resamples an
+escaped particle's velocity from a prescribed (typically Maxwellian) law.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+
+
+def _kat_rows():
+    rows = []
+    with open(GOLDEN) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            w = [int(v, 16) for v in line.split()]
+            rows.append((w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+@pytest.mark.parametrize("ctr,key,want", _kat_rows())
+def test_philox_known_answers(ctr, key, want):
+    assert list(O.philox4x32_10(ctr, key)) == want
+
+
+def test_escape_draw_threshold_is_integer_compare():
+    """p = 0 never escapes, p = 1 essentially always does, and the rate at
+    p matches a binomial law over many (id, step) keys."""
+    assert not any(O.escape_draw(i, 0, 5, 0.0) for i in range(200))
+    assert sum(O.escape_draw(i, 0, 5, 1.0) for i in range(200)) >= 199
+    p, n = 0.137, 20000
+    k = sum(O.escape_draw(i % 1000, 3, i // 1000, p) for i in range(n))
+    assert abs(k - n * p) < 5 * math.sqrt(n * p * (1 - p))
+
+
+def _mj_mean_gamma(theta):
+    """<gamma> of the Maxwell-Juettner law: K1(1/theta)/K2(1/theta) + 3 theta."""
+    from scipy.special import kve
+    z = 1.0 / theta
+    return kve(1, z) / kve(2, z) + 3 * theta
+
+
+def _mj_cdf_table(theta):
+    """CDF of gamma for f(gamma) ~ gamma sqrt(gamma^2 - 1) exp(-gamma/theta),
+    by quadrature on a fine grid (independent of the sampler's construction)."""
+    from scipy.integrate import cumulative_trapezoid
+    e_max = theta * 60 + 1
+    e = np.concatenate([np.linspace(0, 1e-3 * e_max, 20001)[:-1], np.linspace(1e-3 * e_max, e_max, 200001)])
+    g = 1 + e
+    f = g * np.sqrt(e * (e + 2)) * np.exp(-e / theta)
+    cdf = cumulative_trapezoid(f, g, initial=0.0)
+    return g, cdf / cdf[-1]
+
+
+@pytest.mark.parametrize("theta", [0.05, 0.3, 1.0, 4.0])
+def test_maxwell_juettner_sampler(theta):
+    from scipy.stats import kstest
+    c = 0.45
+    n = 20000
+    us = np.array([O.sample_mj(i, 11, 7, theta, c)[0] for i in range(n)])
+    gam = np.sqrt(1 + (us**2).sum(axis=1) / c**2)
+    mean = _mj_mean_gamma(theta)
+    se = gam.std() / math.sqrt(n)
+    assert abs(gam.mean() - mean) < 5 * se
+    gg, cdf = _mj_cdf_table(theta)
+    res = kstest(gam, lambda v: np.interp(v, gg, cdf))
+    assert res.pvalue > 1e-4
+    # isotropy: mean direction ~ 0, <mu^2> = 1/3
+    nh = us / np.linalg.norm(us, axis=1, keepdims=True)
+    assert np.abs(nh.mean(axis=0)).max() < 5 / math.sqrt(3 * n)
+    assert abs((nh[:, 2] ** 2).mean() - 1 / 3) < 5 * math.sqrt(4 / 45 / n)
+
+
+def test_maxwell_juettner_attempts_bounded():
+    """Acceptance is at least 1/sqrt(2) per attempt whatever theta."""
+    for theta in (0.01, 0.2, 2.0, 30.0):
+        att = [O.sample_mj(i, 1, 0, theta, 1.0)[1] for i in range(3000)]
+        assert np.mean(att) < 1.0 / (1.0 / math.sqrt(2)) + 0.05

@@ -1,0 +1,171 @@
+"""Pins of the oracle's whole step (no GPU): invariants and reductions of the
+three box methods (Secs. 2.2, 3.2, 4.1) on small synthetic plasmas."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+C = 0.45
+
+
+def plasma(n, ppc, seed, uth=0.1, q=0.05):
+    """Two species of opposite charge, uniform in the box, Gaussian momenta."""
+    r = np.random.default_rng(seed)
+    ncell = n[0] * n[1] * n[2]
+    sp = []
+    for s, sign in enumerate((-1.0, 1.0)):
+        N = ncell * ppc
+        x = r.uniform(0, 1, (N, 3)) * np.array(n, dtype=float)
+        u = r.normal(0, uth, (N, 3))
+        sp.append({"q": sign * q, "m": 1.0, "x": x, "u": u, "id": np.arange(N) + s * N})
+    return sp
+
+
+def div_node(F):
+    return ((F[0] - np.roll(F[0], 1, axis=2)) + (F[1] - np.roll(F[1], 1, axis=1))
+            + (F[2] - np.roll(F[2], 1, axis=0)))
+
+
+def rho_nodes(p, st):
+    return O.rho_of(p, [(d["q"], d["x"]) for d in st.species])
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("n", [(6, 5, 4), (8, 1, 6)])
+def test_gauss_law_preserved_by_full_steps(order, n):
+    """div E - 4 pi rho stays constant: the charge-conserving deposit and the
+    Yee update together (standard PIC, and the leaky box, Sec. 4.1)."""
+    p = O.make_params(*n, C, order=order)
+    r = np.random.default_rng(1)
+    E = r.normal(0, 0.01, (3, n[2], n[1], n[0]))
+    B = r.normal(0, 0.05, (3, n[2], n[1], n[0]))
+    st = O.State(p, E, B, plasma(n, 4, 2))
+    g0 = div_node(st.E) - 4 * math.pi * rho_nodes(p, st)
+    st.step(5)
+    g1 = div_node(st.E) - 4 * math.pi * rho_nodes(p, st)
+    assert np.abs(g1 - g0).max() < 1e-12
+
+
+def test_expanding_box_with_zero_rate_is_standard_pic():
+    n = (6, 5, 4)
+    r = np.random.default_rng(3)
+    E = r.normal(0, 0.01, (3, 4, 5, 6))
+    B = r.normal(0, 0.05, (3, 4, 5, 6))
+    a = O.State(O.make_params(*n, C, order=2), E, B, plasma(n, 3, 4))
+    b = O.State(O.make_params(*n, C, order=2, box=O.BOX_EXPAND, rate=(0, 0, 0)), E, B, plasma(n, 3, 4))
+    a.step(3)
+    b.step(3)
+    np.testing.assert_allclose(b.E, a.E, atol=1e-15)
+    np.testing.assert_allclose(b.B, a.B, atol=1e-15)
+    for sa, sb in zip(a.species, b.species):
+        np.testing.assert_allclose(sb["x"], sa["x"], atol=1e-13)
+        np.testing.assert_allclose(sb["u"], sa["u"], atol=1e-15)
+
+
+def test_shearing_box_particle_phase_reduces_to_standard_pic():
+    """With Omega0 = 0 the shearing-box push, position update and (advected)
+    current equal the standard ones; only the field solver differs."""
+    n = (6, 5, 4)
+    r = np.random.default_rng(5)
+    E = r.normal(0, 0.01, (3, 4, 5, 6))
+    B = r.normal(0, 0.05, (3, 4, 5, 6))
+    a = O.State(O.make_params(*n, C, order=1), E, B, plasma(n, 3, 6))
+    b = O.State(O.make_params(*n, C, order=1, box=O.BOX_SHEAR, s=1.5, Omega0=0.0), E, B, plasma(n, 3, 6))
+    a.step(1)
+    b.step(1)
+    np.testing.assert_allclose(b.J, a.J, atol=1e-16)
+    for sa, sb in zip(a.species, b.species):
+        np.testing.assert_allclose(sb["x"], sa["x"], atol=1e-13)
+        np.testing.assert_allclose(sb["u"], sa["u"], atol=1e-16)
+
+
+def test_shearing_box_particle_at_rest_rides_the_shear_flow():
+    """u' = 0 and no fields: the particle stays at rest in the shearing frame
+    and its lab position moves with v_s = -s Omega0 x e_y (Sec. 2.1)."""
+    n = (16, 32, 1)
+    s, Om = 1.5, 0.01
+    p = O.make_params(*n, C, order=1, box=O.BOX_SHEAR, s=s, Omega0=Om)
+    x0 = np.array([[12.25, 20.0, 0.5], [3.5, 5.0, 0.5]])
+    sp = [{"q": 1e-9, "m": 1.0, "x": x0, "u": np.zeros((2, 3))}]
+    st = O.State(p, np.zeros((3, 1, 32, 16)), np.zeros((3, 1, 32, 16)), sp)
+    st.step(10)
+    xc = x0[:, 0] - 8
+    want_y = np.mod(x0[:, 1] - s * Om * xc * 10, 32)
+    np.testing.assert_allclose(st.species[0]["x"][:, 1], want_y, atol=1e-10)
+    np.testing.assert_allclose(st.species[0]["x"][:, 0], x0[:, 0], atol=1e-12)
+
+
+def test_shearing_box_boundary_crossing_shifts_y():
+    """A particle leaving through x_o re-enters at x_i with y + Dy_s(t^{n+1}),
+    and through x_i with y - Dy_s, with u' unchanged (the particle counterpart
+    of X(x_i, y) = X(x_o, y - Dy_s))."""
+    n = (8, 20, 1)
+    s, Om = 1.5, 0.003
+    p = O.make_params(*n, C, order=1, box=O.BOX_SHEAR, s=s, Omega0=Om)
+    step0 = 40
+    u = np.array([[0.3, 0.0, 0.0], [-0.3, 0.0, 0.0]])
+    x0 = np.array([[7.9, 10.0, 0.5], [0.1, 10.0, 0.5]])
+    sp = [{"q": 1e-12, "m": 1.0, "x": x0, "u": u}]
+    st = O.State(p, np.zeros((3, 1, 20, 8)), np.zeros((3, 1, 20, 8)), sp, step=step0)
+    st.step(1)
+    dys = O.shear_shift(p, step0 + 1.0)
+    uu = st.species[0]["u"]
+    g = np.sqrt(1 + (uu**2).sum(axis=1) / C**2)
+    xp = x0[:, 0] + uu[:, 0] / g
+    xc0 = x0[:, 0] - 4
+    y_sh = x0[:, 1] + uu[:, 1] / g - s * Om * ((xp - 4) + xc0) / 2
+    got = st.species[0]["x"]
+    assert got[0, 0] == pytest.approx(xp[0] - 8, abs=1e-12)
+    assert got[1, 0] == pytest.approx(xp[1] + 8, abs=1e-12)
+    assert got[0, 1] == pytest.approx(np.mod(y_sh[0] + dys, 20), abs=1e-10)
+    assert got[1, 1] == pytest.approx(np.mod(y_sh[1] - dys, 20), abs=1e-10)
+
+
+def test_leaky_displacement_escape_is_ballistic_exact():
+    """E = B = 0: a particle of velocity v escapes at the first step n with
+    n |v_x| dt >= l_esc; it is reinjected at the same position with Dr = 0."""
+    n = (8, 8, 1)
+    v = 0.2
+    u = v / math.sqrt(1 - (v / C) ** 2)
+    g = math.sqrt(1 + (u / C) ** 2)
+    vstep = u / g
+    l_esc = 2.3
+    p = O.make_params(*n, C, order=1, box=O.BOX_LEAKY, esc_mode=O.ESC_DISPLACEMENT,
+                      l_esc=l_esc, theta_inj=0.1, seed=9)
+    sp = [{"q": 1e-12, "m": 1.0, "x": np.array([[1.0, 4.0, 0.5]]), "u": np.array([[u, 0.0, 0.0]])}]
+    st = O.State(p, np.zeros((3, 1, 8, 8)), np.zeros((3, 1, 8, 8)), sp)
+    first = math.ceil(l_esc / vstep - 1e-12)
+    for k in range(1, first + 1):
+        x_before = st.species[0]["x"].copy()
+        info = st.step(1)
+        if k < first:
+            assert info["escaped"] == 0
+            assert st.species[0]["dr"][0, 0] == pytest.approx(k * vstep, rel=1e-13)
+        else:
+            assert info["escaped"] == 1
+            assert np.all(st.species[0]["dr"][0] == 0.0)
+            np.testing.assert_allclose(st.species[0]["x"][0, 0], np.mod(x_before[0, 0] + vstep, 8), atol=1e-13)
+            assert not np.allclose(st.species[0]["u"][0], [u, 0, 0])
+
+
+def test_leaky_probabilistic_survival_is_binomial():
+    """Probabilistic escape at p = dt / t_esc per step: the fraction of
+    particles never reinjected after n steps is (1 - p)^n ~ exp(-t/t_esc);
+    checked at 5 sigma.  Particles start at rest without fields, so a particle
+    has been reinjected iff its momentum is non-zero (uncharged test
+    particles, so no field ever acts on them)."""
+    n = (4, 4, 1)
+    N = 8000
+    p_esc = 0.02
+    p = O.make_params(*n, C, order=1, box=O.BOX_LEAKY, esc_mode=O.ESC_PROBABILISTIC,
+                      p_esc=p_esc, theta_inj=0.2, seed=5)
+    r = np.random.default_rng(0)
+    sp = [{"q": 0.0, "m": 1.0, "x": r.uniform(0, 4, (N, 3)) * [1, 1, 0.25], "u": np.zeros((N, 3))}]
+    st = O.State(p, np.zeros((3, 1, 4, 4)), np.zeros((3, 1, 4, 4)), sp)
+    steps = 40
+    st.step(steps)
+    surv = np.all(st.species[0]["u"] == 0.0, axis=1).sum()
+    pr = (1 - p_esc) ** steps
+    assert abs(surv - N * pr) < 5 * math.sqrt(N * pr * (1 - pr))
