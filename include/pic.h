@@ -1,0 +1,205 @@
+/*
+ * pic.h -- C ABI of libpic, a single-GPU (GB300, sm_103a) particle-in-cell
+ * step for the three box methods of "Particle-in-Cell Methods for Simulations
+ * of Sheared, Expanding, or Escaping Astrophysical Plasma" (arXiv 2602.15939):
+ * the kinetic shearing box with orbital advection (KSB-OA, Sec. 2), the
+ * kinetic expanding box (KEB, Sec. 3) and the leaky box (Sec. 4).
+ *
+ * Units and layout shared by every call:
+ *  - code units dx = dt = 1; `c` is the Courant number c dt/dx (cells/step);
+ *    Gaussian units as in the paper (4 pi in Ampere's law);
+ *  - momentum u is the spatial part of the four-velocity, u = gamma v, in
+ *    cells/step, gamma = sqrt(1 + (u/c)^2);
+ *  - positions are absolute cell coordinates, x in [0,nx), y in [0,ny),
+ *    z in [0,nz); node (i,j,k) sits at (i,j,k);
+ *  - fields use Yee staggering: Ex (i+1/2,j,k), Ey (i,j+1/2,k), Ez (i,j,k+1/2),
+ *    Bx (i,j+1/2,k+1/2), By (i+1/2,j,k+1/2), Bz (i+1/2,j+1/2,k); J like E.
+ *    Host field arrays are float64 [3][nz][ny][nx], index ((c*nz+k)*ny+j)*nx+i;
+ *  - 2D runs set the ignorable axis to one cell (plane XY: nz = 1; plane XZ:
+ *    ny = 1); all three vector components are kept (2D3V); the ignorable
+ *    coordinate of a particle is not tracked and reads back as 0.5;
+ *  - shearing box: the radial coordinate in v_s = -s Omega0 x e_y is measured
+ *    from the box centre (x - nx/2); E passed in and out is the comoving E'
+ *    and u the comoving u' (Sec. 2.1);
+ *  - expanding box: positions are the comoving x' and fields and momenta the
+ *    lab-frame values on the x' grid (Sec. 3.2); l_i(t) = exp(rate_i t).
+ *
+ * Ownership: the library owns all device memory (allocated at pic_init and
+ * at particle load).  Host arrays passed in are copied before the call
+ * returns and never retained; host arrays passed out are filled by the call.
+ * Errors: every call returns a pic_status; nothing is thrown across the ABI.
+ * After a non-OK status, pic_last_error(h) describes it.  Device-side
+ * failures (a bounded wait that expired, a non-finite momentum) are recorded
+ * in a device error word and reported by the next pic_step or
+ * pic_diagnostics as PIC_ERR_TIMEOUT or PIC_ERR_NUMERIC.
+ * Streams: all work of a handle is ordered on its stream (pic_set_stream);
+ * pic_step returns without waiting for the GPU.  Calls on one handle must
+ * not run concurrently from several host threads.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_ABI_VERSION 1
+#define PIC_MAX_SPECIES 4
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_ERR_ARG = 1,     /* invalid argument or configuration */
+    PIC_ERR_OOM = 2,     /* device or host allocation failed */
+    PIC_ERR_CUDA = 3,    /* a CUDA runtime call failed (no device, launch error) */
+    PIC_ERR_TIMEOUT = 4, /* a bounded device-side wait expired */
+    PIC_ERR_STATE = 5,   /* call not valid in the handle's current state */
+    PIC_ERR_NUMERIC = 6  /* non-finite particle momentum detected */
+} pic_status;
+
+typedef enum {
+    PIC_BOX_PERIODIC = 0, /* standard periodic PIC */
+    PIC_BOX_SHEAR = 1,    /* KSB-OA shearing box, Sec. 2 */
+    PIC_BOX_EXPAND = 2,   /* KEB expanding box, Sec. 3 */
+    PIC_BOX_LEAKY = 3     /* leaky box, Sec. 4 */
+} pic_box;
+
+enum { PIC_PLANE_XY = 0, PIC_PLANE_XZ = 1 };
+enum { PIC_FP32 = 0, PIC_FP64 = 1 };
+enum { PIC_KEB_CLOSED_FORM = 0, PIC_KEB_EXACT = 1 };
+enum { PIC_ESC_NONE = 0, PIC_ESC_DISPLACEMENT = 1, PIC_ESC_PROBABILISTIC = 2 };
+
+typedef struct pic_config {
+    int32_t box;          /* pic_box */
+    int32_t ndim;         /* 2 or 3 */
+    int32_t plane;        /* 2D only: PIC_PLANE_XY (z ignorable) or PIC_PLANE_XZ (y ignorable) */
+    int32_t nx, ny, nz;   /* cells per axis; the 2D ignorable axis must be 1 */
+    int32_t shape_order;  /* 1 (linear) or 2 (quadratic) particle shapes */
+    int32_t precision;    /* PIC_FP32 (int32 cell + float offset, float u) or PIC_FP64 */
+    int32_t fp_iters;     /* shearing box: fixed-point sweeps of the implicit Maxwell
+                             solve (Sec. 2.2); counts of 3, 4, 7, 8, ... are stable */
+    int32_t keb_push;     /* expanding box: PIC_KEB_CLOSED_FORM (the operator of Sec. 3.2)
+                             or PIC_KEB_EXACT (direct 3x3 solve of its defining equation) */
+    int32_t escape_mode;  /* leaky box: PIC_ESC_* */
+    int32_t escape_dims;  /* leaky displacement test over (x,y) [2] or (x,y,z) [3] */
+    int32_t tile[3];      /* particle tile in cells per axis; 0 = automatic */
+    int32_t reserved0;
+    uint32_t seed;        /* key word of the Philox streams (escape, reinjection, loading) */
+    uint32_t reserved1;
+    double c;             /* Courant number; 0 < c, and c * sqrt(ndim) < 1 */
+    double s_shear;       /* shearing box: s in v_s = -s Omega0 x e_y (3/2 Keplerian) */
+    double Omega0;        /* shearing box: rotation frequency per step */
+    double expand_rate[3];/* expanding box: l_i(t) = exp(expand_rate[i] * t) */
+    double l_esc;         /* leaky box, displacement mode: escape distance in cells */
+    double p_esc;         /* leaky box, probabilistic mode: escape probability per step */
+    double theta_inj;     /* leaky box: temperature k T / m c^2 of the reinjection law */
+    double capacity_slack;/* spare particle slots per tile as a fraction; 0 = 0.3 */
+} pic_config;
+
+typedef struct pic_diag {
+    int64_t step;             /* n: state is at t = n */
+    double t;
+    double shear_shift;       /* Dy_s(t) mod ny (shearing box), cells */
+    double l[3];              /* l_i(t) (expanding box) */
+    double field_energy_E[3]; /* sum over cells of E_c^2 / (8 pi), cell volume 1 */
+    double field_energy_B[3];
+    double kinetic_energy[PIC_MAX_SPECIES]; /* sum of m c^2 (gamma - 1) */
+    int64_t count[PIC_MAX_SPECIES];
+    int64_t escaped_total;    /* leaky box: reinjections since load */
+    int64_t superluminal_total; /* shearing box: |u'/gamma' + v_s| >= c occurrences */
+    int64_t loose;            /* particles currently outside the tile layout (slow path) */
+    int32_t error_word;       /* device error bits (0 = none) */
+    int32_t reserved;
+} pic_diag;
+
+typedef struct pic_profile {
+    double ms_particle;       /* accumulated device time of the fused particle kernels */
+    double ms_field;          /* field solve, guard fill, current fold */
+    double ms_other;          /* loose-particle path, bookkeeping */
+    int64_t launches;         /* kernels launched by the library since the last reset */
+    int64_t particle_launches;
+    int64_t particle_steps;   /* sum over steps of the particle count */
+} pic_profile;
+
+typedef struct pic_handle pic_handle;
+
+/* Library version string and ABI version. */
+const char *pic_version(void);
+int pic_abi_version(void);
+
+/* Validate *cfg, select the current CUDA device, allocate the grid state and
+ * return a new handle in *out (NULL on failure).  Fields start at zero. */
+pic_status pic_init(const pic_config *cfg, pic_handle **out);
+
+/* Release everything the handle owns; h may be NULL. */
+pic_status pic_destroy(pic_handle *h);
+
+/* Text of the last error on h (or of the last failed pic_init when h is NULL). */
+const char *pic_last_error(pic_handle *h);
+
+/* Order all of h's work on `stream` (a cudaStream_t; NULL = the handle's own stream). */
+pic_status pic_set_stream(pic_handle *h, void *stream);
+
+/* Wait for all of h's queued work. */
+pic_status pic_synchronize(pic_handle *h);
+
+/* Load (replacing) species `species` (< PIC_MAX_SPECIES) with n particles of
+ * macro-charge q and macro-mass m from host arrays x[n][3] (cells) and
+ * u[n][3] (cells/step).  id (nullable) gives particle ids (default 0..n-1);
+ * ids key the leaky box's random streams.  Positions are wrapped into the box.
+ * The particle-step order within a tile is not preserved. */
+pic_status pic_load_particles(pic_handle *h, int species, double q, double m, int64_t n,
+                              const double *x, const double *u, const uint32_t *id);
+
+/* Device-side loader: ppc particles per cell, positions uniform in each cell,
+ * momenta isotropic Maxwell-Juettner at temperature theta (k T / m c^2), plus
+ * drift[3] (cells/step) and independent Gaussian noise of deviation
+ * noise_sigma (cells/step) per component.  ids are assigned 0.. in cell order
+ * offset by id_base.  Random numbers come from Philox4x32-10 keyed on
+ * (id, seed). */
+pic_status pic_load_maxwellian(pic_handle *h, int species, double q, double m, int ppc,
+                               double theta, const double drift[3], double noise_sigma,
+                               uint32_t seed, uint32_t id_base);
+
+/* Set E (E' for the shearing box) and B from host arrays [3][nz][ny][nx]. */
+pic_status pic_set_fields(pic_handle *h, const double *E, const double *B);
+
+/* Set uniform E and B (3 components each). */
+pic_status pic_set_uniform_fields(pic_handle *h, const double E[3], const double B[3]);
+
+/* Set the step counter n (time t = n): the time of the state already loaded.
+ * Used to restart a run; the shearing shift Dy_s(t) and the expansion factors
+ * l_i(t) follow from it.  Guard cells are refilled for the new time. */
+pic_status pic_set_step(pic_handle *h, int64_t step);
+
+/* Advance nsteps steps (asynchronous on the handle's stream). */
+pic_status pic_step(pic_handle *h, int nsteps);
+
+/* Synchronize and fill *out with FP64 sums over the current state. */
+pic_status pic_diagnostics(pic_handle *h, pic_diag *out);
+
+/* Number of particles of a species. */
+pic_status pic_get_count(pic_handle *h, int species, int64_t *n);
+
+/* Copy a species to host arrays sized by pic_get_count: x[n][3], u[n][3],
+ * id[n] and dr[n][3] (leaky displacement); each pointer may be NULL.  The
+ * order is the device's tile order; match particles by id. */
+pic_status pic_get_particles(pic_handle *h, int species, double *x, double *u, uint32_t *id,
+                             double *dr);
+
+/* Copy E (E'), B and the current J of the last step (after folding, and for
+ * the shearing box after the y advection) to host arrays [3][nz][ny][nx];
+ * each pointer may be NULL. */
+pic_status pic_get_fields(pic_handle *h, double *E, double *B, double *J);
+
+/* Per-kernel device timing (CUDA events on the handle's stream). */
+pic_status pic_set_profiling(pic_handle *h, int enable);
+pic_status pic_get_profile(pic_handle *h, pic_profile *out);
+pic_status pic_reset_profile(pic_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,208 @@
+// common.cuh -- shared device-side definitions of libpic (CUDA, sm_103a).
+//
+// Grid arrays are padded with guard cells on every active axis: GL = 2 on the
+// low side and at least GR = 3 on the high side (the x pitch is rounded up so
+// that rows start on 16-byte boundaries, as TMA requires).  The 2D ignorable
+// axis has extent 1 and no guards.  Particles are stored per species in SoA
+// arrays, grouped by tile; see particle.cuh.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pic {
+
+constexpr int GL = 2;  // low guard cells
+constexpr int GR = 3;  // high guard cells (deposits reach node n+2)
+
+// geometry kinds: which axes are active
+enum Geom : int { G3D = 0, G2XY = 1, G2XZ = 2 };
+// particle pusher kinds
+enum Push : int { PUSH_BORIS = 0, PUSH_KSB = 1, PUSH_KEB = 2 };
+// escape kinds (leaky box)
+enum Esc : int { ESC_NONE = 0, ESC_DISP = 1, ESC_PROB = 2 };
+
+// device error word bits
+enum : int {
+    ERRB_TMA_TIMEOUT = 1,
+    ERRB_NONFINITE = 2,
+    ERRB_LOOSE_OVERFLOW = 4,
+    ERRB_BAD_CELL = 8,
+};
+
+template <int G> struct GeomT {
+    static constexpr bool AX = true;
+    static constexpr bool AY = (G != G2XZ);
+    static constexpr bool AZ = (G != G2XY);
+    static constexpr int IGN = (G == G2XY) ? 2 : ((G == G2XZ) ? 1 : -1);  // ignorable axis
+};
+
+// Padded grid geometry (element offsets).  cell (i,j,k) -> index
+// ((k+gz)*py + (j+gy))*px + (i+gx).
+struct Grid {
+    int nx, ny, nz;     // physical cells
+    int px, py, pz;     // padded extents
+    int gx, gy, gz;     // low guards per axis (0 on an ignorable axis)
+    long long cstride;  // elements per component (px*py*pz)
+    __host__ __device__ long long idx(int i, int j, int k) const {
+        return ((long long)(k + gz) * py + (j + gy)) * px + (i + gx);
+    }
+};
+
+// ---- packed cell index --------------------------------------------------
+// 3D: i in bits 0..10, j in 11..21, k in 22..31 (nx, ny <= 2048, nz <= 1024).
+// 2D: first active axis in bits 0..15, second in 16..31 (<= 65536 cells each).
+template <int G> struct CellPack {
+    __host__ __device__ static int pack(int i, int j, int k) {
+        if (G == G3D) return (int)((unsigned)i | ((unsigned)j << 11) | ((unsigned)k << 22));
+        if (G == G2XY) return (int)((unsigned)i | ((unsigned)j << 16));
+        return (int)((unsigned)i | ((unsigned)k << 16));
+    }
+    __host__ __device__ static void unpack(int c, int& i, int& j, int& k) {
+        unsigned u = (unsigned)c;
+        if (G == G3D) { i = u & 2047u; j = (u >> 11) & 2047u; k = u >> 22; }
+        else if (G == G2XY) { i = u & 65535u; j = u >> 16; k = 0; }
+        else { i = u & 65535u; k = u >> 16; j = 0; }
+    }
+};
+
+// ---- Philox4x32-10 (Salmon et al., SC'11) --------------------------------
+struct U4 { uint32_t x[4]; };
+
+__host__ __device__ inline U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                             uint32_t k0, uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+#ifdef __CUDA_ARCH__
+        uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
+        uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+#else
+        uint64_t p0 = (uint64_t)M0 * c0, p1 = (uint64_t)M1 * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+        uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += W0; k1 += W1;
+    }
+    U4 r; r.x[0] = c0; r.x[1] = c1; r.x[2] = c2; r.x[3] = c3;
+    return r;
+}
+
+// stream tags (third counter word)
+constexpr uint32_t TAG_ESCAPE = 0x45534350u;  // escape decision
+constexpr uint32_t TAG_ENERGY = 0x494E4A54u;  // reinjection energy attempts
+constexpr uint32_t TAG_DIRECT = 0x44495243u;  // reinjection direction
+constexpr uint32_t TAG_LOADPOS = 0x4C504F53u; // loader: position in cell
+constexpr uint32_t TAG_LOADNOI = 0x4C4E4F49u; // loader: Gaussian noise
+
+__host__ __device__ inline U4 draw(uint32_t id, uint32_t seed, long long step, uint32_t tag, uint32_t w3) {
+    unsigned long long s = (unsigned long long)step;
+    return philox4x32_10((uint32_t)s, (uint32_t)(s >> 32), tag, w3, id, seed);
+}
+
+__host__ __device__ inline double u01(uint32_t v) { return ((double)v + 0.5) * (1.0 / 4294967296.0); }
+
+// Isotropic Maxwell-Juettner momentum (u = c gamma beta) at temperature theta.
+// Kinetic energy e = gamma - 1 has density ~ (1+e) sqrt(e(e+2)) exp(-e/theta),
+// dominated by (sqrt2 e^1/2 + e + sqrt2 e^3/2 + e^2) exp(-e/theta) because
+// sqrt(e+2) <= sqrt2 + sqrt(e): draw from that Gamma mixture, accept with
+// probability sqrt(e+2)/(sqrt2 + sqrt e) >= 1/sqrt2.  At most 64 attempts
+// (the 64th draw is kept).  Computed in FP64 in every precision mode.
+__host__ __device__ inline void sample_mj(uint32_t id, uint32_t seed, long long step, double theta,
+                                          double c, double& ux, double& uy, double& uz) {
+    const double SQ2 = 1.4142135623730951, SQPI = 1.7724538509055159;
+    double w0 = SQ2 * (0.5 * SQPI) * theta * sqrt(theta);
+    double w1 = theta * theta;
+    double w2 = SQ2 * (0.75 * SQPI) * theta * theta * sqrt(theta);
+    double w3 = 2.0 * theta * theta * theta;
+    double wsum = w0 + w1 + w2 + w3;
+    double e = 0.0;
+    for (int a = 0; a < 64; ++a) {
+        U4 r0 = draw(id, seed, step, TAG_ENERGY, 2u * (uint32_t)a);
+        U4 r1 = draw(id, seed, step, TAG_ENERGY, 2u * (uint32_t)a + 1u);
+        double pick = u01(r0.x[0]) * wsum;
+        double x1 = -log(u01(r0.x[1]));
+        double x2 = -log(u01(r0.x[2]));
+        double x3 = -log(u01(r0.x[3]));
+        double cb = cos(6.283185307179586 * u01(r1.x[1]));
+        double hg = -log(u01(r1.x[0])) * cb * cb;
+        if (pick < w0) e = theta * (x1 + hg);
+        else if (pick < w0 + w1) e = theta * (x1 + x2);
+        else if (pick < w0 + w1 + w2) e = theta * (x1 + x2 + hg);
+        else e = theta * (x1 + x2 + x3);
+        if (u01(r1.x[2]) < sqrt(e + 2.0) / (SQ2 + sqrt(e))) break;
+    }
+    U4 rd = draw(id, seed, step, TAG_DIRECT, 0u);
+    double mu = 2.0 * u01(rd.x[0]) - 1.0;
+    double phi = 6.283185307179586 * u01(rd.x[1]);
+    double um = c * sqrt(e * (e + 2.0));
+    double st = sqrt(1.0 - mu * mu);
+    ux = um * st * cos(phi);
+    uy = um * st * sin(phi);
+    uz = um * mu;
+}
+
+// ---- PTX wrappers: mbarrier and TMA ----------------------------------------
+__device__ inline uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ inline void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ inline void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: returns false if the phase did not complete within `limit` polls.
+__device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ inline void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int w, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <class T> __device__ inline void atomic_add_shared(T* p, T v) { atomicAdd(p, v); }
+
+template <class T> __device__ inline void red_add_global(T* p, T v) { atomicAdd(p, v); }
+
+template <class T> __device__ inline T t_floor(T x);
+template <> __device__ inline float t_floor<float>(float x) { return floorf(x); }
+template <> __device__ inline double t_floor<double>(double x) { return floor(x); }
+template <class T> __device__ inline T t_sqrt(T x);
+template <> __device__ inline float t_sqrt<float>(float x) { return sqrtf(x); }
+template <> __device__ inline double t_sqrt<double>(double x) { return sqrt(x); }
+template <class T> __device__ inline T t_abs(T x);
+template <> __device__ inline float t_abs<float>(float x) { return fabsf(x); }
+template <> __device__ inline double t_abs<double>(double x) { return fabs(x); }
+
+}  // namespace pic

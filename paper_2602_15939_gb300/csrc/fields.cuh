@@ -1,0 +1,398 @@
+// fields.cuh -- grid kernels of libpic: Yee curl updates (standard and
+// expanding box), the shearing-box implicit-midpoint sweep, guard-cell fill
+// and current fold with the shearing-periodic shift, the shearing-box
+// current advection, and FP64 reductions.  All kernels work on padded
+// component arrays (see common.cuh); one thread per grid point.
+#pragma once
+
+#include "common.cuh"
+
+namespace pic {
+
+// ---- Yee curl updates ------------------------------------------------------------------
+// out_c <- alpha_c out_c + beta_c curl(sigma (.) in)_c + gam_c J_c over interior cells.
+// CURL_E: curl of an E-located field, result at B locations; else curl of a
+// B-located field, result at E locations.  The ignorable 2D axis contributes no
+// differences.  Standard Yee: alpha = 1, sigma = 1; expanding box: the
+// transforms X' = ell L^-1 X folded into alpha, beta, gam, sigma (Sec. 3.2).
+struct Coef3 { double a[3], b[3], g[3], s[3]; };
+
+template <class T, int G, bool CURL_E>
+__global__ void curl_update_kernel(Grid g, const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ J, Coef3 cf) {
+    using GT = GeomT<G>;
+    long long n = (long long)g.nx * g.ny * g.nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(q % g.nx);
+        long long r = q / g.nx;
+        int j = (int)(r % g.ny);
+        int k = (int)(r / g.ny);
+        long long c0 = g.idx(i, j, k);
+        const long long sx = 1, sy = g.px, sz = (long long)g.px * g.py, cs = g.cstride;
+        const T* X = in;
+        const T* Y = in + cs;
+        const T* Z = in + 2 * cs;
+        T s0 = T(cf.s[0]), s1 = T(cf.s[1]), s2 = T(cf.s[2]);
+        T cu[3];
+        if (CURL_E) {
+            // (curl E)_x = dy Ez - dz Ey, (curl E)_y = dz Ex - dx Ez, (curl E)_z = dx Ey - dy Ex, forward differences
+            T dyEz = GT::AY ? s2 * (Z[c0 + sy] - Z[c0]) : T(0);
+            T dzEy = GT::AZ ? s1 * (Y[c0 + sz] - Y[c0]) : T(0);
+            T dzEx = GT::AZ ? s0 * (X[c0 + sz] - X[c0]) : T(0);
+            T dxEz = s2 * (Z[c0 + sx] - Z[c0]);
+            T dxEy = s1 * (Y[c0 + sx] - Y[c0]);
+            T dyEx = GT::AY ? s0 * (X[c0 + sy] - X[c0]) : T(0);
+            cu[0] = dyEz - dzEy;
+            cu[1] = dzEx - dxEz;
+            cu[2] = dxEy - dyEx;
+        } else {
+            // backward differences
+            T dyBz = GT::AY ? s2 * (Z[c0] - Z[c0 - sy]) : T(0);
+            T dzBy = GT::AZ ? s1 * (Y[c0] - Y[c0 - sz]) : T(0);
+            T dzBx = GT::AZ ? s0 * (X[c0] - X[c0 - sz]) : T(0);
+            T dxBz = s2 * (Z[c0] - Z[c0 - sx]);
+            T dxBy = s1 * (Y[c0] - Y[c0 - sx]);
+            T dyBx = GT::AY ? s0 * (X[c0] - X[c0 - sy]) : T(0);
+            cu[0] = dyBz - dzBy;
+            cu[1] = dzBx - dxBz;
+            cu[2] = dxBy - dyBx;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            T v = T(cf.a[c]) * out[c * cs + c0] + T(cf.b[c]) * cu[c];
+            if (J) v += T(cf.g[c]) * J[c * cs + c0];
+            out[c * cs + c0] = v;
+        }
+    }
+}
+
+// ---- shearing-box implicit-midpoint sweep ---------------------------------------------
+// X_out = X_n + dt F((X_n + X_k)/2), F the right-hand sides of the KSB-OA
+// field equations (Sec. 2.1) with V(x) = -s Omega0 (x - nx/2):
+//   F_B  = -c curl E' - V dy B - s Omega0 Bx e_y
+//   F_Ex = c (curl B)_x - 4 pi J'_x + V dy E'_x - V dx E'_y
+//   F_Ey = c (curl B)_y - 4 pi J'_y - V dy E'_y - V (dx E'_x + dz E'_z)
+//   F_Ez = c (curl B)_z - 4 pi J'_z + V dy E'_z - V dz E'_y
+// The advection term of each component is upwinded for its own transport
+// velocity (V in the B and E'_y rows, -V in the E'_x and E'_z rows); the
+// other V-terms are centred and averaged in y onto the component's location;
+// Bx in the By row is the mean of its four neighbours.  Guards of X_n and X_k
+// hold the shearing-periodic images at t^{n+1/2}.
+template <class T, int G>
+__global__ void ksb_sweep_kernel(Grid g, const T* __restrict__ En, const T* __restrict__ Bn, const T* __restrict__ Ek,
+                                 const T* __restrict__ Bk, const T* __restrict__ J, T* __restrict__ Eo, T* __restrict__ Bo,
+                                 double c_, double sO_, double half_nx) {
+    using GT = GeomT<G>;
+    const T c = T(c_), sO = T(sO_);
+    const T FOUR_PI = T(12.566370614359172);
+    long long n = (long long)g.nx * g.ny * g.nz;
+    const long long sx = 1, sy = GT::AY ? g.px : 0, sz = GT::AZ ? (long long)g.px * g.py : 0, cs = g.cstride;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(q % g.nx);
+        long long r = q / g.nx;
+        int j = (int)(r % g.ny);
+        int k = (int)(r / g.ny);
+        long long c0 = g.idx(i, j, k);
+        // midpoint fields
+        auto ME = [&](int comp, long long off) -> T { return T(0.5) * (En[comp * cs + c0 + off] + Ek[comp * cs + c0 + off]); };
+        auto MB = [&](int comp, long long off) -> T { return T(0.5) * (Bn[comp * cs + c0 + off] + Bk[comp * cs + c0 + off]); };
+        const T VN = -sO * T((double)i - half_nx);
+        const T VH = -sO * T((double)i + 0.5 - half_nx);
+        // curls (ignorable-axis differences vanish because its stride is 0)
+        T curlEx = (ME(2, sy) - ME(2, 0)) - (ME(1, sz) - ME(1, 0));
+        T curlEy = (ME(0, sz) - ME(0, 0)) - (ME(2, sx) - ME(2, 0));
+        T curlEz = (ME(1, sx) - ME(1, 0)) - (ME(0, sy) - ME(0, 0));
+        T curlBx = (MB(2, 0) - MB(2, -sy)) - (MB(1, 0) - MB(1, -sz));
+        T curlBy = (MB(0, 0) - MB(0, -sz)) - (MB(2, 0) - MB(2, -sx));
+        T curlBz = (MB(1, 0) - MB(1, -sx)) - (MB(0, 0) - MB(0, -sy));
+        auto upB = [&](int comp, T v) -> T { return v > T(0) ? MB(comp, 0) - MB(comp, -sy) : MB(comp, sy) - MB(comp, 0); };
+        auto upE = [&](int comp, T v) -> T { return v > T(0) ? ME(comp, 0) - ME(comp, -sy) : ME(comp, sy) - ME(comp, 0); };
+        T bx4 = T(0.25) * (MB(0, 0) + MB(0, sx) + MB(0, -sy) + MB(0, sx - sy));
+        T FBx = -c * curlEx - VN * upB(0, VN);
+        T FBy = -c * curlEy - VH * upB(1, VH) - sO * bx4;
+        T FBz = -c * curlEz - VH * upB(2, VH);
+        T dxEy = T(0.5) * ((ME(1, sx) - ME(1, 0)) + (ME(1, sx - sy) - ME(1, -sy)));
+        T divxz = T(0.5) * ((ME(0, 0) - ME(0, -sx)) + (ME(0, sy) - ME(0, sy - sx)) + (ME(2, 0) - ME(2, -sz)) +
+                            (ME(2, sy) - ME(2, sy - sz)));
+        T dzEy = T(0.5) * ((ME(1, sz) - ME(1, 0)) + (ME(1, sz - sy) - ME(1, -sy)));
+        T FEx = c * curlBx - FOUR_PI * J[c0] + VH * upE(0, -VH) - VH * dxEy;
+        T FEy = c * curlBy - FOUR_PI * J[cs + c0] - VN * upE(1, VN) - VN * divxz;
+        T FEz = c * curlBz - FOUR_PI * J[2 * cs + c0] + VN * upE(2, -VN) - VN * dzEy;
+        Eo[c0] = En[c0] + FEx;
+        Eo[cs + c0] = En[cs + c0] + FEy;
+        Eo[2 * cs + c0] = En[2 * cs + c0] + FEz;
+        Bo[c0] = Bn[c0] + FBx;
+        Bo[cs + c0] = Bn[cs + c0] + FBy;
+        Bo[2 * cs + c0] = Bn[2 * cs + c0] + FBz;
+    }
+}
+
+// ---- guard fill -----------------------------------------------------------------------
+// Axis passes: x first (interior y, z rows; with the shear shift dys for the
+// shearing box: the ghost at (i >= nx, j) is the interior value at
+// (i - nx, j + dys), linearly interpolated, and at (i < 0, j) the one at
+// (i + nx, j - dys)), then y over all padded x, then z over all padded x, y.
+template <class T, int G>
+__global__ void fill_x_kernel(Grid g, T* F, int ncomp, int dys_i, double dys_f) {
+    using GT = GeomT<G>;
+    const int nguard = g.px - g.nx;  // gx low + the rest high
+    long long n = (long long)ncomp * nguard * g.ny * g.nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int gi = (int)(q % nguard);
+        long long r = q / nguard;
+        int j = (int)(r % g.ny);
+        r /= g.ny;
+        int k = (int)(r % g.nz);
+        int comp = (int)(r / g.nz);
+        int i = gi < g.gx ? gi - g.gx : g.nx + (gi - g.gx);  // physical ghost index
+        int w = i < 0 ? -1 : 1;
+        int is = i - w * g.nx;
+        T* Fc = F + (long long)comp * g.cstride;
+        T v;
+        if (GT::AY && (dys_i != 0 || dys_f != 0.0)) {
+            // y + w dys = j + w (dys_i + dys_f)
+            int m;
+            double f;
+            if (w > 0) { m = dys_i; f = dys_f; }
+            else { m = -dys_i; f = -dys_f; if (f < 0.0) { f += 1.0; m -= 1; } }
+            int j0 = j + m, j1 = j0 + 1;
+            j0 %= g.ny; if (j0 < 0) j0 += g.ny;
+            j1 %= g.ny; if (j1 < 0) j1 += g.ny;
+            v = T(1.0 - f) * Fc[g.idx(is, j0, k)] + T(f) * Fc[g.idx(is, j1, k)];
+        } else {
+            v = Fc[g.idx(is, j, k)];
+        }
+        Fc[g.idx(i, j, k)] = v;
+    }
+}
+
+template <class T>
+__global__ void fill_y_kernel(Grid g, T* F, int ncomp) {
+    const int nguard = g.py - g.ny;
+    long long n = (long long)ncomp * nguard * g.px * g.nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int pi = (int)(q % g.px);
+        long long r = q / g.px;
+        int gj = (int)(r % nguard);
+        r /= nguard;
+        int k = (int)(r % g.nz);
+        int comp = (int)(r / g.nz);
+        int j = gj < g.gy ? gj - g.gy : g.ny + (gj - g.gy);
+        int js = j < 0 ? j + g.ny : j - g.ny;
+        T* Fc = F + (long long)comp * g.cstride;
+        long long row = (long long)(k + g.gz) * g.py;
+        Fc[(row + j + g.gy) * g.px + pi] = Fc[(row + js + g.gy) * g.px + pi];
+    }
+}
+
+template <class T>
+__global__ void fill_z_kernel(Grid g, T* F, int ncomp) {
+    const int nguard = g.pz - g.nz;
+    long long plane = (long long)g.px * g.py;
+    long long n = (long long)ncomp * nguard * plane;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        long long pp = q % plane;
+        long long r = q / plane;
+        int gk = (int)(r % nguard);
+        int comp = (int)(r / nguard);
+        int k = gk < g.gz ? gk - g.gz : g.nz + (gk - g.gz);
+        int ks = k < 0 ? k + g.nz : k - g.nz;
+        T* Fc = F + (long long)comp * g.cstride;
+        Fc[(long long)(k + g.gz) * plane + pp] = Fc[(long long)(ks + g.gz) * plane + pp];
+    }
+}
+
+// ---- current fold (adjoint of the fill) ------------------------------------------------
+// Pull form: each interior point near a boundary adds the guard values that
+// map onto it.  Order z, y (over all padded x), then x with the shear shift at
+// t^{n+1/2}: a guard value at (i >= nx, j) belongs at (i - nx, j + dys), split
+// (1 - f, f) between rows floor and floor + 1; at (i < 0, j) at (i + nx, j - dys).
+template <class T>
+__global__ void fold_z_kernel(Grid g, T* F) {
+    long long plane = (long long)g.px * g.py;
+    const int band = g.pz - g.nz;  // receiving interior planes: k in [0, gzh) and [nz - gz, nz)
+    long long n = 3ll * band * plane;
+    const int gzh = g.pz - g.gz - g.nz;  // high guards
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        long long pp = q % plane;
+        long long r = q / plane;
+        int b = (int)(r % band);
+        int comp = (int)(r / band);
+        T* Fc = F + (long long)comp * g.cstride;
+        int k;  // receiving interior plane
+        T add = T(0);
+        if (b < gzh) {
+            k = b;  // from high guard nz + b
+            add += Fc[(long long)(g.nz + b + g.gz) * plane + pp];
+        } else {
+            k = g.nz - g.gz + (b - gzh);  // from low guard k - nz
+            add += Fc[(long long)(k - g.nz + g.gz) * plane + pp];
+        }
+        Fc[(long long)(k + g.gz) * plane + pp] += add;
+    }
+}
+
+template <class T>
+__global__ void fold_y_kernel(Grid g, T* F) {
+    const int band = g.py - g.ny;
+    const int gyh = g.py - g.gy - g.ny;
+    long long n = 3ll * band * g.px * g.nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int pi = (int)(q % g.px);
+        long long r = q / g.px;
+        int b = (int)(r % band);
+        r /= band;
+        int k = (int)(r % g.nz);
+        int comp = (int)(r / g.nz);
+        T* Fc = F + (long long)comp * g.cstride;
+        long long row = (long long)(k + g.gz) * g.py;
+        int j;
+        T add;
+        if (b < gyh) { j = b; add = Fc[(row + g.ny + b + g.gy) * g.px + pi]; }
+        else { j = g.ny - g.gy + (b - gyh); add = Fc[(row + j - g.ny + g.gy) * g.px + pi]; }
+        Fc[(row + j + g.gy) * g.px + pi] += add;
+    }
+}
+
+template <class T, int G>
+__global__ void fold_x_kernel(Grid g, T* F, int dys_i, double dys_f) {
+    using GT = GeomT<G>;
+    const int band = g.px - g.nx;
+    const int gxh = g.px - g.gx - g.nx;
+    long long n = 3ll * band * g.ny * g.nz;
+    const bool sh = GT::AY && (dys_i != 0 || dys_f != 0.0);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int b = (int)(q % band);
+        long long r = q / band;
+        int j = (int)(r % g.ny);
+        r /= g.ny;
+        int k = (int)(r % g.nz);
+        int comp = (int)(r / g.nz);
+        T* Fc = F + (long long)comp * g.cstride;
+        int i, is, w;  // receiving interior column, source ghost column, side
+        if (b < gxh) { i = b; is = g.nx + b; w = 1; }
+        else { i = g.nx - g.gx + (b - gxh); is = i - g.nx; w = -1; }
+        T add;
+        if (sh) {
+            // sources: ghost rows js with floor(js + w dys) = j (weight 1-f) or j - 1 (weight f)
+            int m;
+            double f;
+            if (w > 0) { m = dys_i; f = dys_f; }
+            else { m = -dys_i; f = -dys_f; if (f < 0.0) { f += 1.0; m -= 1; } }
+            int ja = j - m, jb = j - m - 1;
+            ja %= g.ny; if (ja < 0) ja += g.ny;
+            jb %= g.ny; if (jb < 0) jb += g.ny;
+            add = T(1.0 - f) * Fc[g.idx(is, ja, k)] + T(f) * Fc[g.idx(is, jb, k)];
+        } else {
+            add = Fc[g.idx(is, j, k)];
+        }
+        Fc[g.idx(i, j, k)] += add;
+    }
+}
+
+// Shearing box: advect J' along y by v_{s,y} dt / 2 = -s Omega0 x dt / 2 per x
+// column (x of each component's location from the box centre), linear
+// interpolation, periodic in y: Jn(j) = (1-f) J(j0) + f J(j0+1), j - d = j0 + f.
+template <class T>
+__global__ void ksb_advect_kernel(Grid g, const T* __restrict__ Jin, T* __restrict__ Jout, double sO, double half_nx) {
+    long long n = 3ll * g.nx * g.ny * g.nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(q % g.nx);
+        long long r = q / g.nx;
+        int j = (int)(r % g.ny);
+        r /= g.ny;
+        int k = (int)(r % g.nz);
+        int comp = (int)(r / g.nz);
+        double xc = (double)i + (comp == 0 ? 0.5 : 0.0) - half_nx;
+        double d = -sO * xc * 0.5;
+        double ys = (double)j - d;
+        double y0 = floor(ys);
+        double f = ys - y0;
+        int j0 = (int)y0 % g.ny; if (j0 < 0) j0 += g.ny;
+        int j1 = j0 + 1; if (j1 >= g.ny) j1 -= g.ny;
+        const T* Jc = Jin + (long long)comp * g.cstride;
+        Jout[(long long)comp * g.cstride + g.idx(i, j, k)] = T(1.0 - f) * Jc[g.idx(i, j0, k)] + T(f) * Jc[g.idx(i, j1, k)];
+    }
+}
+
+// ---- host <-> padded layout -----------------------------------------------------------
+template <class T>
+__global__ void scatter_field_kernel(Grid g, const double* __restrict__ src, T* __restrict__ dst) {
+    long long n = 3ll * g.nx * g.ny * g.nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(q % g.nx);
+        long long r = q / g.nx;
+        int j = (int)(r % g.ny);
+        r /= g.ny;
+        int k = (int)(r % g.nz);
+        int comp = (int)(r / g.nz);
+        dst[(long long)comp * g.cstride + g.idx(i, j, k)] = T(src[q]);
+    }
+}
+
+template <class T>
+__global__ void gather_field_kernel(Grid g, const T* __restrict__ src, double* __restrict__ dst) {
+    long long n = 3ll * g.nx * g.ny * g.nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(q % g.nx);
+        long long r = q / g.nx;
+        int j = (int)(r % g.ny);
+        r /= g.ny;
+        int k = (int)(r % g.nz);
+        int comp = (int)(r / g.nz);
+        dst[q] = (double)src[(long long)comp * g.cstride + g.idx(i, j, k)];
+    }
+}
+
+template <class T>
+__global__ void uniform_field_kernel(Grid g, T* dst, double v0, double v1, double v2) {
+    long long n = 3ll * g.cstride;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int comp = (int)(q / g.cstride);
+        dst[q] = T(comp == 0 ? v0 : (comp == 1 ? v1 : v2));
+    }
+}
+
+// ---- FP64 reductions -------------------------------------------------------------------
+// Sum of squares of each component over interior cells: block partials in
+// `partial` ([gridDim.x][3]), then one block adds them (deterministic order).
+template <class T>
+__global__ void sumsq_partial_kernel(Grid g, const T* __restrict__ F, double* __restrict__ partial) {
+    __shared__ double red[3][32];
+    double acc[3] = {0.0, 0.0, 0.0};
+    long long n = (long long)g.nx * g.ny * g.nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(q % g.nx);
+        long long r = q / g.nx;
+        int j = (int)(r % g.ny);
+        int k = (int)(r / g.ny);
+        long long c0 = g.idx(i, j, k);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double v = (double)F[c * g.cstride + c0];
+            acc[c] += v * v;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double v = acc[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+        partial[blockIdx.x * 3 + threadIdx.x] = s;
+    }
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ partial, int nblocks, int width, double* __restrict__ out) {
+    // one thread per output column, sequential over blocks: deterministic
+    int c = threadIdx.x;
+    if (c >= width) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partial[b * width + c];
+    out[c] = s;
+}
+
+}  // namespace pic

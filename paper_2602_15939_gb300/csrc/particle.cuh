@@ -1,0 +1,780 @@
+// particle.cuh -- the fused particle step of libpic (CUDA, sm_103a).
+//
+// One CTA owns one tile of cells.  It stages the tile's E and B (plus guard
+// cells) into shared memory with two TMA copies, then, for every particle of
+// every species in the tile:
+//   gather E, B at x^n (shape order 1 or 2, each component at its own Yee
+//   location) -> push (Boris; KSB-OA Boris-like, Sec. 2.2; KEB modified Boris,
+//   Sec. 3.2) -> position update (two-stage for the shearing box) ->
+//   charge-conserving (Esirkepov) current into a shared-memory J tile ->
+//   leaky-box escape test and reinjection (Sec. 4.1) -> write the particle to
+//   its slot in the tile-sorted output buffer.
+// Particles that stay in the tile are packed at the front of the tile's slot
+// range (warp-aggregated shared-memory counter); particles that move to a
+// neighbouring tile are appended at the back of that tile's range through a
+// global counter.  A particle whose destination tile has no free slot goes to
+// a "loose" list handled by loose_kernel (global-memory gather and atomics),
+// which re-inserts it as soon as room appears.  After all particles, the J
+// tile is added to the global (guarded) J array with one atomic per non-zero
+// point.
+#pragma once
+
+#include "common.cuh"
+
+namespace pic {
+
+// ---- kernel arguments --------------------------------------------------------
+
+template <class T> struct PView {
+    int* cell;
+    T* o[3];   // in-cell offsets of the active axes (o[2] unused in 2D)
+    T* u[3];
+    uint32_t* id;
+    T* dr[3];  // leaky-box displacement (null otherwise)
+};
+
+template <class T> struct SpecStep {
+    PView<T> in, out;      // tile-sorted buffers
+    PView<T> lin, lout;    // loose lists
+    const int* stay_in;    // [ntiles]
+    int* arr_in;           // [ntiles], zeroed by the kernel after reading
+    int* stay_out;         // [ntiles]
+    int* arr_out;          // [ntiles], must be zero on entry
+    const int* lcount_in;  // loose count of lin
+    int* lcount_out;       // loose count of lout (atomic)
+    long long tcap;        // slots per tile
+    long long lcap;        // loose-list capacity
+    T qdt2m;               // q dt / (2 m)
+    T qdt2mc;              // q dt / (2 m c)
+    T q;                   // macro charge
+};
+
+constexpr int MAXSP = 4;
+
+template <class T> struct SpecPack { SpecStep<T> s[MAXSP]; };
+
+struct Tiling {
+    int tx, ty, tz;     // tile extent (cells) per axis, 1 on the ignorable axis
+    int ntx, nty, ntz;  // tiles per axis
+    int ntiles;
+    int bx, by, bz;     // staged field box (elements)
+    int xalign;         // TMA x quantum (elements)
+    int jx, jy, jz;     // shared J box (points)
+};
+
+struct StepP {
+    double c;
+    long long step;
+    int nsp;
+    int keb_exact;
+    // shearing box
+    double sO;          // s Omega0
+    double Omega0;
+    double half_nx;     // box centre
+    int dys_end_i;      // floor of Dy_s(t^{n+1}) mod ny
+    double dys_end_f;   // fractional part
+    // expanding box
+    double Lam[3];      // -(dt/2) L^{-1} dL/dt
+    double inv_lh[3];   // 1 / l_i(t^{n+1/2})
+    // leaky box
+    double l_esc;
+    uint32_t esc_thresh;
+    uint32_t seed;
+    double theta_inj;
+    int esc_dims;
+    int* err;
+    unsigned long long* counters;  // [0] escaped, [1] superluminal
+};
+
+// ---- shapes --------------------------------------------------------------------
+// Weights on ORD+1 consecutive grid points starting at cell + off, for a
+// particle at offset o in [0,1) of that cell: node-centred ("n") or
+// half-staggered ("s") quantities.
+template <class T, int ORD> struct Shape;
+
+template <class T> struct Shape<T, 1> {
+    __device__ static void node(T o, int& off, T w[2]) { off = 0; w[0] = T(1) - o; w[1] = o; }
+    __device__ static void stag(T o, int& off, T w[2]) {
+        T f;
+        if (o >= T(0.5)) { off = 0; f = o - T(0.5); } else { off = -1; f = o + T(0.5); }
+        w[0] = T(1) - f; w[1] = f;
+    }
+    // node shape on a window [wb, wb+3) for a position x relative to the cell origin
+    __device__ static void window(T x, int wb, T w[4]) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            T d = t_abs<T>(x - T(wb + m));
+            w[m] = d < T(1) ? T(1) - d : T(0);
+        }
+    }
+};
+
+template <class T> struct Shape<T, 2> {
+    __device__ static void q3(T d, T w[3]) {
+        T a = T(0.5) - d, b = T(0.5) + d;
+        w[0] = T(0.5) * a * a; w[1] = T(0.75) - d * d; w[2] = T(0.5) * b * b;
+    }
+    __device__ static void node(T o, int& off, T w[3]) {
+        T d;
+        if (o >= T(0.5)) { off = 0; d = o - T(1); } else { off = -1; d = o; }
+        q3(d, w);
+    }
+    __device__ static void stag(T o, int& off, T w[3]) { off = -1; q3(o - T(0.5), w); }
+    __device__ static void window(T x, int wb, T w[4]) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            T d = t_abs<T>(x - T(wb + m));
+            w[m] = d <= T(0.5) ? T(0.75) - d * d : (d < T(1.5) ? T(0.5) * (T(1.5) - d) * (T(1.5) - d) : T(0));
+        }
+    }
+};
+
+// ---- field accessors -------------------------------------------------------------
+
+// Shared-memory field boxes: E and B, 3 components each, [comp][bz][by][bx].
+template <class T> struct SmemFields {
+    const T* e;
+    const T* b;
+    int bx, by, bz;
+    __device__ T get(int comp, int i, int j, int k) const {
+        const T* f = comp < 3 ? e : b;
+        const int c = comp < 3 ? comp : comp - 3;
+        return f[((c * bz + k) * by + j) * bx + i];
+    }
+};
+
+// Global padded fields.
+template <class T> struct GlobalFields {
+    const T* E;
+    const T* B;
+    Grid g;
+    __device__ T get(int comp, int i, int j, int k) const {
+        // (i,j,k) are padded indices here
+        const T* base = comp < 3 ? E + (long long)comp * g.cstride : B + (long long)(comp - 3) * g.cstride;
+        return __ldg(base + ((long long)k * g.py + j) * g.px + i);
+    }
+};
+
+template <class T> struct SmemJ {
+    T* j;
+    int jx, jy, jz;
+    __device__ void add(int comp, int i, int j_, int k, T v) const {
+        atomic_add_shared(&j[((comp * jz + k) * jy + j_) * jx + i], v);
+    }
+};
+
+template <class T> struct GlobalJ {
+    T* J;
+    Grid g;
+    __device__ void add(int comp, int i, int j_, int k, T v) const {
+        red_add_global(J + (long long)comp * g.cstride + ((long long)k * g.py + j_) * g.px + i, v);
+    }
+};
+
+// ---- gather ------------------------------------------------------------------------
+// (li, lj, lk): the particle's cell in the accessor's index space; o: offsets.
+template <class T, int G, int ORD, class F>
+__device__ inline void gather(const F& fa, int li, int lj, int lk, const T o[3], T Ep[3], T Bp[3]) {
+    using GT = GeomT<G>;
+    constexpr int NP = ORD + 1;
+    T wn[3][NP], ws[3][NP];
+    int offn[3], offs[3];
+    Shape<T, ORD>::node(o[0], offn[0], wn[0]);
+    Shape<T, ORD>::stag(o[0], offs[0], ws[0]);
+    if (GT::AY) { Shape<T, ORD>::node(o[1], offn[1], wn[1]); Shape<T, ORD>::stag(o[1], offs[1], ws[1]); }
+    if (GT::AZ) { Shape<T, ORD>::node(o[2], offn[2], wn[2]); Shape<T, ORD>::stag(o[2], offs[2], ws[2]); }
+    // components: E x,y,z then B x,y,z; stag[comp][axis]
+    constexpr bool ST[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+    T out[6];
+#pragma unroll
+    for (int comp = 0; comp < 6; ++comp) {
+        const T* wx = ST[comp][0] ? ws[0] : wn[0];
+        const int ox = ST[comp][0] ? offs[0] : offn[0];
+        T acc = T(0);
+        if (GT::AY && GT::AZ) {
+            const T* wy = ST[comp][1] ? ws[1] : wn[1];
+            const T* wz = ST[comp][2] ? ws[2] : wn[2];
+            const int oy = ST[comp][1] ? offs[1] : offn[1];
+            const int oz = ST[comp][2] ? offs[2] : offn[2];
+#pragma unroll
+            for (int c = 0; c < NP; ++c)
+#pragma unroll
+                for (int b = 0; b < NP; ++b) {
+                    T wyz = wy[b] * wz[c];
+                    T row = T(0);
+#pragma unroll
+                    for (int a = 0; a < NP; ++a) row += wx[a] * fa.get(comp, li + ox + a, lj + oy + b, lk + oz + c);
+                    acc += wyz * row;
+                }
+        } else {
+            constexpr int A2 = GT::AY ? 1 : 2;  // second active axis
+            const T* w2 = ST[comp][A2] ? ws[A2] : wn[A2];
+            const int o2 = ST[comp][A2] ? offs[A2] : offn[A2];
+#pragma unroll
+            for (int b = 0; b < NP; ++b) {
+                T row = T(0);
+#pragma unroll
+                for (int a = 0; a < NP; ++a) {
+                    if (A2 == 1) row += wx[a] * fa.get(comp, li + ox + a, lj + o2 + b, lk);
+                    else row += wx[a] * fa.get(comp, li + ox + a, lj, lk + o2 + b);
+                }
+                acc += w2[b] * row;
+            }
+        }
+        out[comp] = acc;
+    }
+    Ep[0] = out[0]; Ep[1] = out[1]; Ep[2] = out[2];
+    Bp[0] = out[3]; Bp[1] = out[4]; Bp[2] = out[5];
+}
+
+// ---- pushers ------------------------------------------------------------------------
+
+template <class T> __device__ inline void cross(const T a[3], const T b[3], T r[3]) {
+    r[0] = a[1] * b[2] - a[2] * b[1];
+    r[1] = a[2] * b[0] - a[0] * b[2];
+    r[2] = a[0] * b[1] - a[1] * b[0];
+}
+template <class T> __device__ inline T dot(const T a[3], const T b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// nu x t + (nu x t) x t, divided by 1 + t^2, times k: the rotation part of
+// the Boris (k = 2) and half-Boris (k = 1) operators of Sec. 2.2.
+template <class T> __device__ inline void rot(const T nu[3], const T t[3], T k_over_den, T out[3]) {
+    T a[3], b[3];
+    cross(nu, t, a);
+    cross(a, t, b);
+    out[0] = nu[0] + k_over_den * (a[0] + b[0]);
+    out[1] = nu[1] + k_over_den * (a[1] + b[1]);
+    out[2] = nu[2] + k_over_den * (a[2] + b[2]);
+}
+
+// Standard Boris push with gamma at u^-.
+template <class T> __device__ inline void push_boris(T u[3], const T E[3], const T B[3], T qdt2m, T qdt2mc, T inv_c2) {
+    T eps[3] = {qdt2m * E[0], qdt2m * E[1], qdt2m * E[2]};
+    T um[3] = {u[0] + eps[0], u[1] + eps[1], u[2] + eps[2]};
+    T g = t_sqrt<T>(T(1) + dot(um, um) * inv_c2);
+    T ig = T(1) / g;
+    T tau[3] = {qdt2mc * B[0] * ig, qdt2mc * B[1] * ig, qdt2mc * B[2] * ig};
+    T up[3];
+    rot(um, tau, T(2) / (T(1) + dot(tau, tau)), up);
+    u[0] = up[0] + eps[0]; u[1] = up[1] + eps[1]; u[2] = up[2] + eps[2];
+}
+
+// Shearing-box (KSB-OA) push of Sec. 2.2.  xc: x^n from the box centre.
+template <class T>
+__device__ inline void push_ksb(T u[3], const T E[3], const T B[3], T qdt2m, T qdt2mc, T c, T sO, T Om, T xc) {
+    T eps[3] = {qdt2m * E[0], qdt2m * E[1], qdt2m * E[2]};
+    T um[3] = {u[0] + eps[0], u[1] + eps[1], u[2] + eps[2]};
+    T a1 = sO * T(0.5);
+    T a2 = sO * xc / c;
+    T ic2 = T(1) / (c * c);
+    // gbar: root >= 1 of g^3 - A g - C = 0 (the Lorentz-factor relation of Sec. 2.2)
+    T u2 = dot(um, um), ue = dot(um, eps);
+    T A = T(1) + (u2 + T(2) * a1 * um[0] * um[1]) * ic2;
+    T Cc = T(2) * a2 * ue * um[1] * ic2;
+    T gm = t_sqrt<T>(T(1) + u2 * ic2);
+    T g = gm + (a1 * um[0] * um[1] * gm + a2 * ue * um[1]) * ic2 / (gm * gm);
+    // Newton: converged for FP64, two corrections for FP32 (quadratic convergence
+    // from an O(Omega0^2)-accurate start)
+    const int NIT = sizeof(T) == 8 ? 8 : 2;
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+        T f = (g * g - A) * g - Cc;
+        T df = T(3) * g * g - A;
+        g -= f / df;
+    }
+    T ig = T(1) / g;
+    T et[3] = {eps[0] * ig / c, eps[1] * ig / c, eps[2] * ig / c};
+    T tt[3] = {qdt2mc * B[0] * ig, qdt2mc * B[1] * ig, qdt2mc * B[2] * ig + Om};
+    T den = T(1) / (T(1) + dot(tt, tt));
+    T S2[3] = {a1 + a2 * et[0], a2 * et[1], a2 * et[2]};
+    // R(e_y) and g = S2 . R(e_y)
+    T ey[3] = {T(0), T(1), T(0)}, Rey[3];
+    rot(ey, tt, den, Rey);
+    T gg = dot(S2, Rey);
+    // w = B(u-) + R(S u-) ; S v = (S2.v) e_y, so R(S v) = (S2.v) R(e_y)
+    T w[3];
+    rot(um, tt, T(2) * den, w);
+    T su = dot(S2, um);
+    w[0] += su * Rey[0]; w[1] += su * Rey[1]; w[2] += su * Rey[2];
+    T sw = dot(S2, w) / (T(1) - gg);
+    u[0] = w[0] + sw * Rey[0] + eps[0];
+    u[1] = w[1] + sw * Rey[1] + eps[1];
+    u[2] = w[2] + sw * Rey[2] + eps[2];
+}
+
+// Expanding-box modified Boris push of Sec. 3.2 (diagonal Lambda), or the
+// direct 3x3 solve of its defining equation when exact != 0.
+template <class T>
+__device__ inline void push_keb(T u[3], const T E[3], const T B[3], T qdt2m, T qdt2mc, T inv_c2, const T Lam[3], bool exact) {
+    T eps[3] = {qdt2m * E[0], qdt2m * E[1], qdt2m * E[2]};
+    T um[3] = {u[0] + eps[0], u[1] + eps[1], u[2] + eps[2]};
+    T lu[3] = {(T(1) + Lam[0]) * um[0], (T(1) + Lam[1]) * um[1], (T(1) + Lam[2]) * um[2]};
+    T g = t_sqrt<T>(T(1) + dot(lu, lu) * inv_c2);
+    T ig = T(1) / g;
+    T tau[3] = {qdt2mc * B[0] * ig, qdt2mc * B[1] * ig, qdt2mc * B[2] * ig};
+    T up[3];
+    if (!exact) {
+        T tt[3], Lt[3], a[3], ax[3], bx[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            T im = T(1) / (T(1) - Lam[i]);
+            tt[i] = tau[i] * im;
+            Lt[i] = (T(1) + Lam[i]) * im;
+            a[i] = (T(1) + Lt[i]) * um[i];
+        }
+        T den = T(1) / (T(1) + dot(tt, tt));
+        cross(a, tt, ax);
+        cross(ax, tt, bx);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) up[i] = Lt[i] * um[i] + (ax[i] + bx[i]) * den;
+    } else {
+        // (I - Lambda - T) u+ = (I + Lambda + T) u-, T v = v x tau
+        T r[3];
+        cross(um, tau, r);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) r[i] += (T(1) + Lam[i]) * um[i];
+        T M[3][3] = {{T(1) - Lam[0], -tau[2], tau[1]}, {tau[2], T(1) - Lam[1], -tau[0]}, {-tau[1], tau[0], T(1) - Lam[2]}};
+        T det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+        T id = T(1) / det;
+#pragma unroll
+        for (int col = 0; col < 3; ++col) {
+            T A_[3][3];
+#pragma unroll
+            for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) A_[rr][cc] = (cc == col) ? r[rr] : M[rr][cc];
+            T d = A_[0][0] * (A_[1][1] * A_[2][2] - A_[1][2] * A_[2][1]) - A_[0][1] * (A_[1][0] * A_[2][2] - A_[1][2] * A_[2][0]) +
+                  A_[0][2] * (A_[1][0] * A_[2][1] - A_[1][1] * A_[2][0]);
+            up[col] = d * id;
+        }
+    }
+    u[0] = up[0] + eps[0]; u[1] = up[1] + eps[1]; u[2] = up[2] + eps[2];
+}
+
+// ---- charge-conserving deposit (Esirkepov) -------------------------------------------
+// The particle moves from x0 = o (offsets in its start cell) to x1 = o + d,
+// |d| < 1 per axis.  With S0, S1 the node shapes on a 4-point window starting
+// at node wb (relative to the start cell), W_x = dS_x * F_yz with
+// F_yz = S0y S0z + dSy S0z / 2 + S0y dSz / 2 + dSy dSz / 3, so the running sum
+// J_x(l + 1/2) = -q sum_{l' <= l} W_x(l') = -q CS_x(l) F_yz.  On the 2D
+// ignorable axis the current is q v F of the two active axes.
+template <class T, int G, int ORD, class JA>
+__device__ inline void deposit(const JA& ja, int li, int lj, int lk, const T o[3], const T d[3], T q) {
+    using GT = GeomT<G>;
+    T S0[3][4], S1[3][4], DS[3][4], CS[3][4];
+    int wb[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if ((a == 1 && !GT::AY) || (a == 2 && !GT::AZ)) continue;
+        T x1 = o[a] + d[a];
+        // lowest node that can carry weight for either position
+        if (ORD == 1) {
+            wb[a] = x1 < T(0) ? -1 : 0;
+        } else {
+            int n0 = o[a] >= T(0.5) ? 1 : 0;
+            int n1 = (int)t_floor<T>(x1 + T(0.5));
+            wb[a] = (n0 < n1 ? n0 : n1) - 1;
+        }
+        Shape<T, ORD>::window(o[a], wb[a], S0[a]);
+        Shape<T, ORD>::window(x1, wb[a], S1[a]);
+        T run = T(0);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            DS[a][m] = S1[a][m] - S0[a][m];
+            run += DS[a][m];
+            CS[a][m] = run;
+        }
+    }
+    constexpr int NW = ORD + 2;  // window points that can be non-zero: 3 (order 1), 4 (order 2)
+    const T third = T(1) / T(3);
+    if (GT::AY && GT::AZ) {
+        // J_x
+#pragma unroll
+        for (int n = 0; n < NW; ++n)
+#pragma unroll
+            for (int m = 0; m < NW; ++m) {
+                T fyz = S0[1][m] * S0[2][n] + T(0.5) * (DS[1][m] * S0[2][n] + S0[1][m] * DS[2][n]) + third * DS[1][m] * DS[2][n];
+                if (fyz != T(0)) {
+#pragma unroll
+                    for (int l = 0; l < NW - 1; ++l)
+                        if (CS[0][l] != T(0)) ja.add(0, li + wb[0] + l, lj + wb[1] + m, lk + wb[2] + n, -q * CS[0][l] * fyz);
+                }
+            }
+        // J_y
+#pragma unroll
+        for (int n = 0; n < NW; ++n)
+#pragma unroll
+            for (int l = 0; l < NW; ++l) {
+                T fxz = S0[0][l] * S0[2][n] + T(0.5) * (DS[0][l] * S0[2][n] + S0[0][l] * DS[2][n]) + third * DS[0][l] * DS[2][n];
+                if (fxz != T(0)) {
+#pragma unroll
+                    for (int m = 0; m < NW - 1; ++m)
+                        if (CS[1][m] != T(0)) ja.add(1, li + wb[0] + l, lj + wb[1] + m, lk + wb[2] + n, -q * CS[1][m] * fxz);
+                }
+            }
+        // J_z
+#pragma unroll
+        for (int m = 0; m < NW; ++m)
+#pragma unroll
+            for (int l = 0; l < NW; ++l) {
+                T fxy = S0[0][l] * S0[1][m] + T(0.5) * (DS[0][l] * S0[1][m] + S0[0][l] * DS[1][m]) + third * DS[0][l] * DS[1][m];
+                if (fxy != T(0)) {
+#pragma unroll
+                    for (int n = 0; n < NW - 1; ++n)
+                        if (CS[2][n] != T(0)) ja.add(2, li + wb[0] + l, lj + wb[1] + m, lk + wb[2] + n, -q * CS[2][n] * fxy);
+                }
+            }
+    } else {
+        constexpr int A2 = GT::AY ? 1 : 2;   // second active axis
+        constexpr int IG = GT::AY ? 2 : 1;   // ignorable axis
+        // in-plane components
+#pragma unroll
+        for (int m = 0; m < NW; ++m) {
+            T f2 = S0[A2][m] + T(0.5) * DS[A2][m];
+            if (f2 != T(0)) {
+#pragma unroll
+                for (int l = 0; l < NW - 1; ++l)
+                    if (CS[0][l] != T(0)) {
+                        if (A2 == 1) ja.add(0, li + wb[0] + l, lj + wb[1] + m, lk, -q * CS[0][l] * f2);
+                        else ja.add(0, li + wb[0] + l, lj, lk + wb[2] + m, -q * CS[0][l] * f2);
+                    }
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < NW; ++l) {
+            T f1 = S0[0][l] + T(0.5) * DS[0][l];
+            if (f1 != T(0)) {
+#pragma unroll
+                for (int m = 0; m < NW - 1; ++m)
+                    if (CS[A2][m] != T(0)) {
+                        if (A2 == 1) ja.add(1, li + wb[0] + l, lj + wb[1] + m, lk, -q * CS[A2][m] * f1);
+                        else ja.add(2, li + wb[0] + l, lj, lk + wb[2] + m, -q * CS[A2][m] * f1);
+                    }
+            }
+        }
+        // out-of-plane component: q v_ign F(x, a2)
+        T qv = q * d[IG];
+        if (qv != T(0)) {
+#pragma unroll
+            for (int m = 0; m < NW; ++m)
+#pragma unroll
+                for (int l = 0; l < NW; ++l) {
+                    T f = S0[0][l] * S0[A2][m] + T(0.5) * (DS[0][l] * S0[A2][m] + S0[0][l] * DS[A2][m]) + third * DS[0][l] * DS[A2][m];
+                    if (f != T(0)) {
+                        if (A2 == 1) ja.add(IG, li + wb[0] + l, lj + wb[1] + m, lk, qv * f);
+                        else ja.add(IG, li + wb[0] + l, lj, lk + wb[2] + m, qv * f);
+                    }
+                }
+        }
+    }
+}
+
+// ---- one particle ---------------------------------------------------------------------
+
+template <class T> struct Particle {
+    int ci, cj, ck;  // physical cell
+    T o[3];
+    T u[3];
+    uint32_t id;
+    T dr[3];
+};
+
+template <class T, int G> __device__ inline void load_particle(const PView<T>& v, long long s, bool leaky, Particle<T>& p) {
+    using GT = GeomT<G>;
+    CellPack<G>::unpack(v.cell[s], p.ci, p.cj, p.ck);
+    p.o[0] = v.o[0][s];
+    p.o[1] = GT::AY ? v.o[1][s] : T(0.5);
+    p.o[2] = GT::AZ ? v.o[GT::AY ? 2 : 1][s] : T(0.5);
+    p.u[0] = v.u[0][s]; p.u[1] = v.u[1][s]; p.u[2] = v.u[2][s];
+    p.id = v.id[s];
+    if (leaky) { p.dr[0] = v.dr[0][s]; p.dr[1] = v.dr[1][s]; p.dr[2] = v.dr[2][s]; }
+    else { p.dr[0] = p.dr[1] = p.dr[2] = T(0); }
+}
+
+template <class T, int G> __device__ inline void store_particle(const PView<T>& v, long long s, bool leaky, const Particle<T>& p) {
+    using GT = GeomT<G>;
+    v.cell[s] = CellPack<G>::pack(p.ci, p.cj, p.ck);
+    v.o[0][s] = p.o[0];
+    if (GT::AY) v.o[1][s] = p.o[1];
+    if (GT::AZ) v.o[GT::AY ? 2 : 1][s] = p.o[2];
+    v.u[0][s] = p.u[0]; v.u[1][s] = p.u[1]; v.u[2][s] = p.u[2];
+    v.id[s] = p.id;
+    if (leaky) { v.dr[0][s] = p.dr[0]; v.dr[1][s] = p.dr[1]; v.dr[2][s] = p.dr[2]; }
+}
+
+// Normalise offset o (possibly outside [0,1)) into [0,1), moving the cell.
+template <class T> __device__ inline void renorm(T& o, int& c) {
+    T f = t_floor<T>(o);
+    int df = (int)f;
+    o -= f;
+    if (o >= T(1)) { o = T(0); df += 1; }  // -tiny + 1 rounded up to 1
+    c += df;
+}
+
+// Push, move and deposit one particle; returns its destination physical cell
+// in p.  FA: field accessor, JA: current accumulator; (fi,fj,fk) and
+// (ji,jj,jk) are the particle's start cell in their index spaces.
+template <class T, int G, int ORD, int PUSH, int ESC, class FA, class JA>
+__device__ inline void advance_particle(Particle<T>& p, const FA& fa, int fi, int fj, int fk, const JA& ja, int ji, int jj,
+                                        int jk, const SpecStep<T>& S, const StepP& P, const Grid& g) {
+    using GT = GeomT<G>;
+    T E[3], B[3];
+    gather<T, G, ORD>(fa, fi, fj, fk, p.o, E, B);
+    const T c = T(P.c);
+    const T inv_c2 = T(1) / (c * c);
+    T d[3];
+    T xc0 = T(0);
+    if (PUSH == PUSH_KSB) {
+        xc0 = T((double)p.ci - P.half_nx) + p.o[0];
+        push_ksb<T>(p.u, E, B, S.qdt2m, S.qdt2mc, c, T(P.sO), T(P.Omega0), xc0);
+    } else if (PUSH == PUSH_KEB) {
+        T Lam[3] = {T(P.Lam[0]), T(P.Lam[1]), T(P.Lam[2])};
+        push_keb<T>(p.u, E, B, S.qdt2m, S.qdt2mc, inv_c2, Lam, P.keb_exact != 0);
+    } else {
+        push_boris<T>(p.u, E, B, S.qdt2m, S.qdt2mc, inv_c2);
+    }
+    T ig = T(1) / t_sqrt<T>(T(1) + dot(p.u, p.u) * inv_c2);
+    d[0] = p.u[0] * ig; d[1] = p.u[1] * ig; d[2] = p.u[2] * ig;
+    if (PUSH == PUSH_KEB) { d[0] *= T(P.inv_lh[0]); d[1] *= T(P.inv_lh[1]); d[2] *= T(P.inv_lh[2]); }
+    if (!(d[0] == d[0]) || !(d[1] == d[1]) || !(d[2] == d[2])) {
+        atomicOr(P.err, ERRB_NONFINITE);
+        d[0] = d[1] = d[2] = T(0);
+    }
+    // current from the (comoving) displacement x^n -> x^n + d
+    deposit<T, G, ORD>(ja, ji, jj, jk, p.o, d, S.q);
+
+    if (ESC == ESC_DISP) { p.dr[0] += d[0]; p.dr[1] += d[1]; p.dr[2] += d[2]; }
+
+    // new position
+    T nx_ = p.o[0] + d[0];
+    T ny_ = p.o[1] + d[1];
+    T nz_ = p.o[2] + d[2];
+    if (PUSH == PUSH_KSB) {
+        // x^{n+1} = x' - s Omega0 (x' + x^n)/2 dt e_y (Sec. 2.2)
+        T xc1 = T((double)p.ci - P.half_nx) + nx_;
+        T vs = T(P.sO) * (xc1 + xc0) * T(0.5);
+        {
+            // superluminal effective velocity u'/gamma' + v_s (counted, not corrected)
+            T vy = d[1] - T(P.sO) * xc0;
+            if (d[0] * d[0] + vy * vy + d[2] * d[2] >= c * c) atomicAdd(P.counters + 1, 1ull);
+        }
+        ny_ -= vs;
+    }
+    p.o[0] = nx_; renorm(p.o[0], p.ci);
+    if (GT::AY) { p.o[1] = ny_; renorm(p.o[1], p.cj); } else { p.o[1] = T(0.5); }
+    if (GT::AZ) { p.o[2] = nz_; renorm(p.o[2], p.ck); } else { p.o[2] = T(0.5); }
+    // periodic / shearing-periodic wrap
+    if (p.ci >= g.nx) {
+        p.ci -= g.nx;
+        if (PUSH == PUSH_KSB && GT::AY) {
+            p.cj += P.dys_end_i;
+            p.o[1] += T(P.dys_end_f);
+            renorm(p.o[1], p.cj);
+        }
+    } else if (p.ci < 0) {
+        p.ci += g.nx;
+        if (PUSH == PUSH_KSB && GT::AY) {
+            p.cj -= P.dys_end_i;
+            p.o[1] -= T(P.dys_end_f);
+            renorm(p.o[1], p.cj);
+        }
+    }
+    if (GT::AY) {
+        if (p.cj >= g.ny) p.cj -= g.ny;
+        if (p.cj >= g.ny) p.cj -= g.ny;
+        if (p.cj < 0) p.cj += g.ny;
+        if (p.cj < 0) p.cj += g.ny;
+    }
+    if (GT::AZ) { if (p.ck >= g.nz) p.ck -= g.nz; else if (p.ck < 0) p.ck += g.nz; }
+
+    if (ESC != ESC_NONE) {
+        bool esc;
+        if (ESC == ESC_DISP) {
+            T m = t_abs<T>(p.dr[0]);
+            T ay = t_abs<T>(p.dr[1]);
+            m = ay > m ? ay : m;
+            if (P.esc_dims == 3) { T az = t_abs<T>(p.dr[2]); m = az > m ? az : m; }
+            esc = m >= T(P.l_esc);
+        } else {
+            U4 r = draw(p.id, P.seed, P.step, TAG_ESCAPE, 0u);
+            esc = r.x[0] < P.esc_thresh;
+        }
+        if (esc) {
+            double ux, uy, uz;
+            sample_mj(p.id, P.seed, P.step, P.theta_inj, P.c, ux, uy, uz);
+            p.u[0] = T(ux); p.u[1] = T(uy); p.u[2] = T(uz);
+            p.dr[0] = p.dr[1] = p.dr[2] = T(0);
+            atomicAdd(P.counters, 1ull);
+        }
+    }
+}
+
+
+template <int G> __device__ inline int tile_of(const Tiling& tl, int ci, int cj, int ck) {
+    using GT = GeomT<G>;
+    int a = ci / tl.tx;
+    int b = GT::AY ? cj / tl.ty : 0;
+    int cc = GT::AZ ? ck / tl.tz : 0;
+    return a + tl.ntx * (b + tl.nty * cc);
+}
+
+// Put a particle that left its tile into the arrival range (the back of the
+// slot range) of tile `dest`.  Slots below the tile's start-of-step count may
+// be taken by its stayers, so the k-th arrival (slot tcap-1-k) is valid only
+// above it; otherwise the particle joins the loose list.  Failed claims
+// over-count arr_out; finalize_kernel clamps it to the valid range.
+template <class T, int G>
+__device__ inline void place_mover(const Particle<T>& p, int dest, const SpecStep<T>& S, const StepP& P, bool leaky) {
+    int cnt_in = S.stay_in[dest] + S.arr_in[dest];
+    int k = atomicAdd(S.arr_out + dest, 1);
+    long long rel = S.tcap - 1 - k;
+    if (rel >= cnt_in) {
+        store_particle<T, G>(S.out, (long long)dest * S.tcap + rel, leaky, p);
+        return;
+    }
+    int l = atomicAdd(S.lcount_out, 1);
+    if (l < S.lcap) store_particle<T, G>(S.lout, l, leaky, p);
+    else atomicOr(P.err, ERRB_LOOSE_OVERFLOW);
+}
+
+constexpr int TPB = 256;
+constexpr long long TMA_WAIT_LIMIT = 1ll << 24;
+
+// Dynamic shared memory: E box, B box (each 128-byte aligned, the TMA
+// destinations), the J box, the mbarrier and small counters.
+template <class T> struct SmemLayout {
+    int FB, JB;
+    size_t off_B, off_J, off_bar, bytes;
+    __host__ __device__ SmemLayout(const Tiling& tl) {
+        FB = tl.bx * tl.by * tl.bz;
+        JB = tl.jx * tl.jy * tl.jz;
+        off_B = ((size_t)3 * FB * sizeof(T) + 127) & ~(size_t)127;
+        off_J = off_B + (size_t)3 * FB * sizeof(T);
+        off_J = (off_J + 127) & ~(size_t)127;
+        off_bar = off_J + (size_t)3 * JB * sizeof(T);
+        off_bar = (off_bar + 15) & ~(size_t)15;
+        bytes = off_bar + 16 + 4 * (MAXSP + 2);
+    }
+};
+
+// The fused particle step for one tile (see the file header).
+template <class T, int G, int ORD, int PUSH, int ESC>
+__global__ void __launch_bounds__(TPB) tile_kernel(const __grid_constant__ CUtensorMap tmE,
+                                                   const __grid_constant__ CUtensorMap tmB, Grid g, Tiling tl,
+                                                   StepP P, SpecPack<T> SP, T* __restrict__ J) {
+    using GT = GeomT<G>;
+    constexpr bool LEAKY = (ESC == ESC_DISP);
+    extern __shared__ __align__(128) unsigned char smem[];
+    const SmemLayout<T> L(tl);
+    T* sE = reinterpret_cast<T*>(smem);
+    T* sB = reinterpret_cast<T*>(smem + L.off_B);
+    T* sJ = reinterpret_cast<T*>(smem + L.off_J);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bar);
+    int* s_cnt = reinterpret_cast<int*>(smem + L.off_bar + 16);
+    int* s_ok = s_cnt + MAXSP;
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int t = blockIdx.x;
+    const int ti = t % tl.ntx, tj = (t / tl.ntx) % tl.nty, tk = t / (tl.ntx * tl.nty);
+    const int t0x = ti * tl.tx, t0y = tj * tl.ty, t0z = tk * tl.tz;
+    // padded coordinate of physical t0 - 2 is t0 (GL = 2); x rounded down to the TMA quantum
+    const int xs = t0x & ~(tl.xalign - 1);
+    const int ys = GT::AY ? t0y : 0;
+    const int zs = GT::AZ ? t0z : 0;
+
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(bar, (uint32_t)(6 * L.FB * sizeof(T)));
+        tma_load_4d(sE, &tmE, xs, ys, zs, 0, bar);
+        tma_load_4d(sB, &tmB, xs, ys, zs, 0, bar);
+    }
+    for (int i = tid; i < 3 * L.JB; i += blockDim.x) sJ[i] = T(0);
+    if (tid < MAXSP) s_cnt[tid] = 0;
+    if (tid == 0) s_ok[0] = mbar_wait_bounded(bar, 0, TMA_WAIT_LIMIT) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok[0]) {
+        if (tid == 0) atomicOr(P.err, ERRB_TMA_TIMEOUT);
+        return;
+    }
+
+    const SmemFields<T> fa{sE, sB, tl.bx, tl.by, tl.bz};
+    const SmemJ<T> ja{sJ, tl.jx, tl.jy, tl.jz};
+    // index-space origins (physical cell of local index 0)
+    const int fox = xs - 2, foy = GT::AY ? t0y - 2 : 0, foz = GT::AZ ? t0z - 2 : 0;
+    const int jox = t0x - 2, joy = GT::AY ? t0y - 2 : 0, joz = GT::AZ ? t0z - 2 : 0;
+
+    for (int s = 0; s < P.nsp; ++s) {
+        const SpecStep<T>& S = SP.s[s];
+        const int nst = S.stay_in[t], nar = S.arr_in[t];
+        const int n = nst + nar;
+        const long long base = (long long)t * S.tcap;
+        for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+            const int i = i0 + tid;
+            const bool valid = i < n;
+            Particle<T> p;
+            int dest = -1;
+            if (valid) {
+                const long long slot = i < nst ? base + i : base + S.tcap - nar + (i - nst);
+                load_particle<T, G>(S.in, slot, LEAKY, p);
+                advance_particle<T, G, ORD, PUSH, ESC>(p, fa, p.ci - fox, GT::AY ? p.cj - foy : 0,
+                                                       GT::AZ ? p.ck - foz : 0, ja, p.ci - jox,
+                                                       GT::AY ? p.cj - joy : 0, GT::AZ ? p.ck - joz : 0, S, P, g);
+                dest = tile_of<G>(tl, p.ci, p.cj, p.ck);
+            }
+            const bool stay = valid && dest == t;
+            const unsigned m = __ballot_sync(0xffffffffu, stay);
+            int wb = 0;
+            if (lane == 0 && m) wb = atomicAdd(&s_cnt[s], __popc(m));
+            wb = __shfl_sync(0xffffffffu, wb, 0);
+            if (stay) store_particle<T, G>(S.out, base + wb + __popc(m & ((1u << lane) - 1u)), LEAKY, p);
+            else if (valid) place_mover<T, G>(p, dest, S, P, LEAKY);
+        }
+    }
+    __syncthreads();
+    // flush the J tile: padded index of local point (a,b,c) is (t0x + a, t0y + b, t0z + c)
+    for (int idx = tid; idx < 3 * L.JB; idx += blockDim.x) {
+        T v = sJ[idx];
+        if (v == T(0)) continue;
+        int comp = idx / L.JB;
+        int r = idx - comp * L.JB;
+        int a = r % tl.jx;
+        int b = (r / tl.jx) % tl.jy;
+        int c = r / (tl.jx * tl.jy);
+        const int pi = jox + g.gx + a, pj = joy + g.gy + b, pk = joz + g.gz + c;
+        if (pi >= g.px || pj >= g.py || pk >= g.pz) continue;  // beyond a ragged last tile: never deposited
+        long long gi = (long long)comp * g.cstride + ((long long)pk * g.py + pj) * g.px + pi;
+        red_add_global(J + gi, v);
+    }
+    if (tid < P.nsp) SP.s[tid].stay_out[t] = s_cnt[tid];
+}
+
+// Loose particles: the same per-particle step with fields read from global
+// memory and the current added with global atomics; afterwards each particle
+// is inserted into its tile like any mover, or stays loose.
+template <class T, int G, int ORD, int PUSH, int ESC>
+__global__ void __launch_bounds__(TPB) loose_kernel(Grid g, Tiling tl, StepP P, SpecPack<T> SP,
+                                                    const T* __restrict__ E, const T* __restrict__ B, T* __restrict__ J) {
+    using GT = GeomT<G>;
+    constexpr bool LEAKY = (ESC == ESC_DISP);
+    const GlobalFields<T> fa{E, B, g};
+    const GlobalJ<T> ja{J, g};
+    for (int s = 0; s < P.nsp; ++s) {
+        const SpecStep<T>& S = SP.s[s];
+        long long n = *S.lcount_in;
+        if (n > S.lcap) n = S.lcap;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+            Particle<T> p;
+            load_particle<T, G>(S.lin, i, LEAKY, p);
+            const int pi = p.ci + g.gx, pj = GT::AY ? p.cj + g.gy : 0, pk = GT::AZ ? p.ck + g.gz : 0;
+            advance_particle<T, G, ORD, PUSH, ESC>(p, fa, pi, pj, pk, ja, pi, pj, pk, S, P, g);
+            place_mover<T, G>(p, tile_of<G>(tl, p.ci, p.cj, p.ck), S, P, LEAKY);
+        }
+    }
+}
+
+}  // namespace pic

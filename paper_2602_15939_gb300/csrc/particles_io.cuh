@@ -1,0 +1,224 @@
+// particles_io.cuh -- loading, re-binning and read-back of tile-sorted
+// particles, plus per-step counter bookkeeping and the kinetic-energy sum.
+// None of this is on the per-step hot path except finalize_kernel.
+#pragma once
+
+#include "particle.cuh"
+
+namespace pic {
+
+// Wrap an absolute coordinate into [0, n) and split it into cell + offset.
+template <class T> __device__ inline void split_coord(double x, int n, int& c, T& o) {
+    double w = x - floor(x / (double)n) * (double)n;
+    if (w >= (double)n) w -= (double)n;
+    if (w < 0.0) w = 0.0;
+    double f = floor(w);
+    c = (int)f;
+    if (c >= n) c = n - 1;
+    double r = w - f;
+    o = T(r);
+    if (o >= T(1)) { o = T(0); c += 1; if (c >= n) c = 0; }
+}
+
+// Pass 1 of a load: per particle, its tile; per tile, a count.
+template <class T, int G>
+__global__ void load_bin_kernel(long long n, const double* __restrict__ x, Tiling tl, Grid g, int* __restrict__ tile_of_p,
+                                int* __restrict__ count) {
+    using GT = GeomT<G>;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        int ci, cj = 0, ck = 0;
+        T o;
+        split_coord<T>(x[3 * q + 0], g.nx, ci, o);
+        if (GT::AY) split_coord<T>(x[3 * q + 1], g.ny, cj, o);
+        if (GT::AZ) split_coord<T>(x[3 * q + 2], g.nz, ck, o);
+        int t = tile_of<G>(tl, ci, cj, ck);
+        tile_of_p[q] = t;
+        atomicAdd(count + t, 1);
+    }
+}
+
+// Pass 2: write each particle to a slot of its tile (order within a tile is
+// arbitrary).
+template <class T, int G>
+__global__ void load_scatter_kernel(long long n, const double* __restrict__ x, const double* __restrict__ u,
+                                    const uint32_t* __restrict__ id, const double* __restrict__ dr, Grid g,
+                                    const int* __restrict__ tile_of_p, int* __restrict__ fill, long long tcap, PView<T> v,
+                                    bool has_dr) {
+    using GT = GeomT<G>;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        Particle<T> p;
+        p.cj = 0; p.ck = 0;
+        split_coord<T>(x[3 * q + 0], g.nx, p.ci, p.o[0]);
+        if (GT::AY) split_coord<T>(x[3 * q + 1], g.ny, p.cj, p.o[1]); else p.o[1] = T(0.5);
+        if (GT::AZ) split_coord<T>(x[3 * q + 2], g.nz, p.ck, p.o[2]); else p.o[2] = T(0.5);
+        p.u[0] = T(u[3 * q]); p.u[1] = T(u[3 * q + 1]); p.u[2] = T(u[3 * q + 2]);
+        p.id = id ? id[q] : (uint32_t)q;
+        if (has_dr) {
+            p.dr[0] = dr ? T(dr[3 * q]) : T(0);
+            p.dr[1] = dr ? T(dr[3 * q + 1]) : T(0);
+            p.dr[2] = dr ? T(dr[3 * q + 2]) : T(0);
+        }
+        int t = tile_of_p[q];
+        int s = atomicAdd(fill + t, 1);
+        store_particle<T, G>(v, (long long)t * tcap + s, has_dr, p);
+    }
+}
+
+// Device Maxwellian loader: slot r of tile t holds particle r of the tile's
+// cells in order, ppc per cell.  Positions uniform in the cell, momenta
+// Maxwell-Juettner(theta) + drift + Gaussian noise (Box-Muller), all from
+// Philox keyed on (id, seed).
+template <class T, int G>
+__global__ void maxwellian_kernel(Tiling tl, Grid g, int ppc, double theta, double c, double dx_, double dy_, double dz_,
+                                  double noise, uint32_t seed, uint32_t id_base, long long tcap, PView<T> v, bool has_dr,
+                                  int* __restrict__ count) {
+    using GT = GeomT<G>;
+    const int t = blockIdx.x;
+    const int ti = t % tl.ntx, tj = (t / tl.ntx) % tl.nty, tk = t / (tl.ntx * tl.nty);
+    const int t0x = ti * tl.tx, t0y = tj * tl.ty, t0z = tk * tl.tz;
+    const int ex = min(tl.tx, g.nx - t0x), ey = GT::AY ? min(tl.ty, g.ny - t0y) : 1, ez = GT::AZ ? min(tl.tz, g.nz - t0z) : 1;
+    const int ncell = ex * ey * ez;
+    const int n = ncell * ppc;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        int lc = r / ppc, pc = r % ppc;
+        int a = lc % ex, b = (lc / ex) % ey, cc = lc / (ex * ey);
+        Particle<T> p;
+        p.ci = t0x + a; p.cj = GT::AY ? t0y + b : 0; p.ck = GT::AZ ? t0z + cc : 0;
+        long long cell_lin = ((long long)p.ck * g.ny + p.cj) * g.nx + p.ci;
+        p.id = id_base + (uint32_t)(cell_lin * ppc + pc);
+        U4 rp = draw(p.id, seed, 0, TAG_LOADPOS, 0u);
+        p.o[0] = T(u01(rp.x[0]));
+        p.o[1] = GT::AY ? T(u01(rp.x[1])) : T(0.5);
+        p.o[2] = GT::AZ ? T(u01(rp.x[2])) : T(0.5);
+        if (p.o[0] >= T(1)) p.o[0] = T(0);
+        if (p.o[1] >= T(1)) p.o[1] = T(0);
+        if (p.o[2] >= T(1)) p.o[2] = T(0);
+        double ux = 0.0, uy = 0.0, uz = 0.0;
+        if (theta > 0.0) sample_mj(p.id, seed, 0, theta, c, ux, uy, uz);
+        ux += dx_; uy += dy_; uz += dz_;
+        if (noise > 0.0) {
+            U4 rn = draw(p.id, seed, 0, TAG_LOADNOI, 0u);
+            double r1 = sqrt(-2.0 * log(u01(rn.x[0]))), r2 = sqrt(-2.0 * log(u01(rn.x[2])));
+            double a1 = 6.283185307179586 * u01(rn.x[1]), a2 = 6.283185307179586 * u01(rn.x[3]);
+            ux += noise * r1 * cos(a1);
+            uy += noise * r1 * sin(a1);
+            uz += noise * r2 * cos(a2);
+        }
+        p.u[0] = T(ux); p.u[1] = T(uy); p.u[2] = T(uz);
+        p.dr[0] = p.dr[1] = p.dr[2] = T(0);
+        store_particle<T, G>(v, (long long)t * tcap + r, has_dr, p);
+    }
+    if (threadIdx.x == 0) count[t] = n;
+}
+
+// Copy tile t's particles (front and back segments) to double arrays at
+// offset off[t]: absolute positions, momenta, ids, displacements.
+template <class T, int G>
+__global__ void compact_kernel(Tiling tl, Grid g, PView<T> v, const int* __restrict__ stay, const int* __restrict__ arr,
+                               long long tcap, const long long* __restrict__ off, bool has_dr, double* __restrict__ x,
+                               double* __restrict__ u, uint32_t* __restrict__ id, double* __restrict__ dr) {
+    const int t = blockIdx.x;
+    const int nst = stay[t], nar = arr[t];
+    const long long base = (long long)t * tcap;
+    for (int i = threadIdx.x; i < nst + nar; i += blockDim.x) {
+        long long slot = i < nst ? base + i : base + tcap - nar + (i - nst);
+        Particle<T> p;
+        load_particle<T, G>(v, slot, has_dr, p);
+        long long o = off[t] + i;
+        if (x) {
+            x[3 * o + 0] = (double)p.ci + (double)p.o[0];
+            x[3 * o + 1] = (double)p.cj + (double)p.o[1];
+            x[3 * o + 2] = (double)p.ck + (double)p.o[2];
+        }
+        if (u) { u[3 * o] = (double)p.u[0]; u[3 * o + 1] = (double)p.u[1]; u[3 * o + 2] = (double)p.u[2]; }
+        if (id) id[o] = p.id;
+        if (dr) {
+            dr[3 * o] = has_dr ? (double)p.dr[0] : 0.0;
+            dr[3 * o + 1] = has_dr ? (double)p.dr[1] : 0.0;
+            dr[3 * o + 2] = has_dr ? (double)p.dr[2] : 0.0;
+        }
+    }
+}
+
+template <class T, int G>
+__global__ void compact_loose_kernel(PView<T> v, const int* __restrict__ lcount, long long lcap, long long off0, bool has_dr,
+                                     double* __restrict__ x, double* __restrict__ u, uint32_t* __restrict__ id,
+                                     double* __restrict__ dr) {
+    long long n = *lcount;
+    if (n > lcap) n = lcap;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        Particle<T> p;
+        load_particle<T, G>(v, i, has_dr, p);
+        long long o = off0 + i;
+        if (x) {
+            x[3 * o + 0] = (double)p.ci + (double)p.o[0];
+            x[3 * o + 1] = (double)p.cj + (double)p.o[1];
+            x[3 * o + 2] = (double)p.ck + (double)p.o[2];
+        }
+        if (u) { u[3 * o] = (double)p.u[0]; u[3 * o + 1] = (double)p.u[1]; u[3 * o + 2] = (double)p.u[2]; }
+        if (id) id[o] = p.id;
+        if (dr) {
+            dr[3 * o] = has_dr ? (double)p.dr[0] : 0.0;
+            dr[3 * o + 1] = has_dr ? (double)p.dr[1] : 0.0;
+            dr[3 * o + 2] = has_dr ? (double)p.dr[2] : 0.0;
+        }
+    }
+}
+
+// After the particle kernels of a step: clamp each tile's arrival count to
+// the claims that got a slot (failed claims over-count), clamp the loose
+// count to the list capacity, and zero the counters of the consumed buffer,
+// which the next step writes.
+__global__ void finalize_kernel(int ntiles, long long tcap, const int* __restrict__ stay_in, int* __restrict__ arr_in,
+                                       int* __restrict__ arr_out, int* __restrict__ lcount_in, int* __restrict__ lcount_out,
+                                       long long lcap, int* err) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+        int room = (int)(tcap - (stay_in[t] + arr_in[t]));
+        if (arr_out[t] > room) arr_out[t] = room;
+        arr_in[t] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (*lcount_out > lcap) { atomicOr(err, ERRB_LOOSE_OVERFLOW); *lcount_out = (int)lcap; }
+        *lcount_in = 0;
+    }
+}
+
+// Sum of m c^2 (gamma - 1) over the tile-sorted particles and the loose list.
+template <class T, int G>
+__global__ void kinetic_kernel(Tiling tl, PView<T> v, const int* __restrict__ stay, const int* __restrict__ arr, long long tcap,
+                               PView<T> lv, const int* __restrict__ lcount, long long lcap, double c, double m,
+                               double* __restrict__ partial) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    const double ic2 = 1.0 / (c * c);
+    for (int t = blockIdx.x; t < tl.ntiles + 1; t += gridDim.x) {
+        if (t < tl.ntiles) {
+            const int nst = stay[t], nar = arr[t];
+            const long long base = (long long)t * tcap;
+            for (int i = threadIdx.x; i < nst + nar; i += blockDim.x) {
+                long long slot = i < nst ? base + i : base + tcap - nar + (i - nst);
+                double ux = v.u[0][slot], uy = v.u[1][slot], uz = v.u[2][slot];
+                double u2 = (ux * ux + uy * uy + uz * uz) * ic2;
+                acc += m * c * c * (u2 / (sqrt(1.0 + u2) + 1.0));
+            }
+        } else {
+            long long n = *lcount;
+            if (n > lcap) n = lcap;
+            for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+                double ux = lv.u[0][i], uy = lv.u[1][i], uz = lv.u[2][i];
+                double u2 = (ux * ux + uy * uy + uz * uz) * ic2;
+                acc += m * c * c * (u2 / (sqrt(1.0 + u2) + 1.0));
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        partial[blockIdx.x] = s;
+    }
+}
+
+}  // namespace pic

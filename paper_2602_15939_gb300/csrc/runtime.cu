@@ -1,0 +1,1030 @@
+// runtime.cu -- host runtime of libpic: the C ABI declared in include/pic.h.
+//
+// A handle owns one box: padded field arrays (E, B, J, scratch), the tile
+// layout, and per species double-buffered SoA particle arrays in tile order.
+// pic_step enqueues, per step: the fused particle kernel (one CTA per tile),
+// the loose-particle kernel, counter bookkeeping, the current fold (with the
+// shearing-periodic shift), the shearing-box current advection, and the box's
+// field update with guard fills, all on the handle's stream.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "dispatch.h"
+#include "fields.cuh"
+#include "particles_io.cuh"
+
+using namespace pic;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+constexpr int NTHR = 256;
+
+struct DevSpecies {
+    bool loaded = false;
+    double q = 0, m = 1;
+    long long n = 0;     // particles loaded
+    long long tcap = 0;  // slots per tile
+    long long lcap = 0;  // loose capacity
+    // [buffer][array]: cell, o0, o1, o2, u0, u1, u2, id, d0, d1, d2
+    void* arr[2][11] = {};
+    void* larr[2][11] = {};
+    int* stay[2] = {};
+    int* arrv[2] = {};
+    int* lcount = nullptr;  // [2]
+};
+
+struct EvPair {
+    cudaEvent_t a, b;
+    int cat;  // 0 particle, 1 other, 2 field
+};
+
+struct Prof {
+    bool on = false;
+    double ms[3] = {0, 0, 0};
+    long long launches = 0, particle_launches = 0, particle_steps = 0;
+    std::vector<EvPair> pending;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t open = nullptr;
+};
+
+}  // namespace
+
+struct pic_handle {
+    pic_config cfg;
+    int geom = 0;  // 0 3D, 1 2D-XY, 2 2D-XZ
+    bool fp64 = false;
+    size_t esz = 4;
+    Grid g;
+    Tiling tl;
+    int push = PUSH_BORIS, esc = ESC_NONE;
+    KernelSet ks{};
+    size_t smem_bytes = 0;
+    // fields
+    void* E = nullptr;
+    void* B = nullptr;
+    void* J = nullptr;
+    void* Jtmp = nullptr;
+    void* Es = nullptr;  // shearing box: saved X^n
+    void* Bs = nullptr;
+    void* Ec = nullptr;  // shearing box: alternate iterate
+    void* Bc = nullptr;
+    double* stage = nullptr;  // host-layout staging [3][nz][ny][nx] doubles
+    size_t stage_elems = 0;
+    double* partial = nullptr;  // reduction partials
+    int partial_blocks = 0;
+    int* err = nullptr;
+    unsigned long long* counters = nullptr;
+    CUtensorMap tmE;
+    CUtensorMap tmB;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int buf = 0;  // particle buffer holding the current state
+    long long step = 0;
+    DevSpecies sp[PIC_MAX_SPECIES];
+    int nsp_loaded = 0;
+    Prof prof;
+    std::string last_error;
+};
+
+// ---- helpers ----------------------------------------------------------------------------
+
+static pic_status fail(pic_handle* h, pic_status st, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->last_error = buf;
+    else g_init_error = buf;
+    return st;
+}
+
+#define CK(call)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? PIC_ERR_OOM : PIC_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                            \
+    } while (0)
+
+static int grid_blocks(long long n) {
+    long long b = (n + NTHR - 1) / NTHR;
+    if (b < 1) b = 1;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)b;
+}
+
+// Device-time accounting: event pairs recorded on the handle's stream around
+// each kernel group, resolved later (pic_get_profile), so timing never
+// synchronises the stream.
+static cudaEvent_t prof_event(pic_handle* h) {
+    if (!h->prof.pool.empty()) {
+        cudaEvent_t e = h->prof.pool.back();
+        h->prof.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+static void prof_begin(pic_handle* h) {
+    if (!h->prof.on) return;
+    h->prof.open = prof_event(h);
+    cudaEventRecord(h->prof.open, h->stream);
+}
+static void prof_end(pic_handle* h, int cat) {
+    if (!h->prof.on || !h->prof.open) return;
+    cudaEvent_t b = prof_event(h);
+    cudaEventRecord(b, h->stream);
+    h->prof.pending.push_back(EvPair{h->prof.open, b, cat});
+    h->prof.open = nullptr;
+}
+static void prof_resolve(pic_handle* h) {
+    for (const EvPair& p : h->prof.pending) {
+        cudaEventSynchronize(p.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        h->prof.ms[p.cat] += ms;
+        h->prof.pool.push_back(p.a);
+        h->prof.pool.push_back(p.b);
+    }
+    h->prof.pending.clear();
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                                  const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static pic_status encode_field_map(pic_handle* h, CUtensorMap* map, void* base) {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
+            return fail(h, PIC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        fn = (EncodeTiledFn)p;
+    }
+    const Grid& g = h->g;
+    cuuint64_t dims[4] = {(cuuint64_t)g.px, (cuuint64_t)g.py, (cuuint64_t)g.pz, 3};
+    cuuint64_t strides[3] = {(cuuint64_t)g.px * h->esz, (cuuint64_t)g.px * g.py * h->esz, (cuuint64_t)g.cstride * h->esz};
+    cuuint32_t box[4] = {(cuuint32_t)h->tl.bx, (cuuint32_t)h->tl.by, (cuuint32_t)h->tl.bz, 3};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(map, h->fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, PIC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return PIC_OK;
+}
+
+// ---- field kernel launchers ----------------------------------------------------------------
+
+template <class T, int G> static void fill_guards_t(pic_handle* h, T* F, double dys) {
+    const Grid& g = h->g;
+    int di = 0;
+    double df = 0.0;
+    if (dys != 0.0) {
+        di = (int)std::floor(dys);
+        df = dys - di;
+        di %= g.ny;
+    }
+    long long nx_ = 3ll * (g.px - g.nx) * g.ny * g.nz;
+    fill_x_kernel<T, G><<<grid_blocks(nx_), NTHR, 0, h->stream>>>(g, F, 3, di, df);
+    h->prof.launches++;
+    if (GeomT<G>::AY) {
+        fill_y_kernel<T><<<grid_blocks(3ll * (g.py - g.ny) * g.px * g.nz), NTHR, 0, h->stream>>>(g, F, 3);
+        h->prof.launches++;
+    }
+    if (GeomT<G>::AZ) {
+        fill_z_kernel<T><<<grid_blocks(3ll * (g.pz - g.nz) * g.px * g.py), NTHR, 0, h->stream>>>(g, F, 3);
+        h->prof.launches++;
+    }
+}
+
+template <class T, int G> static void fold_current_t(pic_handle* h, T* J, double dys) {
+    const Grid& g = h->g;
+    if (GeomT<G>::AZ) {
+        fold_z_kernel<T><<<grid_blocks(3ll * (g.pz - g.nz) * g.px * g.py), NTHR, 0, h->stream>>>(g, J);
+        h->prof.launches++;
+    }
+    if (GeomT<G>::AY) {
+        fold_y_kernel<T><<<grid_blocks(3ll * (g.py - g.ny) * g.px * g.nz), NTHR, 0, h->stream>>>(g, J);
+        h->prof.launches++;
+    }
+    int di = 0;
+    double df = 0.0;
+    if (dys != 0.0) {
+        di = (int)std::floor(dys);
+        df = dys - di;
+        di %= g.ny;
+    }
+    fold_x_kernel<T, G><<<grid_blocks(3ll * (g.px - g.nx) * g.ny * g.nz), NTHR, 0, h->stream>>>(g, J, di, df);
+    h->prof.launches++;
+}
+
+template <class T, int G> static void curl_t(pic_handle* h, bool curlE, const void* in, void* out, const void* J, const Coef3& cf) {
+    long long n = (long long)h->g.nx * h->g.ny * h->g.nz;
+    if (curlE)
+        curl_update_kernel<T, G, true><<<grid_blocks(n), NTHR, 0, h->stream>>>(h->g, (const T*)in, (T*)out, (const T*)J, cf);
+    else
+        curl_update_kernel<T, G, false><<<grid_blocks(n), NTHR, 0, h->stream>>>(h->g, (const T*)in, (T*)out, (const T*)J, cf);
+    h->prof.launches++;
+}
+
+static double shear_shift(const pic_handle* h, double t) {
+    if (h->cfg.box != PIC_BOX_SHEAR) return 0.0;
+    double ny = (double)h->cfg.ny;
+    double d = std::fmod(h->cfg.s_shear * h->cfg.Omega0 * (double)h->cfg.nx * t, ny);
+    if (d < 0) d += ny;
+    return d;
+}
+
+static void lvals(const pic_handle* h, double t, double l[3]) {
+    for (int a = 0; a < 3; ++a) l[a] = h->cfg.box == PIC_BOX_EXPAND ? std::exp(h->cfg.expand_rate[a] * t) : 1.0;
+}
+
+template <class T, int G> static void fill_all_t(pic_handle* h, double t) {
+    double d = shear_shift(h, t);
+    fill_guards_t<T, G>(h, (T*)h->E, d);
+    fill_guards_t<T, G>(h, (T*)h->B, d);
+}
+
+// Field update of one step (t = t^n), after J holds the folded current.
+template <class T, int G> static void field_step_t(pic_handle* h, double t) {
+    const Grid& g = h->g;
+    const double c = h->cfg.c;
+    const double FOUR_PI = 12.566370614359172;
+    if (h->cfg.box == PIC_BOX_SHEAR) {
+        const double dh = shear_shift(h, t + 0.5);
+        const size_t bytes = (size_t)3 * g.cstride * h->esz;
+        // guards of X^n at t^{n+1/2}, then save X^n
+        fill_guards_t<T, G>(h, (T*)h->E, dh);
+        fill_guards_t<T, G>(h, (T*)h->B, dh);
+        cudaMemcpyAsync(h->Es, h->E, bytes, cudaMemcpyDeviceToDevice, h->stream);
+        cudaMemcpyAsync(h->Bs, h->B, bytes, cudaMemcpyDeviceToDevice, h->stream);
+        const int N = h->cfg.fp_iters;
+        const void* Ek = h->Es;
+        const void* Bk = h->Bs;
+        long long n = (long long)g.nx * g.ny * g.nz;
+        for (int k = 1; k <= N; ++k) {
+            bool to_main = ((N - k) % 2) == 0;
+            T* Eo = (T*)(to_main ? h->E : h->Ec);
+            T* Bo = (T*)(to_main ? h->B : h->Bc);
+            ksb_sweep_kernel<T, G><<<grid_blocks(n), NTHR, 0, h->stream>>>(g, (const T*)h->Es, (const T*)h->Bs, (const T*)Ek,
+                                                                            (const T*)Bk, (const T*)h->J, Eo, Bo, c,
+                                                                            h->cfg.s_shear * h->cfg.Omega0, 0.5 * g.nx);
+            h->prof.launches++;
+            fill_guards_t<T, G>(h, Eo, k == N ? shear_shift(h, t + 1.0) : dh);
+            fill_guards_t<T, G>(h, Bo, k == N ? shear_shift(h, t + 1.0) : dh);
+            Ek = Eo;
+            Bk = Bo;
+        }
+        return;
+    }
+    double l0[3], lh[3], l1[3];
+    lvals(h, t, l0);
+    lvals(h, t + 0.5, lh);
+    lvals(h, t + 1.0, l1);
+    const double e0 = l0[0] * l0[1] * l0[2], eh = lh[0] * lh[1] * lh[2], e1 = l1[0] * l1[1] * l1[2];
+    Coef3 cf;
+    // B^{n+1/2}: B' = ell L^-1 B at t^n, minus (c/2) curl(L E), back with L at n+1/2
+    for (int a = 0; a < 3; ++a) {
+        cf.a[a] = (lh[a] / eh) * (e0 / l0[a]);
+        cf.b[a] = -0.5 * c * (lh[a] / eh);
+        cf.g[a] = 0.0;
+        cf.s[a] = l0[a];
+    }
+    curl_t<T, G>(h, true, h->E, h->B, nullptr, cf);
+    fill_guards_t<T, G>(h, (T*)h->B, 0.0);
+    // E^{n+1}: E' + c curl(L B^{n+1/2}) - 4 pi (ell J'), back with L at n+1
+    for (int a = 0; a < 3; ++a) {
+        cf.a[a] = (l1[a] / e1) * (e0 / l0[a]);
+        cf.b[a] = c * (l1[a] / e1);
+        cf.g[a] = -FOUR_PI * (l1[a] / e1);
+        cf.s[a] = lh[a];
+    }
+    curl_t<T, G>(h, false, h->B, h->E, h->J, cf);
+    fill_guards_t<T, G>(h, (T*)h->E, 0.0);
+    // B^{n+1}
+    for (int a = 0; a < 3; ++a) {
+        cf.a[a] = (l1[a] / e1) * (eh / lh[a]);
+        cf.b[a] = -0.5 * c * (l1[a] / e1);
+        cf.g[a] = 0.0;
+        cf.s[a] = l1[a];
+    }
+    curl_t<T, G>(h, true, h->E, h->B, nullptr, cf);
+    fill_guards_t<T, G>(h, (T*)h->B, 0.0);
+}
+
+template <class T> static PView<T> view_of(void* const a[11]) {
+    PView<T> v;
+    v.cell = (int*)a[0];
+    for (int i = 0; i < 3; ++i) {
+        v.o[i] = (T*)a[1 + i];
+        v.u[i] = (T*)a[4 + i];
+        v.dr[i] = (T*)a[8 + i];
+    }
+    v.id = (uint32_t*)a[7];
+    return v;
+}
+
+// ---- the step -----------------------------------------------------------------------------
+
+template <class T, int G> static pic_status step_t(pic_handle* h) {
+    const Grid& g = h->g;
+    const pic_config& cf = h->cfg;
+    const int b = h->buf, o = 1 - b;
+    const double t = (double)h->step;
+    CK(cudaMemsetAsync(h->J, 0, (size_t)3 * g.cstride * h->esz, h->stream));
+
+    StepP P;
+    memset(&P, 0, sizeof(P));
+    P.c = cf.c;
+    P.step = h->step;
+    P.keb_exact = cf.keb_push == PIC_KEB_EXACT;
+    P.sO = cf.s_shear * cf.Omega0;
+    P.Omega0 = cf.Omega0;
+    P.half_nx = 0.5 * g.nx;
+    double de = shear_shift(h, t + 1.0);
+    P.dys_end_i = (int)std::floor(de);
+    P.dys_end_f = de - P.dys_end_i;
+    double lh[3];
+    lvals(h, t + 0.5, lh);
+    for (int a = 0; a < 3; ++a) {
+        P.Lam[a] = cf.box == PIC_BOX_EXPAND ? -0.5 * cf.expand_rate[a] : 0.0;
+        P.inv_lh[a] = 1.0 / lh[a];
+    }
+    P.l_esc = cf.l_esc;
+    double pe = cf.p_esc < 0 ? 0 : cf.p_esc;
+    P.esc_thresh = pe >= 1.0 ? 0xFFFFFFFFu : (uint32_t)std::floor(pe * 4294967296.0);
+    P.seed = cf.seed;
+    P.theta_inj = cf.theta_inj;
+    P.esc_dims = cf.escape_dims;
+    P.err = h->err;
+    P.counters = h->counters;
+
+    SpecPack<T> SP;
+    memset(&SP, 0, sizeof(SP));
+    int nsp = 0;
+    long long nparticles = 0;
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
+        DevSpecies& d = h->sp[s];
+        if (!d.loaded) continue;
+        SpecStep<T>& S = SP.s[nsp++];
+        S.in = view_of<T>(d.arr[b]);
+        S.out = view_of<T>(d.arr[o]);
+        S.lin = view_of<T>(d.larr[b]);
+        S.lout = view_of<T>(d.larr[o]);
+        S.stay_in = d.stay[b];
+        S.arr_in = d.arrv[b];
+        S.stay_out = d.stay[o];
+        S.arr_out = d.arrv[o];
+        S.lcount_in = d.lcount + b;
+        S.lcount_out = d.lcount + o;
+        S.tcap = d.tcap;
+        S.lcap = d.lcap;
+        S.qdt2m = T(d.q / (2.0 * d.m));
+        S.qdt2mc = T(d.q / (2.0 * d.m * cf.c));
+        S.q = T(d.q);
+        nparticles += d.n;
+    }
+    P.nsp = nsp;
+
+    if (nsp > 0) {
+        prof_begin(h);
+        T* Jp = (T*)h->J;
+        void* args[] = {&h->tmE, &h->tmB, (void*)&g, &h->tl, &P, &SP, &Jp};
+        CK(cudaLaunchKernel(h->ks.tile, dim3(h->tl.ntiles), dim3(TPB), args, h->smem_bytes, h->stream));
+        h->prof.launches++;
+        h->prof.particle_launches++;
+        h->prof.particle_steps += nparticles;
+        prof_end(h, 0);
+        prof_begin(h);
+        const T* Ep = (const T*)h->E;
+        const T* Bp = (const T*)h->B;
+        void* largs[] = {(void*)&g, &h->tl, &P, &SP, &Ep, &Bp, &Jp};
+        CK(cudaLaunchKernel(h->ks.loose, dim3(152), dim3(TPB), largs, 0, h->stream));
+        h->prof.launches++;
+        for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
+            DevSpecies& d = h->sp[s];
+            if (!d.loaded) continue;
+            finalize_kernel<<<grid_blocks(h->tl.ntiles), NTHR, 0, h->stream>>>(
+                h->tl.ntiles, d.tcap, d.stay[b], d.arrv[b], d.arrv[o], d.lcount + b, d.lcount + o, d.lcap, h->err);
+            h->prof.launches++;
+        }
+        prof_end(h, 1);
+    }
+
+    prof_begin(h);
+    fold_current_t<T, G>(h, (T*)h->J, shear_shift(h, t + 0.5));
+    if (cf.box == PIC_BOX_SHEAR && GeomT<G>::AY) {
+        ksb_advect_kernel<T><<<grid_blocks(3ll * g.nx * g.ny * g.nz), NTHR, 0, h->stream>>>(g, (const T*)h->J, (T*)h->Jtmp,
+                                                                                             cf.s_shear * cf.Omega0, 0.5 * g.nx);
+        h->prof.launches++;
+        std::swap(h->J, h->Jtmp);
+    }
+    field_step_t<T, G>(h, t);
+    prof_end(h, 2);
+    CK(cudaGetLastError());
+    h->buf = o;
+    h->step += 1;
+    return PIC_OK;
+}
+
+// ---- loading / read-back ------------------------------------------------------------------
+
+static pic_status alloc_species(pic_handle* h, DevSpecies& d, long long tcap) {
+    const int nt = h->tl.ntiles;
+    const bool leaky = h->esc == ESC_DISP;
+    const int nact = h->geom == 0 ? 3 : 2;
+    for (int b = 0; b < 2; ++b)
+        for (int i = 0; i < 11; ++i) {
+            if (d.arr[b][i]) cudaFree(d.arr[b][i]);
+            if (d.larr[b][i]) cudaFree(d.larr[b][i]);
+            d.arr[b][i] = d.larr[b][i] = nullptr;
+        }
+    d.tcap = tcap;
+    const long long cap = (long long)nt * tcap;
+    for (int b = 0; b < 2; ++b) {
+        for (int i = 0; i < 11; ++i) {
+            bool need = i == 0 || (i >= 1 && i <= nact) || (i >= 4 && i <= 7) || (i >= 8 && leaky);
+            if (!need) continue;
+            size_t es = (i == 0 || i == 7) ? 4 : h->esz;
+            CK(cudaMalloc(&d.arr[b][i], (size_t)cap * es));
+            CK(cudaMalloc(&d.larr[b][i], (size_t)d.lcap * es));
+        }
+        if (!d.stay[b]) CK(cudaMalloc(&d.stay[b], sizeof(int) * nt));
+        if (!d.arrv[b]) CK(cudaMalloc(&d.arrv[b], sizeof(int) * nt));
+        CK(cudaMemsetAsync(d.stay[b], 0, sizeof(int) * nt, h->stream));
+        CK(cudaMemsetAsync(d.arrv[b], 0, sizeof(int) * nt, h->stream));
+    }
+    // 2D: o[1] of the view is the second active axis; the kernels index o[AY ? 1 : ...]
+    if (!d.lcount) CK(cudaMalloc(&d.lcount, sizeof(int) * 2));
+    CK(cudaMemsetAsync(d.lcount, 0, sizeof(int) * 2, h->stream));
+    return PIC_OK;
+}
+
+template <class T, int G>
+static pic_status load_t(pic_handle* h, int species, long long n, const double* dx, const double* du, const uint32_t* did,
+                         const double* ddr) {
+    DevSpecies& d = h->sp[species];
+    const int nt = h->tl.ntiles;
+    int* tile_p = nullptr;
+    int* cnt = nullptr;
+    CK(cudaMalloc(&tile_p, sizeof(int) * std::max(1ll, n)));
+    CK(cudaMalloc(&cnt, sizeof(int) * nt));
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int) * nt, h->stream));
+    if (n > 0) load_bin_kernel<T, G><<<grid_blocks(n), NTHR, 0, h->stream>>>(n, dx, h->tl, h->g, tile_p, cnt);
+    std::vector<int> hc(nt);
+    CK(cudaMemcpyAsync(hc.data(), cnt, sizeof(int) * nt, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    int mx = 0;
+    for (int v : hc) mx = std::max(mx, v);
+    double slack = h->cfg.capacity_slack > 0 ? h->cfg.capacity_slack : 0.3;
+    long long tcap = (long long)std::ceil(mx * (1.0 + slack)) + 32;
+    tcap = (tcap + 3) & ~3ll;
+    d.lcap = std::max(4096ll, n / 32);
+    pic_status st = alloc_species(h, d, tcap);
+    if (st != PIC_OK) { cudaFree(tile_p); cudaFree(cnt); return st; }
+    const int b = h->buf;
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int) * nt, h->stream));
+    if (n > 0)
+        load_scatter_kernel<T, G><<<grid_blocks(n), NTHR, 0, h->stream>>>(n, dx, du, did, ddr, h->g, tile_p, cnt, tcap,
+                                                                          view_of<T>(d.arr[b]), h->esc == ESC_DISP);
+    CK(cudaMemcpyAsync(d.stay[b], cnt, sizeof(int) * nt, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaGetLastError());
+    cudaFree(tile_p);
+    cudaFree(cnt);
+    d.n = n;
+    d.loaded = true;
+    return PIC_OK;
+}
+
+template <class T, int G>
+static pic_status compact_t(pic_handle* h, int species, double* dx, double* du, uint32_t* did, double* ddr) {
+    DevSpecies& d = h->sp[species];
+    const int nt = h->tl.ntiles;
+    const int b = h->buf;
+    std::vector<int> st(nt), ar(nt);
+    int lc = 0;
+    CK(cudaMemcpyAsync(st.data(), d.stay[b], sizeof(int) * nt, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(ar.data(), d.arrv[b], sizeof(int) * nt, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&lc, d.lcount + b, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    std::vector<long long> off(nt);
+    long long acc = 0;
+    for (int t = 0; t < nt; ++t) { off[t] = acc; acc += st[t] + ar[t]; }
+    if (acc + lc != d.n)
+        return fail(h, PIC_ERR_STATE, "species %d holds %lld particles, expected %lld", species, acc + lc, d.n);
+    long long* doff = nullptr;
+    CK(cudaMalloc(&doff, sizeof(long long) * nt));
+    CK(cudaMemcpyAsync(doff, off.data(), sizeof(long long) * nt, cudaMemcpyHostToDevice, h->stream));
+    const bool hd = h->esc == ESC_DISP;
+    compact_kernel<T, G><<<nt, NTHR, 0, h->stream>>>(h->tl, h->g, view_of<T>(d.arr[b]), d.stay[b], d.arrv[b], d.tcap, doff, hd, dx,
+                                                   du, did, ddr);
+    compact_loose_kernel<T, G><<<64, NTHR, 0, h->stream>>>(view_of<T>(d.larr[b]), d.lcount + b, d.lcap, acc, hd, dx, du, did, ddr);
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaGetLastError());
+    cudaFree(doff);
+    return PIC_OK;
+}
+
+template <class T, int G> static pic_status maxwellian_t(pic_handle* h, int species, int ppc, double theta, const double drift[3],
+                                                         double noise, uint32_t seed, uint32_t id_base) {
+    DevSpecies& d = h->sp[species];
+    const int cells_per_tile = h->tl.tx * h->tl.ty * h->tl.tz;
+    double slack = h->cfg.capacity_slack > 0 ? h->cfg.capacity_slack : 0.3;
+    long long tcap = (long long)std::ceil((double)ppc * cells_per_tile * (1.0 + slack)) + 32;
+    tcap = (tcap + 3) & ~3ll;
+    long long n = (long long)ppc * h->g.nx * h->g.ny * h->g.nz;
+    d.lcap = std::max(4096ll, n / 32);
+    pic_status st = alloc_species(h, d, tcap);
+    if (st != PIC_OK) return st;
+    const int b = h->buf;
+    maxwellian_kernel<T, G><<<h->tl.ntiles, NTHR, 0, h->stream>>>(h->tl, h->g, ppc, theta, h->cfg.c, drift ? drift[0] : 0.0,
+                                                                 drift ? drift[1] : 0.0, drift ? drift[2] : 0.0, noise, seed,
+                                                                 id_base, tcap, view_of<T>(d.arr[b]), h->esc == ESC_DISP,
+                                                                 d.stay[b]);
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaGetLastError());
+    d.n = n;
+    d.loaded = true;
+    return PIC_OK;
+}
+
+// ---- dispatch by precision / geometry --------------------------------------------------------
+
+#define DISPATCH(h, FN, ...)                                                       \
+    ((h)->fp64 ? ((h)->geom == 0   ? FN<double, 0>(__VA_ARGS__)                  \
+                  : (h)->geom == 1 ? FN<double, 1>(__VA_ARGS__)                  \
+                                   : FN<double, 2>(__VA_ARGS__))                 \
+               : ((h)->geom == 0   ? FN<float, 0>(__VA_ARGS__)                   \
+                  : (h)->geom == 1 ? FN<float, 1>(__VA_ARGS__)                   \
+                                   : FN<float, 2>(__VA_ARGS__)))
+
+template <class T, int G> static pic_status set_fields_t(pic_handle* h, const double* E, const double* B) {
+    const Grid& g = h->g;
+    long long n = 3ll * g.nx * g.ny * g.nz;
+    CK(cudaMemcpyAsync(h->stage, E, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+    scatter_field_kernel<T><<<grid_blocks(n), NTHR, 0, h->stream>>>(g, h->stage, (T*)h->E);
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpyAsync(h->stage, B, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+    scatter_field_kernel<T><<<grid_blocks(n), NTHR, 0, h->stream>>>(g, h->stage, (T*)h->B);
+    fill_all_t<T, G>(h, (double)h->step);
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
+template <class T, int G> static pic_status uniform_fields_t(pic_handle* h, const double* E, const double* B) {
+    const Grid& g = h->g;
+    uniform_field_kernel<T><<<grid_blocks(3ll * g.cstride), NTHR, 0, h->stream>>>(g, (T*)h->E, E[0], E[1], E[2]);
+    uniform_field_kernel<T><<<grid_blocks(3ll * g.cstride), NTHR, 0, h->stream>>>(g, (T*)h->B, B[0], B[1], B[2]);
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
+template <class T, int G> static pic_status get_fields_t(pic_handle* h, double* E, double* B, double* J) {
+    const Grid& g = h->g;
+    long long n = 3ll * g.nx * g.ny * g.nz;
+    void* src[3] = {h->E, h->B, h->J};
+    double* dst[3] = {E, B, J};
+    for (int f = 0; f < 3; ++f) {
+        if (!dst[f]) continue;
+        gather_field_kernel<T><<<grid_blocks(n), NTHR, 0, h->stream>>>(g, (const T*)src[f], h->stage);
+        CK(cudaMemcpyAsync(dst[f], h->stage, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
+template <class T, int G> static pic_status diag_t(pic_handle* h, pic_diag* out) {
+    const Grid& g = h->g;
+    double* dsum = h->partial + (size_t)h->partial_blocks * 3;
+    double hs[3];
+    void* f[2] = {h->E, h->B};
+    for (int k = 0; k < 2; ++k) {
+        sumsq_partial_kernel<T><<<h->partial_blocks, NTHR, 0, h->stream>>>(g, (const T*)f[k], h->partial);
+        sum_partials_kernel<<<1, 32, 0, h->stream>>>(h->partial, h->partial_blocks, 3, dsum);
+        CK(cudaMemcpyAsync(hs, dsum, sizeof(hs), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        for (int c = 0; c < 3; ++c) (k == 0 ? out->field_energy_E : out->field_energy_B)[c] = hs[c] / 25.132741228718345;
+    }
+    const int b = h->buf;
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
+        DevSpecies& d = h->sp[s];
+        out->kinetic_energy[s] = 0.0;
+        out->count[s] = 0;
+        if (!d.loaded) continue;
+        kinetic_kernel<T, G><<<h->partial_blocks, NTHR, 0, h->stream>>>(h->tl, view_of<T>(d.arr[b]), d.stay[b], d.arrv[b], d.tcap,
+                                                                       view_of<T>(d.larr[b]), d.lcount + b, d.lcap, h->cfg.c,
+                                                                       d.m, h->partial);
+        sum_partials_kernel<<<1, 32, 0, h->stream>>>(h->partial, h->partial_blocks, 1, dsum);
+        CK(cudaMemcpyAsync(hs, dsum, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        int lc = 0;
+        CK(cudaMemcpyAsync(&lc, d.lcount + b, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        out->kinetic_energy[s] = hs[0];
+        out->count[s] = d.n;
+        out->loose += lc;
+    }
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
+// ---- configuration ----------------------------------------------------------------------------
+
+static int pick_tile(int n, int pref, bool xaxis, int align) {
+    if (n <= pref) return n;
+    (void)xaxis;
+    (void)align;
+    return pref;
+}
+
+static pic_status validate(const pic_config* c) {
+    pic_handle* h = nullptr;
+    if (!c) return fail(h, PIC_ERR_ARG, "config is NULL");
+    if (c->box < 0 || c->box > 3) return fail(h, PIC_ERR_ARG, "box must be 0..3");
+    if (c->ndim != 2 && c->ndim != 3) return fail(h, PIC_ERR_ARG, "ndim must be 2 or 3");
+    if (c->ndim == 2 && c->plane != PIC_PLANE_XY && c->plane != PIC_PLANE_XZ)
+        return fail(h, PIC_ERR_ARG, "2D plane must be PIC_PLANE_XY or PIC_PLANE_XZ");
+    if (c->ndim == 2 && c->plane == PIC_PLANE_XY && c->nz != 1) return fail(h, PIC_ERR_ARG, "2D x-y plane needs nz = 1");
+    if (c->ndim == 2 && c->plane == PIC_PLANE_XZ && c->ny != 1) return fail(h, PIC_ERR_ARG, "2D x-z plane needs ny = 1");
+    int act[3] = {c->nx, c->ny, c->nz};
+    bool active[3] = {true, !(c->ndim == 2 && c->plane == PIC_PLANE_XZ), !(c->ndim == 2 && c->plane == PIC_PLANE_XY)};
+    for (int a = 0; a < 3; ++a)
+        if (active[a] && act[a] < 8) return fail(h, PIC_ERR_ARG, "active axes need at least 8 cells (axis %d has %d)", a, act[a]);
+    if (c->nx > (c->ndim == 3 ? 2048 : 65536) || c->ny > (c->ndim == 3 ? 2048 : 65536) || c->nz > (c->ndim == 3 ? 1024 : 65536))
+        return fail(h, PIC_ERR_ARG, "grid too large for the packed cell index (3D: 2048 x 2048 x 1024)");
+    if (c->shape_order != 1 && c->shape_order != 2) return fail(h, PIC_ERR_ARG, "shape_order must be 1 or 2");
+    if (c->precision != PIC_FP32 && c->precision != PIC_FP64) return fail(h, PIC_ERR_ARG, "precision must be FP32 or FP64");
+    if (!(c->c > 0) || !(c->c * std::sqrt((double)c->ndim) < 1.0))
+        return fail(h, PIC_ERR_ARG, "Courant number c must satisfy 0 < c sqrt(ndim) < 1");
+    if (c->box == PIC_BOX_SHEAR) {
+        if (c->fp_iters < 1 || c->fp_iters > 64) return fail(h, PIC_ERR_ARG, "fp_iters must be in 1..64");
+        double vmax = std::fabs(c->s_shear * c->Omega0) * 0.5 * c->nx;
+        if (c->c + vmax >= 1.0) return fail(h, PIC_ERR_ARG, "c + max shear speed must stay below one cell per step");
+    }
+    if (c->box == PIC_BOX_LEAKY) {
+        if (c->escape_mode < 0 || c->escape_mode > 2) return fail(h, PIC_ERR_ARG, "escape_mode must be 0..2");
+        if (c->escape_mode == PIC_ESC_DISPLACEMENT && !(c->l_esc > 0)) return fail(h, PIC_ERR_ARG, "l_esc must be > 0");
+        if (c->escape_dims != 2 && c->escape_dims != 3) return fail(h, PIC_ERR_ARG, "escape_dims must be 2 or 3");
+        if (c->escape_mode != PIC_ESC_NONE && !(c->theta_inj > 0)) return fail(h, PIC_ERR_ARG, "theta_inj must be > 0");
+    }
+    for (int a = 0; a < 3; ++a)
+        if (c->tile[a] < 0) return fail(h, PIC_ERR_ARG, "tile sizes must be >= 0");
+    return PIC_OK;
+}
+
+template <class T, int G> static pic_status refill_t(pic_handle* h) {
+    fill_all_t<T, G>(h, (double)h->step);
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
+extern "C" {
+
+const char* pic_version(void) { return "libpic 0.1 (sm_103a)"; }
+int pic_abi_version(void) { return PIC_ABI_VERSION; }
+
+const char* pic_last_error(pic_handle* h) { return h ? h->last_error.c_str() : g_init_error.c_str(); }
+
+pic_status pic_init(const pic_config* cfg, pic_handle** out) {
+    if (!out) return fail(nullptr, PIC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    pic_status st = validate(cfg);
+    if (st != PIC_OK) return st;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return fail(nullptr, PIC_ERR_CUDA, "no CUDA device available");
+    pic_handle* h = new pic_handle();
+    h->cfg = *cfg;
+    pic_config& c = h->cfg;
+    if (c.escape_dims == 0) c.escape_dims = 2;
+    h->geom = c.ndim == 3 ? 0 : (c.plane == PIC_PLANE_XY ? 1 : 2);
+    h->fp64 = c.precision == PIC_FP64;
+    h->esz = h->fp64 ? 8 : 4;
+    h->push = c.box == PIC_BOX_SHEAR ? PUSH_KSB : (c.box == PIC_BOX_EXPAND ? PUSH_KEB : PUSH_BORIS);
+    h->esc = c.box == PIC_BOX_LEAKY ? (c.escape_mode == PIC_ESC_DISPLACEMENT ? ESC_DISP
+                                       : c.escape_mode == PIC_ESC_PROBABILISTIC ? ESC_PROB
+                                                                                 : ESC_NONE)
+                                    : ESC_NONE;
+    const bool AY = h->geom != 2, AZ = h->geom != 1;
+    const int A = (int)(16 / h->esz);  // TMA x quantum
+    Grid& g = h->g;
+    g.nx = c.nx; g.ny = c.ny; g.nz = c.nz;
+    g.gx = GL; g.gy = AY ? GL : 0; g.gz = AZ ? GL : 0;
+    g.px = ((c.nx + GL + GR) + A - 1) / A * A;
+    g.py = AY ? c.ny + GL + GR : 1;
+    g.pz = AZ ? c.nz + GL + GR : 1;
+    g.cstride = (long long)g.px * g.py * g.pz;
+    Tiling& tl = h->tl;
+    int defx = h->geom == 0 ? 8 : 16, defy = h->geom == 0 ? 8 : 16;
+    tl.tx = c.tile[0] ? c.tile[0] : pick_tile(c.nx, defx, true, A);
+    tl.ty = AY ? (c.tile[1] ? c.tile[1] : pick_tile(c.ny, h->geom == 0 ? defy : defy, false, 1)) : 1;
+    tl.tz = AZ ? (c.tile[2] ? c.tile[2] : pick_tile(c.nz, h->geom == 0 ? 8 : 16, false, 1)) : 1;
+    tl.tx = std::min(tl.tx, c.nx);
+    tl.ty = std::min(tl.ty, c.ny);
+    tl.tz = std::min(tl.tz, c.nz);
+    tl.ntx = (c.nx + tl.tx - 1) / tl.tx;
+    tl.nty = (c.ny + tl.ty - 1) / tl.ty;
+    tl.ntz = (c.nz + tl.tz - 1) / tl.tz;
+    tl.ntiles = tl.ntx * tl.nty * tl.ntz;
+    tl.xalign = A;
+    int bxraw = tl.tx + 4 + ((tl.tx % A) ? A - 1 : 0);
+    tl.bx = (bxraw + A - 1) / A * A;
+    tl.by = AY ? tl.ty + 4 : 1;
+    tl.bz = AZ ? tl.tz + 4 : 1;
+    tl.jx = tl.tx + 5;
+    tl.jy = AY ? tl.ty + 5 : 1;
+    tl.jz = AZ ? tl.tz + 5 : 1;
+    if (tl.bx > 256 || tl.by > 256 || tl.bz > 256) {
+        delete h;
+        return fail(nullptr, PIC_ERR_ARG, "tile too large for one TMA box");
+    }
+    h->smem_bytes = h->fp64 ? SmemLayout<double>(tl).bytes : SmemLayout<float>(tl).bytes;
+    if (h->smem_bytes > 227 * 1024) {
+        delete h;
+        return fail(nullptr, PIC_ERR_ARG, "tile needs %zu bytes of shared memory (> 227 KB)", h->smem_bytes);
+    }
+    h->ks = lookup_kernels(h->fp64, h->geom, c.shape_order, h->push, h->esc);
+
+    auto bail = [&](pic_status s) {
+        g_init_error = h->last_error;
+        pic_destroy(h);
+        return s;
+    };
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete h;
+        return fail(nullptr, PIC_ERR_CUDA, "cudaStreamCreate failed");
+    }
+    h->own_stream = true;
+    if (cudaFuncSetAttribute(h->ks.tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_bytes) != cudaSuccess)
+        return bail(fail(h, PIC_ERR_CUDA, "cannot set %zu bytes of dynamic shared memory", h->smem_bytes));
+    const size_t fb = (size_t)3 * g.cstride * h->esz;
+    void** bufs[] = {&h->E, &h->B, &h->J, &h->Jtmp};
+    for (void** p : bufs) {
+        if (cudaMalloc(p, fb) != cudaSuccess) return bail(fail(h, PIC_ERR_OOM, "field allocation failed"));
+        cudaMemsetAsync(*p, 0, fb, h->stream);
+    }
+    if (c.box == PIC_BOX_SHEAR) {
+        void** kb[] = {&h->Es, &h->Bs, &h->Ec, &h->Bc};
+        for (void** p : kb) {
+            if (cudaMalloc(p, fb) != cudaSuccess) return bail(fail(h, PIC_ERR_OOM, "field allocation failed"));
+            cudaMemsetAsync(*p, 0, fb, h->stream);
+        }
+    }
+    h->stage_elems = (size_t)3 * c.nx * c.ny * c.nz;
+    if (cudaMalloc(&h->stage, sizeof(double) * h->stage_elems) != cudaSuccess)
+        return bail(fail(h, PIC_ERR_OOM, "staging allocation failed"));
+    h->partial_blocks = 152 * 4;
+    if (cudaMalloc(&h->partial, sizeof(double) * (h->partial_blocks * 3 + 8)) != cudaSuccess)
+        return bail(fail(h, PIC_ERR_OOM, "allocation failed"));
+    if (cudaMalloc(&h->err, sizeof(int)) != cudaSuccess || cudaMalloc(&h->counters, 2 * sizeof(unsigned long long)) != cudaSuccess)
+        return bail(fail(h, PIC_ERR_OOM, "allocation failed"));
+    cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
+    cudaMemsetAsync(h->counters, 0, 2 * sizeof(unsigned long long), h->stream);
+    if (encode_field_map(h, &h->tmE, h->E) != PIC_OK || encode_field_map(h, &h->tmB, h->B) != PIC_OK)
+        return bail(PIC_ERR_CUDA);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(fail(h, PIC_ERR_CUDA, "initialisation failed"));
+    *out = h;
+    return PIC_OK;
+}
+
+pic_status pic_destroy(pic_handle* h) {
+    if (!h) return PIC_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto& d : h->sp) {
+        for (int b = 0; b < 2; ++b) {
+            for (int i = 0; i < 11; ++i) {
+                if (d.arr[b][i]) cudaFree(d.arr[b][i]);
+                if (d.larr[b][i]) cudaFree(d.larr[b][i]);
+            }
+            if (d.stay[b]) cudaFree(d.stay[b]);
+            if (d.arrv[b]) cudaFree(d.arrv[b]);
+        }
+        if (d.lcount) cudaFree(d.lcount);
+    }
+    void* ptrs[] = {h->E, h->B, h->J, h->Jtmp, h->Es, h->Bs, h->Ec, h->Bc, h->stage, h->partial, h->err, h->counters};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    prof_resolve(h);
+    for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return PIC_OK;
+}
+
+pic_status pic_set_stream(pic_handle* h, void* stream) {
+    if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    cudaStreamSynchronize(h->stream);
+    if (stream) {
+        if (h->own_stream) cudaStreamDestroy(h->stream);
+        h->stream = (cudaStream_t)stream;
+        h->own_stream = false;
+    } else if (!h->own_stream) {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(h, PIC_ERR_CUDA, "cudaStreamCreate failed");
+        h->own_stream = true;
+    }
+    return PIC_OK;
+}
+
+pic_status pic_synchronize(pic_handle* h) {
+    if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    CK(cudaStreamSynchronize(h->stream));
+    return PIC_OK;
+}
+
+static pic_status check_species(pic_handle* h, int species) {
+    if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    if (species < 0 || species >= PIC_MAX_SPECIES) return fail(h, PIC_ERR_ARG, "species index %d out of range", species);
+    return PIC_OK;
+}
+
+pic_status pic_load_particles(pic_handle* h, int species, double q, double m, int64_t n, const double* x, const double* u,
+                              const uint32_t* id) {
+    pic_status st = check_species(h, species);
+    if (st != PIC_OK) return st;
+    if (n < 0 || (n > 0 && (!x || !u))) return fail(h, PIC_ERR_ARG, "bad particle arrays");
+    if (!(m > 0) || !std::isfinite(q)) return fail(h, PIC_ERR_ARG, "mass must be > 0 and charge finite");
+    if (n >= (1ll << 31)) return fail(h, PIC_ERR_ARG, "at most 2^31 - 1 particles per species");
+    CK(cudaStreamSynchronize(h->stream));
+    double *dx = nullptr, *du = nullptr;
+    uint32_t* did = nullptr;
+    size_t n3 = (size_t)std::max<int64_t>(n, 1) * 3;
+    CK(cudaMalloc(&dx, sizeof(double) * n3));
+    CK(cudaMalloc(&du, sizeof(double) * n3));
+    if (n > 0) {
+        CK(cudaMemcpyAsync(dx, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(du, u, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+        if (id) {
+            CK(cudaMalloc(&did, sizeof(uint32_t) * n));
+            CK(cudaMemcpyAsync(did, id, sizeof(uint32_t) * n, cudaMemcpyHostToDevice, h->stream));
+        }
+    }
+    h->sp[species].q = q;
+    h->sp[species].m = m;
+    st = DISPATCH(h, load_t, h, species, n, dx, du, did, (const double*)nullptr);
+    cudaFree(dx);
+    cudaFree(du);
+    if (did) cudaFree(did);
+    return st;
+}
+
+pic_status pic_load_maxwellian(pic_handle* h, int species, double q, double m, int ppc, double theta, const double drift[3],
+                               double noise_sigma, uint32_t seed, uint32_t id_base) {
+    pic_status st = check_species(h, species);
+    if (st != PIC_OK) return st;
+    if (ppc < 0 || !(m > 0) || theta < 0 || noise_sigma < 0) return fail(h, PIC_ERR_ARG, "bad loader arguments");
+    CK(cudaStreamSynchronize(h->stream));
+    h->sp[species].q = q;
+    h->sp[species].m = m;
+    return DISPATCH(h, maxwellian_t, h, species, ppc, theta, drift, noise_sigma, seed, id_base);
+}
+
+pic_status pic_set_fields(pic_handle* h, const double* E, const double* B) {
+    if (!h || !E || !B) return fail(h, PIC_ERR_ARG, "NULL argument");
+    return DISPATCH(h, set_fields_t, h, E, B);
+}
+
+pic_status pic_set_uniform_fields(pic_handle* h, const double E[3], const double B[3]) {
+    if (!h || !E || !B) return fail(h, PIC_ERR_ARG, "NULL argument");
+    return DISPATCH(h, uniform_fields_t, h, E, B);
+}
+
+static pic_status check_error_word(pic_handle* h) {
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (e & ERRB_TMA_TIMEOUT) return fail(h, PIC_ERR_TIMEOUT, "a field-staging wait expired (error word %d)", e);
+    if (e & ERRB_NONFINITE) return fail(h, PIC_ERR_NUMERIC, "non-finite particle velocity (error word %d)", e);
+    if (e & ERRB_LOOSE_OVERFLOW) return fail(h, PIC_ERR_STATE, "loose-particle list overflowed (error word %d)", e);
+    if (e) return fail(h, PIC_ERR_STATE, "device error word %d", e);
+    return PIC_OK;
+}
+
+pic_status pic_set_step(pic_handle* h, int64_t step) {
+    if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    if (step < 0) return fail(h, PIC_ERR_ARG, "step must be >= 0");
+    h->step = step;
+    return DISPATCH(h, refill_t, h);
+}
+
+pic_status pic_step(pic_handle* h, int nsteps) {
+    if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    if (nsteps < 0) return fail(h, PIC_ERR_ARG, "nsteps must be >= 0");
+    for (int k = 0; k < nsteps; ++k) {
+        pic_status st = DISPATCH(h, step_t, h);
+        if (st != PIC_OK) return st;
+    }
+    return PIC_OK;
+}
+
+pic_status pic_diagnostics(pic_handle* h, pic_diag* out) {
+    if (!h || !out) return fail(h, PIC_ERR_ARG, "NULL argument");
+    memset(out, 0, sizeof(*out));
+    CK(cudaStreamSynchronize(h->stream));
+    out->step = h->step;
+    out->t = (double)h->step;
+    out->shear_shift = shear_shift(h, out->t);
+    lvals(h, out->t, out->l);
+    pic_status st = DISPATCH(h, diag_t, h, out);
+    if (st != PIC_OK) return st;
+    unsigned long long cnt[2];
+    CK(cudaMemcpyAsync(cnt, h->counters, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    out->escaped_total = (int64_t)cnt[0];
+    out->superluminal_total = (int64_t)cnt[1];
+    out->error_word = e;
+    return check_error_word(h);
+}
+
+pic_status pic_get_count(pic_handle* h, int species, int64_t* n) {
+    pic_status st = check_species(h, species);
+    if (st != PIC_OK) return st;
+    if (!n) return fail(h, PIC_ERR_ARG, "n is NULL");
+    *n = h->sp[species].loaded ? h->sp[species].n : 0;
+    return PIC_OK;
+}
+
+pic_status pic_get_particles(pic_handle* h, int species, double* x, double* u, uint32_t* id, double* dr) {
+    pic_status st = check_species(h, species);
+    if (st != PIC_OK) return st;
+    DevSpecies& d = h->sp[species];
+    if (!d.loaded) return fail(h, PIC_ERR_STATE, "species %d is not loaded", species);
+    CK(cudaStreamSynchronize(h->stream));
+    long long n = d.n;
+    double *dx = nullptr, *du = nullptr, *ddr = nullptr;
+    uint32_t* did = nullptr;
+    size_t n3 = (size_t)std::max(n, 1ll) * 3;
+    if (x) CK(cudaMalloc(&dx, sizeof(double) * n3));
+    if (u) CK(cudaMalloc(&du, sizeof(double) * n3));
+    if (id) CK(cudaMalloc(&did, sizeof(uint32_t) * std::max(n, 1ll)));
+    if (dr) CK(cudaMalloc(&ddr, sizeof(double) * n3));
+    st = DISPATCH(h, compact_t, h, species, dx, du, did, ddr);
+    if (st == PIC_OK && n > 0) {
+        if (x) CK(cudaMemcpy(x, dx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+        if (u) CK(cudaMemcpy(u, du, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+        if (id) CK(cudaMemcpy(id, did, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+        if (dr) CK(cudaMemcpy(dr, ddr, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+        if (x && h->geom != 0) {
+            // the ignorable coordinate is not tracked
+            int ig = h->geom == 1 ? 2 : 1;
+            for (long long i = 0; i < n; ++i) x[3 * i + ig] = 0.5;
+        }
+    }
+    if (dx) cudaFree(dx);
+    if (du) cudaFree(du);
+    if (did) cudaFree(did);
+    if (ddr) cudaFree(ddr);
+    return st;
+}
+
+pic_status pic_get_fields(pic_handle* h, double* E, double* B, double* J) {
+    if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    return DISPATCH(h, get_fields_t, h, E, B, J);
+}
+
+pic_status pic_set_profiling(pic_handle* h, int enable) {
+    if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    h->prof.on = enable != 0;
+    return PIC_OK;
+}
+
+pic_status pic_get_profile(pic_handle* h, pic_profile* out) {
+    if (!h || !out) return fail(h, PIC_ERR_ARG, "NULL argument");
+    prof_resolve(h);
+    out->ms_particle = h->prof.ms[0];
+    out->ms_other = h->prof.ms[1];
+    out->ms_field = h->prof.ms[2];
+    out->launches = h->prof.launches;
+    out->particle_launches = h->prof.particle_launches;
+    out->particle_steps = h->prof.particle_steps;
+    return PIC_OK;
+}
+
+pic_status pic_reset_profile(pic_handle* h) {
+    if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    prof_resolve(h);
+    h->prof.ms[0] = h->prof.ms[1] = h->prof.ms[2] = 0.0;
+    h->prof.launches = h->prof.particle_launches = h->prof.particle_steps = 0;
+    return PIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,327 @@
+"""ctypes binding of libpic (include/pic.h): the same entry points under the
+same names, plus a small ``Box`` convenience wrapper.  Argument marshalling
+only -- every step of the PIC path runs in the CUDA kernels of libpic.  The
+binding fails loudly (``LibraryMissing``) when the library has not been built;
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpic.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "pic.h")
+
+PIC_OK, PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_CUDA, PIC_ERR_TIMEOUT, PIC_ERR_STATE, PIC_ERR_NUMERIC = range(7)
+PIC_BOX_PERIODIC, PIC_BOX_SHEAR, PIC_BOX_EXPAND, PIC_BOX_LEAKY = range(4)
+PIC_PLANE_XY, PIC_PLANE_XZ = 0, 1
+PIC_FP32, PIC_FP64 = 0, 1
+PIC_KEB_CLOSED_FORM, PIC_KEB_EXACT = 0, 1
+PIC_ESC_NONE, PIC_ESC_DISPLACEMENT, PIC_ESC_PROBABILISTIC = 0, 1, 2
+PIC_MAX_SPECIES = 4
+
+STATUS_NAMES = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_OOM", 3: "PIC_ERR_CUDA", 4: "PIC_ERR_TIMEOUT",
+                5: "PIC_ERR_STATE", 6: "PIC_ERR_NUMERIC"}
+
+
+class LibraryMissing(RuntimeError):
+    pass
+
+
+class PicError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class pic_config(C.Structure):
+    _fields_ = [
+        ("box", C.c_int32), ("ndim", C.c_int32), ("plane", C.c_int32),
+        ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+        ("shape_order", C.c_int32), ("precision", C.c_int32), ("fp_iters", C.c_int32),
+        ("keb_push", C.c_int32), ("escape_mode", C.c_int32), ("escape_dims", C.c_int32),
+        ("tile", C.c_int32 * 3), ("reserved0", C.c_int32),
+        ("seed", C.c_uint32), ("reserved1", C.c_uint32),
+        ("c", C.c_double), ("s_shear", C.c_double), ("Omega0", C.c_double),
+        ("expand_rate", C.c_double * 3), ("l_esc", C.c_double), ("p_esc", C.c_double),
+        ("theta_inj", C.c_double), ("capacity_slack", C.c_double),
+    ]
+
+
+class pic_diag(C.Structure):
+    _fields_ = [
+        ("step", C.c_int64), ("t", C.c_double), ("shear_shift", C.c_double), ("l", C.c_double * 3),
+        ("field_energy_E", C.c_double * 3), ("field_energy_B", C.c_double * 3),
+        ("kinetic_energy", C.c_double * PIC_MAX_SPECIES), ("count", C.c_int64 * PIC_MAX_SPECIES),
+        ("escaped_total", C.c_int64), ("superluminal_total", C.c_int64), ("loose", C.c_int64),
+        ("error_word", C.c_int32), ("reserved", C.c_int32),
+    ]
+
+
+class pic_profile(C.Structure):
+    _fields_ = [("ms_particle", C.c_double), ("ms_field", C.c_double), ("ms_other", C.c_double),
+                ("launches", C.c_int64), ("particle_launches", C.c_int64), ("particle_steps", C.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+_H = C.c_void_p
+_D = C.POINTER(C.c_double)
+_U32 = C.POINTER(C.c_uint32)
+
+_SIGS = {
+    "pic_version": (C.c_char_p, []),
+    "pic_abi_version": (C.c_int, []),
+    "pic_init": (C.c_int, [C.POINTER(pic_config), C.POINTER(_H)]),
+    "pic_destroy": (C.c_int, [_H]),
+    "pic_last_error": (C.c_char_p, [_H]),
+    "pic_set_stream": (C.c_int, [_H, C.c_void_p]),
+    "pic_synchronize": (C.c_int, [_H]),
+    "pic_load_particles": (C.c_int, [_H, C.c_int, C.c_double, C.c_double, C.c_int64, _D, _D, _U32]),
+    "pic_load_maxwellian": (C.c_int, [_H, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, _D,
+                                      C.c_double, C.c_uint32, C.c_uint32]),
+    "pic_set_fields": (C.c_int, [_H, _D, _D]),
+    "pic_set_uniform_fields": (C.c_int, [_H, _D, _D]),
+    "pic_step": (C.c_int, [_H, C.c_int]),
+    "pic_set_step": (C.c_int, [_H, C.c_int64]),
+    "pic_diagnostics": (C.c_int, [_H, C.POINTER(pic_diag)]),
+    "pic_get_count": (C.c_int, [_H, C.c_int, C.POINTER(C.c_int64)]),
+    "pic_get_particles": (C.c_int, [_H, C.c_int, _D, _D, _U32, _D]),
+    "pic_get_fields": (C.c_int, [_H, _D, _D, _D]),
+    "pic_set_profiling": (C.c_int, [_H, C.c_int]),
+    "pic_get_profile": (C.c_int, [_H, C.POINTER(pic_profile)]),
+    "pic_reset_profile": (C.c_int, [_H]),
+}
+
+
+def header_functions(path: str = HEADER):
+    """Names of every function the public header declares."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pic_[a-z_0-9]+)\s*\(", text)))
+
+
+def lib():
+    """Load libpic.so (built by paper_2602_15939_gb300.build); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise LibraryMissing(f"libpic is not built ({LIB_PATH} missing); run paper_2602_15939_gb300.build.build()")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(h, st):
+    if st != PIC_OK:
+        msg = lib().pic_last_error(h)
+        raise PicError(st, msg.decode() if msg else "")
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+# ---- the C entry points, same names ---------------------------------------------
+
+def pic_version() -> str:
+    return lib().pic_version().decode()
+
+
+def pic_abi_version() -> int:
+    return lib().pic_abi_version()
+
+
+def pic_init(cfg: pic_config):
+    h = _H()
+    st = lib().pic_init(C.byref(cfg), C.byref(h))
+    _check(None, st)
+    return h
+
+
+def pic_destroy(h):
+    _check(h, lib().pic_destroy(h))
+
+
+def pic_last_error(h=None) -> str:
+    m = lib().pic_last_error(h)
+    return m.decode() if m else ""
+
+
+def pic_set_stream(h, stream: int | None):
+    _check(h, lib().pic_set_stream(h, C.c_void_p(stream) if stream else None))
+
+
+def pic_synchronize(h):
+    _check(h, lib().pic_synchronize(h))
+
+
+def pic_load_particles(h, species, q, m, x, u, ids=None):
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1, 3)
+    n = len(x)
+    idp = None
+    if ids is not None:
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        idp = ids.ctypes.data_as(_U32)
+    _check(h, lib().pic_load_particles(h, species, q, m, n, _dptr(x), _dptr(u), idp))
+
+
+def pic_load_maxwellian(h, species, q, m, ppc, theta, drift=(0.0, 0.0, 0.0), noise_sigma=0.0, seed=0, id_base=0):
+    d = np.ascontiguousarray(drift, dtype=np.float64)
+    _check(h, lib().pic_load_maxwellian(h, species, q, m, ppc, theta, _dptr(d), noise_sigma, seed & 0xFFFFFFFF,
+                                        id_base & 0xFFFFFFFF))
+
+
+def pic_set_fields(h, E, B):
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    _check(h, lib().pic_set_fields(h, _dptr(E), _dptr(B)))
+
+
+def pic_set_uniform_fields(h, E, B):
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    _check(h, lib().pic_set_uniform_fields(h, _dptr(E), _dptr(B)))
+
+
+def pic_set_step(h, step):
+    _check(h, lib().pic_set_step(h, step))
+
+
+def pic_step(h, nsteps=1):
+    _check(h, lib().pic_step(h, nsteps))
+
+
+def pic_diagnostics(h) -> pic_diag:
+    d = pic_diag()
+    _check(h, lib().pic_diagnostics(h, C.byref(d)))
+    return d
+
+
+def pic_get_count(h, species) -> int:
+    n = C.c_int64()
+    _check(h, lib().pic_get_count(h, species, C.byref(n)))
+    return n.value
+
+
+def pic_get_particles(h, species, want_dr=False):
+    n = pic_get_count(h, species)
+    x = np.zeros((n, 3))
+    u = np.zeros((n, 3))
+    ids = np.zeros(n, dtype=np.uint32)
+    dr = np.zeros((n, 3)) if want_dr else None
+    _check(h, lib().pic_get_particles(h, species, _dptr(x), _dptr(u), ids.ctypes.data_as(_U32), _dptr(dr)))
+    return x, u, ids, dr
+
+
+def pic_get_fields(h, shape):
+    E, B, J = (np.zeros(shape) for _ in range(3))
+    _check(h, lib().pic_get_fields(h, _dptr(E), _dptr(B), _dptr(J)))
+    return E, B, J
+
+
+def pic_set_profiling(h, enable=True):
+    _check(h, lib().pic_set_profiling(h, int(enable)))
+
+
+def pic_get_profile(h) -> pic_profile:
+    p = pic_profile()
+    _check(h, lib().pic_get_profile(h, C.byref(p)))
+    return p
+
+
+def pic_reset_profile(h):
+    _check(h, lib().pic_reset_profile(h))
+
+
+# ---- convenience ------------------------------------------------------------------
+
+def make_config(box=PIC_BOX_PERIODIC, nx=8, ny=8, nz=8, ndim=3, plane=PIC_PLANE_XY, c=0.45, order=1,
+                precision=PIC_FP64, fp_iters=4, keb_push=PIC_KEB_CLOSED_FORM, escape_mode=PIC_ESC_NONE,
+                escape_dims=2, tile=(0, 0, 0), seed=0, s=0.0, Omega0=0.0, rate=(0.0, 0.0, 0.0), l_esc=0.0,
+                p_esc=0.0, theta_inj=0.0, capacity_slack=0.0) -> pic_config:
+    cfg = pic_config()
+    cfg.box, cfg.ndim, cfg.plane = box, ndim, plane
+    cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
+    cfg.shape_order, cfg.precision, cfg.fp_iters, cfg.keb_push = order, precision, fp_iters, keb_push
+    cfg.escape_mode, cfg.escape_dims = escape_mode, escape_dims
+    for a in range(3):
+        cfg.tile[a] = tile[a]
+        cfg.expand_rate[a] = rate[a]
+    cfg.seed = seed & 0xFFFFFFFF
+    cfg.c, cfg.s_shear, cfg.Omega0 = c, s, Omega0
+    cfg.l_esc, cfg.p_esc, cfg.theta_inj, cfg.capacity_slack = l_esc, p_esc, theta_inj, capacity_slack
+    return cfg
+
+
+class Box:
+    """One simulation box on the current CUDA device (thin owner of a handle)."""
+
+    def __init__(self, cfg: pic_config):
+        self.cfg = cfg
+        self.h = pic_init(cfg)
+        self.shape = (3, cfg.nz, cfg.ny, cfg.nx)
+
+    def close(self):
+        if self.h:
+            pic_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, species, q, m, x, u, ids=None):
+        pic_load_particles(self.h, species, q, m, x, u, ids)
+
+    def load_maxwellian(self, species, q, m, ppc, theta, drift=(0, 0, 0), noise_sigma=0.0, seed=0, id_base=0):
+        pic_load_maxwellian(self.h, species, q, m, ppc, theta, drift, noise_sigma, seed, id_base)
+
+    def set_fields(self, E, B):
+        pic_set_fields(self.h, E, B)
+
+    def set_uniform_fields(self, E, B):
+        pic_set_uniform_fields(self.h, E, B)
+
+    def step(self, n=1):
+        pic_step(self.h, n)
+
+    def set_step(self, step):
+        pic_set_step(self.h, step)
+
+    def sync(self):
+        pic_synchronize(self.h)
+
+    def diagnostics(self):
+        return pic_diagnostics(self.h)
+
+    def particles(self, species, want_dr=False):
+        return pic_get_particles(self.h, species, want_dr)
+
+    def fields(self):
+        return pic_get_fields(self.h, self.shape)
+
+    def count(self, species):
+        return pic_get_count(self.h, species)

@@ -1,0 +1,198 @@
+"""Seeded synthetic inputs shaped like the paper's setups.
+
+This module holds only input generation and unit bookkeeping (no part of the
+PIC method's arithmetic); both the CUDA path and the CPU oracle are fed from
+it.  Units are code units: dx = dt = 1, c = Courant number.  The paper's
+simulation data are not available, so every workload here is a seeded
+stand-in with the same kind of plasma: a pair plasma (e-, e+) with total
+density n0 = 2 ppc per cell, plasma frequency omega_p = c / d_e (d_e the skin
+depth in cells), macro mass 1 and macro charge q = omega_p sqrt(1/(4 pi n0)),
+guide field B0 from the cold magnetisation sigma = B0^2 / (4 pi n0 m c^2),
+or from the plasma beta = n0 theta m c^2 / (B0^2 / 8 pi).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class PairUnits:
+    c: float
+    skin_depth: float
+    ppc: int  # per species
+
+    @property
+    def n0(self) -> float:
+        return 2.0 * self.ppc
+
+    @property
+    def omega_p(self) -> float:
+        return self.c / self.skin_depth
+
+    @property
+    def q(self) -> float:
+        return self.omega_p * math.sqrt(1.0 / (4.0 * math.pi * self.n0))
+
+    def b0_from_sigma(self, sigma: float) -> float:
+        return math.sqrt(sigma * 4.0 * math.pi * self.n0 * self.c**2)
+
+    def b0_from_beta(self, beta: float, theta: float) -> float:
+        return math.sqrt(8.0 * math.pi * self.n0 * theta * self.c**2 / beta)
+
+
+def uniform_plasma(n, ppc, seed, uth=0.1, drift=(0.0, 0.0, 0.0), charges=(-1.0, 1.0), q=0.05, ignorable=None):
+    """Species dicts with ppc particles per cell uniformly placed, Gaussian
+    momenta of deviation uth (cells/step) per component.  `ignorable` is the
+    2D ignorable axis (its coordinate is set to 0.5)."""
+    r = np.random.default_rng(seed)
+    ncell = int(n[0]) * int(n[1]) * int(n[2])
+    out = []
+    next_id = 0
+    for sign in charges:
+        N = ncell * ppc
+        x = r.uniform(0.0, 1.0, (N, 3)) * np.asarray(n, dtype=float)
+        if ignorable is not None:
+            x[:, ignorable] = 0.5
+        u = r.normal(0.0, uth, (N, 3)) + np.asarray(drift, dtype=float)
+        out.append({"q": sign * q, "m": 1.0, "x": x, "u": u,
+                    "id": np.arange(next_id, next_id + N, dtype=np.uint32)})
+        next_id += N
+    return out
+
+
+def random_fields(n, seed, e_amp=0.01, b_amp=0.05, b0=(0.0, 0.0, 0.0)):
+    """E, B arrays [3][nz][ny][nx] with independent Gaussian values plus a
+    uniform B0 (a single step is defined for any field)."""
+    r = np.random.default_rng(seed)
+    shape = (3, n[2], n[1], n[0])
+    E = r.normal(0.0, e_amp, shape)
+    B = r.normal(0.0, b_amp, shape)
+    for c in range(3):
+        B[c] += b0[c]
+    return E, B
+
+
+def smooth_fields(n, seed, e_amp=0.01, b_amp=0.05, modes=(1, 2), b0=(0.0, 0.0, 0.0)):
+    """Sum of a few random-phase Fourier modes per component (periodic)."""
+    r = np.random.default_rng(seed)
+    nx, ny, nz = n
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    E = np.zeros((3, nz, ny, nx))
+    B = np.zeros((3, nz, ny, nx))
+    for arr, amp in ((E, e_amp), (B, b_amp)):
+        for c in range(3):
+            for m in modes:
+                ph = r.uniform(0, 2 * math.pi, 3)
+                kx = 2 * math.pi * m / nx
+                ky = 2 * math.pi * m / ny if ny > 1 else 0.0
+                kz = 2 * math.pi * m / nz if nz > 1 else 0.0
+                arr[c] += amp * np.cos(kx * i + ph[0]) * np.cos(ky * j + ph[1]) * np.cos(kz * k + ph[2])
+    for c in range(3):
+        B[c] += b0[c]
+    return E, B
+
+
+@dataclass
+class Workload:
+    """A configuration of the paper-shaped benchmark suite."""
+    name: str
+    box: int
+    ndim: int
+    plane: int
+    n: tuple
+    ppc: int
+    theta: float
+    order: int
+    fp64: bool
+    steps: int
+    c: float = 0.45
+    skin_depth: float = 5.0
+    sigma: float | None = None
+    beta: float | None = None
+    b_dir: tuple = (0.0, 0.0, 1.0)
+    s: float = 0.0
+    Omega0_wp: float = 0.0       # Omega0 in units of omega_p
+    rate_wp: tuple = (0.0, 0.0, 0.0)  # expansion rates in units of omega_p
+    escape_mode: int = 0
+    t_esc_Lc: float = 0.0        # t_esc in units of L/c
+    l_esc_L: float = 0.0         # l_esc in units of L
+    theta_inj: float = 0.0
+    noise: float = 0.0           # Gaussian momentum noise, units of c
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def units(self) -> PairUnits:
+        return PairUnits(self.c, self.skin_depth, self.ppc)
+
+    @property
+    def n_particles(self) -> int:
+        return 2 * self.ppc * self.n[0] * self.n[1] * self.n[2]
+
+    def b0(self):
+        u = self.units
+        if self.sigma is not None:
+            mag = u.b0_from_sigma(self.sigma)
+        elif self.beta is not None:
+            mag = u.b0_from_beta(self.beta, self.theta)
+        else:
+            mag = 0.0
+        d = np.asarray(self.b_dir, dtype=float)
+        return tuple(mag * d / np.linalg.norm(d))
+
+    def config_kwargs(self):
+        u = self.units
+        wp = u.omega_p
+        L = float(self.n[0])
+        kw = dict(box=self.box, nx=self.n[0], ny=self.n[1], nz=self.n[2], ndim=self.ndim, plane=self.plane,
+                  c=self.c, order=self.order, s=self.s, Omega0=self.Omega0_wp * wp,
+                  rate=tuple(r * wp for r in self.rate_wp), escape_mode=self.escape_mode,
+                  theta_inj=self.theta_inj)
+        if self.escape_mode == 2:
+            kw["p_esc"] = 1.0 / (self.t_esc_Lc * L / self.c)
+        if self.escape_mode == 1:
+            kw["l_esc"] = self.l_esc_L * L
+        return kw
+
+
+# The benchmark suite: synthetic stand-ins for the paper's three example
+# setups (Sec. 2.3 MRI shearing box, Sec. 3.3 expanding firehose box, Sec. 4.2
+# leaky turbulence box), with the sizes of the measured configurations.
+SHEAR_2D_FP64 = Workload("ksb2d_64x64_fp64", box=1, ndim=2, plane=1, n=(64, 1, 64), ppc=16, theta=0.1, order=1,
+                         fp64=True, steps=100, sigma=1.0, b_dir=(0, 0, 1), s=1.5, Omega0_wp=1e-3)
+EXPAND_3D_FP32 = Workload("keb3d_128_fp32", box=2, ndim=3, plane=0, n=(128, 128, 128), ppc=32, theta=0.05, order=2,
+                          fp64=False, steps=2000, sigma=0.5, b_dir=(1, 1, 0), rate_wp=(0.0, 1e-4, 1e-4))
+SHEAR_3D_FP32 = Workload("ksb3d_256_fp32", box=1, ndim=3, plane=0, n=(256, 256, 256), ppc=32, theta=0.3, order=2,
+                         fp64=False, steps=5000, beta=1e3, b_dir=(0, 0, 1), s=1.5, Omega0_wp=2e-3, noise=1e-3)
+LEAKY_2D_FP32 = Workload("leaky2d_2048_fp32", box=3, ndim=2, plane=0, n=(2048, 2048, 1), ppc=64, theta=1.0, order=1,
+                         fp64=False, steps=10000, sigma=0.1, b_dir=(0, 0, 1), escape_mode=2, t_esc_Lc=1.0,
+                         theta_inj=1.0)
+
+SUITE = {w.name: w for w in (SHEAR_2D_FP64, EXPAND_3D_FP32, SHEAR_3D_FP32, LEAKY_2D_FP32)}
+
+
+def scaled(w: Workload, n, ppc=None, name=None) -> Workload:
+    """The same workload on another grid (and optionally ppc)."""
+    from dataclasses import replace
+    return replace(w, n=tuple(n), ppc=ppc or w.ppc, name=name or f"{w.name}@{'x'.join(map(str, n))}")
+
+
+def host_maxwellian(w: Workload, seed: int, n=None, ppc=None):
+    """Host-side load of workload w (or a sub-box n): positions uniform,
+    momenta isotropic with Gaussian components of variance theta c^2 for
+    theta < 0.2 (nonrelativistic) -- an input recipe, not the reinjection law."""
+    n = n or w.n
+    ppc = ppc or w.ppc
+    u = w.units
+    uth = math.sqrt(w.theta) * w.c
+    ign = None
+    if w.ndim == 2:
+        ign = 2 if w.plane == 0 else 1
+    sp = uniform_plasma(n, ppc, seed, uth=uth, q=u.q, ignorable=ign)
+    if w.noise:
+        r = np.random.default_rng(seed + 1)
+        for d in sp:
+            d["u"] += r.normal(0.0, w.noise * w.c, d["u"].shape)
+    return sp

@@ -1,0 +1,56 @@
+"""The C-ABI library loads and exports every symbol include/pic.h declares,
+and host-side validation rejects bad configurations -- no GPU needed."""
+import ctypes
+
+import pytest
+
+from paper_2602_15939_gb300 import build as B
+from paper_2602_15939_gb300 import pic as P
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def test_exports_every_declared_symbol():
+    names = P.header_functions()
+    assert len(names) >= 19
+    lib = ctypes.CDLL(P.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header():
+    assert set(P.header_functions()) <= set(P._SIGS)
+
+
+def test_version():
+    assert P.pic_abi_version() == 1
+    assert "sm_103a" in P.pic_version()
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(ndim=4), "ndim"),
+    (dict(nx=4), "at least 8"),
+    (dict(order=3), "shape_order"),
+    (dict(c=0.7), "Courant"),
+    (dict(ndim=2, plane=P.PIC_PLANE_XY, nz=8), "nz = 1"),
+    (dict(box=P.PIC_BOX_LEAKY, escape_mode=P.PIC_ESC_DISPLACEMENT, l_esc=0.0, theta_inj=1.0), "l_esc"),
+    (dict(box=P.PIC_BOX_SHEAR, s=1.5, Omega0=0.5, nx=64), "shear speed"),
+])
+def test_validation_rejects_bad_configs(kw, msg):
+    base = dict(nx=8, ny=8, nz=8)
+    base.update(kw)
+    cfg = P.make_config(**base)
+    with pytest.raises(P.PicError) as e:
+        P.pic_init(cfg)
+    assert e.value.status == P.PIC_ERR_ARG
+    assert msg in str(e.value)
+
+
+def test_null_handle_calls_fail_cleanly():
+    lib = P.lib()
+    assert lib.pic_step(None, 1) == P.PIC_ERR_ARG
+    assert lib.pic_destroy(None) == P.PIC_OK
+    assert lib.pic_synchronize(None) == P.PIC_ERR_ARG
