@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the PIC step (particle-steps/s) on GB300.
+
+Default workload: the 3D expanding-box pair plasma, 128^3 cells, 32 particles
+per cell per species (134,217,728 particles), quadratic shapes, FP32 particle
+state (int32 cell + float offsets) with FP64 expansion factors -- a seeded
+synthetic stand-in shaped like the paper's expanding-box setup (Sec. 3.3).
+A "step" is one full PIC step: sort-in-place, gather, push, deposit, current
+fold and the transformed Maxwell update.  Inputs (4.3 GB of particles) are
+larger than the L2 cache, so no flush is needed between steps.
+
+Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs an independent replica (weak scaling;
+the box does not shard), timing is the max over ranks of CUDA-event time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (gather+push+deposit), FP32 vs FP64; ensemble p99 latency"
+UNIT = "particle-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="keb3d_128_fp32")
+    ap.add_argument("--grid", default=None, help="override the grid, e.g. 64,64,64 (profiling a smaller case)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--kernel-only", action="store_true", help="warmup + timed steps only (for profiler runs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("particle.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2602_15939_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(workload):
+    """DRAM bytes per launch of the particle kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", f"tile_kernel_{workload}.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
+    if not m_hash or not m_b or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_b.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_rate(w, n_sub, steps, seed=0):
+    """Particle-steps/s of the FP64 CPU oracle on a sub-box of workload w."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2602_15939_gb300 import workloads as W
+
+    sp = W.host_maxwellian(w, seed, n=n_sub)
+    wp = w.units.omega_p
+    box = {0: O.BOX_PERIODIC, 1: O.BOX_SHEAR, 2: O.BOX_EXPAND, 3: O.BOX_LEAKY}[w.box]
+    kw = w.config_kwargs()
+    p = O.make_params(*n_sub, w.c, order=w.order, box=box, s=w.s, Omega0=w.Omega0_wp * wp,
+                      rate=tuple(r * wp for r in w.rate_wp), esc_mode=w.escape_mode,
+                      p_esc=kw.get("p_esc", 0.0), l_esc=kw.get("l_esc", 0.0), theta_inj=w.theta_inj)
+    E = np.zeros((3, n_sub[2], n_sub[1], n_sub[0]))
+    B = np.zeros_like(E)
+    for c, v in enumerate(w.b0()):
+        B[c] = v
+    st = O.State(p, E, B, sp)
+    npart = sum(len(d["x"]) for d in sp)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        st.step(1)
+        times.append(time.perf_counter() - t0)
+    return npart, times
+
+
+def sub_box(w):
+    if w.ndim == 3:
+        return (16, 16, 16)
+    return (64, 64, 1) if w.plane == 0 else (64, 1, 64)
+
+
+def run_reference(args):
+    from paper_2602_15939_gb300 import workloads as W
+
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = W.SUITE[args.workload]
+    n_sub = sub_box(w)
+    npart, _ = oracle_rate(w, n_sub, 0)
+    _, wt = oracle_rate(w, n_sub, args.warmup + args.steps)
+    times = wt[args.warmup:]
+    tot = sum(times)
+    value = npart * len(times) / tot
+    sample = f"{n_sub[0]}x{n_sub[1]}x{n_sub[2]} sub-box of {w.name}, {w.ppc} ppc/species ({npart} particles), " \
+             f"{len(times)} timed steps after {args.warmup} warm-up"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "sample": sample, "box": "expanding" if w.box == 2 else str(w.box)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def particle_bytes(fp64, ndim, leaky_disp):
+    """Algorithmic bytes per particle-step of the fused kernel: the particle
+    state read once and written once (cell index, in-cell offsets, momentum,
+    id, and the leaky displacement when tracked)."""
+    es = 8 if fp64 else 4
+    state = 4 + ndim * es + 3 * es + 4 + (3 * es if leaky_disp else 0)
+    return 2 * state
+
+
+def setup_box(w, device, stream, fp64=None, seed=0):
+    from paper_2602_15939_gb300 import pic as P
+
+    fp64 = w.fp64 if fp64 is None else fp64
+    cfg = P.make_config(precision=P.PIC_FP64 if fp64 else P.PIC_FP32, device=device, seed=seed,
+                        **w.config_kwargs())
+    box = P.Box(cfg)
+    P.pic_set_stream(box.h, stream)
+    u = w.units
+    box.load_maxwellian(0, -u.q, 1.0, w.ppc, w.theta, noise_sigma=w.noise * w.c, seed=seed, id_base=0)
+    box.load_maxwellian(1, u.q, 1.0, w.ppc, w.theta, noise_sigma=w.noise * w.c, seed=seed + 1,
+                        id_base=w.ppc * w.n[0] * w.n[1] * w.n[2])
+    box.set_uniform_fields((0.0, 0.0, 0.0), w.b0())
+    return box
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2602_15939_gb300 import build as libbuild
+    from paper_2602_15939_gb300 import pic as P
+    from paper_2602_15939_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    libbuild.build()
+    w = W.SUITE[args.workload]
+    if args.grid:
+        w = W.scaled(w, tuple(int(v) for v in args.grid.split(",")))
+    stream = torch.cuda.Stream()
+    box = setup_box(w, local, stream.cuda_stream, seed=1000 * rank)
+    npart = w.n_particles
+    box.step(args.warmup)
+    box.sync()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    P.pic_set_profiling(box.h, True)
+    P.pic_reset_profile(box.h)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    box.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    prof = P.pic_get_profile(box.h)
+    P.pic_set_profiling(box.h, False)
+    diag = box.diagnostics()
+    assert diag.error_word == 0, diag.error_word
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = npart * args.steps * world / (ms / 1e3)
+    particle_ms = prof.ms_particle / max(1, prof.particle_launches)
+    gpu_launches = int(prof.launches)
+
+    peak, peak_kind = measured_peaks()
+    ncell = w.n[0] * w.n[1] * w.n[2]
+    bpp = particle_bytes(w.fp64, w.ndim, w.escape_mode == 1)
+    es = 8 if w.fp64 else 4
+    alg_bytes = npart * bpp + ncell * (6 + 3) * es
+    achieved = alg_bytes / (particle_ms / 1e3) / 1e9
+    traffic = stored_traffic(w.name)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                "kernel": "tile_kernel (fused gather+push+deposit+sort)",
+                "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_particle": bpp,
+                "avg_launch_ms": particle_ms}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if w.fp64 else "f32", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.n), "ppc_per_species": w.ppc, "particles": npart,
+                       "shape_order": w.order, "box": "expanding", "expansion_rate_wp": list(w.rate_wp),
+                       "precision": "int32 cell + fp32 offsets/momenta, fp64 l(t)",
+                       "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"},
+            "particle_phase": {"value": npart / (particle_ms / 1e3), "unit": UNIT, "avg_launch_ms": particle_ms},
+            "profile_ms": {"particle": prof.ms_particle, "field": prof.ms_field, "other": prof.ms_other},
+            "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks}
+
+    # FP64 path on the same workload (the plain FP64 method), a few steps
+    if not args.no_fp64 and not args.kernel_only:
+        box.close()
+        torch.cuda.synchronize()
+        b64 = setup_box(w, local, stream.cuda_stream, fp64=True, seed=1000 * rank)
+        b64.step(2)
+        b64.sync()
+        k64 = max(2, min(args.steps, 5))
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        b64.step(k64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        line["fp64"] = {"value": npart * k64 / (ms64 / 1e3), "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64}
+        b64.close()
+        box = None
+    elif box is not None:
+        box.close()
+
+    # end to end through the C ABI with pinned host buffers
+    if not args.no_e2e and not args.kernel_only:
+        line["e2e"] = run_e2e(w, local, stream, args.steps, rank)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.kernel_only:
+        n_sub = sub_box(w)
+        n_o, times = oracle_rate(w, n_sub, 5)
+        line["cpu_baseline"] = {"value": n_o * len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{n_sub[0]}x{n_sub[1]}x{n_sub[2]} sub-box of {w.name} at {w.ppc} "
+                                          f"ppc/species ({n_o} particles), 5 steps, single-threaded FP64 C"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(w, device, stream, steps, rank):
+    """Same metric through the public API with host buffers: load the whole
+    particle state from pinned host memory, K x (step + diagnostics read-back),
+    read the final particle state back; all inside the timed region."""
+    import numpy as np
+    import torch
+
+    from paper_2602_15939_gb300 import pic as P
+    from paper_2602_15939_gb300 import workloads as W
+
+    sp = W.host_maxwellian(w, 7 + rank)
+    pinned = []
+    for d in sp:
+        n = len(d["x"])
+        tx = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+        tu = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+        ti = torch.empty((n,), dtype=torch.int32, pin_memory=True)
+        tx.numpy()[:] = d["x"]
+        tu.numpy()[:] = d["u"]
+        ti.numpy()[:] = d["id"].view(np.int32)
+        pinned.append((d["q"], tx, tu, ti))
+    del sp
+    outs = [(torch.empty_like(tx), torch.empty_like(tu), torch.empty_like(ti)) for _, tx, tu, ti in pinned]
+    cfg = P.make_config(precision=P.PIC_FP64 if w.fp64 else P.PIC_FP32, device=device, **w.config_kwargs())
+    box = P.Box(cfg)
+    P.pic_set_stream(box.h, stream.cuda_stream)
+    npart = sum(len(t[1]) for t in pinned)
+    lib = P.lib()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s, (q, tx, tu, ti) in enumerate(pinned):
+        P._check(box.h, lib.pic_load_particles(box.h, s, q, 1.0, len(tx), P.C.cast(tx.data_ptr(), P._D),
+                                               P.C.cast(tu.data_ptr(), P._D), P.C.cast(ti.data_ptr(), P._U32)))
+    box.set_uniform_fields((0.0, 0.0, 0.0), w.b0())
+    for _ in range(steps):
+        box.step(1)
+        box.diagnostics()
+    for s, (ox, ou, oi) in enumerate(outs):
+        P._check(box.h, lib.pic_get_particles(box.h, s, P.C.cast(ox.data_ptr(), P._D), P.C.cast(ou.data_ptr(), P._D),
+                                              P.C.cast(oi.data_ptr(), P._U32), None))
+    box.sync()
+    dt = time.perf_counter() - t0
+    box.close()
+    h2d = sum(tx.numel() * 8 + tu.numel() * 8 + ti.numel() * 4 for _, tx, tu, ti in pinned)
+    d2h = h2d + steps * P.C.sizeof(P.pic_diag)
+    return {"value": npart * steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h / steps, "steps": steps, "seconds": dt,
+            "includes": "pic_load_particles from pinned host memory, per step pic_step + pic_diagnostics, "
+                        "final pic_get_particles"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
