@@ -85,7 +85,7 @@ typedef struct pic_config {
     int32_t escape_mode;  /* leaky box: PIC_ESC_* */
     int32_t escape_dims;  /* leaky displacement test over (x,y) [2] or (x,y,z) [3] */
     int32_t tile[3];      /* particle tile in cells per axis; 0 = automatic */
-    int32_t reserved0;
+    int32_t device;       /* CUDA device ordinal the handle lives on */
     uint32_t seed;        /* key word of the Philox streams (escape, reinjection, loading) */
     uint32_t reserved1;
     double c;             /* Courant number; 0 < c, and c * sqrt(ndim) < 1 */

@@ -29,6 +29,7 @@ enum : int {
     ERRB_NONFINITE = 2,
     ERRB_LOOSE_OVERFLOW = 4,
     ERRB_BAD_CELL = 8,
+    ERRB_J_RANGE = 16,  // a fixed-point current sum reached half its range
 };
 
 template <int G> struct GeomT {

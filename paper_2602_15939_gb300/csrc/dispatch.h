@@ -7,7 +7,8 @@
 namespace pic {
 
 struct KernelSet {
-    const void* tile;
+    const void* tile;      // 256 threads per CTA
+    const void* tile512;   // 512 threads per CTA
     const void* loose;
 };
 

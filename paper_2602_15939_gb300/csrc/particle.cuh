@@ -19,6 +19,8 @@
 // point.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace pic {
@@ -84,6 +86,12 @@ struct StepP {
     int esc_dims;
     int* err;
     unsigned long long* counters;  // [0] escaped, [1] superluminal
+    // FP32 path: fixed-point current accumulation in shared memory.  A
+    // contribution v is added as round(v * fx_scale) to an int32 word; one
+    // unit is worth fx_unit = 1 / fx_scale.  The range 2^31 fx_unit is 16x
+    // the current of the mean density moving coherently at c (at least 64 q).
+    float fx_scale;
+    double fx_unit;
 };
 
 // ---- shapes --------------------------------------------------------------------
@@ -129,61 +137,93 @@ template <class T> struct Shape<T, 2> {
     }
 };
 
-// ---- field accessors -------------------------------------------------------------
+// ---- field and current accessors -------------------------------------------------
+// Fields and currents are addressed by a linear index: cell (i,j,k) of an
+// accessor's box is i + j*SY + k*SZ and component c adds c*SC.  The shared-
+// memory boxes of a tile have compile-time strides (fixed tile shape per
+// geometry), so every stencil offset is an immediate; the global padded
+// arrays (loose particles) use runtime strides.
+
+template <int G> struct TileDims {
+    static constexpr int TX = (G == G3D) ? 8 : 16;
+    static constexpr int TY = (G == G3D) ? 8 : (G == G2XY ? 16 : 1);
+    static constexpr int TZ = (G == G3D) ? 8 : (G == G2XZ ? 16 : 1);
+    static constexpr int BX = TX + 4;
+    static constexpr int BY = GeomT<G>::AY ? TY + 4 : 1;
+    static constexpr int BZ = GeomT<G>::AZ ? TZ + 4 : 1;
+    static constexpr int JX = TX + 5;
+    static constexpr int JY = GeomT<G>::AY ? TY + 5 : 1;
+    static constexpr int JZ = GeomT<G>::AZ ? TZ + 5 : 1;
+    static constexpr int FB = BX * BY * BZ;
+    static constexpr int JB = JX * JY * JZ;
+};
 
 // Shared-memory field boxes: E and B, 3 components each, [comp][bz][by][bx].
-template <class T> struct SmemFields {
+template <class T, int G> struct SmemFields {
+    using D = TileDims<G>;
+    static constexpr int SY = D::BX, SZ = D::BX * D::BY, SC = D::FB;
     const T* e;
     const T* b;
-    int bx, by, bz;
-    __device__ T get(int comp, int i, int j, int k) const {
-        const T* f = comp < 3 ? e : b;
-        const int c = comp < 3 ? comp : comp - 3;
-        return f[((c * bz + k) * by + j) * bx + i];
-    }
+    __device__ T at(int comp, int idx) const { return comp < 3 ? e[comp * SC + idx] : b[(comp - 3) * SC + idx]; }
 };
 
-// Global padded fields.
+// Global padded fields (index = padded linear index).
 template <class T> struct GlobalFields {
-    const T* E;
-    const T* B;
-    Grid g;
-    __device__ T get(int comp, int i, int j, int k) const {
-        // (i,j,k) are padded indices here
-        const T* base = comp < 3 ? E + (long long)comp * g.cstride : B + (long long)(comp - 3) * g.cstride;
-        return __ldg(base + ((long long)k * g.py + j) * g.px + i);
+    const T* e;
+    const T* b;
+    long long SY, SZ, SC;
+    __device__ T at(int comp, long long idx) const {
+        return comp < 3 ? __ldg(e + comp * SC + idx) : __ldg(b + (comp - 3) * SC + idx);
     }
 };
 
-template <class T> struct SmemJ {
-    T* j;
-    int jx, jy, jz;
-    __device__ void add(int comp, int i, int j_, int k, T v) const {
-        atomic_add_shared(&j[((comp * jz + k) * jy + j_) * jx + i], v);
+// Shared-memory current box of a tile.  FP32: one int32 fixed-point word per
+// point (native integer shared atomics); values arrive pre-multiplied by the
+// fixed-point scale and are rounded to the nearest unit.  Integer addition is
+// exact modulo 2^32, so only the tile's final sum per point must fit (checked
+// at the flush).  FP64: one double per point.
+template <class T, int G> struct SmemJ;
+
+template <int G> struct SmemJ<float, G> {
+    using D = TileDims<G>;
+    static constexpr int SY = D::JX, SZ = D::JX * D::JY, SC = D::JB;
+    int* j;
+    __device__ void add(int comp, int idx, float v) const {
+        const int iv = __float2int_rn(v);
+        if (iv != 0) atomicAdd(j + comp * SC + idx, iv);
+    }
+};
+
+template <int G> struct SmemJ<double, G> {
+    using D = TileDims<G>;
+    static constexpr int SY = D::JX, SZ = D::JX * D::JY, SC = D::JB;
+    double* j;
+    __device__ void add(int comp, int idx, double v) const {
+        if (v != 0.0) atomicAdd(j + comp * SC + idx, v);
     }
 };
 
 template <class T> struct GlobalJ {
     T* J;
-    Grid g;
-    __device__ void add(int comp, int i, int j_, int k, T v) const {
-        red_add_global(J + (long long)comp * g.cstride + ((long long)k * g.py + j_) * g.px + i, v);
+    long long SY, SZ, SC;
+    __device__ void add(int comp, long long idx, T v) const {
+        if (v != T(0)) red_add_global(J + comp * SC + idx, v);
     }
 };
 
 // ---- gather ------------------------------------------------------------------------
-// (li, lj, lk): the particle's cell in the accessor's index space; o: offsets.
-template <class T, int G, int ORD, class F>
-__device__ inline void gather(const F& fa, int li, int lj, int lk, const T o[3], T Ep[3], T Bp[3]) {
+// cidx: linear index of the particle's cell in the accessor's box; o: offsets.
+template <class T, int G, int ORD, class F, class I>
+__device__ inline void gather(const F& fa, I cidx, const T o[3], T Ep[3], T Bp[3]) {
     using GT = GeomT<G>;
     constexpr int NP = ORD + 1;
     T wn[3][NP], ws[3][NP];
-    int offn[3], offs[3];
+    int offn[3] = {0, 0, 0}, offs[3] = {0, 0, 0};
     Shape<T, ORD>::node(o[0], offn[0], wn[0]);
     Shape<T, ORD>::stag(o[0], offs[0], ws[0]);
     if (GT::AY) { Shape<T, ORD>::node(o[1], offn[1], wn[1]); Shape<T, ORD>::stag(o[1], offs[1], ws[1]); }
     if (GT::AZ) { Shape<T, ORD>::node(o[2], offn[2], wn[2]); Shape<T, ORD>::stag(o[2], offs[2], ws[2]); }
-    // components: E x,y,z then B x,y,z; stag[comp][axis]
+    // components: E x,y,z then B x,y,z; staggered (1) or node-centred (0) per axis
     constexpr bool ST[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
     T out[6];
 #pragma unroll
@@ -194,30 +234,26 @@ __device__ inline void gather(const F& fa, int li, int lj, int lk, const T o[3],
         if (GT::AY && GT::AZ) {
             const T* wy = ST[comp][1] ? ws[1] : wn[1];
             const T* wz = ST[comp][2] ? ws[2] : wn[2];
-            const int oy = ST[comp][1] ? offs[1] : offn[1];
-            const int oz = ST[comp][2] ? offs[2] : offn[2];
+            const I b0 = cidx + ox + (ST[comp][1] ? offs[1] : offn[1]) * fa.SY + (ST[comp][2] ? offs[2] : offn[2]) * fa.SZ;
 #pragma unroll
             for (int c = 0; c < NP; ++c)
 #pragma unroll
                 for (int b = 0; b < NP; ++b) {
-                    T wyz = wy[b] * wz[c];
                     T row = T(0);
 #pragma unroll
-                    for (int a = 0; a < NP; ++a) row += wx[a] * fa.get(comp, li + ox + a, lj + oy + b, lk + oz + c);
-                    acc += wyz * row;
+                    for (int a = 0; a < NP; ++a) row += wx[a] * fa.at(comp, b0 + a + b * fa.SY + c * fa.SZ);
+                    acc += (wy[b] * wz[c]) * row;
                 }
         } else {
             constexpr int A2 = GT::AY ? 1 : 2;  // second active axis
             const T* w2 = ST[comp][A2] ? ws[A2] : wn[A2];
-            const int o2 = ST[comp][A2] ? offs[A2] : offn[A2];
+            const auto s2 = A2 == 1 ? fa.SY : fa.SZ;
+            const I b0 = cidx + ox + (ST[comp][A2] ? offs[A2] : offn[A2]) * s2;
 #pragma unroll
             for (int b = 0; b < NP; ++b) {
                 T row = T(0);
 #pragma unroll
-                for (int a = 0; a < NP; ++a) {
-                    if (A2 == 1) row += wx[a] * fa.get(comp, li + ox + a, lj + o2 + b, lk);
-                    else row += wx[a] * fa.get(comp, li + ox + a, lj, lk + o2 + b);
-                }
+                for (int a = 0; a < NP; ++a) row += wx[a] * fa.at(comp, b0 + a + b * s2);
                 acc += w2[b] * row;
             }
         }
@@ -354,119 +390,95 @@ __device__ inline void push_keb(T u[3], const T E[3], const T B[3], T qdt2m, T q
 
 // ---- charge-conserving deposit (Esirkepov) -------------------------------------------
 // The particle moves from x0 = o (offsets in its start cell) to x1 = o + d,
-// |d| < 1 per axis.  With S0, S1 the node shapes on a 4-point window starting
-// at node wb (relative to the start cell), W_x = dS_x * F_yz with
-// F_yz = S0y S0z + dSy S0z / 2 + S0y dSz / 2 + dSy dSz / 3, so the running sum
-// J_x(l + 1/2) = -q sum_{l' <= l} W_x(l') = -q CS_x(l) F_yz.  On the 2D
-// ignorable axis the current is q v F of the two active axes.
-template <class T, int G, int ORD, class JA>
-__device__ inline void deposit(const JA& ja, int li, int lj, int lk, const T o[3], const T d[3], T q) {
+// |d| < 1 per axis.  With S0, S1 the node shapes on a window of ORD+2 nodes
+// starting at node wb (relative to the start cell), W_x = dS_x * F_yz with
+// F_yz = S0y S0z + dSy S0z / 2 + S0y dSz / 2 + dSy dSz / 3, so the running
+// sum J_x(l + 1/2) = -q sum_{l' <= l} W_x(l') = -q CS_x(l) F_yz: an outer
+// product of ORD+1 running sums and (ORD+2)^2 weights per component.  On the
+// 2D ignorable axis the current is q v F of the two active axes.  qs is the
+// charge times the accumulator's value scale; cidx the start cell's linear
+// index in the accumulator's box.
+template <class T, int G, int ORD, class JA, class I>
+__device__ inline void deposit(const JA& ja, I cidx, const T o[3], const T d[3], T qs) {
     using GT = GeomT<G>;
-    T S0[3][4], S1[3][4], DS[3][4], CS[3][4];
+    constexpr int NW = ORD + 2;  // window nodes
+    T S0[3][4], DS[3][4], CS[3][4];
     int wb[3] = {0, 0, 0};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if ((a == 1 && !GT::AY) || (a == 2 && !GT::AZ)) continue;
-        T x1 = o[a] + d[a];
-        // lowest node that can carry weight for either position
+        const T x1 = o[a] + d[a];
         if (ORD == 1) {
             wb[a] = x1 < T(0) ? -1 : 0;
         } else {
-            int n0 = o[a] >= T(0.5) ? 1 : 0;
-            int n1 = (int)t_floor<T>(x1 + T(0.5));
+            const int n0 = o[a] >= T(0.5) ? 1 : 0;
+            const int n1 = (int)t_floor<T>(x1 + T(0.5));
             wb[a] = (n0 < n1 ? n0 : n1) - 1;
         }
+        T S1[4];
         Shape<T, ORD>::window(o[a], wb[a], S0[a]);
-        Shape<T, ORD>::window(x1, wb[a], S1[a]);
+        Shape<T, ORD>::window(x1, wb[a], S1);
         T run = T(0);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            DS[a][m] = S1[a][m] - S0[a][m];
+            DS[a][m] = S1[m] - S0[a][m];
             run += DS[a][m];
-            CS[a][m] = run;
+            CS[a][m] = -qs * run;
         }
     }
-    constexpr int NW = ORD + 2;  // window points that can be non-zero: 3 (order 1), 4 (order 2)
     const T third = T(1) / T(3);
+    const I base = cidx + wb[0] + wb[1] * ja.SY + wb[2] * ja.SZ;
     if (GT::AY && GT::AZ) {
-        // J_x
 #pragma unroll
         for (int n = 0; n < NW; ++n)
 #pragma unroll
             for (int m = 0; m < NW; ++m) {
-                T fyz = S0[1][m] * S0[2][n] + T(0.5) * (DS[1][m] * S0[2][n] + S0[1][m] * DS[2][n]) + third * DS[1][m] * DS[2][n];
-                if (fyz != T(0)) {
+                const T fyz = S0[1][m] * S0[2][n] + T(0.5) * (DS[1][m] * S0[2][n] + S0[1][m] * DS[2][n]) + third * DS[1][m] * DS[2][n];
 #pragma unroll
-                    for (int l = 0; l < NW - 1; ++l)
-                        if (CS[0][l] != T(0)) ja.add(0, li + wb[0] + l, lj + wb[1] + m, lk + wb[2] + n, -q * CS[0][l] * fyz);
-                }
+                for (int l = 0; l < NW - 1; ++l) ja.add(0, base + l + m * ja.SY + n * ja.SZ, CS[0][l] * fyz);
             }
-        // J_y
 #pragma unroll
         for (int n = 0; n < NW; ++n)
 #pragma unroll
             for (int l = 0; l < NW; ++l) {
-                T fxz = S0[0][l] * S0[2][n] + T(0.5) * (DS[0][l] * S0[2][n] + S0[0][l] * DS[2][n]) + third * DS[0][l] * DS[2][n];
-                if (fxz != T(0)) {
+                const T fxz = S0[0][l] * S0[2][n] + T(0.5) * (DS[0][l] * S0[2][n] + S0[0][l] * DS[2][n]) + third * DS[0][l] * DS[2][n];
 #pragma unroll
-                    for (int m = 0; m < NW - 1; ++m)
-                        if (CS[1][m] != T(0)) ja.add(1, li + wb[0] + l, lj + wb[1] + m, lk + wb[2] + n, -q * CS[1][m] * fxz);
-                }
+                for (int m = 0; m < NW - 1; ++m) ja.add(1, base + l + m * ja.SY + n * ja.SZ, CS[1][m] * fxz);
             }
-        // J_z
 #pragma unroll
         for (int m = 0; m < NW; ++m)
 #pragma unroll
             for (int l = 0; l < NW; ++l) {
-                T fxy = S0[0][l] * S0[1][m] + T(0.5) * (DS[0][l] * S0[1][m] + S0[0][l] * DS[1][m]) + third * DS[0][l] * DS[1][m];
-                if (fxy != T(0)) {
+                const T fxy = S0[0][l] * S0[1][m] + T(0.5) * (DS[0][l] * S0[1][m] + S0[0][l] * DS[1][m]) + third * DS[0][l] * DS[1][m];
 #pragma unroll
-                    for (int n = 0; n < NW - 1; ++n)
-                        if (CS[2][n] != T(0)) ja.add(2, li + wb[0] + l, lj + wb[1] + m, lk + wb[2] + n, -q * CS[2][n] * fxy);
-                }
+                for (int n = 0; n < NW - 1; ++n) ja.add(2, base + l + m * ja.SY + n * ja.SZ, CS[2][n] * fxy);
             }
     } else {
-        constexpr int A2 = GT::AY ? 1 : 2;   // second active axis
-        constexpr int IG = GT::AY ? 2 : 1;   // ignorable axis
-        // in-plane components
+        constexpr int A2 = GT::AY ? 1 : 2;  // second active axis
+        constexpr int IG = GT::AY ? 2 : 1;  // ignorable axis
+        constexpr int C2 = GT::AY ? 1 : 2;  // current component along A2
+        const auto s2 = A2 == 1 ? ja.SY : ja.SZ;
 #pragma unroll
         for (int m = 0; m < NW; ++m) {
-            T f2 = S0[A2][m] + T(0.5) * DS[A2][m];
-            if (f2 != T(0)) {
+            const T f2 = S0[A2][m] + T(0.5) * DS[A2][m];
 #pragma unroll
-                for (int l = 0; l < NW - 1; ++l)
-                    if (CS[0][l] != T(0)) {
-                        if (A2 == 1) ja.add(0, li + wb[0] + l, lj + wb[1] + m, lk, -q * CS[0][l] * f2);
-                        else ja.add(0, li + wb[0] + l, lj, lk + wb[2] + m, -q * CS[0][l] * f2);
-                    }
-            }
+            for (int l = 0; l < NW - 1; ++l) ja.add(0, base + l + m * s2, CS[0][l] * f2);
         }
 #pragma unroll
         for (int l = 0; l < NW; ++l) {
-            T f1 = S0[0][l] + T(0.5) * DS[0][l];
-            if (f1 != T(0)) {
+            const T f1 = S0[0][l] + T(0.5) * DS[0][l];
 #pragma unroll
-                for (int m = 0; m < NW - 1; ++m)
-                    if (CS[A2][m] != T(0)) {
-                        if (A2 == 1) ja.add(1, li + wb[0] + l, lj + wb[1] + m, lk, -q * CS[A2][m] * f1);
-                        else ja.add(2, li + wb[0] + l, lj, lk + wb[2] + m, -q * CS[A2][m] * f1);
-                    }
-            }
+            for (int m = 0; m < NW - 1; ++m) ja.add(C2, base + l + m * s2, CS[A2][m] * f1);
         }
         // out-of-plane component: q v_ign F(x, a2)
-        T qv = q * d[IG];
-        if (qv != T(0)) {
+        const T qv = qs * d[IG];
 #pragma unroll
-            for (int m = 0; m < NW; ++m)
+        for (int m = 0; m < NW; ++m)
 #pragma unroll
-                for (int l = 0; l < NW; ++l) {
-                    T f = S0[0][l] * S0[A2][m] + T(0.5) * (DS[0][l] * S0[A2][m] + S0[0][l] * DS[A2][m]) + third * DS[0][l] * DS[A2][m];
-                    if (f != T(0)) {
-                        if (A2 == 1) ja.add(IG, li + wb[0] + l, lj + wb[1] + m, lk, qv * f);
-                        else ja.add(IG, li + wb[0] + l, lj, lk + wb[2] + m, qv * f);
-                    }
-                }
-        }
+            for (int l = 0; l < NW; ++l) {
+                const T f = S0[0][l] * S0[A2][m] + T(0.5) * (DS[0][l] * S0[A2][m] + S0[0][l] * DS[A2][m]) + third * DS[0][l] * DS[A2][m];
+                ja.add(IG, base + l + m * s2, qv * f);
+            }
     }
 }
 
@@ -515,12 +527,12 @@ template <class T> __device__ inline void renorm(T& o, int& c) {
 // Push, move and deposit one particle; returns its destination physical cell
 // in p.  FA: field accessor, JA: current accumulator; (fi,fj,fk) and
 // (ji,jj,jk) are the particle's start cell in their index spaces.
-template <class T, int G, int ORD, int PUSH, int ESC, class FA, class JA>
-__device__ inline void advance_particle(Particle<T>& p, const FA& fa, int fi, int fj, int fk, const JA& ja, int ji, int jj,
-                                        int jk, const SpecStep<T>& S, const StepP& P, const Grid& g) {
+template <class T, int G, int ORD, int PUSH, int ESC, class FA, class JA, class I>
+__device__ inline void advance_particle(Particle<T>& p, const FA& fa, I fidx, const JA& ja, I jidx, T qs,
+                                        const SpecStep<T>& S, const StepP& P, const Grid& g) {
     using GT = GeomT<G>;
     T E[3], B[3];
-    gather<T, G, ORD>(fa, fi, fj, fk, p.o, E, B);
+    gather<T, G, ORD>(fa, fidx, p.o, E, B);
     const T c = T(P.c);
     const T inv_c2 = T(1) / (c * c);
     T d[3];
@@ -542,7 +554,7 @@ __device__ inline void advance_particle(Particle<T>& p, const FA& fa, int fi, in
         d[0] = d[1] = d[2] = T(0);
     }
     // current from the (comoving) displacement x^n -> x^n + d
-    deposit<T, G, ORD>(ja, ji, jj, jk, p.o, d, S.q);
+    deposit<T, G, ORD>(ja, jidx, p.o, d, qs);
 
     if (ESC == ESC_DISP) { p.dr[0] += d[0]; p.dr[1] += d[1]; p.dr[2] += d[2]; }
 
@@ -638,48 +650,44 @@ __device__ inline void place_mover(const Particle<T>& p, int dest, const SpecSte
     else atomicOr(P.err, ERRB_LOOSE_OVERFLOW);
 }
 
-constexpr int TPB = 256;
+constexpr int TPB = 256;  // threads per CTA of the loose kernel
 constexpr long long TMA_WAIT_LIMIT = 1ll << 24;
 
 // Dynamic shared memory: E box, B box (each 128-byte aligned, the TMA
-// destinations), the J box, the mbarrier and small counters.
-template <class T> struct SmemLayout {
-    int FB, JB;
-    size_t off_B, off_J, off_bar, bytes;
-    __host__ __device__ SmemLayout(const Tiling& tl) {
-        FB = tl.bx * tl.by * tl.bz;
-        JB = tl.jx * tl.jy * tl.jz;
-        off_B = ((size_t)3 * FB * sizeof(T) + 127) & ~(size_t)127;
-        off_J = off_B + (size_t)3 * FB * sizeof(T);
-        off_J = (off_J + 127) & ~(size_t)127;
-        off_bar = off_J + (size_t)3 * JB * sizeof(T);
-        off_bar = (off_bar + 15) & ~(size_t)15;
-        bytes = off_bar + 16 + 4 * (MAXSP + 2);
-    }
+// destinations), the J box (int32 for FP32, double for FP64), the mbarrier
+// and small counters.
+template <class T, int G> struct SmemLayout {
+    static constexpr int FB = TileDims<G>::FB, JB = TileDims<G>::JB;
+    static constexpr size_t off_B = ((size_t)3 * FB * sizeof(T) + 127) & ~(size_t)127;
+    static constexpr size_t off_J = (off_B + (size_t)3 * FB * sizeof(T) + 127) & ~(size_t)127;
+    static constexpr size_t off_bar = (off_J + (size_t)3 * JB * sizeof(T) + 15) & ~(size_t)15;
+    static constexpr size_t bytes = off_bar + 16 + 4 * (MAXSP + 2);
 };
 
-// The fused particle step for one tile (see the file header).
-template <class T, int G, int ORD, int PUSH, int ESC>
-__global__ void __launch_bounds__(TPB) tile_kernel(const __grid_constant__ CUtensorMap tmE,
+// The fused particle step for one tile (see the file header).  NT threads per CTA.
+template <class T, int G, int ORD, int PUSH, int ESC, int NT>
+__global__ void __launch_bounds__(NT, NT == 512 ? 2 : 3) tile_kernel(const __grid_constant__ CUtensorMap tmE,
                                                    const __grid_constant__ CUtensorMap tmB, Grid g, Tiling tl,
                                                    StepP P, SpecPack<T> SP, T* __restrict__ J) {
     using GT = GeomT<G>;
     constexpr bool LEAKY = (ESC == ESC_DISP);
+    using D = TileDims<G>;
+    using L = SmemLayout<T, G>;
+    using JW = typename std::conditional<sizeof(T) == 4, int, double>::type;
     extern __shared__ __align__(128) unsigned char smem[];
-    const SmemLayout<T> L(tl);
     T* sE = reinterpret_cast<T*>(smem);
-    T* sB = reinterpret_cast<T*>(smem + L.off_B);
-    T* sJ = reinterpret_cast<T*>(smem + L.off_J);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bar);
-    int* s_cnt = reinterpret_cast<int*>(smem + L.off_bar + 16);
+    T* sB = reinterpret_cast<T*>(smem + L::off_B);
+    JW* sJ = reinterpret_cast<JW*>(smem + L::off_J);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::off_bar);
+    int* s_cnt = reinterpret_cast<int*>(smem + L::off_bar + 16);
     int* s_ok = s_cnt + MAXSP;
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int t = blockIdx.x;
     const int ti = t % tl.ntx, tj = (t / tl.ntx) % tl.nty, tk = t / (tl.ntx * tl.nty);
-    const int t0x = ti * tl.tx, t0y = tj * tl.ty, t0z = tk * tl.tz;
-    // padded coordinate of physical t0 - 2 is t0 (GL = 2); x rounded down to the TMA quantum
-    const int xs = t0x & ~(tl.xalign - 1);
+    const int t0x = ti * D::TX, t0y = tj * D::TY, t0z = tk * D::TZ;
+    // padded coordinate of physical t0 - 2 is t0 (GL = 2); TX is a multiple of the TMA x quantum
+    const int xs = t0x;
     const int ys = GT::AY ? t0y : 0;
     const int zs = GT::AZ ? t0z : 0;
 
@@ -689,11 +697,11 @@ __global__ void __launch_bounds__(TPB) tile_kernel(const __grid_constant__ CUten
     }
     __syncthreads();
     if (tid == 0) {
-        mbar_arrive_expect_tx(bar, (uint32_t)(6 * L.FB * sizeof(T)));
+        mbar_arrive_expect_tx(bar, (uint32_t)(6 * L::FB * sizeof(T)));
         tma_load_4d(sE, &tmE, xs, ys, zs, 0, bar);
         tma_load_4d(sB, &tmB, xs, ys, zs, 0, bar);
     }
-    for (int i = tid; i < 3 * L.JB; i += blockDim.x) sJ[i] = T(0);
+    for (int i = tid; i < 3 * L::JB; i += NT) sJ[i] = JW(0);
     if (tid < MAXSP) s_cnt[tid] = 0;
     if (tid == 0) s_ok[0] = mbar_wait_bounded(bar, 0, TMA_WAIT_LIMIT) ? 1 : 0;
     __syncthreads();
@@ -702,8 +710,11 @@ __global__ void __launch_bounds__(TPB) tile_kernel(const __grid_constant__ CUten
         return;
     }
 
-    const SmemFields<T> fa{sE, sB, tl.bx, tl.by, tl.bz};
-    const SmemJ<T> ja{sJ, tl.jx, tl.jy, tl.jz};
+    const SmemFields<T, G> fa{sE, sB};
+    const SmemJ<T, G> ja{sJ};
+    using FA = SmemFields<T, G>;
+    using JA = SmemJ<T, G>;
+    const T vscale = sizeof(T) == 4 ? T(P.fx_scale) : T(1);
     // index-space origins (physical cell of local index 0)
     const int fox = xs - 2, foy = GT::AY ? t0y - 2 : 0, foz = GT::AZ ? t0z - 2 : 0;
     const int jox = t0x - 2, joy = GT::AY ? t0y - 2 : 0, joz = GT::AZ ? t0z - 2 : 0;
@@ -713,7 +724,8 @@ __global__ void __launch_bounds__(TPB) tile_kernel(const __grid_constant__ CUten
         const int nst = S.stay_in[t], nar = S.arr_in[t];
         const int n = nst + nar;
         const long long base = (long long)t * S.tcap;
-        for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+        const T qs = S.q * vscale;
+        for (int i0 = 0; i0 < n; i0 += NT) {
             const int i = i0 + tid;
             const bool valid = i < n;
             Particle<T> p;
@@ -721,9 +733,9 @@ __global__ void __launch_bounds__(TPB) tile_kernel(const __grid_constant__ CUten
             if (valid) {
                 const long long slot = i < nst ? base + i : base + S.tcap - nar + (i - nst);
                 load_particle<T, G>(S.in, slot, LEAKY, p);
-                advance_particle<T, G, ORD, PUSH, ESC>(p, fa, p.ci - fox, GT::AY ? p.cj - foy : 0,
-                                                       GT::AZ ? p.ck - foz : 0, ja, p.ci - jox,
-                                                       GT::AY ? p.cj - joy : 0, GT::AZ ? p.ck - joz : 0, S, P, g);
+                const int fidx = (p.ci - fox) + (GT::AY ? (p.cj - foy) * FA::SY : 0) + (GT::AZ ? (p.ck - foz) * FA::SZ : 0);
+                const int jidx = (p.ci - jox) + (GT::AY ? (p.cj - joy) * JA::SY : 0) + (GT::AZ ? (p.ck - joz) * JA::SZ : 0);
+                advance_particle<T, G, ORD, PUSH, ESC>(p, fa, fidx, ja, jidx, qs, S, P, g);
                 dest = tile_of<G>(tl, p.ci, p.cj, p.ck);
             }
             const bool stay = valid && dest == t;
@@ -737,18 +749,25 @@ __global__ void __launch_bounds__(TPB) tile_kernel(const __grid_constant__ CUten
     }
     __syncthreads();
     // flush the J tile: padded index of local point (a,b,c) is (t0x + a, t0y + b, t0z + c)
-    for (int idx = tid; idx < 3 * L.JB; idx += blockDim.x) {
-        T v = sJ[idx];
-        if (v == T(0)) continue;
-        int comp = idx / L.JB;
-        int r = idx - comp * L.JB;
-        int a = r % tl.jx;
-        int b = (r / tl.jx) % tl.jy;
-        int c = r / (tl.jx * tl.jy);
+    for (int idx = tid; idx < 3 * L::JB; idx += NT) {
+        T v;
+        if constexpr (sizeof(T) == 4) {
+            const int iv = sJ[idx];
+            if (iv == 0) continue;
+            if (iv > (1 << 30) || iv < -(1 << 30)) atomicOr(P.err, ERRB_J_RANGE);
+            v = (float)((double)iv * P.fx_unit);
+        } else {
+            v = sJ[idx];
+            if (v == T(0)) continue;
+        }
+        const int comp = idx / L::JB;
+        const int r = idx - comp * L::JB;
+        const int a = r % D::JX;
+        const int b = (r / D::JX) % D::JY;
+        const int c = r / (D::JX * D::JY);
         const int pi = jox + g.gx + a, pj = joy + g.gy + b, pk = joz + g.gz + c;
         if (pi >= g.px || pj >= g.py || pk >= g.pz) continue;  // beyond a ragged last tile: never deposited
-        long long gi = (long long)comp * g.cstride + ((long long)pk * g.py + pj) * g.px + pi;
-        red_add_global(J + gi, v);
+        red_add_global(J + (long long)comp * g.cstride + ((long long)pk * g.py + pj) * g.px + pi, v);
     }
     if (tid < P.nsp) SP.s[tid].stay_out[t] = s_cnt[tid];
 }
@@ -761,8 +780,9 @@ __global__ void __launch_bounds__(TPB) loose_kernel(Grid g, Tiling tl, StepP P, 
                                                     const T* __restrict__ E, const T* __restrict__ B, T* __restrict__ J) {
     using GT = GeomT<G>;
     constexpr bool LEAKY = (ESC == ESC_DISP);
-    const GlobalFields<T> fa{E, B, g};
-    const GlobalJ<T> ja{J, g};
+    const long long SY = g.px, SZ = (long long)g.px * g.py;
+    const GlobalFields<T> fa{E, B, SY, SZ, g.cstride};
+    const GlobalJ<T> ja{J, SY, SZ, g.cstride};
     for (int s = 0; s < P.nsp; ++s) {
         const SpecStep<T>& S = SP.s[s];
         long long n = *S.lcount_in;
@@ -770,8 +790,9 @@ __global__ void __launch_bounds__(TPB) loose_kernel(Grid g, Tiling tl, StepP P, 
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
             Particle<T> p;
             load_particle<T, G>(S.lin, i, LEAKY, p);
-            const int pi = p.ci + g.gx, pj = GT::AY ? p.cj + g.gy : 0, pk = GT::AZ ? p.ck + g.gz : 0;
-            advance_particle<T, G, ORD, PUSH, ESC>(p, fa, pi, pj, pk, ja, pi, pj, pk, S, P, g);
+            const long long cidx = (long long)(p.ci + g.gx) + (GT::AY ? (long long)(p.cj + g.gy) * SY : 0) +
+                                   (GT::AZ ? (long long)(p.ck + g.gz) * SZ : 0);
+            advance_particle<T, G, ORD, PUSH, ESC>(p, fa, cidx, ja, cidx, S.q, S, P, g);
             place_mover<T, G>(p, tile_of<G>(tl, p.ci, p.cj, p.ck), S, P, LEAKY);
         }
     }

@@ -69,6 +69,8 @@ struct pic_handle {
     Tiling tl;
     int push = PUSH_BORIS, esc = ESC_NONE;
     KernelSet ks{};
+    const void* tile_fn = nullptr;
+    int tile_threads = 256;
     size_t smem_bytes = 0;
     // fields
     void* E = nullptr;
@@ -400,12 +402,31 @@ template <class T, int G> static pic_status step_t(pic_handle* h) {
         nparticles += d.n;
     }
     P.nsp = nsp;
+    {
+        // FP32 fixed-point current: one int32 unit is worth fx_unit; the range
+        // 2^31 fx_unit is 16x the current of the mean total density moving
+        // coherently at c, and at least 64 q_max.  Integer sums are exact mod
+        // 2^32, so only a tile's final sum per point must stay inside the
+        // range; the flush flags sums above half of it.
+        long long ntot = 0;
+        double qmax = 0.0;
+        for (int s = 0; s < PIC_MAX_SPECIES; ++s)
+            if (h->sp[s].loaded) {
+                ntot += h->sp[s].n;
+                qmax = std::max(qmax, std::fabs(h->sp[s].q));
+            }
+        if (qmax == 0.0) qmax = 1.0;
+        const double rho0 = (double)ntot / ((double)g.nx * g.ny * g.nz);
+        const double range = std::max(64.0, 16.0 * rho0 * cf.c) * qmax;
+        P.fx_scale = (float)(2147483648.0 / range);
+        P.fx_unit = 1.0 / (double)P.fx_scale;
+    }
 
     if (nsp > 0) {
         prof_begin(h);
         T* Jp = (T*)h->J;
         void* args[] = {&h->tmE, &h->tmB, (void*)&g, &h->tl, &P, &SP, &Jp};
-        CK(cudaLaunchKernel(h->ks.tile, dim3(h->tl.ntiles), dim3(TPB), args, h->smem_bytes, h->stream));
+        CK(cudaLaunchKernel(h->tile_fn, dim3(h->tl.ntiles), dim3(h->tile_threads), args, h->smem_bytes, h->stream));
         h->prof.launches++;
         h->prof.particle_launches++;
         h->prof.particle_steps += nparticles;
@@ -648,13 +669,6 @@ template <class T, int G> static pic_status diag_t(pic_handle* h, pic_diag* out)
 
 // ---- configuration ----------------------------------------------------------------------------
 
-static int pick_tile(int n, int pref, bool xaxis, int align) {
-    if (n <= pref) return n;
-    (void)xaxis;
-    (void)align;
-    return pref;
-}
-
 static pic_status validate(const pic_config* c) {
     pic_handle* h = nullptr;
     if (!c) return fail(h, PIC_ERR_ARG, "config is NULL");
@@ -710,6 +724,9 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
     if (st != PIC_OK) return st;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return fail(nullptr, PIC_ERR_CUDA, "no CUDA device available");
+    if (cfg->device < 0 || cfg->device >= ndev)
+        return fail(nullptr, PIC_ERR_ARG, "device %d out of range (%d devices)", cfg->device, ndev);
+    if (cudaSetDevice(cfg->device) != cudaSuccess) return fail(nullptr, PIC_ERR_CUDA, "cudaSetDevice(%d) failed", cfg->device);
     pic_handle* h = new pic_handle();
     h->cfg = *cfg;
     pic_config& c = h->cfg;
@@ -732,35 +749,42 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
     g.pz = AZ ? c.nz + GL + GR : 1;
     g.cstride = (long long)g.px * g.py * g.pz;
     Tiling& tl = h->tl;
-    int defx = h->geom == 0 ? 8 : 16, defy = h->geom == 0 ? 8 : 16;
-    tl.tx = c.tile[0] ? c.tile[0] : pick_tile(c.nx, defx, true, A);
-    tl.ty = AY ? (c.tile[1] ? c.tile[1] : pick_tile(c.ny, h->geom == 0 ? defy : defy, false, 1)) : 1;
-    tl.tz = AZ ? (c.tile[2] ? c.tile[2] : pick_tile(c.nz, h->geom == 0 ? 8 : 16, false, 1)) : 1;
-    tl.tx = std::min(tl.tx, c.nx);
-    tl.ty = std::min(tl.ty, c.ny);
-    tl.tz = std::min(tl.tz, c.nz);
+    // tile shape is fixed per geometry (compile-time strides of the shared boxes)
+    const int dtx = h->geom == 0 ? 8 : 16;
+    const int dty = h->geom == 0 ? 8 : (h->geom == 1 ? 16 : 1);
+    const int dtz = h->geom == 0 ? 8 : (h->geom == 2 ? 16 : 1);
+    if ((c.tile[0] && c.tile[0] != dtx) || (c.tile[1] && AY && c.tile[1] != dty) || (c.tile[2] && AZ && c.tile[2] != dtz)) {
+        delete h;
+        return fail(nullptr, PIC_ERR_ARG, "tile must be 0 (automatic) or %dx%dx%d for this geometry", dtx, dty, dtz);
+    }
+    tl.tx = dtx;
+    tl.ty = dty;
+    tl.tz = dtz;
     tl.ntx = (c.nx + tl.tx - 1) / tl.tx;
     tl.nty = (c.ny + tl.ty - 1) / tl.ty;
     tl.ntz = (c.nz + tl.tz - 1) / tl.tz;
     tl.ntiles = tl.ntx * tl.nty * tl.ntz;
     tl.xalign = A;
-    int bxraw = tl.tx + 4 + ((tl.tx % A) ? A - 1 : 0);
-    tl.bx = (bxraw + A - 1) / A * A;
+    tl.bx = tl.tx + 4;
     tl.by = AY ? tl.ty + 4 : 1;
     tl.bz = AZ ? tl.tz + 4 : 1;
     tl.jx = tl.tx + 5;
     tl.jy = AY ? tl.ty + 5 : 1;
     tl.jz = AZ ? tl.tz + 5 : 1;
-    if (tl.bx > 256 || tl.by > 256 || tl.bz > 256) {
-        delete h;
-        return fail(nullptr, PIC_ERR_ARG, "tile too large for one TMA box");
-    }
-    h->smem_bytes = h->fp64 ? SmemLayout<double>(tl).bytes : SmemLayout<float>(tl).bytes;
+    h->smem_bytes = h->fp64 ? (h->geom == 0   ? SmemLayout<double, 0>::bytes
+                               : h->geom == 1 ? SmemLayout<double, 1>::bytes
+                                              : SmemLayout<double, 2>::bytes)
+                            : (h->geom == 0   ? SmemLayout<float, 0>::bytes
+                               : h->geom == 1 ? SmemLayout<float, 1>::bytes
+                                              : SmemLayout<float, 2>::bytes);
     if (h->smem_bytes > 227 * 1024) {
         delete h;
         return fail(nullptr, PIC_ERR_ARG, "tile needs %zu bytes of shared memory (> 227 KB)", h->smem_bytes);
     }
     h->ks = lookup_kernels(h->fp64, h->geom, c.shape_order, h->push, h->esc);
+    h->tile_threads = 256;
+    if (const char* e = getenv("PIC_TILE_THREADS")) h->tile_threads = atoi(e) == 512 ? 512 : 256;
+    h->tile_fn = h->tile_threads == 512 ? h->ks.tile512 : h->ks.tile;
 
     auto bail = [&](pic_status s) {
         g_init_error = h->last_error;
@@ -772,7 +796,7 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
         return fail(nullptr, PIC_ERR_CUDA, "cudaStreamCreate failed");
     }
     h->own_stream = true;
-    if (cudaFuncSetAttribute(h->ks.tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_bytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(h->tile_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_bytes) != cudaSuccess)
         return bail(fail(h, PIC_ERR_CUDA, "cannot set %zu bytes of dynamic shared memory", h->smem_bytes));
     const size_t fb = (size_t)3 * g.cstride * h->esz;
     void** bufs[] = {&h->E, &h->B, &h->J, &h->Jtmp};
@@ -806,6 +830,7 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
 
 pic_status pic_destroy(pic_handle* h) {
     if (!h) return PIC_OK;
+    cudaSetDevice(h->cfg.device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (auto& d : h->sp) {
         for (int b = 0; b < 2; ++b) {
@@ -830,6 +855,7 @@ pic_status pic_destroy(pic_handle* h) {
 
 pic_status pic_set_stream(pic_handle* h, void* stream) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    cudaSetDevice(h->cfg.device);
     cudaStreamSynchronize(h->stream);
     if (stream) {
         if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -845,12 +871,14 @@ pic_status pic_set_stream(pic_handle* h, void* stream) {
 
 pic_status pic_synchronize(pic_handle* h) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    cudaSetDevice(h->cfg.device);
     CK(cudaStreamSynchronize(h->stream));
     return PIC_OK;
 }
 
 static pic_status check_species(pic_handle* h, int species) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    cudaSetDevice(h->cfg.device);
     if (species < 0 || species >= PIC_MAX_SPECIES) return fail(h, PIC_ERR_ARG, "species index %d out of range", species);
     return PIC_OK;
 }
@@ -898,11 +926,13 @@ pic_status pic_load_maxwellian(pic_handle* h, int species, double q, double m, i
 
 pic_status pic_set_fields(pic_handle* h, const double* E, const double* B) {
     if (!h || !E || !B) return fail(h, PIC_ERR_ARG, "NULL argument");
+    cudaSetDevice(h->cfg.device);
     return DISPATCH(h, set_fields_t, h, E, B);
 }
 
 pic_status pic_set_uniform_fields(pic_handle* h, const double E[3], const double B[3]) {
     if (!h || !E || !B) return fail(h, PIC_ERR_ARG, "NULL argument");
+    cudaSetDevice(h->cfg.device);
     return DISPATCH(h, uniform_fields_t, h, E, B);
 }
 
@@ -913,12 +943,15 @@ static pic_status check_error_word(pic_handle* h) {
     if (e & ERRB_TMA_TIMEOUT) return fail(h, PIC_ERR_TIMEOUT, "a field-staging wait expired (error word %d)", e);
     if (e & ERRB_NONFINITE) return fail(h, PIC_ERR_NUMERIC, "non-finite particle velocity (error word %d)", e);
     if (e & ERRB_LOOSE_OVERFLOW) return fail(h, PIC_ERR_STATE, "loose-particle list overflowed (error word %d)", e);
+    if (e & ERRB_J_RANGE)
+        return fail(h, PIC_ERR_NUMERIC, "a tile current reached half the fixed-point range (error word %d)", e);
     if (e) return fail(h, PIC_ERR_STATE, "device error word %d", e);
     return PIC_OK;
 }
 
 pic_status pic_set_step(pic_handle* h, int64_t step) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    cudaSetDevice(h->cfg.device);
     if (step < 0) return fail(h, PIC_ERR_ARG, "step must be >= 0");
     h->step = step;
     return DISPATCH(h, refill_t, h);
@@ -926,6 +959,7 @@ pic_status pic_set_step(pic_handle* h, int64_t step) {
 
 pic_status pic_step(pic_handle* h, int nsteps) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    cudaSetDevice(h->cfg.device);
     if (nsteps < 0) return fail(h, PIC_ERR_ARG, "nsteps must be >= 0");
     for (int k = 0; k < nsteps; ++k) {
         pic_status st = DISPATCH(h, step_t, h);
@@ -936,6 +970,7 @@ pic_status pic_step(pic_handle* h, int nsteps) {
 
 pic_status pic_diagnostics(pic_handle* h, pic_diag* out) {
     if (!h || !out) return fail(h, PIC_ERR_ARG, "NULL argument");
+    cudaSetDevice(h->cfg.device);
     memset(out, 0, sizeof(*out));
     CK(cudaStreamSynchronize(h->stream));
     out->step = h->step;
@@ -998,6 +1033,7 @@ pic_status pic_get_particles(pic_handle* h, int species, double* x, double* u, u
 
 pic_status pic_get_fields(pic_handle* h, double* E, double* B, double* J) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    cudaSetDevice(h->cfg.device);
     return DISPATCH(h, get_fields_t, h, E, B, J);
 }
 

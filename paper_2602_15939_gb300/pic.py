@@ -45,7 +45,7 @@ class pic_config(C.Structure):
         ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
         ("shape_order", C.c_int32), ("precision", C.c_int32), ("fp_iters", C.c_int32),
         ("keb_push", C.c_int32), ("escape_mode", C.c_int32), ("escape_dims", C.c_int32),
-        ("tile", C.c_int32 * 3), ("reserved0", C.c_int32),
+        ("tile", C.c_int32 * 3), ("device", C.c_int32),
         ("seed", C.c_uint32), ("reserved1", C.c_uint32),
         ("c", C.c_double), ("s_shear", C.c_double), ("Omega0", C.c_double),
         ("expand_rate", C.c_double * 3), ("l_esc", C.c_double), ("p_esc", C.c_double),
@@ -253,7 +253,7 @@ def pic_reset_profile(h):
 def make_config(box=PIC_BOX_PERIODIC, nx=8, ny=8, nz=8, ndim=3, plane=PIC_PLANE_XY, c=0.45, order=1,
                 precision=PIC_FP64, fp_iters=4, keb_push=PIC_KEB_CLOSED_FORM, escape_mode=PIC_ESC_NONE,
                 escape_dims=2, tile=(0, 0, 0), seed=0, s=0.0, Omega0=0.0, rate=(0.0, 0.0, 0.0), l_esc=0.0,
-                p_esc=0.0, theta_inj=0.0, capacity_slack=0.0) -> pic_config:
+                p_esc=0.0, theta_inj=0.0, capacity_slack=0.0, device=0) -> pic_config:
     cfg = pic_config()
     cfg.box, cfg.ndim, cfg.plane = box, ndim, plane
     cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
@@ -265,6 +265,7 @@ def make_config(box=PIC_BOX_PERIODIC, nx=8, ny=8, nz=8, ndim=3, plane=PIC_PLANE_
     cfg.seed = seed & 0xFFFFFFFF
     cfg.c, cfg.s_shear, cfg.Omega0 = c, s, Omega0
     cfg.l_esc, cfg.p_esc, cfg.theta_inj, cfg.capacity_slack = l_esc, p_esc, theta_inj, capacity_slack
+    cfg.device = device
     return cfg
 
 
