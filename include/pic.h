@@ -48,6 +48,7 @@ extern "C" {
 
 #define PIC_ABI_VERSION 1
 #define PIC_MAX_SPECIES 4
+#define PIC_NOALLOC_MAX_COMPONENTS 8
 
 typedef enum {
     PIC_OK = 0,
@@ -198,6 +199,35 @@ pic_status pic_get_fields(pic_handle *h, double *E, double *B, double *J);
 pic_status pic_set_profiling(pic_handle *h, int enable);
 pic_status pic_get_profile(pic_handle *h, pic_profile *out);
 pic_status pic_reset_profile(pic_handle *h);
+
+/* Field energy without any device allocation.  The paper has no counterpart:
+ * this is a service entry point of the library.
+ *
+ * Some callers cannot call cudaMalloc: a host application whose device memory
+ * is owned up front by its own pool allocator (a new allocation would fail or
+ * fragment that pool), a latency-critical loop where an allocation call (which
+ * may synchronise the device) is not allowed, or a plug-in running inside a
+ * framework callback that forbids allocation.  For them this call computes
+ * what pic_diagnostics reports as field energy -- out[c] = sum_i F[c][i]^2 /
+ * (8 pi) for c < ncomp -- on a caller-owned device array, using a fixed
+ * scratch array compiled into the library instead of allocated memory.
+ *
+ * d_field: device pointer, ncomp component arrays of n values each, component
+ *          after component (float for PIC_FP32, double for PIC_FP64).
+ * d_out:   device pointer to ncomp doubles, written by the call.
+ * stream:  cudaStream_t the work is ordered on (NULL = the legacy default
+ *          stream of the current device); the call returns without waiting.
+ * Limits:  1 <= ncomp <= PIC_NOALLOC_MAX_COMPONENTS; otherwise PIC_ERR_ARG.
+ * Scratch: every GPU that loads libpic holds a 64 KB static array until the
+ *          process exits.  All calls on a device share it, so calls whose work
+ *          can overlap on the GPU race and return wrong sums: order them (one
+ *          stream, or events).  The first call on a device looks up the
+ *          array's device address (one-time set-up with that device current);
+ *          make that first call before any stream capture.
+ * Errors:  PIC_ERR_ARG / PIC_ERR_CUDA with text in pic_last_error(NULL).
+ * Nothing is allocated: no cudaMalloc, cudaFree or allocating library call. */
+pic_status pic_field_energy_noalloc(const void *d_field, int precision, int64_t n, int ncomp,
+                                    double *d_out, void *stream);
 
 #ifdef __cplusplus
 }

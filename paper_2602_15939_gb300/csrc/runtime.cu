@@ -712,6 +712,9 @@ template <class T, int G> static pic_status refill_t(pic_handle* h) {
 
 extern "C" {
 
+// used by entry points without a handle (noalloc.cu)
+void pic_internal_set_global_error(const char* msg) { g_init_error = msg ? msg : ""; }
+
 const char* pic_version(void) { return "libpic 0.1 (sm_103a)"; }
 int pic_abi_version(void) { return PIC_ABI_VERSION; }
 

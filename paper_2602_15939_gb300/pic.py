@@ -96,6 +96,7 @@ _SIGS = {
     "pic_set_profiling": (C.c_int, [_H, C.c_int]),
     "pic_get_profile": (C.c_int, [_H, C.POINTER(pic_profile)]),
     "pic_reset_profile": (C.c_int, [_H]),
+    "pic_field_energy_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -246,6 +247,13 @@ def pic_get_profile(h) -> pic_profile:
 
 def pic_reset_profile(h):
     _check(h, lib().pic_reset_profile(h))
+
+
+def pic_field_energy_noalloc(d_field: int, precision: int, n: int, ncomp: int, d_out: int, stream: int | None = None):
+    """Allocation-free field energy of a caller-owned device array (raw device
+    pointers as integers); see include/pic.h."""
+    _check(None, lib().pic_field_energy_noalloc(C.c_void_p(d_field), precision, n, ncomp, C.c_void_p(d_out),
+                                                C.c_void_p(stream) if stream else None))
 
 
 # ---- convenience ------------------------------------------------------------------
