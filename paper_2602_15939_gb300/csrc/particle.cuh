@@ -77,6 +77,8 @@ struct StepP {
     double dys_end_f;   // fractional part
     // expanding box
     double Lam[3];      // -(dt/2) L^{-1} dL/dt
+    double keb_im[3];   // 1 / (1 - Lambda_ii)
+    double keb_Lt[3];   // (1 + Lambda_ii) / (1 - Lambda_ii)
     double inv_lh[3];   // 1 / l_i(t^{n+1/2})
     // leaky box
     double l_esc;
@@ -89,7 +91,8 @@ struct StepP {
     // FP32 path: fixed-point current accumulation in shared memory.  A
     // contribution v is added as round(v * fx_scale) to an int32 word; one
     // unit is worth fx_unit = 1 / fx_scale.  The range 2^31 fx_unit is 16x
-    // the current of the mean density moving coherently at c (at least 64 q).
+    // the current of the mean density moving coherently at c, and at least
+    // 512 c q_max, so a single contribution (|v| <= c q) stays below 2^22 units.
     float fx_scale;
     double fx_unit;
 };
@@ -107,13 +110,17 @@ template <class T> struct Shape<T, 1> {
         if (o >= T(0.5)) { off = 0; f = o - T(0.5); } else { off = -1; f = o + T(0.5); }
         w[0] = T(1) - f; w[1] = f;
     }
-    // node shape on a window [wb, wb+3) for a position x relative to the cell origin
+    // node shape of a position x (relative to the cell origin, -1 <= x < 2) on
+    // the 3-node window starting at node wb: weights (1-f, f) at floor(x) and
+    // floor(x)+1, placed at window index k = floor(x) - wb (0 or 1)
     __device__ static void window(T x, int wb, T w[4]) {
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            T d = t_abs<T>(x - T(wb + m));
-            w[m] = d < T(1) ? T(1) - d : T(0);
-        }
+        const T fl = t_floor<T>(x);
+        const T f = x - fl;
+        const bool k = ((int)fl - wb) != 0;
+        w[0] = k ? T(0) : T(1) - f;
+        w[1] = k ? T(1) - f : f;
+        w[2] = k ? f : T(0);
+        w[3] = T(0);
     }
 };
 
@@ -128,12 +135,18 @@ template <class T> struct Shape<T, 2> {
         q3(d, w);
     }
     __device__ static void stag(T o, int& off, T w[3]) { off = -1; q3(o - T(0.5), w); }
+    // node shape of a position x on the 4-node window starting at node wb: the
+    // three weights q3(x - n) around the nearest node n, placed at window
+    // index k = n - 1 - wb (0 or 1)
     __device__ static void window(T x, int wb, T w[4]) {
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            T d = t_abs<T>(x - T(wb + m));
-            w[m] = d <= T(0.5) ? T(0.75) - d * d : (d < T(1.5) ? T(0.5) * (T(1.5) - d) * (T(1.5) - d) : T(0));
-        }
+        const T n = t_floor<T>(x + T(0.5));
+        T q[3];
+        q3(x - n, q);
+        const bool k = ((int)n - 1 - wb) != 0;
+        w[0] = k ? T(0) : q[0];
+        w[1] = k ? q[0] : q[1];
+        w[2] = k ? q[1] : q[2];
+        w[3] = k ? q[2] : T(0);
     }
 };
 
@@ -184,12 +197,15 @@ template <class T> struct GlobalFields {
 // at the flush).  FP64: one double per point.
 template <class T, int G> struct SmemJ;
 
+// The contribution added is a * b.  FP32 converts it to the nearest integer
+// unit with the 1.5 * 2^23 trick (one FMA and one integer subtract, exact
+// round-to-nearest for |a b| < 2^22 units, which the unit choice guarantees).
 template <int G> struct SmemJ<float, G> {
     using D = TileDims<G>;
     static constexpr int SY = D::JX, SZ = D::JX * D::JY, SC = D::JB;
     int* j;
-    __device__ void add(int comp, int idx, float v) const {
-        const int iv = __float2int_rn(v);
+    __device__ void add(int comp, int idx, float a, float b) const {
+        const int iv = __float_as_int(fmaf(a, b, 12582912.0f)) - 0x4B400000;
         if (iv != 0) atomicAdd(j + comp * SC + idx, iv);
     }
 };
@@ -198,7 +214,8 @@ template <int G> struct SmemJ<double, G> {
     using D = TileDims<G>;
     static constexpr int SY = D::JX, SZ = D::JX * D::JY, SC = D::JB;
     double* j;
-    __device__ void add(int comp, int idx, double v) const {
+    __device__ void add(int comp, int idx, double a, double b) const {
+        const double v = a * b;
         if (v != 0.0) atomicAdd(j + comp * SC + idx, v);
     }
 };
@@ -206,7 +223,8 @@ template <int G> struct SmemJ<double, G> {
 template <class T> struct GlobalJ {
     T* J;
     long long SY, SZ, SC;
-    __device__ void add(int comp, long long idx, T v) const {
+    __device__ void add(int comp, long long idx, T a, T b) const {
+        const T v = a * b;
         if (v != T(0)) red_add_global(J + comp * SC + idx, v);
     }
 };
@@ -341,7 +359,8 @@ __device__ inline void push_ksb(T u[3], const T E[3], const T B[3], T qdt2m, T q
 // Expanding-box modified Boris push of Sec. 3.2 (diagonal Lambda), or the
 // direct 3x3 solve of its defining equation when exact != 0.
 template <class T>
-__device__ inline void push_keb(T u[3], const T E[3], const T B[3], T qdt2m, T qdt2mc, T inv_c2, const T Lam[3], bool exact) {
+__device__ inline void push_keb(T u[3], const T E[3], const T B[3], T qdt2m, T qdt2mc, T inv_c2, const T Lam[3],
+                                const T im[3], const T Lt[3], bool exact) {
     T eps[3] = {qdt2m * E[0], qdt2m * E[1], qdt2m * E[2]};
     T um[3] = {u[0] + eps[0], u[1] + eps[1], u[2] + eps[2]};
     T lu[3] = {(T(1) + Lam[0]) * um[0], (T(1) + Lam[1]) * um[1], (T(1) + Lam[2]) * um[2]};
@@ -350,12 +369,10 @@ __device__ inline void push_keb(T u[3], const T E[3], const T B[3], T qdt2m, T q
     T tau[3] = {qdt2mc * B[0] * ig, qdt2mc * B[1] * ig, qdt2mc * B[2] * ig};
     T up[3];
     if (!exact) {
-        T tt[3], Lt[3], a[3], ax[3], bx[3];
+        T tt[3], a[3], ax[3], bx[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            T im = T(1) / (T(1) - Lam[i]);
-            tt[i] = tau[i] * im;
-            Lt[i] = (T(1) + Lam[i]) * im;
+            tt[i] = tau[i] * im[i];
             a[i] = (T(1) + Lt[i]) * um[i];
         }
         T den = T(1) / (T(1) + dot(tt, tt));
@@ -426,32 +443,42 @@ __device__ inline void deposit(const JA& ja, I cidx, const T o[3], const T d[3],
             CS[a][m] = -qs * run;
         }
     }
+    // F_ab[m][n] = S0a[m] S0b[n] + dSa[m] S0b[n]/2 + S0a[m] dSb[n]/2 + dSa[m] dSb[n]/3
+    //            = S0a[m] A_b[n] + dSa[m] Q_b[n],  A = S0 + dS/2,  Q = S0/2 + dS/3
     const T third = T(1) / T(3);
+    T A[3][4], Q[3][4];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            A[a][m] = S0[a][m] + T(0.5) * DS[a][m];
+            Q[a][m] = T(0.5) * S0[a][m] + third * DS[a][m];
+        }
     const I base = cidx + wb[0] + wb[1] * ja.SY + wb[2] * ja.SZ;
     if (GT::AY && GT::AZ) {
 #pragma unroll
         for (int n = 0; n < NW; ++n)
 #pragma unroll
             for (int m = 0; m < NW; ++m) {
-                const T fyz = S0[1][m] * S0[2][n] + T(0.5) * (DS[1][m] * S0[2][n] + S0[1][m] * DS[2][n]) + third * DS[1][m] * DS[2][n];
+                const T fyz = S0[1][m] * A[2][n] + DS[1][m] * Q[2][n];
 #pragma unroll
-                for (int l = 0; l < NW - 1; ++l) ja.add(0, base + l + m * ja.SY + n * ja.SZ, CS[0][l] * fyz);
+                for (int l = 0; l < NW - 1; ++l) ja.add(0, base + l + m * ja.SY + n * ja.SZ, CS[0][l], fyz);
             }
 #pragma unroll
         for (int n = 0; n < NW; ++n)
 #pragma unroll
             for (int l = 0; l < NW; ++l) {
-                const T fxz = S0[0][l] * S0[2][n] + T(0.5) * (DS[0][l] * S0[2][n] + S0[0][l] * DS[2][n]) + third * DS[0][l] * DS[2][n];
+                const T fxz = S0[0][l] * A[2][n] + DS[0][l] * Q[2][n];
 #pragma unroll
-                for (int m = 0; m < NW - 1; ++m) ja.add(1, base + l + m * ja.SY + n * ja.SZ, CS[1][m] * fxz);
+                for (int m = 0; m < NW - 1; ++m) ja.add(1, base + l + m * ja.SY + n * ja.SZ, CS[1][m], fxz);
             }
 #pragma unroll
         for (int m = 0; m < NW; ++m)
 #pragma unroll
             for (int l = 0; l < NW; ++l) {
-                const T fxy = S0[0][l] * S0[1][m] + T(0.5) * (DS[0][l] * S0[1][m] + S0[0][l] * DS[1][m]) + third * DS[0][l] * DS[1][m];
+                const T fxy = S0[0][l] * A[1][m] + DS[0][l] * Q[1][m];
 #pragma unroll
-                for (int n = 0; n < NW - 1; ++n) ja.add(2, base + l + m * ja.SY + n * ja.SZ, CS[2][n] * fxy);
+                for (int n = 0; n < NW - 1; ++n) ja.add(2, base + l + m * ja.SY + n * ja.SZ, CS[2][n], fxy);
             }
     } else {
         constexpr int A2 = GT::AY ? 1 : 2;  // second active axis
@@ -460,25 +487,20 @@ __device__ inline void deposit(const JA& ja, I cidx, const T o[3], const T d[3],
         const auto s2 = A2 == 1 ? ja.SY : ja.SZ;
 #pragma unroll
         for (int m = 0; m < NW; ++m) {
-            const T f2 = S0[A2][m] + T(0.5) * DS[A2][m];
 #pragma unroll
-            for (int l = 0; l < NW - 1; ++l) ja.add(0, base + l + m * s2, CS[0][l] * f2);
+            for (int l = 0; l < NW - 1; ++l) ja.add(0, base + l + m * s2, CS[0][l], A[A2][m]);
         }
 #pragma unroll
         for (int l = 0; l < NW; ++l) {
-            const T f1 = S0[0][l] + T(0.5) * DS[0][l];
 #pragma unroll
-            for (int m = 0; m < NW - 1; ++m) ja.add(C2, base + l + m * s2, CS[A2][m] * f1);
+            for (int m = 0; m < NW - 1; ++m) ja.add(C2, base + l + m * s2, CS[A2][m], A[0][l]);
         }
         // out-of-plane component: q v_ign F(x, a2)
         const T qv = qs * d[IG];
 #pragma unroll
         for (int m = 0; m < NW; ++m)
 #pragma unroll
-            for (int l = 0; l < NW; ++l) {
-                const T f = S0[0][l] * S0[A2][m] + T(0.5) * (DS[0][l] * S0[A2][m] + S0[0][l] * DS[A2][m]) + third * DS[0][l] * DS[A2][m];
-                ja.add(IG, base + l + m * s2, qv * f);
-            }
+            for (int l = 0; l < NW; ++l) ja.add(IG, base + l + m * s2, qv, S0[0][l] * A[A2][m] + DS[0][l] * Q[A2][m]);
     }
 }
 
@@ -541,8 +563,10 @@ __device__ inline void advance_particle(Particle<T>& p, const FA& fa, I fidx, co
         xc0 = T((double)p.ci - P.half_nx) + p.o[0];
         push_ksb<T>(p.u, E, B, S.qdt2m, S.qdt2mc, c, T(P.sO), T(P.Omega0), xc0);
     } else if (PUSH == PUSH_KEB) {
-        T Lam[3] = {T(P.Lam[0]), T(P.Lam[1]), T(P.Lam[2])};
-        push_keb<T>(p.u, E, B, S.qdt2m, S.qdt2mc, inv_c2, Lam, P.keb_exact != 0);
+        const T Lam[3] = {T(P.Lam[0]), T(P.Lam[1]), T(P.Lam[2])};
+        const T im[3] = {T(P.keb_im[0]), T(P.keb_im[1]), T(P.keb_im[2])};
+        const T Lt[3] = {T(P.keb_Lt[0]), T(P.keb_Lt[1]), T(P.keb_Lt[2])};
+        push_keb<T>(p.u, E, B, S.qdt2m, S.qdt2mc, inv_c2, Lam, im, Lt, P.keb_exact != 0);
     } else {
         push_boris<T>(p.u, E, B, S.qdt2m, S.qdt2mc, inv_c2);
     }
@@ -625,9 +649,10 @@ __device__ inline void advance_particle(Particle<T>& p, const FA& fa, I fidx, co
 
 template <int G> __device__ inline int tile_of(const Tiling& tl, int ci, int cj, int ck) {
     using GT = GeomT<G>;
-    int a = ci / tl.tx;
-    int b = GT::AY ? cj / tl.ty : 0;
-    int cc = GT::AZ ? ck / tl.tz : 0;
+    using D = TileDims<G>;
+    const int a = ci / D::TX;  // compile-time powers of two: shifts
+    const int b = GT::AY ? cj / D::TY : 0;
+    const int cc = GT::AZ ? ck / D::TZ : 0;
     return a + tl.ntx * (b + tl.nty * cc);
 }
 

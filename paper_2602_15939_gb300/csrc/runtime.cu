@@ -365,6 +365,8 @@ template <class T, int G> static pic_status step_t(pic_handle* h) {
     lvals(h, t + 0.5, lh);
     for (int a = 0; a < 3; ++a) {
         P.Lam[a] = cf.box == PIC_BOX_EXPAND ? -0.5 * cf.expand_rate[a] : 0.0;
+        P.keb_im[a] = 1.0 / (1.0 - P.Lam[a]);
+        P.keb_Lt[a] = (1.0 + P.Lam[a]) / (1.0 - P.Lam[a]);
         P.inv_lh[a] = 1.0 / lh[a];
     }
     P.l_esc = cf.l_esc;
@@ -405,7 +407,9 @@ template <class T, int G> static pic_status step_t(pic_handle* h) {
     {
         // FP32 fixed-point current: one int32 unit is worth fx_unit; the range
         // 2^31 fx_unit is 16x the current of the mean total density moving
-        // coherently at c, and at least 64 q_max.  Integer sums are exact mod
+        // coherently at c, and at least 512 c q_max.  A single contribution is
+        // at most c q (|running shape sum| <= |displacement| < c, weights <= 1),
+        // so it stays below 2^22 units, as the kernel's conversion requires.  Integer sums are exact mod
         // 2^32, so only a tile's final sum per point must stay inside the
         // range; the flush flags sums above half of it.
         long long ntot = 0;
@@ -417,7 +421,7 @@ template <class T, int G> static pic_status step_t(pic_handle* h) {
             }
         if (qmax == 0.0) qmax = 1.0;
         const double rho0 = (double)ntot / ((double)g.nx * g.ny * g.nz);
-        const double range = std::max(64.0, 16.0 * rho0 * cf.c) * qmax;
+        const double range = std::max(512.0, 16.0 * rho0) * cf.c * qmax;
         P.fx_scale = (float)(2147483648.0 / range);
         P.fx_unit = 1.0 / (double)P.fx_scale;
     }

@@ -89,9 +89,17 @@ def run_gpu(case: Case, nsteps: int, fp64: bool):
     return parts, fields, diag
 
 
-def rel_maxerr(a, b):
-    scale = np.abs(b).max()
+def rel_maxerr(a, b, floor=0.0):
+    """max |a - b| over the largest |b|, or over `floor` when that is larger"""
+    scale = max(float(np.abs(b).max()), floor)
     return float(np.abs(a - b).max() / scale) if scale > 0 else float(np.abs(a - b).max())
+
+
+def current_scale(case):
+    """J_ref = |q| c n0: the current of the total density moving at c, the
+    natural size of J in a cell; 4 pi J_ref is the field change it drives in
+    one step."""
+    return abs(case.q) * case.c * 2 * case.ppc
 
 
 def compare(case: Case, nsteps: int, fp64: bool):
@@ -115,9 +123,10 @@ def compare(case: Case, nsteps: int, fp64: bool):
         out["u"] = max(out["u"], rel_maxerr(ug, uo))
         if dr is not None:
             out["dr"] = max(out["dr"], float(np.abs(dr[og] - d["dr"][oo]).max()))
-    out["E"] = rel_maxerr(E, st.E)
-    out["B"] = rel_maxerr(B, st.B)
-    out["J"] = rel_maxerr(J, st.J)
+    jref = 0.0 if fp64 else current_scale(case)
+    out["E"] = rel_maxerr(E, st.E, 4 * np.pi * jref)
+    out["B"] = rel_maxerr(B, st.B, 4 * np.pi * jref)
+    out["J"] = rel_maxerr(J, st.J, jref)
     out["escaped_gpu"] = int(diag.escaped_total)
     out["escaped_oracle"] = int(info["escaped"])
     out["loose"] = int(diag.loose)

@@ -5,9 +5,12 @@ precision.  Grids span several tiles with a ragged last tile.
 
 Tolerances (max-norm errors relative to the largest reference value):
 FP64 1e-12 for momenta, fields and currents after one step (rounding order
-only); FP32 1e-6 for one step (single precision storage of momenta, in-cell
-offsets and fields), with positions compared in cells.  Escape decisions of
-the probabilistic leaky box are integer comparisons and must agree exactly.
+only).  FP32 1e-6 for one step (single-precision momenta, in-cell offsets and
+fields; fixed-point current units of about 2e-7 of a particle charge), with
+positions compared in cells; for J the reference is at least the physical
+current scale J_ref = |q| c n0 and for E and B at least 4 pi J_ref, the field
+change such a current drives in one step.  Escape decisions of the
+probabilistic leaky box are integer comparisons and must agree exactly.
 """
 import pytest
 
