@@ -51,6 +51,76 @@ struct Grid {
     }
 };
 
+// Coefficients of one Yee curl update: out_c <- a_c out_c + b_c curl(s (.) in)_c + g_c J_c.
+struct Coef3 { double a[3], b[3], g[3], s[3]; };
+
+// Per-step, time-dependent scalars, kept in device memory so that a captured
+// CUDA graph of a step stays valid from one step to the next.  ctx_kernel
+// fills it at the start of every step from the step counter next_step.
+struct StepCtx {
+    long long next_step;  // the step the next ctx_kernel starts (written by the host on pic_set_step)
+    long long step;       // n of the step in progress (fields at t^n = n)
+    int dys_i[3];         // shearing shift Dy_s mod ny at t, t+1/2, t+1: integer part
+    double dys_f[3];      //                                               fractional part
+    double inv_lh[3];     // 1 / l_i(t + 1/2) (expanding box)
+    Coef3 curl[3];        // curl updates of the step: B half, E full, B half
+};
+
+// Constants ctx_kernel needs (fixed for a handle).
+struct CtxConst {
+    int box;        // 1 shearing, 2 expanding, other: static
+    int ny;
+    double sO_Lx;   // s Omega0 nx: Dy_s(t) = sO_Lx t mod ny
+    double rate[3]; // l_i(t) = exp(rate_i t)
+    double c;
+};
+
+__global__ inline void ctx_kernel(StepCtx* ctx, CtxConst k) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const long long n = ctx->next_step;
+    ctx->step = n;
+    ctx->next_step = n + 1;
+    const double t = (double)n;
+    for (int w = 0; w < 3; ++w) {
+        double d = 0.0;
+        if (k.box == 1) {
+            d = fmod(k.sO_Lx * (t + 0.5 * w), (double)k.ny);
+            if (d < 0.0) d += (double)k.ny;
+        }
+        double fl = floor(d);
+        int di = (int)fl;
+        ctx->dys_f[w] = d - fl;
+        ctx->dys_i[w] = k.ny > 0 ? di % k.ny : 0;
+    }
+    double l0[3], lh[3], l1[3];
+    for (int a = 0; a < 3; ++a) {
+        const bool ex = k.box == 2;
+        l0[a] = ex ? exp(k.rate[a] * t) : 1.0;
+        lh[a] = ex ? exp(k.rate[a] * (t + 0.5)) : 1.0;
+        l1[a] = ex ? exp(k.rate[a] * (t + 1.0)) : 1.0;
+        ctx->inv_lh[a] = 1.0 / lh[a];
+    }
+    const double e0 = l0[0] * l0[1] * l0[2], eh = lh[0] * lh[1] * lh[2], e1 = l1[0] * l1[1] * l1[2];
+    const double FOUR_PI = 12.566370614359172;
+    // B^{n+1/2}: B' = ell L^-1 B at t^n, minus (c/2) curl(L E), back with L at n+1/2
+    // E^{n+1}:   E' + c curl(L B^{n+1/2}) - 4 pi (ell J'), back with L at n+1
+    // B^{n+1}:   B'^{n+1/2} - (c/2) curl(L E^{n+1}), back with L at n+1
+    for (int a = 0; a < 3; ++a) {
+        ctx->curl[0].a[a] = (lh[a] / eh) * (e0 / l0[a]);
+        ctx->curl[0].b[a] = -0.5 * k.c * (lh[a] / eh);
+        ctx->curl[0].g[a] = 0.0;
+        ctx->curl[0].s[a] = l0[a];
+        ctx->curl[1].a[a] = (l1[a] / e1) * (e0 / l0[a]);
+        ctx->curl[1].b[a] = k.c * (l1[a] / e1);
+        ctx->curl[1].g[a] = -FOUR_PI * (l1[a] / e1);
+        ctx->curl[1].s[a] = lh[a];
+        ctx->curl[2].a[a] = (l1[a] / e1) * (eh / lh[a]);
+        ctx->curl[2].b[a] = -0.5 * k.c * (l1[a] / e1);
+        ctx->curl[2].g[a] = 0.0;
+        ctx->curl[2].s[a] = l1[a];
+    }
+}
+
 // ---- packed cell index --------------------------------------------------
 // 3D: i in bits 0..10, j in 11..21, k in 22..31 (nx, ny <= 2048, nz <= 1024).
 // 2D: first active axis in bits 0..15, second in 16..31 (<= 65536 cells each).

@@ -15,11 +15,11 @@ namespace pic {
 // B-located field, result at E locations.  The ignorable 2D axis contributes no
 // differences.  Standard Yee: alpha = 1, sigma = 1; expanding box: the
 // transforms X' = ell L^-1 X folded into alpha, beta, gam, sigma (Sec. 3.2).
-struct Coef3 { double a[3], b[3], g[3], s[3]; };
-
 template <class T, int G, bool CURL_E>
-__global__ void curl_update_kernel(Grid g, const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ J, Coef3 cf) {
+__global__ void curl_update_kernel(Grid g, const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ J,
+                                   const StepCtx* __restrict__ ctx, int which) {
     using GT = GeomT<G>;
+    const Coef3 cf = ctx->curl[which];
     long long n = (long long)g.nx * g.ny * g.nz;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         int i = (int)(q % g.nx);
@@ -131,9 +131,14 @@ __global__ void ksb_sweep_kernel(Grid g, const T* __restrict__ En, const T* __re
 // shearing box: the ghost at (i >= nx, j) is the interior value at
 // (i - nx, j + dys), linearly interpolated, and at (i < 0, j) the one at
 // (i + nx, j - dys)), then y over all padded x, then z over all padded x, y.
+// The shift is (dys_i, dys_f), or ctx->dys_*[which] when ctx is given.
 template <class T, int G>
-__global__ void fill_x_kernel(Grid g, T* F, int ncomp, int dys_i, double dys_f) {
+__global__ void fill_x_kernel(Grid g, T* F, int ncomp, int dys_i, double dys_f, const StepCtx* __restrict__ ctx, int which) {
     using GT = GeomT<G>;
+    if (ctx) {
+        dys_i = ctx->dys_i[which];
+        dys_f = ctx->dys_f[which];
+    }
     const int nguard = g.px - g.nx;  // gx low + the rest high
     long long n = (long long)ncomp * nguard * g.ny * g.nz;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
@@ -254,8 +259,10 @@ __global__ void fold_y_kernel(Grid g, T* F) {
 }
 
 template <class T, int G>
-__global__ void fold_x_kernel(Grid g, T* F, int dys_i, double dys_f) {
+__global__ void fold_x_kernel(Grid g, T* F, const StepCtx* __restrict__ ctx, int which) {
     using GT = GeomT<G>;
+    const int dys_i = ctx->dys_i[which];
+    const double dys_f = ctx->dys_f[which];
     const int band = g.px - g.nx;
     const int gxh = g.px - g.gx - g.nx;
     long long n = 3ll * band * g.ny * g.nz;
@@ -311,6 +318,17 @@ __global__ void ksb_advect_kernel(Grid g, const T* __restrict__ Jin, T* __restri
         int j1 = j0 + 1; if (j1 >= g.ny) j1 -= g.ny;
         const T* Jc = Jin + (long long)comp * g.cstride;
         Jout[(long long)comp * g.cstride + g.idx(i, j, k)] = T(1.0 - f) * Jc[g.idx(i, j0, k)] + T(f) * Jc[g.idx(i, j1, k)];
+    }
+}
+
+// FP32 current: fixed-point int32 sums -> float, flagging sums that reached
+// half of the int32 range (the only place a wrap could show).
+__global__ void fixed_to_float_kernel(long long n, const int* __restrict__ src, float* __restrict__ dst, double unit,
+                                      int* err) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int v = src[q];
+        if (v > (1 << 30) || v < -(1 << 30)) atomicOr(err, ERRB_J_RANGE);
+        dst[q] = (float)((double)v * unit);
     }
 }
 

@@ -220,14 +220,31 @@ template <int G> struct SmemJ<double, G> {
     }
 };
 
-template <class T> struct GlobalJ {
-    T* J;
+// Global padded current (loose particles).  FP32: the int32 fixed-point
+// array the tiles flush into (same units and rounding as the shared box);
+// FP64: doubles.
+template <class T> struct GlobalJ;
+
+template <> struct GlobalJ<float> {
+    int* J;
     long long SY, SZ, SC;
-    __device__ void add(int comp, long long idx, T a, T b) const {
-        const T v = a * b;
-        if (v != T(0)) red_add_global(J + comp * SC + idx, v);
+    __device__ void add(int comp, long long idx, float a, float b) const {
+        const int iv = __float_as_int(fmaf(a, b, 12582912.0f)) - 0x4B400000;
+        if (iv != 0) atomicAdd(J + comp * SC + idx, iv);
     }
 };
+
+template <> struct GlobalJ<double> {
+    double* J;
+    long long SY, SZ, SC;
+    __device__ void add(int comp, long long idx, double a, double b) const {
+        const double v = a * b;
+        if (v != 0.0) red_add_global(J + comp * SC + idx, v);
+    }
+};
+
+// word type of the current accumulators: int32 fixed point (FP32), double (FP64)
+template <class T> using JWord = typename std::conditional<sizeof(T) == 4, int, double>::type;
 
 // ---- gather ------------------------------------------------------------------------
 // cidx: linear index of the particle's cell in the accessor's box; o: offsets.
@@ -647,6 +664,18 @@ __device__ inline void advance_particle(Particle<T>& p, const FA& fa, I fidx, co
 }
 
 
+// The per-step scalars of a step come from the device-resident context.
+__device__ inline StepP with_ctx(const StepP& P0, const StepCtx* ctx) {
+    StepP P = P0;
+    P.step = ctx->step;
+    P.dys_end_i = ctx->dys_i[2];
+    P.dys_end_f = ctx->dys_f[2];
+    P.inv_lh[0] = ctx->inv_lh[0];
+    P.inv_lh[1] = ctx->inv_lh[1];
+    P.inv_lh[2] = ctx->inv_lh[2];
+    return P;
+}
+
 template <int G> __device__ inline int tile_of(const Tiling& tl, int ci, int cj, int ck) {
     using GT = GeomT<G>;
     using D = TileDims<G>;
@@ -693,12 +722,14 @@ template <class T, int G> struct SmemLayout {
 template <class T, int G, int ORD, int PUSH, int ESC, int NT>
 __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 3) tile_kernel(const __grid_constant__ CUtensorMap tmE,
                                                    const __grid_constant__ CUtensorMap tmB, Grid g, Tiling tl,
-                                                   StepP P, SpecPack<T> SP, T* __restrict__ J) {
+                                                   StepP P0, SpecPack<T> SP, JWord<T>* __restrict__ J,
+                                                   const StepCtx* __restrict__ ctx) {
     using GT = GeomT<G>;
     constexpr bool LEAKY = (ESC == ESC_DISP);
     using D = TileDims<G>;
     using L = SmemLayout<T, G>;
-    using JW = typename std::conditional<sizeof(T) == 4, int, double>::type;
+    using JW = JWord<T>;
+    const StepP P = with_ctx(P0, ctx);
     extern __shared__ __align__(128) unsigned char smem[];
     T* sE = reinterpret_cast<T*>(smem);
     T* sB = reinterpret_cast<T*>(smem + L::off_B);
@@ -773,18 +804,12 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 3) tile_kernel(const __gri
         }
     }
     __syncthreads();
-    // flush the J tile: padded index of local point (a,b,c) is (t0x + a, t0y + b, t0z + c)
+    // flush the J tile into the global accumulator (integer adds for FP32, so
+    // the result does not depend on the order tiles finish in): padded index
+    // of local point (a,b,c) is (t0x + a, t0y + b, t0z + c)
     for (int idx = tid; idx < 3 * L::JB; idx += NT) {
-        T v;
-        if constexpr (sizeof(T) == 4) {
-            const int iv = sJ[idx];
-            if (iv == 0) continue;
-            if (iv > (1 << 30) || iv < -(1 << 30)) atomicOr(P.err, ERRB_J_RANGE);
-            v = (float)((double)iv * P.fx_unit);
-        } else {
-            v = sJ[idx];
-            if (v == T(0)) continue;
-        }
+        const JW v = sJ[idx];
+        if (v == JW(0)) continue;
         const int comp = idx / L::JB;
         const int r = idx - comp * L::JB;
         const int a = r % D::JX;
@@ -792,7 +817,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 3) tile_kernel(const __gri
         const int c = r / (D::JX * D::JY);
         const int pi = jox + g.gx + a, pj = joy + g.gy + b, pk = joz + g.gz + c;
         if (pi >= g.px || pj >= g.py || pk >= g.pz) continue;  // beyond a ragged last tile: never deposited
-        red_add_global(J + (long long)comp * g.cstride + ((long long)pk * g.py + pj) * g.px + pi, v);
+        atomicAdd(J + (long long)comp * g.cstride + ((long long)pk * g.py + pj) * g.px + pi, v);
     }
     if (tid < P.nsp) SP.s[tid].stay_out[t] = s_cnt[tid];
 }
@@ -801,9 +826,11 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 3) tile_kernel(const __gri
 // memory and the current added with global atomics; afterwards each particle
 // is inserted into its tile like any mover, or stays loose.
 template <class T, int G, int ORD, int PUSH, int ESC>
-__global__ void __launch_bounds__(TPB) loose_kernel(Grid g, Tiling tl, StepP P, SpecPack<T> SP,
-                                                    const T* __restrict__ E, const T* __restrict__ B, T* __restrict__ J) {
+__global__ void __launch_bounds__(TPB) loose_kernel(Grid g, Tiling tl, StepP P0, SpecPack<T> SP,
+                                                    const T* __restrict__ E, const T* __restrict__ B,
+                                                    JWord<T>* __restrict__ J, const StepCtx* __restrict__ ctx) {
     using GT = GeomT<G>;
+    const StepP P = with_ctx(P0, ctx);
     constexpr bool LEAKY = (ESC == ESC_DISP);
     const long long SY = g.px, SZ = (long long)g.px * g.py;
     const GlobalFields<T> fa{E, B, SY, SZ, g.cstride};
@@ -817,7 +844,8 @@ __global__ void __launch_bounds__(TPB) loose_kernel(Grid g, Tiling tl, StepP P, 
             load_particle<T, G>(S.lin, i, LEAKY, p);
             const long long cidx = (long long)(p.ci + g.gx) + (GT::AY ? (long long)(p.cj + g.gy) * SY : 0) +
                                    (GT::AZ ? (long long)(p.ck + g.gz) * SZ : 0);
-            advance_particle<T, G, ORD, PUSH, ESC>(p, fa, cidx, ja, cidx, S.q, S, P, g);
+            const T qs = sizeof(T) == 4 ? T(S.q * P.fx_scale) : S.q;
+            advance_particle<T, G, ORD, PUSH, ESC>(p, fa, cidx, ja, cidx, qs, S, P, g);
             place_mover<T, G>(p, tile_of<G>(tl, p.ci, p.cj, p.ck), S, P, LEAKY);
         }
     }

@@ -77,6 +77,15 @@ struct pic_handle {
     void* B = nullptr;
     void* J = nullptr;
     void* Jtmp = nullptr;
+    int* Jint = nullptr;  // FP32: fixed-point current the particle kernels add into
+    void* Jcur = nullptr; // the current the field update uses (J, or Jtmp after the shearing-box advection)
+    StepCtx* ctx = nullptr;  // device-resident per-step scalars
+    CtxConst cc{};
+    // CUDA graphs of two consecutive steps, one per starting particle buffer
+    bool graphs_on = true;
+    bool graph_ok[2] = {false, false};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    long long graph_kernels = 0;  // kernels in one two-step graph
     void* Es = nullptr;  // shearing box: saved X^n
     void* Bs = nullptr;
     void* Ec = nullptr;  // shearing box: alternate iterate
@@ -192,17 +201,21 @@ static pic_status encode_field_map(pic_handle* h, CUtensorMap* map, void* base) 
 
 // ---- field kernel launchers ----------------------------------------------------------------
 
-template <class T, int G> static void fill_guards_t(pic_handle* h, T* F, double dys) {
+// Guard fill of a 3-component field.  The x-pass takes the shearing shift
+// from the step context (ctx_which = 0, 1, 2 for t, t+1/2, t+1) during a
+// step, or an explicit shift (ctx_which < 0) outside of one.
+template <class T, int G> static void fill_guards_t(pic_handle* h, T* F, int ctx_which, double dys = 0.0) {
     const Grid& g = h->g;
     int di = 0;
     double df = 0.0;
-    if (dys != 0.0) {
+    if (ctx_which < 0 && dys != 0.0) {
         di = (int)std::floor(dys);
         df = dys - di;
         di %= g.ny;
     }
     long long nx_ = 3ll * (g.px - g.nx) * g.ny * g.nz;
-    fill_x_kernel<T, G><<<grid_blocks(nx_), NTHR, 0, h->stream>>>(g, F, 3, di, df);
+    const StepCtx* ctx = (ctx_which >= 0 && h->cfg.box == PIC_BOX_SHEAR) ? h->ctx : nullptr;
+    fill_x_kernel<T, G><<<grid_blocks(nx_), NTHR, 0, h->stream>>>(g, F, 3, di, df, ctx, ctx_which < 0 ? 0 : ctx_which);
     h->prof.launches++;
     if (GeomT<G>::AY) {
         fill_y_kernel<T><<<grid_blocks(3ll * (g.py - g.ny) * g.px * g.nz), NTHR, 0, h->stream>>>(g, F, 3);
@@ -214,7 +227,8 @@ template <class T, int G> static void fill_guards_t(pic_handle* h, T* F, double 
     }
 }
 
-template <class T, int G> static void fold_current_t(pic_handle* h, T* J, double dys) {
+// Current fold with the shift at t^{n+1/2} (step context slot 1).
+template <class T, int G> static void fold_current_t(pic_handle* h, T* J) {
     const Grid& g = h->g;
     if (GeomT<G>::AZ) {
         fold_z_kernel<T><<<grid_blocks(3ll * (g.pz - g.nz) * g.px * g.py), NTHR, 0, h->stream>>>(g, J);
@@ -224,26 +238,23 @@ template <class T, int G> static void fold_current_t(pic_handle* h, T* J, double
         fold_y_kernel<T><<<grid_blocks(3ll * (g.py - g.ny) * g.px * g.nz), NTHR, 0, h->stream>>>(g, J);
         h->prof.launches++;
     }
-    int di = 0;
-    double df = 0.0;
-    if (dys != 0.0) {
-        di = (int)std::floor(dys);
-        df = dys - di;
-        di %= g.ny;
-    }
-    fold_x_kernel<T, G><<<grid_blocks(3ll * (g.px - g.nx) * g.ny * g.nz), NTHR, 0, h->stream>>>(g, J, di, df);
+    fold_x_kernel<T, G><<<grid_blocks(3ll * (g.px - g.nx) * g.ny * g.nz), NTHR, 0, h->stream>>>(g, J, h->ctx, 1);
     h->prof.launches++;
 }
 
-template <class T, int G> static void curl_t(pic_handle* h, bool curlE, const void* in, void* out, const void* J, const Coef3& cf) {
+template <class T, int G> static void curl_t(pic_handle* h, bool curlE, const void* in, void* out, const void* J, int which) {
     long long n = (long long)h->g.nx * h->g.ny * h->g.nz;
     if (curlE)
-        curl_update_kernel<T, G, true><<<grid_blocks(n), NTHR, 0, h->stream>>>(h->g, (const T*)in, (T*)out, (const T*)J, cf);
+        curl_update_kernel<T, G, true><<<grid_blocks(n), NTHR, 0, h->stream>>>(h->g, (const T*)in, (T*)out, (const T*)J,
+                                                                              h->ctx, which);
     else
-        curl_update_kernel<T, G, false><<<grid_blocks(n), NTHR, 0, h->stream>>>(h->g, (const T*)in, (T*)out, (const T*)J, cf);
+        curl_update_kernel<T, G, false><<<grid_blocks(n), NTHR, 0, h->stream>>>(h->g, (const T*)in, (T*)out, (const T*)J,
+                                                                               h->ctx, which);
     h->prof.launches++;
 }
 
+// Host-side shearing shift and expansion factors (diagnostics, set-up fills);
+// the step itself takes them from the device context.
 static double shear_shift(const pic_handle* h, double t) {
     if (h->cfg.box != PIC_BOX_SHEAR) return 0.0;
     double ny = (double)h->cfg.ny;
@@ -258,21 +269,19 @@ static void lvals(const pic_handle* h, double t, double l[3]) {
 
 template <class T, int G> static void fill_all_t(pic_handle* h, double t) {
     double d = shear_shift(h, t);
-    fill_guards_t<T, G>(h, (T*)h->E, d);
-    fill_guards_t<T, G>(h, (T*)h->B, d);
+    fill_guards_t<T, G>(h, (T*)h->E, -1, d);
+    fill_guards_t<T, G>(h, (T*)h->B, -1, d);
 }
 
-// Field update of one step (t = t^n), after J holds the folded current.
-template <class T, int G> static void field_step_t(pic_handle* h, double t) {
+// Field update of one step, after h->Jcur holds the folded current.
+template <class T, int G> static void field_step_t(pic_handle* h) {
     const Grid& g = h->g;
     const double c = h->cfg.c;
-    const double FOUR_PI = 12.566370614359172;
     if (h->cfg.box == PIC_BOX_SHEAR) {
-        const double dh = shear_shift(h, t + 0.5);
         const size_t bytes = (size_t)3 * g.cstride * h->esz;
         // guards of X^n at t^{n+1/2}, then save X^n
-        fill_guards_t<T, G>(h, (T*)h->E, dh);
-        fill_guards_t<T, G>(h, (T*)h->B, dh);
+        fill_guards_t<T, G>(h, (T*)h->E, 1);
+        fill_guards_t<T, G>(h, (T*)h->B, 1);
         cudaMemcpyAsync(h->Es, h->E, bytes, cudaMemcpyDeviceToDevice, h->stream);
         cudaMemcpyAsync(h->Bs, h->B, bytes, cudaMemcpyDeviceToDevice, h->stream);
         const int N = h->cfg.fp_iters;
@@ -284,49 +293,23 @@ template <class T, int G> static void field_step_t(pic_handle* h, double t) {
             T* Eo = (T*)(to_main ? h->E : h->Ec);
             T* Bo = (T*)(to_main ? h->B : h->Bc);
             ksb_sweep_kernel<T, G><<<grid_blocks(n), NTHR, 0, h->stream>>>(g, (const T*)h->Es, (const T*)h->Bs, (const T*)Ek,
-                                                                            (const T*)Bk, (const T*)h->J, Eo, Bo, c,
+                                                                            (const T*)Bk, (const T*)h->Jcur, Eo, Bo, c,
                                                                             h->cfg.s_shear * h->cfg.Omega0, 0.5 * g.nx);
             h->prof.launches++;
-            fill_guards_t<T, G>(h, Eo, k == N ? shear_shift(h, t + 1.0) : dh);
-            fill_guards_t<T, G>(h, Bo, k == N ? shear_shift(h, t + 1.0) : dh);
+            fill_guards_t<T, G>(h, Eo, k == N ? 2 : 1);
+            fill_guards_t<T, G>(h, Bo, k == N ? 2 : 1);
             Ek = Eo;
             Bk = Bo;
         }
         return;
     }
-    double l0[3], lh[3], l1[3];
-    lvals(h, t, l0);
-    lvals(h, t + 0.5, lh);
-    lvals(h, t + 1.0, l1);
-    const double e0 = l0[0] * l0[1] * l0[2], eh = lh[0] * lh[1] * lh[2], e1 = l1[0] * l1[1] * l1[2];
-    Coef3 cf;
-    // B^{n+1/2}: B' = ell L^-1 B at t^n, minus (c/2) curl(L E), back with L at n+1/2
-    for (int a = 0; a < 3; ++a) {
-        cf.a[a] = (lh[a] / eh) * (e0 / l0[a]);
-        cf.b[a] = -0.5 * c * (lh[a] / eh);
-        cf.g[a] = 0.0;
-        cf.s[a] = l0[a];
-    }
-    curl_t<T, G>(h, true, h->E, h->B, nullptr, cf);
-    fill_guards_t<T, G>(h, (T*)h->B, 0.0);
-    // E^{n+1}: E' + c curl(L B^{n+1/2}) - 4 pi (ell J'), back with L at n+1
-    for (int a = 0; a < 3; ++a) {
-        cf.a[a] = (l1[a] / e1) * (e0 / l0[a]);
-        cf.b[a] = c * (l1[a] / e1);
-        cf.g[a] = -FOUR_PI * (l1[a] / e1);
-        cf.s[a] = lh[a];
-    }
-    curl_t<T, G>(h, false, h->B, h->E, h->J, cf);
-    fill_guards_t<T, G>(h, (T*)h->E, 0.0);
-    // B^{n+1}
-    for (int a = 0; a < 3; ++a) {
-        cf.a[a] = (l1[a] / e1) * (eh / lh[a]);
-        cf.b[a] = -0.5 * c * (l1[a] / e1);
-        cf.g[a] = 0.0;
-        cf.s[a] = l1[a];
-    }
-    curl_t<T, G>(h, true, h->E, h->B, nullptr, cf);
-    fill_guards_t<T, G>(h, (T*)h->B, 0.0);
+    // standard / expanding leapfrog: coefficients of the three curl updates in the context
+    curl_t<T, G>(h, true, h->E, h->B, nullptr, 0);
+    fill_guards_t<T, G>(h, (T*)h->B, -1);
+    curl_t<T, G>(h, false, h->B, h->E, h->Jcur, 1);
+    fill_guards_t<T, G>(h, (T*)h->E, -1);
+    curl_t<T, G>(h, true, h->E, h->B, nullptr, 2);
+    fill_guards_t<T, G>(h, (T*)h->B, -1);
 }
 
 template <class T> static PView<T> view_of(void* const a[11]) {
@@ -347,8 +330,12 @@ template <class T, int G> static pic_status step_t(pic_handle* h) {
     const Grid& g = h->g;
     const pic_config& cf = h->cfg;
     const int b = h->buf, o = 1 - b;
-    const double t = (double)h->step;
-    CK(cudaMemsetAsync(h->J, 0, (size_t)3 * g.cstride * h->esz, h->stream));
+    // per-step scalars (step index, shearing shifts, expansion factors, curl
+    // coefficients) are computed on the device from its step counter
+    ctx_kernel<<<1, 1, 0, h->stream>>>(h->ctx, h->cc);
+    h->prof.launches++;
+    if (h->fp64) CK(cudaMemsetAsync(h->J, 0, (size_t)3 * g.cstride * h->esz, h->stream));
+    else CK(cudaMemsetAsync(h->Jint, 0, (size_t)3 * g.cstride * sizeof(int), h->stream));
 
     StepP P;
     memset(&P, 0, sizeof(P));
@@ -358,16 +345,10 @@ template <class T, int G> static pic_status step_t(pic_handle* h) {
     P.sO = cf.s_shear * cf.Omega0;
     P.Omega0 = cf.Omega0;
     P.half_nx = 0.5 * g.nx;
-    double de = shear_shift(h, t + 1.0);
-    P.dys_end_i = (int)std::floor(de);
-    P.dys_end_f = de - P.dys_end_i;
-    double lh[3];
-    lvals(h, t + 0.5, lh);
     for (int a = 0; a < 3; ++a) {
         P.Lam[a] = cf.box == PIC_BOX_EXPAND ? -0.5 * cf.expand_rate[a] : 0.0;
         P.keb_im[a] = 1.0 / (1.0 - P.Lam[a]);
         P.keb_Lt[a] = (1.0 + P.Lam[a]) / (1.0 - P.Lam[a]);
-        P.inv_lh[a] = 1.0 / lh[a];
     }
     P.l_esc = cf.l_esc;
     double pe = cf.p_esc < 0 ? 0 : cf.p_esc;
@@ -428,8 +409,8 @@ template <class T, int G> static pic_status step_t(pic_handle* h) {
 
     if (nsp > 0) {
         prof_begin(h);
-        T* Jp = (T*)h->J;
-        void* args[] = {&h->tmE, &h->tmB, (void*)&g, &h->tl, &P, &SP, &Jp};
+        void* Jp = h->fp64 ? h->J : (void*)h->Jint;
+        void* args[] = {&h->tmE, &h->tmB, (void*)&g, &h->tl, &P, &SP, &Jp, &h->ctx};
         CK(cudaLaunchKernel(h->tile_fn, dim3(h->tl.ntiles), dim3(h->tile_threads), args, h->smem_bytes, h->stream));
         h->prof.launches++;
         h->prof.particle_launches++;
@@ -438,7 +419,7 @@ template <class T, int G> static pic_status step_t(pic_handle* h) {
         prof_begin(h);
         const T* Ep = (const T*)h->E;
         const T* Bp = (const T*)h->B;
-        void* largs[] = {(void*)&g, &h->tl, &P, &SP, &Ep, &Bp, &Jp};
+        void* largs[] = {(void*)&g, &h->tl, &P, &SP, &Ep, &Bp, &Jp, &h->ctx};
         CK(cudaLaunchKernel(h->ks.loose, dim3(152), dim3(TPB), largs, 0, h->stream));
         h->prof.launches++;
         for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
@@ -452,14 +433,19 @@ template <class T, int G> static pic_status step_t(pic_handle* h) {
     }
 
     prof_begin(h);
-    fold_current_t<T, G>(h, (T*)h->J, shear_shift(h, t + 0.5));
+    if (!h->fp64) {
+        fixed_to_float_kernel<<<grid_blocks(3ll * g.cstride), NTHR, 0, h->stream>>>(3ll * g.cstride, h->Jint, (float*)h->J,
+                                                                                    P.fx_unit, h->err);
+        h->prof.launches++;
+    }
+    fold_current_t<T, G>(h, (T*)h->J);
     if (cf.box == PIC_BOX_SHEAR && GeomT<G>::AY) {
+        // J'(x') -> J'(x): advect along y into the second buffer (h->Jcur)
         ksb_advect_kernel<T><<<grid_blocks(3ll * g.nx * g.ny * g.nz), NTHR, 0, h->stream>>>(g, (const T*)h->J, (T*)h->Jtmp,
                                                                                              cf.s_shear * cf.Omega0, 0.5 * g.nx);
         h->prof.launches++;
-        std::swap(h->J, h->Jtmp);
     }
-    field_step_t<T, G>(h, t);
+    field_step_t<T, G>(h);
     prof_end(h, 2);
     CK(cudaGetLastError());
     h->buf = o;
@@ -469,7 +455,16 @@ template <class T, int G> static pic_status step_t(pic_handle* h) {
 
 // ---- loading / read-back ------------------------------------------------------------------
 
+static void drop_graphs(pic_handle* h) {
+    for (int b = 0; b < 2; ++b) {
+        if (h->gexec[b]) cudaGraphExecDestroy(h->gexec[b]);
+        h->gexec[b] = nullptr;
+        h->graph_ok[b] = false;
+    }
+}
+
 static pic_status alloc_species(pic_handle* h, DevSpecies& d, long long tcap) {
+    drop_graphs(h);
     const int nt = h->tl.ntiles;
     const bool leaky = h->esc == ESC_DISP;
     const int nact = h->geom == 0 ? 3 : 2;
@@ -625,7 +620,7 @@ template <class T, int G> static pic_status uniform_fields_t(pic_handle* h, cons
 template <class T, int G> static pic_status get_fields_t(pic_handle* h, double* E, double* B, double* J) {
     const Grid& g = h->g;
     long long n = 3ll * g.nx * g.ny * g.nz;
-    void* src[3] = {h->E, h->B, h->J};
+    void* src[3] = {h->E, h->B, h->Jcur};
     double* dst[3] = {E, B, J};
     for (int f = 0; f < 3; ++f) {
         if (!dst[f]) continue;
@@ -811,6 +806,20 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
         if (cudaMalloc(p, fb) != cudaSuccess) return bail(fail(h, PIC_ERR_OOM, "field allocation failed"));
         cudaMemsetAsync(*p, 0, fb, h->stream);
     }
+    h->Jcur = (c.box == PIC_BOX_SHEAR && AY) ? h->Jtmp : h->J;
+    if (cudaMalloc(&h->ctx, sizeof(StepCtx)) != cudaSuccess) return bail(fail(h, PIC_ERR_OOM, "allocation failed"));
+    cudaMemsetAsync(h->ctx, 0, sizeof(StepCtx), h->stream);
+    h->cc.box = c.box == PIC_BOX_SHEAR ? 1 : (c.box == PIC_BOX_EXPAND ? 2 : 0);
+    h->cc.ny = c.ny;
+    h->cc.sO_Lx = c.s_shear * c.Omega0 * (double)c.nx;
+    for (int a = 0; a < 3; ++a) h->cc.rate[a] = c.expand_rate[a];
+    h->cc.c = c.c;
+    if (const char* e = getenv("PIC_NO_GRAPHS")) h->graphs_on = atoi(e) == 0;
+    if (!h->fp64) {
+        if (cudaMalloc(&h->Jint, (size_t)3 * g.cstride * sizeof(int)) != cudaSuccess)
+            return bail(fail(h, PIC_ERR_OOM, "field allocation failed"));
+        cudaMemsetAsync(h->Jint, 0, (size_t)3 * g.cstride * sizeof(int), h->stream);
+    }
     if (c.box == PIC_BOX_SHEAR) {
         void** kb[] = {&h->Es, &h->Bs, &h->Ec, &h->Bc};
         for (void** p : kb) {
@@ -850,11 +859,14 @@ pic_status pic_destroy(pic_handle* h) {
         }
         if (d.lcount) cudaFree(d.lcount);
     }
-    void* ptrs[] = {h->E, h->B, h->J, h->Jtmp, h->Es, h->Bs, h->Ec, h->Bc, h->stage, h->partial, h->err, h->counters};
+    void* ptrs[] = {h->E,     h->B,     h->J,       h->Jtmp,    h->Es,       h->Bs,       h->Ec,
+                    h->Bc,    h->stage, h->partial, h->err,     h->counters, (void*)h->Jint};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     prof_resolve(h);
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+    drop_graphs(h);
+    if (h->ctx) cudaFree(h->ctx);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return PIC_OK;
@@ -956,11 +968,52 @@ static pic_status check_error_word(pic_handle* h) {
     return PIC_OK;
 }
 
+// Capture two consecutive steps (starting from the current particle buffer)
+// into a CUDA graph; all per-step scalars come from the device context, so
+// the graph is replayed unchanged for every later pair of steps.  On any
+// capture failure graphs are switched off for this handle.
+static pic_status capture_pair(pic_handle* h) {
+    const int b0 = h->buf;
+    const long long s0 = h->step, l0 = h->prof.launches;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        h->graphs_on = false;
+        cudaGetLastError();
+        return PIC_OK;
+    }
+    pic_status st = DISPATCH(h, step_t, h);
+    if (st == PIC_OK) st = DISPATCH(h, step_t, h);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    h->buf = b0;
+    h->step = s0;
+    h->graph_kernels = h->prof.launches - l0;
+    h->prof.launches = l0;
+    if (st != PIC_OK || e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        h->graphs_on = false;
+        return st == PIC_OK ? PIC_OK : st;
+    }
+    e = cudaGraphInstantiate(&h->gexec[b0], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->gexec[b0] = nullptr;
+        h->graphs_on = false;
+        return PIC_OK;
+    }
+    h->graph_ok[b0] = true;
+    return PIC_OK;
+}
+
 pic_status pic_set_step(pic_handle* h, int64_t step) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
     cudaSetDevice(h->cfg.device);
     if (step < 0) return fail(h, PIC_ERR_ARG, "step must be >= 0");
     h->step = step;
+    long long ns = step;
+    CK(cudaMemcpyAsync(&h->ctx->next_step, &ns, sizeof(ns), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     return DISPATCH(h, refill_t, h);
 }
 
@@ -968,9 +1021,24 @@ pic_status pic_step(pic_handle* h, int nsteps) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
     cudaSetDevice(h->cfg.device);
     if (nsteps < 0) return fail(h, PIC_ERR_ARG, "nsteps must be >= 0");
-    for (int k = 0; k < nsteps; ++k) {
+    while (nsteps > 0) {
+        if (h->graphs_on && !h->prof.on && nsteps >= 2) {
+            const int b0 = h->buf;
+            if (!h->graph_ok[b0]) {
+                pic_status st = capture_pair(h);
+                if (st != PIC_OK) return st;
+            }
+            if (h->graph_ok[b0]) {
+                CK(cudaGraphLaunch(h->gexec[b0], h->stream));
+                h->step += 2;
+                h->prof.launches += h->graph_kernels;
+                nsteps -= 2;
+                continue;
+            }
+        }
         pic_status st = DISPATCH(h, step_t, h);
         if (st != PIC_OK) return st;
+        nsteps -= 1;
     }
     return PIC_OK;
 }

@@ -38,6 +38,8 @@ class Case:
     b0: tuple = (0.0, 0.0, 0.2)
     tile: tuple = (0, 0, 0)
     q: float = 0.05
+    drift: tuple = (0.0, 0.0, 0.0)
+    slack: float = 0.0
     extra: dict = field(default_factory=dict)
 
     @property
@@ -58,11 +60,13 @@ class Case:
                              precision=P.PIC_FP64 if fp64 else P.PIC_FP32, fp_iters=self.fp_iters,
                              keb_push=self.keb_exact, escape_mode=self.esc_mode, escape_dims=self.esc_dims,
                              tile=self.tile, seed=self.seed, s=self.s, Omega0=self.Omega0, rate=self.rate,
-                             l_esc=self.l_esc, p_esc=self.p_esc, theta_inj=self.theta_inj)
+                             l_esc=self.l_esc, p_esc=self.p_esc, theta_inj=self.theta_inj,
+                             capacity_slack=self.slack)
 
 
 def inputs(case: Case):
-    sp = W.uniform_plasma(case.n, case.ppc, case.seed, uth=case.uth, q=case.q, ignorable=case.ignorable)
+    sp = W.uniform_plasma(case.n, case.ppc, case.seed, uth=case.uth, q=case.q, ignorable=case.ignorable,
+                          drift=case.drift)
     E, B = W.random_fields(case.n, case.seed + 100, b0=case.b0)
     return sp, E, B
 
