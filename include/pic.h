@@ -200,6 +200,72 @@ pic_status pic_set_profiling(pic_handle *h, int enable);
 pic_status pic_get_profile(pic_handle *h, pic_profile *out);
 pic_status pic_reset_profile(pic_handle *h);
 
+/* ---- serving: continuous batching of independent runs ------------------------
+ * A run is one box advanced for nsteps from a device Maxwellian load and
+ * uniform initial fields.  The server admits queued runs in arrival order as
+ * soon as their estimated device footprint fits the HBM budget and an active
+ * slot is free; every active run has its own stream, so their kernels overlap
+ * on the GPU; finished runs free their memory for the next ones.  Results are
+ * the same alone and in a mix: each run's state is private and the FP32 path
+ * is bitwise reproducible.  (Service layer of the library; the paper has no
+ * counterpart -- its runs are single boxes.) */
+typedef struct pic_run_spec {
+    pic_config cfg;       /* box configuration (cfg.device is overridden by the server's) */
+    int32_t nspecies;     /* species loaded with pic_load_maxwellian, 1..PIC_MAX_SPECIES */
+    int32_t ppc;          /* particles per cell per species */
+    double theta;         /* temperature of the load, k T / m c^2 */
+    double q[PIC_MAX_SPECIES], m[PIC_MAX_SPECIES];
+    double drift[3];
+    double noise_sigma;
+    double E0[3], B0[3];  /* uniform initial fields */
+    uint32_t load_seed;
+    uint32_t reserved;
+    int64_t nsteps;
+} pic_run_spec;
+
+typedef struct pic_server_info {
+    int32_t queued, active;
+    int64_t completed;
+    uint64_t bytes_in_use, peak_bytes;
+    int32_t peak_active;
+    int32_t reserved;
+} pic_server_info;
+
+typedef struct pic_server pic_server;
+
+/* Estimated device bytes a run holds while active (host arithmetic only). */
+pic_status pic_run_footprint(const pic_run_spec *spec, uint64_t *bytes);
+
+/* How many runs at the front of a queue (device footprints queued_bytes[0..n))
+ * to admit now, given the budget, the bytes and slots in use: the longest
+ * prefix that fits (a run is always admitted when nothing else is active).
+ * Host arithmetic only; the server's admission rule. */
+int pic_admission_count(uint64_t budget, uint64_t in_use, int active, int max_active,
+                        const uint64_t *queued_bytes, int nqueued);
+
+/* Start a server on `device` with an HBM budget, at most max_active runs at
+ * once, advancing each active run steps_per_round steps per round. */
+pic_status pic_server_create(int device, uint64_t hbm_budget_bytes, int max_active,
+                             int steps_per_round, pic_server **out);
+
+/* Queue a run (the spec is copied); *ticket identifies it. */
+pic_status pic_submit(pic_server *s, const pic_run_spec *spec, uint64_t *ticket);
+
+/* *done = 1 once the run has finished; then *out holds its final diagnostics
+ * and *latency_s the time from submission to result.  Returns the run's
+ * status once done. */
+pic_status pic_poll(pic_server *s, uint64_t ticket, int *done, pic_diag *out, double *latency_s);
+
+/* Block until run `ticket` (0: every submitted run) has finished, or timeout_s
+ * seconds pass (PIC_ERR_TIMEOUT). */
+pic_status pic_server_wait(pic_server *s, uint64_t ticket, double timeout_s);
+
+pic_status pic_server_stats(pic_server *s, pic_server_info *out);
+
+/* Stop the server: runs not yet admitted are dropped (PIC_ERR_STATE), active
+ * runs are finished first. */
+pic_status pic_server_destroy(pic_server *s);
+
 /* Field energy without any device allocation.  The paper has no counterpart:
  * this is a service entry point of the library.
  *

@@ -1,0 +1,377 @@
+// server.cu -- continuous-batching run server of libpic (host C++).
+//
+// Independent runs (a box configuration, a Maxwellian load, uniform initial
+// fields and a step count) are submitted to a queue.  A worker thread admits
+// queued runs in arrival order whenever their estimated device footprint fits
+// the HBM budget and an active slot is free, gives each admitted run its own
+// handle and stream (so the kernels of all active runs overlap on the GPU),
+// advances every active run by a chunk of steps per round (at most two
+// chunks in flight per run), and retires finished runs: final diagnostics,
+// time from submission to result, handle destroyed, memory returned to the
+// budget -- which lets the next queued runs in while others keep stepping.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/pic.h"
+
+extern "C" void pic_internal_set_global_error(const char* msg);
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Run {
+    uint64_t ticket = 0;
+    pic_run_spec spec{};
+    uint64_t bytes = 0;
+    Clock::time_point t_submit;
+    pic_handle* h = nullptr;
+    cudaStream_t stream = nullptr;
+    int64_t remaining = 0;
+    std::deque<cudaEvent_t> inflight;
+    bool done = false;
+    pic_status status = PIC_OK;
+    std::string error;
+    pic_diag diag{};
+    double latency_s = 0.0;
+};
+
+}  // namespace
+
+struct pic_server {
+    int device = 0;
+    uint64_t budget = 0;
+    int max_active = 0;
+    int steps_per_round = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Run*> queue;
+    std::vector<Run*> active;
+    std::map<uint64_t, Run*> all;
+    uint64_t next_ticket = 1;
+    uint64_t bytes_in_use = 0;
+    uint64_t peak_bytes = 0;
+    int starting = 0;  // admitted runs being set up (neither queued nor active)
+    int64_t completed = 0;
+    int peak_active = 0;
+    bool stop = false;
+    std::thread worker;
+};
+
+// ---- footprint and admission (host arithmetic only) ------------------------------------------
+
+static void tile_shape(const pic_config& c, int& tx, int& ty, int& tz) {
+    const int geom = c.ndim == 3 ? 0 : (c.plane == PIC_PLANE_XY ? 1 : 2);
+    tx = geom == 0 ? 8 : 16;
+    ty = geom == 0 ? 8 : (geom == 1 ? 16 : 1);
+    tz = geom == 0 ? 8 : (geom == 2 ? 16 : 1);
+}
+
+extern "C" pic_status pic_run_footprint(const pic_run_spec* s, uint64_t* bytes) {
+    if (!s || !bytes) {
+        pic_internal_set_global_error("pic_run_footprint: NULL argument");
+        return PIC_ERR_ARG;
+    }
+    const pic_config& c = s->cfg;
+    if (c.nx < 1 || c.ny < 1 || c.nz < 1 || s->nspecies < 1 || s->nspecies > PIC_MAX_SPECIES || s->ppc < 0) {
+        pic_internal_set_global_error("pic_run_footprint: bad grid, species count or ppc");
+        return PIC_ERR_ARG;
+    }
+    const bool fp64 = c.precision == PIC_FP64;
+    const uint64_t es = fp64 ? 8 : 4;
+    const bool ay = !(c.ndim == 2 && c.plane == PIC_PLANE_XZ), az = !(c.ndim == 2 && c.plane == PIC_PLANE_XY);
+    const uint64_t a = 16 / es;
+    const uint64_t px = ((uint64_t)c.nx + 5 + a - 1) / a * a, py = ay ? c.ny + 5 : 1, pz = az ? c.nz + 5 : 1;
+    const uint64_t cells = (uint64_t)c.nx * c.ny * c.nz, padded = px * py * pz;
+    uint64_t fields = 4;  // E, B, J, J scratch
+    if (c.box == PIC_BOX_SHEAR) fields += 4;
+    uint64_t total = fields * 3 * padded * es + (fp64 ? 0 : 3 * padded * 4) + 3 * cells * 8;
+    int tx, ty, tz;
+    tile_shape(c, tx, ty, tz);
+    const uint64_t ntiles = (uint64_t)((c.nx + tx - 1) / tx) * ((c.ny + ty - 1) / ty) * ((c.nz + tz - 1) / tz);
+    const double slack = c.capacity_slack > 0 ? c.capacity_slack : 0.3;
+    uint64_t tcap = (uint64_t)std::ceil((double)s->ppc * tx * ty * tz * (1.0 + slack)) + 32;
+    tcap = (tcap + 3) & ~3ull;
+    const uint64_t nact = c.ndim == 3 ? 3 : 2;
+    const bool leaky_disp = c.box == PIC_BOX_LEAKY && c.escape_mode == PIC_ESC_DISPLACEMENT;
+    const uint64_t bpp = 4 + nact * es + 3 * es + 4 + (leaky_disp ? 3 * es : 0);
+    const uint64_t n = (uint64_t)s->ppc * cells;
+    const uint64_t lcap = std::max<uint64_t>(4096, n / 32);
+    total += (uint64_t)s->nspecies * 2 * (ntiles * tcap + lcap) * bpp + (uint64_t)s->nspecies * 4 * ntiles * 4;
+    *bytes = total + (1u << 20);  // counters, contexts, reduction scratch
+    return PIC_OK;
+}
+
+extern "C" int pic_admission_count(uint64_t budget, uint64_t in_use, int active, int max_active,
+                                   const uint64_t* queued_bytes, int nqueued) {
+    // FIFO: admit the longest prefix of the queue that fits the memory budget
+    // and the free active slots (a run that can never fit is admitted alone).
+    int k = 0;
+    uint64_t used = in_use;
+    while (k < nqueued && active + k < max_active) {
+        const uint64_t b = queued_bytes[k];
+        const bool fits = used + b <= budget;
+        const bool alone = active + k == 0;  // nothing else running: admit even if over budget
+        if (!fits && !alone) break;
+        used += b;
+        ++k;
+    }
+    return k;
+}
+
+// ---- the worker ------------------------------------------------------------------------------
+
+static pic_status start_run(pic_server* S, Run* r) {
+    pic_config cfg = r->spec.cfg;
+    cfg.device = S->device;
+    pic_status st = pic_init(&cfg, &r->h);
+    if (st != PIC_OK) {
+        r->error = pic_last_error(nullptr);
+        return st;
+    }
+    if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        r->error = "cudaStreamCreate failed";
+        return PIC_ERR_CUDA;
+    }
+    st = pic_set_stream(r->h, r->stream);
+    const pic_run_spec& s = r->spec;
+    uint32_t id_base = 0;
+    const uint64_t per_species = (uint64_t)s.ppc * cfg.nx * cfg.ny * cfg.nz;
+    for (int k = 0; st == PIC_OK && k < s.nspecies; ++k) {
+        st = pic_load_maxwellian(r->h, k, s.q[k], s.m[k], s.ppc, s.theta, s.drift, s.noise_sigma, s.load_seed + 7919u * k,
+                                 id_base);
+        id_base += (uint32_t)per_species;
+    }
+    if (st == PIC_OK) st = pic_set_uniform_fields(r->h, s.E0, s.B0);
+    if (st != PIC_OK) r->error = pic_last_error(r->h);
+    r->remaining = s.nsteps;
+    return st;
+}
+
+static void finish_run(pic_server* S, Run* r, pic_status st) {
+    if (st == PIC_OK && r->h) {
+        st = pic_diagnostics(r->h, &r->diag);
+        if (st != PIC_OK) r->error = pic_last_error(r->h);
+    }
+    for (cudaEvent_t e : r->inflight) cudaEventDestroy(e);
+    r->inflight.clear();
+    if (r->h) pic_destroy(r->h);
+    r->h = nullptr;
+    if (r->stream) cudaStreamDestroy(r->stream);
+    r->stream = nullptr;
+    r->latency_s = std::chrono::duration<double>(Clock::now() - r->t_submit).count();
+    std::lock_guard<std::mutex> lock(S->mu);
+    r->status = st;
+    r->done = true;
+    S->bytes_in_use -= r->bytes;
+    S->completed += 1;
+    S->cv.notify_all();
+}
+
+static void worker_main(pic_server* S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        std::vector<Run*> admit;
+        {
+            std::unique_lock<std::mutex> lock(S->mu);
+            S->cv.wait(lock, [&] { return S->stop || !S->queue.empty() || !S->active.empty(); });
+            if (S->stop && S->active.empty()) break;
+            std::vector<uint64_t> qb;
+            for (Run* q : S->queue) qb.push_back(q->bytes);
+            const int k = pic_admission_count(S->budget, S->bytes_in_use, (int)S->active.size(), S->max_active, qb.data(),
+                                              (int)qb.size());
+            for (int i = 0; i < k; ++i) {
+                Run* r = S->queue.front();
+                S->queue.pop_front();
+                S->bytes_in_use += r->bytes;
+                S->starting += 1;
+                admit.push_back(r);
+            }
+            S->peak_bytes = std::max(S->peak_bytes, S->bytes_in_use);
+        }
+        for (Run* r : admit) {
+            pic_status st = start_run(S, r);
+            if (st != PIC_OK) {
+                finish_run(S, r, st);
+                std::lock_guard<std::mutex> lock(S->mu);
+                S->starting -= 1;
+                S->cv.notify_all();
+                continue;
+            }
+            std::lock_guard<std::mutex> lock(S->mu);
+            S->starting -= 1;
+            S->active.push_back(r);
+            S->peak_active = std::max(S->peak_active, (int)S->active.size());
+        }
+        std::vector<Run*> act;
+        {
+            std::lock_guard<std::mutex> lock(S->mu);
+            act = S->active;
+        }
+        // one round: keep up to two chunks of steps queued per active run
+        for (Run* r : act) {
+            while (!r->inflight.empty() && cudaEventQuery(r->inflight.front()) == cudaSuccess) {
+                cudaEventDestroy(r->inflight.front());
+                r->inflight.pop_front();
+            }
+            if (r->remaining > 0 && r->inflight.size() < 2) {
+                const int k = (int)std::min<int64_t>(r->remaining, S->steps_per_round);
+                pic_status st = pic_step(r->h, k);
+                if (st != PIC_OK) {
+                    r->error = pic_last_error(r->h);
+                    r->remaining = -1;
+                    continue;
+                }
+                r->remaining -= k;
+                cudaEvent_t e;
+                cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+                cudaEventRecord(e, r->stream);
+                r->inflight.push_back(e);
+            }
+        }
+        // retire runs whose last chunk has completed
+        std::vector<Run*> finished;
+        for (Run* r : act) {
+            if (r->remaining < 0 || (r->remaining == 0 && (r->inflight.empty() || cudaEventQuery(r->inflight.back()) == cudaSuccess)))
+                finished.push_back(r);
+        }
+        if (!finished.empty()) {
+            {
+                std::lock_guard<std::mutex> lock(S->mu);
+                for (Run* r : finished) S->active.erase(std::find(S->active.begin(), S->active.end(), r));
+            }
+            for (Run* r : finished) finish_run(S, r, r->remaining < 0 ? PIC_ERR_STATE : PIC_OK);
+        } else if (!act.empty()) {
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+    }
+}
+
+// ---- C ABI ---------------------------------------------------------------------------------------
+
+extern "C" pic_status pic_server_create(int device, uint64_t hbm_budget_bytes, int max_active, int steps_per_round,
+                                        pic_server** out) {
+    if (!out || max_active < 1 || steps_per_round < 1 || hbm_budget_bytes == 0) {
+        pic_internal_set_global_error("pic_server_create: bad arguments");
+        return PIC_ERR_ARG;
+    }
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        pic_internal_set_global_error("pic_server_create: no such CUDA device");
+        return PIC_ERR_CUDA;
+    }
+    pic_server* S = new pic_server();
+    S->device = device;
+    S->budget = hbm_budget_bytes;
+    S->max_active = max_active;
+    S->steps_per_round = steps_per_round;
+    S->worker = std::thread(worker_main, S);
+    *out = S;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_submit(pic_server* S, const pic_run_spec* spec, uint64_t* ticket) {
+    if (!S || !spec || !ticket || spec->nsteps < 0) {
+        pic_internal_set_global_error("pic_submit: bad arguments");
+        return PIC_ERR_ARG;
+    }
+    Run* r = new Run();
+    r->spec = *spec;
+    pic_status st = pic_run_footprint(spec, &r->bytes);
+    if (st != PIC_OK) {
+        delete r;
+        return st;
+    }
+    r->t_submit = Clock::now();
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (S->stop) {
+        delete r;
+        pic_internal_set_global_error("pic_submit: server is shutting down");
+        return PIC_ERR_STATE;
+    }
+    r->ticket = S->next_ticket++;
+    *ticket = r->ticket;
+    S->all[r->ticket] = r;
+    S->queue.push_back(r);
+    S->cv.notify_all();
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_poll(pic_server* S, uint64_t ticket, int* done, pic_diag* out, double* latency_s) {
+    if (!S || !done) {
+        pic_internal_set_global_error("pic_poll: bad arguments");
+        return PIC_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) {
+        pic_internal_set_global_error("pic_poll: unknown ticket");
+        return PIC_ERR_ARG;
+    }
+    Run* r = it->second;
+    *done = r->done ? 1 : 0;
+    if (!r->done) return PIC_OK;
+    if (out) *out = r->diag;
+    if (latency_s) *latency_s = r->latency_s;
+    if (r->status != PIC_OK) pic_internal_set_global_error(r->error.c_str());
+    return r->status;
+}
+
+extern "C" pic_status pic_server_wait(pic_server* S, uint64_t ticket, double timeout_s) {
+    if (!S) return PIC_ERR_ARG;
+    std::unique_lock<std::mutex> lock(S->mu);
+    auto pred = [&] {
+        if (ticket == 0) return S->queue.empty() && S->active.empty() && S->starting == 0;
+        auto it = S->all.find(ticket);
+        return it == S->all.end() || it->second->done;
+    };
+    if (!S->cv.wait_for(lock, std::chrono::duration<double>(timeout_s), pred)) {
+        pic_internal_set_global_error("pic_server_wait: timed out");
+        return PIC_ERR_TIMEOUT;
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_server_stats(pic_server* S, pic_server_info* out) {
+    if (!S || !out) return PIC_ERR_ARG;
+    std::lock_guard<std::mutex> lock(S->mu);
+    out->queued = (int32_t)S->queue.size();
+    out->active = (int32_t)S->active.size();
+    out->completed = S->completed;
+    out->bytes_in_use = S->bytes_in_use;
+    out->peak_bytes = S->peak_bytes;
+    out->peak_active = S->peak_active;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_server_destroy(pic_server* S) {
+    if (!S) return PIC_OK;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        S->stop = true;
+        // drop runs never admitted
+        for (Run* r : S->queue) {
+            r->done = true;
+            r->status = PIC_ERR_STATE;
+            r->error = "server destroyed before the run was admitted";
+        }
+        S->queue.clear();
+        S->cv.notify_all();
+    }
+    if (S->worker.joinable()) S->worker.join();
+    for (auto& kv : S->all) delete kv.second;
+    delete S;
+    return PIC_OK;
+}

@@ -68,6 +68,21 @@ class pic_profile(C.Structure):
                 ("launches", C.c_int64), ("particle_launches", C.c_int64), ("particle_steps", C.c_int64)]
 
 
+class pic_run_spec(C.Structure):
+    _fields_ = [
+        ("cfg", pic_config), ("nspecies", C.c_int32), ("ppc", C.c_int32), ("theta", C.c_double),
+        ("q", C.c_double * PIC_MAX_SPECIES), ("m", C.c_double * PIC_MAX_SPECIES), ("drift", C.c_double * 3),
+        ("noise_sigma", C.c_double), ("E0", C.c_double * 3), ("B0", C.c_double * 3),
+        ("load_seed", C.c_uint32), ("reserved", C.c_uint32), ("nsteps", C.c_int64),
+    ]
+
+
+class pic_server_info(C.Structure):
+    _fields_ = [("queued", C.c_int32), ("active", C.c_int32), ("completed", C.c_int64),
+                ("bytes_in_use", C.c_uint64), ("peak_bytes", C.c_uint64), ("peak_active", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 _lib = None
 _lock = threading.Lock()
 _H = C.c_void_p
@@ -97,6 +112,14 @@ _SIGS = {
     "pic_get_profile": (C.c_int, [_H, C.POINTER(pic_profile)]),
     "pic_reset_profile": (C.c_int, [_H]),
     "pic_field_energy_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
+    "pic_run_footprint": (C.c_int, [C.POINTER(pic_run_spec), C.POINTER(C.c_uint64)]),
+    "pic_admission_count": (C.c_int, [C.c_uint64, C.c_uint64, C.c_int, C.c_int, C.POINTER(C.c_uint64), C.c_int]),
+    "pic_server_create": (C.c_int, [C.c_int, C.c_uint64, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "pic_submit": (C.c_int, [C.c_void_p, C.POINTER(pic_run_spec), C.POINTER(C.c_uint64)]),
+    "pic_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_int), C.POINTER(pic_diag), C.POINTER(C.c_double)]),
+    "pic_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_double]),
+    "pic_server_stats": (C.c_int, [C.c_void_p, C.POINTER(pic_server_info)]),
+    "pic_server_destroy": (C.c_int, [C.c_void_p]),
 }
 
 
@@ -334,3 +357,70 @@ class Box:
 
     def count(self, species):
         return pic_get_count(self.h, species)
+
+
+# ---- serving -------------------------------------------------------------------------
+
+def make_run_spec(cfg: pic_config, nsteps, ppc, theta, q=(-1.0, 1.0), m=(1.0, 1.0), drift=(0.0, 0.0, 0.0),
+                  noise_sigma=0.0, E0=(0.0, 0.0, 0.0), B0=(0.0, 0.0, 0.0), load_seed=0) -> pic_run_spec:
+    s = pic_run_spec()
+    s.cfg = cfg
+    s.nspecies = len(q)
+    s.ppc, s.theta = ppc, theta
+    for i, (qq, mm) in enumerate(zip(q, m)):
+        s.q[i], s.m[i] = qq, mm
+    for a in range(3):
+        s.drift[a], s.E0[a], s.B0[a] = drift[a], E0[a], B0[a]
+    s.noise_sigma, s.load_seed, s.nsteps = noise_sigma, load_seed & 0xFFFFFFFF, nsteps
+    return s
+
+
+def pic_run_footprint(spec: pic_run_spec) -> int:
+    b = C.c_uint64()
+    _check(None, lib().pic_run_footprint(C.byref(spec), C.byref(b)))
+    return b.value
+
+
+def pic_admission_count(budget, in_use, active, max_active, queued_bytes) -> int:
+    arr = (C.c_uint64 * max(1, len(queued_bytes)))(*queued_bytes)
+    return lib().pic_admission_count(budget, in_use, active, max_active, arr, len(queued_bytes))
+
+
+class Server:
+    """Continuous-batching run server (libpic's pic_server_*)."""
+
+    def __init__(self, device=0, hbm_budget_bytes=64 << 30, max_active=64, steps_per_round=8):
+        h = C.c_void_p()
+        _check(None, lib().pic_server_create(device, hbm_budget_bytes, max_active, steps_per_round, C.byref(h)))
+        self.h = h
+
+    def submit(self, spec: pic_run_spec) -> int:
+        t = C.c_uint64()
+        _check(None, lib().pic_submit(self.h, C.byref(spec), C.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        done = C.c_int()
+        d = pic_diag()
+        lat = C.c_double()
+        _check(None, lib().pic_poll(self.h, ticket, C.byref(done), C.byref(d), C.byref(lat)))
+        return (d, lat.value) if done.value else None
+
+    def wait(self, ticket=0, timeout_s=600.0):
+        _check(None, lib().pic_server_wait(self.h, ticket, timeout_s))
+
+    def stats(self) -> pic_server_info:
+        s = pic_server_info()
+        _check(None, lib().pic_server_stats(self.h, C.byref(s)))
+        return s
+
+    def close(self):
+        if self.h:
+            lib().pic_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
