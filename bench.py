@@ -205,19 +205,9 @@ def particle_bytes(fp64, ndim, leaky_disp):
 
 
 def setup_box(w, device, stream, fp64=None, seed=0):
-    from paper_2602_15939_gb300 import pic as P
+    from paper_2602_15939_gb300 import workloads as W
 
-    fp64 = w.fp64 if fp64 is None else fp64
-    cfg = P.make_config(precision=P.PIC_FP64 if fp64 else P.PIC_FP32, device=device, seed=seed,
-                        **w.config_kwargs())
-    box = P.Box(cfg)
-    P.pic_set_stream(box.h, stream)
-    u = w.units
-    box.load_maxwellian(0, -u.q, 1.0, w.ppc, w.theta, noise_sigma=w.noise * w.c, seed=seed, id_base=0)
-    box.load_maxwellian(1, u.q, 1.0, w.ppc, w.theta, noise_sigma=w.noise * w.c, seed=seed + 1,
-                        id_base=w.ppc * w.n[0] * w.n[1] * w.n[2])
-    box.set_uniform_fields((0.0, 0.0, 0.0), w.b0())
-    return box
+    return W.setup_box(w, device=device, stream=stream, fp64=fp64, seed=seed)
 
 
 def run_gb300(args):

@@ -190,6 +190,15 @@ pic_status pic_get_count(pic_handle *h, int species, int64_t *n);
 pic_status pic_get_particles(pic_handle *h, int species, double *x, double *u, uint32_t *id,
                              double *dr);
 
+/* Copy the particles of a species whose id is remainder (mod modulus) --
+ * the same subset at every step, for following particles through a large
+ * run -- to host arrays with room for max_out entries (x[max_out][3], u, id,
+ * dr; each may be NULL), in any order.  *n_out is the number in the subset
+ * (entries beyond max_out are not copied). */
+pic_status pic_get_particles_sampled(pic_handle *h, int species, uint32_t modulus, uint32_t remainder,
+                                     int64_t max_out, double *x, double *u, uint32_t *id, double *dr,
+                                     int64_t *n_out);
+
 /* Copy E (E'), B and the current J of the last step (after folding, and for
  * the shearing box after the y advection) to host arrays [3][nz][ny][nx];
  * each pointer may be NULL. */

@@ -101,6 +101,8 @@ def lib():
                 "ora_ksb_rhs": (None, [P, _D, _D, _D, C.c_double, _D, _D]),
                 "ora_step": (None, [P, C.POINTER(Fields), C.c_int, C.POINTER(Species),
                                     C.POINTER(StepInfo)]),
+                "ora_advance_particle": (None, [P, _D, _D, _D, C.c_int64, C.c_double, C.c_double, C.c_uint32,
+                                                _D, _D, _D, C.POINTER(StepInfo)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -227,6 +229,22 @@ def ksb_rhs(p: Params, E, B, J, t):
     FE, FB = np.zeros_like(E), np.zeros_like(B)
     lib().ora_ksb_rhs(C.byref(p), _dp(E), _dp(B), _dp(J), t, _dp(FE), _dp(FB))
     return FE, FB
+
+
+def advance_particles(p: Params, E, B, step, q, m, ids, x, u, dr=None):
+    """Advance a set of particles one step in given fields without depositing
+    (gather, push, move, boundary, escape); returns new x, u, dr and counts."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, 3)).copy()
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1, 3)).copy()
+    dr = np.zeros_like(x) if dr is None else np.ascontiguousarray(np.asarray(dr, dtype=np.float64).reshape(-1, 3)).copy()
+    ids = np.asarray(ids, dtype=np.uint32)
+    info = StepInfo()
+    L = lib()
+    for i in range(len(x)):
+        L.ora_advance_particle(C.byref(p), _dp(E), _dp(B), None, int(step), q, m, int(ids[i]),
+                               x[i].ctypes.data_as(_D), u[i].ctypes.data_as(_D), dr[i].ctypes.data_as(_D),
+                               C.byref(info))
+    return x, u, dr, {"escaped": info.escaped, "superluminal": info.superluminal}
 
 
 # ---- whole steps ----------------------------------------------------------------

@@ -767,6 +767,90 @@ static void wrap_coord(double *x, int64_t n)
  *  expanding box (KEB, the four steps of Sec. 3.2):
  *    gather lab E, B at x'^n; modified Boris; x'^{n+1} = x'^n + L^{-1}u/gamma
  *    with L at t^{n+1/2}; deposit ell J'; transformed leapfrog. */
+/* One particle's part of a step n -> n+1 (see ora_step): gather at x^n,
+ * push, position update with the box's boundary identification, current
+ * deposit into J (skipped when J is NULL), and the leaky box's escape test and
+ * reinjection.  x, u (and dr for the displacement rule) are updated in place;
+ * the escape and superluminal counters of *loc are incremented. */
+void ora_advance_particle(const ora_params *p, const double *E, const double *B, double *J, int64_t n,
+                          double q, double m, uint32_t id, double x[3], double u[3], double dr[3],
+                          ora_stepinfo *loc)
+{
+    double t = (double)n;
+    double half_nx = 0.5 * (double)p->nx;
+    double Ep[3], Bp[3], x1[3];
+    ora_gather(p, E, B, t, x, Ep, Bp);
+
+    if (p->box == ORA_BOX_SHEAR) {
+        double dys_end = ora_shear_shift(p, t + 1.0);
+        double xc = x[0] - half_nx;
+        ora_push_ksb(q, m, p->c, p->s, p->Omega0, xc, Ep, Bp, u, NULL);
+        double gp = sqrt(1.0 + dot3(u, u) / (p->c * p->c));
+        for (int a = 0; a < 3; ++a) x1[a] = x[a] + u[a] / gp; /* x' */
+        {
+            double vy = u[1] / gp - p->s * p->Omega0 * xc;
+            double v2 = (u[0] / gp) * (u[0] / gp) + vy * vy + (u[2] / gp) * (u[2] / gp);
+            if (v2 >= p->c * p->c) loc->superluminal++;
+        }
+        if (J) ora_deposit_current(p, J, t + 0.5, q, x, x1);
+        double xpc = x1[0] - half_nx;
+        x1[1] -= p->s * p->Omega0 * (xpc + xc) / 2.0;
+        /* shearing-periodic crossing of x: y shifts by Dy_s at t^{n+1} */
+        if (x1[0] >= (double)p->nx) {
+            x1[0] -= (double)p->nx;
+            x1[1] += dys_end;
+        } else if (x1[0] < 0.0) {
+            x1[0] += (double)p->nx;
+            x1[1] -= dys_end;
+            if (x1[0] >= (double)p->nx) x1[0] = 0.0;
+        }
+        x1[1] = fmod(x1[1], (double)p->ny);
+        wrap_coord(&x1[1], p->ny);
+        wrap_coord(&x1[2], p->nz);
+    } else if (p->box == ORA_BOX_EXPAND) {
+        double Lambda[3], lh[3];
+        for (int a = 0; a < 3; ++a) {
+            Lambda[a] = -0.5 * p->rate[a]; /* -(dt/2) L^{-1} dL/dt for l = exp(rate t) */
+            lh[a] = exp(p->rate[a] * (t + 0.5));
+        }
+        ora_push_keb(q, m, p->c, Lambda, Ep, Bp, u, p->keb_exact);
+        double g = sqrt(1.0 + dot3(u, u) / (p->c * p->c));
+        for (int a = 0; a < 3; ++a) x1[a] = x[a] + u[a] / (g * lh[a]);
+        if (J) ora_deposit_current(p, J, t + 0.5, q, x, x1);
+        wrap_coord(&x1[0], p->nx);
+        wrap_coord(&x1[1], p->ny);
+        wrap_coord(&x1[2], p->nz);
+    } else {
+        ora_push_boris(q, m, p->c, Ep, Bp, u);
+        double g = sqrt(1.0 + dot3(u, u) / (p->c * p->c));
+        for (int a = 0; a < 3; ++a) x1[a] = x[a] + u[a] / g;
+        if (J) ora_deposit_current(p, J, t + 0.5, q, x, x1);
+        wrap_coord(&x1[0], p->nx);
+        wrap_coord(&x1[1], p->ny);
+        wrap_coord(&x1[2], p->nz);
+        if (p->box == ORA_BOX_LEAKY && p->esc_mode != ORA_ESC_NONE) {
+            /* Sec. 4.1: end-of-step escape test and reinjection */
+            int esc;
+            if (p->esc_mode == ORA_ESC_DISPLACEMENT) {
+                for (int a = 0; a < 3; ++a) dr[a] += u[a] / g;
+                double mx = fabs(dr[0]) > fabs(dr[1]) ? fabs(dr[0]) : fabs(dr[1]);
+                if (p->esc_dims == 3 && fabs(dr[2]) > mx) mx = fabs(dr[2]);
+                esc = mx >= p->l_esc;
+            } else {
+                esc = ora_escape_draw(id, p->seed, n, p->p_esc);
+            }
+            if (esc) {
+                ora_sample_mj(id, p->seed, n, p->theta_inj, p->c, u);
+                if (dr) dr[0] = dr[1] = dr[2] = 0.0;
+                loc->escaped++;
+            }
+        }
+    }
+    x[0] = x1[0];
+    x[1] = x1[1];
+    x[2] = x1[2];
+}
+
 void ora_step(const ora_params *p, ora_fields *f, int nsp, ora_species *sp, ora_stepinfo *info)
 {
     int64_t n = f->step;
@@ -774,88 +858,11 @@ void ora_step(const ora_params *p, ora_fields *f, int nsp, ora_species *sp, ora_
     int64_t N = 3 * ncell(p);
     memset(f->J, 0, sizeof(double) * (size_t)N);
     ora_stepinfo loc = {0, 0};
-    double half_nx = 0.5 * (double)p->nx;
-    double dys_end = ora_shear_shift(p, t + 1.0);
-    double Lambda[3], lh[3];
-    for (int a = 0; a < 3; ++a) {
-        Lambda[a] = -0.5 * p->rate[a]; /* -(dt/2) L^{-1} dL/dt for l = exp(rate t) */
-        lh[a] = exp(p->rate[a] * (t + 0.5));
-    }
-
     for (int s = 0; s < nsp; ++s) {
         ora_species *S = &sp[s];
-        for (int64_t ip = 0; ip < S->n; ++ip) {
-            double *x = &S->x[3 * ip], *u = &S->u[3 * ip];
-            double Ep[3], Bp[3], x1[3];
-            ora_gather(p, f->E, f->B, t, x, Ep, Bp);
-
-            if (p->box == ORA_BOX_SHEAR) {
-                double xc = x[0] - half_nx;
-                ora_push_ksb(S->q, S->m, p->c, p->s, p->Omega0, xc, Ep, Bp, u, NULL);
-                double gp = sqrt(1.0 + dot3(u, u) / (p->c * p->c));
-                for (int a = 0; a < 3; ++a) x1[a] = x[a] + u[a] / gp; /* x' */
-                {
-                    double vy = u[1] / gp - p->s * p->Omega0 * xc;
-                    double v2 = (u[0] / gp) * (u[0] / gp) + vy * vy + (u[2] / gp) * (u[2] / gp);
-                    if (v2 >= p->c * p->c) loc.superluminal++;
-                }
-                ora_deposit_current(p, f->J, t + 0.5, S->q, x, x1);
-                double xpc = x1[0] - half_nx;
-                x1[1] -= p->s * p->Omega0 * (xpc + xc) / 2.0;
-                /* shearing-periodic crossing of x: y shifts by Dy_s at t^{n+1} */
-                if (x1[0] >= (double)p->nx) {
-                    x1[0] -= (double)p->nx;
-                    x1[1] += dys_end;
-                } else if (x1[0] < 0.0) {
-                    x1[0] += (double)p->nx;
-                    x1[1] -= dys_end;
-                    if (x1[0] >= (double)p->nx) x1[0] = 0.0;
-                }
-                x1[1] = fmod(x1[1], (double)p->ny);
-                wrap_coord(&x1[1], p->ny);
-                wrap_coord(&x1[2], p->nz);
-            } else if (p->box == ORA_BOX_EXPAND) {
-                ora_push_keb(S->q, S->m, p->c, Lambda, Ep, Bp, u, p->keb_exact);
-                double g = sqrt(1.0 + dot3(u, u) / (p->c * p->c));
-                for (int a = 0; a < 3; ++a) x1[a] = x[a] + u[a] / (g * lh[a]);
-                ora_deposit_current(p, f->J, t + 0.5, S->q, x, x1);
-                wrap_coord(&x1[0], p->nx);
-                wrap_coord(&x1[1], p->ny);
-                wrap_coord(&x1[2], p->nz);
-            } else {
-                ora_push_boris(S->q, S->m, p->c, Ep, Bp, u);
-                double g = sqrt(1.0 + dot3(u, u) / (p->c * p->c));
-                for (int a = 0; a < 3; ++a) x1[a] = x[a] + u[a] / g;
-                ora_deposit_current(p, f->J, t + 0.5, S->q, x, x1);
-                wrap_coord(&x1[0], p->nx);
-                wrap_coord(&x1[1], p->ny);
-                wrap_coord(&x1[2], p->nz);
-                if (p->box == ORA_BOX_LEAKY && p->esc_mode != ORA_ESC_NONE) {
-                    /* Sec. 4.1: end-of-step escape test and reinjection */
-                    int esc;
-                    if (p->esc_mode == ORA_ESC_DISPLACEMENT) {
-                        double *dr = &S->dr[3 * ip];
-                        for (int a = 0; a < 3; ++a) dr[a] += u[a] / g;
-                        double mx = fabs(dr[0]) > fabs(dr[1]) ? fabs(dr[0]) : fabs(dr[1]);
-                        if (p->esc_dims == 3 && fabs(dr[2]) > mx) mx = fabs(dr[2]);
-                        esc = mx >= p->l_esc;
-                    } else {
-                        esc = ora_escape_draw(S->id[ip], p->seed, n, p->p_esc);
-                    }
-                    if (esc) {
-                        ora_sample_mj(S->id[ip], p->seed, n, p->theta_inj, p->c, u);
-                        if (S->dr) {
-                            double *dr = &S->dr[3 * ip];
-                            dr[0] = dr[1] = dr[2] = 0.0;
-                        }
-                        loc.escaped++;
-                    }
-                }
-            }
-            x[0] = x1[0];
-            x[1] = x1[1];
-            x[2] = x1[2];
-        }
+        for (int64_t ip = 0; ip < S->n; ++ip)
+            ora_advance_particle(p, f->E, f->B, f->J, n, S->q, S->m, S->id[ip], &S->x[3 * ip], &S->u[3 * ip],
+                                 S->dr ? &S->dr[3 * ip] : NULL, &loc);
     }
 
     if (p->box == ORA_BOX_SHEAR) {

@@ -97,7 +97,11 @@ void ora_ksb_field_solve(const ora_params *p, double *E, double *B, const double
 void ora_ksb_rhs(const ora_params *p, const double *E, const double *B, const double *J,
                  double t, double *FE, double *FB);
 
-/* ---- the whole step ----------------------------------------------------- */
+/* ---- one particle's part of a step (gather, push, move, deposit when J is
+ * non-NULL, escape); the whole step ------------------------------------------ */
+void ora_advance_particle(const ora_params *p, const double *E, const double *B, double *J, int64_t n,
+                          double q, double m, uint32_t id, double x[3], double u[3], double dr[3],
+                          ora_stepinfo *loc);
 void ora_step(const ora_params *p, ora_fields *f, int nsp, ora_species *sp, ora_stepinfo *info);
 
 #ifdef __cplusplus

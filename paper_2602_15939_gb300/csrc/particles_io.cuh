@@ -165,6 +165,50 @@ __global__ void compact_loose_kernel(PView<T> v, const int* __restrict__ lcount,
     }
 }
 
+// Particles whose id is remainder mod modulus (a fixed subset that can be
+// followed from step to step), appended in any order up to max_out.
+template <class T, int G>
+__global__ void sample_kernel(Tiling tl, PView<T> v, const int* __restrict__ stay, const int* __restrict__ arr, long long tcap,
+                              PView<T> lv, const int* __restrict__ lcount, long long lcap, uint32_t modulus,
+                              uint32_t remainder, bool has_dr, long long max_out, unsigned long long* __restrict__ count,
+                              double* __restrict__ x, double* __restrict__ u, uint32_t* __restrict__ id,
+                              double* __restrict__ dr) {
+    for (int t = blockIdx.x; t < tl.ntiles + 1; t += gridDim.x) {
+        const bool loose = t == tl.ntiles;
+        long long n;
+        int nst = 0, nar = 0;
+        if (loose) {
+            n = *lcount;
+            if (n > lcap) n = lcap;
+        } else {
+            nst = stay[t];
+            nar = arr[t];
+            n = nst + nar;
+        }
+        const long long base = (long long)t * tcap;
+        for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+            const long long slot = loose ? i : (i < nst ? base + i : base + tcap - nar + (i - nst));
+            const PView<T>& src = loose ? lv : v;
+            const uint32_t pid = src.id[slot];
+            if (pid % modulus != remainder) continue;
+            const unsigned long long o = atomicAdd(count, 1ull);
+            if ((long long)o >= max_out) continue;
+            Particle<T> p;
+            load_particle<T, G>(src, slot, has_dr, p);
+            x[3 * o + 0] = (double)p.ci + (double)p.o[0];
+            x[3 * o + 1] = (double)p.cj + (double)p.o[1];
+            x[3 * o + 2] = (double)p.ck + (double)p.o[2];
+            u[3 * o] = (double)p.u[0];
+            u[3 * o + 1] = (double)p.u[1];
+            u[3 * o + 2] = (double)p.u[2];
+            id[o] = p.id;
+            dr[3 * o] = has_dr ? (double)p.dr[0] : 0.0;
+            dr[3 * o + 1] = has_dr ? (double)p.dr[1] : 0.0;
+            dr[3 * o + 2] = has_dr ? (double)p.dr[2] : 0.0;
+        }
+    }
+}
+
 // After the particle kernels of a step: clamp each tile's arrival count to
 // the claims that got a slot (failed claims over-count), clamp the loose
 // count to the list capacity, and zero the counters of the consumed buffer,

@@ -561,6 +561,48 @@ static pic_status compact_t(pic_handle* h, int species, double* dx, double* du, 
     return PIC_OK;
 }
 
+template <class T, int G>
+static pic_status sample_t(pic_handle* h, int species, uint32_t modulus, uint32_t remainder, long long max_out, double* x,
+                           double* u, uint32_t* id, double* dr, long long* n_out) {
+    DevSpecies& d = h->sp[species];
+    const int b = h->buf;
+    double *dx = nullptr, *du = nullptr, *ddr = nullptr;
+    uint32_t* did = nullptr;
+    unsigned long long* dcount = nullptr;
+    const size_t m = (size_t)std::max(max_out, 1ll);
+    CK(cudaMalloc(&dx, sizeof(double) * 3 * m));
+    CK(cudaMalloc(&du, sizeof(double) * 3 * m));
+    CK(cudaMalloc(&ddr, sizeof(double) * 3 * m));
+    CK(cudaMalloc(&did, sizeof(uint32_t) * m));
+    CK(cudaMalloc(&dcount, sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), h->stream));
+    sample_kernel<T, G><<<std::min(h->tl.ntiles + 1, 152 * 8), NTHR, 0, h->stream>>>(
+        h->tl, view_of<T>(d.arr[b]), d.stay[b], d.arrv[b], d.tcap, view_of<T>(d.larr[b]), d.lcount + b, d.lcap, modulus,
+        remainder, h->esc == ESC_DISP, max_out, dcount, dx, du, did, ddr);
+    unsigned long long cnt = 0;
+    CK(cudaMemcpyAsync(&cnt, dcount, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaGetLastError());
+    const long long k = std::min((long long)cnt, max_out);
+    if (k > 0) {
+        if (x) CK(cudaMemcpy(x, dx, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost));
+        if (u) CK(cudaMemcpy(u, du, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost));
+        if (id) CK(cudaMemcpy(id, did, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost));
+        if (dr) CK(cudaMemcpy(dr, ddr, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost));
+        if (x && h->geom != 0) {
+            const int ig = h->geom == 1 ? 2 : 1;
+            for (long long i = 0; i < k; ++i) x[3 * i + ig] = 0.5;
+        }
+    }
+    *n_out = (long long)cnt;
+    cudaFree(dx);
+    cudaFree(du);
+    cudaFree(ddr);
+    cudaFree(did);
+    cudaFree(dcount);
+    return PIC_OK;
+}
+
 template <class T, int G> static pic_status maxwellian_t(pic_handle* h, int species, int ppc, double theta, const double drift[3],
                                                          double noise, uint32_t seed, uint32_t id_base) {
     DevSpecies& d = h->sp[species];
@@ -1103,6 +1145,20 @@ pic_status pic_get_particles(pic_handle* h, int species, double* x, double* u, u
     if (du) cudaFree(du);
     if (did) cudaFree(did);
     if (ddr) cudaFree(ddr);
+    return st;
+}
+
+pic_status pic_get_particles_sampled(pic_handle* h, int species, uint32_t modulus, uint32_t remainder, int64_t max_out,
+                                     double* x, double* u, uint32_t* id, double* dr, int64_t* n_out) {
+    pic_status st = check_species(h, species);
+    if (st != PIC_OK) return st;
+    if (!h->sp[species].loaded) return fail(h, PIC_ERR_STATE, "species %d is not loaded", species);
+    if (modulus == 0 || remainder >= modulus || max_out < 0 || !n_out)
+        return fail(h, PIC_ERR_ARG, "need modulus > remainder, max_out >= 0 and n_out");
+    CK(cudaStreamSynchronize(h->stream));
+    long long n = 0;
+    st = DISPATCH(h, sample_t, h, species, modulus, remainder, (long long)max_out, x, u, id, dr, &n);
+    *n_out = n;
     return st;
 }
 

@@ -108,6 +108,8 @@ _SIGS = {
     "pic_get_count": (C.c_int, [_H, C.c_int, C.POINTER(C.c_int64)]),
     "pic_get_particles": (C.c_int, [_H, C.c_int, _D, _D, _U32, _D]),
     "pic_get_fields": (C.c_int, [_H, _D, _D, _D]),
+    "pic_get_particles_sampled": (C.c_int, [_H, C.c_int, C.c_uint32, C.c_uint32, C.c_int64, _D, _D, _U32, _D,
+                                            C.POINTER(C.c_int64)]),
     "pic_set_profiling": (C.c_int, [_H, C.c_int]),
     "pic_get_profile": (C.c_int, [_H, C.POINTER(pic_profile)]),
     "pic_reset_profile": (C.c_int, [_H]),
@@ -252,6 +254,19 @@ def pic_get_particles(h, species, want_dr=False):
     return x, u, ids, dr
 
 
+def pic_get_particles_sampled(h, species, modulus, remainder, max_out):
+    """The particles with id % modulus == remainder (any order): x, u, ids, dr."""
+    x = np.zeros((max_out, 3))
+    u = np.zeros((max_out, 3))
+    ids = np.zeros(max_out, dtype=np.uint32)
+    dr = np.zeros((max_out, 3))
+    n = C.c_int64()
+    _check(h, lib().pic_get_particles_sampled(h, species, modulus, remainder, max_out, _dptr(x), _dptr(u),
+                                              ids.ctypes.data_as(_U32), _dptr(dr), C.byref(n)))
+    k = min(n.value, max_out)
+    return x[:k], u[:k], ids[:k], dr[:k]
+
+
 def pic_get_fields(h, shape):
     E, B, J = (np.zeros(shape) for _ in range(3))
     _check(h, lib().pic_get_fields(h, _dptr(E), _dptr(B), _dptr(J)))
@@ -354,6 +369,9 @@ class Box:
 
     def fields(self):
         return pic_get_fields(self.h, self.shape)
+
+    def particles_sampled(self, species, modulus, remainder=0, max_out=1 << 20):
+        return pic_get_particles_sampled(self.h, species, modulus, remainder, max_out)
 
     def count(self, species):
         return pic_get_count(self.h, species)

@@ -196,3 +196,56 @@ def host_maxwellian(w: Workload, seed: int, n=None, ppc=None):
         for d in sp:
             d["u"] += r.normal(0.0, w.noise * w.c, d["u"].shape)
     return sp
+
+
+def random_phase_dB(n, seed, modes=(2, 3, 4), amplitude=1.0):
+    """In-plane magnetic perturbation of a 2D x-y box from a random-phase
+    vector potential A_z(i, j) = sum a cos(k.x + phi) on the nodes, over mode
+    numbers with |n| in `modes`: B_x(i, j+1/2) = A(i, j+1) - A(i, j) and
+    B_y(i+1/2, j) = A(i, j) - A(i+1, j), so the Yee divergence vanishes
+    identically; scaled to the given rms.  Returns the [3][1][ny][nx] array."""
+    nx, ny = n[0], n[1]
+    r = np.random.default_rng(seed)
+    j, i = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    A = np.zeros((ny, nx))
+    for mx in range(-max(modes), max(modes) + 1):
+        for my in range(-max(modes), max(modes) + 1):
+            m2 = mx * mx + my * my
+            if m2 == 0 or int(round(math.sqrt(m2))) not in modes:
+                continue
+            A += r.normal() * np.cos(2 * math.pi * (mx * i / nx + my * j / ny) + r.uniform(0, 2 * math.pi))
+    bx = np.roll(A, -1, axis=0) - A
+    by = A - np.roll(A, -1, axis=1)
+    rms = math.sqrt((bx**2 + by**2).mean())
+    B = np.zeros((3, 1, ny, nx))
+    if rms > 0:
+        B[0, 0] = bx * amplitude / rms
+        B[1, 0] = by * amplitude / rms
+    return B
+
+
+def setup_box(w: Workload, device=0, stream=None, fp64=None, seed=0):
+    """A libpic box for workload w on `device`, loaded as the benchmark
+    does: the device Maxwellian loader for both species, uniform B0 (plus the
+    random-phase dB of a leaky turbulence box), E = 0."""
+    from . import pic as P
+
+    fp64 = w.fp64 if fp64 is None else fp64
+    cfg = P.make_config(precision=P.PIC_FP64 if fp64 else P.PIC_FP32, device=device, seed=seed,
+                        **w.config_kwargs())
+    box = P.Box(cfg)
+    if stream is not None:
+        P.pic_set_stream(box.h, stream)
+    u = w.units
+    box.load_maxwellian(0, -u.q, 1.0, w.ppc, w.theta, noise_sigma=w.noise * w.c, seed=seed, id_base=0)
+    box.load_maxwellian(1, u.q, 1.0, w.ppc, w.theta, noise_sigma=w.noise * w.c, seed=seed + 1,
+                        id_base=w.ppc * w.n[0] * w.n[1] * w.n[2])
+    b0 = w.b0()
+    if w.box == 3 and w.ndim == 2:
+        B = random_phase_dB(w.n, seed + 2, amplitude=float(np.linalg.norm(b0)))
+        for c in range(3):
+            B[c] += b0[c]
+        box.set_fields(np.zeros_like(B), B)
+    else:
+        box.set_uniform_fields((0.0, 0.0, 0.0), b0)
+    return box
