@@ -826,8 +826,8 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
         return fail(nullptr, PIC_ERR_ARG, "tile needs %zu bytes of shared memory (> 227 KB)", h->smem_bytes);
     }
     h->ks = lookup_kernels(h->fp64, h->geom, c.shape_order, h->push, h->esc);
-    h->tile_threads = 256;
-    if (const char* e = getenv("PIC_TILE_THREADS")) h->tile_threads = atoi(e) == 512 ? 512 : 256;
+    h->tile_threads = 512;
+    if (const char* e = getenv("PIC_TILE_THREADS")) h->tile_threads = atoi(e) == 256 ? 256 : 512;
     h->tile_fn = h->tile_threads == 512 ? h->ks.tile512 : h->ks.tile;
 
     auto bail = [&](pic_status s) {

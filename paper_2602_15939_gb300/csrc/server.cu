@@ -247,11 +247,12 @@ static void worker_main(pic_server* S) {
                 finished.push_back(r);
         }
         if (!finished.empty()) {
-            {
-                std::lock_guard<std::mutex> lock(S->mu);
-                for (Run* r : finished) S->active.erase(std::find(S->active.begin(), S->active.end(), r));
-            }
+            // mark done first, then leave the active set, so a waiter never sees
+            // a run that is neither active nor done
             for (Run* r : finished) finish_run(S, r, r->remaining < 0 ? PIC_ERR_STATE : PIC_OK);
+            std::lock_guard<std::mutex> lock(S->mu);
+            for (Run* r : finished) S->active.erase(std::find(S->active.begin(), S->active.end(), r));
+            S->cv.notify_all();
         } else if (!act.empty()) {
             std::this_thread::sleep_for(std::chrono::microseconds(50));
         }

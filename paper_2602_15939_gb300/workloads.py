@@ -249,3 +249,64 @@ def setup_box(w: Workload, device=0, stream=None, fp64=None, seed=0):
     else:
         box.set_uniform_fields((0.0, 0.0, 0.0), b0)
     return box
+
+
+def served_ensemble(M, seed=0, full=False, mean_gap_s=0.002):
+    """Seeded stream of M independent runs shaped like the served-ensemble
+    configuration: shearing, expanding and leaky boxes, 2D and 3D, FP32, with
+    s in [0.5, 1.8], expansion rate in [1e-5, 1e-3] omega_p, t_esc in
+    [0.5, 4] L/c, Poisson arrivals.  full=True draws the configuration's own
+    ranges (2D 32^2..512^2, 3D 32^3..96^3, 8..64 ppc, 200..2000 steps); the
+    default draws a bounded sample (2D 32^2..128^2, 3D 16^3..32^3, 8..32 ppc,
+    20..100 steps) for a benchmark that must finish in seconds.  Returns a
+    list of dicts: arrival time (s) and the run's parameters."""
+    r = np.random.default_rng(seed)
+    n2 = [32, 64, 128, 256, 512] if full else [32, 48, 64, 96, 128]
+    n3 = [32, 48, 64, 96] if full else [16, 24, 32]
+    ppc_lo, ppc_hi = (8, 64) if full else (8, 32)
+    st_lo, st_hi = (200, 2000) if full else (20, 100)
+    t = 0.0
+    out = []
+    for k in range(M):
+        t += r.exponential(mean_gap_s)
+        box = int(r.choice([1, 2, 3]))
+        ndim = int(r.choice([2, 3]))
+        if ndim == 2:
+            m = int(r.choice(n2))
+            plane = 1 if box == 1 else 0
+            n = (m, 1, m) if plane == 1 else (m, m, 1)
+            order = 1
+        else:
+            m = int(r.choice(n3))
+            n, plane, order = (m, m, m), 0, 2
+        ppc = int(r.integers(ppc_lo, ppc_hi + 1))
+        run = dict(arrival_s=t, box=box, ndim=ndim, plane=plane, n=n, order=order, ppc=ppc,
+                   steps=int(r.integers(st_lo, st_hi + 1)), c=0.45, skin_depth=5.0, sigma=0.5,
+                   s=float(r.uniform(0.5, 1.8)), Omega0_wp=1e-3,
+                   rate_wp=float(10 ** r.uniform(-5, -3)), t_esc_Lc=float(r.uniform(0.5, 4.0)),
+                   theta={1: 0.1, 2: 0.05, 3: 1.0}[box], seed=int(r.integers(0, 2**31)))
+        out.append(run)
+    return out
+
+
+def run_spec_of(run):
+    """libpic run spec (pic_run_spec) for one entry of served_ensemble."""
+    from . import pic as P
+
+    units = PairUnits(run["c"], run["skin_depth"], run["ppc"])
+    wp = units.omega_p
+    kw = dict(box=run["box"], nx=run["n"][0], ny=run["n"][1], nz=run["n"][2], ndim=run["ndim"], plane=run["plane"],
+              c=run["c"], order=run["order"], precision=P.PIC_FP32, seed=run["seed"])
+    b0 = units.b0_from_sigma(run["sigma"])
+    B0 = (0.0, 0.0, b0)
+    if run["box"] == 1:
+        kw.update(s=run["s"], Omega0=run["Omega0_wp"] * wp)
+    elif run["box"] == 2:
+        kw.update(rate=(0.0, run["rate_wp"] * wp, run["rate_wp"] * wp if run["ndim"] == 3 else 0.0))
+        B0 = (b0 / math.sqrt(2.0), b0 / math.sqrt(2.0), 0.0)
+    else:
+        kw.update(escape_mode=P.PIC_ESC_PROBABILISTIC, p_esc=1.0 / (run["t_esc_Lc"] * run["n"][0] / run["c"]),
+                  theta_inj=run["theta"])
+    cfg = P.make_config(**kw)
+    return P.make_run_spec(cfg, run["steps"], run["ppc"], run["theta"], q=(-units.q, units.q), B0=B0,
+                           load_seed=run["seed"])
