@@ -58,6 +58,31 @@ def dist_env():
     return rank, world, local
 
 
+def replica_seed(rank):
+    """Seed of the replica a rank runs: independent boxes, no shared data."""
+    return 1000 * rank
+
+
+def max_over_ranks(x, world, device="cpu"):
+    """Maximum of a per-rank scalar over all ranks: the job's time is that of
+    its slowest replica.  Works on any process-group backend (NCCL on the GPU,
+    gloo in the CPU tests)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, steps, world, ms):
+    """Whole-job throughput: units every rank processed per second of the
+    (max-over-ranks) timed region."""
+    return units_per_rank * steps * world / (ms / 1e3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -230,7 +255,7 @@ def run_gb300(args):
     if args.grid:
         w = W.scaled(w, tuple(int(v) for v in args.grid.split(",")))
     stream = torch.cuda.Stream()
-    box = setup_box(w, local, stream.cuda_stream, seed=1000 * rank)
+    box = setup_box(w, local, stream.cuda_stream, seed=replica_seed(rank))
     npart = w.n_particles
     box.step(args.warmup)
     box.sync()
@@ -265,11 +290,8 @@ def run_gb300(args):
     P.pic_set_profiling(box.h, False)
     diag = box.diagnostics()
     assert diag.error_word == 0, diag.error_word
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = npart * args.steps * world / (ms / 1e3)
+    ms = max_over_ranks(ms, world, device="cuda")
+    value = whole_job_rate(npart, args.steps, world, ms)
     particle_ms = prof.ms_particle / max(1, prof.particle_launches)
 
     peak, peak_kind = measured_peaks()
@@ -300,7 +322,7 @@ def run_gb300(args):
     if not args.no_fp64 and not args.kernel_only:
         box.close()
         torch.cuda.synchronize()
-        b64 = setup_box(w, local, stream.cuda_stream, fp64=True, seed=1000 * rank)
+        b64 = setup_box(w, local, stream.cuda_stream, fp64=True, seed=replica_seed(rank))
         b64.step(2)
         b64.sync()
         k64 = max(2, min(args.steps, 5))
