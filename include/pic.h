@@ -88,7 +88,9 @@ typedef struct pic_config {
     int32_t tile[3];      /* particle tile in cells per axis; 0 = automatic */
     int32_t device;       /* CUDA device ordinal the handle lives on */
     uint32_t seed;        /* key word of the Philox streams (escape, reinjection, loading) */
-    uint32_t reserved1;
+    uint32_t kernel_variant; /* particle-kernel launch shape: 0 = automatic (the tuned choice
+                             for the precision and geometry); k = 1..4 forces variant k (see
+                             pic_kernel_variant_info); a variant that does not fit is PIC_ERR_ARG */
     double c;             /* Courant number; 0 < c, and c * sqrt(ndim) < 1 */
     double s_shear;       /* shearing box: s in v_s = -s Omega0 x e_y (3/2 Keplerian) */
     double Omega0;        /* shearing box: rotation frequency per step */
@@ -208,6 +210,24 @@ pic_status pic_get_fields(pic_handle *h, double *E, double *B, double *J);
 pic_status pic_set_profiling(pic_handle *h, int enable);
 pic_status pic_get_profile(pic_handle *h, pic_profile *out);
 pic_status pic_reset_profile(pic_handle *h);
+
+/* Particle-kernel variants: launch shapes of the fused particle kernel (no
+ * counterpart in the paper, which gives no kernel design), numbered
+ * 1..pic_kernel_variant_count().  Variant k runs *threads_per_cta threads per
+ * CTA, one CTA per tile.  *stable = 1: each tile's stayers are written in
+ * their input order (particles stay grouped by cell, as the device loader
+ * stores them, so the lanes of a warp add their currents conflict-free, and
+ * every contribution is added); 0: warps write in any order and skip zero
+ * contributions.  All variants compute the same result; particle states and
+ * FP32 currents are bit-identical.  Outputs may be NULL; k out of range is
+ * PIC_ERR_ARG. */
+int pic_kernel_variant_count(void);
+pic_status pic_kernel_variant_info(int32_t k, int32_t *threads_per_cta, int32_t *stable);
+/* The variant handle h runs (1-based) / switch it to variant k (takes effect at
+ * the next pic_step; PIC_ERR_ARG if its shared memory does not fit the
+ * configuration).  Switching drops the handle's captured step graphs. */
+pic_status pic_get_kernel_variant(pic_handle *h, int32_t *k);
+pic_status pic_set_kernel_variant(pic_handle *h, int32_t k);
 
 /* ---- serving: continuous batching of independent runs ------------------------
  * A run is one box advanced for nsteps from a device Maxwellian load and

@@ -63,6 +63,8 @@ struct StepCtx {
     int dys_i[3];         // shearing shift Dy_s mod ny at t, t+1/2, t+1: integer part
     double dys_f[3];      //                                               fractional part
     double inv_lh[3];     // 1 / l_i(t + 1/2) (expanding box)
+    float f_dys_f[3];     // the same two in FP32, for the FP32 particle path
+    float f_inv_lh[3];
     Coef3 curl[3];        // curl updates of the step: B half, E full, B half
 };
 
@@ -90,6 +92,7 @@ __global__ inline void ctx_kernel(StepCtx* ctx, CtxConst k) {
         double fl = floor(d);
         int di = (int)fl;
         ctx->dys_f[w] = d - fl;
+        ctx->f_dys_f[w] = (float)(d - fl);
         ctx->dys_i[w] = k.ny > 0 ? di % k.ny : 0;
     }
     double l0[3], lh[3], l1[3];
@@ -99,6 +102,7 @@ __global__ inline void ctx_kernel(StepCtx* ctx, CtxConst k) {
         lh[a] = ex ? exp(k.rate[a] * (t + 0.5)) : 1.0;
         l1[a] = ex ? exp(k.rate[a] * (t + 1.0)) : 1.0;
         ctx->inv_lh[a] = 1.0 / lh[a];
+        ctx->f_inv_lh[a] = (float)(1.0 / lh[a]);
     }
     const double e0 = l0[0] * l0[1] * l0[2], eh = lh[0] * lh[1] * lh[2], e1 = l1[0] * l1[1] * l1[2];
     const double FOUR_PI = 12.566370614359172;
@@ -263,6 +267,28 @@ __device__ inline void tma_load_4d(void* dst, const CUtensorMap* map, int x, int
 }
 
 template <class T> __device__ inline void atomic_add_shared(T* p, T v) { atomicAdd(p, v); }
+
+// Add v to the shared int32 word at shared-window address a (no return).
+__device__ inline void red_shared(uint32_t a, int v) {
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+__device__ inline void red_shared(uint32_t a, double v) {
+    asm volatile("red.shared.add.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+
+// Add v to the shared word at shared-window address a unless v is zero, as a
+// predicated reduction: no branch, so a warp whose lanes differ in which
+// contributions vanish still issues a single instruction per word.
+__device__ inline void red_shared_nz(uint32_t a, int v) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.s32 p, %1, 0;\n\t@p red.shared.add.s32 [%0], %1;\n\t}" ::"r"(a), "r"(v)
+                 : "memory");
+}
+__device__ inline void red_shared_nz(uint32_t a, double v) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.neu.f64 p, %1, 0d0000000000000000;\n\t@p red.shared.add.f64 [%0], %1;\n\t}" ::"r"(a),
+                 "d"(v)
+                 : "memory");
+}
 
 template <class T> __device__ inline void red_add_global(T* p, T v) { atomicAdd(p, v); }
 

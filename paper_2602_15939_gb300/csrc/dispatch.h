@@ -7,8 +7,7 @@
 namespace pic {
 
 struct KernelSet {
-    const void* tile;      // 256 threads per CTA
-    const void* tile512;   // 512 threads per CTA
+    const void* tile[4];  // one per TILE_VARIANTS entry (threads per CTA, current copies)
     const void* loose;
 };
 

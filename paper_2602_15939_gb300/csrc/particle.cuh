@@ -64,8 +64,22 @@ struct Tiling {
     int jx, jy, jz;     // shared J box (points)
 };
 
+// FP32 copies of the FP64 step constants below (the time-dependent ones are
+// refreshed by with_ctx from the device context): the FP32 particle path
+// reads them from the parameter bank, with no FP64 conversion per particle.
+struct StepPF {
+    float c, inv_c2, sO, Omega0, half_nx, l_esc, dys_end_f;
+    float Lam[3], im[3], Lt[3], inv_lh[3];
+};
+
+// The step constant of the path's arithmetic type: FP64 or its FP32 copy.
+template <class T> __device__ inline T pk(double d, float f);
+template <> __device__ inline float pk<float>(double, float f) { return f; }
+template <> __device__ inline double pk<double>(double d, float) { return d; }
+
 struct StepP {
     double c;
+    double inv_c2;      // 1 / c^2
     long long step;
     int nsp;
     int keb_exact;
@@ -95,6 +109,7 @@ struct StepP {
     // 512 c q_max, so a single contribution (|v| <= c q) stays below 2^22 units.
     float fx_scale;
     double fx_unit;
+    StepPF f;
 };
 
 // ---- shapes --------------------------------------------------------------------
@@ -195,6 +210,9 @@ template <class T> struct GlobalFields {
 // fixed-point scale and are rounded to the nearest unit.  Integer addition is
 // exact modulo 2^32, so only the tile's final sum per point must fit (checked
 // at the flush).  FP64: one double per point.
+// Every add is made (no branch); trash(base) is the base that exact-zero
+// contributions are sent to (see deposit): word `lane` of the box, so the
+// lanes of a warp hit distinct banks.  All trash addresses lie inside the box.
 template <class T, int G> struct SmemJ;
 
 // The contribution added is a * b.  FP32 converts it to the nearest integer
@@ -203,20 +221,27 @@ template <class T, int G> struct SmemJ;
 template <int G> struct SmemJ<float, G> {
     using D = TileDims<G>;
     static constexpr int SY = D::JX, SZ = D::JX * D::JY, SC = D::JB;
-    int* j;
+    static_assert(31 + 3 * (1 + (GeomT<G>::AY ? SY : 0) + (GeomT<G>::AZ ? SZ : 0)) < SC,
+                  "trash words of the last component stay inside the box");
+    uint32_t j;  // shared-window address of the box
+    __device__ explicit SmemJ(int* p) : j(smem_u32(p)) {}
+    __device__ int trash(int) const { return (int)(threadIdx.x & 31); }
     __device__ void add(int comp, int idx, float a, float b) const {
         const int iv = __float_as_int(fmaf(a, b, 12582912.0f)) - 0x4B400000;
-        if (iv != 0) atomicAdd(j + comp * SC + idx, iv);
+        red_shared(j + 4u * (uint32_t)(comp * SC + idx), iv);
     }
 };
 
 template <int G> struct SmemJ<double, G> {
     using D = TileDims<G>;
     static constexpr int SY = D::JX, SZ = D::JX * D::JY, SC = D::JB;
-    double* j;
+    static_assert(31 + 3 * (1 + (GeomT<G>::AY ? SY : 0) + (GeomT<G>::AZ ? SZ : 0)) < SC,
+                  "trash words of the last component stay inside the box");
+    uint32_t j;
+    __device__ explicit SmemJ(double* p) : j(smem_u32(p)) {}
+    __device__ int trash(int) const { return (int)(threadIdx.x & 31); }
     __device__ void add(int comp, int idx, double a, double b) const {
-        const double v = a * b;
-        if (v != 0.0) atomicAdd(j + comp * SC + idx, v);
+        red_shared(j + 8u * (uint32_t)(comp * SC + idx), a * b);
     }
 };
 
@@ -228,6 +253,7 @@ template <class T> struct GlobalJ;
 template <> struct GlobalJ<float> {
     int* J;
     long long SY, SZ, SC;
+    __device__ long long trash(long long base) const { return base; }  // exact zeros are skipped below
     __device__ void add(int comp, long long idx, float a, float b) const {
         const int iv = __float_as_int(fmaf(a, b, 12582912.0f)) - 0x4B400000;
         if (iv != 0) atomicAdd(J + comp * SC + idx, iv);
@@ -237,6 +263,7 @@ template <> struct GlobalJ<float> {
 template <> struct GlobalJ<double> {
     double* J;
     long long SY, SZ, SC;
+    __device__ long long trash(long long base) const { return base; }
     __device__ void add(int comp, long long idx, double a, double b) const {
         const double v = a * b;
         if (v != 0.0) red_add_global(J + comp * SC + idx, v);
@@ -432,23 +459,49 @@ __device__ inline void push_keb(T u[3], const T E[3], const T B[3], T qdt2m, T q
 // 2D ignorable axis the current is q v F of the two active axes.  qs is the
 // charge times the accumulator's value scale; cidx the start cell's linear
 // index in the accumulator's box.
+// First window node of axis a relative to the start cell: the lowest node
+// either shape touches (order 1: floor of the lower end point; order 2: one
+// below the lower nearest node).
+template <class T, int ORD> __device__ inline int window_base(T o, T x1) {
+    if (ORD == 1) return x1 < T(0) ? -1 : 0;
+    const int n0 = o >= T(0.5) ? 1 : 0;
+    const int n1 = (int)t_floor<T>(x1 + T(0.5));
+    return (n0 < n1 ? n0 : n1) - 1;
+}
+
+// The last window node of an axis (index ORD+1) carries shape weight only when
+// the particle changes its nearest node (order 2) or its cell (order 1) on
+// that axis ("crosses"); otherwise every contribution that involves it is an
+// exact zero: the weights there are exactly 0, and the running sum that
+// reaches it is set to exactly 0 (the shape sums of both end points are 1, so
+// only rounding is dropped).  Such contributions are not added where they
+// belong: they go, unconditionally, to the accumulator's trash base, which
+// for the shared box is a word of the box chosen by lane (distinct banks
+// across a warp; adding an exact zero changes nothing).  So no add is skipped
+// by a branch.  The global accumulator skips zeros itself.
 template <class T, int G, int ORD, class JA, class I>
 __device__ inline void deposit(const JA& ja, I cidx, const T o[3], const T d[3], T qs) {
     using GT = GeomT<G>;
     constexpr int NW = ORD + 2;  // window nodes
     T S0[3][4], DS[3][4], CS[3][4];
     int wb[3] = {0, 0, 0};
+    int crm = 0;  // bit a: the particle crosses on axis a
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if ((a == 1 && !GT::AY) || (a == 2 && !GT::AZ)) continue;
         const T x1 = o[a] + d[a];
+        bool cr;
         if (ORD == 1) {
-            wb[a] = x1 < T(0) ? -1 : 0;
+            const int f1 = (int)t_floor<T>(x1);
+            cr = f1 != 0;
+            wb[a] = f1 < 0 ? -1 : 0;
         } else {
             const int n0 = o[a] >= T(0.5) ? 1 : 0;
             const int n1 = (int)t_floor<T>(x1 + T(0.5));
+            cr = n0 != n1;
             wb[a] = (n0 < n1 ? n0 : n1) - 1;
         }
+        crm |= cr ? (1 << a) : 0;
         T S1[4];
         Shape<T, ORD>::window(o[a], wb[a], S0[a]);
         Shape<T, ORD>::window(x1, wb[a], S1);
@@ -459,6 +512,7 @@ __device__ inline void deposit(const JA& ja, I cidx, const T o[3], const T d[3],
             run += DS[a][m];
             CS[a][m] = -qs * run;
         }
+        if (!cr) CS[a][NW - 2] = T(0);
     }
     // F_ab[m][n] = S0a[m] S0b[n] + dSa[m] S0b[n]/2 + S0a[m] dSb[n]/2 + dSa[m] dSb[n]/3
     //            = S0a[m] A_b[n] + dSa[m] Q_b[n],  A = S0 + dS/2,  Q = S0/2 + dS/3
@@ -472,6 +526,12 @@ __device__ inline void deposit(const JA& ja, I cidx, const T o[3], const T d[3],
             Q[a][m] = T(0.5) * S0[a][m] + third * DS[a][m];
         }
     const I base = cidx + wb[0] + wb[1] * ja.SY + wb[2] * ja.SZ;
+    // bs[k]: base of the adds that touch the last node on the axes of bit set k
+    const I trash = ja.trash(base);
+    I bs[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) bs[k] = (k & ~crm) ? trash : base;
+    constexpr int LX = NW - 2, LN = NW - 1;  // last current index, last node index
     if (GT::AY && GT::AZ) {
 #pragma unroll
         for (int n = 0; n < NW; ++n)
@@ -479,7 +539,10 @@ __device__ inline void deposit(const JA& ja, I cidx, const T o[3], const T d[3],
             for (int m = 0; m < NW; ++m) {
                 const T fyz = S0[1][m] * A[2][n] + DS[1][m] * Q[2][n];
 #pragma unroll
-                for (int l = 0; l < NW - 1; ++l) ja.add(0, base + l + m * ja.SY + n * ja.SZ, CS[0][l], fyz);
+                for (int l = 0; l < NW - 1; ++l) {
+                    const int k = (l == LX ? 1 : 0) | (m == LN ? 2 : 0) | (n == LN ? 4 : 0);
+                    ja.add(0, bs[k] + l + m * ja.SY + n * ja.SZ, CS[0][l], fyz);
+                }
             }
 #pragma unroll
         for (int n = 0; n < NW; ++n)
@@ -487,7 +550,10 @@ __device__ inline void deposit(const JA& ja, I cidx, const T o[3], const T d[3],
             for (int l = 0; l < NW; ++l) {
                 const T fxz = S0[0][l] * A[2][n] + DS[0][l] * Q[2][n];
 #pragma unroll
-                for (int m = 0; m < NW - 1; ++m) ja.add(1, base + l + m * ja.SY + n * ja.SZ, CS[1][m], fxz);
+                for (int m = 0; m < NW - 1; ++m) {
+                    const int k = (l == LN ? 1 : 0) | (m == LX ? 2 : 0) | (n == LN ? 4 : 0);
+                    ja.add(1, bs[k] + l + m * ja.SY + n * ja.SZ, CS[1][m], fxz);
+                }
             }
 #pragma unroll
         for (int m = 0; m < NW; ++m)
@@ -495,30 +561,145 @@ __device__ inline void deposit(const JA& ja, I cidx, const T o[3], const T d[3],
             for (int l = 0; l < NW; ++l) {
                 const T fxy = S0[0][l] * A[1][m] + DS[0][l] * Q[1][m];
 #pragma unroll
-                for (int n = 0; n < NW - 1; ++n) ja.add(2, base + l + m * ja.SY + n * ja.SZ, CS[2][n], fxy);
+                for (int n = 0; n < NW - 1; ++n) {
+                    const int k = (l == LN ? 1 : 0) | (m == LN ? 2 : 0) | (n == LX ? 4 : 0);
+                    ja.add(2, bs[k] + l + m * ja.SY + n * ja.SZ, CS[2][n], fxy);
+                }
             }
     } else {
         constexpr int A2 = GT::AY ? 1 : 2;  // second active axis
         constexpr int IG = GT::AY ? 2 : 1;  // ignorable axis
         constexpr int C2 = GT::AY ? 1 : 2;  // current component along A2
+        constexpr int B2 = 1 << A2;         // crossing bit of A2
         const auto s2 = A2 == 1 ? ja.SY : ja.SZ;
 #pragma unroll
         for (int m = 0; m < NW; ++m) {
 #pragma unroll
-            for (int l = 0; l < NW - 1; ++l) ja.add(0, base + l + m * s2, CS[0][l], A[A2][m]);
+            for (int l = 0; l < NW - 1; ++l) {
+                const int k = (l == LX ? 1 : 0) | (m == LN ? B2 : 0);
+                ja.add(0, bs[k] + l + m * s2, CS[0][l], A[A2][m]);
+            }
         }
 #pragma unroll
         for (int l = 0; l < NW; ++l) {
 #pragma unroll
-            for (int m = 0; m < NW - 1; ++m) ja.add(C2, base + l + m * s2, CS[A2][m], A[0][l]);
+            for (int m = 0; m < NW - 1; ++m) {
+                const int k = (l == LN ? 1 : 0) | (m == LX ? B2 : 0);
+                ja.add(C2, bs[k] + l + m * s2, CS[A2][m], A[0][l]);
+            }
         }
         // out-of-plane component: q v_ign F(x, a2)
         const T qv = qs * d[IG];
 #pragma unroll
         for (int m = 0; m < NW; ++m)
 #pragma unroll
-            for (int l = 0; l < NW; ++l) ja.add(IG, base + l + m * s2, qv, S0[0][l] * A[A2][m] + DS[0][l] * Q[A2][m]);
+            for (int l = 0; l < NW; ++l) {
+                const int k = (l == LN ? 1 : 0) | (m == LN ? B2 : 0);
+                ja.add(IG, bs[k] + l + m * s2, qv, S0[0][l] * A[A2][m] + DS[0][l] * Q[A2][m]);
+            }
     }
+}
+
+// Core deposit: the part of the current of a particle that crosses no
+// boundary (order 2: keeps its nearest node, order 1: keeps its cell, on every
+// axis), on the window of ORD+1 nodes that holds both of its shapes: (ORD)
+// running sums times (ORD+1)^2 weights per component.  It equals deposit() for
+// such a particle (the words deposit() adds beyond this window are exact
+// zeros).  A crossing particle passes cross = true: its contributions are set
+// to exact zeros and sent to the trash base, and deposit() must be called for
+// it separately.
+template <class T, int G, int ORD, class JA, class I>
+__device__ inline void deposit_core(const JA& ja, I cidx, const T o[3], const T d[3], T qs, bool cross) {
+    using GT = GeomT<G>;
+    constexpr int NC = ORD + 1;  // core window nodes
+    const T qz = cross ? T(0) : qs;
+    T S0[3][3], DS[3][3], CS[3][2];
+    int wb[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if ((a == 1 && !GT::AY) || (a == 2 && !GT::AZ)) continue;
+        const T x1 = o[a] + d[a];
+        wb[a] = ORD == 1 ? 0 : (o[a] >= T(0.5) ? 0 : -1);  // start node (non-crossing particle)
+        T w0[4], w1[4];
+        Shape<T, ORD>::window(o[a], wb[a], w0);
+        Shape<T, ORD>::window(x1, wb[a], w1);
+        T run = T(0);
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            S0[a][m] = w0[m];
+            DS[a][m] = w1[m] - w0[m];
+            run += DS[a][m];
+            if (m < NC - 1) CS[a][m] = -qz * run;
+        }
+    }
+    const T third = T(1) / T(3);
+    T A[3][3], Q[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            A[a][m] = S0[a][m] + T(0.5) * DS[a][m];
+            Q[a][m] = T(0.5) * S0[a][m] + third * DS[a][m];
+        }
+    const I b = cross ? ja.trash(cidx) : cidx + wb[0] + wb[1] * ja.SY + wb[2] * ja.SZ;
+    if (GT::AY && GT::AZ) {
+#pragma unroll
+        for (int n = 0; n < NC; ++n)
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                const T fyz = S0[1][m] * A[2][n] + DS[1][m] * Q[2][n];
+#pragma unroll
+                for (int l = 0; l < NC - 1; ++l) ja.add(0, b + l + m * ja.SY + n * ja.SZ, CS[0][l], fyz);
+            }
+#pragma unroll
+        for (int n = 0; n < NC; ++n)
+#pragma unroll
+            for (int l = 0; l < NC; ++l) {
+                const T fxz = S0[0][l] * A[2][n] + DS[0][l] * Q[2][n];
+#pragma unroll
+                for (int m = 0; m < NC - 1; ++m) ja.add(1, b + l + m * ja.SY + n * ja.SZ, CS[1][m], fxz);
+            }
+#pragma unroll
+        for (int m = 0; m < NC; ++m)
+#pragma unroll
+            for (int l = 0; l < NC; ++l) {
+                const T fxy = S0[0][l] * A[1][m] + DS[0][l] * Q[1][m];
+#pragma unroll
+                for (int n = 0; n < NC - 1; ++n) ja.add(2, b + l + m * ja.SY + n * ja.SZ, CS[2][n], fxy);
+            }
+    } else {
+        constexpr int A2 = GT::AY ? 1 : 2;
+        constexpr int IG = GT::AY ? 2 : 1;
+        constexpr int C2 = GT::AY ? 1 : 2;
+        const auto s2 = A2 == 1 ? ja.SY : ja.SZ;
+#pragma unroll
+        for (int m = 0; m < NC; ++m)
+#pragma unroll
+            for (int l = 0; l < NC - 1; ++l) ja.add(0, b + l + m * s2, CS[0][l], A[A2][m]);
+#pragma unroll
+        for (int l = 0; l < NC; ++l)
+#pragma unroll
+            for (int m = 0; m < NC - 1; ++m) ja.add(C2, b + l + m * s2, CS[A2][m], A[0][l]);
+        const T qv = qz * d[IG];
+#pragma unroll
+        for (int m = 0; m < NC; ++m)
+#pragma unroll
+            for (int l = 0; l < NC; ++l) ja.add(IG, b + l + m * s2, qv, S0[0][l] * A[A2][m] + DS[0][l] * Q[A2][m]);
+    }
+}
+
+// Does the move o -> o + d cross a boundary on some active axis (see deposit_core)?
+template <class T, int G, int ORD> __device__ inline bool crosses(const T o[3], const T d[3]) {
+    using GT = GeomT<G>;
+    bool c = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if ((a == 1 && !GT::AY) || (a == 2 && !GT::AZ)) continue;
+        const T x1 = o[a] + d[a];
+        if (ORD == 1) c |= t_floor<T>(x1) != T(0);
+        else c |= t_floor<T>(x1 + T(0.5)) != (o[a] >= T(0.5) ? T(1) : T(0));
+    }
+    return c;
 }
 
 // ---- one particle ---------------------------------------------------------------------
@@ -563,53 +744,63 @@ template <class T> __device__ inline void renorm(T& o, int& c) {
     c += df;
 }
 
-// Push, move and deposit one particle; returns its destination physical cell
-// in p.  FA: field accessor, JA: current accumulator; (fi,fj,fk) and
-// (ji,jj,jk) are the particle's start cell in their index spaces.
-template <class T, int G, int ORD, int PUSH, int ESC, class FA, class JA, class I>
-__device__ inline void advance_particle(Particle<T>& p, const FA& fa, I fidx, const JA& ja, I jidx, T qs,
-                                        const SpecStep<T>& S, const StepP& P, const Grid& g) {
-    using GT = GeomT<G>;
+// Gather and push one particle: p.u becomes u^{n+1/2}; d is the displacement
+// of the position update in cells (comoving for the expanding box; for the
+// shearing box the comoving move x^n -> x' of Sec. 2.2).  FA: field accessor;
+// fidx: the start cell's linear index in the accessor's box.
+template <class T, int G, int ORD, int PUSH, class FA, class I>
+__device__ inline void push_particle(Particle<T>& p, const FA& fa, I fidx, const SpecStep<T>& S, const StepP& P,
+                                     T d[3]) {
     T E[3], B[3];
     gather<T, G, ORD>(fa, fidx, p.o, E, B);
-    const T c = T(P.c);
-    const T inv_c2 = T(1) / (c * c);
-    T d[3];
-    T xc0 = T(0);
+    const T c = pk<T>(P.c, P.f.c);
+    const T inv_c2 = pk<T>(P.inv_c2, P.f.inv_c2);
     if (PUSH == PUSH_KSB) {
-        xc0 = T((double)p.ci - P.half_nx) + p.o[0];
-        push_ksb<T>(p.u, E, B, S.qdt2m, S.qdt2mc, c, T(P.sO), T(P.Omega0), xc0);
+        const T xc0 = (T(p.ci) - pk<T>(P.half_nx, P.f.half_nx)) + p.o[0];  // exact: integer and half-integer
+        push_ksb<T>(p.u, E, B, S.qdt2m, S.qdt2mc, c, pk<T>(P.sO, P.f.sO), pk<T>(P.Omega0, P.f.Omega0), xc0);
     } else if (PUSH == PUSH_KEB) {
-        const T Lam[3] = {T(P.Lam[0]), T(P.Lam[1]), T(P.Lam[2])};
-        const T im[3] = {T(P.keb_im[0]), T(P.keb_im[1]), T(P.keb_im[2])};
-        const T Lt[3] = {T(P.keb_Lt[0]), T(P.keb_Lt[1]), T(P.keb_Lt[2])};
+        const T Lam[3] = {pk<T>(P.Lam[0], P.f.Lam[0]), pk<T>(P.Lam[1], P.f.Lam[1]), pk<T>(P.Lam[2], P.f.Lam[2])};
+        const T im[3] = {pk<T>(P.keb_im[0], P.f.im[0]), pk<T>(P.keb_im[1], P.f.im[1]), pk<T>(P.keb_im[2], P.f.im[2])};
+        const T Lt[3] = {pk<T>(P.keb_Lt[0], P.f.Lt[0]), pk<T>(P.keb_Lt[1], P.f.Lt[1]), pk<T>(P.keb_Lt[2], P.f.Lt[2])};
         push_keb<T>(p.u, E, B, S.qdt2m, S.qdt2mc, inv_c2, Lam, im, Lt, P.keb_exact != 0);
     } else {
         push_boris<T>(p.u, E, B, S.qdt2m, S.qdt2mc, inv_c2);
     }
     T ig = T(1) / t_sqrt<T>(T(1) + dot(p.u, p.u) * inv_c2);
     d[0] = p.u[0] * ig; d[1] = p.u[1] * ig; d[2] = p.u[2] * ig;
-    if (PUSH == PUSH_KEB) { d[0] *= T(P.inv_lh[0]); d[1] *= T(P.inv_lh[1]); d[2] *= T(P.inv_lh[2]); }
+    if (PUSH == PUSH_KEB) {
+        d[0] *= pk<T>(P.inv_lh[0], P.f.inv_lh[0]);
+        d[1] *= pk<T>(P.inv_lh[1], P.f.inv_lh[1]);
+        d[2] *= pk<T>(P.inv_lh[2], P.f.inv_lh[2]);
+    }
     if (!(d[0] == d[0]) || !(d[1] == d[1]) || !(d[2] == d[2])) {
         atomicOr(P.err, ERRB_NONFINITE);
         d[0] = d[1] = d[2] = T(0);
     }
-    // current from the (comoving) displacement x^n -> x^n + d
-    deposit<T, G, ORD>(ja, jidx, p.o, d, qs);
+}
 
+// Move a pushed particle by d (p still holds its start position): the leaky
+// displacement, the shearing-box second stage and superluminal count, the
+// cell update, periodic and shearing-periodic wraps, and the leaky escape
+// and reinjection.  Afterwards p holds the particle at t^{n+1}.
+template <class T, int G, int PUSH, int ESC>
+__device__ inline void move_particle(Particle<T>& p, const T d[3], const StepP& P, const Grid& g) {
+    using GT = GeomT<G>;
     if (ESC == ESC_DISP) { p.dr[0] += d[0]; p.dr[1] += d[1]; p.dr[2] += d[2]; }
-
-    // new position
     T nx_ = p.o[0] + d[0];
     T ny_ = p.o[1] + d[1];
     T nz_ = p.o[2] + d[2];
     if (PUSH == PUSH_KSB) {
         // x^{n+1} = x' - s Omega0 (x' + x^n)/2 dt e_y (Sec. 2.2)
-        T xc1 = T((double)p.ci - P.half_nx) + nx_;
-        T vs = T(P.sO) * (xc1 + xc0) * T(0.5);
+        const T c = pk<T>(P.c, P.f.c);
+        const T sO = pk<T>(P.sO, P.f.sO);
+        const T half_nx = pk<T>(P.half_nx, P.f.half_nx);
+        const T xc0 = (T(p.ci) - half_nx) + p.o[0];
+        const T xc1 = (T(p.ci) - half_nx) + nx_;
+        const T vs = sO * (xc1 + xc0) * T(0.5);
         {
             // superluminal effective velocity u'/gamma' + v_s (counted, not corrected)
-            T vy = d[1] - T(P.sO) * xc0;
+            T vy = d[1] - sO * xc0;
             if (d[0] * d[0] + vy * vy + d[2] * d[2] >= c * c) atomicAdd(P.counters + 1, 1ull);
         }
         ny_ -= vs;
@@ -622,14 +813,14 @@ __device__ inline void advance_particle(Particle<T>& p, const FA& fa, I fidx, co
         p.ci -= g.nx;
         if (PUSH == PUSH_KSB && GT::AY) {
             p.cj += P.dys_end_i;
-            p.o[1] += T(P.dys_end_f);
+            p.o[1] += pk<T>(P.dys_end_f, P.f.dys_end_f);
             renorm(p.o[1], p.cj);
         }
     } else if (p.ci < 0) {
         p.ci += g.nx;
         if (PUSH == PUSH_KSB && GT::AY) {
             p.cj -= P.dys_end_i;
-            p.o[1] -= T(P.dys_end_f);
+            p.o[1] -= pk<T>(P.dys_end_f, P.f.dys_end_f);
             renorm(p.o[1], p.cj);
         }
     }
@@ -648,7 +839,7 @@ __device__ inline void advance_particle(Particle<T>& p, const FA& fa, I fidx, co
             T ay = t_abs<T>(p.dr[1]);
             m = ay > m ? ay : m;
             if (P.esc_dims == 3) { T az = t_abs<T>(p.dr[2]); m = az > m ? az : m; }
-            esc = m >= T(P.l_esc);
+            esc = m >= pk<T>(P.l_esc, P.f.l_esc);
         } else {
             U4 r = draw(p.id, P.seed, P.step, TAG_ESCAPE, 0u);
             esc = r.x[0] < P.esc_thresh;
@@ -663,6 +854,18 @@ __device__ inline void advance_particle(Particle<T>& p, const FA& fa, I fidx, co
     }
 }
 
+// Push, deposit and move one particle: FA/fidx as for
+// push_particle, JA: current accumulator, jidx: the start cell's linear index
+// in its box.
+template <class T, int G, int ORD, int PUSH, int ESC, class FA, class JA, class I>
+__device__ inline void advance_particle(Particle<T>& p, const FA& fa, I fidx, const JA& ja, I jidx, T qs,
+                                        const SpecStep<T>& S, const StepP& P, const Grid& g) {
+    T d[3];
+    push_particle<T, G, ORD, PUSH>(p, fa, fidx, S, P, d);
+    deposit<T, G, ORD>(ja, jidx, p.o, d, qs);  // current from the (comoving) move x^n -> x^n + d
+    move_particle<T, G, PUSH, ESC>(p, d, P, g);
+}
+
 
 // The per-step scalars of a step come from the device-resident context.
 __device__ inline StepP with_ctx(const StepP& P0, const StepCtx* ctx) {
@@ -673,6 +876,10 @@ __device__ inline StepP with_ctx(const StepP& P0, const StepCtx* ctx) {
     P.inv_lh[0] = ctx->inv_lh[0];
     P.inv_lh[1] = ctx->inv_lh[1];
     P.inv_lh[2] = ctx->inv_lh[2];
+    P.f.dys_end_f = ctx->f_dys_f[2];
+    P.f.inv_lh[0] = ctx->f_inv_lh[0];
+    P.f.inv_lh[1] = ctx->f_inv_lh[1];
+    P.f.inv_lh[2] = ctx->f_inv_lh[2];
     return P;
 }
 
@@ -707,27 +914,54 @@ __device__ inline void place_mover(const Particle<T>& p, int dest, const SpecSte
 constexpr int TPB = 256;  // threads per CTA of the loose kernel
 constexpr long long TMA_WAIT_LIMIT = 1ll << 24;
 
+// Tile-kernel variants: threads per CTA, the order of the stayers' write,
+// and whether zero current contributions are skipped.
+//
+// Shared-memory atomics of a warp cost one pass per distinct address in the
+// busiest bank (lanes adding to the same word are merged).  Every deposit of a
+// particle adds to words at fixed offsets from its window base, and the
+// window bases of particles in one or two neighbouring cells fall in distinct
+// banks, so a warp whose particles share a cell adds conflict-free.  The
+// device loader stores each tile's particles grouped by cell; the "stable"
+// variants keep that order, writing each chunk's stayers in input order (a
+// CTA-wide prefix over the warps' counts, one barrier per chunk), so warps
+// stay cell-coherent and every contribution is added unconditionally.  The
+// other variants let warps claim output ranges in any order (no barrier),
+// which mixes the cells within warps over a few steps; they skip zero
+// contributions per lane instead.  Particle states and FP32 currents are the
+// same in all variants (exact integer sums).
+struct TileVariant { int nt, stable, min_blocks; };
+constexpr int N_TILE_VARIANTS = 4;
+constexpr TileVariant TILE_VARIANTS[N_TILE_VARIANTS] = {{256, 0, 3}, {512, 0, 2}, {512, 1, 2}, {256, 1, 3}};
+
 // Dynamic shared memory: E box, B box (each 128-byte aligned, the TMA
-// destinations), the J box (int32 for FP32, double for FP64), the mbarrier
-// and small counters.
-template <class T, int G> struct SmemLayout {
+// destinations), the J box (int32 for FP32, double for FP64), the mbarrier,
+// small counters, and for stable variants two buffers of per-warp stayer
+// counts.
+template <class T, int G, int NT, int STABLE> struct SmemLayout {
     static constexpr int FB = TileDims<G>::FB, JB = TileDims<G>::JB;
+    static constexpr int QCAP = 64;  // entries of a warp's crossing-particle queue
     static constexpr size_t off_B = ((size_t)3 * FB * sizeof(T) + 127) & ~(size_t)127;
     static constexpr size_t off_J = (off_B + (size_t)3 * FB * sizeof(T) + 127) & ~(size_t)127;
-    static constexpr size_t off_bar = (off_J + (size_t)3 * JB * sizeof(T) + 15) & ~(size_t)15;
-    static constexpr size_t bytes = off_bar + 16 + 4 * (MAXSP + 2);
+    static constexpr size_t off_q = (off_J + (size_t)3 * JB * sizeof(T) + 15) & ~(size_t)15;
+    static constexpr size_t off_qc = off_q + (size_t)(NT / 32) * QCAP * 6 * sizeof(T);
+    static constexpr size_t off_bar = (off_qc + (size_t)(NT / 32) * QCAP * 4 + 15) & ~(size_t)15;
+    static constexpr size_t off_wc = off_bar + 16 + 4 * (MAXSP + 2);
+    static constexpr size_t bytes = off_wc + (STABLE ? 2 * (NT / 32) * 4 : 0);
 };
 
-// The fused particle step for one tile (see the file header).  NT threads per CTA.
-template <class T, int G, int ORD, int PUSH, int ESC, int NT>
-__global__ void __launch_bounds__(NT, NT == 512 ? 2 : 3) tile_kernel(const __grid_constant__ CUtensorMap tmE,
+// The fused particle step for one tile (see the file header).  NT threads per
+// CTA; STABLE: order-preserving stayer write and unconditional adds (above).
+template <class T, int G, int ORD, int PUSH, int ESC, int NT, int STABLE>
+__global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (NT == 512 ? 2 : 3)) tile_kernel(const __grid_constant__ CUtensorMap tmE,
                                                    const __grid_constant__ CUtensorMap tmB, Grid g, Tiling tl,
                                                    StepP P0, SpecPack<T> SP, JWord<T>* __restrict__ J,
                                                    const StepCtx* __restrict__ ctx) {
     using GT = GeomT<G>;
     constexpr bool LEAKY = (ESC == ESC_DISP);
     using D = TileDims<G>;
-    using L = SmemLayout<T, G>;
+    using L = SmemLayout<T, G, NT, STABLE>;
+    constexpr int NW = NT / 32;
     using JW = JWord<T>;
     const StepP P = with_ctx(P0, ctx);
     extern __shared__ __align__(128) unsigned char smem[];
@@ -738,7 +972,7 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 3) tile_kernel(const __gri
     int* s_cnt = reinterpret_cast<int*>(smem + L::off_bar + 16);
     int* s_ok = s_cnt + MAXSP;
 
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int t = blockIdx.x;
     const int ti = t % tl.ntx, tj = (t / tl.ntx) % tl.nty, tk = t / (tl.ntx * tl.nty);
     const int t0x = ti * D::TX, t0y = tj * D::TY, t0z = tk * D::TZ;
@@ -767,13 +1001,18 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 3) tile_kernel(const __gri
     }
 
     const SmemFields<T, G> fa{sE, sB};
-    const SmemJ<T, G> ja{sJ};
+    const SmemJ<T, G> ja(sJ);
     using FA = SmemFields<T, G>;
     using JA = SmemJ<T, G>;
     const T vscale = sizeof(T) == 4 ? T(P.fx_scale) : T(1);
     // index-space origins (physical cell of local index 0)
     const int fox = xs - 2, foy = GT::AY ? t0y - 2 : 0, foz = GT::AZ ? t0z - 2 : 0;
     const int jox = t0x - 2, joy = GT::AY ? t0y - 2 : 0, joz = GT::AZ ? t0z - 2 : 0;
+    T* q_od = reinterpret_cast<T*>(smem + L::off_q) + (size_t)warp * 6 * L::QCAP;  // this warp's queue:
+    int* q_cell = reinterpret_cast<int*>(smem + L::off_qc) + warp * L::QCAP;        // start offsets, moves, cells
+    int qn = 0;                                                                     // entries (warp-uniform)
+    int* s_wc = reinterpret_cast<int*>(smem + L::off_wc);  // [2][NW] stayer counts (stable variants)
+    int wcb = 0;                                            // their buffer for the current chunk
 
     for (int s = 0; s < P.nsp; ++s) {
         const SpecStep<T>& S = SP.s[s];
@@ -781,28 +1020,104 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 2 : 3) tile_kernel(const __gri
         const int n = nst + nar;
         const long long base = (long long)t * S.tcap;
         const T qs = S.q * vscale;
+        int run = 0;  // stayers written so far (stable variants)
+        // full deposit of queue entry e (lanes read their entries before any write)
+        auto queued_deposit = [&](int e) {
+            T oe[3], de[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                oe[a] = q_od[a * L::QCAP + e];
+                de[a] = q_od[(3 + a) * L::QCAP + e];
+            }
+            deposit<T, G, ORD>(ja, q_cell[e], oe, de, qs);
+        };
         for (int i0 = 0; i0 < n; i0 += NT) {
             const int i = i0 + tid;
             const bool valid = i < n;
             Particle<T> p;
             int dest = -1;
+            bool cross = false;
+            int jidx = 0;
+            T o0[3], d[3];
             if (valid) {
                 const long long slot = i < nst ? base + i : base + S.tcap - nar + (i - nst);
                 load_particle<T, G>(S.in, slot, LEAKY, p);
                 const int fidx = (p.ci - fox) + (GT::AY ? (p.cj - foy) * FA::SY : 0) + (GT::AZ ? (p.ck - foz) * FA::SZ : 0);
-                const int jidx = (p.ci - jox) + (GT::AY ? (p.cj - joy) * JA::SY : 0) + (GT::AZ ? (p.ck - joz) * JA::SZ : 0);
-                advance_particle<T, G, ORD, PUSH, ESC>(p, fa, fidx, ja, jidx, qs, S, P, g);
+                jidx = (p.ci - jox) + (GT::AY ? (p.cj - joy) * JA::SY : 0) + (GT::AZ ? (p.ck - joz) * JA::SZ : 0);
+                push_particle<T, G, ORD, PUSH>(p, fa, fidx, S, P, d);
+                cross = crosses<T, G, ORD>(p.o, d);
+                deposit_core<T, G, ORD>(ja, jidx, p.o, d, qs, cross);
+                o0[0] = p.o[0]; o0[1] = p.o[1]; o0[2] = p.o[2];
+                move_particle<T, G, PUSH, ESC>(p, d, P, g);
                 dest = tile_of<G>(tl, p.ci, p.cj, p.ck);
             }
+            // crossing particles join the warp's queue; their full deposit is
+            // made 32 at a time, every lane adding real contributions
+            const unsigned qm = __ballot_sync(0xffffffffu, cross);
+            if (cross) {
+                const int pos = qn + __popc(qm & ((1u << lane) - 1u));
+                q_cell[pos] = jidx;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    q_od[a * L::QCAP + pos] = o0[a];
+                    q_od[(3 + a) * L::QCAP + pos] = d[a];
+                }
+            }
+            qn += __popc(qm);
             const bool stay = valid && dest == t;
             const unsigned m = __ballot_sync(0xffffffffu, stay);
             int wb = 0;
-            if (lane == 0 && m) wb = atomicAdd(&s_cnt[s], __popc(m));
-            wb = __shfl_sync(0xffffffffu, wb, 0);
+            if (STABLE) {
+                // this warp's stayers go after those of the chunk's lower warps
+                int* wc = s_wc + wcb * NW;
+                if (lane == 0) wc[warp] = __popc(m);
+                __syncthreads();
+                const int cw = lane < NW ? wc[lane] : 0;
+                int incl = cw;
+#pragma unroll
+                for (int sh = 1; sh < 32; sh <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, sh);
+                    if (lane >= sh) incl += v;
+                }
+                wb = run + __shfl_sync(0xffffffffu, incl - cw, warp);
+                run += __shfl_sync(0xffffffffu, incl, 31);
+                wcb ^= 1;
+            } else {
+                if (lane == 0 && m) wb = atomicAdd(&s_cnt[s], __popc(m));
+                wb = __shfl_sync(0xffffffffu, wb, 0);
+            }
             if (stay) store_particle<T, G>(S.out, base + wb + __popc(m & ((1u << lane) - 1u)), LEAKY, p);
             else if (valid) place_mover<T, G>(p, dest, S, P, LEAKY);
+            if (qn >= 32) {
+                __syncwarp();
+                queued_deposit(lane);
+                // move the remaining entries (qn - 32 < 32) to the front
+                const int rest = qn - 32;
+                int c = 0;
+                T od[6];
+                if (lane < rest) {
+                    c = q_cell[32 + lane];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) od[k] = q_od[k * L::QCAP + 32 + lane];
+                }
+                __syncwarp();
+                if (lane < rest) {
+                    q_cell[lane] = c;
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) q_od[k * L::QCAP + lane] = od[k];
+                }
+                __syncwarp();
+                qn = rest;
+            }
         }
+        // the species' remaining queue (charge qs)
+        __syncwarp();
+        if (lane < qn) queued_deposit(lane);
+        __syncwarp();
+        qn = 0;
+        if (STABLE && tid == 0) s_cnt[s] = run;
     }
+
     __syncthreads();
     // flush the J tile into the global accumulator (integer adds for FP32, so
     // the result does not depend on the order tiles finish in): padded index

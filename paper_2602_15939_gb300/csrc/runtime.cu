@@ -60,6 +60,37 @@ struct Prof {
 
 }  // namespace
 
+// Shared memory of the particle kernel of variant v (E and B boxes, the
+// variant's current copies, barrier and counters).
+constexpr size_t MAX_SMEM = 227 * 1024;
+
+template <class T, int G, int V> static size_t smem_v() {
+    return SmemLayout<T, G, TILE_VARIANTS[V].nt, TILE_VARIANTS[V].stable>::bytes;
+}
+
+template <class T, int G> static size_t tile_smem_bytes_t(int v) {
+    static_assert(N_TILE_VARIANTS == 4, "one entry per tile variant");
+    switch (v) {
+        case 0: return smem_v<T, G, 0>();
+        case 1: return smem_v<T, G, 1>();
+        case 2: return smem_v<T, G, 2>();
+        default: return smem_v<T, G, 3>();
+    }
+}
+
+static size_t tile_smem_bytes(bool fp64, int geom, int v) {
+    if (fp64) return geom == 0 ? tile_smem_bytes_t<double, 0>(v) : geom == 1 ? tile_smem_bytes_t<double, 1>(v)
+                                                                              : tile_smem_bytes_t<double, 2>(v);
+    return geom == 0 ? tile_smem_bytes_t<float, 0>(v) : geom == 1 ? tile_smem_bytes_t<float, 1>(v)
+                                                                   : tile_smem_bytes_t<float, 2>(v);
+}
+
+// Variant used when the configuration leaves the choice to the library.
+static int default_variant(bool fp64, int geom) {
+    (void)geom;
+    return fp64 ? 1 : 2;
+}
+
 struct pic_handle {
     pic_config cfg;
     int geom = 0;  // 0 3D, 1 2D-XY, 2 2D-XZ
@@ -70,7 +101,8 @@ struct pic_handle {
     int push = PUSH_BORIS, esc = ESC_NONE;
     KernelSet ks{};
     const void* tile_fn = nullptr;
-    int tile_threads = 256;
+    int tile_variant = 1;  // index into TILE_VARIANTS
+    int tile_threads = 512;
     size_t smem_bytes = 0;
     // fields
     void* E = nullptr;
@@ -356,6 +388,18 @@ template <class T, int G> static pic_status step_t(pic_handle* h) {
     P.seed = cf.seed;
     P.theta_inj = cf.theta_inj;
     P.esc_dims = cf.escape_dims;
+    P.inv_c2 = 1.0 / (cf.c * cf.c);
+    P.f.c = (float)P.c;
+    P.f.inv_c2 = (float)P.inv_c2;
+    P.f.sO = (float)P.sO;
+    P.f.Omega0 = (float)P.Omega0;
+    P.f.half_nx = (float)P.half_nx;
+    P.f.l_esc = (float)P.l_esc;
+    for (int a = 0; a < 3; ++a) {
+        P.f.Lam[a] = (float)P.Lam[a];
+        P.f.im[a] = (float)P.keb_im[a];
+        P.f.Lt[a] = (float)P.keb_Lt[a];
+    }
     P.err = h->err;
     P.counters = h->counters;
 
@@ -815,20 +859,20 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
     tl.jx = tl.tx + 5;
     tl.jy = AY ? tl.ty + 5 : 1;
     tl.jz = AZ ? tl.tz + 5 : 1;
-    h->smem_bytes = h->fp64 ? (h->geom == 0   ? SmemLayout<double, 0>::bytes
-                               : h->geom == 1 ? SmemLayout<double, 1>::bytes
-                                              : SmemLayout<double, 2>::bytes)
-                            : (h->geom == 0   ? SmemLayout<float, 0>::bytes
-                               : h->geom == 1 ? SmemLayout<float, 1>::bytes
-                                              : SmemLayout<float, 2>::bytes);
-    if (h->smem_bytes > 227 * 1024) {
-        delete h;
-        return fail(nullptr, PIC_ERR_ARG, "tile needs %zu bytes of shared memory (> 227 KB)", h->smem_bytes);
+    {
+        int v = c.kernel_variant > 0 ? (int)c.kernel_variant - 1 : default_variant(h->fp64, h->geom);
+        if (c.kernel_variant == 0)
+            if (const char* e = getenv("PIC_KERNEL_VARIANT")) v = atoi(e) - 1;
+        if (v < 0 || v >= N_TILE_VARIANTS || tile_smem_bytes(h->fp64, h->geom, v) > MAX_SMEM) {
+            delete h;
+            return fail(nullptr, PIC_ERR_ARG, "particle-kernel variant %d does not fit this configuration", v + 1);
+        }
+        h->tile_variant = v;
+        h->tile_threads = TILE_VARIANTS[v].nt;
+        h->smem_bytes = tile_smem_bytes(h->fp64, h->geom, v);
     }
     h->ks = lookup_kernels(h->fp64, h->geom, c.shape_order, h->push, h->esc);
-    h->tile_threads = 512;
-    if (const char* e = getenv("PIC_TILE_THREADS")) h->tile_threads = atoi(e) == 256 ? 256 : 512;
-    h->tile_fn = h->tile_threads == 512 ? h->ks.tile512 : h->ks.tile;
+    h->tile_fn = h->ks.tile[h->tile_variant];
 
     auto bail = [&](pic_status s) {
         g_init_error = h->last_error;
@@ -1183,6 +1227,38 @@ pic_status pic_get_profile(pic_handle* h, pic_profile* out) {
     out->launches = h->prof.launches;
     out->particle_launches = h->prof.particle_launches;
     out->particle_steps = h->prof.particle_steps;
+    return PIC_OK;
+}
+
+int pic_kernel_variant_count(void) { return N_TILE_VARIANTS; }
+
+pic_status pic_kernel_variant_info(int32_t k, int32_t* threads_per_cta, int32_t* stable) {
+    if (k < 1 || k > N_TILE_VARIANTS) return fail(nullptr, PIC_ERR_ARG, "kernel variant %d out of range", (int)k);
+    if (threads_per_cta) *threads_per_cta = TILE_VARIANTS[k - 1].nt;
+    if (stable) *stable = TILE_VARIANTS[k - 1].stable;
+    return PIC_OK;
+}
+
+pic_status pic_get_kernel_variant(pic_handle* h, int32_t* k) {
+    if (!h || !k) return fail(h, PIC_ERR_ARG, "NULL argument");
+    *k = h->tile_variant + 1;
+    return PIC_OK;
+}
+
+pic_status pic_set_kernel_variant(pic_handle* h, int32_t k) {
+    if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    if (k < 1 || k > N_TILE_VARIANTS) return fail(h, PIC_ERR_ARG, "kernel variant %d out of range", (int)k);
+    const int v = k - 1;
+    const size_t smem = tile_smem_bytes(h->fp64, h->geom, v);
+    if (smem > MAX_SMEM) return fail(h, PIC_ERR_ARG, "kernel variant %d needs %zu bytes of shared memory", (int)k, smem);
+    cudaSetDevice(h->cfg.device);
+    if (cudaFuncSetAttribute(h->ks.tile[v], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return fail(h, PIC_ERR_CUDA, "cannot set %zu bytes of dynamic shared memory", smem);
+    drop_graphs(h);
+    h->tile_variant = v;
+    h->tile_threads = TILE_VARIANTS[v].nt;
+    h->smem_bytes = smem;
+    h->tile_fn = h->ks.tile[v];
     return PIC_OK;
 }
 

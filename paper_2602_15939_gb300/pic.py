@@ -46,7 +46,7 @@ class pic_config(C.Structure):
         ("shape_order", C.c_int32), ("precision", C.c_int32), ("fp_iters", C.c_int32),
         ("keb_push", C.c_int32), ("escape_mode", C.c_int32), ("escape_dims", C.c_int32),
         ("tile", C.c_int32 * 3), ("device", C.c_int32),
-        ("seed", C.c_uint32), ("reserved1", C.c_uint32),
+        ("seed", C.c_uint32), ("kernel_variant", C.c_uint32),
         ("c", C.c_double), ("s_shear", C.c_double), ("Omega0", C.c_double),
         ("expand_rate", C.c_double * 3), ("l_esc", C.c_double), ("p_esc", C.c_double),
         ("theta_inj", C.c_double), ("capacity_slack", C.c_double),
@@ -113,6 +113,10 @@ _SIGS = {
     "pic_set_profiling": (C.c_int, [_H, C.c_int]),
     "pic_get_profile": (C.c_int, [_H, C.POINTER(pic_profile)]),
     "pic_reset_profile": (C.c_int, [_H]),
+    "pic_kernel_variant_count": (C.c_int, []),
+    "pic_kernel_variant_info": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "pic_get_kernel_variant": (C.c_int, [_H, C.POINTER(C.c_int32)]),
+    "pic_set_kernel_variant": (C.c_int, [_H, C.c_int32]),
     "pic_field_energy_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
     "pic_run_footprint": (C.c_int, [C.POINTER(pic_run_spec), C.POINTER(C.c_uint64)]),
     "pic_admission_count": (C.c_int, [C.c_uint64, C.c_uint64, C.c_int, C.c_int, C.POINTER(C.c_uint64), C.c_int]),
@@ -287,6 +291,27 @@ def pic_reset_profile(h):
     _check(h, lib().pic_reset_profile(h))
 
 
+def pic_kernel_variant_count() -> int:
+    return lib().pic_kernel_variant_count()
+
+
+def pic_kernel_variant_info(k: int):
+    """(threads per CTA, stable stayer order 0/1) of particle-kernel variant k (1-based)."""
+    nt, jc = C.c_int32(), C.c_int32()
+    _check(None, lib().pic_kernel_variant_info(k, C.byref(nt), C.byref(jc)))
+    return nt.value, jc.value
+
+
+def pic_get_kernel_variant(h) -> int:
+    k = C.c_int32()
+    _check(h, lib().pic_get_kernel_variant(h, C.byref(k)))
+    return k.value
+
+
+def pic_set_kernel_variant(h, k: int):
+    _check(h, lib().pic_set_kernel_variant(h, k))
+
+
 def pic_field_energy_noalloc(d_field: int, precision: int, n: int, ncomp: int, d_out: int, stream: int | None = None):
     """Allocation-free field energy of a caller-owned device array (raw device
     pointers as integers); see include/pic.h."""
@@ -299,7 +324,7 @@ def pic_field_energy_noalloc(d_field: int, precision: int, n: int, ncomp: int, d
 def make_config(box=PIC_BOX_PERIODIC, nx=8, ny=8, nz=8, ndim=3, plane=PIC_PLANE_XY, c=0.45, order=1,
                 precision=PIC_FP64, fp_iters=4, keb_push=PIC_KEB_CLOSED_FORM, escape_mode=PIC_ESC_NONE,
                 escape_dims=2, tile=(0, 0, 0), seed=0, s=0.0, Omega0=0.0, rate=(0.0, 0.0, 0.0), l_esc=0.0,
-                p_esc=0.0, theta_inj=0.0, capacity_slack=0.0, device=0) -> pic_config:
+                p_esc=0.0, theta_inj=0.0, capacity_slack=0.0, device=0, kernel_variant=0) -> pic_config:
     cfg = pic_config()
     cfg.box, cfg.ndim, cfg.plane = box, ndim, plane
     cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
@@ -312,6 +337,7 @@ def make_config(box=PIC_BOX_PERIODIC, nx=8, ny=8, nz=8, ndim=3, plane=PIC_PLANE_
     cfg.c, cfg.s_shear, cfg.Omega0 = c, s, Omega0
     cfg.l_esc, cfg.p_esc, cfg.theta_inj, cfg.capacity_slack = l_esc, p_esc, theta_inj, capacity_slack
     cfg.device = device
+    cfg.kernel_variant = kernel_variant
     return cfg
 
 

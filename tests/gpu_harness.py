@@ -40,6 +40,7 @@ class Case:
     q: float = 0.05
     drift: tuple = (0.0, 0.0, 0.0)
     slack: float = 0.0
+    variant: int = 0
     extra: dict = field(default_factory=dict)
 
     @property
@@ -61,7 +62,7 @@ class Case:
                              keb_push=self.keb_exact, escape_mode=self.esc_mode, escape_dims=self.esc_dims,
                              tile=self.tile, seed=self.seed, s=self.s, Omega0=self.Omega0, rate=self.rate,
                              l_esc=self.l_esc, p_esc=self.p_esc, theta_inj=self.theta_inj,
-                             capacity_slack=self.slack)
+                             capacity_slack=self.slack, kernel_variant=self.variant)
 
 
 def inputs(case: Case):

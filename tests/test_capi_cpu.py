@@ -54,3 +54,13 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.pic_step(None, 1) == P.PIC_ERR_ARG
     assert lib.pic_destroy(None) == P.PIC_OK
     assert lib.pic_synchronize(None) == P.PIC_ERR_ARG
+
+
+def test_kernel_variant_table():
+    n = P.pic_kernel_variant_count()
+    assert n == 4
+    shapes = [P.pic_kernel_variant_info(k) for k in range(1, n + 1)]
+    assert shapes == [(256, 0), (512, 0), (512, 1), (256, 1)]
+    for bad in (0, n + 1):
+        with pytest.raises(P.PicError):
+            P.pic_kernel_variant_info(bad)
