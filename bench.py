@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-runs", type=int, default=64)
     ap.add_argument("--kernel-only", action="store_true", help="warmup + timed steps only (for profiler runs)")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="particle-kernel variant (1-based); 0 = autotune on the box after warm-up")
     return ap.parse_args()
 
 
@@ -258,6 +260,17 @@ def run_gb300(args):
     box = setup_box(w, local, stream.cuda_stream, seed=replica_seed(rank))
     npart = w.n_particles
     box.step(args.warmup)
+    # particle-kernel launch variant: autotuned on this machine (trial steps are
+    # ordinary, untimed steps) unless forced
+    if args.variant:
+        P.pic_set_kernel_variant(box.h, args.variant)
+        tune = {"chosen": args.variant, "how": "forced"}
+    else:
+        best, ms_v, taken = box.autotune(4)
+        tune = {"chosen": best, "how": f"autotuned on {taken} untimed steps",
+                "particle_ms_per_variant": [None if v is None else round(v, 4) for v in ms_v]}
+    nt_, st_ = P.pic_kernel_variant_info(tune["chosen"])
+    tune.update({"threads_per_cta": nt_, "stable_order": bool(st_)})
     box.sync()
     torch.cuda.synchronize()
 
@@ -312,7 +325,8 @@ def run_gb300(args):
             "config": {"workload": w.name, "grid": list(w.n), "ppc_per_species": w.ppc, "particles": npart,
                        "shape_order": w.order, "box": "expanding", "expansion_rate_wp": list(w.rate_wp),
                        "precision": "int32 cell + fp32 offsets/momenta, fp64 l(t)",
-                       "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"},
+                       "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}",
+                       "kernel_variant": tune},
             "particle_phase": {"value": npart / (particle_ms / 1e3), "unit": UNIT, "avg_launch_ms": particle_ms},
             "profile_ms_per_step": {"particle": prof.ms_particle / args.steps, "field": prof.ms_field / args.steps,
                                     "other": prof.ms_other / args.steps},

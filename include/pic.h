@@ -229,6 +229,18 @@ pic_status pic_kernel_variant_info(int32_t k, int32_t *threads_per_cta, int32_t 
 pic_status pic_get_kernel_variant(pic_handle *h, int32_t *k);
 pic_status pic_set_kernel_variant(pic_handle *h, int32_t k);
 
+/* Autotuner: run each variant that fits for trial_steps ordinary steps of
+ * this box (two interleaved rounds, the first step after each switch
+ * untimed), time its particle kernel with CUDA events, and keep the fastest.
+ * The trial steps advance the simulation like pic_step (all variants give
+ * the same result), so tuning costs no extra work beyond those steps.
+ * Outputs (nullable): *best (1-based), ms_per_variant[pic_kernel_variant_count()]
+ * (mean particle-kernel ms per step; -1 where the variant does not fit) and
+ * *steps_taken.  Synchronizes the handle's stream; captured step graphs are
+ * dropped. */
+pic_status pic_autotune(pic_handle *h, int32_t trial_steps, int32_t *best, double *ms_per_variant,
+                        int64_t *steps_taken);
+
 /* ---- serving: continuous batching of independent runs ------------------------
  * A run is one box advanced for nsteps from a device Maxwellian load and
  * uniform initial fields.  The server admits queued runs in arrival order as

@@ -85,10 +85,11 @@ static size_t tile_smem_bytes(bool fp64, int geom, int v) {
                                                                    : tile_smem_bytes_t<float, 2>(v);
 }
 
-// Variant used when the configuration leaves the choice to the library.
+// Variant used when the configuration leaves the choice to the library
+// (measured on GB300: 256 threads for 3D FP32 tiles, 512 otherwise;
+// pic_autotune refines it for a given box).
 static int default_variant(bool fp64, int geom) {
-    (void)geom;
-    return fp64 ? 1 : 2;
+    return (!fp64 && geom == 0) ? 0 : 1;
 }
 
 struct pic_handle {
@@ -1259,6 +1260,73 @@ pic_status pic_set_kernel_variant(pic_handle* h, int32_t k) {
     h->tile_threads = TILE_VARIANTS[v].nt;
     h->smem_bytes = smem;
     h->tile_fn = h->ks.tile[v];
+    return PIC_OK;
+}
+
+pic_status pic_autotune(pic_handle* h, int32_t trial_steps, int32_t* best, double* ms_per_variant,
+                        int64_t* steps_taken) {
+    if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    if (trial_steps < 1) return fail(h, PIC_ERR_ARG, "trial_steps must be >= 1");
+    cudaSetDevice(h->cfg.device);
+    const bool prof_was = h->prof.on;
+    const int start_variant = h->tile_variant;
+    double ms[N_TILE_VARIANTS];
+    long long launches[N_TILE_VARIANTS];
+    bool fits[N_TILE_VARIANTS];
+    for (int v = 0; v < N_TILE_VARIANTS; ++v) {
+        ms[v] = 0.0;
+        launches[v] = 0;
+        fits[v] = tile_smem_bytes(h->fp64, h->geom, v) <= MAX_SMEM;
+    }
+    long long taken = 0;
+    // two interleaved rounds, so that every variant sees particles in a
+    // similar order (the order within tiles evolves from step to step)
+    const int rounds = 2;
+    const int per_round = (trial_steps + rounds - 1) / rounds;
+    prof_resolve(h);
+    const double ms0[3] = {h->prof.ms[0], h->prof.ms[1], h->prof.ms[2]};
+    const long long l0 = h->prof.launches, pl0 = h->prof.particle_launches, ps0 = h->prof.particle_steps;
+    pic_status st = PIC_OK;
+    for (int r = 0; r < rounds && st == PIC_OK; ++r)
+        for (int v = 0; v < N_TILE_VARIANTS && st == PIC_OK; ++v) {
+            if (!fits[v]) continue;
+            st = pic_set_kernel_variant(h, v + 1);
+            if (st != PIC_OK) break;
+            h->prof.on = false;
+            st = pic_step(h, 1);  // first launch of the variant: not timed
+            taken += 1;
+            if (st != PIC_OK) break;
+            prof_resolve(h);
+            const double before = h->prof.ms[0];
+            const long long lb = h->prof.particle_launches;
+            h->prof.on = true;
+            st = pic_step(h, per_round);
+            taken += per_round;
+            prof_resolve(h);
+            ms[v] += h->prof.ms[0] - before;
+            launches[v] += h->prof.particle_launches - lb;
+        }
+    // the profile counters are the caller's: put them back
+    h->prof.ms[0] = ms0[0];
+    h->prof.ms[1] = ms0[1];
+    h->prof.ms[2] = ms0[2];
+    h->prof.launches = l0;
+    h->prof.particle_launches = pl0;
+    h->prof.particle_steps = ps0;
+    h->prof.on = prof_was;
+    if (st != PIC_OK) {
+        pic_set_kernel_variant(h, start_variant + 1);
+        return st;
+    }
+    int bv = start_variant;
+    for (int v = 0; v < N_TILE_VARIANTS; ++v)
+        if (fits[v] && launches[v] > 0 && (launches[bv] == 0 || ms[v] / launches[v] < ms[bv] / launches[bv])) bv = v;
+    st = pic_set_kernel_variant(h, bv + 1);
+    if (st != PIC_OK) return st;
+    if (best) *best = bv + 1;
+    if (ms_per_variant)
+        for (int v = 0; v < N_TILE_VARIANTS; ++v) ms_per_variant[v] = launches[v] > 0 ? ms[v] / launches[v] : -1.0;
+    if (steps_taken) *steps_taken = taken;
     return PIC_OK;
 }
 

@@ -117,6 +117,7 @@ _SIGS = {
     "pic_kernel_variant_info": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pic_get_kernel_variant": (C.c_int, [_H, C.POINTER(C.c_int32)]),
     "pic_set_kernel_variant": (C.c_int, [_H, C.c_int32]),
+    "pic_autotune": (C.c_int, [_H, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "pic_field_energy_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
     "pic_run_footprint": (C.c_int, [C.POINTER(pic_run_spec), C.POINTER(C.c_uint64)]),
     "pic_admission_count": (C.c_int, [C.c_uint64, C.c_uint64, C.c_int, C.c_int, C.POINTER(C.c_uint64), C.c_int]),
@@ -312,6 +313,17 @@ def pic_set_kernel_variant(h, k: int):
     _check(h, lib().pic_set_kernel_variant(h, k))
 
 
+def pic_autotune(h, trial_steps: int = 4):
+    """Time every fitting particle-kernel variant on live steps and keep the
+    fastest: returns (best variant, ms per variant (None where it does not
+    fit), steps taken)."""
+    n = pic_kernel_variant_count()
+    best, taken = C.c_int32(), C.c_int64()
+    ms = (C.c_double * n)()
+    _check(h, lib().pic_autotune(h, trial_steps, C.byref(best), ms, C.byref(taken)))
+    return best.value, [v if v >= 0 else None for v in ms], taken.value
+
+
 def pic_field_energy_noalloc(d_field: int, precision: int, n: int, ncomp: int, d_out: int, stream: int | None = None):
     """Allocation-free field energy of a caller-owned device array (raw device
     pointers as integers); see include/pic.h."""
@@ -377,6 +389,10 @@ class Box:
 
     def set_uniform_fields(self, E, B):
         pic_set_uniform_fields(self.h, E, B)
+
+    def autotune(self, trial_steps=4):
+        """Pick the fastest particle-kernel variant on live steps; see pic_autotune."""
+        return pic_autotune(self.h, trial_steps)
 
     def step(self, n=1):
         pic_step(self.h, n)

@@ -108,3 +108,36 @@ def test_switch_variant_on_a_live_box():
         assert np.array_equal(ia, ib) and np.array_equal(xa, xb) and np.array_equal(ua, ub)
     for a, b in zip(fields_ref, fields):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.gpu
+def test_autotune_steps_are_ordinary_steps():
+    """The autotuner's trial steps advance the box exactly like pic_step: the
+    state after autotune + k steps equals that of a fixed variant run for the
+    same total number of steps, bit for bit (FP32)."""
+    from gpu_harness import inputs
+
+    case = CASES[0]
+    sp, E, B = inputs(case)
+    box = P.Box(case.gpu_config(False))
+    try:
+        box.set_fields(E, B)
+        for i, d in enumerate(sp):
+            box.load(i, d["q"], d["m"], d["x"], d["u"], d["id"])
+        box.set_step(case.step0)
+        best, ms, taken = box.autotune(2)
+        assert 1 <= best <= P.pic_kernel_variant_count()
+        assert all(v is not None and v > 0 for v in ms)
+        assert ms[best - 1] == min(ms)
+        assert P.pic_get_kernel_variant(box.h) == best
+        box.step(1)
+        parts = [box.particles(i) for i in range(len(sp))]
+        fields = box.fields()
+        assert box.diagnostics().step == case.step0 + taken + 1
+    finally:
+        box.close()
+    parts_ref, fields_ref, _ = run_gpu(dataclasses.replace(case, variant=1), taken + 1, False)
+    for (xa, ua, ia), (xb, ub, ib) in zip(by_id(parts_ref), by_id(parts)):
+        assert np.array_equal(ia, ib) and np.array_equal(xa, xb) and np.array_equal(ua, ub)
+    for a, b in zip(fields_ref, fields):
+        assert np.array_equal(a, b)
