@@ -269,8 +269,8 @@ def run_gb300(args):
         best, ms_v, taken = box.autotune(4)
         tune = {"chosen": best, "how": f"autotuned on {taken} untimed steps",
                 "particle_ms_per_variant": [None if v is None else round(v, 4) for v in ms_v]}
-    nt_, st_ = P.pic_kernel_variant_info(tune["chosen"])
-    tune.update({"threads_per_cta": nt_, "stable_order": bool(st_)})
+    nt_, st_, jc_ = P.pic_kernel_variant_info(tune["chosen"])
+    tune.update({"threads_per_cta": nt_, "stable_order": bool(st_), "current_copies": jc_})
     box.sync()
     torch.cuda.synchronize()
 

@@ -215,14 +215,13 @@ pic_status pic_reset_profile(pic_handle *h);
  * counterpart in the paper, which gives no kernel design), numbered
  * 1..pic_kernel_variant_count().  Variant k runs *threads_per_cta threads per
  * CTA, one CTA per tile.  *stable = 1: each tile's stayers are written in
- * their input order (particles stay grouped by cell, as the device loader
- * stores them, so the lanes of a warp add their currents conflict-free, and
- * every contribution is added); 0: warps write in any order and skip zero
- * contributions.  All variants compute the same result; particle states and
- * FP32 currents are bit-identical.  Outputs may be NULL; k out of range is
- * PIC_ERR_ARG. */
+ * their input order (one barrier per chunk; particles stay grouped by cell as
+ * the device loader stores them); 0: warps write in any order.  *copies: 1 or
+ * 2 copies of the tile's shared current box, lanes alternating between them.
+ * All variants compute the same result; particle states and FP32 currents are
+ * bit-identical.  Outputs may be NULL; k out of range is PIC_ERR_ARG. */
 int pic_kernel_variant_count(void);
-pic_status pic_kernel_variant_info(int32_t k, int32_t *threads_per_cta, int32_t *stable);
+pic_status pic_kernel_variant_info(int32_t k, int32_t *threads_per_cta, int32_t *stable, int32_t *copies);
 /* The variant handle h runs (1-based) / switch it to variant k (takes effect at
  * the next pic_step; PIC_ERR_ARG if its shared memory does not fit the
  * configuration).  Switching drops the handle's captured step graphs. */

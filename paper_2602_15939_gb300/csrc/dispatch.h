@@ -7,7 +7,7 @@
 namespace pic {
 
 struct KernelSet {
-    const void* tile[4];  // one per TILE_VARIANTS entry (threads per CTA, current copies)
+    const void* tile[6];  // one per TILE_VARIANTS entry
     const void* loose;
 };
 

@@ -930,20 +930,28 @@ constexpr long long TMA_WAIT_LIMIT = 1ll << 24;
 // which mixes the cells within warps over a few steps; they skip zero
 // contributions per lane instead.  Particle states and FP32 currents are the
 // same in all variants (exact integer sums).
-struct TileVariant { int nt, stable, min_blocks; };
-constexpr int N_TILE_VARIANTS = 4;
-constexpr TileVariant TILE_VARIANTS[N_TILE_VARIANTS] = {{256, 0, 3}, {512, 0, 2}, {512, 1, 2}, {256, 1, 3}};
+//
+// jc = 2: two copies of the shared current box, lane parity choosing the
+// copy (the second offset by 16 banks), which halves the groups of lanes
+// adding to one word when a warp's particles share a cell; the flush sums
+// the copies.
+struct TileVariant { int nt, stable, jc; };
+constexpr int N_TILE_VARIANTS = 6;
+constexpr TileVariant TILE_VARIANTS[N_TILE_VARIANTS] = {{256, 0, 1}, {512, 0, 1}, {512, 1, 1},
+                                                        {256, 1, 1}, {256, 0, 2}, {256, 1, 2}};
 
 // Dynamic shared memory: E box, B box (each 128-byte aligned, the TMA
 // destinations), the J box (int32 for FP32, double for FP64), the mbarrier,
 // small counters, and for stable variants two buffers of per-warp stayer
 // counts.
-template <class T, int G, int NT, int STABLE> struct SmemLayout {
+template <class T, int G, int NT, int STABLE, int JC> struct SmemLayout {
     static constexpr int FB = TileDims<G>::FB, JB = TileDims<G>::JB;
     static constexpr int QCAP = 64;  // entries of a warp's crossing-particle queue
+    // copy stride in words: a multiple of 32 plus 16 (the second copy is 16 banks over)
+    static constexpr int JCS = JC == 1 ? 3 * JB : ((3 * JB + 31) / 32) * 32 + 16;
     static constexpr size_t off_B = ((size_t)3 * FB * sizeof(T) + 127) & ~(size_t)127;
     static constexpr size_t off_J = (off_B + (size_t)3 * FB * sizeof(T) + 127) & ~(size_t)127;
-    static constexpr size_t off_q = (off_J + (size_t)3 * JB * sizeof(T) + 15) & ~(size_t)15;
+    static constexpr size_t off_q = (off_J + (size_t)JC * JCS * sizeof(T) + 15) & ~(size_t)15;
     static constexpr size_t off_qc = off_q + (size_t)(NT / 32) * QCAP * 6 * sizeof(T);
     static constexpr size_t off_bar = (off_qc + (size_t)(NT / 32) * QCAP * 4 + 15) & ~(size_t)15;
     static constexpr size_t off_wc = off_bar + 16 + 4 * (MAXSP + 2);
@@ -952,7 +960,7 @@ template <class T, int G, int NT, int STABLE> struct SmemLayout {
 
 // The fused particle step for one tile (see the file header).  NT threads per
 // CTA; STABLE: order-preserving stayer write and unconditional adds (above).
-template <class T, int G, int ORD, int PUSH, int ESC, int NT, int STABLE>
+template <class T, int G, int ORD, int PUSH, int ESC, int NT, int STABLE, int JC>
 __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (NT == 512 ? 2 : 3)) tile_kernel(const __grid_constant__ CUtensorMap tmE,
                                                    const __grid_constant__ CUtensorMap tmB, Grid g, Tiling tl,
                                                    StepP P0, SpecPack<T> SP, JWord<T>* __restrict__ J,
@@ -960,7 +968,7 @@ __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (NT == 512 ? 2 : 3)) tile
     using GT = GeomT<G>;
     constexpr bool LEAKY = (ESC == ESC_DISP);
     using D = TileDims<G>;
-    using L = SmemLayout<T, G, NT, STABLE>;
+    using L = SmemLayout<T, G, NT, STABLE, JC>;
     constexpr int NW = NT / 32;
     using JW = JWord<T>;
     const StepP P = with_ctx(P0, ctx);
@@ -991,7 +999,7 @@ __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (NT == 512 ? 2 : 3)) tile
         tma_load_4d(sE, &tmE, xs, ys, zs, 0, bar);
         tma_load_4d(sB, &tmB, xs, ys, zs, 0, bar);
     }
-    for (int i = tid; i < 3 * L::JB; i += NT) sJ[i] = JW(0);
+    for (int i = tid; i < JC * L::JCS; i += NT) sJ[i] = JW(0);
     if (tid < MAXSP) s_cnt[tid] = 0;
     if (tid == 0) s_ok[0] = mbar_wait_bounded(bar, 0, TMA_WAIT_LIMIT) ? 1 : 0;
     __syncthreads();
@@ -1001,7 +1009,7 @@ __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (NT == 512 ? 2 : 3)) tile
     }
 
     const SmemFields<T, G> fa{sE, sB};
-    const SmemJ<T, G> ja(sJ);
+    const SmemJ<T, G> ja(sJ + (lane % JC) * L::JCS);
     using FA = SmemFields<T, G>;
     using JA = SmemJ<T, G>;
     const T vscale = sizeof(T) == 4 ? T(P.fx_scale) : T(1);
@@ -1123,7 +1131,8 @@ __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (NT == 512 ? 2 : 3)) tile
     // the result does not depend on the order tiles finish in): padded index
     // of local point (a,b,c) is (t0x + a, t0y + b, t0z + c)
     for (int idx = tid; idx < 3 * L::JB; idx += NT) {
-        const JW v = sJ[idx];
+        JW v = sJ[idx];
+        if (JC == 2) v += sJ[L::JCS + idx];  // FP32: exact mod 2^32
         if (v == JW(0)) continue;
         const int comp = idx / L::JB;
         const int r = idx - comp * L::JB;

@@ -65,16 +65,18 @@ struct Prof {
 constexpr size_t MAX_SMEM = 227 * 1024;
 
 template <class T, int G, int V> static size_t smem_v() {
-    return SmemLayout<T, G, TILE_VARIANTS[V].nt, TILE_VARIANTS[V].stable>::bytes;
+    return SmemLayout<T, G, TILE_VARIANTS[V].nt, TILE_VARIANTS[V].stable, TILE_VARIANTS[V].jc>::bytes;
 }
 
 template <class T, int G> static size_t tile_smem_bytes_t(int v) {
-    static_assert(N_TILE_VARIANTS == 4, "one entry per tile variant");
+    static_assert(N_TILE_VARIANTS == 6, "one entry per tile variant");
     switch (v) {
         case 0: return smem_v<T, G, 0>();
         case 1: return smem_v<T, G, 1>();
         case 2: return smem_v<T, G, 2>();
-        default: return smem_v<T, G, 3>();
+        case 3: return smem_v<T, G, 3>();
+        case 4: return smem_v<T, G, 4>();
+        default: return smem_v<T, G, 5>();
     }
 }
 
@@ -1233,10 +1235,11 @@ pic_status pic_get_profile(pic_handle* h, pic_profile* out) {
 
 int pic_kernel_variant_count(void) { return N_TILE_VARIANTS; }
 
-pic_status pic_kernel_variant_info(int32_t k, int32_t* threads_per_cta, int32_t* stable) {
+pic_status pic_kernel_variant_info(int32_t k, int32_t* threads_per_cta, int32_t* stable, int32_t* copies) {
     if (k < 1 || k > N_TILE_VARIANTS) return fail(nullptr, PIC_ERR_ARG, "kernel variant %d out of range", (int)k);
     if (threads_per_cta) *threads_per_cta = TILE_VARIANTS[k - 1].nt;
     if (stable) *stable = TILE_VARIANTS[k - 1].stable;
+    if (copies) *copies = TILE_VARIANTS[k - 1].jc;
     return PIC_OK;
 }
 

@@ -114,7 +114,7 @@ _SIGS = {
     "pic_get_profile": (C.c_int, [_H, C.POINTER(pic_profile)]),
     "pic_reset_profile": (C.c_int, [_H]),
     "pic_kernel_variant_count": (C.c_int, []),
-    "pic_kernel_variant_info": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "pic_kernel_variant_info": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pic_get_kernel_variant": (C.c_int, [_H, C.POINTER(C.c_int32)]),
     "pic_set_kernel_variant": (C.c_int, [_H, C.c_int32]),
     "pic_autotune": (C.c_int, [_H, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -297,10 +297,11 @@ def pic_kernel_variant_count() -> int:
 
 
 def pic_kernel_variant_info(k: int):
-    """(threads per CTA, stable stayer order 0/1) of particle-kernel variant k (1-based)."""
-    nt, jc = C.c_int32(), C.c_int32()
-    _check(None, lib().pic_kernel_variant_info(k, C.byref(nt), C.byref(jc)))
-    return nt.value, jc.value
+    """(threads per CTA, stable stayer order 0/1, current-box copies) of
+    particle-kernel variant k (1-based)."""
+    nt, st, jc = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(None, lib().pic_kernel_variant_info(k, C.byref(nt), C.byref(st), C.byref(jc)))
+    return nt.value, st.value, jc.value
 
 
 def pic_get_kernel_variant(h) -> int:

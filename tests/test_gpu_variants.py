@@ -141,3 +141,4 @@ def test_autotune_steps_are_ordinary_steps():
         assert np.array_equal(ia, ib) and np.array_equal(xa, xb) and np.array_equal(ua, ub)
     for a, b in zip(fields_ref, fields):
         assert np.array_equal(a, b)
+
