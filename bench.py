@@ -102,15 +102,16 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def stored_traffic(workload):
-    """DRAM bytes per launch of the particle kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+def stored_traffic(workload, variant):
+    """DRAM bytes per launch of the particle kernel (launch variant `variant`)
+    from the committed ncu summary, if it was taken on the current kernel
+    source."""
     p = os.path.join(ROOT, "profiles", f"tile_kernel_{workload}.md")
     if not os.path.exists(p):
         return None
     txt = open(p).read()
     m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
-    m_b = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
+    m_b = re.search(r"dram_bytes_per_launch_full_size\[v%d\]:\s*([0-9.eE+]+)" % variant, txt)
     if not m_hash or not m_b or m_hash.group(1) != kernel_source_hash():
         return None
     return float(m_b.group(1))
@@ -313,7 +314,7 @@ def run_gb300(args):
     es = 8 if w.fp64 else 4
     alg_bytes = npart * bpp + ncell * (6 + 3) * es
     achieved = alg_bytes / (particle_ms / 1e3) / 1e9
-    traffic = stored_traffic(w.name)
+    traffic = stored_traffic(w.name, tune["chosen"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": f"{peak_kind} HBM copy bandwidth",
                 "kernel": "tile_kernel (fused gather+push+deposit+sort)",

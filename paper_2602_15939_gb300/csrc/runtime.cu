@@ -88,10 +88,10 @@ static size_t tile_smem_bytes(bool fp64, int geom, int v) {
 }
 
 // Variant used when the configuration leaves the choice to the library
-// (measured on GB300: 256 threads for 3D FP32 tiles, 512 otherwise;
-// pic_autotune refines it for a given box).
+// (measured on GB300: 256 threads with two current boxes for 3D FP32 tiles,
+// 512 threads otherwise; pic_autotune refines it for a given box).
 static int default_variant(bool fp64, int geom) {
-    return (!fp64 && geom == 0) ? 0 : 1;
+    return (!fp64 && geom == 0) ? 4 : 1;
 }
 
 struct pic_handle {
