@@ -240,6 +240,28 @@ pic_status pic_set_kernel_variant(pic_handle *h, int32_t k);
 pic_status pic_autotune(pic_handle *h, int32_t trial_steps, int32_t *best, double *ms_per_variant,
                         int64_t *steps_taken);
 
+/* ---- batches: many boxes of one kind stepped together --------------------------
+ * (no counterpart in the paper; the ensembles of independent boxes the method
+ * is run on).  A batch steps n boxes together: each step launches one
+ * persistent particle kernel over the tiles of all boxes (at most
+ * pic_batch_max_boxes_per_launch boxes per launch; more make several
+ * launches), while each box's own field update, current fold and bookkeeping
+ * run as parallel branches; pairs of steps are captured in one CUDA graph and
+ * replayed.  The boxes must share device, precision, geometry (3D, 2D x-y, 2D
+ * x-z), shape order and box type; they may differ in grid, parameters, species
+ * and particle counts.  They must be loaded before pic_batch_create and stay
+ * owned by the caller; until pic_batch_destroy they are stepped only through
+ * the batch (pic_step on a member is PIC_ERR_STATE), may be read back after
+ * pic_batch_synchronize, and must not be destroyed.  The particle kernel of a
+ * batch uses the default launch variant of its kind.  Results are those of
+ * stepping each box alone (FP32: bit-identical). */
+typedef struct pic_batch pic_batch;
+pic_status pic_batch_create(pic_handle *const *boxes, int32_t n, pic_batch **out);
+pic_status pic_batch_step(pic_batch *b, int32_t nsteps);   /* asynchronous */
+pic_status pic_batch_synchronize(pic_batch *b);
+pic_status pic_batch_destroy(pic_batch *b);                 /* synchronizes; members are free again */
+int32_t pic_batch_max_boxes_per_launch(int32_t precision);
+
 /* ---- serving: continuous batching of independent runs ------------------------
  * A run is one box advanced for nsteps from a device Maxwellian load and
  * uniform initial fields.  The server admits queued runs in arrival order as

@@ -9,6 +9,7 @@ namespace pic {
 struct KernelSet {
     const void* tile[6];  // one per TILE_VARIANTS entry
     const void* loose;
+    const void* batch;    // batched launch, variant default_tile_variant
 };
 
 KernelSet lookup_f32_g0(int ord, int push, int esc);

@@ -940,6 +940,11 @@ constexpr int N_TILE_VARIANTS = 6;
 constexpr TileVariant TILE_VARIANTS[N_TILE_VARIANTS] = {{256, 0, 1}, {512, 0, 1}, {512, 1, 1},
                                                         {256, 1, 1}, {256, 0, 2}, {256, 1, 2}};
 
+// Variant (index) used when the choice is left to the library, and the one
+// batched launches use (measured on GB300: 256 threads with two current
+// boxes for 3D FP32 tiles, 512 threads otherwise).
+constexpr int default_tile_variant(bool fp64, int geom) { return (!fp64 && geom == 0) ? 4 : 1; }
+
 // Dynamic shared memory: E box, B box (each 128-byte aligned, the TMA
 // destinations), the J box (int32 for FP32, double for FP64), the mbarrier,
 // small counters, and for stable variants two buffers of per-warp stayer
@@ -958,20 +963,21 @@ template <class T, int G, int NT, int STABLE, int JC> struct SmemLayout {
     static constexpr size_t bytes = off_wc + (STABLE ? 2 * (NT / 32) * 4 : 0);
 };
 
-// The fused particle step for one tile (see the file header).  NT threads per
-// CTA; STABLE: order-preserving stayer write and unconditional adds (above).
+// The fused particle step for tile t of one box (see the file header), made
+// by a CTA of NT threads whose mbarrier is initialised; parity: the phase of
+// its next use.  STABLE: order-preserving stayer write; JC: current copies.
+// Returns false (error bit set) if the tile's fields did not arrive.  Ends
+// with a barrier, so the CTA may go on to another tile.
 template <class T, int G, int ORD, int PUSH, int ESC, int NT, int STABLE, int JC>
-__global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (NT == 512 ? 2 : 3)) tile_kernel(const __grid_constant__ CUtensorMap tmE,
-                                                   const __grid_constant__ CUtensorMap tmB, Grid g, Tiling tl,
-                                                   StepP P0, SpecPack<T> SP, JWord<T>* __restrict__ J,
-                                                   const StepCtx* __restrict__ ctx) {
+__device__ __forceinline__ bool tile_body(const CUtensorMap* tmE, const CUtensorMap* tmB, const Grid& g, const Tiling& tl,
+                                          const StepP& P, const SpecPack<T>& SP, JWord<T>* __restrict__ J, const int t,
+                                          const uint32_t parity) {
     using GT = GeomT<G>;
     constexpr bool LEAKY = (ESC == ESC_DISP);
     using D = TileDims<G>;
     using L = SmemLayout<T, G, NT, STABLE, JC>;
     constexpr int NW = NT / 32;
     using JW = JWord<T>;
-    const StepP P = with_ctx(P0, ctx);
     extern __shared__ __align__(128) unsigned char smem[];
     T* sE = reinterpret_cast<T*>(smem);
     T* sB = reinterpret_cast<T*>(smem + L::off_B);
@@ -981,7 +987,6 @@ __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (NT == 512 ? 2 : 3)) tile
     int* s_ok = s_cnt + MAXSP;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int t = blockIdx.x;
     const int ti = t % tl.ntx, tj = (t / tl.ntx) % tl.nty, tk = t / (tl.ntx * tl.nty);
     const int t0x = ti * D::TX, t0y = tj * D::TY, t0z = tk * D::TZ;
     // padded coordinate of physical t0 - 2 is t0 (GL = 2); TX is a multiple of the TMA x quantum
@@ -990,22 +995,17 @@ __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (NT == 512 ? 2 : 3)) tile
     const int zs = GT::AZ ? t0z : 0;
 
     if (tid == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
         mbar_arrive_expect_tx(bar, (uint32_t)(6 * L::FB * sizeof(T)));
-        tma_load_4d(sE, &tmE, xs, ys, zs, 0, bar);
-        tma_load_4d(sB, &tmB, xs, ys, zs, 0, bar);
+        tma_load_4d(sE, tmE, xs, ys, zs, 0, bar);
+        tma_load_4d(sB, tmB, xs, ys, zs, 0, bar);
     }
     for (int i = tid; i < JC * L::JCS; i += NT) sJ[i] = JW(0);
     if (tid < MAXSP) s_cnt[tid] = 0;
-    if (tid == 0) s_ok[0] = mbar_wait_bounded(bar, 0, TMA_WAIT_LIMIT) ? 1 : 0;
+    if (tid == 0) s_ok[0] = mbar_wait_bounded(bar, parity, TMA_WAIT_LIMIT) ? 1 : 0;
     __syncthreads();
     if (!s_ok[0]) {
         if (tid == 0) atomicOr(P.err, ERRB_TMA_TIMEOUT);
-        return;
+        return false;
     }
 
     const SmemFields<T, G> fa{sE, sB};
@@ -1144,6 +1144,68 @@ __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (NT == 512 ? 2 : 3)) tile
         atomicAdd(J + (long long)comp * g.cstride + ((long long)pk * g.py + pj) * g.px + pi, v);
     }
     if (tid < P.nsp) SP.s[tid].stay_out[t] = s_cnt[tid];
+    __syncthreads();
+    return true;
+}
+
+template <class T, int G, int NT, int STABLE, int JC> __device__ __forceinline__ void init_tile_barrier() {
+    using L = SmemLayout<T, G, NT, STABLE, JC>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (threadIdx.x == 0) {
+        mbar_init(reinterpret_cast<uint64_t*>(smem + L::off_bar), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+// One box: one CTA per tile.
+template <class T, int G, int ORD, int PUSH, int ESC, int NT, int STABLE, int JC>
+__global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (NT == 512 ? 2 : 3)) tile_kernel(const __grid_constant__ CUtensorMap tmE,
+                                                   const __grid_constant__ CUtensorMap tmB, Grid g, Tiling tl,
+                                                   StepP P0, SpecPack<T> SP, JWord<T>* __restrict__ J,
+                                                   const StepCtx* __restrict__ ctx) {
+    init_tile_barrier<T, G, NT, STABLE, JC>();
+    const StepP P = with_ctx(P0, ctx);
+    tile_body<T, G, ORD, PUSH, ESC, NT, STABLE, JC>(&tmE, &tmB, g, tl, P, SP, J, blockIdx.x, 0u);
+}
+
+// A batch of boxes of one kind (precision, geometry, order, pusher, escape
+// rule) in one persistent launch: the tiles of all boxes form one work list,
+// box b owning items [first[b], first[b+1]); CTA k takes items k, k + grid,
+// ...  The boxes' descriptors, tensor maps included, are kernel parameters.
+template <class T> struct BoxDesc {
+    CUtensorMap tmE, tmB;
+    Grid g;
+    Tiling tl;
+    StepP P0;
+    SpecPack<T> SP;
+    JWord<T>* J;
+    const StepCtx* ctx;
+};
+constexpr int BATCH_PARAM_BYTES = 32000;  // kernel parameters allow 32,764 bytes
+template <class T> struct BatchArgs {
+    static constexpr int MAXB = (BATCH_PARAM_BYTES - 64) / (int)sizeof(BoxDesc<T>);
+    BoxDesc<T> box[MAXB];
+    int first[MAXB + 1];
+    int nbox;
+};
+
+template <class T, int G, int ORD, int PUSH, int ESC, int NT, int STABLE, int JC>
+__global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (NT == 512 ? 2 : 3)) batch_tile_kernel(
+    const __grid_constant__ BatchArgs<T> A) {
+    init_tile_barrier<T, G, NT, STABLE, JC>();
+    uint32_t parity = 0;
+    int b = 0;
+    const int nwork = A.first[A.nbox];
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        while (w >= A.first[b + 1]) ++b;  // items are visited in increasing order
+        const BoxDesc<T>& B = A.box[b];
+        const StepP P = with_ctx(B.P0, B.ctx);
+        if (!tile_body<T, G, ORD, PUSH, ESC, NT, STABLE, JC>(&B.tmE, &B.tmB, B.g, B.tl, P, B.SP, B.J, w - A.first[b],
+                                                              parity))
+            return;
+        parity ^= 1;
+    }
 }
 
 // Loose particles: the same per-particle step with fields read from global

@@ -88,11 +88,8 @@ static size_t tile_smem_bytes(bool fp64, int geom, int v) {
 }
 
 // Variant used when the configuration leaves the choice to the library
-// (measured on GB300: 256 threads with two current boxes for 3D FP32 tiles,
-// 512 threads otherwise; pic_autotune refines it for a given box).
-static int default_variant(bool fp64, int geom) {
-    return (!fp64 && geom == 0) ? 4 : 1;
-}
+// (pic_autotune refines it for a given box).
+static int default_variant(bool fp64, int geom) { return default_tile_variant(fp64, geom); }
 
 struct pic_handle {
     pic_config cfg;
@@ -135,6 +132,7 @@ struct pic_handle {
     CUtensorMap tmB;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    bool batched = false;  // stepped by a pic_batch; pic_step refuses
     int buf = 0;  // particle buffer holding the current state
     long long step = 0;
     DevSpecies sp[PIC_MAX_SPECIES];
@@ -361,18 +359,13 @@ template <class T> static PView<T> view_of(void* const a[11]) {
 
 // ---- the step -----------------------------------------------------------------------------
 
-template <class T, int G> static pic_status step_t(pic_handle* h) {
+// The step's parameters for particle buffer b (input) -> 1 - b (output):
+// the StepP scalars (the time-dependent ones come from the device context)
+// and the per-species buffer views.  Returns the particle count.
+template <class T> static long long step_params(pic_handle* h, int b, StepP& P, SpecPack<T>& SP) {
     const Grid& g = h->g;
     const pic_config& cf = h->cfg;
-    const int b = h->buf, o = 1 - b;
-    // per-step scalars (step index, shearing shifts, expansion factors, curl
-    // coefficients) are computed on the device from its step counter
-    ctx_kernel<<<1, 1, 0, h->stream>>>(h->ctx, h->cc);
-    h->prof.launches++;
-    if (h->fp64) CK(cudaMemsetAsync(h->J, 0, (size_t)3 * g.cstride * h->esz, h->stream));
-    else CK(cudaMemsetAsync(h->Jint, 0, (size_t)3 * g.cstride * sizeof(int), h->stream));
-
-    StepP P;
+    const int o = 1 - b;
     memset(&P, 0, sizeof(P));
     P.c = cf.c;
     P.step = h->step;
@@ -406,7 +399,6 @@ template <class T, int G> static pic_status step_t(pic_handle* h) {
     P.err = h->err;
     P.counters = h->counters;
 
-    SpecPack<T> SP;
     memset(&SP, 0, sizeof(SP));
     int nsp = 0;
     long long nparticles = 0;
@@ -454,19 +446,36 @@ template <class T, int G> static pic_status step_t(pic_handle* h) {
         P.fx_unit = 1.0 / (double)P.fx_scale;
     }
 
-    if (nsp > 0) {
+    return nparticles;
+}
+
+// Start of a step: the device step context, and a zero current.
+static pic_status pre_particle(pic_handle* h) {
+    const Grid& g = h->g;
+    // per-step scalars (step index, shearing shifts, expansion factors, curl
+    // coefficients) are computed on the device from its step counter
+    ctx_kernel<<<1, 1, 0, h->stream>>>(h->ctx, h->cc);
+    h->prof.launches++;
+    if (h->fp64) CK(cudaMemsetAsync(h->J, 0, (size_t)3 * g.cstride * h->esz, h->stream));
+    else CK(cudaMemsetAsync(h->Jint, 0, (size_t)3 * g.cstride * sizeof(int), h->stream));
+    return PIC_OK;
+}
+
+// Rest of a step after the tile kernel: loose particles, counter bookkeeping,
+// the current's conversion and guard fold, the field update; then the buffers
+// flip and the step count advances.
+template <class T, int G> static pic_status post_particle_t(pic_handle* h, const StepP& P, const SpecPack<T>& SP) {
+    const Grid& g = h->g;
+    const pic_config& cf = h->cfg;
+    const int b = h->buf, o = 1 - b;
+    if (P.nsp > 0) {
         prof_begin(h);
         void* Jp = h->fp64 ? h->J : (void*)h->Jint;
-        void* args[] = {&h->tmE, &h->tmB, (void*)&g, &h->tl, &P, &SP, &Jp, &h->ctx};
-        CK(cudaLaunchKernel(h->tile_fn, dim3(h->tl.ntiles), dim3(h->tile_threads), args, h->smem_bytes, h->stream));
-        h->prof.launches++;
-        h->prof.particle_launches++;
-        h->prof.particle_steps += nparticles;
-        prof_end(h, 0);
-        prof_begin(h);
         const T* Ep = (const T*)h->E;
         const T* Bp = (const T*)h->B;
-        void* largs[] = {(void*)&g, &h->tl, &P, &SP, &Ep, &Bp, &Jp, &h->ctx};
+        StepP Pc = P;
+        SpecPack<T> SPc = SP;
+        void* largs[] = {(void*)&g, &h->tl, &Pc, &SPc, &Ep, &Bp, &Jp, &h->ctx};
         CK(cudaLaunchKernel(h->ks.loose, dim3(152), dim3(TPB), largs, 0, h->stream));
         h->prof.launches++;
         for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
@@ -478,7 +487,6 @@ template <class T, int G> static pic_status step_t(pic_handle* h) {
         }
         prof_end(h, 1);
     }
-
     prof_begin(h);
     if (!h->fp64) {
         fixed_to_float_kernel<<<grid_blocks(3ll * g.cstride), NTHR, 0, h->stream>>>(3ll * g.cstride, h->Jint, (float*)h->J,
@@ -498,6 +506,25 @@ template <class T, int G> static pic_status step_t(pic_handle* h) {
     h->buf = o;
     h->step += 1;
     return PIC_OK;
+}
+
+template <class T, int G> static pic_status step_t(pic_handle* h) {
+    pic_status st = pre_particle(h);
+    if (st != PIC_OK) return st;
+    StepP P;
+    SpecPack<T> SP;
+    const long long nparticles = step_params<T>(h, h->buf, P, SP);
+    if (P.nsp > 0) {
+        prof_begin(h);
+        void* Jp = h->fp64 ? h->J : (void*)h->Jint;
+        void* args[] = {&h->tmE, &h->tmB, (void*)&h->g, &h->tl, &P, &SP, &Jp, &h->ctx};
+        CK(cudaLaunchKernel(h->tile_fn, dim3(h->tl.ntiles), dim3(h->tile_threads), args, h->smem_bytes, h->stream));
+        h->prof.launches++;
+        h->prof.particle_launches++;
+        h->prof.particle_steps += nparticles;
+        prof_end(h, 0);
+    }
+    return post_particle_t<T, G>(h, P, SP);
 }
 
 // ---- loading / read-back ------------------------------------------------------------------
@@ -1108,6 +1135,7 @@ pic_status pic_set_step(pic_handle* h, int64_t step) {
 
 pic_status pic_step(pic_handle* h, int nsteps) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    if (h->batched) return fail(h, PIC_ERR_STATE, "the box is stepped by a batch");
     cudaSetDevice(h->cfg.device);
     if (nsteps < 0) return fail(h, PIC_ERR_ARG, "nsteps must be >= 0");
     while (nsteps > 0) {
@@ -1339,6 +1367,307 @@ pic_status pic_reset_profile(pic_handle* h) {
     h->prof.ms[0] = h->prof.ms[1] = h->prof.ms[2] = 0.0;
     h->prof.launches = h->prof.particle_launches = h->prof.particle_steps = 0;
     return PIC_OK;
+}
+
+
+// ---- batches: many boxes of one kind, one persistent particle kernel per step ----------------
+
+}  // extern "C"
+
+struct pic_batch {
+    std::vector<pic_handle*> box;
+    std::vector<cudaStream_t> home;  // the boxes' streams, given back at destroy
+    cudaStream_t stream = nullptr;   // the batch's stream
+    std::vector<cudaStream_t> side;  // box i runs its own kernels on side[i % side.size()]
+    std::vector<cudaEvent_t> ev;     // fork / join events: one per side stream, plus the fork
+    int device = 0;
+    bool fp64 = false;
+    int geom = 0;
+    const void* kern = nullptr;
+    int nt = 256;
+    size_t smem = 0;
+    int max_grid = 0;  // resident CTAs of the batched kernel on the device
+    size_t args_bytes = 0;
+    // per phase (parity of the step relative to creation): one parameter image per launch
+    std::vector<std::vector<unsigned char>> args[2];
+    std::vector<int> nwork[2];
+    int phase = 0;
+    bool graphs_on = true;
+    bool graph_ok[2] = {false, false};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+thread_local std::string g_batch_error;
+
+pic_status batch_fail(pic_status st, const char* msg) {
+    g_batch_error = msg;
+    pic_internal_set_global_error(msg);
+    return st;
+}
+
+template <class T, int G> pic_status batch_build_t(pic_batch* B) {
+    using A_t = BatchArgs<T>;
+    const int n = (int)B->box.size();
+    B->args_bytes = sizeof(A_t);
+    for (int ph = 0; ph < 2; ++ph) {
+        B->args[ph].clear();
+        B->nwork[ph].clear();
+        for (int g0 = 0; g0 < n; g0 += A_t::MAXB) {
+            const int k = std::min(A_t::MAXB, n - g0);
+            std::vector<unsigned char> img(sizeof(A_t), 0);
+            A_t* A = reinterpret_cast<A_t*>(img.data());
+            A->nbox = k;
+            A->first[0] = 0;
+            for (int j = 0; j < k; ++j) {
+                pic_handle* h = B->box[g0 + j];
+                BoxDesc<T>& D = A->box[j];
+                D.tmE = h->tmE;
+                D.tmB = h->tmB;
+                D.g = h->g;
+                D.tl = h->tl;
+                step_params<T>(h, ph == 0 ? h->buf : 1 - h->buf, D.P0, D.SP);
+                D.J = h->fp64 ? (JWord<T>*)h->J : (JWord<T>*)(void*)h->Jint;
+                D.ctx = h->ctx;
+                A->first[j + 1] = A->first[j] + h->tl.ntiles;
+            }
+            B->nwork[ph].push_back(A->first[k]);
+            B->args[ph].push_back(std::move(img));
+        }
+    }
+    return PIC_OK;
+}
+
+// Fork: every side stream waits for the batch stream; join: the reverse.
+pic_status batch_fork(pic_batch* B) {
+    const size_t K = B->side.size();
+    if (cudaEventRecord(B->ev[K], B->stream) != cudaSuccess) return batch_fail(PIC_ERR_CUDA, "event record failed");
+    for (size_t k = 0; k < K; ++k)
+        if (cudaStreamWaitEvent(B->side[k], B->ev[K], 0) != cudaSuccess) return batch_fail(PIC_ERR_CUDA, "stream wait failed");
+    return PIC_OK;
+}
+
+pic_status batch_join(pic_batch* B) {
+    for (size_t k = 0; k < B->side.size(); ++k) {
+        if (cudaEventRecord(B->ev[k], B->side[k]) != cudaSuccess) return batch_fail(PIC_ERR_CUDA, "event record failed");
+        if (cudaStreamWaitEvent(B->stream, B->ev[k], 0) != cudaSuccess) return batch_fail(PIC_ERR_CUDA, "stream wait failed");
+    }
+    return PIC_OK;
+}
+
+template <class T, int G> pic_status batch_step_t(pic_batch* B) {
+    using A_t = BatchArgs<T>;
+    const int ph = B->phase;
+    pic_status st = batch_fork(B);
+    for (size_t i = 0; i < B->box.size() && st == PIC_OK; ++i) st = pre_particle(B->box[i]);
+    if (st == PIC_OK) st = batch_join(B);
+    if (st != PIC_OK) return st;
+    for (size_t gi = 0; gi < B->args[ph].size(); ++gi) {
+        const int grid = std::max(1, std::min(B->nwork[ph][gi], B->max_grid));
+        void* a[] = {B->args[ph][gi].data()};
+        if (cudaLaunchKernel(B->kern, dim3(grid), dim3(B->nt), a, B->smem, B->stream) != cudaSuccess)
+            return batch_fail(PIC_ERR_CUDA, "batched particle kernel launch failed");
+    }
+    st = batch_fork(B);
+    for (size_t i = 0; i < B->box.size() && st == PIC_OK; ++i) {
+        const A_t* A = reinterpret_cast<const A_t*>(B->args[ph][i / A_t::MAXB].data());
+        const BoxDesc<T>& D = A->box[i % A_t::MAXB];
+        st = post_particle_t<T, G>(B->box[i], D.P0, D.SP);
+    }
+    if (st == PIC_OK) st = batch_join(B);
+    if (st != PIC_OK) return st;
+    B->phase ^= 1;
+    return PIC_OK;
+}
+
+#define BDISPATCH(B, FN, ...)                                                      \
+    ((B)->fp64 ? ((B)->geom == 0   ? FN<double, 0>(__VA_ARGS__)                  \
+                  : (B)->geom == 1 ? FN<double, 1>(__VA_ARGS__)                  \
+                                   : FN<double, 2>(__VA_ARGS__))                 \
+               : ((B)->geom == 0   ? FN<float, 0>(__VA_ARGS__)                   \
+                  : (B)->geom == 1 ? FN<float, 1>(__VA_ARGS__)                   \
+                                   : FN<float, 2>(__VA_ARGS__)))
+
+void batch_drop_graphs(pic_batch* B) {
+    for (int p = 0; p < 2; ++p) {
+        if (B->gexec[p]) cudaGraphExecDestroy(B->gexec[p]);
+        B->gexec[p] = nullptr;
+        B->graph_ok[p] = false;
+    }
+}
+
+// Capture two steps from the current phase into one graph (the boxes' state
+// is put back: capturing runs nothing).
+pic_status batch_capture(pic_batch* B) {
+    const int ph0 = B->phase;
+    std::vector<int> buf0;
+    std::vector<long long> step0, l0;
+    for (pic_handle* h : B->box) {
+        buf0.push_back(h->buf);
+        step0.push_back(h->step);
+        l0.push_back(h->prof.launches);
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        B->graphs_on = false;
+        return PIC_OK;
+    }
+    pic_status st = BDISPATCH(B, batch_step_t, B);
+    if (st == PIC_OK) st = BDISPATCH(B, batch_step_t, B);
+    cudaError_t e = cudaStreamEndCapture(B->stream, &graph);
+    B->phase = ph0;
+    for (size_t i = 0; i < B->box.size(); ++i) {
+        B->box[i]->buf = buf0[i];
+        B->box[i]->step = step0[i];
+        B->box[i]->prof.launches = l0[i];
+    }
+    if (st != PIC_OK || e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        B->graphs_on = false;
+        return st;
+    }
+    e = cudaGraphInstantiate(&B->gexec[ph0], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        B->gexec[ph0] = nullptr;
+        B->graphs_on = false;
+        return PIC_OK;
+    }
+    B->graph_ok[ph0] = true;
+    return PIC_OK;
+}
+
+void batch_release(pic_batch* B) {
+    if (B->stream) cudaStreamSynchronize(B->stream);
+    for (size_t i = 0; i < B->box.size(); ++i) {
+        B->box[i]->stream = B->home[i];
+        B->box[i]->batched = false;
+    }
+    batch_drop_graphs(B);
+    for (cudaEvent_t e : B->ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t s : B->side)
+        if (s) cudaStreamDestroy(s);
+    if (B->stream) cudaStreamDestroy(B->stream);
+    delete B;
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_batch_create(pic_handle* const* boxes, int32_t n, pic_batch** out) {
+    if (!out) return batch_fail(PIC_ERR_ARG, "pic_batch_create: out is NULL");
+    *out = nullptr;
+    if (!boxes || n < 1) return batch_fail(PIC_ERR_ARG, "pic_batch_create: no boxes");
+    pic_handle* h0 = boxes[0];
+    for (int i = 0; i < n; ++i) {
+        pic_handle* h = boxes[i];
+        if (!h) return batch_fail(PIC_ERR_ARG, "pic_batch_create: NULL box");
+        if (h->batched) return batch_fail(PIC_ERR_STATE, "pic_batch_create: a box is already in a batch");
+        for (int j = 0; j < i; ++j)
+            if (boxes[j] == h) return batch_fail(PIC_ERR_ARG, "pic_batch_create: a box appears twice");
+        if (h->cfg.device != h0->cfg.device || h->fp64 != h0->fp64 || h->geom != h0->geom ||
+            h->cfg.shape_order != h0->cfg.shape_order || h->push != h0->push || h->esc != h0->esc)
+            return batch_fail(PIC_ERR_ARG,
+                              "pic_batch_create: boxes differ in device, precision, geometry, shape order or box type");
+        bool any = false;
+        for (int s = 0; s < PIC_MAX_SPECIES; ++s) any |= h->sp[s].loaded;
+        if (!any) return batch_fail(PIC_ERR_STATE, "pic_batch_create: a box has no particles");
+    }
+    cudaSetDevice(h0->cfg.device);
+    pic_batch* B = new pic_batch();
+    B->device = h0->cfg.device;
+    B->fp64 = h0->fp64;
+    B->geom = h0->geom;
+    B->kern = h0->ks.batch;
+    const int v = default_tile_variant(B->fp64, B->geom);
+    B->nt = TILE_VARIANTS[v].nt;
+    B->smem = tile_smem_bytes(B->fp64, B->geom, v);
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B->device);
+    if (cudaFuncSetAttribute(B->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, B->kern, B->nt, B->smem) != cudaSuccess || per_sm < 1) {
+        delete B;
+        return batch_fail(PIC_ERR_CUDA, "pic_batch_create: the batched kernel cannot be launched");
+    }
+    B->max_grid = sms * per_sm;
+    // every box's queued work ends before the batch takes over
+    for (int i = 0; i < n; ++i) cudaStreamSynchronize(boxes[i]->stream);
+    const int K = std::min(n, 8);
+    bool ok = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) == cudaSuccess;
+    B->side.assign(K, nullptr);
+    B->ev.assign(K + 1, nullptr);
+    for (int k = 0; k < K && ok; ++k) ok = cudaStreamCreateWithFlags(&B->side[k], cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k <= K && ok; ++k) ok = cudaEventCreateWithFlags(&B->ev[k], cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < n; ++i) {
+        B->box.push_back(boxes[i]);
+        B->home.push_back(boxes[i]->stream);
+    }
+    if (!ok) {
+        batch_release(B);
+        return batch_fail(PIC_ERR_CUDA, "pic_batch_create: stream or event creation failed");
+    }
+    for (int i = 0; i < n; ++i) {
+        boxes[i]->stream = B->side[i % K];
+        boxes[i]->batched = true;
+    }
+    pic_status st = BDISPATCH(B, batch_build_t, B);
+    if (st != PIC_OK) {
+        batch_release(B);
+        return st;
+    }
+    if (const char* e = getenv("PIC_NO_GRAPHS")) B->graphs_on = atoi(e) == 0;
+    *out = B;
+    return PIC_OK;
+}
+
+pic_status pic_batch_step(pic_batch* B, int32_t nsteps) {
+    if (!B) return batch_fail(PIC_ERR_ARG, "pic_batch_step: batch is NULL");
+    if (nsteps < 0) return batch_fail(PIC_ERR_ARG, "pic_batch_step: nsteps must be >= 0");
+    cudaSetDevice(B->device);
+    while (nsteps > 0) {
+        if (B->graphs_on && nsteps >= 2) {
+            const int ph = B->phase;
+            if (!B->graph_ok[ph]) {
+                pic_status st = batch_capture(B);
+                if (st != PIC_OK) return st;
+            }
+            if (B->graph_ok[ph]) {
+                if (cudaGraphLaunch(B->gexec[ph], B->stream) != cudaSuccess)
+                    return batch_fail(PIC_ERR_CUDA, "pic_batch_step: graph launch failed");
+                for (pic_handle* h : B->box) h->step += 2;  // two buffer flips: buf unchanged
+                nsteps -= 2;
+                continue;
+            }
+        }
+        pic_status st = BDISPATCH(B, batch_step_t, B);
+        if (st != PIC_OK) return st;
+        nsteps -= 1;
+    }
+    return PIC_OK;
+}
+
+pic_status pic_batch_synchronize(pic_batch* B) {
+    if (!B) return batch_fail(PIC_ERR_ARG, "pic_batch_synchronize: batch is NULL");
+    cudaSetDevice(B->device);
+    if (cudaStreamSynchronize(B->stream) != cudaSuccess) return batch_fail(PIC_ERR_CUDA, "pic_batch_synchronize failed");
+    return PIC_OK;
+}
+
+pic_status pic_batch_destroy(pic_batch* B) {
+    if (!B) return PIC_OK;
+    cudaSetDevice(B->device);
+    batch_release(B);
+    return PIC_OK;
+}
+
+int32_t pic_batch_max_boxes_per_launch(int32_t precision) {
+    return precision == PIC_FP64 ? BatchArgs<double>::MAXB : BatchArgs<float>::MAXB;
 }
 
 }  // extern "C"

@@ -117,6 +117,11 @@ _SIGS = {
     "pic_kernel_variant_info": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pic_get_kernel_variant": (C.c_int, [_H, C.POINTER(C.c_int32)]),
     "pic_set_kernel_variant": (C.c_int, [_H, C.c_int32]),
+    "pic_batch_create": (C.c_int, [C.POINTER(_H), C.c_int32, C.POINTER(_H)]),
+    "pic_batch_step": (C.c_int, [_H, C.c_int32]),
+    "pic_batch_synchronize": (C.c_int, [_H]),
+    "pic_batch_destroy": (C.c_int, [_H]),
+    "pic_batch_max_boxes_per_launch": (C.c_int32, [C.c_int32]),
     "pic_autotune": (C.c_int, [_H, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "pic_field_energy_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
     "pic_run_footprint": (C.c_int, [C.POINTER(pic_run_spec), C.POINTER(C.c_uint64)]),
@@ -323,6 +328,45 @@ def pic_autotune(h, trial_steps: int = 4):
     ms = (C.c_double * n)()
     _check(h, lib().pic_autotune(h, trial_steps, C.byref(best), ms, C.byref(taken)))
     return best.value, [v if v >= 0 else None for v in ms], taken.value
+
+
+class Batch:
+    """Boxes of one kind stepped together (pic_batch_*): one persistent
+    particle kernel per step over all their tiles, graph-replayed."""
+
+    def __init__(self, boxes):
+        self.boxes = list(boxes)
+        arr = (_H * len(self.boxes))(*[b.h for b in self.boxes])
+        out = _H()
+        _check(None, lib().pic_batch_create(arr, len(self.boxes), C.byref(out)))
+        self.b = out
+
+    def step(self, n=1):
+        _check(None, lib().pic_batch_step(self.b, n))
+
+    def sync(self):
+        _check(None, lib().pic_batch_synchronize(self.b))
+
+    def close(self):
+        if self.b:
+            lib().pic_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pic_batch_max_boxes_per_launch(precision=None) -> int:
+    return lib().pic_batch_max_boxes_per_launch(PIC_FP32 if precision is None else precision)
 
 
 def pic_field_energy_noalloc(d_field: int, precision: int, n: int, ncomp: int, d_out: int, stream: int | None = None):
