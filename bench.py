@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-runs", type=int, default=64)
     ap.add_argument("--kernel-only", action="store_true", help="warmup + timed steps only (for profiler runs)")
+    ap.add_argument("--batch-legs-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--seed", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--variant", type=int, default=0,
                     help="particle-kernel variant (1-based); 0 = autotune on the box after warm-up")
     return ap.parse_args()
@@ -360,6 +362,7 @@ def run_gb300(args):
 
     if not args.no_serving and not args.kernel_only:
         line["serving"] = run_serving(local, seed=rank, runs=args.serve_runs)
+        line["batched_ensemble"] = batch_legs_subprocess(local, rank)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.kernel_only:
         n_sub = sub_box(w)
@@ -412,6 +415,88 @@ def run_serving(device, seed=0, runs=64):
             "peak_active": int(info.peak_active), "wall_s": wall,
             "sample": "Poisson arrivals (mean gap 2 ms); shearing/expanding/leaky x 2D (32^2-128^2) / 3D (16^3-32^3); "
                       "8-32 ppc/species; 20-100 steps; FP32"}
+
+
+def run_batch_leg(device, steps=20, seed=0, nbox=16, sizes=(32, 48, 64)):
+    """Batched against separate stepping of an ensemble of one kind: nbox 3D
+    expanding boxes with grids drawn from `sizes` (cubes) at 8-32 ppc per
+    species (FP32, quadratic shapes).  Batched: one Batch, one persistent
+    particle kernel per step, graph-replayed.  Separate: each box with its own
+    graphs, either one after another on one stream or all at once on their
+    own streams."""
+    import torch
+
+    from paper_2602_15939_gb300 import pic as P
+    from paper_2602_15939_gb300 import workloads as W
+
+    runs = W.ensemble_of_kind(nbox, box=2, ndim=3, seed=seed, sizes=sizes)
+    npart = sum(2 * r["ppc"] * r["n"][0] * r["n"][1] * r["n"][2] for r in runs)
+    out = {"boxes": len(runs), "particles": npart, "steps": steps,
+           "grids": sorted(set(r["n"][0] for r in runs)),
+           "sample": f"{nbox} x 3D expanding box, {min(sizes)}^3-{max(sizes)}^3, 8-32 ppc/species"}
+
+    def timed(fn, stream):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    s = torch.cuda.Stream()
+    boxes = [W.box_of_run(r, device, s.cuda_stream) for r in runs]
+    for b in boxes:
+        b.step(2)
+    ms = timed(lambda: [b.step(steps) for b in boxes], s)
+    out["separate_one_stream"] = npart * steps / (ms / 1e3)
+    streams = [torch.cuda.Stream() for _ in boxes]
+    for b, st in zip(boxes, streams):
+        P.pic_set_stream(b.h, st.cuda_stream)
+        b.step(2)
+    torch.cuda.synchronize()
+
+    def concurrent():
+        ev = torch.cuda.Event()
+        ev.record(s)
+        for st in streams:
+            st.wait_event(ev)
+        for b in boxes:
+            b.step(steps)
+        for st in streams:
+            e = torch.cuda.Event()
+            e.record(st)
+            s.wait_event(e)
+
+    ms = timed(concurrent, s)
+    out["separate_concurrent_streams"] = npart * steps / (ms / 1e3)
+    with P.Batch(boxes) as bt:
+        bt.step(2)
+        bt.sync()
+        t0 = time.perf_counter()
+        bt.step(steps)
+        bt.sync()
+        ms = 1e3 * (time.perf_counter() - t0)
+    out["batched"] = npart * steps / (ms / 1e3)
+    out["unit"] = UNIT
+    for b in boxes:
+        b.close()
+    return out
+
+
+def batch_legs_subprocess(device, rank):
+    """The batched-ensemble comparison, run in a child process of its own (its
+    own CUDA context), so that nothing it does can affect this run's line."""
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES=os.environ.get("CUDA_VISIBLE_DEVICES", str(device)))
+    cmd = [sys.executable, os.path.abspath(__file__), "--batch-legs-only", "--seed", str(rank)]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, env=env)
+        if r.returncode == 0 and r.stdout.strip():
+            return json.loads(r.stdout.strip().splitlines()[-1])
+        return {"error": f"exit {r.returncode}: {r.stderr.strip()[-300:]}"}
+    except Exception as e:  # a failed comparison leg is reported, not fatal
+        return {"error": repr(e)[:300]}
 
 
 def run_e2e(w, device, stream, steps, rank):
@@ -467,6 +552,17 @@ def run_e2e(w, device, stream, steps, rank):
 
 def main():
     args = parse()
+    if args.batch_legs_only:
+        import torch
+
+        torch.cuda.set_device(0)
+        from paper_2602_15939_gb300 import build as libbuild
+
+        libbuild.build()
+        out = {"medium": run_batch_leg(0, seed=args.seed),
+               "small": run_batch_leg(0, seed=args.seed, nbox=64, sizes=(16, 24, 32))}
+        print(json.dumps(out), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_gb300(args)

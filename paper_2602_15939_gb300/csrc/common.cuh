@@ -30,6 +30,8 @@ enum : int {
     ERRB_LOOSE_OVERFLOW = 4,
     ERRB_BAD_CELL = 8,
     ERRB_J_RANGE = 16,  // a fixed-point current sum reached half its range
+    ERRB_SMEM_ALIGN = 32,  // a TMA destination in shared memory was not 128-byte aligned (copy skipped)
+    ERRB_BATCH = 64,       // a batched launch met an inconsistent work item (skipped)
 };
 
 template <int G> struct GeomT {

@@ -994,6 +994,13 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* tmE, const CUtensor
     const int ys = GT::AY ? t0y : 0;
     const int zs = GT::AZ ? t0z : 0;
 
+    // tensor copies need 128-byte aligned shared destinations: check, and
+    // report instead of copying if the layout ever breaks that
+    if (((smem_u32(sE) | smem_u32(sB)) & 127u) != 0u) {
+        if (tid == 0) atomicOr(P.err, ERRB_SMEM_ALIGN);
+        __syncthreads();
+        return false;
+    }
     if (tid == 0) {
         mbar_arrive_expect_tx(bar, (uint32_t)(6 * L::FB * sizeof(T)));
         tma_load_4d(sE, tmE, xs, ys, zs, 0, bar);
@@ -1171,8 +1178,10 @@ __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (NT == 512 ? 2 : 3)) tile
 
 // A batch of boxes of one kind (precision, geometry, order, pusher, escape
 // rule) in one persistent launch: the tiles of all boxes form one work list,
-// box b owning items [first[b], first[b+1]); CTA k takes items k, k + grid,
-// ...  The boxes' descriptors, tensor maps included, are kernel parameters.
+// box b owning items [first[b], first[b+1]) (boxes in decreasing particles per
+// tile), and every CTA claims its next item from a counter (zero at launch),
+// so CTAs that drew light tiles take more of them.  The boxes' descriptors,
+// tensor maps included, are kernel parameters.
 template <class T> struct BoxDesc {
     CUtensorMap tmE, tmB;
     Grid g;
@@ -1188,21 +1197,43 @@ template <class T> struct BatchArgs {
     BoxDesc<T> box[MAXB];
     int first[MAXB + 1];
     int nbox;
+    int* next;  // work counter of this launch
 };
 
 template <class T, int G, int ORD, int PUSH, int ESC, int NT, int STABLE, int JC>
 __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (NT == 512 ? 2 : 3)) batch_tile_kernel(
     const __grid_constant__ BatchArgs<T> A) {
     init_tile_barrier<T, G, NT, STABLE, JC>();
+    // the claimed item goes through the layout's spare word (no static
+    // shared variable: it would shift the dynamic area the tensor copies
+    // address off its 128-byte alignment)
+    using L = SmemLayout<T, G, NT, STABLE, JC>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    int* s_item = reinterpret_cast<int*>(smem + L::off_bar + 16) + MAXSP + 1;
+    if (A.nbox < 1 || A.nbox > BatchArgs<T>::MAXB || A.next == nullptr) return;
     uint32_t parity = 0;
     int b = 0;
     const int nwork = A.first[A.nbox];
-    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
-        while (w >= A.first[b + 1]) ++b;  // items are visited in increasing order
+    for (;;) {
+        if (threadIdx.x == 0) *s_item = atomicAdd(A.next, 1);
+        __syncthreads();
+        const int w = *s_item;
+        __syncthreads();
+        if (w >= nwork) break;
+        while (b < A.nbox && w >= A.first[b + 1]) ++b;  // a CTA's items increase
+        const int t = b < A.nbox ? w - A.first[b] : -1;
+        if (w < 0 || b >= A.nbox || t < 0 || t >= A.box[b < A.nbox ? b : 0].tl.ntiles) {
+            if (threadIdx.x == 0) atomicOr(A.box[0].P0.err, ERRB_BATCH);
+            break;
+        }
         const BoxDesc<T>& B = A.box[b];
+        // tensor maps must sit on 64-byte boundaries
+        if ((reinterpret_cast<uintptr_t>(&B.tmE) | reinterpret_cast<uintptr_t>(&B.tmB)) & 63u) {
+            if (threadIdx.x == 0) atomicOr(A.box[0].P0.err, ERRB_BATCH);
+            break;
+        }
         const StepP P = with_ctx(B.P0, B.ctx);
-        if (!tile_body<T, G, ORD, PUSH, ESC, NT, STABLE, JC>(&B.tmE, &B.tmB, B.g, B.tl, P, B.SP, B.J, w - A.first[b],
-                                                              parity))
+        if (!tile_body<T, G, ORD, PUSH, ESC, NT, STABLE, JC>(&B.tmE, &B.tmB, B.g, B.tl, P, B.SP, B.J, t, parity))
             return;
         parity ^= 1;
     }

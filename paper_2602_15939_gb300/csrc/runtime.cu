@@ -1078,6 +1078,8 @@ static pic_status check_error_word(pic_handle* h) {
     if (e & ERRB_TMA_TIMEOUT) return fail(h, PIC_ERR_TIMEOUT, "a field-staging wait expired (error word %d)", e);
     if (e & ERRB_NONFINITE) return fail(h, PIC_ERR_NUMERIC, "non-finite particle velocity (error word %d)", e);
     if (e & ERRB_LOOSE_OVERFLOW) return fail(h, PIC_ERR_STATE, "loose-particle list overflowed (error word %d)", e);
+    if (e & ERRB_BATCH) return fail(h, PIC_ERR_STATE, "a batched launch met an inconsistent work item (error word %d)", e);
+    if (e & ERRB_SMEM_ALIGN) return fail(h, PIC_ERR_STATE, "misaligned shared-memory staging area (error word %d)", e);
     if (e & ERRB_J_RANGE)
         return fail(h, PIC_ERR_NUMERIC, "a tile current reached half the fixed-point range (error word %d)", e);
     if (e) return fail(h, PIC_ERR_STATE, "device error word %d", e);
@@ -1391,6 +1393,7 @@ struct pic_batch {
     // per phase (parity of the step relative to creation): one parameter image per launch
     std::vector<std::vector<unsigned char>> args[2];
     std::vector<int> nwork[2];
+    int* counters = nullptr;  // work counters, one per launch
     int phase = 0;
     bool graphs_on = true;
     bool graph_ok[2] = {false, false};
@@ -1411,6 +1414,9 @@ template <class T, int G> pic_status batch_build_t(pic_batch* B) {
     using A_t = BatchArgs<T>;
     const int n = (int)B->box.size();
     B->args_bytes = sizeof(A_t);
+    const int ngroups = (n + A_t::MAXB - 1) / A_t::MAXB;
+    if (cudaMalloc(&B->counters, sizeof(int) * ngroups) != cudaSuccess)
+        return batch_fail(PIC_ERR_OOM, "pic_batch_create: allocation failed");
     for (int ph = 0; ph < 2; ++ph) {
         B->args[ph].clear();
         B->nwork[ph].clear();
@@ -1419,6 +1425,7 @@ template <class T, int G> pic_status batch_build_t(pic_batch* B) {
             std::vector<unsigned char> img(sizeof(A_t), 0);
             A_t* A = reinterpret_cast<A_t*>(img.data());
             A->nbox = k;
+            A->next = B->counters + g0 / A_t::MAXB;
             A->first[0] = 0;
             for (int j = 0; j < k; ++j) {
                 pic_handle* h = B->box[g0 + j];
@@ -1463,12 +1470,19 @@ template <class T, int G> pic_status batch_step_t(pic_batch* B) {
     for (size_t i = 0; i < B->box.size() && st == PIC_OK; ++i) st = pre_particle(B->box[i]);
     if (st == PIC_OK) st = batch_join(B);
     if (st != PIC_OK) return st;
-    for (size_t gi = 0; gi < B->args[ph].size(); ++gi) {
+    // one launch per group of boxes, the groups side by side
+    const size_t ng = B->args[ph].size();
+    if (cudaMemsetAsync(B->counters, 0, sizeof(int) * ng, B->stream) != cudaSuccess)
+        return batch_fail(PIC_ERR_CUDA, "work counter reset failed");
+    if (ng > 1 && (st = batch_fork(B)) != PIC_OK) return st;
+    for (size_t gi = 0; gi < ng; ++gi) {
         const int grid = std::max(1, std::min(B->nwork[ph][gi], B->max_grid));
         void* a[] = {B->args[ph][gi].data()};
-        if (cudaLaunchKernel(B->kern, dim3(grid), dim3(B->nt), a, B->smem, B->stream) != cudaSuccess)
+        cudaStream_t s = ng > 1 ? B->side[gi % B->side.size()] : B->stream;
+        if (cudaLaunchKernel(B->kern, dim3(grid), dim3(B->nt), a, B->smem, s) != cudaSuccess)
             return batch_fail(PIC_ERR_CUDA, "batched particle kernel launch failed");
     }
+    if (ng > 1 && (st = batch_join(B)) != PIC_OK) return st;
     st = batch_fork(B);
     for (size_t i = 0; i < B->box.size() && st == PIC_OK; ++i) {
         const A_t* A = reinterpret_cast<const A_t*>(B->args[ph][i / A_t::MAXB].data());
@@ -1548,6 +1562,7 @@ void batch_release(pic_batch* B) {
         B->box[i]->batched = false;
     }
     batch_drop_graphs(B);
+    if (B->counters) cudaFree(B->counters);
     for (cudaEvent_t e : B->ev)
         if (e) cudaEventDestroy(e);
     for (cudaStream_t s : B->side)
@@ -1598,13 +1613,24 @@ pic_status pic_batch_create(pic_handle* const* boxes, int32_t n, pic_batch** out
     B->max_grid = sms * per_sm;
     // every box's queued work ends before the batch takes over
     for (int i = 0; i < n; ++i) cudaStreamSynchronize(boxes[i]->stream);
-    const int K = std::min(n, 8);
+    int K = std::min(n, 16);  // parallel branches for the boxes' own kernels
+    if (const char* e = getenv("PIC_BATCH_STREAMS")) K = std::max(1, std::min(n, atoi(e)));
     bool ok = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) == cudaSuccess;
     B->side.assign(K, nullptr);
     B->ev.assign(K + 1, nullptr);
     for (int k = 0; k < K && ok; ++k) ok = cudaStreamCreateWithFlags(&B->side[k], cudaStreamNonBlocking) == cudaSuccess;
     for (int k = 0; k <= K && ok; ++k) ok = cudaEventCreateWithFlags(&B->ev[k], cudaEventDisableTiming) == cudaSuccess;
-    for (int i = 0; i < n; ++i) {
+    // heaviest tiles first: boxes in decreasing particles per tile
+    std::vector<int> ord(n);
+    for (int i = 0; i < n; ++i) ord[i] = i;
+    auto per_tile = [&](int i) {
+        long long np = 0;
+        for (int s = 0; s < PIC_MAX_SPECIES; ++s)
+            if (boxes[i]->sp[s].loaded) np += boxes[i]->sp[s].n;
+        return (double)np / boxes[i]->tl.ntiles;
+    };
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return per_tile(a) > per_tile(b); });
+    for (int i : ord) {
         B->box.push_back(boxes[i]);
         B->home.push_back(boxes[i]->stream);
     }
@@ -1613,8 +1639,8 @@ pic_status pic_batch_create(pic_handle* const* boxes, int32_t n, pic_batch** out
         return batch_fail(PIC_ERR_CUDA, "pic_batch_create: stream or event creation failed");
     }
     for (int i = 0; i < n; ++i) {
-        boxes[i]->stream = B->side[i % K];
-        boxes[i]->batched = true;
+        B->box[i]->stream = B->side[i % K];
+        B->box[i]->batched = true;
     }
     pic_status st = BDISPATCH(B, batch_build_t, B);
     if (st != PIC_OK) {

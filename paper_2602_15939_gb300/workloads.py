@@ -310,3 +310,43 @@ def run_spec_of(run):
     cfg = P.make_config(**kw)
     return P.make_run_spec(cfg, run["steps"], run["ppc"], run["theta"], q=(-units.q, units.q), B0=B0,
                            load_seed=run["seed"])
+
+
+def ensemble_of_kind(M, box=2, ndim=3, seed=0, sizes=(32, 48, 64), ppc_range=(8, 32)):
+    """M runs of one kind (box type, dimensionality: a batchable class of the
+    served ensemble) with uneven grids and densities, drawn like
+    served_ensemble's entries; used to compare batched and separate
+    stepping."""
+    r = np.random.default_rng(seed)
+    out = []
+    for k in range(M):
+        m = int(r.choice(sizes))
+        if ndim == 2:
+            plane = 1 if box == 1 else 0
+            n = (m, 1, m) if plane == 1 else (m, m, 1)
+            order = 1
+        else:
+            n, plane, order = (m, m, m), 0, 2
+        out.append(dict(arrival_s=0.0, box=box, ndim=ndim, plane=plane, n=n, order=order,
+                        ppc=int(r.integers(ppc_range[0], ppc_range[1] + 1)), steps=0, c=0.45, skin_depth=5.0,
+                        sigma=0.5, s=float(r.uniform(0.5, 1.8)), Omega0_wp=1e-3,
+                        rate_wp=float(10 ** r.uniform(-5, -3)), t_esc_Lc=float(r.uniform(0.5, 4.0)),
+                        theta={1: 0.1, 2: 0.05, 3: 1.0}[box], seed=int(r.integers(0, 2**31))))
+    return out
+
+
+def box_of_run(run, device=0, stream=None):
+    """A loaded libpic box for one run dict (served_ensemble / ensemble_of_kind)."""
+    from . import pic as P
+
+    spec = run_spec_of(run)
+    cfg = spec.cfg
+    cfg.device = device
+    box = P.Box(cfg)
+    if stream is not None:
+        P.pic_set_stream(box.h, stream)
+    for s in range(spec.nspecies):
+        box.load_maxwellian(s, spec.q[s], spec.m[s], spec.ppc, spec.theta, seed=spec.load_seed + s,
+                            id_base=s * spec.ppc * cfg.nx * cfg.ny * cfg.nz)
+    box.set_uniform_fields(tuple(spec.E0), tuple(spec.B0))
+    return box
