@@ -162,6 +162,7 @@ pic_status pic_load_particles(pic_handle *h, int species, double q, double m, in
  * noise_sigma (cells/step) per component.  ids are assigned 0.. in cell order
  * offset by id_base.  Random numbers come from Philox4x32-10 keyed on
  * (id, seed). */
+/* The load is queued on the handle's stream (the call does not wait for it). */
 pic_status pic_load_maxwellian(pic_handle *h, int species, double q, double m, int ppc,
                                double theta, const double drift[3], double noise_sigma,
                                uint32_t seed, uint32_t id_base);
@@ -210,6 +211,12 @@ pic_status pic_get_fields(pic_handle *h, double *E, double *B, double *J);
 pic_status pic_set_profiling(pic_handle *h, int enable);
 pic_status pic_get_profile(pic_handle *h, pic_profile *out);
 pic_status pic_reset_profile(pic_handle *h);
+
+/* Load the library's particle kernels for one precision on `device` now
+ * rather than at their first use (CUDA loads code lazily: the first box of
+ * each geometry otherwise pays some tens of milliseconds).  The server calls
+ * it for FP32 when it starts. */
+pic_status pic_preload_kernels(int32_t device, int32_t precision);
 
 /* Particle-kernel variants: launch shapes of the fused particle kernel (no
  * counterpart in the paper, which gives no kernel design), numbered

@@ -65,7 +65,8 @@ __global__ void load_scatter_kernel(long long n, const double* __restrict__ x, c
 }
 
 // Device Maxwellian loader: slot r of tile t holds particle r of the tile's
-// cells in order, ppc per cell.  Positions uniform in the cell, momenta
+// cells in order, ppc per cell.  blockIdx.x is the tile; the gridDim.y CTAs
+// of a tile share its particles (small boxes still fill the GPU).  Positions uniform in the cell, momenta
 // Maxwell-Juettner(theta) + drift + Gaussian noise (Box-Muller), all from
 // Philox keyed on (id, seed).
 template <class T, int G>
@@ -79,7 +80,7 @@ __global__ void maxwellian_kernel(Tiling tl, Grid g, int ppc, double theta, doub
     const int ex = min(tl.tx, g.nx - t0x), ey = GT::AY ? min(tl.ty, g.ny - t0y) : 1, ez = GT::AZ ? min(tl.tz, g.nz - t0z) : 1;
     const int ncell = ex * ey * ez;
     const int n = ncell * ppc;
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    for (int r = blockIdx.y * blockDim.x + threadIdx.x; r < n; r += blockDim.x * gridDim.y) {
         int lc = r / ppc, pc = r % ppc;
         int a = lc % ex, b = (lc / ex) % ey, cc = lc / (ex * ey);
         Particle<T> p;
@@ -108,7 +109,7 @@ __global__ void maxwellian_kernel(Tiling tl, Grid g, int ppc, double theta, doub
         p.dr[0] = p.dr[1] = p.dr[2] = T(0);
         store_particle<T, G>(v, (long long)t * tcap + r, has_dr, p);
     }
-    if (threadIdx.x == 0) count[t] = n;
+    if (threadIdx.x == 0 && blockIdx.y == 0) count[t] = n;
 }
 
 // Copy tile t's particles (front and back segments) to double arrays at

@@ -14,6 +14,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -529,6 +531,48 @@ template <class T, int G> static pic_status step_t(pic_handle* h) {
 
 // ---- loading / read-back ------------------------------------------------------------------
 
+// ---- device memory ------------------------------------------------------------------------
+// All device memory of a handle comes from one stream-ordered memory pool per
+// device, allocated and freed on the handle's stream.  The pool keeps up to
+// POOL_KEEP bytes of freed memory for reuse, so the tens of allocations of a
+// short run (a served ensemble admits and retires many) cost microseconds
+// instead of a cudaMalloc each; large boxes still return their memory.
+constexpr uint64_t POOL_KEEP = 8ull << 30;
+
+static cudaMemPool_t lib_pool(int device) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = pools.find(device);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        pool = nullptr;  // fall back to plain allocations
+    } else {
+        uint64_t keep = POOL_KEEP;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    pools[device] = pool;
+    return pool;
+}
+
+static cudaError_t dalloc(pic_handle* h, void** p, size_t bytes) {
+    cudaMemPool_t pool = lib_pool(h->cfg.device);
+    if (!pool) return cudaMalloc(p, bytes);
+    return cudaMallocFromPoolAsync(p, bytes, pool, h->stream);
+}
+
+static void dfree(pic_handle* h, void* p) {
+    if (!p) return;
+    if (lib_pool(h->cfg.device)) cudaFreeAsync(p, h->stream);
+    else cudaFree(p);
+}
+
 static void drop_graphs(pic_handle* h) {
     for (int b = 0; b < 2; ++b) {
         if (h->gexec[b]) cudaGraphExecDestroy(h->gexec[b]);
@@ -544,8 +588,8 @@ static pic_status alloc_species(pic_handle* h, DevSpecies& d, long long tcap) {
     const int nact = h->geom == 0 ? 3 : 2;
     for (int b = 0; b < 2; ++b)
         for (int i = 0; i < 11; ++i) {
-            if (d.arr[b][i]) cudaFree(d.arr[b][i]);
-            if (d.larr[b][i]) cudaFree(d.larr[b][i]);
+            if (d.arr[b][i]) dfree(h, d.arr[b][i]);
+            if (d.larr[b][i]) dfree(h, d.larr[b][i]);
             d.arr[b][i] = d.larr[b][i] = nullptr;
         }
     d.tcap = tcap;
@@ -555,16 +599,16 @@ static pic_status alloc_species(pic_handle* h, DevSpecies& d, long long tcap) {
             bool need = i == 0 || (i >= 1 && i <= nact) || (i >= 4 && i <= 7) || (i >= 8 && leaky);
             if (!need) continue;
             size_t es = (i == 0 || i == 7) ? 4 : h->esz;
-            CK(cudaMalloc(&d.arr[b][i], (size_t)cap * es));
-            CK(cudaMalloc(&d.larr[b][i], (size_t)d.lcap * es));
+            CK(dalloc(h, (void**)&d.arr[b][i], (size_t)cap * es));
+            CK(dalloc(h, (void**)&d.larr[b][i], (size_t)d.lcap * es));
         }
-        if (!d.stay[b]) CK(cudaMalloc(&d.stay[b], sizeof(int) * nt));
-        if (!d.arrv[b]) CK(cudaMalloc(&d.arrv[b], sizeof(int) * nt));
+        if (!d.stay[b]) CK(dalloc(h, (void**)&d.stay[b], sizeof(int) * nt));
+        if (!d.arrv[b]) CK(dalloc(h, (void**)&d.arrv[b], sizeof(int) * nt));
         CK(cudaMemsetAsync(d.stay[b], 0, sizeof(int) * nt, h->stream));
         CK(cudaMemsetAsync(d.arrv[b], 0, sizeof(int) * nt, h->stream));
     }
     // 2D: o[1] of the view is the second active axis; the kernels index o[AY ? 1 : ...]
-    if (!d.lcount) CK(cudaMalloc(&d.lcount, sizeof(int) * 2));
+    if (!d.lcount) CK(dalloc(h, (void**)&d.lcount, sizeof(int) * 2));
     CK(cudaMemsetAsync(d.lcount, 0, sizeof(int) * 2, h->stream));
     return PIC_OK;
 }
@@ -576,8 +620,8 @@ static pic_status load_t(pic_handle* h, int species, long long n, const double* 
     const int nt = h->tl.ntiles;
     int* tile_p = nullptr;
     int* cnt = nullptr;
-    CK(cudaMalloc(&tile_p, sizeof(int) * std::max(1ll, n)));
-    CK(cudaMalloc(&cnt, sizeof(int) * nt));
+    CK(dalloc(h, (void**)&tile_p, sizeof(int) * std::max(1ll, n)));
+    CK(dalloc(h, (void**)&cnt, sizeof(int) * nt));
     CK(cudaMemsetAsync(cnt, 0, sizeof(int) * nt, h->stream));
     if (n > 0) load_bin_kernel<T, G><<<grid_blocks(n), NTHR, 0, h->stream>>>(n, dx, h->tl, h->g, tile_p, cnt);
     std::vector<int> hc(nt);
@@ -590,7 +634,7 @@ static pic_status load_t(pic_handle* h, int species, long long n, const double* 
     tcap = (tcap + 3) & ~3ll;
     d.lcap = std::max(4096ll, n / 32);
     pic_status st = alloc_species(h, d, tcap);
-    if (st != PIC_OK) { cudaFree(tile_p); cudaFree(cnt); return st; }
+    if (st != PIC_OK) { dfree(h, tile_p); dfree(h, cnt); return st; }
     const int b = h->buf;
     CK(cudaMemsetAsync(cnt, 0, sizeof(int) * nt, h->stream));
     if (n > 0)
@@ -599,8 +643,8 @@ static pic_status load_t(pic_handle* h, int species, long long n, const double* 
     CK(cudaMemcpyAsync(d.stay[b], cnt, sizeof(int) * nt, cudaMemcpyDeviceToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     CK(cudaGetLastError());
-    cudaFree(tile_p);
-    cudaFree(cnt);
+    dfree(h, tile_p);
+    dfree(h, cnt);
     d.n = n;
     d.loaded = true;
     return PIC_OK;
@@ -623,7 +667,7 @@ static pic_status compact_t(pic_handle* h, int species, double* dx, double* du, 
     if (acc + lc != d.n)
         return fail(h, PIC_ERR_STATE, "species %d holds %lld particles, expected %lld", species, acc + lc, d.n);
     long long* doff = nullptr;
-    CK(cudaMalloc(&doff, sizeof(long long) * nt));
+    CK(dalloc(h, (void**)&doff, sizeof(long long) * nt));
     CK(cudaMemcpyAsync(doff, off.data(), sizeof(long long) * nt, cudaMemcpyHostToDevice, h->stream));
     const bool hd = h->esc == ESC_DISP;
     compact_kernel<T, G><<<nt, NTHR, 0, h->stream>>>(h->tl, h->g, view_of<T>(d.arr[b]), d.stay[b], d.arrv[b], d.tcap, doff, hd, dx,
@@ -631,7 +675,7 @@ static pic_status compact_t(pic_handle* h, int species, double* dx, double* du, 
     compact_loose_kernel<T, G><<<64, NTHR, 0, h->stream>>>(view_of<T>(d.larr[b]), d.lcount + b, d.lcap, acc, hd, dx, du, did, ddr);
     CK(cudaStreamSynchronize(h->stream));
     CK(cudaGetLastError());
-    cudaFree(doff);
+    dfree(h, doff);
     return PIC_OK;
 }
 
@@ -644,11 +688,11 @@ static pic_status sample_t(pic_handle* h, int species, uint32_t modulus, uint32_
     uint32_t* did = nullptr;
     unsigned long long* dcount = nullptr;
     const size_t m = (size_t)std::max(max_out, 1ll);
-    CK(cudaMalloc(&dx, sizeof(double) * 3 * m));
-    CK(cudaMalloc(&du, sizeof(double) * 3 * m));
-    CK(cudaMalloc(&ddr, sizeof(double) * 3 * m));
-    CK(cudaMalloc(&did, sizeof(uint32_t) * m));
-    CK(cudaMalloc(&dcount, sizeof(unsigned long long)));
+    CK(dalloc(h, (void**)&dx, sizeof(double) * 3 * m));
+    CK(dalloc(h, (void**)&du, sizeof(double) * 3 * m));
+    CK(dalloc(h, (void**)&ddr, sizeof(double) * 3 * m));
+    CK(dalloc(h, (void**)&did, sizeof(uint32_t) * m));
+    CK(dalloc(h, (void**)&dcount, sizeof(unsigned long long)));
     CK(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), h->stream));
     sample_kernel<T, G><<<std::min(h->tl.ntiles + 1, 152 * 8), NTHR, 0, h->stream>>>(
         h->tl, view_of<T>(d.arr[b]), d.stay[b], d.arrv[b], d.tcap, view_of<T>(d.larr[b]), d.lcount + b, d.lcap, modulus,
@@ -659,21 +703,22 @@ static pic_status sample_t(pic_handle* h, int species, uint32_t modulus, uint32_
     CK(cudaGetLastError());
     const long long k = std::min((long long)cnt, max_out);
     if (k > 0) {
-        if (x) CK(cudaMemcpy(x, dx, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost));
-        if (u) CK(cudaMemcpy(u, du, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost));
-        if (id) CK(cudaMemcpy(id, did, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost));
-        if (dr) CK(cudaMemcpy(dr, ddr, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost));
+        if (x) CK(cudaMemcpyAsync(x, dx, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, h->stream));
+        if (u) CK(cudaMemcpyAsync(u, du, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, h->stream));
+        if (id) CK(cudaMemcpyAsync(id, did, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost, h->stream));
+        if (dr) CK(cudaMemcpyAsync(dr, ddr, sizeof(double) * 3 * k, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
         if (x && h->geom != 0) {
             const int ig = h->geom == 1 ? 2 : 1;
             for (long long i = 0; i < k; ++i) x[3 * i + ig] = 0.5;
         }
     }
     *n_out = (long long)cnt;
-    cudaFree(dx);
-    cudaFree(du);
-    cudaFree(ddr);
-    cudaFree(did);
-    cudaFree(dcount);
+    dfree(h, dx);
+    dfree(h, du);
+    dfree(h, ddr);
+    dfree(h, did);
+    dfree(h, dcount);
     return PIC_OK;
 }
 
@@ -689,11 +734,13 @@ template <class T, int G> static pic_status maxwellian_t(pic_handle* h, int spec
     pic_status st = alloc_species(h, d, tcap);
     if (st != PIC_OK) return st;
     const int b = h->buf;
-    maxwellian_kernel<T, G><<<h->tl.ntiles, NTHR, 0, h->stream>>>(h->tl, h->g, ppc, theta, h->cfg.c, drift ? drift[0] : 0.0,
+    // about four CTAs per SM in all, at most one per 256 particles of a tile
+    const int per_tile = ppc * cells_per_tile;
+    const int ny = std::max(1, std::min((per_tile + NTHR - 1) / NTHR, (4 * 152 + h->tl.ntiles - 1) / h->tl.ntiles));
+    maxwellian_kernel<T, G><<<dim3(h->tl.ntiles, ny), NTHR, 0, h->stream>>>(h->tl, h->g, ppc, theta, h->cfg.c, drift ? drift[0] : 0.0,
                                                                  drift ? drift[1] : 0.0, drift ? drift[2] : 0.0, noise, seed,
                                                                  id_base, tcap, view_of<T>(d.arr[b]), h->esc == ESC_DISP,
                                                                  d.stay[b]);
-    CK(cudaStreamSynchronize(h->stream));
     CK(cudaGetLastError());
     d.n = n;
     d.loaded = true;
@@ -919,11 +966,11 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
     const size_t fb = (size_t)3 * g.cstride * h->esz;
     void** bufs[] = {&h->E, &h->B, &h->J, &h->Jtmp};
     for (void** p : bufs) {
-        if (cudaMalloc(p, fb) != cudaSuccess) return bail(fail(h, PIC_ERR_OOM, "field allocation failed"));
+        if (dalloc(h, p, fb) != cudaSuccess) return bail(fail(h, PIC_ERR_OOM, "field allocation failed"));
         cudaMemsetAsync(*p, 0, fb, h->stream);
     }
     h->Jcur = (c.box == PIC_BOX_SHEAR && AY) ? h->Jtmp : h->J;
-    if (cudaMalloc(&h->ctx, sizeof(StepCtx)) != cudaSuccess) return bail(fail(h, PIC_ERR_OOM, "allocation failed"));
+    if (dalloc(h, (void**)&h->ctx, sizeof(StepCtx)) != cudaSuccess) return bail(fail(h, PIC_ERR_OOM, "allocation failed"));
     cudaMemsetAsync(h->ctx, 0, sizeof(StepCtx), h->stream);
     h->cc.box = c.box == PIC_BOX_SHEAR ? 1 : (c.box == PIC_BOX_EXPAND ? 2 : 0);
     h->cc.ny = c.ny;
@@ -932,24 +979,24 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
     h->cc.c = c.c;
     if (const char* e = getenv("PIC_NO_GRAPHS")) h->graphs_on = atoi(e) == 0;
     if (!h->fp64) {
-        if (cudaMalloc(&h->Jint, (size_t)3 * g.cstride * sizeof(int)) != cudaSuccess)
+        if (dalloc(h, (void**)&h->Jint, (size_t)3 * g.cstride * sizeof(int)) != cudaSuccess)
             return bail(fail(h, PIC_ERR_OOM, "field allocation failed"));
         cudaMemsetAsync(h->Jint, 0, (size_t)3 * g.cstride * sizeof(int), h->stream);
     }
     if (c.box == PIC_BOX_SHEAR) {
         void** kb[] = {&h->Es, &h->Bs, &h->Ec, &h->Bc};
         for (void** p : kb) {
-            if (cudaMalloc(p, fb) != cudaSuccess) return bail(fail(h, PIC_ERR_OOM, "field allocation failed"));
+            if (dalloc(h, p, fb) != cudaSuccess) return bail(fail(h, PIC_ERR_OOM, "field allocation failed"));
             cudaMemsetAsync(*p, 0, fb, h->stream);
         }
     }
     h->stage_elems = (size_t)3 * c.nx * c.ny * c.nz;
-    if (cudaMalloc(&h->stage, sizeof(double) * h->stage_elems) != cudaSuccess)
+    if (dalloc(h, (void**)&h->stage, sizeof(double) * h->stage_elems) != cudaSuccess)
         return bail(fail(h, PIC_ERR_OOM, "staging allocation failed"));
     h->partial_blocks = 152 * 4;
-    if (cudaMalloc(&h->partial, sizeof(double) * (h->partial_blocks * 3 + 8)) != cudaSuccess)
+    if (dalloc(h, (void**)&h->partial, sizeof(double) * (h->partial_blocks * 3 + 8)) != cudaSuccess)
         return bail(fail(h, PIC_ERR_OOM, "allocation failed"));
-    if (cudaMalloc(&h->err, sizeof(int)) != cudaSuccess || cudaMalloc(&h->counters, 2 * sizeof(unsigned long long)) != cudaSuccess)
+    if (dalloc(h, (void**)&h->err, sizeof(int)) != cudaSuccess || dalloc(h, (void**)&h->counters, 2 * sizeof(unsigned long long)) != cudaSuccess)
         return bail(fail(h, PIC_ERR_OOM, "allocation failed"));
     cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
     cudaMemsetAsync(h->counters, 0, 2 * sizeof(unsigned long long), h->stream);
@@ -967,22 +1014,22 @@ pic_status pic_destroy(pic_handle* h) {
     for (auto& d : h->sp) {
         for (int b = 0; b < 2; ++b) {
             for (int i = 0; i < 11; ++i) {
-                if (d.arr[b][i]) cudaFree(d.arr[b][i]);
-                if (d.larr[b][i]) cudaFree(d.larr[b][i]);
+                if (d.arr[b][i]) dfree(h, d.arr[b][i]);
+                if (d.larr[b][i]) dfree(h, d.larr[b][i]);
             }
-            if (d.stay[b]) cudaFree(d.stay[b]);
-            if (d.arrv[b]) cudaFree(d.arrv[b]);
+            if (d.stay[b]) dfree(h, d.stay[b]);
+            if (d.arrv[b]) dfree(h, d.arrv[b]);
         }
-        if (d.lcount) cudaFree(d.lcount);
+        if (d.lcount) dfree(h, d.lcount);
     }
     void* ptrs[] = {h->E,     h->B,     h->J,       h->Jtmp,    h->Es,       h->Bs,       h->Ec,
                     h->Bc,    h->stage, h->partial, h->err,     h->counters, (void*)h->Jint};
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) dfree(h, p);
     prof_resolve(h);
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
     drop_graphs(h);
-    if (h->ctx) cudaFree(h->ctx);
+    if (h->ctx) dfree(h, h->ctx);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return PIC_OK;
@@ -1029,22 +1076,22 @@ pic_status pic_load_particles(pic_handle* h, int species, double q, double m, in
     double *dx = nullptr, *du = nullptr;
     uint32_t* did = nullptr;
     size_t n3 = (size_t)std::max<int64_t>(n, 1) * 3;
-    CK(cudaMalloc(&dx, sizeof(double) * n3));
-    CK(cudaMalloc(&du, sizeof(double) * n3));
+    CK(dalloc(h, (void**)&dx, sizeof(double) * n3));
+    CK(dalloc(h, (void**)&du, sizeof(double) * n3));
     if (n > 0) {
         CK(cudaMemcpyAsync(dx, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
         CK(cudaMemcpyAsync(du, u, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
         if (id) {
-            CK(cudaMalloc(&did, sizeof(uint32_t) * n));
+            CK(dalloc(h, (void**)&did, sizeof(uint32_t) * n));
             CK(cudaMemcpyAsync(did, id, sizeof(uint32_t) * n, cudaMemcpyHostToDevice, h->stream));
         }
     }
     h->sp[species].q = q;
     h->sp[species].m = m;
     st = DISPATCH(h, load_t, h, species, n, dx, du, did, (const double*)nullptr);
-    cudaFree(dx);
-    cudaFree(du);
-    if (did) cudaFree(did);
+    dfree(h, dx);
+    dfree(h, du);
+    if (did) dfree(h, did);
     return st;
 }
 
@@ -1053,7 +1100,7 @@ pic_status pic_load_maxwellian(pic_handle* h, int species, double q, double m, i
     pic_status st = check_species(h, species);
     if (st != PIC_OK) return st;
     if (ppc < 0 || !(m > 0) || theta < 0 || noise_sigma < 0) return fail(h, PIC_ERR_ARG, "bad loader arguments");
-    CK(cudaStreamSynchronize(h->stream));
+    // no host wait: reallocation and loading are ordered on the handle's stream
     h->sp[species].q = q;
     h->sp[species].m = m;
     return DISPATCH(h, maxwellian_t, h, species, ppc, theta, drift, noise_sigma, seed, id_base);
@@ -1202,26 +1249,27 @@ pic_status pic_get_particles(pic_handle* h, int species, double* x, double* u, u
     double *dx = nullptr, *du = nullptr, *ddr = nullptr;
     uint32_t* did = nullptr;
     size_t n3 = (size_t)std::max(n, 1ll) * 3;
-    if (x) CK(cudaMalloc(&dx, sizeof(double) * n3));
-    if (u) CK(cudaMalloc(&du, sizeof(double) * n3));
-    if (id) CK(cudaMalloc(&did, sizeof(uint32_t) * std::max(n, 1ll)));
-    if (dr) CK(cudaMalloc(&ddr, sizeof(double) * n3));
+    if (x) CK(dalloc(h, (void**)&dx, sizeof(double) * n3));
+    if (u) CK(dalloc(h, (void**)&du, sizeof(double) * n3));
+    if (id) CK(dalloc(h, (void**)&did, sizeof(uint32_t) * std::max(n, 1ll)));
+    if (dr) CK(dalloc(h, (void**)&ddr, sizeof(double) * n3));
     st = DISPATCH(h, compact_t, h, species, dx, du, did, ddr);
     if (st == PIC_OK && n > 0) {
-        if (x) CK(cudaMemcpy(x, dx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
-        if (u) CK(cudaMemcpy(u, du, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
-        if (id) CK(cudaMemcpy(id, did, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
-        if (dr) CK(cudaMemcpy(dr, ddr, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+        if (x) CK(cudaMemcpyAsync(x, dx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+        if (u) CK(cudaMemcpyAsync(u, du, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+        if (id) CK(cudaMemcpyAsync(id, did, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->stream));
+        if (dr) CK(cudaMemcpyAsync(dr, ddr, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
         if (x && h->geom != 0) {
             // the ignorable coordinate is not tracked
             int ig = h->geom == 1 ? 2 : 1;
             for (long long i = 0; i < n; ++i) x[3 * i + ig] = 0.5;
         }
     }
-    if (dx) cudaFree(dx);
-    if (du) cudaFree(du);
-    if (did) cudaFree(did);
-    if (ddr) cudaFree(ddr);
+    if (dx) dfree(h, dx);
+    if (du) dfree(h, du);
+    if (did) dfree(h, did);
+    if (ddr) dfree(h, ddr);
     return st;
 }
 
@@ -1260,6 +1308,25 @@ pic_status pic_get_profile(pic_handle* h, pic_profile* out) {
     out->launches = h->prof.launches;
     out->particle_launches = h->prof.particle_launches;
     out->particle_steps = h->prof.particle_steps;
+    return PIC_OK;
+}
+
+pic_status pic_preload_kernels(int32_t device, int32_t precision) {
+    if (precision != PIC_FP32 && precision != PIC_FP64) return fail(nullptr, PIC_ERR_ARG, "bad precision");
+    if (cudaSetDevice(device) != cudaSuccess) return fail(nullptr, PIC_ERR_CUDA, "no such CUDA device");
+    const bool fp64 = precision == PIC_FP64;
+    const int pushes[5][2] = {{PUSH_BORIS, ESC_NONE}, {PUSH_BORIS, ESC_DISP}, {PUSH_BORIS, ESC_PROB},
+                              {PUSH_KSB, ESC_NONE}, {PUSH_KEB, ESC_NONE}};
+    cudaFuncAttributes a;
+    for (int geom = 0; geom < 3; ++geom)
+        for (int ord = 1; ord <= 2; ++ord)
+            for (const auto& pe : pushes) {
+                const KernelSet ks = lookup_kernels(fp64, geom, ord, pe[0], pe[1]);
+                for (const void* f : ks.tile)
+                    if (cudaFuncGetAttributes(&a, f) != cudaSuccess) return fail(nullptr, PIC_ERR_CUDA, "kernel load failed");
+                if (cudaFuncGetAttributes(&a, ks.loose) != cudaSuccess || cudaFuncGetAttributes(&a, ks.batch) != cudaSuccess)
+                    return fail(nullptr, PIC_ERR_CUDA, "kernel load failed");
+            }
     return PIC_OK;
 }
 

@@ -273,6 +273,8 @@ extern "C" pic_status pic_server_create(int device, uint64_t hbm_budget_bytes, i
         pic_internal_set_global_error("pic_server_create: no such CUDA device");
         return PIC_ERR_CUDA;
     }
+    // the served runs are FP32: load their kernels now, not at the first run of each kind
+    if (pic_preload_kernels(device, PIC_FP32) != PIC_OK) return PIC_ERR_CUDA;
     pic_server* S = new pic_server();
     S->device = device;
     S->budget = hbm_budget_bytes;

@@ -113,6 +113,7 @@ _SIGS = {
     "pic_set_profiling": (C.c_int, [_H, C.c_int]),
     "pic_get_profile": (C.c_int, [_H, C.POINTER(pic_profile)]),
     "pic_reset_profile": (C.c_int, [_H]),
+    "pic_preload_kernels": (C.c_int, [C.c_int32, C.c_int32]),
     "pic_kernel_variant_count": (C.c_int, []),
     "pic_kernel_variant_info": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pic_get_kernel_variant": (C.c_int, [_H, C.POINTER(C.c_int32)]),
@@ -295,6 +296,10 @@ def pic_get_profile(h) -> pic_profile:
 
 def pic_reset_profile(h):
     _check(h, lib().pic_reset_profile(h))
+
+
+def pic_preload_kernels(device=0, precision=None):
+    _check(None, lib().pic_preload_kernels(device, PIC_FP32 if precision is None else precision))
 
 
 def pic_kernel_variant_count() -> int:
