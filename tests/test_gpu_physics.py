@@ -1,0 +1,86 @@
+"""Physics of the whole GPU path over hundreds of steps, on many particles at
+once: closed forms that the box equations fix (beyond the one-step parity
+tests against the oracle)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2602_15939_gb300 import pic as P
+from paper_2602_15939_gb300 import workloads as W
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision,tol", [(P.PIC_FP32, 2e-4), (P.PIC_FP64, 1e-10)], ids=["fp32", "fp64"])
+def test_shearing_box_epicycles(precision, tol):
+    """Uncharged particles in the shearing box with E = B = 0: the momentum
+    equation of Sec. 2.2 reduces to du_x/dt = 2 Omega0 u_y, du_y/dt =
+    -(2 - s) Omega0 u_x (epicycles, kappa^2 = 2 (2 - s) Omega0^2), and its
+    discretisation is the implicit midpoint rule.  So after N steps every
+    particle's (sqrt(2-s) u_x, sqrt(2) u_y) has turned clockwise by exactly
+    N 2 atan(kappa / 2), and u_z is unchanged -- whatever the particle's x, its
+    crossings of the shearing-periodic boundary and its Lorentz factor."""
+    s, Om, N = 1.5, 1e-2, 800
+    n = (32, 32, 16)
+    cfg = P.make_config(box=P.PIC_BOX_SHEAR, nx=n[0], ny=n[1], nz=n[2], order=2, precision=precision, s=s, Omega0=Om)
+    sp = W.uniform_plasma(n, 2, seed=3, uth=0.2, charges=(0.0,), q=0.0)[0]
+    box = P.Box(cfg)
+    try:
+        z = np.zeros((3, n[2], n[1], n[0]))
+        box.set_fields(z, z)
+        box.load(0, 0.0, 1.0, sp["x"], sp["u"], sp["id"])
+        box.step(N)
+        _, u1, ids, _ = box.particles(0)
+        assert box.diagnostics().error_word == 0
+    finally:
+        box.close()
+    u0 = sp["u"][ids]
+    kappa = math.sqrt(2 * (2 - s)) * Om
+    phi = N * 2 * math.atan(kappa / 2)
+    a, b = math.sqrt(2 - s) * u0[:, 0], math.sqrt(2) * u0[:, 1]
+    ux = (a * math.cos(phi) + b * math.sin(phi)) / math.sqrt(2 - s)
+    uy = (-a * math.sin(phi) + b * math.cos(phi)) / math.sqrt(2)
+    scale = np.abs(u0).max()
+    assert phi > 2 * math.pi  # more than one epicycle
+    assert np.abs(u1[:, 0] - ux).max() <= tol * scale
+    assert np.abs(u1[:, 1] - uy).max() <= tol * scale
+    assert np.abs(u1[:, 2] - u0[:, 2]).max() <= tol * scale
+
+
+@pytest.mark.gpu
+def test_expanding_box_cooling_across_the_field():
+    """Expanding box (Sec. 3) with l_y = l_z = a = exp(r t), l_x = 1, a pair
+    plasma and a uniform magnetic field along x.  The expansion drags the
+    momenta across the field as u_perp ~ 1/a (gyration only mixes the two
+    expanding directions), so T_perp falls as a^-2 while T_par stays put, and
+    the lab-frame field B_x ~ l_x / (l_x l_y l_z) = a^-2 (field energy a^-4):
+    the double-adiabatic (CGL) behaviour of a field along the non-expanding
+    axis.  FP32 particles, FP64 l(t)."""
+    r, N = 1e-3, 400
+    n, ppc, theta = (32, 32, 32), 8, 0.01
+    units = W.PairUnits(0.45, 5.0, ppc)
+    b0 = units.b0_from_sigma(1.0)
+    cfg = P.make_config(box=P.PIC_BOX_EXPAND, nx=n[0], ny=n[1], nz=n[2], order=2, precision=P.PIC_FP32,
+                        rate=(0.0, r, r), c=0.45)
+    box = P.Box(cfg)
+    try:
+        box.load_maxwellian(0, -units.q, 1.0, ppc, theta, seed=1, id_base=0)
+        box.load_maxwellian(1, units.q, 1.0, ppc, theta, seed=2, id_base=ppc * n[0] * n[1] * n[2])
+        box.set_uniform_fields((0.0, 0.0, 0.0), (b0, 0.0, 0.0))
+
+        def temps():
+            us = np.concatenate([box.particles(k)[1] for k in (0, 1)])
+            d = box.diagnostics()
+            assert d.error_word == 0
+            return (np.mean(us[:, 1] ** 2 + us[:, 2] ** 2) / 2, np.mean(us[:, 0] ** 2), d.field_energy_B[0], d.l[1])
+
+        tp0, tl0, wb0, a0 = temps()
+        box.step(N)
+        tp1, tl1, wb1, a1 = temps()
+    finally:
+        box.close()
+    a = a1 / a0
+    assert a == pytest.approx(math.exp(r * N), rel=1e-12)
+    assert tp1 / tp0 == pytest.approx(a ** -2, rel=0.02)
+    assert tl1 / tl0 == pytest.approx(1.0, rel=0.02)
+    assert wb1 / wb0 == pytest.approx(a ** -4, rel=0.02)
