@@ -41,6 +41,7 @@ class Case:
     drift: tuple = (0.0, 0.0, 0.0)
     slack: float = 0.0
     variant: int = 0
+    masses: tuple = (1.0, 1.0)  # per species (electron, positive species)
     extra: dict = field(default_factory=dict)
 
     @property
@@ -68,6 +69,8 @@ class Case:
 def inputs(case: Case):
     sp = W.uniform_plasma(case.n, case.ppc, case.seed, uth=case.uth, q=case.q, ignorable=case.ignorable,
                           drift=case.drift)
+    for d, m in zip(sp, case.masses):
+        d["m"] = m  # u is the momentum per unit mass (gamma v): the same spread for every species
     E, B = W.random_fields(case.n, case.seed + 100, b0=case.b0)
     return sp, E, B
 

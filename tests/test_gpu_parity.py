@@ -37,6 +37,11 @@ CASES = [
     Case("expand3d_o2", BOX_E, (16, 12, 8), order=2, rate=(0.0, 1e-3, 1e-3), step0=200),
     Case("expand3d_o2_exact", BOX_E, (16, 12, 8), order=2, rate=(0.0, 1e-3, 2e-3), step0=150, keb_exact=1),
     Case("expand2dxy_o1", BOX_E, (32, 24, 1), ndim=2, plane=XY, order=1, ppc=6, rate=(2e-3, 1e-3, 0.0), step0=50),
+    # electron-ion plasmas, m_i / m_e = 25 (the expanding-box example of Sec. 3.3)
+    Case("expand3d_o2_ion25", BOX_E, (16, 12, 8), order=2, rate=(0.0, 1e-3, 1e-3), step0=20, masses=(1.0, 25.0)),
+    Case("shear3d_o2_ion25", BOX_S, (16, 12, 8), order=2, s=1.5, Omega0=3e-3, step0=7, masses=(1.0, 25.0)),
+    Case("leaky2d_prob_o1_ion25", BOX_L, (32, 24, 1), ndim=2, plane=XY, order=1, ppc=6, esc_mode=2, p_esc=0.05,
+         theta_inj=0.5, masses=(1.0, 25.0)),
 ]
 
 IDS = [c.name for c in CASES]
