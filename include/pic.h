@@ -212,6 +212,31 @@ pic_status pic_set_profiling(pic_handle *h, int enable);
 pic_status pic_get_profile(pic_handle *h, pic_profile *out);
 pic_status pic_reset_profile(pic_handle *h);
 
+/* Tile capacity.  Each tile holds a fixed number of particle slots (set at
+ * load from the fullest tile and cfg.capacity_slack); particles crowding into
+ * a tile beyond it take a loose list, and beyond the loose list's room are
+ * lost (PIC_ERR_STATE).  Every step keeps each species' fullest-tile
+ * occupancy on the device; pic_step checks it every 8 steps it runs (an
+ * asynchronous snapshot of the maxima since the last one, acted on one check
+ * later) and, when a
+ * species' fullest tile passes 90% of its slots or its loose list a quarter
+ * of its room, lays every species out again with more slots (the fullest tile
+ * x max(1 + slack, 1.25) + 32) and a larger loose list.  Particle states
+ * and results do not change.  pic_rebalance runs the check now (force != 0:
+ * re-layout regardless; *grown, nullable, says whether it did);
+ * pic_get_capacity reports a species' slots per tile, loose-list room and
+ * the re-layouts so far (each output nullable).  Not a part of the paper's
+ * method: the bookkeeping of the tile-sorted particle layout. */
+pic_status pic_rebalance(pic_handle *h, int32_t force, int32_t *grown);
+/* Capacity checks every `every` steps (default 8; 0: none).  block != 0
+ * (default): a check waits for the snapshot taken one check earlier, which
+ * also keeps the host at most about two checks ahead of the GPU; block = 0:
+ * a check whose snapshot has not landed is skipped (for callers that bound
+ * their own lead, like the server). */
+pic_status pic_set_capacity_check(pic_handle *h, int32_t every, int32_t block);
+pic_status pic_get_capacity(pic_handle *h, int species, int64_t *slots_per_tile, int64_t *loose_capacity,
+                            int64_t *relayouts);
+
 /* Load the library's particle kernels for one precision on `device` now
  * rather than at their first use (CUDA loads code lazily: the first box of
  * each geometry otherwise pays some tens of milliseconds).  The server calls

@@ -214,18 +214,61 @@ __global__ void sample_kernel(Tiling tl, PView<T> v, const int* __restrict__ sta
 // the claims that got a slot (failed claims over-count), clamp the loose
 // count to the list capacity, and zero the counters of the consumed buffer,
 // which the next step writes.
+// occ_max keeps the largest tile occupancy since it was last reset, occ_loose
+// the loose count after the step (the library's capacity check reads them).
 __global__ void finalize_kernel(int ntiles, long long tcap, const int* __restrict__ stay_in, int* __restrict__ arr_in,
                                        int* __restrict__ arr_out, int* __restrict__ lcount_in, int* __restrict__ lcount_out,
-                                       long long lcap, int* err) {
+                                       long long lcap, int* err, int* __restrict__ occ_max,
+                                       int* __restrict__ occ_loose) {
+    int mx = 0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
-        int room = (int)(tcap - (stay_in[t] + arr_in[t]));
+        const int cnt = stay_in[t] + arr_in[t];
+        mx = max(mx, cnt);
+        int room = (int)(tcap - cnt);
         if (arr_out[t] > room) arr_out[t] = room;
         arr_in[t] = 0;
     }
+    for (int sh = 16; sh > 0; sh >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, sh));
+    if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(occ_max, mx);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (*lcount_out > lcap) { atomicOr(err, ERRB_LOOSE_OVERFLOW); *lcount_out = (int)lcap; }
+        int lc = *lcount_out;
+        if (lc > lcap) { atomicOr(err, ERRB_LOOSE_OVERFLOW); lc = (int)lcap; *lcount_out = lc; }
+        *occ_loose = lc;
         *lcount_in = 0;
     }
+}
+
+// Re-lay tile-sorted particles out with another capacity per tile: tile t's
+// stayers and arrivals in buffer `in` (capacity tcap_in) become the first
+// stay_out[t] slots of tile t in `out` (capacity tcap_out).
+template <class T, int G>
+__global__ void regrow_kernel(PView<T> in, PView<T> out, const int* __restrict__ stay_in, const int* __restrict__ arr_in,
+                              long long tcap_in, long long tcap_out, int* __restrict__ stay_out, bool has_dr) {
+    const int t = blockIdx.x;
+    const int nst = stay_in[t], nar = arr_in[t], n = nst + nar;
+    const long long bi = (long long)t * tcap_in, bo = (long long)t * tcap_out;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const long long slot = i < nst ? bi + i : bi + tcap_in - nar + (i - nst);
+        Particle<T> p;
+        load_particle<T, G>(in, slot, has_dr, p);
+        store_particle<T, G>(out, bo + i, has_dr, p);
+    }
+    __syncthreads();  // stay_in may be stay_out: every thread has read it
+    if (threadIdx.x == 0) stay_out[t] = n;
+}
+
+// Copy the first *count_in entries of a loose list (at most lcap_in).
+template <class T, int G>
+__global__ void copy_loose_kernel(PView<T> in, PView<T> out, const int* __restrict__ count_in, long long lcap_in,
+                                  int* __restrict__ count_out, bool has_dr) {
+    long long n = *count_in;
+    if (n > lcap_in) n = lcap_in;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        Particle<T> p;
+        load_particle<T, G>(in, i, has_dr, p);
+        store_particle<T, G>(out, i, has_dr, p);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count_out = (int)n;
 }
 
 // Sum of m c^2 (gamma - 1) over the tile-sorted particles and the loose list.

@@ -135,6 +135,17 @@ struct pic_handle {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     bool batched = false;  // stepped by a pic_batch; pic_step refuses
+    int since_check = 0;   // steps since the last tile-capacity check
+    long long regrows = 0; // tile re-layouts so far
+    // asynchronous occupancy snapshot: per species [stay x ntiles, arrivals x
+    // ntiles, loose count] of the buffer current when it was taken
+    int* occ_dev = nullptr;   // largest tile occupancy of each species since the last check, then each loose count
+    int* occ_host = nullptr;  // pinned, two slots
+    cudaEvent_t occ_ev[2] = {nullptr, nullptr};
+    bool occ_pending[2] = {false, false};
+    int occ_next = 0;         // slot of the next snapshot (the older one)
+    int check_every = 8;      // steps between capacity checks (0: none)
+    bool check_block = true;  // wait for the older snapshot (bounds the host's lead)
     int buf = 0;  // particle buffer holding the current state
     long long step = 0;
     DevSpecies sp[PIC_MAX_SPECIES];
@@ -484,7 +495,8 @@ template <class T, int G> static pic_status post_particle_t(pic_handle* h, const
             DevSpecies& d = h->sp[s];
             if (!d.loaded) continue;
             finalize_kernel<<<grid_blocks(h->tl.ntiles), NTHR, 0, h->stream>>>(
-                h->tl.ntiles, d.tcap, d.stay[b], d.arrv[b], d.arrv[o], d.lcount + b, d.lcount + o, d.lcap, h->err);
+                h->tl.ntiles, d.tcap, d.stay[b], d.arrv[b], d.arrv[o], d.lcount + b, d.lcount + o, d.lcap, h->err,
+                h->occ_dev + s, h->occ_dev + PIC_MAX_SPECIES + s);
             h->prof.launches++;
         }
         prof_end(h, 1);
@@ -573,6 +585,46 @@ static void dfree(pic_handle* h, void* p) {
     else cudaFree(p);
 }
 
+// ---- pinned snapshot slots --------------------------------------------------------------------
+// A capacity check copies a few counters of a handle to pinned host memory.
+// cudaMallocHost and cudaFreeHost per handle would synchronise the device at
+// every create and destroy (a served ensemble makes hundreds of handles), so
+// the slots come from process-wide slabs that stay allocated until exit.
+constexpr int SNAP_INTS = 4 * PIC_MAX_SPECIES;  // two snapshots of (maxima, loose counts)
+constexpr int SNAP_PER_SLAB = 1024;
+
+struct SnapSlots {
+    std::mutex mu;
+    std::vector<int*> free;
+};
+static SnapSlots& snap_slots() {
+    static SnapSlots* s = new SnapSlots();  // never destroyed: handles may outlive static destructors
+    return *s;
+}
+
+static int* snap_take() {
+    SnapSlots& S = snap_slots();
+    std::lock_guard<std::mutex> lk(S.mu);
+    if (S.free.empty()) {
+        int* slab = nullptr;
+        if (cudaMallocHost(&slab, sizeof(int) * SNAP_INTS * SNAP_PER_SLAB) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        for (int i = SNAP_PER_SLAB - 1; i >= 0; --i) S.free.push_back(slab + (size_t)i * SNAP_INTS);
+    }
+    int* p = S.free.back();
+    S.free.pop_back();
+    return p;
+}
+
+static void snap_give(int* p) {
+    if (!p) return;
+    SnapSlots& S = snap_slots();
+    std::lock_guard<std::mutex> lk(S.mu);
+    S.free.push_back(p);
+}
+
 static void drop_graphs(pic_handle* h) {
     for (int b = 0; b < 2; ++b) {
         if (h->gexec[b]) cudaGraphExecDestroy(h->gexec[b]);
@@ -647,6 +699,86 @@ static pic_status load_t(pic_handle* h, int species, long long n, const double* 
     dfree(h, cnt);
     d.n = n;
     d.loaded = true;
+    return PIC_OK;
+}
+
+// ---- tile capacity ------------------------------------------------------------------------
+// Particles crowding into some tiles fill their slots; arrivals beyond a
+// tile's capacity take the loose list, and beyond its capacity are lost
+// (PIC_ERR_STATE).  Each step's bookkeeping kernel keeps the fullest tile's
+// occupancy on the device; a check copies those maxima and the loose counts
+// to the host (one small copy, read one check later), and when a species'
+// fullest tile passed 90% of its slots, or its loose list a quarter of its
+// room, every species is laid out again into buffer 0 with capacity
+// (fullest tile) x max(1 + slack, 1.25) + 32 (never less than before) and a loose list
+// at least 4x its current fill.  Re-layout keeps every particle and its order
+// within a tile, so the physics does not change.
+constexpr double REGROW_HEADROOM = 1.25;  // at least 25% free slots after a re-layout
+
+template <class T, int G> static pic_status regrow_t(pic_handle* h, bool force, bool* grown) {
+    *grown = false;
+    const int nt = h->tl.ntiles;
+    const int b = h->buf;
+    const bool leaky = h->esc == ESC_DISP;
+    CK(cudaStreamSynchronize(h->stream));
+    long long new_tcap[PIC_MAX_SPECIES] = {}, new_lcap[PIC_MAX_SPECIES] = {};
+    bool need = force;
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
+        DevSpecies& d = h->sp[s];
+        if (!d.loaded) continue;
+        std::vector<int> st(nt), ar(nt);
+        int lc = 0;
+        CK(cudaMemcpyAsync(st.data(), d.stay[b], sizeof(int) * nt, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(ar.data(), d.arrv[b], sizeof(int) * nt, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(&lc, d.lcount + b, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        long long mx = 0;
+        for (int t = 0; t < nt; ++t) mx = std::max(mx, (long long)st[t] + ar[t]);
+        const double slack = h->cfg.capacity_slack > 0 ? h->cfg.capacity_slack : 0.3;
+        long long tc = (long long)std::ceil(mx * std::max(1.0 + slack, REGROW_HEADROOM)) + 32;
+        tc = std::max(d.tcap, (tc + 3) & ~3ll);
+        new_tcap[s] = tc;
+        new_lcap[s] = std::max(d.lcap, 4ll * lc);
+        if (mx > 0.9 * d.tcap || lc > d.lcap / 4) need = true;
+    }
+    if (!need) return PIC_OK;
+    drop_graphs(h);
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
+        DevSpecies& d = h->sp[s];
+        if (!d.loaded) continue;
+        const int nact = h->geom == 0 ? 3 : 2;
+        void* na[2][11] = {};
+        void* nl[2][11] = {};
+        for (int bb = 0; bb < 2; ++bb)
+            for (int i = 0; i < 11; ++i) {
+                const bool use = i == 0 || (i >= 1 && i <= nact) || (i >= 4 && i <= 7) || (i >= 8 && leaky);
+                if (!use) continue;
+                const size_t es = (i == 0 || i == 7) ? 4 : h->esz;
+                CK(dalloc(h, &na[bb][i], (size_t)nt * new_tcap[s] * es));
+                CK(dalloc(h, &nl[bb][i], (size_t)new_lcap[s] * es));
+            }
+        PView<T> vin = view_of<T>(d.arr[b]), vout = view_of<T>(na[0]);
+        regrow_kernel<T, G><<<nt, NTHR, 0, h->stream>>>(vin, vout, d.stay[b], d.arrv[b], d.tcap, new_tcap[s], d.stay[0], leaky);
+        copy_loose_kernel<T, G><<<64, NTHR, 0, h->stream>>>(view_of<T>(d.larr[b]), view_of<T>(nl[0]), d.lcount + b, d.lcap,
+                                                            d.lcount + 0, leaky);
+        CK(cudaGetLastError());
+        if (b == 1) CK(cudaMemsetAsync(d.lcount + 1, 0, sizeof(int), h->stream));
+        CK(cudaMemsetAsync(d.arrv[0], 0, sizeof(int) * nt, h->stream));
+        CK(cudaMemsetAsync(d.arrv[1], 0, sizeof(int) * nt, h->stream));
+        for (int bb = 0; bb < 2; ++bb)
+            for (int i = 0; i < 11; ++i) {
+                dfree(h, d.arr[bb][i]);
+                dfree(h, d.larr[bb][i]);
+                d.arr[bb][i] = na[bb][i];
+                d.larr[bb][i] = nl[bb][i];
+            }
+        d.tcap = new_tcap[s];
+        d.lcap = new_lcap[s];
+    }
+    h->buf = 0;
+    h->regrows += 1;
+    *grown = true;
+    CK(cudaStreamSynchronize(h->stream));
     return PIC_OK;
 }
 
@@ -998,6 +1130,9 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
         return bail(fail(h, PIC_ERR_OOM, "allocation failed"));
     if (dalloc(h, (void**)&h->err, sizeof(int)) != cudaSuccess || dalloc(h, (void**)&h->counters, 2 * sizeof(unsigned long long)) != cudaSuccess)
         return bail(fail(h, PIC_ERR_OOM, "allocation failed"));
+    if (dalloc(h, (void**)&h->occ_dev, sizeof(int) * 2 * PIC_MAX_SPECIES) != cudaSuccess)
+        return bail(fail(h, PIC_ERR_OOM, "allocation failed"));
+    cudaMemsetAsync(h->occ_dev, 0, sizeof(int) * 2 * PIC_MAX_SPECIES, h->stream);
     cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
     cudaMemsetAsync(h->counters, 0, 2 * sizeof(unsigned long long), h->stream);
     if (encode_field_map(h, &h->tmE, h->E) != PIC_OK || encode_field_map(h, &h->tmB, h->B) != PIC_OK)
@@ -1023,12 +1158,18 @@ pic_status pic_destroy(pic_handle* h) {
         if (d.lcount) dfree(h, d.lcount);
     }
     void* ptrs[] = {h->E,     h->B,     h->J,       h->Jtmp,    h->Es,       h->Bs,       h->Ec,
-                    h->Bc,    h->stage, h->partial, h->err,     h->counters, (void*)h->Jint};
+                    h->Bc,    h->stage, h->partial, h->err,     h->counters, (void*)h->Jint, (void*)h->occ_dev};
     for (void* p : ptrs)
         if (p) dfree(h, p);
     prof_resolve(h);
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
     drop_graphs(h);
+    for (cudaEvent_t e : h->occ_ev)
+        if (e) {
+            cudaEventSynchronize(e);
+            cudaEventDestroy(e);
+        }
+    snap_give(h->occ_host);
     if (h->ctx) dfree(h, h->ctx);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -1182,12 +1323,60 @@ pic_status pic_set_step(pic_handle* h, int64_t step) {
     return DISPATCH(h, refill_t, h);
 }
 
+// The periodic capacity check of pic_step.  Two occupancy snapshots are in
+// flight, taken one check apart; each check acts on the older one -- waiting
+// for it if the GPU is that far behind, which also bounds how many steps the
+// host queues ahead of the GPU (about two checks) -- and takes a new snapshot
+// in its slot.  Only a re-layout, when the snapshot shows crowding, waits for
+// the GPU to drain.
+static pic_status capacity_check(pic_handle* h) {
+    const int nv = 2 * PIC_MAX_SPECIES;  // largest occupancy of each species since the last snapshot, loose counts
+    static_assert(2 * nv == SNAP_INTS, "a snapshot slot holds two snapshots");
+    for (cudaEvent_t& e : h->occ_ev)
+        if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            e = nullptr;
+            return fail(h, PIC_ERR_CUDA, "cannot create the occupancy snapshot events");
+        }
+    if (!h->occ_host && !(h->occ_host = snap_take())) return fail(h, PIC_ERR_OOM, "cannot allocate the occupancy snapshots");
+    const int k = h->occ_next;
+    int* snap = h->occ_host + k * nv;
+    if (h->occ_pending[k]) {
+        if (!h->check_block && cudaEventQuery(h->occ_ev[k]) != cudaSuccess) return PIC_OK;  // look again next time
+        CK(cudaEventSynchronize(h->occ_ev[k]));
+        h->occ_pending[k] = false;
+        bool pressure = false;
+        for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
+            const DevSpecies& d = h->sp[s];
+            if (!d.loaded) continue;
+            if (snap[s] > 0.9 * d.tcap || snap[PIC_MAX_SPECIES + s] > d.lcap / 4) pressure = true;
+        }
+        if (pressure) {
+            bool grown = false;
+            pic_status st = DISPATCH(h, regrow_t, h, false, &grown);
+            if (st != PIC_OK) return st;
+            if (grown) h->occ_pending[1 - k] = false;  // taken on the old layout
+        }
+    }
+    CK(cudaMemcpyAsync(snap, h->occ_dev, sizeof(int) * nv, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemsetAsync(h->occ_dev, 0, sizeof(int) * PIC_MAX_SPECIES, h->stream));  // restart the running maxima
+    CK(cudaEventRecord(h->occ_ev[k], h->stream));
+    h->occ_pending[k] = true;
+    h->occ_next = 1 - k;
+    return PIC_OK;
+}
+
 pic_status pic_step(pic_handle* h, int nsteps) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
     if (h->batched) return fail(h, PIC_ERR_STATE, "the box is stepped by a batch");
     cudaSetDevice(h->cfg.device);
     if (nsteps < 0) return fail(h, PIC_ERR_ARG, "nsteps must be >= 0");
     while (nsteps > 0) {
+        if (h->check_every > 0 && h->since_check >= h->check_every) {
+            h->since_check = 0;
+            pic_status st = capacity_check(h);
+            if (st != PIC_OK) return st;
+        }
         if (h->graphs_on && !h->prof.on && nsteps >= 2) {
             const int b0 = h->buf;
             if (!h->graph_ok[b0]) {
@@ -1197,6 +1386,7 @@ pic_status pic_step(pic_handle* h, int nsteps) {
             if (h->graph_ok[b0]) {
                 CK(cudaGraphLaunch(h->gexec[b0], h->stream));
                 h->step += 2;
+                h->since_check += 2;
                 h->prof.launches += h->graph_kernels;
                 nsteps -= 2;
                 continue;
@@ -1204,8 +1394,37 @@ pic_status pic_step(pic_handle* h, int nsteps) {
         }
         pic_status st = DISPATCH(h, step_t, h);
         if (st != PIC_OK) return st;
+        h->since_check += 1;
         nsteps -= 1;
     }
+    return PIC_OK;
+}
+
+pic_status pic_set_capacity_check(pic_handle* h, int32_t every, int32_t block) {
+    if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    if (every < 0) return fail(h, PIC_ERR_ARG, "check interval must be >= 0");
+    h->check_every = every;
+    h->check_block = block != 0;
+    return PIC_OK;
+}
+
+pic_status pic_rebalance(pic_handle* h, int32_t force, int32_t* grown) {
+    if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    if (h->batched) return fail(h, PIC_ERR_STATE, "the box is stepped by a batch");
+    cudaSetDevice(h->cfg.device);
+    bool g = false;
+    pic_status st = DISPATCH(h, regrow_t, h, force != 0, &g);
+    if (grown) *grown = g ? 1 : 0;
+    return st;
+}
+
+pic_status pic_get_capacity(pic_handle* h, int species, int64_t* slots_per_tile, int64_t* loose_capacity,
+                            int64_t* relayouts) {
+    pic_status st = check_species(h, species);
+    if (st != PIC_OK) return st;
+    if (slots_per_tile) *slots_per_tile = h->sp[species].tcap;
+    if (loose_capacity) *loose_capacity = h->sp[species].lcap;
+    if (relayouts) *relayouts = h->regrows;
     return PIC_OK;
 }
 

@@ -145,6 +145,8 @@ static pic_status start_run(pic_server* S, Run* r) {
         return PIC_ERR_CUDA;
     }
     st = pic_set_stream(r->h, r->stream);
+    // the worker keeps at most two chunks of a run queued: capacity checks need not wait
+    if (st == PIC_OK) st = pic_set_capacity_check(r->h, 8, 0);
     const pic_run_spec& s = r->spec;
     uint32_t id_base = 0;
     const uint64_t per_species = (uint64_t)s.ppc * cfg.nx * cfg.ny * cfg.nz;

@@ -114,6 +114,9 @@ _SIGS = {
     "pic_get_profile": (C.c_int, [_H, C.POINTER(pic_profile)]),
     "pic_reset_profile": (C.c_int, [_H]),
     "pic_preload_kernels": (C.c_int, [C.c_int32, C.c_int32]),
+    "pic_rebalance": (C.c_int, [_H, C.c_int32, C.POINTER(C.c_int32)]),
+    "pic_set_capacity_check": (C.c_int, [_H, C.c_int32, C.c_int32]),
+    "pic_get_capacity": (C.c_int, [_H, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "pic_kernel_variant_count": (C.c_int, []),
     "pic_kernel_variant_info": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pic_get_kernel_variant": (C.c_int, [_H, C.POINTER(C.c_int32)]),
@@ -296,6 +299,23 @@ def pic_get_profile(h) -> pic_profile:
 
 def pic_reset_profile(h):
     _check(h, lib().pic_reset_profile(h))
+
+
+def pic_rebalance(h, force=False) -> bool:
+    g = C.c_int32()
+    _check(h, lib().pic_rebalance(h, int(force), C.byref(g)))
+    return bool(g.value)
+
+
+def pic_set_capacity_check(h, every=8, block=True):
+    _check(h, lib().pic_set_capacity_check(h, every, int(block)))
+
+
+def pic_get_capacity(h, species: int):
+    """(slots per tile, loose-list room, re-layouts so far) of a species."""
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(h, lib().pic_get_capacity(h, species, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
 
 
 def pic_preload_kernels(device=0, precision=None):
