@@ -89,7 +89,7 @@ typedef struct pic_config {
     int32_t device;       /* CUDA device ordinal the handle lives on */
     uint32_t seed;        /* key word of the Philox streams (escape, reinjection, loading) */
     uint32_t kernel_variant; /* particle-kernel launch shape: 0 = automatic (the tuned choice
-                             for the precision and geometry); k = 1..4 forces variant k (see
+                             for the precision and geometry); k >= 1 forces variant k (see
                              pic_kernel_variant_info); a variant that does not fit is PIC_ERR_ARG */
     double c;             /* Courant number; 0 < c, and c * sqrt(ndim) < 1 */
     double s_shear;       /* shearing box: s in v_s = -s Omega0 x e_y (3/2 Keplerian) */
@@ -237,6 +237,19 @@ pic_status pic_set_capacity_check(pic_handle *h, int32_t every, int32_t block);
 pic_status pic_get_capacity(pic_handle *h, int species, int64_t *slots_per_tile, int64_t *loose_capacity,
                             int64_t *relayouts);
 
+/* Regrouping by cell.  Every `every` steps (0: never) pic_step first rewrites
+ * each tile's particles into the other particle buffer ordered by cell (a
+ * counting sort per tile: one read and one write of the particle arrays).
+ * Warps of the particle kernel then hold particles of one or two cells, which
+ * makes their field reads and current adds conflict less in shared memory;
+ * the order decays as particles change cells.  Default: 4 for 3D FP32 boxes,
+ * 0 otherwise (FP64 boxes should keep 0: the order of their current's
+ * floating-point adds, and so its last bits, would vary from run to run).
+ * FP32 results are bit-identical for every interval.  Not a part of the
+ * paper's method. */
+pic_status pic_set_regroup_interval(pic_handle *h, int32_t every);
+pic_status pic_get_regroup_interval(pic_handle *h, int32_t *every);
+
 /* Load the library's particle kernels for one precision on `device` now
  * rather than at their first use (CUDA loads code lazily: the first box of
  * each geometry otherwise pays some tens of milliseconds).  The server calls
@@ -248,8 +261,10 @@ pic_status pic_preload_kernels(int32_t device, int32_t precision);
  * 1..pic_kernel_variant_count().  Variant k runs *threads_per_cta threads per
  * CTA, one CTA per tile.  *stable = 1: each tile's stayers are written in
  * their input order (one barrier per chunk; particles stay grouped by cell as
- * the device loader stores them); 0: warps write in any order.  *copies: 1 or
- * 2 copies of the tile's shared current box, lanes alternating between them.
+ * the device loader stores them); 0: warps write in any order.  *copies: 1, 2
+ * or 4 copies of the tile's shared current box, 32/copies banks apart, each
+ * particle's adds dealt onto a copy so that a warp's adds spread over the
+ * banks (FP64: lanes alternate between copies).
  * All variants compute the same result; particle states and FP32 currents are
  * bit-identical.  Outputs may be NULL; k out of range is PIC_ERR_ARG. */
 int pic_kernel_variant_count(void);

@@ -7,7 +7,7 @@
 namespace pic {
 
 struct KernelSet {
-    const void* tile[6];  // one per TILE_VARIANTS entry
+    const void* tile[7];  // one per TILE_VARIANTS entry
     const void* loose;
     const void* batch;    // batched launch, variant default_tile_variant
 };

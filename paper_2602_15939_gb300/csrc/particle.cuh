@@ -224,8 +224,9 @@ template <int G> struct SmemJ<float, G> {
     static_assert(31 + 3 * (1 + (GeomT<G>::AY ? SY : 0) + (GeomT<G>::AZ ? SZ : 0)) < SC,
                   "trash words of the last component stay inside the box");
     uint32_t j;  // shared-window address of the box
-    __device__ explicit SmemJ(int* p) : j(smem_u32(p)) {}
-    __device__ int trash(int) const { return (int)(threadIdx.x & 31); }
+    int tw;      // trash word: exact zeros go here (a word of the first 32)
+    __device__ SmemJ(int* p, int trash_word) : j(smem_u32(p)), tw(trash_word) {}
+    __device__ int trash(int) const { return tw; }
     __device__ void add(int comp, int idx, float a, float b) const {
         const int iv = __float_as_int(fmaf(a, b, 12582912.0f)) - 0x4B400000;
         red_shared(j + 4u * (uint32_t)(comp * SC + idx), iv);
@@ -238,8 +239,9 @@ template <int G> struct SmemJ<double, G> {
     static_assert(31 + 3 * (1 + (GeomT<G>::AY ? SY : 0) + (GeomT<G>::AZ ? SZ : 0)) < SC,
                   "trash words of the last component stay inside the box");
     uint32_t j;
-    __device__ explicit SmemJ(double* p) : j(smem_u32(p)) {}
-    __device__ int trash(int) const { return (int)(threadIdx.x & 31); }
+    int tw;
+    __device__ SmemJ(double* p, int trash_word) : j(smem_u32(p)), tw(trash_word) {}
+    __device__ int trash(int) const { return tw; }
     __device__ void add(int comp, int idx, double a, double b) const {
         red_shared(j + 8u * (uint32_t)(comp * SC + idx), a * b);
     }
@@ -600,6 +602,18 @@ __device__ inline void deposit(const JA& ja, I cidx, const T o[3], const T d[3],
     }
 }
 
+// Base word of the core window of a particle that crosses no boundary: its
+// cell (order 1), or the node below its nearest node (order 2), per axis.
+template <class T, int G, int ORD, class I, class S>
+__device__ __forceinline__ I core_base(I cidx, const T o[3], S sy, S sz) {
+    using GT = GeomT<G>;
+    if (ORD == 1) return cidx;
+    I b = cidx - (o[0] >= T(0.5) ? 0 : 1);
+    if (GT::AY) b -= (o[1] >= T(0.5) ? 0 : 1) * sy;
+    if (GT::AZ) b -= (o[2] >= T(0.5) ? 0 : 1) * sz;
+    return b;
+}
+
 // Core deposit: the part of the current of a particle that crosses no
 // boundary (order 2: keeps its nearest node, order 1: keeps its cell, on every
 // axis), on the window of ORD+1 nodes that holds both of its shapes: (ORD)
@@ -641,7 +655,7 @@ __device__ inline void deposit_core(const JA& ja, I cidx, const T o[3], const T 
             A[a][m] = S0[a][m] + T(0.5) * DS[a][m];
             Q[a][m] = T(0.5) * S0[a][m] + third * DS[a][m];
         }
-    const I b = cross ? ja.trash(cidx) : cidx + wb[0] + wb[1] * ja.SY + wb[2] * ja.SZ;
+    const I b = cross ? ja.trash(cidx) : core_base<T, G, ORD>(cidx, o, ja.SY, ja.SZ);
     if (GT::AY && GT::AZ) {
 #pragma unroll
         for (int n = 0; n < NC; ++n)
@@ -915,45 +929,74 @@ constexpr int TPB = 256;  // threads per CTA of the loose kernel
 constexpr long long TMA_WAIT_LIMIT = 1ll << 24;
 
 // Tile-kernel variants: threads per CTA, the order of the stayers' write,
-// and whether zero current contributions are skipped.
+// and the number of copies of the shared current box.
 //
-// Shared-memory atomics of a warp cost one pass per distinct address in the
-// busiest bank (lanes adding to the same word are merged).  Every deposit of a
-// particle adds to words at fixed offsets from its window base, and the
-// window bases of particles in one or two neighbouring cells fall in distinct
-// banks, so a warp whose particles share a cell adds conflict-free.  The
-// device loader stores each tile's particles grouped by cell; the "stable"
-// variants keep that order, writing each chunk's stayers in input order (a
-// CTA-wide prefix over the warps' counts, one barrier per chunk), so warps
-// stay cell-coherent and every contribution is added unconditionally.  The
-// other variants let warps claim output ranges in any order (no barrier),
-// which mixes the cells within warps over a few steps; they skip zero
-// contributions per lane instead.  Particle states and FP32 currents are the
-// same in all variants (exact integer sums).
-//
-// jc = 2: two copies of the shared current box, lane parity choosing the
-// copy (the second offset by 16 banks), which halves the groups of lanes
-// adding to one word when a warp's particles share a cell; the flush sums
-// the copies.
+// Shared-memory atomics of a warp cost about one pass per lane on the busiest
+// bank, whether those lanes add to one word or to several (only a warp whose
+// 32 lanes all add to one word is merged into one pass).  "stable" variants
+// write each chunk's stayers in input order (a CTA-wide prefix over the warps'
+// counts, one barrier per chunk), which keeps the cell grouping of the device
+// loader longer; the others let warps claim output ranges in any order (no
+// barrier).  jc > 1: copies of the current box 32/jc banks apart, each lane's
+// particle dealt onto a copy so that the warp's adds spread over the banks
+// (pick_copy); the flush sums the copies.  Particle states and FP32 currents
+// are the same in all variants (exact integer sums).
 struct TileVariant { int nt, stable, jc; };
-constexpr int N_TILE_VARIANTS = 6;
-constexpr TileVariant TILE_VARIANTS[N_TILE_VARIANTS] = {{256, 0, 1}, {512, 0, 1}, {512, 1, 1},
-                                                        {256, 1, 1}, {256, 0, 2}, {256, 1, 2}};
+constexpr int N_TILE_VARIANTS = 7;
+constexpr TileVariant TILE_VARIANTS[N_TILE_VARIANTS] = {{256, 0, 1}, {512, 0, 1}, {512, 1, 1}, {256, 1, 1},
+                                                        {256, 0, 2}, {256, 1, 2}, {512, 0, 4}};
 
 // Variant (index) used when the choice is left to the library, and the one
-// batched launches use (measured on GB300: 256 threads with two current
-// boxes for 3D FP32 tiles, 512 threads otherwise).
-constexpr int default_tile_variant(bool fp64, int geom) { return (!fp64 && geom == 0) ? 4 : 1; }
+// batched launches use (measured on GB300: 512 threads with four current
+// boxes for 3D FP32 tiles, 512 threads with one otherwise).
+constexpr int default_tile_variant(bool fp64, int geom) { return (!fp64 && geom == 0) ? 6 : 1; }
 
 // Dynamic shared memory: E box, B box (each 128-byte aligned, the TMA
 // destinations), the J box (int32 for FP32, double for FP64), the mbarrier,
 // small counters, and for stable variants two buffers of per-warp stayer
 // counts.
+// The copy of the shared current box a lane's particle adds into, with JC
+// copies placed 32/JC banks apart (copy stride = 32/JC mod 32 words).  All
+// adds of a warp instruction go to (each lane's base word + one common
+// offset), so two lanes conflict whenever their base words share a bank, and
+// for particles spread over a tile that is random: about 3.5 lanes on the
+// busiest bank.  The lanes whose base banks share a residue mod 32/JC are
+// dealt round-robin onto that residue's JC banks (copy = slot - bank / (32/JC)
+// mod JC), so no bank takes more than ceil(lanes of the residue / JC): about
+// 2.7 lanes with 2 copies, 2.1 with 4.  Lanes of the same cell fall apart the
+// same way.  Lanes that are not dealt (crossing particles, which add only
+// exact zeros here, and idle lanes) use copy 0 and trash word `lane`; the
+// trash word of a dealt lane is the word of its copy whose bank is `lane`, so
+// the exact zeros of a warp still land on 32 distinct banks.  FP64 words span
+// two banks: its copies are chosen by lane parity.
+template <class T, int G, int JC, int JCS>
+__device__ __forceinline__ SmemJ<T, G> pick_copy(JWord<T>* sJ, int lane, bool deal, int base) {
+    if constexpr (JC == 1) {
+        return SmemJ<T, G>(sJ, lane);
+    } else if constexpr (sizeof(JWord<T>) != 4) {
+        return SmemJ<T, G>(sJ + (lane % JC) * JCS, lane);
+    } else {
+        constexpr int OFF = 32 / JC;
+        static_assert(JC * OFF == 32 && JCS % 32 == OFF, "copies 32/JC banks apart");
+        const int bank = base & 31;
+        const int key = bank & (OFF - 1);
+        unsigned same = __ballot_sync(0xffffffffu, deal);
+#pragma unroll
+        for (int k = 1; k < OFF; k <<= 1) {
+            const unsigned bk = __ballot_sync(0xffffffffu, (key & k) != 0);
+            same &= (key & k) ? bk : ~bk;
+        }
+        const int slot = __popc(same & ((1u << lane) - 1u)) & (JC - 1);
+        const int c = deal ? ((slot - bank / OFF) & (JC - 1)) : 0;
+        return SmemJ<T, G>(sJ + c * JCS, (lane - OFF * c) & 31);
+    }
+}
+
 template <class T, int G, int NT, int STABLE, int JC> struct SmemLayout {
     static constexpr int FB = TileDims<G>::FB, JB = TileDims<G>::JB;
     static constexpr int QCAP = 64;  // entries of a warp's crossing-particle queue
-    // copy stride in words: a multiple of 32 plus 16 (the second copy is 16 banks over)
-    static constexpr int JCS = JC == 1 ? 3 * JB : ((3 * JB + 31) / 32) * 32 + 16;
+    // copy stride in words: a multiple of 32 plus 32/JC (copy k is 32k/JC banks over)
+    static constexpr int JCS = JC == 1 ? 3 * JB : ((3 * JB + 31) / 32) * 32 + 32 / JC;
     static constexpr size_t off_B = ((size_t)3 * FB * sizeof(T) + 127) & ~(size_t)127;
     static constexpr size_t off_J = (off_B + (size_t)3 * FB * sizeof(T) + 127) & ~(size_t)127;
     static constexpr size_t off_q = (off_J + (size_t)JC * JCS * sizeof(T) + 15) & ~(size_t)15;
@@ -1016,7 +1059,6 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* tmE, const CUtensor
     }
 
     const SmemFields<T, G> fa{sE, sB};
-    const SmemJ<T, G> ja(sJ + (lane % JC) * L::JCS);
     using FA = SmemFields<T, G>;
     using JA = SmemJ<T, G>;
     const T vscale = sizeof(T) == 4 ? T(P.fx_scale) : T(1);
@@ -1036,15 +1078,25 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* tmE, const CUtensor
         const long long base = (long long)t * S.tcap;
         const T qs = S.q * vscale;
         int run = 0;  // stayers written so far (stable variants)
-        // full deposit of queue entry e (lanes read their entries before any write)
-        auto queued_deposit = [&](int e) {
-            T oe[3], de[3];
+        // full deposit of queue entry e by this lane (have: the lane holds an
+        // entry; every lane of the warp calls it; lanes read their entries
+        // before any write)
+        auto queued_deposit = [&](int e, bool have) {
+            T oe[3] = {T(0), T(0), T(0)}, de[3] = {T(0), T(0), T(0)};
+            int ce = 0;
+            if (have) {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                oe[a] = q_od[a * L::QCAP + e];
-                de[a] = q_od[(3 + a) * L::QCAP + e];
+                for (int a = 0; a < 3; ++a) {
+                    oe[a] = q_od[a * L::QCAP + e];
+                    de[a] = q_od[(3 + a) * L::QCAP + e];
+                }
+                ce = q_cell[e];
             }
-            deposit<T, G, ORD>(ja, q_cell[e], oe, de, qs);
+            int wbase = ce + window_base<T, ORD>(oe[0], oe[0] + de[0]);
+            if (GT::AY) wbase += window_base<T, ORD>(oe[1], oe[1] + de[1]) * JA::SY;
+            if (GT::AZ) wbase += window_base<T, ORD>(oe[2], oe[2] + de[2]) * JA::SZ;
+            const JA jq = pick_copy<T, G, JC, L::JCS>(sJ, lane, have, wbase);
+            if (have) deposit<T, G, ORD>(jq, ce, oe, de, qs);
         };
         for (int i0 = 0; i0 < n; i0 += NT) {
             const int i = i0 + tid;
@@ -1054,6 +1106,7 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* tmE, const CUtensor
             bool cross = false;
             int jidx = 0;
             T o0[3], d[3];
+            int cbase = 0;  // base word of the core deposit
             if (valid) {
                 const long long slot = i < nst ? base + i : base + S.tcap - nar + (i - nst);
                 load_particle<T, G>(S.in, slot, LEAKY, p);
@@ -1061,6 +1114,10 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* tmE, const CUtensor
                 jidx = (p.ci - jox) + (GT::AY ? (p.cj - joy) * JA::SY : 0) + (GT::AZ ? (p.ck - joz) * JA::SZ : 0);
                 push_particle<T, G, ORD, PUSH>(p, fa, fidx, S, P, d);
                 cross = crosses<T, G, ORD>(p.o, d);
+                cbase = core_base<T, G, ORD>(jidx, p.o, JA::SY, JA::SZ);
+            }
+            const JA ja = pick_copy<T, G, JC, L::JCS>(sJ, lane, valid && !cross, cbase);
+            if (valid) {
                 deposit_core<T, G, ORD>(ja, jidx, p.o, d, qs, cross);
                 o0[0] = p.o[0]; o0[1] = p.o[1]; o0[2] = p.o[2];
                 move_particle<T, G, PUSH, ESC>(p, d, P, g);
@@ -1105,7 +1162,7 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* tmE, const CUtensor
             else if (valid) place_mover<T, G>(p, dest, S, P, LEAKY);
             if (qn >= 32) {
                 __syncwarp();
-                queued_deposit(lane);
+                queued_deposit(lane, true);
                 // move the remaining entries (qn - 32 < 32) to the front
                 const int rest = qn - 32;
                 int c = 0;
@@ -1127,7 +1184,7 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* tmE, const CUtensor
         }
         // the species' remaining queue (charge qs)
         __syncwarp();
-        if (lane < qn) queued_deposit(lane);
+        if (qn > 0) queued_deposit(lane, lane < qn);  // qn is warp-uniform
         __syncwarp();
         qn = 0;
         if (STABLE && tid == 0) s_cnt[s] = run;
@@ -1139,7 +1196,8 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* tmE, const CUtensor
     // of local point (a,b,c) is (t0x + a, t0y + b, t0z + c)
     for (int idx = tid; idx < 3 * L::JB; idx += NT) {
         JW v = sJ[idx];
-        if (JC == 2) v += sJ[L::JCS + idx];  // FP32: exact mod 2^32
+#pragma unroll
+        for (int k = 1; k < JC; ++k) v += sJ[k * L::JCS + idx];  // FP32: exact mod 2^32
         if (v == JW(0)) continue;
         const int comp = idx / L::JB;
         const int r = idx - comp * L::JB;
@@ -1167,7 +1225,7 @@ template <class T, int G, int NT, int STABLE, int JC> __device__ __forceinline__
 
 // One box: one CTA per tile.
 template <class T, int G, int ORD, int PUSH, int ESC, int NT, int STABLE, int JC>
-__global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (NT == 512 ? 2 : 3)) tile_kernel(const __grid_constant__ CUtensorMap tmE,
+__global__ void __launch_bounds__(NT, NT == 1024 || JC >= 4 ? 1 : (NT == 512 ? 2 : 3)) tile_kernel(const __grid_constant__ CUtensorMap tmE,
                                                    const __grid_constant__ CUtensorMap tmB, Grid g, Tiling tl,
                                                    StepP P0, SpecPack<T> SP, JWord<T>* __restrict__ J,
                                                    const StepCtx* __restrict__ ctx) {
@@ -1201,7 +1259,7 @@ template <class T> struct BatchArgs {
 };
 
 template <class T, int G, int ORD, int PUSH, int ESC, int NT, int STABLE, int JC>
-__global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (NT == 512 ? 2 : 3)) batch_tile_kernel(
+__global__ void __launch_bounds__(NT, NT == 1024 || JC >= 4 ? 1 : (NT == 512 ? 2 : 3)) batch_tile_kernel(
     const __grid_constant__ BatchArgs<T> A) {
     init_tile_barrier<T, G, NT, STABLE, JC>();
     // the claimed item goes through the layout's spare word (no static

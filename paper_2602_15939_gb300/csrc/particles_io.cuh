@@ -257,6 +257,93 @@ __global__ void regrow_kernel(PView<T> in, PView<T> out, const int* __restrict__
     if (threadIdx.x == 0) stay_out[t] = n;
 }
 
+// Regroup: tile t's particles of one buffer (stayers, then arrivals) are
+// written to the front of its range in the other buffer, ordered by cell (a
+// counting sort in shared memory; the order within a cell is arbitrary).  A
+// warp of the particle kernel then holds the particles of one or two cells:
+// its gathers read few distinct words (lanes reading one word share a pass)
+// and its adds spread over the current copies.  The order decays as particles
+// change cells, so the library repeats this every few steps.  Each array is
+// copied in its own pass (coalesced writes; the scattered reads stay within
+// the tile's range of that array, which L2 holds).  Shared memory: one counter
+// per cell and 4 bytes per slot (tcap < 65536).
+constexpr int RG_THREADS = 512;
+
+template <int G> __host__ __device__ constexpr int tile_cells() { return TileDims<G>::TX * TileDims<G>::TY * TileDims<G>::TZ; }
+
+template <class T, int G>
+__global__ void __launch_bounds__(RG_THREADS) regroup_kernel(Tiling tl, PView<T> in, PView<T> out, const int* __restrict__ stay_in,
+                                                             const int* __restrict__ arr_in, int* __restrict__ stay_out,
+                                                             long long tcap, bool has_dr) {
+    using GT = GeomT<G>;
+    using D = TileDims<G>;
+    constexpr int NCELL = tile_cells<G>();
+    static_assert(NCELL % 32 == 0 && NCELL <= 1024, "one warp scans the cell counters");
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* cnt = reinterpret_cast<int*>(smem);                       // [NCELL]
+    uint16_t* key = reinterpret_cast<uint16_t*>(cnt + NCELL);      // [tcap] local cell of input i
+    uint16_t* src = key + tcap;                                    // [tcap] input index of output j
+    const int t = blockIdx.x;
+    const int nst = stay_in[t], nar = arr_in[t], n = nst + nar;
+    const long long base = (long long)t * tcap;
+    const int ti = t % tl.ntx, tj = (t / tl.ntx) % tl.nty, tk = t / (tl.ntx * tl.nty);
+    const int t0x = ti * D::TX, t0y = tj * D::TY, t0z = tk * D::TZ;
+    auto slot = [&](int i) -> long long { return i < nst ? base + i : base + tcap - nar + (i - nst); };
+    for (int c = threadIdx.x; c < NCELL; c += RG_THREADS) cnt[c] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += RG_THREADS) {
+        int ci, cj, ck;
+        CellPack<G>::unpack(in.cell[slot(i)], ci, cj, ck);
+        int lc = ci - t0x;
+        if (GT::AY) lc += (cj - t0y) * D::TX;
+        if (GT::AZ) lc += (ck - t0z) * D::TX * D::TY;
+        lc = min(max(lc, 0), NCELL - 1);  // a tile's range holds only its own cells
+        key[i] = (uint16_t)lc;
+        atomicAdd(&cnt[lc], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive prefix of the counters, NCELL / 32 per lane
+        constexpr int PER = NCELL / 32;
+        const int lane = threadIdx.x;
+        int loc = 0;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) loc += cnt[lane * PER + k];
+        int incl = loc;
+#pragma unroll
+        for (int sh = 1; sh < 32; sh <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, sh);
+            if (lane >= sh) incl += v;
+        }
+        int run = incl - loc;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int c = cnt[lane * PER + k];
+            cnt[lane * PER + k] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += RG_THREADS) src[atomicAdd(&cnt[key[i]], 1)] = (uint16_t)i;
+    __syncthreads();
+    auto copy = [&](auto* a_in, auto* a_out) {
+        for (int j = threadIdx.x; j < n; j += RG_THREADS) a_out[base + j] = a_in[slot(src[j])];
+    };
+    copy(in.cell, out.cell);
+    copy(in.o[0], out.o[0]);
+    if (GT::AY) copy(in.o[1], out.o[1]);
+    if (GT::AZ) copy(in.o[GT::AY ? 2 : 1], out.o[GT::AY ? 2 : 1]);
+    copy(in.u[0], out.u[0]);
+    copy(in.u[1], out.u[1]);
+    copy(in.u[2], out.u[2]);
+    copy(in.id, out.id);
+    if (has_dr) {
+        copy(in.dr[0], out.dr[0]);
+        copy(in.dr[1], out.dr[1]);
+        copy(in.dr[2], out.dr[2]);
+    }
+    if (threadIdx.x == 0) stay_out[t] = n;
+}
+
 // Copy the first *count_in entries of a loose list (at most lcap_in).
 template <class T, int G>
 __global__ void copy_loose_kernel(PView<T> in, PView<T> out, const int* __restrict__ count_in, long long lcap_in,

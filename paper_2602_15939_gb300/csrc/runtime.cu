@@ -71,13 +71,14 @@ template <class T, int G, int V> static size_t smem_v() {
 }
 
 template <class T, int G> static size_t tile_smem_bytes_t(int v) {
-    static_assert(N_TILE_VARIANTS == 6, "one entry per tile variant");
+    static_assert(N_TILE_VARIANTS == 7, "one entry per tile variant");
     switch (v) {
         case 0: return smem_v<T, G, 0>();
         case 1: return smem_v<T, G, 1>();
         case 2: return smem_v<T, G, 2>();
         case 3: return smem_v<T, G, 3>();
         case 4: return smem_v<T, G, 4>();
+        case 6: return smem_v<T, G, 6>();
         default: return smem_v<T, G, 5>();
     }
 }
@@ -92,6 +93,11 @@ static size_t tile_smem_bytes(bool fp64, int geom, int v) {
 // Variant used when the configuration leaves the choice to the library
 // (pic_autotune refines it for a given box).
 static int default_variant(bool fp64, int geom) { return default_tile_variant(fp64, geom); }
+
+// Steps between regroups of the particles by cell (0: never).  FP64 boxes do
+// not regroup: the order of their current's floating-point adds would then
+// vary from run to run.
+static int default_regroup_interval(bool fp64, int geom) { return fp64 ? 0 : (geom == 0 ? 4 : 0); }
 
 struct pic_handle {
     pic_config cfg;
@@ -136,6 +142,8 @@ struct pic_handle {
     bool own_stream = false;
     bool batched = false;  // stepped by a pic_batch; pic_step refuses
     int since_check = 0;   // steps since the last tile-capacity check
+    int regroup_every = 0;  // regroup the particles by cell every this many steps (0: never)
+    int since_regroup = 0;  // steps since the last regroup (or load)
     long long regrows = 0; // tile re-layouts so far
     // asynchronous occupancy snapshot: per species [stay x ntiles, arrivals x
     // ntiles, loose count] of the buffer current when it was taken
@@ -522,7 +530,49 @@ template <class T, int G> static pic_status post_particle_t(pic_handle* h, const
     return PIC_OK;
 }
 
+// Regroup every species' tiles by cell into the other buffer (see
+// regroup_kernel); a species whose slots per tile exceed the sort's shared
+// memory is copied in order instead.  Loose lists move along.
+template <class T, int G> static pic_status regroup_t(pic_handle* h) {
+    const int b = h->buf, o = 1 - b;
+    const bool leaky = h->esc == ESC_DISP;
+    const int nt = h->tl.ntiles;
+    prof_begin(h);
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
+        DevSpecies& d = h->sp[s];
+        if (!d.loaded) continue;
+        const PView<T> vin = view_of<T>(d.arr[b]), vout = view_of<T>(d.arr[o]);
+        const size_t sm = sizeof(int) * tile_cells<G>() + 4 * (size_t)d.tcap;
+        if (d.tcap < 65536 && sm <= MAX_SMEM) {  // the attribute is set by pic_init (regroup_attr_t)
+            regroup_kernel<T, G><<<nt, RG_THREADS, sm, h->stream>>>(h->tl, vin, vout, d.stay[b], d.arrv[b], d.stay[o], d.tcap,
+                                                                   leaky);
+        } else {
+            regrow_kernel<T, G><<<nt, NTHR, 0, h->stream>>>(vin, vout, d.stay[b], d.arrv[b], d.tcap, d.tcap, d.stay[o], leaky);
+        }
+        CK(cudaMemsetAsync(d.arrv[b], 0, sizeof(int) * nt, h->stream));
+        copy_loose_kernel<T, G><<<64, NTHR, 0, h->stream>>>(view_of<T>(d.larr[b]), view_of<T>(d.larr[o]), d.lcount + b, d.lcap,
+                                                            d.lcount + o, leaky);
+        CK(cudaMemsetAsync(d.lcount + b, 0, sizeof(int), h->stream));
+        h->prof.launches += 2;
+    }
+    prof_end(h, 1);
+    CK(cudaGetLastError());
+    h->buf = o;
+    return PIC_OK;
+}
+
+template <class T, int G> static pic_status regroup_attr_t(pic_handle* h) {
+    CK(cudaFuncSetAttribute(regroup_kernel<T, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MAX_SMEM));
+    return PIC_OK;
+}
+
 template <class T, int G> static pic_status step_t(pic_handle* h) {
+    if (h->regroup_every > 0 && h->since_regroup >= h->regroup_every) {
+        pic_status st = regroup_t<T, G>(h);
+        if (st != PIC_OK) return st;
+        h->since_regroup = 0;
+    }
+    h->since_regroup += 1;
     pic_status st = pre_particle(h);
     if (st != PIC_OK) return st;
     StepP P;
@@ -699,6 +749,7 @@ static pic_status load_t(pic_handle* h, int species, long long n, const double* 
     dfree(h, cnt);
     d.n = n;
     d.loaded = true;
+    h->since_regroup = 0;  // loads leave each tile grouped by cell or freshly ordered
     return PIC_OK;
 }
 
@@ -876,6 +927,7 @@ template <class T, int G> static pic_status maxwellian_t(pic_handle* h, int spec
     CK(cudaGetLastError());
     d.n = n;
     d.loaded = true;
+    h->since_regroup = 0;  // loads leave each tile grouped by cell or freshly ordered
     return PIC_OK;
 }
 
@@ -1095,6 +1147,8 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
     h->own_stream = true;
     if (cudaFuncSetAttribute(h->tile_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_bytes) != cudaSuccess)
         return bail(fail(h, PIC_ERR_CUDA, "cannot set %zu bytes of dynamic shared memory", h->smem_bytes));
+    if (DISPATCH(h, regroup_attr_t, h) != PIC_OK) return bail(PIC_ERR_CUDA);
+    h->regroup_every = default_regroup_interval(h->fp64, h->geom);
     const size_t fb = (size_t)3 * g.cstride * h->esz;
     void** bufs[] = {&h->E, &h->B, &h->J, &h->Jtmp};
     for (void** p : bufs) {
@@ -1278,20 +1332,29 @@ static pic_status check_error_word(pic_handle* h) {
 // into a CUDA graph; all per-step scalars come from the device context, so
 // the graph is replayed unchanged for every later pair of steps.  On any
 // capture failure graphs are switched off for this handle.
-static pic_status capture_pair(pic_handle* h) {
+// Steps per captured graph: a regroup and the steps up to the next one, or a
+// pair of steps.
+static int graph_cycle(const pic_handle* h) { return h->regroup_every > 0 ? h->regroup_every : 2; }
+
+// Capture one cycle of steps starting from buffer h->buf (with the regroup
+// due, when regroups are on) as the graph of that buffer.
+static pic_status capture_cycle(pic_handle* h) {
     const int b0 = h->buf;
     const long long s0 = h->step, l0 = h->prof.launches;
+    const int r0 = h->since_regroup;
+    const int ncyc = graph_cycle(h);
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         h->graphs_on = false;
         cudaGetLastError();
         return PIC_OK;
     }
-    pic_status st = DISPATCH(h, step_t, h);
-    if (st == PIC_OK) st = DISPATCH(h, step_t, h);
+    pic_status st = PIC_OK;
+    for (int k = 0; k < ncyc && st == PIC_OK; ++k) st = DISPATCH(h, step_t, h);
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     h->buf = b0;
     h->step = s0;
+    h->since_regroup = r0;
     h->graph_kernels = h->prof.launches - l0;
     h->prof.launches = l0;
     if (st != PIC_OK || e != cudaSuccess || !graph) {
@@ -1377,18 +1440,24 @@ pic_status pic_step(pic_handle* h, int nsteps) {
             pic_status st = capacity_check(h);
             if (st != PIC_OK) return st;
         }
-        if (h->graphs_on && !h->prof.on && nsteps >= 2) {
+        const int ncyc = graph_cycle(h);
+        const bool due = h->regroup_every == 0 || h->since_regroup >= h->regroup_every;
+        if (h->graphs_on && !h->prof.on && nsteps >= ncyc && due) {
             const int b0 = h->buf;
             if (!h->graph_ok[b0]) {
-                pic_status st = capture_pair(h);
+                pic_status st = capture_cycle(h);
                 if (st != PIC_OK) return st;
             }
             if (h->graph_ok[b0]) {
                 CK(cudaGraphLaunch(h->gexec[b0], h->stream));
-                h->step += 2;
-                h->since_check += 2;
+                h->step += ncyc;
+                h->since_check += ncyc;
+                if (h->regroup_every > 0) {
+                    h->since_regroup = ncyc;
+                    h->buf = (ncyc + 1) % 2 ? 1 - b0 : b0;  // one flip per step and one for the regroup
+                }
                 h->prof.launches += h->graph_kernels;
-                nsteps -= 2;
+                nsteps -= ncyc;
                 continue;
             }
         }
@@ -1405,6 +1474,23 @@ pic_status pic_set_capacity_check(pic_handle* h, int32_t every, int32_t block) {
     if (every < 0) return fail(h, PIC_ERR_ARG, "check interval must be >= 0");
     h->check_every = every;
     h->check_block = block != 0;
+    return PIC_OK;
+}
+
+pic_status pic_set_regroup_interval(pic_handle* h, int32_t every) {
+    if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    if (every < 0) return fail(h, PIC_ERR_ARG, "regroup interval must be >= 0");
+    if (every == h->regroup_every) return PIC_OK;
+    cudaSetDevice(h->cfg.device);
+    CK(cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    h->regroup_every = every;
+    return PIC_OK;
+}
+
+pic_status pic_get_regroup_interval(pic_handle* h, int32_t* every) {
+    if (!h || !every) return fail(h, PIC_ERR_ARG, "NULL argument");
+    *every = h->regroup_every;
     return PIC_OK;
 }
 

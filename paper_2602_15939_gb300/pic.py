@@ -117,6 +117,8 @@ _SIGS = {
     "pic_rebalance": (C.c_int, [_H, C.c_int32, C.POINTER(C.c_int32)]),
     "pic_set_capacity_check": (C.c_int, [_H, C.c_int32, C.c_int32]),
     "pic_get_capacity": (C.c_int, [_H, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "pic_set_regroup_interval": (C.c_int, [_H, C.c_int32]),
+    "pic_get_regroup_interval": (C.c_int, [_H, C.POINTER(C.c_int32)]),
     "pic_kernel_variant_count": (C.c_int, []),
     "pic_kernel_variant_info": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pic_get_kernel_variant": (C.c_int, [_H, C.POINTER(C.c_int32)]),
@@ -316,6 +318,16 @@ def pic_get_capacity(h, species: int):
     a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
     _check(h, lib().pic_get_capacity(h, species, C.byref(a), C.byref(b), C.byref(c)))
     return a.value, b.value, c.value
+
+
+def pic_set_regroup_interval(h, every: int):
+    _check(h, lib().pic_set_regroup_interval(h, every))
+
+
+def pic_get_regroup_interval(h) -> int:
+    k = C.c_int32()
+    _check(h, lib().pic_get_regroup_interval(h, C.byref(k)))
+    return k.value
 
 
 def pic_preload_kernels(device=0, precision=None):

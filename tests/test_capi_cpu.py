@@ -58,9 +58,9 @@ def test_null_handle_calls_fail_cleanly():
 
 def test_kernel_variant_table():
     n = P.pic_kernel_variant_count()
-    assert n == 6
+    assert n == 7
     shapes = [P.pic_kernel_variant_info(k) for k in range(1, n + 1)]
-    assert shapes == [(256, 0, 1), (512, 0, 1), (512, 1, 1), (256, 1, 1), (256, 0, 2), (256, 1, 2)]
+    assert shapes == [(256, 0, 1), (512, 0, 1), (512, 1, 1), (256, 1, 1), (256, 0, 2), (256, 1, 2), (512, 0, 4)]
     for bad in (0, n + 1):
         with pytest.raises(P.PicError):
             P.pic_kernel_variant_info(bad)
