@@ -329,10 +329,11 @@ def run_gb300(args):
                        "shape_order": w.order, "box": "expanding", "expansion_rate_wp": list(w.rate_wp),
                        "precision": "int32 cell + fp32 offsets/momenta, fp64 l(t)",
                        "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}",
-                       "kernel_variant": tune},
+                       "kernel_variant": tune, "regroup_every": P.pic_get_regroup_interval(box.h)},
             "particle_phase": {"value": npart / (particle_ms / 1e3), "unit": UNIT, "avg_launch_ms": particle_ms},
             "profile_ms_per_step": {"particle": prof.ms_particle / args.steps, "field": prof.ms_field / args.steps,
-                                    "other": prof.ms_other / args.steps},
+                                    "other": prof.ms_other / args.steps,
+                                    "other_is": "loose kernel, tile bookkeeping, regroup by cell"},
             "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks}
 
     # FP64 path on the same workload (the plain FP64 method), a few steps

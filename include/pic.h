@@ -242,7 +242,7 @@ pic_status pic_get_capacity(pic_handle *h, int species, int64_t *slots_per_tile,
  * counting sort per tile: one read and one write of the particle arrays).
  * Warps of the particle kernel then hold particles of one or two cells, which
  * makes their field reads and current adds conflict less in shared memory;
- * the order decays as particles change cells.  Default: 4 for 3D FP32 boxes,
+ * the order decays as particles change cells.  Default: 3 for 3D FP32 boxes,
  * 0 otherwise (FP64 boxes should keep 0: the order of their current's
  * floating-point adds, and so its last bits, would vary from run to run).
  * FP32 results are bit-identical for every interval.  Not a part of the

@@ -268,6 +268,7 @@ __global__ void regrow_kernel(PView<T> in, PView<T> out, const int* __restrict__
 // the tile's range of that array, which L2 holds).  Shared memory: one counter
 // per cell and 4 bytes per slot (tcap < 65536).
 constexpr int RG_THREADS = 512;
+constexpr int RG_UNROLL = 8;
 
 template <int G> __host__ __device__ constexpr int tile_cells() { return TileDims<G>::TX * TileDims<G>::TY * TileDims<G>::TZ; }
 
@@ -291,15 +292,28 @@ __global__ void __launch_bounds__(RG_THREADS) regroup_kernel(Tiling tl, PView<T>
     auto slot = [&](int i) -> long long { return i < nst ? base + i : base + tcap - nar + (i - nst); };
     for (int c = threadIdx.x; c < NCELL; c += RG_THREADS) cnt[c] = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += RG_THREADS) {
-        int ci, cj, ck;
-        CellPack<G>::unpack(in.cell[slot(i)], ci, cj, ck);
-        int lc = ci - t0x;
-        if (GT::AY) lc += (cj - t0y) * D::TX;
-        if (GT::AZ) lc += (ck - t0z) * D::TX * D::TY;
-        lc = min(max(lc, 0), NCELL - 1);  // a tile's range holds only its own cells
-        key[i] = (uint16_t)lc;
-        atomicAdd(&cnt[lc], 1);
+    // RG_UNROLL independent loads per thread at a time: one tile's CTA must
+    // keep many loads in flight for the copy to run near HBM speed
+    for (int i0 = threadIdx.x; i0 < n; i0 += RG_THREADS * RG_UNROLL) {
+        int w[RG_UNROLL];
+#pragma unroll
+        for (int u = 0; u < RG_UNROLL; ++u) {
+            const int i = i0 + u * RG_THREADS;
+            w[u] = i < n ? in.cell[slot(i)] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < RG_UNROLL; ++u) {
+            const int i = i0 + u * RG_THREADS;
+            if (i >= n) break;
+            int ci, cj, ck;
+            CellPack<G>::unpack(w[u], ci, cj, ck);
+            int lc = ci - t0x;
+            if (GT::AY) lc += (cj - t0y) * D::TX;
+            if (GT::AZ) lc += (ck - t0z) * D::TX * D::TY;
+            lc = min(max(lc, 0), NCELL - 1);  // a tile's range holds only its own cells
+            key[i] = (uint16_t)lc;
+            atomicAdd(&cnt[lc], 1);
+        }
     }
     __syncthreads();
     if (threadIdx.x < 32) {  // exclusive prefix of the counters, NCELL / 32 per lane
@@ -325,8 +339,20 @@ __global__ void __launch_bounds__(RG_THREADS) regroup_kernel(Tiling tl, PView<T>
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += RG_THREADS) src[atomicAdd(&cnt[key[i]], 1)] = (uint16_t)i;
     __syncthreads();
-    auto copy = [&](auto* a_in, auto* a_out) {
-        for (int j = threadIdx.x; j < n; j += RG_THREADS) a_out[base + j] = a_in[slot(src[j])];
+    auto copy = [&](const auto* a_in, auto* a_out) {
+        for (int j0 = threadIdx.x; j0 < n; j0 += RG_THREADS * RG_UNROLL) {
+            typename std::remove_pointer<decltype(a_out)>::type v[RG_UNROLL];
+#pragma unroll
+            for (int u = 0; u < RG_UNROLL; ++u) {
+                const int j = j0 + u * RG_THREADS;
+                if (j < n) v[u] = a_in[slot(src[j])];
+            }
+#pragma unroll
+            for (int u = 0; u < RG_UNROLL; ++u) {
+                const int j = j0 + u * RG_THREADS;
+                if (j < n) a_out[base + j] = v[u];
+            }
+        }
     };
     copy(in.cell, out.cell);
     copy(in.o[0], out.o[0]);

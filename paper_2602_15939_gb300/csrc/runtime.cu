@@ -97,7 +97,7 @@ static int default_variant(bool fp64, int geom) { return default_tile_variant(fp
 // Steps between regroups of the particles by cell (0: never).  FP64 boxes do
 // not regroup: the order of their current's floating-point adds would then
 // vary from run to run.
-static int default_regroup_interval(bool fp64, int geom) { return fp64 ? 0 : (geom == 0 ? 4 : 0); }
+static int default_regroup_interval(bool fp64, int geom) { return fp64 ? 0 : (geom == 0 ? 3 : 0); }
 
 struct pic_handle {
     pic_config cfg;
