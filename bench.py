@@ -34,6 +34,9 @@ METRIC = "particle-steps/s (gather+push+deposit), FP32 vs FP64; ensemble p99 lat
 UNIT = "particle-steps/s"
 
 
+BOX_NAMES = {0: "periodic", 1: "shearing", 2: "expanding", 3: "leaky"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -326,8 +329,9 @@ def run_gb300(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if w.fp64 else "f32", "data": "synthetic",
             "config": {"workload": w.name, "grid": list(w.n), "ppc_per_species": w.ppc, "particles": npart,
-                       "shape_order": w.order, "box": "expanding", "expansion_rate_wp": list(w.rate_wp),
-                       "precision": "int32 cell + fp32 offsets/momenta, fp64 l(t)",
+                       "shape_order": w.order, "box": BOX_NAMES.get(w.box, str(w.box)), "expansion_rate_wp": list(w.rate_wp),
+                       "precision": ("int32 cell + fp64 offsets/momenta" if w.fp64 else
+                                     "int32 cell + fp32 offsets/momenta, fp64 l(t)"),
                        "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}",
                        "kernel_variant": tune, "regroup_every": P.pic_get_regroup_interval(box.h)},
             "particle_phase": {"value": npart / (particle_ms / 1e3), "unit": UNIT, "avg_launch_ms": particle_ms},

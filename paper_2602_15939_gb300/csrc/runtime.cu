@@ -1767,6 +1767,8 @@ struct pic_batch {
     std::vector<int> nwork[2];
     int* counters = nullptr;  // work counters, one per launch
     int phase = 0;
+    int regroup_every = 0;  // regroup every box by cell every this many steps (0: never)
+    int since_regroup = 0;
     bool graphs_on = true;
     bool graph_ok[2] = {false, false};
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -1837,6 +1839,16 @@ pic_status batch_join(pic_batch* B) {
 
 template <class T, int G> pic_status batch_step_t(pic_batch* B) {
     using A_t = BatchArgs<T>;
+    if (B->regroup_every > 0 && B->since_regroup >= B->regroup_every) {
+        // every box flips its buffer, so the batch changes phase
+        pic_status st = batch_fork(B);
+        for (size_t i = 0; i < B->box.size() && st == PIC_OK; ++i) st = regroup_t<T, G>(B->box[i]);
+        if (st == PIC_OK) st = batch_join(B);
+        if (st != PIC_OK) return st;
+        B->phase ^= 1;
+        B->since_regroup = 0;
+    }
+    B->since_regroup += 1;
     const int ph = B->phase;
     pic_status st = batch_fork(B);
     for (size_t i = 0; i < B->box.size() && st == PIC_OK; ++i) st = pre_particle(B->box[i]);
@@ -1883,10 +1895,16 @@ void batch_drop_graphs(pic_batch* B) {
     }
 }
 
-// Capture two steps from the current phase into one graph (the boxes' state
-// is put back: capturing runs nothing).
+// Steps per captured batch graph: a regroup and the steps up to the next
+// one, or a pair of steps.
+int batch_cycle(const pic_batch* B) { return B->regroup_every > 0 ? B->regroup_every : 2; }
+
+// Capture one cycle of steps from the current phase (with the regroup due,
+// when regroups are on) into one graph (the boxes' state is put back:
+// capturing runs nothing).
 pic_status batch_capture(pic_batch* B) {
     const int ph0 = B->phase;
+    const int r0 = B->since_regroup;
     std::vector<int> buf0;
     std::vector<long long> step0, l0;
     for (pic_handle* h : B->box) {
@@ -1900,10 +1918,11 @@ pic_status batch_capture(pic_batch* B) {
         B->graphs_on = false;
         return PIC_OK;
     }
-    pic_status st = BDISPATCH(B, batch_step_t, B);
-    if (st == PIC_OK) st = BDISPATCH(B, batch_step_t, B);
+    pic_status st = PIC_OK;
+    for (int k = 0; k < batch_cycle(B) && st == PIC_OK; ++k) st = BDISPATCH(B, batch_step_t, B);
     cudaError_t e = cudaStreamEndCapture(B->stream, &graph);
     B->phase = ph0;
+    B->since_regroup = r0;
     for (size_t i = 0; i < B->box.size(); ++i) {
         B->box[i]->buf = buf0[i];
         B->box[i]->step = step0[i];
@@ -1983,6 +2002,7 @@ pic_status pic_batch_create(pic_handle* const* boxes, int32_t n, pic_batch** out
         return batch_fail(PIC_ERR_CUDA, "pic_batch_create: the batched kernel cannot be launched");
     }
     B->max_grid = sms * per_sm;
+    B->regroup_every = default_regroup_interval(B->fp64, B->geom);
     // every box's queued work ends before the batch takes over
     for (int i = 0; i < n; ++i) cudaStreamSynchronize(boxes[i]->stream);
     int K = std::min(n, 16);  // parallel branches for the boxes' own kernels
@@ -2029,7 +2049,9 @@ pic_status pic_batch_step(pic_batch* B, int32_t nsteps) {
     if (nsteps < 0) return batch_fail(PIC_ERR_ARG, "pic_batch_step: nsteps must be >= 0");
     cudaSetDevice(B->device);
     while (nsteps > 0) {
-        if (B->graphs_on && nsteps >= 2) {
+        const int ncyc = batch_cycle(B);
+        const bool due = B->regroup_every == 0 || B->since_regroup >= B->regroup_every;
+        if (B->graphs_on && nsteps >= ncyc && due) {
             const int ph = B->phase;
             if (!B->graph_ok[ph]) {
                 pic_status st = batch_capture(B);
@@ -2038,8 +2060,15 @@ pic_status pic_batch_step(pic_batch* B, int32_t nsteps) {
             if (B->graph_ok[ph]) {
                 if (cudaGraphLaunch(B->gexec[ph], B->stream) != cudaSuccess)
                     return batch_fail(PIC_ERR_CUDA, "pic_batch_step: graph launch failed");
-                for (pic_handle* h : B->box) h->step += 2;  // two buffer flips: buf unchanged
-                nsteps -= 2;
+                // one buffer flip per step, and one for the regroup
+                const int flips = ncyc + (B->regroup_every > 0 ? 1 : 0);
+                for (pic_handle* h : B->box) {
+                    h->step += ncyc;
+                    h->buf ^= flips & 1;
+                }
+                B->phase ^= flips & 1;
+                if (B->regroup_every > 0) B->since_regroup = ncyc;
+                nsteps -= ncyc;
                 continue;
             }
         }
@@ -2047,6 +2076,17 @@ pic_status pic_batch_step(pic_batch* B, int32_t nsteps) {
         if (st != PIC_OK) return st;
         nsteps -= 1;
     }
+    return PIC_OK;
+}
+
+pic_status pic_batch_set_regroup_interval(pic_batch* B, int32_t every) {
+    if (!B) return batch_fail(PIC_ERR_ARG, "pic_batch_set_regroup_interval: batch is NULL");
+    if (every < 0) return batch_fail(PIC_ERR_ARG, "pic_batch_set_regroup_interval: interval must be >= 0");
+    if (every == B->regroup_every) return PIC_OK;
+    cudaSetDevice(B->device);
+    if (cudaStreamSynchronize(B->stream) != cudaSuccess) return batch_fail(PIC_ERR_CUDA, "pic_batch_set_regroup_interval: sync failed");
+    batch_drop_graphs(B);
+    B->regroup_every = every;
     return PIC_OK;
 }
 

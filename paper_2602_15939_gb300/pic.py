@@ -125,6 +125,7 @@ _SIGS = {
     "pic_set_kernel_variant": (C.c_int, [_H, C.c_int32]),
     "pic_batch_create": (C.c_int, [C.POINTER(_H), C.c_int32, C.POINTER(_H)]),
     "pic_batch_step": (C.c_int, [_H, C.c_int32]),
+    "pic_batch_set_regroup_interval": (C.c_int, [_H, C.c_int32]),
     "pic_batch_synchronize": (C.c_int, [_H]),
     "pic_batch_destroy": (C.c_int, [_H]),
     "pic_batch_max_boxes_per_launch": (C.c_int32, [C.c_int32]),
@@ -380,6 +381,9 @@ class Batch:
 
     def step(self, n=1):
         _check(None, lib().pic_batch_step(self.b, n))
+
+    def set_regroup_interval(self, every: int):
+        _check(None, lib().pic_batch_set_regroup_interval(self.b, every))
 
     def sync(self):
         _check(None, lib().pic_batch_synchronize(self.b))

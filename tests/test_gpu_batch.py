@@ -101,6 +101,28 @@ def test_fp32_batch_equals_boxes_alone(cases):
 
 
 @pytest.mark.gpu
+def test_fp32_batch_regroup_cycles_equal_boxes_alone():
+    # 3D FP32 batches regroup every 3 steps: plain steps, then graph-replayed
+    # cycles (a regroup and three steps), then a tail; and with regrouping off
+    n = 14
+    got = run_batched(EXPAND, n, False, chunks=[2, 9, 3])
+    alone = [run_alone(c, n, False) for c in EXPAND]
+    for g, a in zip(got, alone):
+        assert_same(g, a, exact=True)
+    loaded = [load(c, False) for c in EXPAND]
+    try:
+        with P.Batch([b for b, _ in loaded]) as bt:
+            bt.set_regroup_interval(0)
+            bt.step(n)
+            bt.sync()
+        for (b, nsp), a in zip(loaded, alone):
+            assert_same(state(b, nsp), a, exact=True)
+    finally:
+        for b, _ in loaded:
+            b.close()
+
+
+@pytest.mark.gpu
 def test_fp64_batch_equals_boxes_alone():
     got = run_batched(EXPAND, 3, True)
     for c, g in zip(EXPAND, got):
