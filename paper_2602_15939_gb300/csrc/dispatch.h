@@ -9,7 +9,7 @@ namespace pic {
 struct KernelSet {
     const void* tile[7];  // one per TILE_VARIANTS entry
     const void* loose;
-    const void* batch;    // batched launch, variant default_tile_variant
+    const void* batch;    // batched launch, variant batch_tile_variant
 };
 
 KernelSet lookup_f32_g0(int ord, int push, int esc);

@@ -1839,19 +1839,20 @@ pic_status batch_join(pic_batch* B) {
 
 template <class T, int G> pic_status batch_step_t(pic_batch* B) {
     using A_t = BatchArgs<T>;
-    if (B->regroup_every > 0 && B->since_regroup >= B->regroup_every) {
-        // every box flips its buffer, so the batch changes phase
-        pic_status st = batch_fork(B);
-        for (size_t i = 0; i < B->box.size() && st == PIC_OK; ++i) st = regroup_t<T, G>(B->box[i]);
-        if (st == PIC_OK) st = batch_join(B);
-        if (st != PIC_OK) return st;
+    // a regroup, when due, runs in each box's branch before its step context;
+    // every box flips its buffer, so the batch changes phase
+    const bool regroup = B->regroup_every > 0 && B->since_regroup >= B->regroup_every;
+    if (regroup) {
         B->phase ^= 1;
         B->since_regroup = 0;
     }
     B->since_regroup += 1;
     const int ph = B->phase;
     pic_status st = batch_fork(B);
-    for (size_t i = 0; i < B->box.size() && st == PIC_OK; ++i) st = pre_particle(B->box[i]);
+    for (size_t i = 0; i < B->box.size() && st == PIC_OK; ++i) {
+        if (regroup) st = regroup_t<T, G>(B->box[i]);
+        if (st == PIC_OK) st = pre_particle(B->box[i]);
+    }
     if (st == PIC_OK) st = batch_join(B);
     if (st != PIC_OK) return st;
     // one launch per group of boxes, the groups side by side
@@ -1991,7 +1992,7 @@ pic_status pic_batch_create(pic_handle* const* boxes, int32_t n, pic_batch** out
     B->fp64 = h0->fp64;
     B->geom = h0->geom;
     B->kern = h0->ks.batch;
-    const int v = default_tile_variant(B->fp64, B->geom);
+    const int v = batch_tile_variant(B->fp64, B->geom);
     B->nt = TILE_VARIANTS[v].nt;
     B->smem = tile_smem_bytes(B->fp64, B->geom, v);
     int sms = 0, per_sm = 0;
