@@ -112,3 +112,54 @@ def test_regroup_interval_arguments():
         assert P.pic_get_regroup_interval(box.h) == 0  # FP64 default
     finally:
         box.close()
+
+
+def run_species(cfg, sp, every, nsteps):
+    box = P.Box(cfg)
+    try:
+        P.pic_set_regroup_interval(box.h, every)
+        n = (cfg.nx, cfg.ny, cfg.nz)
+        z = np.zeros((3, n[2], n[1], n[0]))
+        box.set_fields(z, z)
+        for i, d in enumerate(sp):
+            box.load(i, d["q"], d["m"], d["x"], d["u"], d["id"])
+        box.step(nsteps)
+        out = []
+        for i in range(len(sp)):
+            x, u, ids, _ = box.particles(i)
+            o = np.argsort(ids)
+            out.append((x[o], u[o], ids[o]))
+        return out, box.fields(), box.diagnostics(), P.pic_get_capacity(box.h, 0)
+    finally:
+        box.close()
+
+
+@pytest.mark.gpu
+def test_regroup_edge_cases_empty_tiles_and_oversized_tiles():
+    # (a) half the tiles empty: particles only in x < 8 of a 16-cell box
+    n = (16, 8, 8)
+    cfg = P.make_config(box=BOX_P, nx=n[0], ny=n[1], nz=n[2], ndim=3, order=2, precision=P.PIC_FP32)
+    sp = [dict(q=-0.05, m=1.0, x=np.random.default_rng(3).uniform(0, 1, (4000, 3)) * [8, 8, 8],
+               u=np.random.default_rng(4).normal(0, 0.05, (4000, 3)), id=np.arange(4000, dtype=np.uint32))]
+    a = run_species(cfg, sp, 0, 7)
+    b = run_species(cfg, sp, 1, 7)
+    assert a[2].error_word == 0 and b[2].error_word == 0
+    for (xa, ua, ia), (xb, ub, ib) in zip(a[0], b[0]):
+        assert np.array_equal(ia, ib) and np.array_equal(xa, xb) and np.array_equal(ua, ub)
+    for x, y in zip(a[1], b[1]):
+        assert np.array_equal(x, y)
+    # (b) one 8^3 tile holding more slots than the in-shared-memory sort takes
+    # (tcap >= 65536): the regroup copies that species in order instead
+    cfg = P.make_config(box=BOX_P, nx=8, ny=8, nz=8, ndim=3, order=1, precision=P.PIC_FP32)
+    N = 512 * 130
+    r = np.random.default_rng(5)
+    sp = [dict(q=-0.01, m=1.0, x=r.uniform(0, 8, (N, 3)), u=r.normal(0, 0.05, (N, 3)),
+               id=np.arange(N, dtype=np.uint32))]
+    a = run_species(cfg, sp, 0, 4)
+    b = run_species(cfg, sp, 1, 4)
+    assert b[3][0] >= 65536  # slots per tile
+    assert a[2].error_word == 0 and b[2].error_word == 0
+    for (xa, ua, ia), (xb, ub, ib) in zip(a[0], b[0]):
+        assert np.array_equal(ia, ib) and np.array_equal(xa, xb) and np.array_equal(ua, ub)
+    for x, y in zip(a[1], b[1]):
+        assert np.array_equal(x, y)
