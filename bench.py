@@ -526,7 +526,9 @@ def run_e2e(w, device, stream, steps, rank):
         ti.numpy()[:] = d["id"].view(np.int32)
         pinned.append((d["q"], tx, tu, ti))
     del sp
-    outs = [(torch.empty_like(tx), torch.empty_like(tu), torch.empty_like(ti)) for _, tx, tu, ti in pinned]
+    # pinned like the inputs (empty_like would give pageable memory)
+    outs = [(torch.empty(tx.shape, dtype=tx.dtype, pin_memory=True), torch.empty(tu.shape, dtype=tu.dtype, pin_memory=True),
+             torch.empty(ti.shape, dtype=ti.dtype, pin_memory=True)) for _, tx, tu, ti in pinned]
     cfg = P.make_config(precision=P.PIC_FP64 if w.fp64 else P.PIC_FP32, device=device, **w.config_kwargs())
     box = P.Box(cfg)
     P.pic_set_stream(box.h, stream.cuda_stream)

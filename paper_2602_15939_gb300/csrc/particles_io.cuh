@@ -22,8 +22,7 @@ template <class T> __device__ inline void split_coord(double x, int n, int& c, T
 
 // Pass 1 of a load: per particle, its tile; per tile, a count.
 template <class T, int G>
-__global__ void load_bin_kernel(long long n, const double* __restrict__ x, Tiling tl, Grid g, int* __restrict__ tile_of_p,
-                                int* __restrict__ count) {
+__global__ void load_bin_kernel(long long n, const double* __restrict__ x, Tiling tl, Grid g, int* __restrict__ count) {
     using GT = GeomT<G>;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         int ci, cj = 0, ck = 0;
@@ -31,19 +30,17 @@ __global__ void load_bin_kernel(long long n, const double* __restrict__ x, Tilin
         split_coord<T>(x[3 * q + 0], g.nx, ci, o);
         if (GT::AY) split_coord<T>(x[3 * q + 1], g.ny, cj, o);
         if (GT::AZ) split_coord<T>(x[3 * q + 2], g.nz, ck, o);
-        int t = tile_of<G>(tl, ci, cj, ck);
-        tile_of_p[q] = t;
-        atomicAdd(count + t, 1);
+        atomicAdd(count + tile_of<G>(tl, ci, cj, ck), 1);
     }
 }
 
 // Pass 2: write each particle to a slot of its tile (order within a tile is
 // arbitrary).
 template <class T, int G>
-__global__ void load_scatter_kernel(long long n, const double* __restrict__ x, const double* __restrict__ u,
-                                    const uint32_t* __restrict__ id, const double* __restrict__ dr, Grid g,
-                                    const int* __restrict__ tile_of_p, int* __restrict__ fill, long long tcap, PView<T> v,
-                                    bool has_dr) {
+__global__ void load_scatter_kernel(long long n, long long q0, const double* __restrict__ x, const double* __restrict__ u,
+                                    const uint32_t* __restrict__ id, const double* __restrict__ dr, Tiling tl, Grid g,
+                                    int* __restrict__ fill, long long tcap, PView<T> v, bool has_dr) {
+    // particles q0 + q of the caller's arrays (x, u, id, dr hold q = 0..n-1)
     using GT = GeomT<G>;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         Particle<T> p;
@@ -52,13 +49,13 @@ __global__ void load_scatter_kernel(long long n, const double* __restrict__ x, c
         if (GT::AY) split_coord<T>(x[3 * q + 1], g.ny, p.cj, p.o[1]); else p.o[1] = T(0.5);
         if (GT::AZ) split_coord<T>(x[3 * q + 2], g.nz, p.ck, p.o[2]); else p.o[2] = T(0.5);
         p.u[0] = T(u[3 * q]); p.u[1] = T(u[3 * q + 1]); p.u[2] = T(u[3 * q + 2]);
-        p.id = id ? id[q] : (uint32_t)q;
+        p.id = id ? id[q] : (uint32_t)(q0 + q);
         if (has_dr) {
             p.dr[0] = dr ? T(dr[3 * q]) : T(0);
             p.dr[1] = dr ? T(dr[3 * q + 1]) : T(0);
             p.dr[2] = dr ? T(dr[3 * q + 2]) : T(0);
         }
-        int t = tile_of_p[q];
+        int t = tile_of<G>(tl, p.ci, p.cj, p.ck);
         int s = atomicAdd(fill + t, 1);
         store_particle<T, G>(v, (long long)t * tcap + s, has_dr, p);
     }
@@ -116,16 +113,18 @@ __global__ void maxwellian_kernel(Tiling tl, Grid g, int ppc, double theta, doub
 // offset off[t]: absolute positions, momenta, ids, displacements.
 template <class T, int G>
 __global__ void compact_kernel(Tiling tl, Grid g, PView<T> v, const int* __restrict__ stay, const int* __restrict__ arr,
-                               long long tcap, const long long* __restrict__ off, bool has_dr, double* __restrict__ x,
-                               double* __restrict__ u, uint32_t* __restrict__ id, double* __restrict__ dr) {
-    const int t = blockIdx.x;
+                               long long tcap, const long long* __restrict__ off, int t_first, long long o_first, bool has_dr,
+                               double* __restrict__ x, double* __restrict__ u, uint32_t* __restrict__ id,
+                               double* __restrict__ dr) {
+    // tiles t_first + blockIdx.x; output index off[t] - o_first + i
+    const int t = t_first + blockIdx.x;
     const int nst = stay[t], nar = arr[t];
     const long long base = (long long)t * tcap;
     for (int i = threadIdx.x; i < nst + nar; i += blockDim.x) {
         long long slot = i < nst ? base + i : base + tcap - nar + (i - nst);
         Particle<T> p;
         load_particle<T, G>(v, slot, has_dr, p);
-        long long o = off[t] + i;
+        long long o = off[t] - o_first + i;
         if (x) {
             x[3 * o + 0] = (double)p.ci + (double)p.o[0];
             x[3 * o + 1] = (double)p.cj + (double)p.o[1];
@@ -389,27 +388,29 @@ template <class T, int G>
 __global__ void kinetic_kernel(Tiling tl, PView<T> v, const int* __restrict__ stay, const int* __restrict__ arr, long long tcap,
                                PView<T> lv, const int* __restrict__ lcount, long long lcap, double c, double m,
                                double* __restrict__ partial) {
+    // gamma - 1 = (u/c)^2 / (gamma + 1) per particle in the particles' own
+    // precision (no cancellation; FP64 division and square root per particle
+    // would cost far more than the pass's memory traffic on this part), summed
+    // in FP64; m c^2 is applied once per block
     __shared__ double red[32];
     double acc = 0.0;
-    const double ic2 = 1.0 / (c * c);
+    const T ic2 = T(1.0 / (c * c));
+    auto term = [&](T ux, T uy, T uz) {
+        const T u2 = (ux * ux + uy * uy + uz * uz) * ic2;
+        return (double)(u2 / (t_sqrt<T>(T(1) + u2) + T(1)));
+    };
     for (int t = blockIdx.x; t < tl.ntiles + 1; t += gridDim.x) {
         if (t < tl.ntiles) {
             const int nst = stay[t], nar = arr[t];
             const long long base = (long long)t * tcap;
             for (int i = threadIdx.x; i < nst + nar; i += blockDim.x) {
                 long long slot = i < nst ? base + i : base + tcap - nar + (i - nst);
-                double ux = v.u[0][slot], uy = v.u[1][slot], uz = v.u[2][slot];
-                double u2 = (ux * ux + uy * uy + uz * uz) * ic2;
-                acc += m * c * c * (u2 / (sqrt(1.0 + u2) + 1.0));
+                acc += term(v.u[0][slot], v.u[1][slot], v.u[2][slot]);
             }
         } else {
             long long n = *lcount;
             if (n > lcap) n = lcap;
-            for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-                double ux = lv.u[0][i], uy = lv.u[1][i], uz = lv.u[2][i];
-                double u2 = (ux * ux + uy * uy + uz * uz) * ic2;
-                acc += m * c * c * (u2 / (sqrt(1.0 + u2) + 1.0));
-            }
+            for (long long i = threadIdx.x; i < n; i += blockDim.x) acc += term(lv.u[0][i], lv.u[1][i], lv.u[2][i]);
         }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -418,7 +419,7 @@ __global__ void kinetic_kernel(Tiling tl, PView<T> v, const int* __restrict__ st
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        partial[blockIdx.x] = s;
+        partial[blockIdx.x] = m * c * c * s;
     }
 }
 

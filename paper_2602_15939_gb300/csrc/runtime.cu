@@ -715,20 +715,61 @@ static pic_status alloc_species(pic_handle* h, DevSpecies& d, long long tcap) {
     return PIC_OK;
 }
 
+// Loads and read-backs move particles between the caller's arrays and the
+// tiles through device staging buffers of at most this many particles: small
+// enough for the memory pool to keep between calls (no new device memory
+// after the first), and no transfer needs memory in proportion to the box.
+constexpr long long STAGE_PARTICLES = 1ll << 23;
+
+// Particles from the caller's arrays (host or device memory), a chunk of at
+// most STAGE_PARTICLES at a time through device staging buffers: one pass
+// counts each tile's particles (positions only), the layout is sized from
+// the fullest tile, a second pass scatters the particles into their tiles.
+// The staging stays small enough for the memory pool to keep: a load needs
+// no device memory in proportion to its input beyond the particle arrays.
 template <class T, int G>
-static pic_status load_t(pic_handle* h, int species, long long n, const double* dx, const double* du, const uint32_t* did,
-                         const double* ddr) {
+static pic_status load_t(pic_handle* h, int species, long long n, const double* x, const double* u, const uint32_t* id,
+                         const double* dr) {
     DevSpecies& d = h->sp[species];
     const int nt = h->tl.ntiles;
-    int* tile_p = nullptr;
+    const bool leaky = h->esc == ESC_DISP;
+    const long long S = std::max(1ll, std::min(STAGE_PARTICLES, n));
     int* cnt = nullptr;
-    CK(dalloc(h, (void**)&tile_p, sizeof(int) * std::max(1ll, n)));
-    CK(dalloc(h, (void**)&cnt, sizeof(int) * nt));
-    CK(cudaMemsetAsync(cnt, 0, sizeof(int) * nt, h->stream));
-    if (n > 0) load_bin_kernel<T, G><<<grid_blocks(n), NTHR, 0, h->stream>>>(n, dx, h->tl, h->g, tile_p, cnt);
+    double *sx = nullptr, *su = nullptr, *sdr = nullptr;
+    uint32_t* sid = nullptr;
+    auto cleanup = [&]() {
+        dfree(h, cnt);
+        dfree(h, sx);
+        dfree(h, su);
+        dfree(h, sid);
+        dfree(h, sdr);
+    };
+    if (dalloc(h, (void**)&cnt, sizeof(int) * nt) != cudaSuccess || dalloc(h, (void**)&sx, sizeof(double) * 3 * S) != cudaSuccess ||
+        dalloc(h, (void**)&su, sizeof(double) * 3 * S) != cudaSuccess ||
+        (id && dalloc(h, (void**)&sid, sizeof(uint32_t) * S) != cudaSuccess) ||
+        (dr && dalloc(h, (void**)&sdr, sizeof(double) * 3 * S) != cudaSuccess)) {
+        cudaGetLastError();
+        cleanup();
+        return fail(h, PIC_ERR_OOM, "load staging allocation failed");
+    }
+    // stream order: each chunk's kernel finishes before the next chunk's copy
+    // overwrites the staging buffers
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * nt, h->stream);
+    for (long long q0 = 0; q0 < n && e == cudaSuccess; q0 += S) {
+        const long long m = std::min(S, n - q0);
+        e = cudaMemcpyAsync(sx, x + 3 * q0, sizeof(double) * 3 * m, cudaMemcpyDefault, h->stream);
+        if (e == cudaSuccess) {
+            load_bin_kernel<T, G><<<grid_blocks(m), NTHR, 0, h->stream>>>(m, sx, h->tl, h->g, cnt);
+            e = cudaGetLastError();
+        }
+    }
     std::vector<int> hc(nt);
-    CK(cudaMemcpyAsync(hc.data(), cnt, sizeof(int) * nt, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), cnt, sizeof(int) * nt, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(h, PIC_ERR_CUDA, "load failed: %s", cudaGetErrorString(e));
+    }
     int mx = 0;
     for (int v : hc) mx = std::max(mx, v);
     double slack = h->cfg.capacity_slack > 0 ? h->cfg.capacity_slack : 0.3;
@@ -736,17 +777,28 @@ static pic_status load_t(pic_handle* h, int species, long long n, const double* 
     tcap = (tcap + 3) & ~3ll;
     d.lcap = std::max(4096ll, n / 32);
     pic_status st = alloc_species(h, d, tcap);
-    if (st != PIC_OK) { dfree(h, tile_p); dfree(h, cnt); return st; }
+    if (st != PIC_OK) {
+        cleanup();
+        return st;
+    }
     const int b = h->buf;
-    CK(cudaMemsetAsync(cnt, 0, sizeof(int) * nt, h->stream));
-    if (n > 0)
-        load_scatter_kernel<T, G><<<grid_blocks(n), NTHR, 0, h->stream>>>(n, dx, du, did, ddr, h->g, tile_p, cnt, tcap,
-                                                                          view_of<T>(d.arr[b]), h->esc == ESC_DISP);
-    CK(cudaMemcpyAsync(d.stay[b], cnt, sizeof(int) * nt, cudaMemcpyDeviceToDevice, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    CK(cudaGetLastError());
-    dfree(h, tile_p);
-    dfree(h, cnt);
+    e = cudaMemsetAsync(cnt, 0, sizeof(int) * nt, h->stream);
+    for (long long q0 = 0; q0 < n && e == cudaSuccess; q0 += S) {
+        const long long m = std::min(S, n - q0);
+        e = cudaMemcpyAsync(sx, x + 3 * q0, sizeof(double) * 3 * m, cudaMemcpyDefault, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(su, u + 3 * q0, sizeof(double) * 3 * m, cudaMemcpyDefault, h->stream);
+        if (id && e == cudaSuccess) e = cudaMemcpyAsync(sid, id + q0, sizeof(uint32_t) * m, cudaMemcpyDefault, h->stream);
+        if (dr && e == cudaSuccess) e = cudaMemcpyAsync(sdr, dr + 3 * q0, sizeof(double) * 3 * m, cudaMemcpyDefault, h->stream);
+        if (e == cudaSuccess) {
+            load_scatter_kernel<T, G><<<grid_blocks(m), NTHR, 0, h->stream>>>(m, q0, sx, su, sid, sdr, h->tl, h->g, cnt, tcap,
+                                                                              view_of<T>(d.arr[b]), leaky);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.stay[b], cnt, sizeof(int) * nt, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cleanup();
+    if (e != cudaSuccess) return fail(h, PIC_ERR_CUDA, "load failed: %s", cudaGetErrorString(e));
     d.n = n;
     d.loaded = true;
     h->since_regroup = 0;  // loads leave each tile grouped by cell or freshly ordered
@@ -833,8 +885,13 @@ template <class T, int G> static pic_status regrow_t(pic_handle* h, bool force, 
     return PIC_OK;
 }
 
+// Particles of a species read back in tile order, then the loose list, into
+// the caller's buffers (host or device memory, any kind): tiles are compacted
+// a chunk at a time into device staging buffers of at most STAGE_PARTICLES
+// particles, each chunk copied out before the next is written.
+
 template <class T, int G>
-static pic_status compact_t(pic_handle* h, int species, double* dx, double* du, uint32_t* did, double* ddr) {
+static pic_status compact_t(pic_handle* h, int species, double* x, double* u, uint32_t* id, double* dr) {
     DevSpecies& d = h->sp[species];
     const int nt = h->tl.ntiles;
     const int b = h->buf;
@@ -844,22 +901,73 @@ static pic_status compact_t(pic_handle* h, int species, double* dx, double* du, 
     CK(cudaMemcpyAsync(ar.data(), d.arrv[b], sizeof(int) * nt, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(&lc, d.lcount + b, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    std::vector<long long> off(nt);
-    long long acc = 0;
-    for (int t = 0; t < nt; ++t) { off[t] = acc; acc += st[t] + ar[t]; }
+    lc = (int)std::min<long long>(lc, d.lcap);
+    std::vector<long long> off(nt + 1);
+    long long acc = 0, big = lc;
+    for (int t = 0; t < nt; ++t) {
+        off[t] = acc;
+        acc += st[t] + ar[t];
+        big = std::max<long long>(big, st[t] + ar[t]);
+    }
+    off[nt] = acc;
     if (acc + lc != d.n)
         return fail(h, PIC_ERR_STATE, "species %d holds %lld particles, expected %lld", species, acc + lc, d.n);
+    if (acc + lc == 0) return PIC_OK;
+    const long long S = std::min(std::max(STAGE_PARTICLES, big), acc + lc);
     long long* doff = nullptr;
-    CK(dalloc(h, (void**)&doff, sizeof(long long) * nt));
-    CK(cudaMemcpyAsync(doff, off.data(), sizeof(long long) * nt, cudaMemcpyHostToDevice, h->stream));
+    double *sx = nullptr, *su = nullptr, *sdr = nullptr;
+    uint32_t* sid = nullptr;
+    pic_status ret = PIC_OK;
+    auto cleanup = [&]() {
+        dfree(h, doff);
+        dfree(h, sx);
+        dfree(h, su);
+        dfree(h, sid);
+        dfree(h, sdr);
+    };
+    if (dalloc(h, (void**)&doff, sizeof(long long) * (nt + 1)) != cudaSuccess ||
+        (x && dalloc(h, (void**)&sx, sizeof(double) * 3 * S) != cudaSuccess) ||
+        (u && dalloc(h, (void**)&su, sizeof(double) * 3 * S) != cudaSuccess) ||
+        (id && dalloc(h, (void**)&sid, sizeof(uint32_t) * S) != cudaSuccess) ||
+        (dr && dalloc(h, (void**)&sdr, sizeof(double) * 3 * S) != cudaSuccess)) {
+        cudaGetLastError();
+        cleanup();
+        return fail(h, PIC_ERR_OOM, "read-back staging allocation failed");
+    }
     const bool hd = h->esc == ESC_DISP;
-    compact_kernel<T, G><<<nt, NTHR, 0, h->stream>>>(h->tl, h->g, view_of<T>(d.arr[b]), d.stay[b], d.arrv[b], d.tcap, doff, hd, dx,
-                                                   du, did, ddr);
-    compact_loose_kernel<T, G><<<64, NTHR, 0, h->stream>>>(view_of<T>(d.larr[b]), d.lcount + b, d.lcap, acc, hd, dx, du, did, ddr);
-    CK(cudaStreamSynchronize(h->stream));
-    CK(cudaGetLastError());
-    dfree(h, doff);
-    return PIC_OK;
+    auto copy_out = [&](long long o0, long long cnt) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        if (x && e == cudaSuccess) e = cudaMemcpyAsync(x + 3 * o0, sx, sizeof(double) * 3 * cnt, cudaMemcpyDefault, h->stream);
+        if (u && e == cudaSuccess) e = cudaMemcpyAsync(u + 3 * o0, su, sizeof(double) * 3 * cnt, cudaMemcpyDefault, h->stream);
+        if (id && e == cudaSuccess) e = cudaMemcpyAsync(id + o0, sid, sizeof(uint32_t) * cnt, cudaMemcpyDefault, h->stream);
+        if (dr && e == cudaSuccess) e = cudaMemcpyAsync(dr + 3 * o0, sdr, sizeof(double) * 3 * cnt, cudaMemcpyDefault, h->stream);
+        return e;
+    };
+    cudaError_t e = cudaMemcpyAsync(doff, off.data(), sizeof(long long) * (nt + 1), cudaMemcpyHostToDevice, h->stream);
+    // stream order: each chunk's copies finish before the next chunk's
+    // compaction overwrites the staging buffers
+    for (int t0 = 0; t0 < nt && e == cudaSuccess;) {
+        int t1 = t0 + 1;
+        while (t1 < nt && off[t1 + 1] - off[t0] <= S) ++t1;
+        const long long cnt = off[t1] - off[t0];
+        if (cnt > 0) {
+            compact_kernel<T, G><<<t1 - t0, NTHR, 0, h->stream>>>(h->tl, h->g, view_of<T>(d.arr[b]), d.stay[b], d.arrv[b],
+                                                                d.tcap, doff, t0, off[t0], hd, sx, su, sid, sdr);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = copy_out(off[t0], cnt);
+        }
+        t0 = t1;
+    }
+    if (lc > 0 && e == cudaSuccess) {
+        compact_loose_kernel<T, G><<<64, NTHR, 0, h->stream>>>(view_of<T>(d.larr[b]), d.lcount + b, d.lcap, 0, hd, sx, su, sid,
+                                                               sdr);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = copy_out(acc, lc);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) ret = fail(h, PIC_ERR_CUDA, "read-back failed: %s", cudaGetErrorString(e));
+    cleanup();
+    return ret;
 }
 
 template <class T, int G>
@@ -1268,26 +1376,9 @@ pic_status pic_load_particles(pic_handle* h, int species, double q, double m, in
     if (!(m > 0) || !std::isfinite(q)) return fail(h, PIC_ERR_ARG, "mass must be > 0 and charge finite");
     if (n >= (1ll << 31)) return fail(h, PIC_ERR_ARG, "at most 2^31 - 1 particles per species");
     CK(cudaStreamSynchronize(h->stream));
-    double *dx = nullptr, *du = nullptr;
-    uint32_t* did = nullptr;
-    size_t n3 = (size_t)std::max<int64_t>(n, 1) * 3;
-    CK(dalloc(h, (void**)&dx, sizeof(double) * n3));
-    CK(dalloc(h, (void**)&du, sizeof(double) * n3));
-    if (n > 0) {
-        CK(cudaMemcpyAsync(dx, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
-        CK(cudaMemcpyAsync(du, u, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
-        if (id) {
-            CK(dalloc(h, (void**)&did, sizeof(uint32_t) * n));
-            CK(cudaMemcpyAsync(did, id, sizeof(uint32_t) * n, cudaMemcpyHostToDevice, h->stream));
-        }
-    }
     h->sp[species].q = q;
     h->sp[species].m = m;
-    st = DISPATCH(h, load_t, h, species, n, dx, du, did, (const double*)nullptr);
-    dfree(h, dx);
-    dfree(h, du);
-    if (did) dfree(h, did);
-    return st;
+    return DISPATCH(h, load_t, h, species, (long long)n, x, u, id, (const double*)nullptr);
 }
 
 pic_status pic_load_maxwellian(pic_handle* h, int species, double q, double m, int ppc, double theta, const double drift[3],
@@ -1547,35 +1638,9 @@ pic_status pic_get_count(pic_handle* h, int species, int64_t* n) {
 pic_status pic_get_particles(pic_handle* h, int species, double* x, double* u, uint32_t* id, double* dr) {
     pic_status st = check_species(h, species);
     if (st != PIC_OK) return st;
-    DevSpecies& d = h->sp[species];
-    if (!d.loaded) return fail(h, PIC_ERR_STATE, "species %d is not loaded", species);
+    if (!h->sp[species].loaded) return fail(h, PIC_ERR_STATE, "species %d is not loaded", species);
     CK(cudaStreamSynchronize(h->stream));
-    long long n = d.n;
-    double *dx = nullptr, *du = nullptr, *ddr = nullptr;
-    uint32_t* did = nullptr;
-    size_t n3 = (size_t)std::max(n, 1ll) * 3;
-    if (x) CK(dalloc(h, (void**)&dx, sizeof(double) * n3));
-    if (u) CK(dalloc(h, (void**)&du, sizeof(double) * n3));
-    if (id) CK(dalloc(h, (void**)&did, sizeof(uint32_t) * std::max(n, 1ll)));
-    if (dr) CK(dalloc(h, (void**)&ddr, sizeof(double) * n3));
-    st = DISPATCH(h, compact_t, h, species, dx, du, did, ddr);
-    if (st == PIC_OK && n > 0) {
-        if (x) CK(cudaMemcpyAsync(x, dx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
-        if (u) CK(cudaMemcpyAsync(u, du, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
-        if (id) CK(cudaMemcpyAsync(id, did, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->stream));
-        if (dr) CK(cudaMemcpyAsync(dr, ddr, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
-        CK(cudaStreamSynchronize(h->stream));
-        if (x && h->geom != 0) {
-            // the ignorable coordinate is not tracked
-            int ig = h->geom == 1 ? 2 : 1;
-            for (long long i = 0; i < n; ++i) x[3 * i + ig] = 0.5;
-        }
-    }
-    if (dx) dfree(h, dx);
-    if (du) dfree(h, du);
-    if (did) dfree(h, did);
-    if (ddr) dfree(h, ddr);
-    return st;
+    return DISPATCH(h, compact_t, h, species, x, u, id, dr);
 }
 
 pic_status pic_get_particles_sampled(pic_handle* h, int species, uint32_t modulus, uint32_t remainder, int64_t max_out,
