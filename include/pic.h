@@ -293,7 +293,8 @@ pic_status pic_autotune(pic_handle *h, int32_t trial_steps, int32_t *best, doubl
  * persistent particle kernel over the tiles of all boxes (at most
  * pic_batch_max_boxes_per_launch boxes per launch; more make several
  * launches), while each box's own field update, current fold and bookkeeping
- * run as parallel branches; pairs of steps are captured in one CUDA graph and
+ * run as parallel branches; each cycle of steps (a regroup by cell and the
+ * steps up to the next, or a pair of steps) is captured in one CUDA graph and
  * replayed.  The boxes must share device, precision, geometry (3D, 2D x-y, 2D
  * x-z), shape order and box type; they may differ in grid, parameters, species
  * and particle counts.  They must be loaded before pic_batch_create and stay

@@ -1419,12 +1419,12 @@ static pic_status check_error_word(pic_handle* h) {
     return PIC_OK;
 }
 
-// Capture two consecutive steps (starting from the current particle buffer)
-// into a CUDA graph; all per-step scalars come from the device context, so
-// the graph is replayed unchanged for every later pair of steps.  On any
-// capture failure graphs are switched off for this handle.
-// Steps per captured graph: a regroup and the steps up to the next one, or a
-// pair of steps.
+// Step graphs: consecutive steps starting from one particle buffer are
+// captured into a CUDA graph; all per-step scalars come from the device
+// context, so the graph is replayed unchanged for every later cycle that
+// starts from that buffer.  On any capture failure graphs are switched off
+// for this handle.  Steps per captured graph: a regroup and the steps up to
+// the next one, or a pair of steps when regrouping is off.
 static int graph_cycle(const pic_handle* h) { return h->regroup_every > 0 ? h->regroup_every : 2; }
 
 // Capture one cycle of steps starting from buffer h->buf (with the regroup
