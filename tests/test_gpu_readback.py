@@ -46,3 +46,45 @@ def test_readback_pinned_device_and_pageable_agree(case):
                 assert np.all(x[:, ig] == 0.5)
     finally:
         box.close()
+
+
+@pytest.mark.gpu
+def test_load_and_readback_across_staging_chunks():
+    # more particles per species than one staging chunk (2^23): a load and a
+    # read-back each take two chunks.  Species 0 brings shuffled ids, species 1
+    # none (ids are then the input positions 0..n-1, also across chunks).
+    n3 = (48, 48, 48)
+    ppc = 80
+    N = n3[0] * n3[1] * n3[2] * ppc
+    assert N > (1 << 23)
+    cfg = P.make_config(box=P.PIC_BOX_PERIODIC, nx=n3[0], ny=n3[1], nz=n3[2], ndim=3, order=1, precision=P.PIC_FP32)
+    r = np.random.default_rng(11)
+    x = r.uniform(0.0, 1.0, (N, 3)) * np.asarray(n3, dtype=float)
+    u = r.normal(0.0, 0.1, (N, 3))
+    ids = r.permutation(N).astype(np.uint32)
+    box = P.Box(cfg)
+    try:
+        z = np.zeros((3, n3[2], n3[1], n3[0]))
+        box.set_fields(z, z)
+        box.load(0, -0.01, 1.0, x, u, ids)
+        box.load(1, 0.01, 1.0, x, u)
+        for s, want_ids in ((0, ids), (1, np.arange(N, dtype=np.uint32))):
+            xo, uo, io, _ = box.particles(s)
+            assert len(io) == N
+            o = np.argsort(io)
+            assert np.array_equal(io[o], np.arange(N, dtype=np.uint32))
+            back = np.empty(N, dtype=np.int64)
+            back[want_ids] = np.arange(N)  # input row of each id
+            xi, ui = x[back], u[back]
+            assert np.abs(xo[o] - xi).max() <= 1e-5  # FP32 in-cell offsets
+            assert np.abs(uo[o] - ui).max() <= 1e-6 * np.abs(ui).max()
+        box.step(1)
+        for s in (0, 1):
+            xo, uo, io, _ = box.particles(s)
+            xs, us, is_, _ = box.particles_sampled(s, 997, 5, max_out=N // 900)
+            o = np.argsort(io)
+            k = np.searchsorted(io[o], is_)
+            assert np.array_equal(io[o][k], is_)
+            assert np.array_equal(xo[o][k], xs) and np.array_equal(uo[o][k], us)
+    finally:
+        box.close()
