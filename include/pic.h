@@ -149,10 +149,13 @@ pic_status pic_set_stream(pic_handle *h, void *stream);
 pic_status pic_synchronize(pic_handle *h);
 
 /* Load (replacing) species `species` (< PIC_MAX_SPECIES) with n particles of
- * macro-charge q and macro-mass m from host arrays x[n][3] (cells) and
- * u[n][3] (cells/step).  id (nullable) gives particle ids (default 0..n-1);
- * ids key the leaky box's random streams.  Positions are wrapped into the box.
- * The particle-step order within a tile is not preserved. */
+ * macro-charge q and macro-mass m from arrays x[n][3] (cells) and u[n][3]
+ * (cells/step), in host (pageable or pinned) or device memory.  id (nullable)
+ * gives particle ids (default 0..n-1); ids key the leaky box's random streams.
+ * Positions are wrapped into the box.  The arrays are read twice (a tile
+ * count of the positions, then the scatter), in chunks of at most 2^23
+ * particles through device staging buffers.  Synchronizes the handle's
+ * stream.  The particle-step order within a tile is not preserved. */
 pic_status pic_load_particles(pic_handle *h, int species, double q, double m, int64_t n,
                               const double *x, const double *u, const uint32_t *id);
 
@@ -187,9 +190,13 @@ pic_status pic_diagnostics(pic_handle *h, pic_diag *out);
 /* Number of particles of a species. */
 pic_status pic_get_count(pic_handle *h, int species, int64_t *n);
 
-/* Copy a species to host arrays sized by pic_get_count: x[n][3], u[n][3],
- * id[n] and dr[n][3] (leaky displacement); each pointer may be NULL.  The
- * order is the device's tile order; match particles by id. */
+/* Copy a species to arrays sized by pic_get_count: x[n][3], u[n][3], id[n]
+ * and dr[n][3] (leaky displacement); each pointer may be NULL.  The arrays may
+ * be pageable or pinned host memory or device memory (pinned host memory
+ * transfers fastest).  The particles pass through device staging buffers of at
+ * most 2^23 particles, so no device memory in proportion to n is needed.
+ * Synchronizes the handle's stream.  The order is the device's tile order;
+ * match particles by id. */
 pic_status pic_get_particles(pic_handle *h, int species, double *x, double *u, uint32_t *id,
                              double *dr);
 
