@@ -476,6 +476,9 @@ class Box:
     def set_uniform_fields(self, E, B):
         pic_set_uniform_fields(self.h, E, B)
 
+    def set_regroup_interval(self, every: int):
+        pic_set_regroup_interval(self.h, every)
+
     def autotune(self, trial_steps=4):
         """Pick the fastest particle-kernel variant on live steps; see pic_autotune."""
         return pic_autotune(self.h, trial_steps)
