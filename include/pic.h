@@ -225,21 +225,23 @@ pic_status pic_reset_profile(pic_handle *h);
  * lost (PIC_ERR_STATE).  Every step keeps each species' fullest-tile
  * occupancy on the device; pic_step checks it every 8 steps it runs (an
  * asynchronous snapshot of the maxima since the last one, acted on one check
- * later) and, when a
- * species' fullest tile passes 90% of its slots or its loose list a quarter
- * of its room, lays every species out again with more slots (the fullest tile
- * x max(1 + slack, 1.25) + 32) and a larger loose list.  Particle states
- * and results do not change.  pic_rebalance runs the check now (force != 0:
- * re-layout regardless; *grown, nullable, says whether it did);
+ * later) and, when a species' fullest tile passes 90% of its slots or its
+ * loose list a quarter of its room, lays every species out again with more
+ * slots (the fullest tile x max(1 + slack, 1.25) + 32) and a larger loose
+ * list.  Particle states and results do not change.  pic_rebalance runs the
+ * check now and synchronizes the handle's stream (force != 0: re-layout
+ * regardless; *grown, nullable, says whether it did); PIC_ERR_OOM if the new
+ * layout does not fit (the old one is kept), PIC_ERR_STATE on a batched box.
  * pic_get_capacity reports a species' slots per tile, loose-list room and
- * the re-layouts so far (each output nullable).  Not a part of the paper's
- * method: the bookkeeping of the tile-sorted particle layout. */
+ * the re-layouts so far (each output nullable; PIC_ERR_ARG for a bad
+ * species).  Not a part of the paper's method: the bookkeeping of the
+ * tile-sorted particle layout. */
 pic_status pic_rebalance(pic_handle *h, int32_t force, int32_t *grown);
-/* Capacity checks every `every` steps (default 8; 0: none).  block != 0
- * (default): a check waits for the snapshot taken one check earlier, which
- * also keeps the host at most about two checks ahead of the GPU; block = 0:
- * a check whose snapshot has not landed is skipped (for callers that bound
- * their own lead, like the server). */
+/* Capacity checks every `every` steps (default 8; 0: none; every < 0 is
+ * PIC_ERR_ARG).  block != 0 (default): a check waits for the snapshot taken
+ * one check earlier, which also keeps the host at most about two checks ahead
+ * of the GPU; block = 0: a check whose snapshot has not landed is skipped
+ * (for callers that bound their own lead, like the server). */
 pic_status pic_set_capacity_check(pic_handle *h, int32_t every, int32_t block);
 pic_status pic_get_capacity(pic_handle *h, int species, int64_t *slots_per_tile, int64_t *loose_capacity,
                             int64_t *relayouts);
@@ -252,8 +254,11 @@ pic_status pic_get_capacity(pic_handle *h, int species, int64_t *slots_per_tile,
  * the order decays as particles change cells.  Default: 3 for 3D FP32 boxes,
  * 0 otherwise (FP64 boxes should keep 0: the order of their current's
  * floating-point adds, and so its last bits, would vary from run to run).
- * FP32 results are bit-identical for every interval.  Not a part of the
- * paper's method. */
+ * FP32 results are bit-identical for every interval.  A tile whose slots
+ * exceed the sort's shared memory (65536 or more) is copied in order instead.
+ * pic_set_regroup_interval synchronizes the handle's stream and drops its
+ * captured step graphs; every < 0 is PIC_ERR_ARG.  Not a part of the paper's
+ * method. */
 pic_status pic_set_regroup_interval(pic_handle *h, int32_t every);
 pic_status pic_get_regroup_interval(pic_handle *h, int32_t *every);
 

@@ -845,24 +845,39 @@ template <class T, int G> static pic_status regrow_t(pic_handle* h, bool force, 
         if (mx > 0.9 * d.tcap || lc > d.lcap / 4) need = true;
     }
     if (!need) return PIC_OK;
+    // every new array first: if one does not fit, the current layout stays as it is
+    const int nact = h->geom == 0 ? 3 : 2;
+    void* na[PIC_MAX_SPECIES][2][11] = {};
+    void* nl[PIC_MAX_SPECIES][2][11] = {};
+    bool fits = true;
+    for (int s = 0; s < PIC_MAX_SPECIES && fits; ++s) {
+        if (!h->sp[s].loaded) continue;
+        for (int bb = 0; bb < 2 && fits; ++bb)
+            for (int i = 0; i < 11 && fits; ++i) {
+                const bool use = i == 0 || (i >= 1 && i <= nact) || (i >= 4 && i <= 7) || (i >= 8 && leaky);
+                if (!use) continue;
+                const size_t es = (i == 0 || i == 7) ? 4 : h->esz;
+                fits = dalloc(h, &na[s][bb][i], (size_t)nt * new_tcap[s] * es) == cudaSuccess &&
+                       dalloc(h, &nl[s][bb][i], (size_t)new_lcap[s] * es) == cudaSuccess;
+            }
+    }
+    if (!fits) {
+        cudaGetLastError();
+        for (int s = 0; s < PIC_MAX_SPECIES; ++s)
+            for (int bb = 0; bb < 2; ++bb)
+                for (int i = 0; i < 11; ++i) {
+                    dfree(h, na[s][bb][i]);
+                    dfree(h, nl[s][bb][i]);
+                }
+        return fail(h, PIC_ERR_OOM, "a larger tile layout does not fit in device memory; the current one is kept");
+    }
     drop_graphs(h);
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
         DevSpecies& d = h->sp[s];
         if (!d.loaded) continue;
-        const int nact = h->geom == 0 ? 3 : 2;
-        void* na[2][11] = {};
-        void* nl[2][11] = {};
-        for (int bb = 0; bb < 2; ++bb)
-            for (int i = 0; i < 11; ++i) {
-                const bool use = i == 0 || (i >= 1 && i <= nact) || (i >= 4 && i <= 7) || (i >= 8 && leaky);
-                if (!use) continue;
-                const size_t es = (i == 0 || i == 7) ? 4 : h->esz;
-                CK(dalloc(h, &na[bb][i], (size_t)nt * new_tcap[s] * es));
-                CK(dalloc(h, &nl[bb][i], (size_t)new_lcap[s] * es));
-            }
-        PView<T> vin = view_of<T>(d.arr[b]), vout = view_of<T>(na[0]);
+        PView<T> vin = view_of<T>(d.arr[b]), vout = view_of<T>(na[s][0]);
         regrow_kernel<T, G><<<nt, NTHR, 0, h->stream>>>(vin, vout, d.stay[b], d.arrv[b], d.tcap, new_tcap[s], d.stay[0], leaky);
-        copy_loose_kernel<T, G><<<64, NTHR, 0, h->stream>>>(view_of<T>(d.larr[b]), view_of<T>(nl[0]), d.lcount + b, d.lcap,
+        copy_loose_kernel<T, G><<<64, NTHR, 0, h->stream>>>(view_of<T>(d.larr[b]), view_of<T>(nl[s][0]), d.lcount + b, d.lcap,
                                                             d.lcount + 0, leaky);
         CK(cudaGetLastError());
         if (b == 1) CK(cudaMemsetAsync(d.lcount + 1, 0, sizeof(int), h->stream));
@@ -872,8 +887,8 @@ template <class T, int G> static pic_status regrow_t(pic_handle* h, bool force, 
             for (int i = 0; i < 11; ++i) {
                 dfree(h, d.arr[bb][i]);
                 dfree(h, d.larr[bb][i]);
-                d.arr[bb][i] = na[bb][i];
-                d.larr[bb][i] = nl[bb][i];
+                d.arr[bb][i] = na[s][bb][i];
+                d.larr[bb][i] = nl[s][bb][i];
             }
         d.tcap = new_tcap[s];
         d.lcap = new_lcap[s];
