@@ -549,14 +549,20 @@ template <class T, int G> static pic_status regroup_t(pic_handle* h) {
         } else {
             regrow_kernel<T, G><<<nt, NTHR, 0, h->stream>>>(vin, vout, d.stay[b], d.arrv[b], d.tcap, d.tcap, d.stay[o], leaky);
         }
-        CK(cudaMemsetAsync(d.arrv[b], 0, sizeof(int) * nt, h->stream));
         copy_loose_kernel<T, G><<<64, NTHR, 0, h->stream>>>(view_of<T>(d.larr[b]), view_of<T>(d.larr[o]), d.lcount + b, d.lcap,
                                                             d.lcount + o, leaky);
-        CK(cudaMemsetAsync(d.lcount + b, 0, sizeof(int), h->stream));
+        CK(cudaGetLastError());
         h->prof.launches += 2;
     }
+    // only once every species is copied: buffer b's arrival and loose counts
+    // restart for the next step's output (a failed launch above leaves b whole)
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
+        DevSpecies& d = h->sp[s];
+        if (!d.loaded) continue;
+        CK(cudaMemsetAsync(d.arrv[b], 0, sizeof(int) * nt, h->stream));
+        CK(cudaMemsetAsync(d.lcount + b, 0, sizeof(int), h->stream));
+    }
     prof_end(h, 1);
-    CK(cudaGetLastError());
     h->buf = o;
     return PIC_OK;
 }
