@@ -321,7 +321,9 @@ pic_status pic_batch_step(pic_batch *b, int32_t nsteps);   /* asynchronous */
 pic_status pic_batch_synchronize(pic_batch *b);
 pic_status pic_batch_destroy(pic_batch *b);                 /* synchronizes; members are free again */
 /* Regroup every member by cell every `every` steps (see
- * pic_set_regroup_interval; the default is that of the members' kind). */
+ * pic_set_regroup_interval; the default is that of the members' kind).
+ * Batches make no tile-capacity checks: to re-lay out crowded members, call
+ * pic_rebalance on them after pic_batch_destroy. */
 pic_status pic_batch_set_regroup_interval(pic_batch *b, int32_t every);
 int32_t pic_batch_max_boxes_per_launch(int32_t precision);
 
