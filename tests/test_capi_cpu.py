@@ -54,6 +54,16 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.pic_step(None, 1) == P.PIC_ERR_ARG
     assert lib.pic_destroy(None) == P.PIC_OK
     assert lib.pic_synchronize(None) == P.PIC_ERR_ARG
+    # capacity, regrouping and batch controls check their handles before any CUDA call
+    k = ctypes.c_int32()
+    n = ctypes.c_int64()
+    assert lib.pic_set_regroup_interval(None, 3) == P.PIC_ERR_ARG
+    assert lib.pic_get_regroup_interval(None, ctypes.byref(k)) == P.PIC_ERR_ARG
+    assert lib.pic_set_capacity_check(None, 8, 1) == P.PIC_ERR_ARG
+    assert lib.pic_rebalance(None, 0, ctypes.byref(k)) == P.PIC_ERR_ARG
+    assert lib.pic_get_capacity(None, 0, ctypes.byref(n), None, None) == P.PIC_ERR_ARG
+    assert lib.pic_batch_set_regroup_interval(None, 3) == P.PIC_ERR_ARG
+    assert lib.pic_batch_step(None, 1) == P.PIC_ERR_ARG
 
 
 def test_kernel_variant_table():
