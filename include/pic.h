@@ -133,7 +133,16 @@ const char *pic_version(void);
 int pic_abi_version(void);
 
 /* Validate *cfg, select the current CUDA device, allocate the grid state and
- * return a new handle in *out (NULL on failure).  Fields start at zero. */
+ * return a new handle in *out (NULL on failure).  Fields start at zero.
+ * The configuration carries each box's parameters as the paper states them:
+ * shearing box (Sec. 2.1): s and Omega0 of the shear flow v_s = -s Omega0 x e_y,
+ * the shearing-periodic x boundary with Dy_s = s Omega0 (x_o - x_i) t, and the
+ * number of fixed-point sweeps of the implicit Maxwell solve (Sec. 2.2);
+ * expanding box (Sec. 3.1): the diagonal L = diag(l_i(t)) through
+ * l_i(t) = exp(rate_i t); leaky box (Sec. 4.1): the escape distance l_esc, the
+ * displacement components tested (x,y or x,y,z) and the temperature of the
+ * reinjection law.  Errors: PIC_ERR_ARG (text in pic_last_error(NULL)) for a
+ * configuration outside these ranges; PIC_ERR_OOM; PIC_ERR_CUDA. */
 pic_status pic_init(const pic_config *cfg, pic_handle **out);
 
 /* Release everything the handle owns; h may be NULL. */
@@ -150,7 +159,14 @@ pic_status pic_synchronize(pic_handle *h);
 
 /* Load (replacing) species `species` (< PIC_MAX_SPECIES) with n particles of
  * macro-charge q and macro-mass m from arrays x[n][3] (cells) and u[n][3]
- * (cells/step), in host (pageable or pinned) or device memory.  id (nullable)
+ * (cells/step), in host (pageable or pinned) or device memory.  The state
+ * loaded is each box's evolving particle state: positions x and comoving
+ * momenta u' = u - gamma' v_s for the shearing box (Sec. 2.1); comoving
+ * positions x' and lab-frame momenta u for the expanding box (Sec. 3.1); for
+ * the leaky box the displacement Delta r starts at zero (Sec. 4.1).  Momenta
+ * are u^{n-1/2} of the leapfrog, positions x^n.  The caller keeps ownership
+ * of the arrays; errors: PIC_ERR_ARG (bad species, n < 0, NULL x or u),
+ * PIC_ERR_OOM, PIC_ERR_CUDA.  id (nullable)
  * gives particle ids (default 0..n-1); ids key the leaky box's random streams.
  * Positions are wrapped into the box.  The arrays are read twice (a tile
  * count of the positions, then the scatter), in chunks of at most 2^23
@@ -170,7 +186,13 @@ pic_status pic_load_maxwellian(pic_handle *h, int species, double q, double m, i
                                double theta, const double drift[3], double noise_sigma,
                                uint32_t seed, uint32_t id_base);
 
-/* Set E (E' for the shearing box) and B from host arrays [3][nz][ny][nx]. */
+/* Set E and B from host arrays [3][nz][ny][nx] (copied; the caller keeps
+ * them).  The shearing box evolves the comoving E' = E + (v_s / c) x B and B
+ * (Sec. 2.1), so E here is E'.  The expanding box passes the lab-frame E and
+ * B sampled on the comoving x' grid (Sec. 3.1; the solver transforms them to
+ * E' = ell L^{-1} E, B' = ell L^{-1} B itself, Sec. 3.2).  Guard cells are
+ * filled for the handle's time (shearing-periodic with Dy_s(t)).  Errors:
+ * PIC_ERR_ARG (NULL array), PIC_ERR_CUDA. */
 pic_status pic_set_fields(pic_handle *h, const double *E, const double *B);
 
 /* Set uniform E and B (3 components each). */
@@ -181,11 +203,40 @@ pic_status pic_set_uniform_fields(pic_handle *h, const double E[3], const double
  * l_i(t) follow from it.  Guard cells are refilled for the new time. */
 pic_status pic_set_step(pic_handle *h, int64_t step);
 
-/* Advance nsteps steps (asynchronous on the handle's stream). */
+/* Advance nsteps steps (asynchronous on the handle's stream).  One step is
+ * the box's step list: the standard PIC step (gather at x^n, Boris push,
+ * position update, charge-conserving current, leapfrog Maxwell update) for the
+ * periodic box; the five steps of Sec. 2.2 for the shearing box (Boris-like
+ * push with the shear, Coriolis and tidal terms; partial move x^n -> x';
+ * current J' from x' - x^n advected along y by v_{s,y} dt / 2; full move
+ * adding the shear motion; implicit Maxwell solve by fixed-point sweeps); the
+ * four steps of Sec. 3.2 for the expanding box (modified Boris push with
+ * Lambda; comoving move with L^{-1}(t^{n+1/2}); current ell J'; leapfrog on the
+ * transformed fields); and the escape algorithm of Sec. 4.1 after the
+ * standard step for the leaky box.  Errors found on the device (a bounded
+ * wait that expired, a non-finite momentum, a fixed-point current beyond its
+ * range) are reported by the next call that synchronises: PIC_ERR_TIMEOUT,
+ * PIC_ERR_NUMERIC, PIC_ERR_STATE (particles lost to a full loose list).
+ * PIC_ERR_STATE also for a handle with no particles loaded or in a batch. */
 pic_status pic_step(pic_handle *h, int nsteps);
 
-/* Synchronize and fill *out with FP64 sums over the current state. */
+/* Synchronize and fill *out with FP64 sums over the current state: the
+ * energies whose time histories the paper's examples follow (Secs. 2.3, 3.3,
+ * 4.2): field energy per component, sum E_c^2 / (8 pi) and B_c^2 / (8 pi)
+ * over the cells (E' for the shearing box), and per species the kinetic
+ * energy sum m c^2 (gamma - 1); plus Dy_s(t) (Sec. 2.1), l_i(t) (Sec. 3.1), the
+ * leaky box's reinjection count (Sec. 4.1) and the shearing box's count of
+ * superluminal effective velocities |u'/gamma' + v_s| >= c (Sec. 2.1).  The
+ * sums are taken in FP64 whatever the particle precision.  Errors: the
+ * device error word as for pic_step; PIC_ERR_ARG for out == NULL. */
 pic_status pic_diagnostics(pic_handle *h, pic_diag *out);
+
+/* Clear the handle's device error word.  A device-side error (see pic_step)
+ * stays recorded, and every later pic_step or pic_diagnostics reports it,
+ * until this call; clear it once the state that caused it has been replaced
+ * (pic_load_particles, pic_set_fields, pic_set_step).  Synchronizes the
+ * handle's stream.  Errors: PIC_ERR_ARG (NULL handle), PIC_ERR_CUDA. */
+pic_status pic_clear_error(pic_handle *h);
 
 /* Number of particles of a species. */
 pic_status pic_get_count(pic_handle *h, int species, int64_t *n);
@@ -211,7 +262,11 @@ pic_status pic_get_particles_sampled(pic_handle *h, int species, uint32_t modulu
 
 /* Copy E (E'), B and the current J of the last step (after folding, and for
  * the shearing box after the y advection) to host arrays [3][nz][ny][nx];
- * each pointer may be NULL. */
+ * each pointer may be NULL.  J is the source term of the box's Maxwell
+ * update: J' advected to the lab-frame grid for the shearing box (Sec. 2.2),
+ * ell J' for the expanding box (Sec. 3.1), J otherwise; ghost currents are
+ * folded back with the shearing-periodic identification of Sec. 2.1.
+ * Synchronizes the handle's stream.  Errors: PIC_ERR_CUDA. */
 pic_status pic_get_fields(pic_handle *h, double *E, double *B, double *J);
 
 /* Per-kernel device timing (CUDA events on the handle's stream). */
@@ -264,7 +319,9 @@ pic_status pic_get_regroup_interval(pic_handle *h, int32_t *every);
 
 /* Load the library's particle kernels for one precision on `device` now
  * rather than at their first use (CUDA loads code lazily: the first box of
- * each geometry otherwise pays some tens of milliseconds).  The server calls
+ * each geometry otherwise pays some tens of milliseconds).  It also loads
+ * the allocation-free field-energy reduction (both precisions) and its
+ * scratch array on `device` (see pic_field_energy_noalloc).  The server calls
  * it for FP32 when it starts. */
 pic_status pic_preload_kernels(int32_t device, int32_t precision);
 
@@ -346,7 +403,7 @@ typedef struct pic_run_spec {
     double noise_sigma;
     double E0[3], B0[3];  /* uniform initial fields */
     uint32_t load_seed;
-    uint32_t reserved;
+    uint32_t keep_state;  /* 1: keep the finished run's box for pic_take_result */
     int64_t nsteps;
 } pic_run_spec;
 
@@ -383,6 +440,16 @@ pic_status pic_submit(pic_server *s, const pic_run_spec *spec, uint64_t *ticket)
  * status once done. */
 pic_status pic_poll(pic_server *s, uint64_t ticket, int *done, pic_diag *out, double *latency_s);
 
+/* Hand over the box of a finished run submitted with keep_state = 1: *out
+ * becomes the caller's handle (state at step nsteps, on its own stream; free
+ * it with pic_destroy), from which pic_get_particles and pic_get_fields read
+ * the run's final particles and fields.  Until it is taken, the box keeps
+ * its device memory and counts against the server's budget; the server
+ * destroys boxes never taken when it is destroyed.  PIC_ERR_STATE if the run
+ * has not finished, failed, was not submitted with keep_state, or was taken
+ * already; PIC_ERR_ARG for an unknown ticket. */
+pic_status pic_take_result(pic_server *s, uint64_t ticket, pic_handle **out);
+
 /* Block until run `ticket` (0: every submitted run) has finished, or timeout_s
  * seconds pass (PIC_ERR_TIMEOUT). */
 pic_status pic_server_wait(pic_server *s, uint64_t ticket, double timeout_s);
@@ -411,12 +478,17 @@ pic_status pic_server_destroy(pic_server *s);
  * stream:  cudaStream_t the work is ordered on (NULL = the legacy default
  *          stream of the current device); the call returns without waiting.
  * Limits:  1 <= ncomp <= PIC_NOALLOC_MAX_COMPONENTS; otherwise PIC_ERR_ARG.
- * Scratch: every GPU that loads libpic holds a 64 KB static array until the
- *          process exits.  All calls on a device share it, so calls whose work
- *          can overlap on the GPU race and return wrong sums: order them (one
- *          stream, or events).  The first call on a device looks up the
- *          array's device address (one-time set-up with that device current);
- *          make that first call before any stream capture.
+ * Scratch: a 64 KB static device array, held on a device from the moment
+ *          the library's module is loaded there until the process exits.  CUDA
+ *          loads modules lazily: the first call on a device (or
+ *          pic_preload_kernels for that device, which does the same set-up
+ *          ahead of time) maps the array and the kernels and looks up the
+ *          array's device address with that device current.  Make that first
+ *          call, or pic_preload_kernels, before any stream capture.  All calls
+ *          on a device share the array, so calls whose work can overlap on the
+ *          GPU race and return wrong sums: order them (one stream, or events).
+ *          Each call overwrites every partial sum it reads, so nothing needs
+ *          clearing between calls.
  * Errors:  PIC_ERR_ARG / PIC_ERR_CUDA with text in pic_last_error(NULL).
  * Nothing is allocated: no cudaMalloc, cudaFree or allocating library call. */
 pic_status pic_field_energy_noalloc(const void *d_field, int precision, int64_t n, int ncomp,

@@ -60,7 +60,37 @@ __global__ void sum_partials_static(const double* __restrict__ partial, int nblo
     out[c] = s * scale;
 }
 
+// Device address of the scratch array on the current device `dev`, looked up
+// once per device (the lookup also loads this file's module there).
+cudaError_t partials_of(int dev, double** out) {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_partials_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess || !p) return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+        g_partials_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_partials_ptr[dev];
+    return cudaSuccess;
+}
+
 }  // namespace
+
+// Set-up of the allocation-free entry point on the current device ahead of
+// its first call: the scratch address and both precisions' kernels.  CUDA
+// loads modules lazily, so without this the first call (or the first call of
+// the other precision) maps the 64 KB array and the kernel code then.
+extern "C" int pic_internal_noalloc_preload(void) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return 1;
+    double* p = nullptr;
+    if (partials_of(dev, &p) != cudaSuccess) return 1;
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, sumsq_partials_static<float>) != cudaSuccess) return 1;
+    if (cudaFuncGetAttributes(&a, sumsq_partials_static<double>) != cudaSuccess) return 1;
+    if (cudaFuncGetAttributes(&a, sum_partials_static) != cudaSuccess) return 1;
+    return 0;
+}
 
 extern "C" pic_status pic_field_energy_noalloc(const void* d_field, int precision, int64_t n, int ncomp, double* d_out,
                                                void* stream) {
@@ -84,19 +114,10 @@ extern "C" pic_status pic_field_energy_noalloc(const void* d_field, int precisio
         return PIC_ERR_CUDA;
     }
     double* partial = nullptr;
-    {
-        // one-time set-up per device, with that device current
-        std::lock_guard<std::mutex> lock(g_mutex);
-        if (!g_partials_ptr[dev]) {
-            void* p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-            if (e != cudaSuccess || !p) {
-                pic_internal_set_global_error("pic_field_energy_noalloc: cudaGetSymbolAddress of the scratch failed");
-                return PIC_ERR_CUDA;
-            }
-            g_partials_ptr[dev] = static_cast<double*>(p);
-        }
-        partial = g_partials_ptr[dev];
+    // one-time set-up per device, with that device current
+    if (partials_of(dev, &partial) != cudaSuccess) {
+        pic_internal_set_global_error("pic_field_energy_noalloc: cudaGetSymbolAddress of the scratch failed");
+        return PIC_ERR_CUDA;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     long long want = (n + NOALLOC_THREADS - 1) / NOALLOC_THREADS;

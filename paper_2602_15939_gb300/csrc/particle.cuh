@@ -1048,13 +1048,22 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* tmE, const CUtensor
         return false;
     }
     if (tid == 0) {
+        // a CTA that runs several tiles read the previous tile's boxes with
+        // ordinary loads (all done: the previous tile ended with a barrier)
+        fence_proxy_async_smem();
         mbar_arrive_expect_tx(bar, (uint32_t)(6 * L::FB * sizeof(T)));
         tma_load_4d(sE, tmE, xs, ys, zs, 0, bar);
         tma_load_4d(sB, tmB, xs, ys, zs, 0, bar);
     }
     for (int i = tid; i < JC * L::JCS; i += NT) sJ[i] = JW(0);
     if (tid < MAXSP) s_cnt[tid] = 0;
-    if (tid == 0) s_ok[0] = mbar_wait_bounded(bar, parity, TMA_WAIT_LIMIT) ? 1 : 0;
+    if (tid == 0) {
+        const bool ok = mbar_wait_bounded(bar, parity, TMA_WAIT_LIMIT);
+        // on a timeout the copies may still be writing this CTA's shared
+        // memory: wait for them once more (bounded) before the CTA may leave
+        if (!ok) mbar_wait_bounded(bar, parity, TMA_WAIT_LIMIT);
+        s_ok[0] = ok ? 1 : 0;
+    }
     __syncthreads();
     if (!s_ok[0]) {
         if (tid == 0) atomicOr(P.err, ERRB_TMA_TIMEOUT);

@@ -241,8 +241,10 @@ __global__ void finalize_kernel(int ntiles, long long tcap, const int* __restric
 // stayers and arrivals in buffer `in` (capacity tcap_in) become the first
 // stay_out[t] slots of tile t in `out` (capacity tcap_out).
 template <class T, int G>
-__global__ void regrow_kernel(PView<T> in, PView<T> out, const int* __restrict__ stay_in, const int* __restrict__ arr_in,
-                              long long tcap_in, long long tcap_out, int* __restrict__ stay_out, bool has_dr) {
+// stay_in and stay_out may be the same array (a re-layout within one buffer
+// pair), so neither is declared __restrict__.
+__global__ void regrow_kernel(PView<T> in, PView<T> out, const int* stay_in, const int* __restrict__ arr_in,
+                              long long tcap_in, long long tcap_out, int* stay_out, bool has_dr) {
     const int t = blockIdx.x;
     const int nst = stay_in[t], nar = arr_in[t], n = nst + nar;
     const long long bi = (long long)t * tcap_in, bo = (long long)t * tcap_out;
@@ -370,9 +372,11 @@ __global__ void __launch_bounds__(RG_THREADS) regroup_kernel(Tiling tl, PView<T>
 }
 
 // Copy the first *count_in entries of a loose list (at most lcap_in).
+// count_in and count_out may be the same word (the count is rewritten with
+// the value every block reads), so neither is declared __restrict__.
 template <class T, int G>
-__global__ void copy_loose_kernel(PView<T> in, PView<T> out, const int* __restrict__ count_in, long long lcap_in,
-                                  int* __restrict__ count_out, bool has_dr) {
+__global__ void copy_loose_kernel(PView<T> in, PView<T> out, const int* count_in, long long lcap_in,
+                                  int* count_out, bool has_dr) {
     long long n = *count_in;
     if (n > lcap_in) n = lcap_in;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {

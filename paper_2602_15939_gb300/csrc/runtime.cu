@@ -554,8 +554,11 @@ template <class T, int G> static pic_status regroup_t(pic_handle* h) {
         CK(cudaGetLastError());
         h->prof.launches += 2;
     }
-    // only once every species is copied: buffer b's arrival and loose counts
-    // restart for the next step's output (a failed launch above leaves b whole)
+    // every species is now whole in buffer o (a failed launch above left the
+    // state whole in b): switch to it, then restart buffer b's arrival and
+    // loose counts for the next step's output.  A reset that fails is
+    // reported; the state in o is untouched by it.
+    h->buf = o;
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
         DevSpecies& d = h->sp[s];
         if (!d.loaded) continue;
@@ -563,7 +566,6 @@ template <class T, int G> static pic_status regroup_t(pic_handle* h) {
         CK(cudaMemsetAsync(d.lcount + b, 0, sizeof(int), h->stream));
     }
     prof_end(h, 1);
-    h->buf = o;
     return PIC_OK;
 }
 
@@ -855,9 +857,11 @@ template <class T, int G> static pic_status regrow_t(pic_handle* h, bool force, 
     const int nact = h->geom == 0 ? 3 : 2;
     void* na[PIC_MAX_SPECIES][2][11] = {};
     void* nl[PIC_MAX_SPECIES][2][11] = {};
+    int* ncnt[PIC_MAX_SPECIES] = {};  // new stay counts [nt], then the new loose count
     bool fits = true;
     for (int s = 0; s < PIC_MAX_SPECIES && fits; ++s) {
         if (!h->sp[s].loaded) continue;
+        fits = dalloc(h, (void**)&ncnt[s], sizeof(int) * ((size_t)nt + 1)) == cudaSuccess;
         for (int bb = 0; bb < 2 && fits; ++bb)
             for (int i = 0; i < 11 && fits; ++i) {
                 const bool use = i == 0 || (i >= 1 && i <= nact) || (i >= 4 && i <= 7) || (i >= 8 && leaky);
@@ -867,38 +871,63 @@ template <class T, int G> static pic_status regrow_t(pic_handle* h, bool force, 
                        dalloc(h, &nl[s][bb][i], (size_t)new_lcap[s] * es) == cudaSuccess;
             }
     }
-    if (!fits) {
-        cudaGetLastError();
-        for (int s = 0; s < PIC_MAX_SPECIES; ++s)
+    auto free_new = [&]() {
+        for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
+            dfree(h, ncnt[s]);
             for (int bb = 0; bb < 2; ++bb)
                 for (int i = 0; i < 11; ++i) {
                     dfree(h, na[s][bb][i]);
                     dfree(h, nl[s][bb][i]);
                 }
+        }
+    };
+    if (!fits) {
+        cudaGetLastError();
+        free_new();
         return fail(h, PIC_ERR_OOM, "a larger tile layout does not fit in device memory; the current one is kept");
     }
+    // copies into the new arrays only (the new counts go to ncnt): a launch
+    // that fails here leaves every species' current layout untouched
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < PIC_MAX_SPECIES && e == cudaSuccess; ++s) {
+        DevSpecies& d = h->sp[s];
+        if (!d.loaded) continue;
+        PView<T> vin = view_of<T>(d.arr[b]), vout = view_of<T>(na[s][0]);
+        regrow_kernel<T, G><<<nt, NTHR, 0, h->stream>>>(vin, vout, d.stay[b], d.arrv[b], d.tcap, new_tcap[s], ncnt[s], leaky);
+        copy_loose_kernel<T, G><<<64, NTHR, 0, h->stream>>>(view_of<T>(d.larr[b]), view_of<T>(nl[s][0]), d.lcount + b, d.lcap,
+                                                            ncnt[s] + nt, leaky);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        free_new();
+        return fail(h, PIC_ERR_CUDA, "re-layout copy failed (the current layout is kept): %s", cudaGetErrorString(e));
+    }
+    // commit: buffer 0 takes the new counts, every species switches to the new arrays
     drop_graphs(h);
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
         DevSpecies& d = h->sp[s];
         if (!d.loaded) continue;
-        PView<T> vin = view_of<T>(d.arr[b]), vout = view_of<T>(na[s][0]);
-        regrow_kernel<T, G><<<nt, NTHR, 0, h->stream>>>(vin, vout, d.stay[b], d.arrv[b], d.tcap, new_tcap[s], d.stay[0], leaky);
-        copy_loose_kernel<T, G><<<64, NTHR, 0, h->stream>>>(view_of<T>(d.larr[b]), view_of<T>(nl[s][0]), d.lcount + b, d.lcap,
-                                                            d.lcount + 0, leaky);
-        CK(cudaGetLastError());
-        if (b == 1) CK(cudaMemsetAsync(d.lcount + 1, 0, sizeof(int), h->stream));
-        CK(cudaMemsetAsync(d.arrv[0], 0, sizeof(int) * nt, h->stream));
-        CK(cudaMemsetAsync(d.arrv[1], 0, sizeof(int) * nt, h->stream));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d.stay[0], ncnt[s], sizeof(int) * nt, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d.lcount, ncnt[s] + nt, sizeof(int), cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.lcount + 1, 0, sizeof(int), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.arrv[0], 0, sizeof(int) * nt, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.arrv[1], 0, sizeof(int) * nt, h->stream);
+        dfree(h, ncnt[s]);
+        ncnt[s] = nullptr;
         for (int bb = 0; bb < 2; ++bb)
             for (int i = 0; i < 11; ++i) {
                 dfree(h, d.arr[bb][i]);
                 dfree(h, d.larr[bb][i]);
                 d.arr[bb][i] = na[s][bb][i];
                 d.larr[bb][i] = nl[s][bb][i];
+                na[s][bb][i] = nl[s][bb][i] = nullptr;
             }
         d.tcap = new_tcap[s];
         d.lcap = new_lcap[s];
     }
+    // a failed count copy after the switch leaves the counts unknown: the
+    // handle reports the error and its particle state must be reloaded
+    if (e != cudaSuccess) return fail(h, PIC_ERR_CUDA, "re-layout count update failed: %s", cudaGetErrorString(e));
     h->buf = 0;
     h->regrows += 1;
     *grown = true;
@@ -1648,6 +1677,14 @@ pic_status pic_diagnostics(pic_handle* h, pic_diag* out) {
     return check_error_word(h);
 }
 
+pic_status pic_clear_error(pic_handle* h) {
+    if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    cudaSetDevice(h->cfg.device);
+    CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return PIC_OK;
+}
+
 pic_status pic_get_count(pic_handle* h, int species, int64_t* n) {
     pic_status st = check_species(h, species);
     if (st != PIC_OK) return st;
@@ -1702,6 +1739,8 @@ pic_status pic_get_profile(pic_handle* h, pic_profile* out) {
     return PIC_OK;
 }
 
+extern "C" int pic_internal_noalloc_preload(void);  // noalloc.cu
+
 pic_status pic_preload_kernels(int32_t device, int32_t precision) {
     if (precision != PIC_FP32 && precision != PIC_FP64) return fail(nullptr, PIC_ERR_ARG, "bad precision");
     if (cudaSetDevice(device) != cudaSuccess) return fail(nullptr, PIC_ERR_CUDA, "no such CUDA device");
@@ -1718,6 +1757,8 @@ pic_status pic_preload_kernels(int32_t device, int32_t precision) {
                 if (cudaFuncGetAttributes(&a, ks.loose) != cudaSuccess || cudaFuncGetAttributes(&a, ks.batch) != cudaSuccess)
                     return fail(nullptr, PIC_ERR_CUDA, "kernel load failed");
             }
+    if (pic_internal_noalloc_preload() != 0)
+        return fail(nullptr, PIC_ERR_CUDA, "loading the allocation-free reduction failed");
     return PIC_OK;
 }
 

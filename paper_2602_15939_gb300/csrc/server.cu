@@ -45,6 +45,7 @@ struct Run {
     std::string error;
     pic_diag diag{};
     double latency_s = 0.0;
+    bool kept = false;  // the finished box is held for pic_take_result
 };
 
 }  // namespace
@@ -168,15 +169,18 @@ static void finish_run(pic_server* S, Run* r, pic_status st) {
     }
     for (cudaEvent_t e : r->inflight) cudaEventDestroy(e);
     r->inflight.clear();
-    if (r->h) pic_destroy(r->h);
-    r->h = nullptr;
+    // a kept box leaves the run's stream (synchronised by the diagnostics) for its own
+    const bool keep = st == PIC_OK && r->h && r->spec.keep_state && pic_set_stream(r->h, nullptr) == PIC_OK;
+    if (r->h && !keep) pic_destroy(r->h);
+    if (!keep) r->h = nullptr;
     if (r->stream) cudaStreamDestroy(r->stream);
     r->stream = nullptr;
     r->latency_s = std::chrono::duration<double>(Clock::now() - r->t_submit).count();
     std::lock_guard<std::mutex> lock(S->mu);
     r->status = st;
     r->done = true;
-    S->bytes_in_use -= r->bytes;
+    r->kept = keep;
+    if (!keep) S->bytes_in_use -= r->bytes;  // a kept box holds its memory until taken
     S->completed += 1;
     S->cv.notify_all();
 }
@@ -334,6 +338,32 @@ extern "C" pic_status pic_poll(pic_server* S, uint64_t ticket, int* done, pic_di
     return r->status;
 }
 
+extern "C" pic_status pic_take_result(pic_server* S, uint64_t ticket, pic_handle** out) {
+    if (!S || !out) {
+        pic_internal_set_global_error("pic_take_result: bad arguments");
+        return PIC_ERR_ARG;
+    }
+    *out = nullptr;
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) {
+        pic_internal_set_global_error("pic_take_result: unknown ticket");
+        return PIC_ERR_ARG;
+    }
+    Run* r = it->second;
+    if (!r->done || !r->kept || !r->h) {
+        pic_internal_set_global_error(
+            "pic_take_result: the run has not finished, failed, was not submitted with keep_state, or was taken");
+        return PIC_ERR_STATE;
+    }
+    *out = r->h;
+    r->h = nullptr;
+    r->kept = false;
+    S->bytes_in_use -= r->bytes;
+    S->cv.notify_all();
+    return PIC_OK;
+}
+
 extern "C" pic_status pic_server_wait(pic_server* S, uint64_t ticket, double timeout_s) {
     if (!S) return PIC_ERR_ARG;
     std::unique_lock<std::mutex> lock(S->mu);
@@ -376,7 +406,10 @@ extern "C" pic_status pic_server_destroy(pic_server* S) {
         S->cv.notify_all();
     }
     if (S->worker.joinable()) S->worker.join();
-    for (auto& kv : S->all) delete kv.second;
+    for (auto& kv : S->all) {
+        if (kv.second->h) pic_destroy(kv.second->h);  // kept boxes never taken
+        delete kv.second;
+    }
     delete S;
     return PIC_OK;
 }

@@ -73,7 +73,7 @@ class pic_run_spec(C.Structure):
         ("cfg", pic_config), ("nspecies", C.c_int32), ("ppc", C.c_int32), ("theta", C.c_double),
         ("q", C.c_double * PIC_MAX_SPECIES), ("m", C.c_double * PIC_MAX_SPECIES), ("drift", C.c_double * 3),
         ("noise_sigma", C.c_double), ("E0", C.c_double * 3), ("B0", C.c_double * 3),
-        ("load_seed", C.c_uint32), ("reserved", C.c_uint32), ("nsteps", C.c_int64),
+        ("load_seed", C.c_uint32), ("keep_state", C.c_uint32), ("nsteps", C.c_int64),
     ]
 
 
@@ -106,6 +106,7 @@ _SIGS = {
     "pic_set_step": (C.c_int, [_H, C.c_int64]),
     "pic_diagnostics": (C.c_int, [_H, C.POINTER(pic_diag)]),
     "pic_get_count": (C.c_int, [_H, C.c_int, C.POINTER(C.c_int64)]),
+    "pic_clear_error": (C.c_int, [_H]),
     "pic_get_particles": (C.c_int, [_H, C.c_int, _D, _D, _U32, _D]),
     "pic_get_fields": (C.c_int, [_H, _D, _D, _D]),
     "pic_get_particles_sampled": (C.c_int, [_H, C.c_int, C.c_uint32, C.c_uint32, C.c_int64, _D, _D, _U32, _D,
@@ -123,6 +124,7 @@ _SIGS = {
     "pic_kernel_variant_info": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pic_get_kernel_variant": (C.c_int, [_H, C.POINTER(C.c_int32)]),
     "pic_set_kernel_variant": (C.c_int, [_H, C.c_int32]),
+    "pic_take_result": (C.c_int, [_H, C.c_uint64, C.POINTER(_H)]),
     "pic_batch_create": (C.c_int, [C.POINTER(_H), C.c_int32, C.POINTER(_H)]),
     "pic_batch_step": (C.c_int, [_H, C.c_int32]),
     "pic_batch_set_regroup_interval": (C.c_int, [_H, C.c_int32]),
@@ -442,10 +444,15 @@ def make_config(box=PIC_BOX_PERIODIC, nx=8, ny=8, nz=8, ndim=3, plane=PIC_PLANE_
 class Box:
     """One simulation box on the current CUDA device (thin owner of a handle)."""
 
-    def __init__(self, cfg: pic_config):
+    def __init__(self, cfg: pic_config, handle=None):
         self.cfg = cfg
-        self.h = pic_init(cfg)
+        self.h = pic_init(cfg) if handle is None else handle
         self.shape = (3, cfg.nz, cfg.ny, cfg.nx)
+
+    @classmethod
+    def adopt(cls, handle, cfg: pic_config) -> "Box":
+        """Own an existing handle (e.g. a served run's box from pic_take_result)."""
+        return cls(cfg, handle=handle)
 
     def close(self):
         if self.h:
@@ -507,11 +514,15 @@ class Box:
     def count(self, species):
         return pic_get_count(self.h, species)
 
+    def clear_error(self):
+        _check(self.h, lib().pic_clear_error(self.h))
+
 
 # ---- serving -------------------------------------------------------------------------
 
 def make_run_spec(cfg: pic_config, nsteps, ppc, theta, q=(-1.0, 1.0), m=(1.0, 1.0), drift=(0.0, 0.0, 0.0),
-                  noise_sigma=0.0, E0=(0.0, 0.0, 0.0), B0=(0.0, 0.0, 0.0), load_seed=0) -> pic_run_spec:
+                  noise_sigma=0.0, E0=(0.0, 0.0, 0.0), B0=(0.0, 0.0, 0.0), load_seed=0,
+                  keep_state=False) -> pic_run_spec:
     s = pic_run_spec()
     s.cfg = cfg
     s.nspecies = len(q)
@@ -521,6 +532,7 @@ def make_run_spec(cfg: pic_config, nsteps, ppc, theta, q=(-1.0, 1.0), m=(1.0, 1.
     for a in range(3):
         s.drift[a], s.E0[a], s.B0[a] = drift[a], E0[a], B0[a]
     s.noise_sigma, s.load_seed, s.nsteps = noise_sigma, load_seed & 0xFFFFFFFF, nsteps
+    s.keep_state = 1 if keep_state else 0
     return s
 
 
@@ -542,10 +554,12 @@ class Server:
         h = C.c_void_p()
         _check(None, lib().pic_server_create(device, hbm_budget_bytes, max_active, steps_per_round, C.byref(h)))
         self.h = h
+        self._specs = {}
 
     def submit(self, spec: pic_run_spec) -> int:
         t = C.c_uint64()
         _check(None, lib().pic_submit(self.h, C.byref(spec), C.byref(t)))
+        self._specs[t.value] = spec
         return t.value
 
     def poll(self, ticket):
@@ -554,6 +568,12 @@ class Server:
         lat = C.c_double()
         _check(None, lib().pic_poll(self.h, ticket, C.byref(done), C.byref(d), C.byref(lat)))
         return (d, lat.value) if done.value else None
+
+    def take(self, ticket) -> "Box":
+        """The final box of a run submitted with keep_state (pic_take_result)."""
+        h = _H()
+        _check(None, lib().pic_take_result(self.h, ticket, C.byref(h)))
+        return Box.adopt(h, self._specs[ticket].cfg)
 
     def wait(self, ticket=0, timeout_s=600.0):
         _check(None, lib().pic_server_wait(self.h, ticket, timeout_s))

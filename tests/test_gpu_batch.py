@@ -140,21 +140,33 @@ def test_more_boxes_than_one_launch_holds():
 
 @pytest.mark.gpu
 def test_batched_box_matches_oracle():
+    """A batched box against the oracle over a graph-replayed pair of steps
+    (regrouping off, so the batch's first cycle is a captured pair; FP32
+    tolerances doubled for two steps)."""
     c = EXPAND[0]
-    got = run_batched(EXPAND, 1, False)[0]
-    st, _ = run_oracle(c, 1)
+    loaded = [load(x, False) for x in EXPAND]
+    try:
+        with P.Batch([b for b, _ in loaded]) as bt:
+            bt.set_regroup_interval(0)
+            bt.step(2)
+            bt.sync()
+        got = state(*loaded[0])
+    finally:
+        for b, _ in loaded:
+            b.close()
+    st, _ = run_oracle(c, 2)
     (parts, (E, B, J), _) = got
     for (x, u, ids), d in zip(parts, st.species):
         o = np.argsort(d["id"])
         assert np.array_equal(ids, d["id"][o])
-        assert rel_maxerr(u, d["u"][o]) <= 1e-6
+        assert rel_maxerr(u, d["u"][o]) <= 2e-6
         dx = x - d["x"][o]
         dx -= np.asarray(c.n) * np.round(dx / np.asarray(c.n))
-        assert np.abs(dx).max() <= 2e-6
+        assert np.abs(dx).max() <= 4e-6
     jref = current_scale(c)
-    assert rel_maxerr(J, st.J, jref) <= 1e-6
-    assert rel_maxerr(E, st.E, 4 * np.pi * jref) <= 1e-6
-    assert rel_maxerr(B, st.B, 4 * np.pi * jref) <= 1e-6
+    assert rel_maxerr(J, st.J, jref) <= 2e-6
+    assert rel_maxerr(E, st.E, 4 * np.pi * jref) <= 2e-6
+    assert rel_maxerr(B, st.B, 4 * np.pi * jref) <= 2e-6
 
 
 @pytest.mark.gpu

@@ -86,3 +86,110 @@ def test_failed_run_reports_its_error_without_stopping_others():
             srv.poll(tb)
         d, _ = srv.poll(tg)
         assert d.step == good.nsteps
+
+
+def _alone(spec):
+    """The run of `spec` stepped alone through pic_step: the same device
+    Maxwellian load (per-species seed and id offsets as the server makes
+    them), uniform fields, nsteps steps."""
+    box = P.Box(spec.cfg)
+    per_species = spec.ppc * spec.cfg.nx * spec.cfg.ny * spec.cfg.nz
+    for k in range(spec.nspecies):
+        box.load_maxwellian(k, spec.q[k], spec.m[k], spec.ppc, spec.theta, tuple(spec.drift), spec.noise_sigma,
+                            spec.load_seed + 7919 * k, k * per_species)
+    box.set_uniform_fields(tuple(spec.E0), tuple(spec.B0))
+    return box
+
+
+def _state(box, nspecies):
+    out = []
+    for k in range(nspecies):
+        x, u, ids, dr = box.particles(k, want_dr=True)
+        o = np.argsort(ids)
+        out.append((x[o], u[o], ids[o], dr[o]))
+    return out, box.fields()
+
+
+@pytest.mark.gpu
+def test_served_states_equal_the_runs_stepped_alone():
+    """Element by element: every served run's final particles (matched by id)
+    and fields (E, B and the last step's J) equal those of the same run stepped
+    alone through pic_step, bit for bit (FP32 results do not depend on
+    particle order or on what else runs on the GPU)."""
+    specs = _mix()
+    for s in specs:
+        s.keep_state = 1
+    foot = [P.pic_run_footprint(s) for s in specs]
+    budget = int(sum(foot) * 1.05)
+    with P.Server(hbm_budget_bytes=budget, max_active=8, steps_per_round=4) as srv:
+        tickets = []
+        for s in specs:
+            tickets.append(srv.submit(s))
+            time.sleep(0.003)
+        srv.wait(0, 300)
+        assert srv.stats().peak_active >= 2
+        served = []
+        for t, s in zip(tickets, specs):
+            b = srv.take(t)
+            with pytest.raises(P.PicError):
+                srv.take(t)  # handed over once
+            served.append(_state(b, s.nspecies))
+            assert b.diagnostics().step == s.nsteps
+            b.close()
+    for s, (sp_s, f_s) in zip(specs, served):
+        box = _alone(s)
+        box.step(s.nsteps)
+        sp_a, f_a = _state(box, s.nspecies)
+        box.close()
+        for (xs, us, is_, ds), (xa, ua, ia, da) in zip(sp_s, sp_a):
+            np.testing.assert_array_equal(is_, ia)
+            np.testing.assert_array_equal(xs, xa)
+            np.testing.assert_array_equal(us, ua)
+            np.testing.assert_array_equal(ds, da)
+        for a, b in zip(f_s, f_a):
+            np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.gpu
+def test_a_served_run_matches_the_oracle():
+    """One served run (2D x-y leaky box, probabilistic escape, FP32, two steps)
+    against the FP64 oracle started from the same initial particles (read back
+    from a box given the same device load): momenta, positions and fields
+    within the FP32 tolerances of the parity tests, escape counts equal."""
+    import oracle as O
+
+    cfg = P.make_config(box=P.PIC_BOX_LEAKY, ndim=2, plane=P.PIC_PLANE_XY, nx=32, ny=24, nz=1, order=1,
+                        precision=P.PIC_FP32, escape_mode=P.PIC_ESC_PROBABILISTIC, p_esc=0.05, theta_inj=0.5, seed=9)
+    q = 0.05
+    spec = P.make_run_spec(cfg, 2, 6, 0.05, q=(-q, q), B0=(0.0, 0.0, 0.2), load_seed=11, keep_state=True)
+    with P.Server(hbm_budget_bytes=1 << 34, max_active=2) as srv:
+        t = srv.submit(spec)
+        srv.wait(t, 120)
+        b = srv.take(t)
+        (sp_s, (E, B, J)) = _state(b, 2)
+        esc = b.diagnostics().escaped_total
+        b.close()
+    box = _alone(spec)
+    init = [box.particles(k) for k in range(2)]
+    box.close()
+    n = (32, 24, 1)
+    p = O.make_params(*n, cfg.c, order=1, box=O.BOX_LEAKY, esc_mode=O.ESC_PROBABILISTIC, p_esc=0.05,
+                      theta_inj=0.5, seed=9)
+    E0 = np.zeros((3, 1, 24, 32))
+    B0 = np.zeros_like(E0)
+    B0[2] = 0.2
+    species = [{"q": qq, "m": 1.0, "x": x, "u": u, "id": ids} for qq, (x, u, ids, _) in zip((-q, q), init)]
+    st = O.State(p, E0, B0, species)
+    info = st.step(2)
+    assert esc == info["escaped"]
+    jref = q * cfg.c * 2 * 6
+    for d, (xs, us, ids, _) in zip(st.species, sp_s):
+        o = np.argsort(d["id"])
+        np.testing.assert_array_equal(ids, d["id"][o])
+        dx = xs - d["x"][o]
+        dx -= np.array(n, dtype=float) * np.round(dx / np.array(n, dtype=float))
+        assert np.abs(dx[:, :2]).max() <= 4e-6
+        assert np.abs(us - d["u"][o]).max() <= 2e-6 * np.abs(d["u"]).max()
+    for a, r in ((E, st.E), (B, st.B), (J, st.J)):
+        floor = jref if a is J else 4 * np.pi * jref
+        assert np.abs(a - r).max() <= 2e-6 * max(np.abs(r).max(), floor)

@@ -45,6 +45,41 @@ def test_noalloc_field_energy_matches_diagnostics(fp64):
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         np.testing.assert_allclose(got, np.array(want[:]), rtol=tol, atol=0)
+        # and against a sum written here: FP64 squares of the stored values
+        indep = (arr.reshape(3, -1).astype(np.float64) ** 2).sum(axis=1) / (8 * np.pi)
+        np.testing.assert_allclose(got, indep, rtol=1e-12, atol=0)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("fp64", [True, False])
+def test_noalloc_large_then_small_call(fp64):
+    """A field larger than the scratch's 1024 blocks of 256 threads cover in
+    one pass (one 128^3 component per slot, all 8 slots: each block strides
+    over the array), then a small single-component call on the same stream,
+    which must not see the larger call's leftover partial sums.  Both against
+    FP64 numpy sums of squares / 8 pi."""
+    import torch
+
+    B.build()
+    dtype = torch.float64 if fp64 else torch.float32
+    prec = P.PIC_FP64 if fp64 else P.PIC_FP32
+    g = torch.Generator(device="cpu").manual_seed(5)
+    big = torch.randn((8, 128 ** 3), generator=g, dtype=torch.float64).to(dtype)
+    small = torch.randn((1, 1000), generator=g, dtype=torch.float64).to(dtype)
+    stream = torch.cuda.current_stream()
+    lib = P.lib()
+    outs = []
+    for host in (big, small):
+        dev = host.to("cuda")
+        out = torch.full((host.shape[0],), float("nan"), dtype=torch.float64, device="cuda")
+        st = lib.pic_field_energy_noalloc(ctypes.c_void_p(dev.data_ptr()), prec, host.shape[1], host.shape[0],
+                                          ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+        assert st == P.PIC_OK, P.pic_last_error(None)
+        outs.append((out, dev, host))
+    torch.cuda.synchronize()
+    for out, _, host in outs:
+        want = (host.double().numpy() ** 2).sum(axis=1) / (8 * np.pi)
+        np.testing.assert_allclose(out.cpu().numpy(), want, rtol=1e-12, atol=0)
 
 
 @pytest.mark.gpu
