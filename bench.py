@@ -1,13 +1,23 @@
 #!/usr/bin/env python
 """Throughput benchmark of the PIC step (particle-steps/s) on GB300.
 
-Default workload: the 3D expanding-box pair plasma, 128^3 cells, 32 particles
-per cell per species (134,217,728 particles), quadratic shapes, FP32 particle
-state (int32 cell + float offsets) with FP64 expansion factors -- a seeded
-synthetic stand-in shaped like the paper's expanding-box setup (Sec. 3.3).
-A "step" is one full PIC step: sort-in-place, gather, push, deposit, current
-fold and the transformed Maxwell update.  Inputs (4.3 GB of particles) are
-larger than the L2 cache, so no flush is needed between steps.
+Headline workload: the 3D shearing-box (KSB-OA) pair plasma, 256^3 cells, 32
+particles per cell per species (1,073,741,824 particles), quadratic shapes,
+FP32 particle state (int32 cell + float offsets) with the FP64 shear-remap
+offset, four fixed-point sweeps of the implicit Maxwell solve -- a seeded
+synthetic stand-in shaped like the paper's MRI shearing box (Sec. 2.3), and
+the largest configuration that fits one GPU.  A "step" is one full PIC step:
+gather, push, position update, charge-conserving deposit and tile sort
+(fused), current fold and y advection, and the field solve.  Inputs (about
+34 GB of particles) are far larger than the L2 cache, so no flush is needed
+between steps.
+
+Beside the headline the line carries the other configurations (3D expanding
+box 128^3, 2D leaky box 2048^2, 2D shearing box 64^2 in FP64), each with its
+FP32 and FP64 rates and its particle-kernel roofline; an end-to-end figure
+through the C ABI with host buffers; the served ensemble (a bounded sample and
+a bounded prefix of the full-range stream); batched against separate stepping;
+and the FP64 CPU oracle timed on the host cores (single-threaded and OpenMP).
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Under torchrun (N > 1) every rank runs an independent replica (weak scaling;
@@ -32,7 +42,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s (gather+push+deposit), FP32 vs FP64; ensemble p99 latency"
 UNIT = "particle-steps/s"
-
+HEADLINE = "ksb3d_256_fp32"
+EXTRA_CONFIGS = ("keb3d_128_fp32", "leaky2d_2048_fp32", "ksb2d_64x64_fp64")
 
 BOX_NAMES = {0: "periodic", 1: "shearing", 2: "expanding", 3: "leaky"}
 
@@ -43,13 +54,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="keb3d_128_fp32")
+    ap.add_argument("--workload", default=HEADLINE)
     ap.add_argument("--grid", default=None, help="override the grid, e.g. 64,64,64 (profiling a smaller case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="headline workload only")
     ap.add_argument("--serve-runs", type=int, default=64)
+    ap.add_argument("--full-serve-runs", type=int, default=24,
+                    help="prefix of the full-range served-ensemble stream that is timed")
     ap.add_argument("--kernel-only", action="store_true", help="warmup + timed steps only (for profiler runs)")
     ap.add_argument("--batch-legs-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--seed", type=int, default=0, help=argparse.SUPPRESS)
@@ -99,6 +113,13 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for name in ("particle.cuh", "common.cuh"):
@@ -109,8 +130,8 @@ def kernel_source_hash():
 
 def stored_traffic(workload, variant):
     """DRAM bytes per launch of the particle kernel (launch variant `variant`)
-    from the committed ncu summary, if it was taken on the current kernel
-    source."""
+    at the workload's full size, from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
     p = os.path.join(ROOT, "profiles", f"tile_kernel_{workload}.md")
     if not os.path.exists(p):
         return None
@@ -120,6 +141,53 @@ def stored_traffic(workload, variant):
     if not m_hash or not m_b or m_hash.group(1) != kernel_source_hash():
         return None
     return float(m_b.group(1))
+
+
+# ---- algorithmic bytes ------------------------------------------------------------------------
+# The particle state the method itself needs, read once and written once per
+# step: the int32 cell index, the in-cell offsets of the active axes and the
+# three momentum components; the particle id only where random numbers are
+# drawn (probabilistic escape keys its Philox stream on it); the tested
+# components of the leaky displacement under the displacement rule.  The grid
+# side of a step moves about 15 words per cell per field sweep (E, B read and
+# written, J read): 60 B/cell in FP32, 120 B/cell in FP64, times the sweeps of
+# the implicit shearing-box solve.  The fused particle kernel itself reads E
+# and B and writes J once per tile: 9 words per cell.
+
+def alg_state_bytes(w, esc_dims=2):
+    es = 8 if w.fp64 else 4
+    need_id = w.escape_mode == 2
+    ndr = esc_dims if w.escape_mode == 1 else 0
+    return 4 + w.ndim * es + 3 * es + (4 if need_id else 0) + ndr * es
+
+
+def stored_state_bytes(w):
+    """What the layout stores per particle: the id always (for read-back), the
+    three displacement components under the displacement rule."""
+    es = 8 if w.fp64 else 4
+    return 4 + w.ndim * es + 3 * es + 4 + (3 * es if w.escape_mode == 1 else 0)
+
+
+def sweeps_of(w):
+    return 4 if w.box == 1 else 1
+
+
+def bytes_model(w, regroup_every):
+    es = 8 if w.fp64 else 4
+    ncell = w.n[0] * w.n[1] * w.n[2]
+    npart = w.n_particles
+    particle = 2 * alg_state_bytes(w)
+    grid_per_particle = 15 * es * sweeps_of(w) / (2.0 * w.ppc)
+    overhead_id = 2 * (stored_state_bytes(w) - alg_state_bytes(w))
+    overhead_regroup = (2.0 * stored_state_bytes(w) / regroup_every) if regroup_every else 0.0
+    return {
+        "particle_bytes_per_particle_step": particle,
+        "grid_bytes_per_particle_step": grid_per_particle,
+        "step_bytes_per_particle_step": particle + grid_per_particle,
+        "kernel_bytes_per_launch": npart * particle + ncell * 9 * es,
+        "overhead_bytes_per_particle_step": {"stored_id_and_unused_components": overhead_id,
+                                             "regroup_pass": overhead_regroup},
+    }
 
 
 class ClockSampler:
@@ -171,8 +239,11 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_rate(w, n_sub, steps, seed=0):
-    """Particle-steps/s of the FP64 CPU oracle on a sub-box of workload w."""
+# ---- the FP64 CPU oracle on the host cores --------------------------------------------------------
+
+def oracle_rate(w, n_sub, steps, seed=0, threads=1):
+    """Per-step wall times of the FP64 CPU oracle on a sub-box of workload w
+    (same particles per cell, same box parameters), on `threads` threads."""
     import numpy as np
 
     import oracle as O
@@ -192,17 +263,40 @@ def oracle_rate(w, n_sub, steps, seed=0):
     st = O.State(p, E, B, sp)
     npart = sum(len(d["x"]) for d in sp)
     times = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        st.step(1)
-        times.append(time.perf_counter() - t0)
+    O.set_threads(threads)
+    try:
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            st.step(1)
+            times.append(time.perf_counter() - t0)
+    finally:
+        O.set_threads(1)
     return npart, times
 
 
-def sub_box(w):
+def sub_box(w, threads=1):
+    """A sub-box of w with the same particles per cell, sized for a few
+    seconds of oracle work per step at the given thread count."""
     if w.ndim == 3:
-        return (16, 16, 16)
-    return (64, 64, 1) if w.plane == 0 else (64, 1, 64)
+        return (32, 32, 32) if threads >= 8 else (16, 16, 16)
+    m = 128 if threads >= 8 else 64
+    return (m, m, 1) if w.plane == 0 else (m, 1, m)
+
+
+def cpu_baseline(w, steps=3):
+    """The oracle as it stands, single-threaded and across every host core."""
+    cores = host_cores()
+    out = {}
+    legs = [("single_thread", 1)] + ([("openmp", cores)] if cores > 1 else [])
+    for name, th in legs:
+        n_sub = sub_box(w, th)
+        n_o, times = oracle_rate(w, n_sub, steps, threads=th)
+        out[name] = {"value": n_o * len(times) / sum(times), "unit": UNIT, "cores": th,
+                     "sample": f"{n_sub[0]}x{n_sub[1]}x{n_sub[2]} sub-box of {w.name} at {w.ppc} ppc/species "
+                               f"({n_o} particles), {len(times)} steps, FP64 C oracle on {th} thread(s)"}
+    best = out.get("openmp", out["single_thread"])
+    return {"value": best["value"], "unit": UNIT, "cores": best["cores"], "kind": "oracle", "sample": best["sample"],
+            "host_cores": cores, "legs": out}
 
 
 def run_reference(args):
@@ -212,31 +306,23 @@ def run_reference(args):
     if rank != 0:
         return 0
     w = W.SUITE[args.workload]
-    n_sub = sub_box(w)
+    cores = host_cores()
+    n_sub = sub_box(w, cores)
     npart, _ = oracle_rate(w, n_sub, 0)
-    _, wt = oracle_rate(w, n_sub, args.warmup + args.steps)
+    _, wt = oracle_rate(w, n_sub, args.warmup + args.steps, threads=cores)
     times = wt[args.warmup:]
     tot = sum(times)
     value = npart * len(times) / tot
     sample = f"{n_sub[0]}x{n_sub[1]}x{n_sub[2]} sub-box of {w.name}, {w.ppc} ppc/species ({npart} particles), " \
-             f"{len(times)} timed steps after {args.warmup} warm-up"
+             f"{len(times)} timed steps after {args.warmup} warm-up, FP64 C oracle on {cores} thread(s)"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / max(1, len(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "sample": sample, "box": "expanding" if w.box == 2 else str(w.box)},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": w.name, "sample": sample, "box": BOX_NAMES.get(w.box, str(w.box))},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
-
-
-def particle_bytes(fp64, ndim, leaky_disp):
-    """Algorithmic bytes per particle-step of the fused kernel: the particle
-    state read once and written once (cell index, in-cell offsets, momentum,
-    id, and the leaky displacement when tracked)."""
-    es = 8 if fp64 else 4
-    state = 4 + ndim * es + 3 * es + 4 + (3 * es if leaky_disp else 0)
-    return 2 * state
 
 
 def setup_box(w, device, stream, fp64=None, seed=0):
@@ -245,34 +331,25 @@ def setup_box(w, device, stream, fp64=None, seed=0):
     return W.setup_box(w, device=device, stream=stream, fp64=fp64, seed=seed)
 
 
-def run_gb300(args):
-    import numpy as np
+# ---- one configuration on the GPU ----------------------------------------------------------------
+
+def measure(w, args, device, stream, rank, world, headline):
+    """Warm-up, autotune (or forced variant), K timed graph-replayed steps
+    (CUDA events on the box's stream), then an untimed profiled pass for the
+    particle kernel's launch time.  Returns the box (still open) and a dict."""
     import torch
     import torch.distributed as dist
 
-    from paper_2602_15939_gb300 import build as libbuild
     from paper_2602_15939_gb300 import pic as P
-    from paper_2602_15939_gb300 import workloads as W
 
-    rank, world, local = dist_env()
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    libbuild.build()
-    w = W.SUITE[args.workload]
-    if args.grid:
-        w = W.scaled(w, tuple(int(v) for v in args.grid.split(",")))
-    stream = torch.cuda.Stream()
-    box = setup_box(w, local, stream.cuda_stream, seed=replica_seed(rank))
+    box = setup_box(w, device, stream.cuda_stream, seed=replica_seed(rank))
     npart = w.n_particles
     box.step(args.warmup)
-    # particle-kernel launch variant: autotuned on this machine (trial steps are
-    # ordinary, untimed steps) unless forced
     if args.variant:
         P.pic_set_kernel_variant(box.h, args.variant)
         tune = {"chosen": args.variant, "how": "forced"}
     else:
-        best, ms_v, taken = box.autotune(4)
+        best, ms_v, taken = box.autotune(4 if headline or w.n_particles > 1e8 else 2)
         tune = {"chosen": best, "how": f"autotuned on {taken} untimed steps",
                 "particle_ms_per_variant": [None if v is None else round(v, 4) for v in ms_v]}
     nt_, st_, jc_ = P.pic_kernel_variant_info(tune["chosen"])
@@ -281,12 +358,12 @@ def run_gb300(args):
     torch.cuda.synchronize()
 
     def barrier():
-        if world > 1:
+        if world > 1 and headline:
             dist.barrier()
 
-    # timed region: K steps (CUDA-graph replay), CUDA events on the box's stream
-    sampler = ClockSampler(local)
-    sampler.start()
+    sampler = ClockSampler(device) if headline else None
+    if sampler:
+        sampler.start()
     P.pic_reset_profile(box.h)
     barrier()
     torch.cuda.synchronize()
@@ -297,7 +374,7 @@ def run_gb300(args):
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler else None
     ms = e0.elapsed_time(e1)
     gpu_launches = int(P.pic_get_profile(box.h).launches)
     # second pass with per-kernel-group events (no graphs) for the roofline
@@ -309,72 +386,115 @@ def run_gb300(args):
     P.pic_set_profiling(box.h, False)
     diag = box.diagnostics()
     assert diag.error_word == 0, diag.error_word
-    ms = max_over_ranks(ms, world, device="cuda")
-    value = whole_job_rate(npart, args.steps, world, ms)
+    if headline:
+        ms = max_over_ranks(ms, world, device="cuda")
+    value = whole_job_rate(npart, args.steps, world if headline else 1, ms)
     particle_ms = prof.ms_particle / max(1, prof.particle_launches)
-
+    regroup = P.pic_get_regroup_interval(box.h)
+    bm = bytes_model(w, regroup)
     peak, peak_kind = measured_peaks()
-    ncell = w.n[0] * w.n[1] * w.n[2]
-    bpp = particle_bytes(w.fp64, w.ndim, w.escape_mode == 1)
-    es = 8 if w.fp64 else 4
-    alg_bytes = npart * bpp + ncell * (6 + 3) * es
-    achieved = alg_bytes / (particle_ms / 1e3) / 1e9
+    achieved = bm["kernel_bytes_per_launch"] / (particle_ms / 1e3) / 1e9
     traffic = stored_traffic(w.name, tune["chosen"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_kind": f"{peak_kind} HBM copy bandwidth",
-                "kernel": "tile_kernel (fused gather+push+deposit+sort)",
-                "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_particle": bpp,
-                "avg_launch_ms": particle_ms}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "traffic": traffic, "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)",
+                "kernel": "tile_kernel (fused gather+push+deposit+tile sort)",
+                "algorithmic_bytes_per_launch": bm["kernel_bytes_per_launch"],
+                "bytes_per_particle": bm["particle_bytes_per_particle_step"],
+                "avg_launch_ms": particle_ms,
+                "step_frac": (npart * bm["step_bytes_per_particle_step"] / (ms / args.steps / 1e3) / 1e9) / peak,
+                "step_bytes_per_particle_step": bm["step_bytes_per_particle_step"],
+                "overhead_bytes_per_particle_step": bm["overhead_bytes_per_particle_step"]}
+    res = {"value": value, "ms_per_step": ms / args.steps, "particles": npart, "steps": args.steps,
+           "particle_phase": {"value": npart / (particle_ms / 1e3), "unit": UNIT, "avg_launch_ms": particle_ms},
+           "profile_ms_per_step": {"particle": prof.ms_particle / args.steps, "field": prof.ms_field / args.steps,
+                                   "other": prof.ms_other / args.steps,
+                                   "other_is": "loose kernel, tile bookkeeping, regroup by cell"},
+           "gpu_launches": gpu_launches, "roofline": roofline, "kernel_variant": tune, "regroup_every": regroup,
+           "clocks": clocks}
+    return box, res
+
+
+def measure_fp64(w, args, device, stream, rank):
+    """The plain FP64 method on the same workload: a few graph-replayed steps."""
+    import torch
+
+    b64 = setup_box(w, device, stream.cuda_stream, fp64=True, seed=replica_seed(rank))
+    b64.step(2)
+    b64.sync()
+    k64 = max(2, min(args.steps, 4))
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    b64.step(k64)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = f0.elapsed_time(f1)
+    b64.close()
+    torch.cuda.synchronize()
+    return {"value": w.n_particles * k64 / (ms64 / 1e3), "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64}
+
+
+def run_gb300(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2602_15939_gb300 import build as libbuild
+    from paper_2602_15939_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    libbuild.build()
+    w = W.SUITE[args.workload]
+    if args.grid:
+        w = W.scaled(w, tuple(int(v) for v in args.grid.split(",")))
+    stream = torch.cuda.Stream()
+    box, res = measure(w, args, local, stream, rank, world, headline=True)
+    box.close()
+    torch.cuda.synchronize()
+    line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if w.fp64 else "f32", "data": "synthetic",
-            "config": {"workload": w.name, "grid": list(w.n), "ppc_per_species": w.ppc, "particles": npart,
-                       "shape_order": w.order, "box": BOX_NAMES.get(w.box, str(w.box)), "expansion_rate_wp": list(w.rate_wp),
+            "config": {"workload": w.name, "grid": list(w.n), "ppc_per_species": w.ppc, "particles": w.n_particles,
+                       "shape_order": w.order, "box": BOX_NAMES.get(w.box, str(w.box)),
+                       "field_sweeps": sweeps_of(w),
                        "precision": ("int32 cell + fp64 offsets/momenta" if w.fp64 else
-                                     "int32 cell + fp32 offsets/momenta, fp64 l(t)"),
+                                     "int32 cell + fp32 offsets/momenta, fp64 shear shift / l(t) / sums"),
                        "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}",
-                       "kernel_variant": tune, "regroup_every": P.pic_get_regroup_interval(box.h)},
-            "particle_phase": {"value": npart / (particle_ms / 1e3), "unit": UNIT, "avg_launch_ms": particle_ms},
-            "profile_ms_per_step": {"particle": prof.ms_particle / args.steps, "field": prof.ms_field / args.steps,
-                                    "other": prof.ms_other / args.steps,
-                                    "other_is": "loose kernel, tile bookkeeping, regroup by cell"},
-            "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks}
+                       "kernel_variant": res["kernel_variant"], "regroup_every": res["regroup_every"]},
+            "particle_phase": res["particle_phase"], "profile_ms_per_step": res["profile_ms_per_step"],
+            "gpu_launches": res["gpu_launches"], "roofline": res["roofline"], "clocks": res["clocks"]}
 
-    # FP64 path on the same workload (the plain FP64 method), a few steps
     if not args.no_fp64 and not args.kernel_only:
-        box.close()
-        torch.cuda.synchronize()
-        b64 = setup_box(w, local, stream.cuda_stream, fp64=True, seed=replica_seed(rank))
-        b64.step(2)
-        b64.sync()
-        k64 = max(2, min(args.steps, 5))
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        b64.step(k64)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = f0.elapsed_time(f1)
-        line["fp64"] = {"value": npart * k64 / (ms64 / 1e3), "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64}
-        b64.close()
-        box = None
-    elif box is not None:
-        box.close()
+        line["fp64"] = measure_fp64(w, args, local, stream, rank)
 
-    # end to end through the C ABI with pinned host buffers
+    # the other configurations: FP32 (or the configuration's precision) and FP64 each
+    if not args.no_extra and not args.kernel_only and not args.grid:
+        configs = {}
+        for name in EXTRA_CONFIGS:
+            wx = W.SUITE[name]
+            bx, rx = measure(wx, args, local, stream, rank, world, headline=False)
+            bx.close()
+            torch.cuda.synchronize()
+            rx.pop("clocks", None)
+            entry = {"workload": name, "grid": list(wx.n), "particles": wx.n_particles,
+                     "box": BOX_NAMES.get(wx.box, str(wx.box)), "dtype": "f64" if wx.fp64 else "f32", **rx}
+            if not wx.fp64 and not args.no_fp64:
+                entry["fp64"] = measure_fp64(wx, args, local, stream, rank)
+            configs[name] = entry
+        line["configs"] = configs
+
     if not args.no_e2e and not args.kernel_only:
         line["e2e"] = run_e2e(w, local, stream, args.steps, rank)
 
     if not args.no_serving and not args.kernel_only:
         line["serving"] = run_serving(local, seed=rank, runs=args.serve_runs)
+        line["serving_full_range"] = run_serving(local, seed=rank, runs=args.full_serve_runs, full=True)
         line["batched_ensemble"] = batch_legs_subprocess(local, rank)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.kernel_only:
-        n_sub = sub_box(w)
-        n_o, times = oracle_rate(w, n_sub, 5)
-        line["cpu_baseline"] = {"value": n_o * len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{n_sub[0]}x{n_sub[1]}x{n_sub[2]} sub-box of {w.name} at {w.ppc} "
-                                          f"ppc/species ({n_o} particles), 5 steps, single-threaded FP64 C"}
+        line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -382,10 +502,13 @@ def run_gb300(args):
     return 0
 
 
-def run_serving(device, seed=0, runs=64):
-    """A bounded sample of the served-ensemble workload: a Poisson stream of
-    independent shearing / expanding / leaky runs (2D and 3D, FP32) submitted
-    to libpic's continuous-batching server; runs/s and time to result."""
+def run_serving(device, seed=0, runs=64, full=False):
+    """The served-ensemble workload through libpic's continuous-batching
+    server: a Poisson stream of independent shearing / expanding / leaky runs
+    (2D and 3D, FP32).  full=False: a bounded sample (reduced grids and step
+    counts); full=True: the first `runs` arrivals of the configuration's own
+    stream (2D 32^2-512^2, 3D 32^3-96^3, 8-64 ppc/species, 200-2000 steps,
+    arrivals at 0.8x the measured capacity).  runs/s, p50/p99 time to result."""
     import threading
 
     import numpy as np
@@ -393,15 +516,22 @@ def run_serving(device, seed=0, runs=64):
     from paper_2602_15939_gb300 import pic as P
     from paper_2602_15939_gb300 import workloads as W
 
-    runs = W.served_ensemble(runs, seed=seed)
-    specs = [W.run_spec_of(r) for r in runs]
-    work = sum(2 * r["ppc"] * r["n"][0] * r["n"][1] * r["n"][2] * r["steps"] for r in runs)
+    gap = 0.002
+    if full:
+        # arrival rate ~0.8x capacity: mean work per run over the sustained
+        # particle-step rate of small and mid-size boxes (~1.2e10 /s)
+        probe = W.served_ensemble(runs, seed=seed, full=True)
+        work = np.mean([2 * r["ppc"] * r["n"][0] * r["n"][1] * r["n"][2] * r["steps"] for r in probe])
+        gap = work / (0.8 * 1.2e10)
+    runs_l = W.served_ensemble(runs, seed=seed, full=full, mean_gap_s=gap)
+    specs = [W.run_spec_of(r) for r in runs_l]
+    work = sum(2 * r["ppc"] * r["n"][0] * r["n"][1] * r["n"][2] * r["steps"] for r in runs_l)
     srv = P.Server(device=device, hbm_budget_bytes=96 << 30, max_active=32, steps_per_round=10)
     tickets = []
     t0 = time.perf_counter()
 
     def feeder():
-        for r, spec in zip(runs, specs):
+        for r, spec in zip(runs_l, specs):
             dt = r["arrival_s"] - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
@@ -410,16 +540,21 @@ def run_serving(device, seed=0, runs=64):
     th = threading.Thread(target=feeder)
     th.start()
     th.join()
-    srv.wait(0, 600)
+    srv.wait(0, 900)
     wall = time.perf_counter() - t0
     lat = sorted(srv.poll(t)[1] for t in tickets)
     info = srv.stats()
     srv.close()
-    return {"runs": len(runs), "runs_per_s": len(runs) / wall, "p50_s": float(np.percentile(lat, 50)),
+    if full:
+        sample = (f"first {len(runs_l)} arrivals of the 2000-run stream (Poisson, mean gap {gap * 1e3:.0f} ms ~ 0.8x "
+                  "capacity); shearing/expanding/leaky x 2D (32^2-512^2) / 3D (32^3-96^3); 8-64 ppc/species; "
+                  "200-2000 steps; FP32")
+    else:
+        sample = ("Poisson arrivals (mean gap 2 ms); shearing/expanding/leaky x 2D (32^2-128^2) / 3D (16^3-32^3); "
+                  "8-32 ppc/species; 20-100 steps; FP32")
+    return {"runs": len(runs_l), "runs_per_s": len(runs_l) / wall, "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "particle_steps_per_s": work / wall,
-            "peak_active": int(info.peak_active), "wall_s": wall,
-            "sample": "Poisson arrivals (mean gap 2 ms); shearing/expanding/leaky x 2D (32^2-128^2) / 3D (16^3-32^3); "
-                      "8-32 ppc/species; 20-100 steps; FP32"}
+            "peak_active": int(info.peak_active), "wall_s": wall, "sample": sample}
 
 
 def run_batch_leg(device, steps=20, seed=0, nbox=16, sizes=(32, 48, 64)):
@@ -504,35 +639,53 @@ def batch_legs_subprocess(device, rank):
         return {"error": repr(e)[:300]}
 
 
+def host_mem_available():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
 def run_e2e(w, device, stream, steps, rank):
     """Same metric through the public API with host buffers: load the whole
-    particle state from pinned host memory, K x (step + diagnostics read-back),
-    read the final particle state back; all inside the timed region."""
+    particle state (float64 x, u and uint32 ids) from pinned host memory, K x
+    (pic_step + pic_diagnostics read-back), then read an id-sampled subset of
+    the final particles (1 in 256) back into pinned memory; all inside the
+    timed region.  The host state is generated chunk by chunk straight into
+    the pinned buffers; the leg is skipped (and says so) when those buffers
+    would take more than a third of the host's available memory."""
     import numpy as np
     import torch
 
     from paper_2602_15939_gb300 import pic as P
     from paper_2602_15939_gb300 import workloads as W
 
-    sp = W.host_maxwellian(w, 7 + rank)
+    npart = w.n_particles
+    need = npart * (8 * 6 + 4)
+    avail = host_mem_available()
+    if avail and need > avail / 3:
+        return {"skipped": f"host memory: the pinned state needs {need / 2**30:.1f} GiB, "
+                           f"available {avail / 2**30:.1f} GiB"}
+    per_species = npart // 2
     pinned = []
-    for d in sp:
-        n = len(d["x"])
-        tx = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
-        tu = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
-        ti = torch.empty((n,), dtype=torch.int32, pin_memory=True)
-        tx.numpy()[:] = d["x"]
-        tu.numpy()[:] = d["u"]
-        ti.numpy()[:] = d["id"].view(np.int32)
-        pinned.append((d["q"], tx, tu, ti))
-    del sp
-    # pinned like the inputs (empty_like would give pageable memory)
-    outs = [(torch.empty(tx.shape, dtype=tx.dtype, pin_memory=True), torch.empty(tu.shape, dtype=tu.dtype, pin_memory=True),
-             torch.empty(ti.shape, dtype=ti.dtype, pin_memory=True)) for _, tx, tu, ti in pinned]
+    for s in range(2):
+        tx = torch.empty((per_species, 3), dtype=torch.float64, pin_memory=True)
+        tu = torch.empty((per_species, 3), dtype=torch.float64, pin_memory=True)
+        ti = torch.empty((per_species,), dtype=torch.int32, pin_memory=True)
+        W.host_maxwellian_into(w, 7 + rank + s, tx.numpy(), tu.numpy(), ti.numpy().view(np.uint32),
+                               id_base=s * per_species)
+        pinned.append(((-1.0 if s == 0 else 1.0) * w.units.q, tx, tu, ti))
+    modulus = 256
+    nsamp = per_species // modulus + 2
+    outs = [(torch.empty((nsamp, 3), dtype=torch.float64, pin_memory=True),
+             torch.empty((nsamp, 3), dtype=torch.float64, pin_memory=True),
+             torch.empty((nsamp,), dtype=torch.int32, pin_memory=True)) for _ in range(2)]
     cfg = P.make_config(precision=P.PIC_FP64 if w.fp64 else P.PIC_FP32, device=device, **w.config_kwargs())
     box = P.Box(cfg)
     P.pic_set_stream(box.h, stream.cuda_stream)
-    npart = sum(len(t[1]) for t in pinned)
     lib = P.lib()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -543,18 +696,22 @@ def run_e2e(w, device, stream, steps, rank):
     for _ in range(steps):
         box.step(1)
         box.diagnostics()
+    got = 0
     for s, (ox, ou, oi) in enumerate(outs):
-        P._check(box.h, lib.pic_get_particles(box.h, s, P.C.cast(ox.data_ptr(), P._D), P.C.cast(ou.data_ptr(), P._D),
-                                              P.C.cast(oi.data_ptr(), P._U32), None))
+        n_out = P.C.c_int64()
+        P._check(box.h, lib.pic_get_particles_sampled(box.h, s, modulus, 0, nsamp, P.C.cast(ox.data_ptr(), P._D),
+                                                      P.C.cast(ou.data_ptr(), P._D), P.C.cast(oi.data_ptr(), P._U32),
+                                                      None, P.C.byref(n_out)))
+        got += min(n_out.value, nsamp)
     box.sync()
     dt = time.perf_counter() - t0
     box.close()
     h2d = sum(tx.numel() * 8 + tu.numel() * 8 + ti.numel() * 4 for _, tx, tu, ti in pinned)
-    d2h = h2d + steps * P.C.sizeof(P.pic_diag)
+    d2h = got * (8 * 6 + 4) + steps * P.C.sizeof(P.pic_diag)
     return {"value": npart * steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
             "d2h_bytes_per_step": d2h / steps, "steps": steps, "seconds": dt,
-            "includes": "pic_load_particles from pinned host memory, per step pic_step + pic_diagnostics, "
-                        "final pic_get_particles"}
+            "includes": "pic_load_particles of the whole state from pinned host memory, per step pic_step + "
+                        "pic_diagnostics, final pic_get_particles_sampled (1 in 256 ids)"}
 
 
 def main():

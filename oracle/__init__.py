@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
              "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -103,6 +103,8 @@ def lib():
                                     C.POINTER(StepInfo)]),
                 "ora_advance_particle": (None, [P, _D, _D, _D, C.c_int64, C.c_double, C.c_double, C.c_uint32,
                                                 _D, _D, _D, C.POINTER(StepInfo)]),
+                "ora_set_threads": (None, [C.c_int]),
+                "ora_max_threads": (C.c_int, []),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -245,6 +247,15 @@ def advance_particles(p: Params, E, B, step, q, m, ids, x, u, dr=None):
                                x[i].ctypes.data_as(_D), u[i].ctypes.data_as(_D), dr[i].ctypes.data_as(_D),
                                C.byref(info))
     return x, u, dr, {"escaped": info.escaped, "superluminal": info.superluminal}
+
+
+def set_threads(n: int) -> None:
+    """Threads of the particle loop of a step (1, the default, for tests)."""
+    lib().ora_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().ora_max_threads())
 
 
 # ---- whole steps ----------------------------------------------------------------

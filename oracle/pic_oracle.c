@@ -27,6 +27,9 @@
  *    u^{n+1/2}/gamma^{n+1/2}; the reinjection distribution is a Maxwell-Juettner
  *    at theta_inj, sampled with Philox4x32-10 keyed on (id, seed).
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include "pic_oracle.h"
 
 #include <math.h>
@@ -851,6 +854,21 @@ void ora_advance_particle(const ora_params *p, const double *E, const double *B,
     x[2] = x1[2];
 }
 
+/* Threads of the particle loop of ora_step (1: the plain loop).  Tests use
+ * one thread; the timed CPU baseline may use every host core. */
+static int g_threads = 1;
+
+void ora_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+
+int ora_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 void ora_step(const ora_params *p, ora_fields *f, int nsp, ora_species *sp, ora_stepinfo *info)
 {
     int64_t n = f->step;
@@ -858,11 +876,44 @@ void ora_step(const ora_params *p, ora_fields *f, int nsp, ora_species *sp, ora_
     int64_t N = 3 * ncell(p);
     memset(f->J, 0, sizeof(double) * (size_t)N);
     ora_stepinfo loc = {0, 0};
-    for (int s = 0; s < nsp; ++s) {
-        ora_species *S = &sp[s];
-        for (int64_t ip = 0; ip < S->n; ++ip)
-            ora_advance_particle(p, f->E, f->B, f->J, n, S->q, S->m, S->id[ip], &S->x[3 * ip], &S->u[3 * ip],
-                                 S->dr ? &S->dr[3 * ip] : NULL, &loc);
+    int nt = 1;
+#ifdef _OPENMP
+    nt = g_threads;
+#endif
+    if (nt <= 1) {
+        for (int s = 0; s < nsp; ++s) {
+            ora_species *S = &sp[s];
+            for (int64_t ip = 0; ip < S->n; ++ip)
+                ora_advance_particle(p, f->E, f->B, f->J, n, S->q, S->m, S->id[ip], &S->x[3 * ip], &S->u[3 * ip],
+                                     S->dr ? &S->dr[3 * ip] : NULL, &loc);
+        }
+    } else {
+#ifdef _OPENMP
+        /* the same per-particle step on nt threads: each thread deposits into
+         * its own current array; the arrays are then added in thread order */
+        double *Jt = (double *)calloc((size_t)nt * (size_t)N, sizeof(double));
+        ora_stepinfo *lt = (ora_stepinfo *)calloc((size_t)nt, sizeof(ora_stepinfo));
+#pragma omp parallel num_threads(nt)
+        {
+            int tid = omp_get_thread_num();
+            double *Jl = Jt + (size_t)tid * (size_t)N;
+            for (int s = 0; s < nsp; ++s) {
+                ora_species *S = &sp[s];
+#pragma omp for schedule(static)
+                for (int64_t ip = 0; ip < S->n; ++ip)
+                    ora_advance_particle(p, f->E, f->B, Jl, n, S->q, S->m, S->id[ip], &S->x[3 * ip], &S->u[3 * ip],
+                                         S->dr ? &S->dr[3 * ip] : NULL, &lt[tid]);
+            }
+        }
+        for (int k = 0; k < nt; ++k) {
+            const double *Jl = Jt + (size_t)k * (size_t)N;
+            for (int64_t q = 0; q < N; ++q) f->J[q] += Jl[q];
+            loc.escaped += lt[k].escaped;
+            loc.superluminal += lt[k].superluminal;
+        }
+        free(Jt);
+        free(lt);
+#endif
     }
 
     if (p->box == ORA_BOX_SHEAR) {

@@ -104,6 +104,10 @@ void ora_advance_particle(const ora_params *p, const double *E, const double *B,
                           ora_stepinfo *loc);
 void ora_step(const ora_params *p, ora_fields *f, int nsp, ora_species *sp, ora_stepinfo *info);
 
+/* ---- threads of ora_step's particle loop (default 1; needs an OpenMP build) -- */
+void ora_set_threads(int n);
+int ora_max_threads(void);
+
 #ifdef __cplusplus
 }
 #endif

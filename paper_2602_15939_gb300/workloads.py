@@ -198,6 +198,31 @@ def host_maxwellian(w: Workload, seed: int, n=None, ppc=None):
     return sp
 
 
+def host_maxwellian_into(w: Workload, seed: int, x_out, u_out, id_out, id_base=0, chunk=1 << 22):
+    """One species of workload w written straight into caller arrays
+    (x_out[n][3], u_out[n][3], id_out[n], n = ppc x cells), chunk by chunk so
+    that no temporary grows with n: positions uniform in the box (the 2D
+    ignorable coordinate 0.5), momenta Gaussian with variance theta c^2 per
+    component plus the workload's noise, ids id_base + 0..n-1.  An input recipe
+    for host-side loads of large boxes, not the reinjection law."""
+    n = len(x_out)
+    r = np.random.default_rng(seed)
+    ext = np.asarray(w.n, dtype=float)
+    uth = math.sqrt(w.theta) * w.c
+    sd = math.sqrt(uth * uth + (w.noise * w.c) ** 2)
+    ign = None
+    if w.ndim == 2:
+        ign = 2 if w.plane == 0 else 1
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        x = r.random((b - a, 3)) * ext
+        if ign is not None:
+            x[:, ign] = 0.5
+        x_out[a:b] = x
+        u_out[a:b] = r.normal(0.0, sd, (b - a, 3))
+        id_out[a:b] = np.arange(id_base + a, id_base + b, dtype=np.uint32)
+
+
 def random_phase_dB(n, seed, modes=(2, 3, 4), amplitude=1.0):
     """In-plane magnetic perturbation of a 2D x-y box from a random-phase
     vector potential A_z(i, j) = sum a cos(k.x + phi) on the nodes, over mode

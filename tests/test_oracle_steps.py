@@ -169,3 +169,33 @@ def test_leaky_probabilistic_survival_is_binomial():
     surv = np.all(st.species[0]["u"] == 0.0, axis=1).sum()
     pr = (1 - p_esc) ** steps
     assert abs(surv - N * pr) < 5 * math.sqrt(N * pr * (1 - pr))
+
+
+def test_threaded_step_equals_the_plain_loop():
+    """The timed CPU baseline runs the oracle's particle loop on several
+    threads (per-thread currents added in thread order): the same step as the
+    plain loop up to the rounding order of the current sums."""
+    from paper_2602_15939_gb300 import workloads as W
+
+    n = (8, 8, 8)
+    sp = W.uniform_plasma(n, 4, seed=3, uth=0.2, q=0.05)
+    E, B = W.random_fields(n, 4, b0=(0.0, 0.0, 0.2))
+    p = O.make_params(*n, 0.45, order=2, box=O.BOX_SHEAR, s=1.5, Omega0=3e-3)
+    out = []
+    try:
+        for th in (1, 3):
+            O.set_threads(th)
+            st = O.State(p, E, B, sp, step=5)
+            info = st.step(2)
+            out.append((st, info))
+    finally:
+        O.set_threads(1)
+    (a, ia), (b, ib) = out
+    assert ia == ib
+    for da, db in zip(a.species, b.species):
+        dx = da["x"] - db["x"]
+        dx -= np.asarray(n, dtype=float) * np.round(dx / np.asarray(n, dtype=float))
+        assert np.abs(dx).max() < 1e-12
+        np.testing.assert_allclose(da["u"], db["u"], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(a.J, b.J, rtol=0, atol=1e-14 * np.abs(a.J).max())
+    np.testing.assert_allclose(a.E, b.E, rtol=0, atol=1e-14 * np.abs(a.E).max())
