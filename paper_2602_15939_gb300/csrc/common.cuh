@@ -305,6 +305,16 @@ template <> __device__ inline double t_floor<double>(double x) { return floor(x)
 template <class T> __device__ inline T t_sqrt(T x);
 template <> __device__ inline float t_sqrt<float>(float x) { return sqrtf(x); }
 template <> __device__ inline double t_sqrt<double>(double x) { return sqrt(x); }
+// Reciprocal and reciprocal square root of the path's arithmetic type: FP64
+// divides and takes the square root exactly rounded; FP32 uses the correctly
+// rounded reciprocal and the hardware reciprocal square root (about 2 ulp),
+// far inside the FP32 path's 1e-6 budget and without the division sequence.
+template <class T> __device__ inline T t_rcp(T x);
+template <> __device__ inline float t_rcp<float>(float x) { return __frcp_rn(x); }
+template <> __device__ inline double t_rcp<double>(double x) { return 1.0 / x; }
+template <class T> __device__ inline T t_rsqrt(T x);
+template <> __device__ inline float t_rsqrt<float>(float x) { return rsqrtf(x); }
+template <> __device__ inline double t_rsqrt<double>(double x) { return 1.0 / sqrt(x); }
 template <class T> __device__ inline T t_abs(T x);
 template <> __device__ inline float t_abs<float>(float x) { return fabsf(x); }
 template <> __device__ inline double t_abs<double>(double x) { return fabs(x); }

@@ -9,6 +9,14 @@
 
 namespace pic {
 
+// Launch shape of the grid kernels: x (or the fastest index) over the
+// threads of a block and over blockIdx.x, the other two indices over
+// blockIdx.y and blockIdx.z, so no thread divides an index.
+constexpr int CELL_THREADS = 128;
+inline dim3 cell_grid(long long nfast, long long ny, long long nz) {
+    return dim3((unsigned)((nfast + CELL_THREADS - 1) / CELL_THREADS), (unsigned)ny, (unsigned)nz);
+}
+
 // ---- Yee curl updates ------------------------------------------------------------------
 // out_c <- alpha_c out_c + beta_c curl(sigma (.) in)_c + gam_c J_c over interior cells.
 // CURL_E: curl of an E-located field, result at B locations; else curl of a
@@ -20,12 +28,11 @@ __global__ void curl_update_kernel(Grid g, const T* __restrict__ in, T* __restri
                                    const StepCtx* __restrict__ ctx, int which) {
     using GT = GeomT<G>;
     const Coef3 cf = ctx->curl[which];
-    long long n = (long long)g.nx * g.ny * g.nz;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(q % g.nx);
-        long long r = q / g.nx;
-        int j = (int)(r % g.ny);
-        int k = (int)(r / g.ny);
+    // launch: cell_grid(nx, ny, nz)
+    {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= g.nx) return;
+        const int j = blockIdx.y, k = blockIdx.z;
         long long c0 = g.idx(i, j, k);
         const long long sx = 1, sy = g.px, sz = (long long)g.px * g.py, cs = g.cstride;
         const T* X = in;
@@ -84,19 +91,19 @@ __global__ void ksb_sweep_kernel(Grid g, const T* __restrict__ En, const T* __re
     using GT = GeomT<G>;
     const T c = T(c_), sO = T(sO_);
     const T FOUR_PI = T(12.566370614359172);
-    long long n = (long long)g.nx * g.ny * g.nz;
     const long long sx = 1, sy = GT::AY ? g.px : 0, sz = GT::AZ ? (long long)g.px * g.py : 0, cs = g.cstride;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(q % g.nx);
-        long long r = q / g.nx;
-        int j = (int)(r % g.ny);
-        int k = (int)(r / g.ny);
+    // launch: cell_grid(nx, ny, nz)
+    {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= g.nx) return;
+        const int j = blockIdx.y, k = blockIdx.z;
         long long c0 = g.idx(i, j, k);
         // midpoint fields
         auto ME = [&](int comp, long long off) -> T { return T(0.5) * (En[comp * cs + c0 + off] + Ek[comp * cs + c0 + off]); };
         auto MB = [&](int comp, long long off) -> T { return T(0.5) * (Bn[comp * cs + c0 + off] + Bk[comp * cs + c0 + off]); };
-        const T VN = -sO * T((double)i - half_nx);
-        const T VH = -sO * T((double)i + 0.5 - half_nx);
+        // x - nx/2 at nodes and half-points: exact in either precision
+        const T VN = -sO * (T(i) - T(half_nx));
+        const T VH = -sO * ((T(i) + T(0.5)) - T(half_nx));
         // curls (ignorable-axis differences vanish because its stride is 0)
         T curlEx = (ME(2, sy) - ME(2, 0)) - (ME(1, sz) - ME(1, 0));
         T curlEy = (ME(0, sz) - ME(0, 0)) - (ME(2, sx) - ME(2, 0));
@@ -140,14 +147,12 @@ __global__ void fill_x_kernel(Grid g, T* F, int ncomp, int dys_i, double dys_f, 
         dys_f = ctx->dys_f[which];
     }
     const int nguard = g.px - g.nx;  // gx low + the rest high
-    long long n = (long long)ncomp * nguard * g.ny * g.nz;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        int gi = (int)(q % nguard);
-        long long r = q / nguard;
-        int j = (int)(r % g.ny);
-        r /= g.ny;
-        int k = (int)(r % g.nz);
-        int comp = (int)(r / g.nz);
+    // launch: cell_grid(ny, nz, ncomp * nguard)
+    {
+        const int j = blockIdx.x * blockDim.x + threadIdx.x;
+        if (j >= g.ny) return;
+        const int k = blockIdx.y;
+        const int comp = blockIdx.z / nguard, gi = blockIdx.z - comp * nguard;
         int i = gi < g.gx ? gi - g.gx : g.nx + (gi - g.gx);  // physical ghost index
         int w = i < 0 ? -1 : 1;
         int is = i - w * g.nx;
@@ -173,14 +178,12 @@ __global__ void fill_x_kernel(Grid g, T* F, int ncomp, int dys_i, double dys_f, 
 template <class T>
 __global__ void fill_y_kernel(Grid g, T* F, int ncomp) {
     const int nguard = g.py - g.ny;
-    long long n = (long long)ncomp * nguard * g.px * g.nz;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        int pi = (int)(q % g.px);
-        long long r = q / g.px;
-        int gj = (int)(r % nguard);
-        r /= nguard;
-        int k = (int)(r % g.nz);
-        int comp = (int)(r / g.nz);
+    // launch: cell_grid(px, nz, ncomp * nguard)
+    {
+        const int pi = blockIdx.x * blockDim.x + threadIdx.x;
+        if (pi >= g.px) return;
+        const int k = blockIdx.y;
+        const int comp = blockIdx.z / nguard, gj = blockIdx.z - comp * nguard;
         int j = gj < g.gy ? gj - g.gy : g.ny + (gj - g.gy);
         int js = j < 0 ? j + g.ny : j - g.ny;
         T* Fc = F + (long long)comp * g.cstride;
@@ -192,18 +195,16 @@ __global__ void fill_y_kernel(Grid g, T* F, int ncomp) {
 template <class T>
 __global__ void fill_z_kernel(Grid g, T* F, int ncomp) {
     const int nguard = g.pz - g.nz;
-    long long plane = (long long)g.px * g.py;
-    long long n = (long long)ncomp * nguard * plane;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        long long pp = q % plane;
-        long long r = q / plane;
-        int gk = (int)(r % nguard);
-        int comp = (int)(r / nguard);
-        int k = gk < g.gz ? gk - g.gz : g.nz + (gk - g.gz);
-        int ks = k < 0 ? k + g.nz : k - g.nz;
-        T* Fc = F + (long long)comp * g.cstride;
-        Fc[(long long)(k + g.gz) * plane + pp] = Fc[(long long)(ks + g.gz) * plane + pp];
-    }
+    const long long plane = (long long)g.px * g.py;
+    // launch: cell_grid(px, py, ncomp * nguard)
+    const int pi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pi >= g.px) return;
+    const long long pp = (long long)blockIdx.y * g.px + pi;
+    const int comp = blockIdx.z / nguard, gk = blockIdx.z - comp * nguard;
+    int k = gk < g.gz ? gk - g.gz : g.nz + (gk - g.gz);
+    int ks = k < 0 ? k + g.nz : k - g.nz;
+    T* Fc = F + (long long)comp * g.cstride;
+    Fc[(long long)(k + g.gz) * plane + pp] = Fc[(long long)(ks + g.gz) * plane + pp];
 }
 
 // ---- current fold (adjoint of the fill) ------------------------------------------------
@@ -213,41 +214,37 @@ __global__ void fill_z_kernel(Grid g, T* F, int ncomp) {
 // (1 - f, f) between rows floor and floor + 1; at (i < 0, j) at (i + nx, j - dys).
 template <class T>
 __global__ void fold_z_kernel(Grid g, T* F) {
-    long long plane = (long long)g.px * g.py;
+    const long long plane = (long long)g.px * g.py;
     const int band = g.pz - g.nz;  // receiving interior planes: k in [0, gzh) and [nz - gz, nz)
-    long long n = 3ll * band * plane;
     const int gzh = g.pz - g.gz - g.nz;  // high guards
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        long long pp = q % plane;
-        long long r = q / plane;
-        int b = (int)(r % band);
-        int comp = (int)(r / band);
-        T* Fc = F + (long long)comp * g.cstride;
-        int k;  // receiving interior plane
-        T add = T(0);
-        if (b < gzh) {
-            k = b;  // from high guard nz + b
-            add += Fc[(long long)(g.nz + b + g.gz) * plane + pp];
-        } else {
-            k = g.nz - g.gz + (b - gzh);  // from low guard k - nz
-            add += Fc[(long long)(k - g.nz + g.gz) * plane + pp];
-        }
-        Fc[(long long)(k + g.gz) * plane + pp] += add;
+    // launch: cell_grid(px, py, 3 * band)
+    const int pi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pi >= g.px) return;
+    const long long pp = (long long)blockIdx.y * g.px + pi;
+    const int comp = blockIdx.z / band, b = blockIdx.z - comp * band;
+    T* Fc = F + (long long)comp * g.cstride;
+    int k;  // receiving interior plane
+    T add = T(0);
+    if (b < gzh) {
+        k = b;  // from high guard nz + b
+        add += Fc[(long long)(g.nz + b + g.gz) * plane + pp];
+    } else {
+        k = g.nz - g.gz + (b - gzh);  // from low guard k - nz
+        add += Fc[(long long)(k - g.nz + g.gz) * plane + pp];
     }
+    Fc[(long long)(k + g.gz) * plane + pp] += add;
 }
 
 template <class T>
 __global__ void fold_y_kernel(Grid g, T* F) {
     const int band = g.py - g.ny;
     const int gyh = g.py - g.gy - g.ny;
-    long long n = 3ll * band * g.px * g.nz;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        int pi = (int)(q % g.px);
-        long long r = q / g.px;
-        int b = (int)(r % band);
-        r /= band;
-        int k = (int)(r % g.nz);
-        int comp = (int)(r / g.nz);
+    // launch: cell_grid(px, nz, 3 * band)
+    {
+        const int pi = blockIdx.x * blockDim.x + threadIdx.x;
+        if (pi >= g.px) return;
+        const int k = blockIdx.y;
+        const int comp = blockIdx.z / band, b = blockIdx.z - comp * band;
         T* Fc = F + (long long)comp * g.cstride;
         long long row = (long long)(k + g.gz) * g.py;
         int j;
@@ -265,15 +262,13 @@ __global__ void fold_x_kernel(Grid g, T* F, const StepCtx* __restrict__ ctx, int
     const double dys_f = ctx->dys_f[which];
     const int band = g.px - g.nx;
     const int gxh = g.px - g.gx - g.nx;
-    long long n = 3ll * band * g.ny * g.nz;
     const bool sh = GT::AY && (dys_i != 0 || dys_f != 0.0);
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        int b = (int)(q % band);
-        long long r = q / band;
-        int j = (int)(r % g.ny);
-        r /= g.ny;
-        int k = (int)(r % g.nz);
-        int comp = (int)(r / g.nz);
+    // launch: cell_grid(ny, nz, 3 * band)
+    {
+        const int j = blockIdx.x * blockDim.x + threadIdx.x;
+        if (j >= g.ny) return;
+        const int k = blockIdx.y;
+        const int comp = blockIdx.z / band, b = blockIdx.z - comp * band;
         T* Fc = F + (long long)comp * g.cstride;
         int i, is, w;  // receiving interior column, source ghost column, side
         if (b < gxh) { i = b; is = g.nx + b; w = 1; }
@@ -299,25 +294,32 @@ __global__ void fold_x_kernel(Grid g, T* F, const StepCtx* __restrict__ ctx, int
 // Shearing box: advect J' along y by v_{s,y} dt / 2 = -s Omega0 x dt / 2 per x
 // column (x of each component's location from the box centre), linear
 // interpolation, periodic in y: Jn(j) = (1-f) J(j0) + f J(j0+1), j - d = j0 + f.
+constexpr int ADVECT_ROWS = 8;  // y rows per thread: the column's shift is computed once
 template <class T>
 __global__ void ksb_advect_kernel(Grid g, const T* __restrict__ Jin, T* __restrict__ Jout, double sO, double half_nx) {
-    long long n = 3ll * g.nx * g.ny * g.nz;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(q % g.nx);
-        long long r = q / g.nx;
-        int j = (int)(r % g.ny);
-        r /= g.ny;
-        int k = (int)(r % g.nz);
-        int comp = (int)(r / g.nz);
-        double xc = (double)i + (comp == 0 ? 0.5 : 0.0) - half_nx;
-        double d = -sO * xc * 0.5;
-        double ys = (double)j - d;
-        double y0 = floor(ys);
-        double f = ys - y0;
-        int j0 = (int)y0 % g.ny; if (j0 < 0) j0 += g.ny;
-        int j1 = j0 + 1; if (j1 >= g.ny) j1 -= g.ny;
-        const T* Jc = Jin + (long long)comp * g.cstride;
-        Jout[(long long)comp * g.cstride + g.idx(i, j, k)] = T(1.0 - f) * Jc[g.idx(i, j0, k)] + T(f) * Jc[g.idx(i, j1, k)];
+    // launch: cell_grid(nx, ceil(ny / ADVECT_ROWS), 3 * nz)
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    const int comp = blockIdx.z / g.nz, k = blockIdx.z - comp * g.nz;
+    // the column moves by d = -s Omega0 xc / 2; row j takes y = j - d = j + m + f, 0 <= f < 1
+    const double xc = (double)i + (comp == 0 ? 0.5 : 0.0) - half_nx;
+    const double md = sO * xc * 0.5;  // -d
+    const double fl = floor(md);
+    const T f = T(md - fl);
+    int m = (int)fmod(fl, (double)g.ny);
+    if (m < 0) m += g.ny;
+    const T* Jc = Jin + (long long)comp * g.cstride;
+    T* Jo = Jout + (long long)comp * g.cstride;
+    const int j0 = blockIdx.y * ADVECT_ROWS;
+#pragma unroll 4
+    for (int jj = 0; jj < ADVECT_ROWS; ++jj) {
+        const int j = j0 + jj;
+        if (j >= g.ny) break;
+        int ja = j + m;
+        if (ja >= g.ny) ja -= g.ny;
+        int jb = ja + 1;
+        if (jb >= g.ny) jb -= g.ny;
+        Jo[g.idx(i, j, k)] = (T(1) - f) * Jc[g.idx(i, ja, k)] + f * Jc[g.idx(i, jb, k)];
     }
 }
 

@@ -68,7 +68,7 @@ struct Tiling {
 // refreshed by with_ctx from the device context): the FP32 particle path
 // reads them from the parameter bank, with no FP64 conversion per particle.
 struct StepPF {
-    float c, inv_c2, sO, Omega0, half_nx, l_esc, dys_end_f;
+    float c, inv_c, inv_c2, sO, Omega0, half_nx, l_esc, dys_end_f;
     float Lam[3], im[3], Lt[3], inv_lh[3];
 };
 
@@ -79,6 +79,7 @@ template <> __device__ inline double pk<double>(double d, float) { return d; }
 
 struct StepP {
     double c;
+    double inv_c;       // 1 / c
     double inv_c2;      // 1 / c^2
     long long step;
     int nsp;
@@ -327,6 +328,99 @@ __device__ inline void gather(const F& fa, I cidx, const T o[3], T Ep[3], T Bp[3
     Bp[0] = out[3]; Bp[1] = out[4]; Bp[2] = out[5];
 }
 
+// FP32 gather from the shared-memory boxes with packed two-wide FP32
+// arithmetic.  E_k and B_k are staggered oppositely on every axis (E_k is
+// half-staggered along k only, B_k along the other two), so with the node
+// and staggered shape weights of each axis held as one pair (node, stag) --
+// or its swap (stag, node) -- every weight, row and accumulator of the pair
+// (E_k, B_k) is one packed register: each fused multiply-add does the work of
+// two, with the rounding of the scalar form.  Same weights, stencils and
+// summation order as gather().
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2swap(float2 v) { return make_float2(v.y, v.x); }
+
+template <int ORD> struct Shape2;
+template <> struct Shape2<1> {
+    // (node, stag) weights of one axis at offset o, and the start offsets
+    __device__ static void pair(float o, int& offn, int& offs, float2 w[2]) {
+        offn = 0;
+        const bool hi = o >= 0.5f;
+        offs = hi ? 0 : -1;
+        const float2 f = f2(o, hi ? o - 0.5f : o + 0.5f);
+        w[0] = __fadd2_rn(f2(1.0f, 1.0f), f2(-f.x, -f.y));
+        w[1] = f;
+    }
+};
+template <> struct Shape2<2> {
+    __device__ static void pair(float o, int& offn, int& offs, float2 w[3]) {
+        const bool hi = o >= 0.5f;
+        offn = hi ? 0 : -1;
+        offs = -1;
+        const float2 d = f2(hi ? o - 1.0f : o, o - 0.5f);
+        const float2 half = f2(0.5f, 0.5f);
+        const float2 a = __fadd2_rn(half, f2(-d.x, -d.y)), bb = __fadd2_rn(half, d);
+        w[0] = __fmul2_rn(half, __fmul2_rn(a, a));
+        w[1] = __ffma2_rn(f2(-d.x, -d.y), d, f2(0.75f, 0.75f));
+        w[2] = __fmul2_rn(half, __fmul2_rn(bb, bb));
+    }
+};
+
+template <int G, int ORD>
+__device__ __forceinline__ void gather_packed(const SmemFields<float, G>& fa, int cidx, const float o[3], float Ep[3],
+                                              float Bp[3]) {
+    using GT = GeomT<G>;
+    using FA = SmemFields<float, G>;
+    constexpr int NP = ORD + 1;
+    float2 w[3][NP];  // (node, stag) per axis
+    int offn[3] = {0, 0, 0}, offs[3] = {0, 0, 0};
+    Shape2<ORD>::pair(o[0], offn[0], offs[0], w[0]);
+    if (GT::AY) Shape2<ORD>::pair(o[1], offn[1], offs[1], w[1]);
+    if (GT::AZ) Shape2<ORD>::pair(o[2], offn[2], offs[2], w[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        // E_k: staggered along k (weights .y of axis k, .x elsewhere); B_k the opposite
+        float2 wk[3][NP];
+        int bE = cidx, bB = cidx;
+        constexpr int SS[3] = {1, FA::SY, FA::SZ};
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const bool act = ax == 0 || (ax == 1 && GT::AY) || (ax == 2 && GT::AZ);
+            if (!act) continue;
+#pragma unroll
+            for (int m = 0; m < NP; ++m) wk[ax][m] = ax == k ? f2swap(w[ax][m]) : w[ax][m];
+            bE += (ax == k ? offs[ax] : offn[ax]) * SS[ax];
+            bB += (ax == k ? offn[ax] : offs[ax]) * SS[ax];
+        }
+        float2 acc = f2(0.0f, 0.0f);
+        if (GT::AY && GT::AZ) {
+#pragma unroll
+            for (int c = 0; c < NP; ++c)
+#pragma unroll
+                for (int b = 0; b < NP; ++b) {
+                    const int off = b * FA::SY + c * FA::SZ;
+                    float2 row = f2(0.0f, 0.0f);
+#pragma unroll
+                    for (int a = 0; a < NP; ++a)
+                        row = __ffma2_rn(wk[0][a], f2(fa.e[k * FA::SC + bE + off + a], fa.b[k * FA::SC + bB + off + a]), row);
+                    acc = __ffma2_rn(__fmul2_rn(wk[1][b], wk[2][c]), row, acc);
+                }
+        } else {
+            constexpr int A2 = GT::AY ? 1 : 2;
+            constexpr int S2 = A2 == 1 ? FA::SY : FA::SZ;
+#pragma unroll
+            for (int b = 0; b < NP; ++b) {
+                float2 row = f2(0.0f, 0.0f);
+#pragma unroll
+                for (int a = 0; a < NP; ++a)
+                    row = __ffma2_rn(wk[0][a], f2(fa.e[k * FA::SC + bE + b * S2 + a], fa.b[k * FA::SC + bB + b * S2 + a]), row);
+                acc = __ffma2_rn(wk[A2][b], row, acc);
+            }
+        }
+        Ep[k] = acc.x;
+        Bp[k] = acc.y;
+    }
+}
+
 // ---- pushers ------------------------------------------------------------------------
 
 template <class T> __device__ inline void cross(const T a[3], const T b[3], T r[3]) {
@@ -351,28 +445,30 @@ template <class T> __device__ inline void rot(const T nu[3], const T t[3], T k_o
 template <class T> __device__ inline void push_boris(T u[3], const T E[3], const T B[3], T qdt2m, T qdt2mc, T inv_c2) {
     T eps[3] = {qdt2m * E[0], qdt2m * E[1], qdt2m * E[2]};
     T um[3] = {u[0] + eps[0], u[1] + eps[1], u[2] + eps[2]};
-    T g = t_sqrt<T>(T(1) + dot(um, um) * inv_c2);
-    T ig = T(1) / g;
+    T ig = t_rsqrt<T>(T(1) + dot(um, um) * inv_c2);  // 1 / gamma^-
     T tau[3] = {qdt2mc * B[0] * ig, qdt2mc * B[1] * ig, qdt2mc * B[2] * ig};
     T up[3];
-    rot(um, tau, T(2) / (T(1) + dot(tau, tau)), up);
+    rot(um, tau, T(2) * t_rcp<T>(T(1) + dot(tau, tau)), up);
     u[0] = up[0] + eps[0]; u[1] = up[1] + eps[1]; u[2] = up[2] + eps[2];
 }
 
 // Shearing-box (KSB-OA) push of Sec. 2.2.  xc: x^n from the box centre.
 template <class T>
-__device__ inline void push_ksb(T u[3], const T E[3], const T B[3], T qdt2m, T qdt2mc, T c, T sO, T Om, T xc) {
+__device__ inline void push_ksb(T u[3], const T E[3], const T B[3], T qdt2m, T qdt2mc, T inv_c, T inv_c2, T sO, T Om,
+                                T xc) {
     T eps[3] = {qdt2m * E[0], qdt2m * E[1], qdt2m * E[2]};
     T um[3] = {u[0] + eps[0], u[1] + eps[1], u[2] + eps[2]};
     T a1 = sO * T(0.5);
-    T a2 = sO * xc / c;
-    T ic2 = T(1) / (c * c);
+    T a2 = sO * xc * inv_c;
+    const T ic2 = inv_c2;
     // gbar: root >= 1 of g^3 - A g - C = 0 (the Lorentz-factor relation of Sec. 2.2)
     T u2 = dot(um, um), ue = dot(um, eps);
     T A = T(1) + (u2 + T(2) * a1 * um[0] * um[1]) * ic2;
     T Cc = T(2) * a2 * ue * um[1] * ic2;
-    T gm = t_sqrt<T>(T(1) + u2 * ic2);
-    T g = gm + (a1 * um[0] * um[1] * gm + a2 * ue * um[1]) * ic2 / (gm * gm);
+    const T g2m = T(1) + u2 * ic2;  // (gamma^-)^2
+    const T igm = t_rsqrt<T>(g2m);
+    const T gm = g2m * igm;
+    T g = gm + (a1 * um[0] * um[1] * gm + a2 * ue * um[1]) * ic2 * (igm * igm);
     // Newton: converged for FP64, two corrections for FP32 (quadratic convergence
     // from an O(Omega0^2)-accurate start)
     const int NIT = sizeof(T) == 8 ? 8 : 2;
@@ -380,12 +476,13 @@ __device__ inline void push_ksb(T u[3], const T E[3], const T B[3], T qdt2m, T q
     for (int it = 0; it < NIT; ++it) {
         T f = (g * g - A) * g - Cc;
         T df = T(3) * g * g - A;
-        g -= f / df;
+        g -= sizeof(T) == 8 ? f / df : f * t_rcp<T>(df);
     }
-    T ig = T(1) / g;
-    T et[3] = {eps[0] * ig / c, eps[1] * ig / c, eps[2] * ig / c};
+    T ig = t_rcp<T>(g);
+    const T igc = ig * inv_c;
+    T et[3] = {eps[0] * igc, eps[1] * igc, eps[2] * igc};
     T tt[3] = {qdt2mc * B[0] * ig, qdt2mc * B[1] * ig, qdt2mc * B[2] * ig + Om};
-    T den = T(1) / (T(1) + dot(tt, tt));
+    T den = t_rcp<T>(T(1) + dot(tt, tt));
     T S2[3] = {a1 + a2 * et[0], a2 * et[1], a2 * et[2]};
     // R(e_y) and g = S2 . R(e_y)
     T ey[3] = {T(0), T(1), T(0)}, Rey[3];
@@ -396,7 +493,7 @@ __device__ inline void push_ksb(T u[3], const T E[3], const T B[3], T qdt2m, T q
     rot(um, tt, T(2) * den, w);
     T su = dot(S2, um);
     w[0] += su * Rey[0]; w[1] += su * Rey[1]; w[2] += su * Rey[2];
-    T sw = dot(S2, w) / (T(1) - gg);
+    T sw = dot(S2, w) * t_rcp<T>(T(1) - gg);
     u[0] = w[0] + sw * Rey[0] + eps[0];
     u[1] = w[1] + sw * Rey[1] + eps[1];
     u[2] = w[2] + sw * Rey[2] + eps[2];
@@ -410,8 +507,7 @@ __device__ inline void push_keb(T u[3], const T E[3], const T B[3], T qdt2m, T q
     T eps[3] = {qdt2m * E[0], qdt2m * E[1], qdt2m * E[2]};
     T um[3] = {u[0] + eps[0], u[1] + eps[1], u[2] + eps[2]};
     T lu[3] = {(T(1) + Lam[0]) * um[0], (T(1) + Lam[1]) * um[1], (T(1) + Lam[2]) * um[2]};
-    T g = t_sqrt<T>(T(1) + dot(lu, lu) * inv_c2);
-    T ig = T(1) / g;
+    T ig = t_rsqrt<T>(T(1) + dot(lu, lu) * inv_c2);  // 1 / gbar
     T tau[3] = {qdt2mc * B[0] * ig, qdt2mc * B[1] * ig, qdt2mc * B[2] * ig};
     T up[3];
     if (!exact) {
@@ -421,7 +517,7 @@ __device__ inline void push_keb(T u[3], const T E[3], const T B[3], T qdt2m, T q
             tt[i] = tau[i] * im[i];
             a[i] = (T(1) + Lt[i]) * um[i];
         }
-        T den = T(1) / (T(1) + dot(tt, tt));
+        T den = t_rcp<T>(T(1) + dot(tt, tt));
         cross(a, tt, ax);
         cross(ax, tt, bx);
 #pragma unroll
@@ -535,39 +631,60 @@ __device__ inline void deposit(const JA& ja, I cidx, const T o[3], const T d[3],
     for (int k = 0; k < 8; ++k) bs[k] = (k & ~crm) ? trash : base;
     constexpr int LX = NW - 2, LN = NW - 1;  // last current index, last node index
     if (GT::AY && GT::AZ) {
-#pragma unroll
-        for (int n = 0; n < NW; ++n)
+        // The outermost loop of each component stays rolled: this full-window
+        // path runs only for the queued crossing particles, and unrolled it
+        // would crowd the particle loop out of the instruction cache.  Values
+        // indexed by the rolled counter are picked by selects (an indexed
+        // register array would go to local memory).
+        auto pick = [](const T* v, int i) -> T { return i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[3])); };
+#pragma unroll 1
+        for (int n = 0; n < NW; ++n) {
+            const T az = pick(A[2], n), qz = pick(Q[2], n);
+            const I noff = (I)n * ja.SZ;
+            const bool nl = n == LN;
 #pragma unroll
             for (int m = 0; m < NW; ++m) {
-                const T fyz = S0[1][m] * A[2][n] + DS[1][m] * Q[2][n];
+                const T fyz = S0[1][m] * az + DS[1][m] * qz;
 #pragma unroll
                 for (int l = 0; l < NW - 1; ++l) {
-                    const int k = (l == LX ? 1 : 0) | (m == LN ? 2 : 0) | (n == LN ? 4 : 0);
-                    ja.add(0, bs[k] + l + m * ja.SY + n * ja.SZ, CS[0][l], fyz);
+                    const int kl = (l == LX ? 1 : 0) | (m == LN ? 2 : 0);
+                    const I bb = nl ? bs[kl | 4] : bs[kl];
+                    ja.add(0, bb + noff + l + m * ja.SY, CS[0][l], fyz);
                 }
             }
-#pragma unroll
-        for (int n = 0; n < NW; ++n)
+        }
+#pragma unroll 1
+        for (int n = 0; n < NW; ++n) {
+            const T az = pick(A[2], n), qz = pick(Q[2], n);
+            const I noff = (I)n * ja.SZ;
+            const bool nl = n == LN;
 #pragma unroll
             for (int l = 0; l < NW; ++l) {
-                const T fxz = S0[0][l] * A[2][n] + DS[0][l] * Q[2][n];
+                const T fxz = S0[0][l] * az + DS[0][l] * qz;
 #pragma unroll
                 for (int m = 0; m < NW - 1; ++m) {
-                    const int k = (l == LN ? 1 : 0) | (m == LX ? 2 : 0) | (n == LN ? 4 : 0);
-                    ja.add(1, bs[k] + l + m * ja.SY + n * ja.SZ, CS[1][m], fxz);
+                    const int kl = (l == LN ? 1 : 0) | (m == LX ? 2 : 0);
+                    const I bb = nl ? bs[kl | 4] : bs[kl];
+                    ja.add(1, bb + noff + l + m * ja.SY, CS[1][m], fxz);
                 }
             }
-#pragma unroll
-        for (int m = 0; m < NW; ++m)
+        }
+#pragma unroll 1
+        for (int m = 0; m < NW; ++m) {
+            const T ay = pick(A[1], m), qy = pick(Q[1], m);
+            const I moff = (I)m * ja.SY;
+            const bool ml = m == LN;
 #pragma unroll
             for (int l = 0; l < NW; ++l) {
-                const T fxy = S0[0][l] * A[1][m] + DS[0][l] * Q[1][m];
+                const T fxy = S0[0][l] * ay + DS[0][l] * qy;
 #pragma unroll
                 for (int n = 0; n < NW - 1; ++n) {
-                    const int k = (l == LN ? 1 : 0) | (m == LN ? 2 : 0) | (n == LX ? 4 : 0);
-                    ja.add(2, bs[k] + l + m * ja.SY + n * ja.SZ, CS[2][n], fxy);
+                    const int kl = (l == LN ? 1 : 0) | (n == LX ? 4 : 0);
+                    const I bb = ml ? bs[kl | 2] : bs[kl];
+                    ja.add(2, bb + moff + l + n * ja.SZ, CS[2][n], fxy);
                 }
             }
+        }
     } else {
         constexpr int A2 = GT::AY ? 1 : 2;  // second active axis
         constexpr int IG = GT::AY ? 2 : 1;  // ignorable axis
@@ -766,12 +883,13 @@ template <class T, int G, int ORD, int PUSH, class FA, class I>
 __device__ inline void push_particle(Particle<T>& p, const FA& fa, I fidx, const SpecStep<T>& S, const StepP& P,
                                      T d[3]) {
     T E[3], B[3];
-    gather<T, G, ORD>(fa, fidx, p.o, E, B);
-    const T c = pk<T>(P.c, P.f.c);
+    if constexpr (std::is_same<FA, SmemFields<float, G>>::value) gather_packed<G, ORD>(fa, fidx, p.o, E, B);
+    else gather<T, G, ORD>(fa, fidx, p.o, E, B);
     const T inv_c2 = pk<T>(P.inv_c2, P.f.inv_c2);
     if (PUSH == PUSH_KSB) {
         const T xc0 = (T(p.ci) - pk<T>(P.half_nx, P.f.half_nx)) + p.o[0];  // exact: integer and half-integer
-        push_ksb<T>(p.u, E, B, S.qdt2m, S.qdt2mc, c, pk<T>(P.sO, P.f.sO), pk<T>(P.Omega0, P.f.Omega0), xc0);
+        push_ksb<T>(p.u, E, B, S.qdt2m, S.qdt2mc, pk<T>(P.inv_c, P.f.inv_c), inv_c2, pk<T>(P.sO, P.f.sO),
+                    pk<T>(P.Omega0, P.f.Omega0), xc0);
     } else if (PUSH == PUSH_KEB) {
         const T Lam[3] = {pk<T>(P.Lam[0], P.f.Lam[0]), pk<T>(P.Lam[1], P.f.Lam[1]), pk<T>(P.Lam[2], P.f.Lam[2])};
         const T im[3] = {pk<T>(P.keb_im[0], P.f.im[0]), pk<T>(P.keb_im[1], P.f.im[1]), pk<T>(P.keb_im[2], P.f.im[2])};
@@ -780,7 +898,7 @@ __device__ inline void push_particle(Particle<T>& p, const FA& fa, I fidx, const
     } else {
         push_boris<T>(p.u, E, B, S.qdt2m, S.qdt2mc, inv_c2);
     }
-    T ig = T(1) / t_sqrt<T>(T(1) + dot(p.u, p.u) * inv_c2);
+    T ig = t_rsqrt<T>(T(1) + dot(p.u, p.u) * inv_c2);  // 1 / gamma^{n+1/2}
     d[0] = p.u[0] * ig; d[1] = p.u[1] * ig; d[2] = p.u[2] * ig;
     if (PUSH == PUSH_KEB) {
         d[0] *= pk<T>(P.inv_lh[0], P.f.inv_lh[0]);

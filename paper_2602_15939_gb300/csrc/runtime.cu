@@ -267,16 +267,16 @@ template <class T, int G> static void fill_guards_t(pic_handle* h, T* F, int ctx
         df = dys - di;
         di %= g.ny;
     }
-    long long nx_ = 3ll * (g.px - g.nx) * g.ny * g.nz;
     const StepCtx* ctx = (ctx_which >= 0 && h->cfg.box == PIC_BOX_SHEAR) ? h->ctx : nullptr;
-    fill_x_kernel<T, G><<<grid_blocks(nx_), NTHR, 0, h->stream>>>(g, F, 3, di, df, ctx, ctx_which < 0 ? 0 : ctx_which);
+    fill_x_kernel<T, G><<<cell_grid(g.ny, g.nz, 3ll * (g.px - g.nx)), CELL_THREADS, 0, h->stream>>>(
+        g, F, 3, di, df, ctx, ctx_which < 0 ? 0 : ctx_which);
     h->prof.launches++;
     if (GeomT<G>::AY) {
-        fill_y_kernel<T><<<grid_blocks(3ll * (g.py - g.ny) * g.px * g.nz), NTHR, 0, h->stream>>>(g, F, 3);
+        fill_y_kernel<T><<<cell_grid(g.px, g.nz, 3ll * (g.py - g.ny)), CELL_THREADS, 0, h->stream>>>(g, F, 3);
         h->prof.launches++;
     }
     if (GeomT<G>::AZ) {
-        fill_z_kernel<T><<<grid_blocks(3ll * (g.pz - g.nz) * g.px * g.py), NTHR, 0, h->stream>>>(g, F, 3);
+        fill_z_kernel<T><<<cell_grid(g.px, g.py, 3ll * (g.pz - g.nz)), CELL_THREADS, 0, h->stream>>>(g, F, 3);
         h->prof.launches++;
     }
 }
@@ -285,25 +285,25 @@ template <class T, int G> static void fill_guards_t(pic_handle* h, T* F, int ctx
 template <class T, int G> static void fold_current_t(pic_handle* h, T* J) {
     const Grid& g = h->g;
     if (GeomT<G>::AZ) {
-        fold_z_kernel<T><<<grid_blocks(3ll * (g.pz - g.nz) * g.px * g.py), NTHR, 0, h->stream>>>(g, J);
+        fold_z_kernel<T><<<cell_grid(g.px, g.py, 3ll * (g.pz - g.nz)), CELL_THREADS, 0, h->stream>>>(g, J);
         h->prof.launches++;
     }
     if (GeomT<G>::AY) {
-        fold_y_kernel<T><<<grid_blocks(3ll * (g.py - g.ny) * g.px * g.nz), NTHR, 0, h->stream>>>(g, J);
+        fold_y_kernel<T><<<cell_grid(g.px, g.nz, 3ll * (g.py - g.ny)), CELL_THREADS, 0, h->stream>>>(g, J);
         h->prof.launches++;
     }
-    fold_x_kernel<T, G><<<grid_blocks(3ll * (g.px - g.nx) * g.ny * g.nz), NTHR, 0, h->stream>>>(g, J, h->ctx, 1);
+    fold_x_kernel<T, G><<<cell_grid(g.ny, g.nz, 3ll * (g.px - g.nx)), CELL_THREADS, 0, h->stream>>>(g, J, h->ctx, 1);
     h->prof.launches++;
 }
 
 template <class T, int G> static void curl_t(pic_handle* h, bool curlE, const void* in, void* out, const void* J, int which) {
-    long long n = (long long)h->g.nx * h->g.ny * h->g.nz;
+    const dim3 grid = cell_grid(h->g.nx, h->g.ny, h->g.nz);
     if (curlE)
-        curl_update_kernel<T, G, true><<<grid_blocks(n), NTHR, 0, h->stream>>>(h->g, (const T*)in, (T*)out, (const T*)J,
-                                                                              h->ctx, which);
+        curl_update_kernel<T, G, true><<<grid, CELL_THREADS, 0, h->stream>>>(h->g, (const T*)in, (T*)out, (const T*)J,
+                                                                            h->ctx, which);
     else
-        curl_update_kernel<T, G, false><<<grid_blocks(n), NTHR, 0, h->stream>>>(h->g, (const T*)in, (T*)out, (const T*)J,
-                                                                               h->ctx, which);
+        curl_update_kernel<T, G, false><<<grid, CELL_THREADS, 0, h->stream>>>(h->g, (const T*)in, (T*)out, (const T*)J,
+                                                                             h->ctx, which);
     h->prof.launches++;
 }
 
@@ -341,12 +341,11 @@ template <class T, int G> static void field_step_t(pic_handle* h) {
         const int N = h->cfg.fp_iters;
         const void* Ek = h->Es;
         const void* Bk = h->Bs;
-        long long n = (long long)g.nx * g.ny * g.nz;
         for (int k = 1; k <= N; ++k) {
             bool to_main = ((N - k) % 2) == 0;
             T* Eo = (T*)(to_main ? h->E : h->Ec);
             T* Bo = (T*)(to_main ? h->B : h->Bc);
-            ksb_sweep_kernel<T, G><<<grid_blocks(n), NTHR, 0, h->stream>>>(g, (const T*)h->Es, (const T*)h->Bs, (const T*)Ek,
+            ksb_sweep_kernel<T, G><<<cell_grid(g.nx, g.ny, g.nz), CELL_THREADS, 0, h->stream>>>(g, (const T*)h->Es, (const T*)h->Bs, (const T*)Ek,
                                                                             (const T*)Bk, (const T*)h->Jcur, Eo, Bo, c,
                                                                             h->cfg.s_shear * h->cfg.Omega0, 0.5 * g.nx);
             h->prof.launches++;
@@ -406,7 +405,9 @@ template <class T> static long long step_params(pic_handle* h, int b, StepP& P, 
     P.theta_inj = cf.theta_inj;
     P.esc_dims = cf.escape_dims;
     P.inv_c2 = 1.0 / (cf.c * cf.c);
+    P.inv_c = 1.0 / cf.c;
     P.f.c = (float)P.c;
+    P.f.inv_c = (float)P.inv_c;
     P.f.inv_c2 = (float)P.inv_c2;
     P.f.sO = (float)P.sO;
     P.f.Omega0 = (float)P.Omega0;
@@ -518,8 +519,8 @@ template <class T, int G> static pic_status post_particle_t(pic_handle* h, const
     fold_current_t<T, G>(h, (T*)h->J);
     if (cf.box == PIC_BOX_SHEAR && GeomT<G>::AY) {
         // J'(x') -> J'(x): advect along y into the second buffer (h->Jcur)
-        ksb_advect_kernel<T><<<grid_blocks(3ll * g.nx * g.ny * g.nz), NTHR, 0, h->stream>>>(g, (const T*)h->J, (T*)h->Jtmp,
-                                                                                             cf.s_shear * cf.Omega0, 0.5 * g.nx);
+        ksb_advect_kernel<T><<<cell_grid(g.nx, (g.ny + ADVECT_ROWS - 1) / ADVECT_ROWS, 3ll * g.nz), CELL_THREADS, 0,
+                               h->stream>>>(g, (const T*)h->J, (T*)h->Jtmp, cf.s_shear * cf.Omega0, 0.5 * g.nx);
         h->prof.launches++;
     }
     field_step_t<T, G>(h);

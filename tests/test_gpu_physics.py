@@ -139,3 +139,64 @@ def test_mri_grows_with_keplerian_shear_and_not_without():
     assert 0.55 * Om <= gamma <= 1.0 * Om, gamma / Om
     h0, _ = _mri_run(0.0)
     assert h0[:, 1].max() < 2 * h0[0, 1]
+
+
+def _mj_mean_gamma_minus_one(theta):
+    """<gamma> - 1 of the isotropic Maxwell-Juettner law at temperature theta:
+    K1(1/theta) / K2(1/theta) + 3 theta - 1 (textbook; scaled Bessel
+    functions so that large 1/theta stays finite)."""
+    from scipy.special import kve
+
+    x = 1.0 / theta
+    return kve(1, x) / kve(2, x) + 3.0 * theta - 1.0
+
+
+@pytest.mark.gpu
+def test_leaky_box_relaxes_to_a_steady_state():
+    """Leaky box (Sec. 4): particles escape and are replaced at their own
+    position by particles drawn from the reinjection law, so the box keeps its
+    particle number and its energy content settles where escape balances what
+    comes in (the steady state of Sec. 4.2).  With the probabilistic escape
+    rule (probability p per step) and no work done by the fields (a hot pair
+    plasma in a uniform guide field), the mean kinetic energy per particle obeys
+    e(n) = e_inj + (e(0) - e_inj) (1 - p)^n, e_inj the mean of the reinjection
+    law, and the escape count is binomial with mean N p n.  The same box with
+    escape off keeps e(0): the drift to the reinjection temperature is the
+    escape's doing.  FP32 particles, FP64 sums."""
+    n, ppc, theta0, theta_inj, p = (64, 64, 1), 32, 1.0, 0.1, 0.02
+    u = W.PairUnits(0.45, 5.0, ppc)
+    npart = 2 * ppc * n[0] * n[1]
+    out = {}
+    for mode in (P.PIC_ESC_PROBABILISTIC, P.PIC_ESC_NONE):
+        cfg = P.make_config(box=P.PIC_BOX_LEAKY, ndim=2, plane=P.PIC_PLANE_XY, nx=n[0], ny=n[1], nz=1, order=1,
+                            precision=P.PIC_FP32, escape_mode=mode, p_esc=p, theta_inj=theta_inj, seed=21)
+        box = P.Box(cfg)
+        try:
+            box.load_maxwellian(0, -u.q, 1.0, ppc, theta0, seed=1, id_base=0)
+            box.load_maxwellian(1, u.q, 1.0, ppc, theta0, seed=2, id_base=ppc * n[0] * n[1])
+            box.set_uniform_fields((0.0, 0.0, 0.0), (0.0, 0.0, u.b0_from_sigma(0.1)))
+            hist = []
+            for k in range(13):
+                if k:
+                    box.step(25)
+                d = box.diagnostics()
+                assert d.error_word == 0
+                assert d.count[0] + d.count[1] == npart
+                ke = (d.kinetic_energy[0] + d.kinetic_energy[1]) / (npart * u.c**2)
+                hist.append((d.step, ke, d.escaped_total))
+        finally:
+            box.close()
+        out[mode] = hist
+    e_inj = _mj_mean_gamma_minus_one(theta_inj)
+    leaky, closed = out[P.PIC_ESC_PROBABILISTIC], out[P.PIC_ESC_NONE]
+    e0 = leaky[0][1]
+    assert e0 == pytest.approx(_mj_mean_gamma_minus_one(theta0), rel=0.01)  # the load itself
+    for step, ke, _ in leaky:
+        want = e_inj + (e0 - e_inj) * (1 - p) ** step
+        assert abs(ke - want) <= 0.02 * want, (step, ke, want)
+    steps, _, esc = leaky[-1]
+    mean = npart * p * steps
+    assert abs(esc - mean) <= 5 * math.sqrt(mean * (1 - p))
+    assert abs(leaky[-1][1] - e_inj) <= 0.03 * e_inj  # the steady state: (1 - p)^300 ~ 2e-3
+    for _, ke, esc in closed:
+        assert esc == 0 and ke == pytest.approx(e0, rel=0.01)
