@@ -28,7 +28,7 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BOX_PERIODIC, BOX_SHEAR, BOX_EXPAND, BOX_LEAKY = 0, 1, 2, 3
+BOX_PERIODIC, BOX_SHEAR, BOX_EXPAND, BOX_LEAKY, BOX_SHEAR_EXPAND = 0, 1, 2, 3, 4
 ESC_NONE, ESC_DISPLACEMENT, ESC_PROBABILISTIC = 0, 1, 2
 
 
@@ -103,6 +103,10 @@ def lib():
                                     C.POINTER(StepInfo)]),
                 "ora_advance_particle": (None, [P, _D, _D, _D, C.c_int64, C.c_double, C.c_double, C.c_uint32,
                                                 _D, _D, _D, C.POINTER(StepInfo)]),
+                "ora_push_sxe": (None, [C.c_double] * 6 + [_D, _D, _D, _D, _D]),
+                "ora_sxe_rhs": (None, [P, _D, _D, _D, C.c_double, _D, _D]),
+                "ora_sxe_advect_current": (None, [P, _D, C.c_double]),
+                "ora_sxe_field_solve": (None, [P, _D, _D, _D, C.c_double]),
                 "ora_set_threads": (None, [C.c_int]),
                 "ora_max_threads": (C.c_int, []),
             }
@@ -162,6 +166,13 @@ def push_keb(q, m, c, Lam, E, B, u, exact=False):
     uu = _vec(u)
     lib().ora_push_keb(q, m, c, _dp(_vec(Lam)), _dp(_vec(E)), _dp(_vec(B)), _dp(uu), int(exact))
     return uu
+
+
+def push_sxe(q, m, c, s, Omega0, xc, Lam, E, B, u):
+    uu = _vec(u)
+    gb = C.c_double()
+    lib().ora_push_sxe(q, m, c, s, Omega0, xc, _dp(_vec(Lam)), _dp(_vec(E)), _dp(_vec(B)), _dp(uu), C.byref(gb))
+    return uu, gb.value
 
 
 def philox4x32_10(ctr, key):
@@ -231,6 +242,20 @@ def ksb_rhs(p: Params, E, B, J, t):
     FE, FB = np.zeros_like(E), np.zeros_like(B)
     lib().ora_ksb_rhs(C.byref(p), _dp(E), _dp(B), _dp(J), t, _dp(FE), _dp(FB))
     return FE, FB
+
+
+def sxe_rhs(p: Params, E, B, J, t):
+    FE, FB = np.zeros_like(E), np.zeros_like(B)
+    lib().ora_sxe_rhs(C.byref(p), _dp(E), _dp(B), _dp(J), t, _dp(FE), _dp(FB))
+    return FE, FB
+
+
+def sxe_advect_current(p: Params, J, t):
+    lib().ora_sxe_advect_current(C.byref(p), _dp(J), t)
+
+
+def sxe_field_solve(p: Params, E, B, J, t):
+    lib().ora_sxe_field_solve(C.byref(p), _dp(E), _dp(B), _dp(J), t)
 
 
 def advance_particles(p: Params, E, B, step, q, m, ids, x, u, dr=None):

@@ -234,6 +234,96 @@ void ora_push_keb(double q, double m, double c, const double Lambda[3], const do
     for (int i = 0; i < 3; ++i) u[i] = up[i] + eps[i];
 }
 
+/* Solve the 3x3 system M x = b by Gaussian elimination with partial pivoting. */
+static void solve3_gauss(const double M0[3][3], const double b0[3], double x[3])
+{
+    double M[3][3], b[3];
+    memcpy(M, M0, sizeof(M));
+    memcpy(b, b0, sizeof(b));
+    for (int col = 0; col < 3; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 3; ++r)
+            if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
+        if (piv != col) {
+            for (int k = 0; k < 3; ++k) {
+                double tmp = M[col][k];
+                M[col][k] = M[piv][k];
+                M[piv][k] = tmp;
+            }
+            double tb = b[col];
+            b[col] = b[piv];
+            b[piv] = tb;
+        }
+        for (int r = col + 1; r < 3; ++r) {
+            double f = M[r][col] / M[col][col];
+            for (int k = col; k < 3; ++k) M[r][k] -= f * M[col][k];
+            b[r] -= f * b[col];
+        }
+    }
+    for (int r = 2; r >= 0; --r) {
+        double acc = b[r];
+        for (int k = r + 1; k < 3; ++k) acc -= M[r][k] * x[k];
+        x[r] = acc / M[r][r];
+    }
+}
+
+/* Combined shearing + expanding box (the combination Sec. 5 leaves for future
+ * work; this library's formulation).  The KSB-OA momentum equation (eq. OAu)
+ * in the coordinates xi = L^{-1} x of the expanding box gains the KEB term
+ * -L^{-1} dL/dt u' (eq. EBu).  Discretised like eqs. OAu_disc and EBu_disc
+ * together:
+ *   (I - Lambda - T - S) u+ = (I + Lambda + T + S) u-,
+ * T v = v x tt, tt = tau/gbar + dt Omega0 e_z, S v = (S_2 . v) e_y with the
+ * alpha terms of Sec. 2.2 (a2 = s Omega0 x^n / c, x^n the physical radial
+ * coordinate from the box centre), Lambda = -(dt/2) L^{-1} dL/dt (diagonal).
+ * gbar: the root >= 1 of
+ *   gbar^2 = 1 + [((I + Lambda) u-)^2 + 2 a1 u-_x u-_y + 2 a2 (u-.eps) u-_y / gbar] / c^2,
+ * which is Sec. 2.2's relation for Lambda = 0 and Sec. 3.2's definition for
+ * Omega0 = 0.  The 3x3 system is solved directly.  u'^{n+1/2} = u+ + eps. */
+void ora_push_sxe(double q, double m, double c, double s, double Omega0, double xc, const double Lambda[3],
+                  const double E[3], const double B[3], double u[3], double *gbar_out)
+{
+    double eps[3], um[3];
+    for (int i = 0; i < 3; ++i) eps[i] = q * E[i] / (2.0 * m);
+    for (int i = 0; i < 3; ++i) um[i] = u[i] + eps[i];
+    double alpha1 = s * Omega0 / 2.0;
+    double alpha2 = s * Omega0 * xc / c;
+    double c2 = c * c;
+    double lu[3];
+    for (int i = 0; i < 3; ++i) lu[i] = (1.0 + Lambda[i]) * um[i];
+    double ue = dot3(um, eps);
+    double A = 1.0 + (dot3(lu, lu) + 2.0 * alpha1 * um[0] * um[1]) / c2;
+    double C = 2.0 * alpha2 * ue * um[1] / c2;
+    /* Newton on gbar^3 - A gbar - C = 0 from the Lambda-corrected Lorentz factor */
+    double g = sqrt(1.0 + dot3(lu, lu) / c2);
+    for (int it = 0; it < 60; ++it) {
+        double f = g * g * g - A * g - C;
+        double dg = f / (3.0 * g * g - A);
+        g -= dg;
+        if (fabs(dg) <= 1e-16 * g) break;
+    }
+    if (gbar_out) *gbar_out = g;
+    double et[3], tt[3];
+    for (int i = 0; i < 3; ++i) et[i] = eps[i] / (c * g);
+    for (int i = 0; i < 3; ++i) tt[i] = q * B[i] / (2.0 * m * c) / g;
+    tt[2] += Omega0;
+    double S2[3] = {alpha1 + alpha2 * et[0], alpha2 * et[1], alpha2 * et[2]};
+    /* rows of K = Lambda + T + S: (K v)_r = Lambda_r v_r + (v x tt)_r + [r == y] S_2 . v */
+    double K[3][3] = {{Lambda[0], tt[2], -tt[1]}, {-tt[2], Lambda[1], tt[0]}, {tt[1], -tt[0], Lambda[2]}};
+    for (int k = 0; k < 3; ++k) K[1][k] += S2[k];
+    double M[3][3], rhs[3];
+    for (int r = 0; r < 3; ++r) {
+        rhs[r] = um[r];
+        for (int k = 0; k < 3; ++k) {
+            M[r][k] = (r == k ? 1.0 : 0.0) - K[r][k];
+            rhs[r] += K[r][k] * um[k];
+        }
+    }
+    double up[3];
+    solve3_gauss(M, rhs, up);
+    for (int i = 0; i < 3; ++i) u[i] = up[i] + eps[i];
+}
+
 /* ======================================================================== */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and the samplers        */
 /* ======================================================================== */
@@ -371,8 +461,20 @@ static int64_t gidx(const ora_params *p, int comp, int64_t i, int64_t j, int64_t
  * Dy_s = s Omega0 (x_o - x_i) t (Sec. 2.1), reduced modulo the box length. */
 double ora_shear_shift(const ora_params *p, double t)
 {
-    if (p->box != ORA_BOX_SHEAR) return 0.0;
-    double d = fmod(p->s * p->Omega0 * (double)p->nx * t, (double)p->ny);
+    double d;
+    if (p->box == ORA_BOX_SHEAR) {
+        d = p->s * p->Omega0 * (double)p->nx * t;
+    } else if (p->box == ORA_BOX_SHEAR_EXPAND) {
+        /* In the expanding coordinates xi = L^{-1} x the two x faces slide
+         * apart along xi_y at s Omega0 (l_1 nx) / l_2, so
+         * Dxi_s(t) = s Omega0 nx int_0^t l_1/l_2 dt' with l_i = exp(rate_i t). */
+        double dr = p->rate[0] - p->rate[1];
+        double I = dr == 0.0 ? t : expm1(dr * t) / dr;
+        d = p->s * p->Omega0 * (double)p->nx * I;
+    } else {
+        return 0.0;
+    }
+    d = fmod(d, (double)p->ny);
     if (d < 0.0) d += (double)p->ny;
     return d;
 }
@@ -675,11 +777,25 @@ void ora_keb_field_update(const ora_params *p, double *E, double *B, const doubl
  * V-terms: centred difference, averaged in y onto the component's location;
  * B_x in the B_y row: average of the four surrounding B_x.  Ghost values
  * across x use the shear shift at time t. */
+static void ksb_rhs_scaled(const ora_params *p, const double *E, const double *B, const double *J, double t,
+                           const double sig[3], double vf, double rx, double rz, double *FE, double *FB);
+
 void ora_ksb_rhs(const ora_params *p, const double *E, const double *B, const double *J,
                  double t, double *FE, double *FB)
 {
+    const double one[3] = {1.0, 1.0, 1.0};
+    ksb_rhs_scaled(p, E, B, J, t, one, 1.0, 1.0, 1.0, FE, FB);
+}
+
+/* The right-hand sides above with the factors of the expanding coordinates
+ * (see ora_sxe_rhs): the curls act on sig (.) X, the shear velocity and the
+ * shear term carry vf, the -V dx E'_y and -V dz E'_y terms rx and rz.  With
+ * all factors one this is ora_ksb_rhs exactly. */
+static void ksb_rhs_scaled(const ora_params *p, const double *E, const double *B, const double *J, double t,
+                           const double sig[3], double vf, double rx, double rz, double *FE, double *FB)
+{
     double dys = ora_shear_shift(p, t);
-    double sO = p->s * p->Omega0, c = p->c;
+    double sO = p->s * p->Omega0 * vf, c = p->c;
     for (int64_t k = 0; k < p->nz; ++k)
         for (int64_t j = 0; j < p->ny; ++j)
             for (int64_t i = 0; i < p->nx; ++i) {
@@ -687,12 +803,16 @@ void ora_ksb_rhs(const ora_params *p, const double *E, const double *B, const do
 #define Bf(cc, di, dj, dk) fetch(p, B, cc, i + (di), j + (dj), k + (dk), dys)
                 double VN = -sO * ((double)i - 0.5 * p->nx);       /* at x-nodes */
                 double VH = -sO * ((double)i + 0.5 - 0.5 * p->nx); /* at x half-points */
-                double curlEx = (Ef(2, 0, 1, 0) - Ef(2, 0, 0, 0)) - (Ef(1, 0, 0, 1) - Ef(1, 0, 0, 0));
-                double curlEy = (Ef(0, 0, 0, 1) - Ef(0, 0, 0, 0)) - (Ef(2, 1, 0, 0) - Ef(2, 0, 0, 0));
-                double curlEz = (Ef(1, 1, 0, 0) - Ef(1, 0, 0, 0)) - (Ef(0, 0, 1, 0) - Ef(0, 0, 0, 0));
-                double curlBx = (Bf(2, 0, 0, 0) - Bf(2, 0, -1, 0)) - (Bf(1, 0, 0, 0) - Bf(1, 0, 0, -1));
-                double curlBy = (Bf(0, 0, 0, 0) - Bf(0, 0, 0, -1)) - (Bf(2, 0, 0, 0) - Bf(2, -1, 0, 0));
-                double curlBz = (Bf(1, 0, 0, 0) - Bf(1, -1, 0, 0)) - (Bf(0, 0, 0, 0) - Bf(0, 0, -1, 0));
+#define SEf(cc, di, dj, dk) (sig[cc] * Ef(cc, di, dj, dk))
+#define SBf(cc, di, dj, dk) (sig[cc] * Bf(cc, di, dj, dk))
+                double curlEx = (SEf(2, 0, 1, 0) - SEf(2, 0, 0, 0)) - (SEf(1, 0, 0, 1) - SEf(1, 0, 0, 0));
+                double curlEy = (SEf(0, 0, 0, 1) - SEf(0, 0, 0, 0)) - (SEf(2, 1, 0, 0) - SEf(2, 0, 0, 0));
+                double curlEz = (SEf(1, 1, 0, 0) - SEf(1, 0, 0, 0)) - (SEf(0, 0, 1, 0) - SEf(0, 0, 0, 0));
+                double curlBx = (SBf(2, 0, 0, 0) - SBf(2, 0, -1, 0)) - (SBf(1, 0, 0, 0) - SBf(1, 0, 0, -1));
+                double curlBy = (SBf(0, 0, 0, 0) - SBf(0, 0, 0, -1)) - (SBf(2, 0, 0, 0) - SBf(2, -1, 0, 0));
+                double curlBz = (SBf(1, 0, 0, 0) - SBf(1, -1, 0, 0)) - (SBf(0, 0, 0, 0) - SBf(0, 0, -1, 0));
+#undef SEf
+#undef SBf
                 /* upwinded d_y for transport velocity v */
 #define UPB(cc, v) ((v) > 0.0 ? Bf(cc, 0, 0, 0) - Bf(cc, 0, -1, 0) : Bf(cc, 0, 1, 0) - Bf(cc, 0, 0, 0))
 #define UPE(cc, v) ((v) > 0.0 ? Ef(cc, 0, 0, 0) - Ef(cc, 0, -1, 0) : Ef(cc, 0, 1, 0) - Ef(cc, 0, 0, 0))
@@ -706,11 +826,11 @@ void ora_ksb_rhs(const ora_params *p, const double *E, const double *B, const do
                                       + (Ef(2, 0, 0, 0) - Ef(2, 0, 0, -1)) + (Ef(2, 0, 1, 0) - Ef(2, 0, 1, -1)));
                 double dzEy = 0.5 * ((Ef(1, 0, 0, 1) - Ef(1, 0, 0, 0)) + (Ef(1, 0, -1, 1) - Ef(1, 0, -1, 0)));
                 FE[gidx(p, 0, i, j, k)] = c * curlBx - FOUR_PI * J[gidx(p, 0, i, j, k)]
-                                          + VH * UPE(0, -VH) - VH * dxEy;
+                                          + VH * UPE(0, -VH) - VH * (rx * dxEy);
                 FE[gidx(p, 1, i, j, k)] = c * curlBy - FOUR_PI * J[gidx(p, 1, i, j, k)]
                                           - VN * UPE(1, VN) - VN * divxz;
                 FE[gidx(p, 2, i, j, k)] = c * curlBz - FOUR_PI * J[gidx(p, 2, i, j, k)]
-                                          + VN * UPE(2, -VN) - VN * dzEy;
+                                          + VN * UPE(2, -VN) - VN * (rz * dzEy);
 #undef UPB
 #undef UPE
 #undef Ef
@@ -742,6 +862,98 @@ void ora_ksb_field_solve(const ora_params *p, double *E, double *B, const double
             B[q] = B0[q] + FB[q];
         }
     }
+    free(E0); free(B0); free(Em); free(Bm); free(FE); free(FB);
+}
+
+/* Combined shearing + expanding box, fields.  The shearing-box equations
+ * (eqs. OAB, OAE) in the expanding coordinates xi = L^{-1} x, with the
+ * expanding-frame fields X^ = ell L^{-1} X of Sec. 3.1 (X = E', B):
+ *   F_B^  = -c curl(L^2 E^/ell) - V^ d_y B^ - s Omega0 (l_1/l_2) B^_x e_y
+ *   F_E^x = [c curl(L^2 B^/ell)]_x - 4 pi ell J^_x + V^ d_y E^_x - V^ (l_2/l_1)^2 d_x E^_y
+ *   F_E^y = [c curl(L^2 B^/ell)]_y - 4 pi ell J^_y - V^ d_y E^_y - V^ (d_x E^_x + d_z E^_z)
+ *   F_E^z = [c curl(L^2 B^/ell)]_z - 4 pi ell J^_z + V^ d_y E^_z - V^ (l_2/l_3)^2 d_z E^_y
+ * all derivatives along xi, V^ = -s Omega0 (l_1/l_2)(xi_x - nx/2): each
+ * shear term of Sec. 2.1 multiplied by ell L^{-1} with X = L X^/ell and
+ * d/dx_a = (1/l_a) d/dxi_a.  L at time t (the midpoint state's level). */
+void ora_sxe_rhs(const ora_params *p, const double *Eh, const double *Bh, const double *J,
+                 double t, double *FE, double *FB)
+{
+    double l[3];
+    for (int a = 0; a < 3; ++a) l[a] = exp(p->rate[a] * t);
+    double ell = l[0] * l[1] * l[2];
+    double sig[3] = {l[0] * l[0] / ell, l[1] * l[1] / ell, l[2] * l[2] / ell};
+    double rx = (l[1] / l[0]) * (l[1] / l[0]), rz = (l[1] / l[2]) * (l[1] / l[2]);
+    ksb_rhs_scaled(p, Eh, Bh, J, t, sig, l[0] / l[1], rx, rz, FE, FB);
+}
+
+/* Combined box: J' collected in xi is advected along xi_y by
+ * v_{s,y} dt / (2 l_2) = -s Omega0 (l_1/l_2) (xi_x - nx/2) dt / 2 at t^{n+1/2}. */
+static void advect_y(const ora_params *p, double *J, double vf)
+{
+    int64_t ny = p->ny;
+    double *col = (double *)malloc(sizeof(double) * (size_t)ny);
+    for (int comp = 0; comp < 3; ++comp)
+        for (int64_t k = 0; k < p->nz; ++k)
+            for (int64_t i = 0; i < p->nx; ++i) {
+                double xc = (double)i + E_STAG[comp][0] - 0.5 * (double)p->nx;
+                double d = -p->s * p->Omega0 * vf * xc / 2.0; /* content moves by d along y */
+                for (int64_t j = 0; j < ny; ++j) col[j] = J[gidx(p, comp, i, j, k)];
+                for (int64_t j = 0; j < ny; ++j) {
+                    double ys = (double)j - d; /* the value now at j came from j - d */
+                    double y0 = floor(ys);
+                    double f = ys - y0;
+                    int64_t j0 = wrapi((int64_t)y0, ny), j1 = wrapi((int64_t)y0 + 1, ny);
+                    J[gidx(p, comp, i, j, k)] = (1.0 - f) * col[j0] + f * col[j1];
+                }
+            }
+    free(col);
+}
+
+void ora_sxe_advect_current(const ora_params *p, double *J, double t)
+{
+    advect_y(p, J, exp((p->rate[0] - p->rate[1]) * (t + 0.5)));
+}
+
+/* Combined box: implicit midpoint on the expanding-frame fields, N
+ * fixed-point sweeps as in Sec. 2.2, X^ = ell L^{-1} X at t^n, the
+ * right-hand sides at t^{n+1/2}, back to X = L X^ / ell at t^{n+1}.
+ * J is the collected ell J^ (deposited in xi).  t is t^n. */
+void ora_sxe_field_solve(const ora_params *p, double *E, double *B, const double *J, double t)
+{
+    int64_t nc = ncell(p), N = 3 * nc;
+    size_t sz = sizeof(double) * (size_t)N;
+    double l0[3], l1[3];
+    for (int a = 0; a < 3; ++a) {
+        l0[a] = exp(p->rate[a] * t);
+        l1[a] = exp(p->rate[a] * (t + 1.0));
+    }
+    double ell0 = l0[0] * l0[1] * l0[2], ell1 = l1[0] * l1[1] * l1[2];
+    double *E0 = (double *)malloc(sz), *B0 = (double *)malloc(sz);
+    double *Em = (double *)malloc(sz), *Bm = (double *)malloc(sz);
+    double *FE = (double *)malloc(sz), *FB = (double *)malloc(sz);
+    for (int c = 0; c < 3; ++c)
+        for (int64_t q = 0; q < nc; ++q) {
+            E0[c * nc + q] = ell0 / l0[c] * E[c * nc + q];
+            B0[c * nc + q] = ell0 / l0[c] * B[c * nc + q];
+        }
+    memcpy(E, E0, sz); /* E, B hold the iterate X^(k) in expanding-frame form */
+    memcpy(B, B0, sz);
+    for (int it = 0; it < p->fp_iters; ++it) {
+        for (int64_t q = 0; q < N; ++q) {
+            Em[q] = 0.5 * (E0[q] + E[q]);
+            Bm[q] = 0.5 * (B0[q] + B[q]);
+        }
+        ora_sxe_rhs(p, Em, Bm, J, t + 0.5, FE, FB);
+        for (int64_t q = 0; q < N; ++q) {
+            E[q] = E0[q] + FE[q];
+            B[q] = B0[q] + FB[q];
+        }
+    }
+    for (int c = 0; c < 3; ++c)
+        for (int64_t q = 0; q < nc; ++q) {
+            E[c * nc + q] *= l1[c] / ell1;
+            B[c * nc + q] *= l1[c] / ell1;
+        }
     free(E0); free(B0); free(Em); free(Bm); free(FE); free(FB);
 }
 
@@ -799,6 +1011,39 @@ void ora_advance_particle(const ora_params *p, const double *E, const double *B,
         double xpc = x1[0] - half_nx;
         x1[1] -= p->s * p->Omega0 * (xpc + xc) / 2.0;
         /* shearing-periodic crossing of x: y shifts by Dy_s at t^{n+1} */
+        if (x1[0] >= (double)p->nx) {
+            x1[0] -= (double)p->nx;
+            x1[1] += dys_end;
+        } else if (x1[0] < 0.0) {
+            x1[0] += (double)p->nx;
+            x1[1] -= dys_end;
+            if (x1[0] >= (double)p->nx) x1[0] = 0.0;
+        }
+        x1[1] = fmod(x1[1], (double)p->ny);
+        wrap_coord(&x1[1], p->ny);
+        wrap_coord(&x1[2], p->nz);
+    } else if (p->box == ORA_BOX_SHEAR_EXPAND) {
+        /* positions are the expanding coordinates xi; u is the comoving u' */
+        double dys_end = ora_shear_shift(p, t + 1.0);
+        double Lambda[3], lh[3];
+        for (int a = 0; a < 3; ++a) {
+            Lambda[a] = -0.5 * p->rate[a];
+            lh[a] = exp(p->rate[a] * (t + 0.5));
+        }
+        double xic = x[0] - half_nx;                 /* xi_x from the box centre */
+        double xc = exp(p->rate[0] * t) * xic;       /* physical radial coordinate at t^n */
+        ora_push_sxe(q, m, p->c, p->s, p->Omega0, xc, Lambda, Ep, Bp, u, NULL);
+        double gp = sqrt(1.0 + dot3(u, u) / (p->c * p->c));
+        for (int a = 0; a < 3; ++a) x1[a] = x[a] + u[a] / (gp * lh[a]); /* xi' = xi^n + L^{-1} u'/gamma' */
+        {
+            double vy = u[1] / gp - p->s * p->Omega0 * xc;
+            double v2 = (u[0] / gp) * (u[0] / gp) + vy * vy + (u[2] / gp) * (u[2] / gp);
+            if (v2 >= p->c * p->c) loc->superluminal++;
+        }
+        if (J) ora_deposit_current(p, J, t + 0.5, q, x, x1);
+        /* the shear motion along xi_y: v_{s,y} / l_2 at t^{n+1/2} */
+        double vf = lh[0] / lh[1];
+        x1[1] -= p->s * p->Omega0 * vf * ((x1[0] - half_nx) + xic) / 2.0;
         if (x1[0] >= (double)p->nx) {
             x1[0] -= (double)p->nx;
             x1[1] += dys_end;
@@ -919,6 +1164,9 @@ void ora_step(const ora_params *p, ora_fields *f, int nsp, ora_species *sp, ora_
     if (p->box == ORA_BOX_SHEAR) {
         ora_ksb_advect_current(p, f->J);
         ora_ksb_field_solve(p, f->E, f->B, f->J, t);
+    } else if (p->box == ORA_BOX_SHEAR_EXPAND) {
+        ora_sxe_advect_current(p, f->J, t);
+        ora_sxe_field_solve(p, f->E, f->B, f->J, t);
     } else if (p->box == ORA_BOX_EXPAND) {
         ora_keb_field_update(p, f->E, f->B, f->J, t);
     } else {

@@ -29,7 +29,8 @@
 extern "C" {
 #endif
 
-enum { ORA_BOX_PERIODIC = 0, ORA_BOX_SHEAR = 1, ORA_BOX_EXPAND = 2, ORA_BOX_LEAKY = 3 };
+enum { ORA_BOX_PERIODIC = 0, ORA_BOX_SHEAR = 1, ORA_BOX_EXPAND = 2, ORA_BOX_LEAKY = 3,
+       ORA_BOX_SHEAR_EXPAND = 4 /* shearing box in expanding coordinates (see pic_oracle.c) */ };
 enum { ORA_ESC_NONE = 0, ORA_ESC_DISPLACEMENT = 1, ORA_ESC_PROBABILISTIC = 2 };
 
 typedef struct {
@@ -77,6 +78,8 @@ double ora_ksb_gamma_bar(double c, double alpha1, double alpha2, const double um
                          const double eps[3], double *residual);
 void ora_push_keb(double q, double m, double c, const double Lambda[3], const double E[3],
                   const double B[3], double u[3], int exact);
+void ora_push_sxe(double q, double m, double c, double s, double Omega0, double xc, const double Lambda[3],
+                  const double E[3], const double B[3], double u[3], double *gbar_out);
 
 /* ---- random numbers ----------------------------------------------------- */
 void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -96,6 +99,10 @@ void ora_keb_field_update(const ora_params *p, double *E, double *B, const doubl
 void ora_ksb_field_solve(const ora_params *p, double *E, double *B, const double *J, double t);
 void ora_ksb_rhs(const ora_params *p, const double *E, const double *B, const double *J,
                  double t, double *FE, double *FB);
+void ora_sxe_rhs(const ora_params *p, const double *Eh, const double *Bh, const double *J,
+                 double t, double *FE, double *FB);
+void ora_sxe_advect_current(const ora_params *p, double *J, double t);
+void ora_sxe_field_solve(const ora_params *p, double *E, double *B, const double *J, double t);
 
 /* ---- one particle's part of a step (gather, push, move, deposit when J is
  * non-NULL, escape); the whole step ------------------------------------------ */
