@@ -64,7 +64,18 @@ typedef enum {
     PIC_BOX_PERIODIC = 0, /* standard periodic PIC */
     PIC_BOX_SHEAR = 1,    /* KSB-OA shearing box, Sec. 2 */
     PIC_BOX_EXPAND = 2,   /* KEB expanding box, Sec. 3 */
-    PIC_BOX_LEAKY = 3     /* leaky box, Sec. 4 */
+    PIC_BOX_LEAKY = 3,    /* leaky box, Sec. 4 */
+    PIC_BOX_SHEAR_EXPAND = 4 /* shearing box that also expands: the combination Sec. 5 names as
+                             future work, in this library's formulation.  The KSB-OA system of
+                             Sec. 2.1 in the expanding coordinates xi = L^{-1} x of Sec. 3.1
+                             (s_shear, Omega0, fp_iters as for PIC_BOX_SHEAR; expand_rate as for
+                             PIC_BOX_EXPAND).  Positions are xi, momenta the comoving u', fields
+                             E' and B on the xi grid.  The push solves the discrete momentum
+                             equations of Secs. 2.2 and 3.2 together; the position update adds
+                             the shear motion v_{s,y}/l_2; the x faces are shear-periodic with
+                             Dxi_s(t) = s Omega0 nx int_0^t l_1/l_2 dt'; the fields are advanced
+                             by the implicit midpoint sweeps of Sec. 2.2 on X^ = ell L^{-1} X,
+                             each shear term multiplied by ell L^{-1}. */
 } pic_box;
 
 enum { PIC_PLANE_XY = 0, PIC_PLANE_XZ = 1 };

@@ -19,7 +19,7 @@ constexpr int GR = 3;  // high guard cells (deposits reach node n+2)
 // geometry kinds: which axes are active
 enum Geom : int { G3D = 0, G2XY = 1, G2XZ = 2 };
 // particle pusher kinds
-enum Push : int { PUSH_BORIS = 0, PUSH_KSB = 1, PUSH_KEB = 2 };
+enum Push : int { PUSH_BORIS = 0, PUSH_KSB = 1, PUSH_KEB = 2, PUSH_SXE = 3 /* shearing + expanding */ };
 // escape kinds (leaky box)
 enum Esc : int { ESC_NONE = 0, ESC_DISP = 1, ESC_PROB = 2 };
 
@@ -65,14 +65,26 @@ struct StepCtx {
     int dys_i[3];         // shearing shift Dy_s mod ny at t, t+1/2, t+1: integer part
     double dys_f[3];      //                                               fractional part
     double inv_lh[3];     // 1 / l_i(t + 1/2) (expanding box)
-    float f_dys_f[3];     // the same two in FP32, for the FP32 particle path
+    double lh[3];         // l_i(t + 1/2)
+    float f_dys_f[3];     // the same three in FP32, for the FP32 particle path
     float f_inv_lh[3];
+    float f_lh[3];
     Coef3 curl[3];        // curl updates of the step: B half, E full, B half
+    // shearing + expanding box (ones for the shearing box): the shear flow in
+    // the expanding coordinates, (l_1/l_2)(t + 1/2); l_1(t), which turns xi_x
+    // into the physical radial coordinate; X^ = ell L^{-1} X at t (pre) and
+    // back with L / ell at t + 1 (post); the midpoint right-hand sides' curl
+    // factors l_a^2 / ell and the factors (l_2/l_1)^2, (l_2/l_3)^2 of the
+    // -V d_x E^_y and -V d_z E^_y terms, all at t + 1/2
+    double sxe_vf, sxe_l0x;
+    float f_sxe_vf, f_sxe_l0x;
+    double sxe_pre[3], sxe_post[3], sxe_sig[3];
+    double sxe_rx, sxe_rz;
 };
 
 // Constants ctx_kernel needs (fixed for a handle).
 struct CtxConst {
-    int box;        // 1 shearing, 2 expanding, other: static
+    int box;        // 1 shearing, 2 expanding, 4 shearing + expanding, other: static
     int ny;
     double sO_Lx;   // s Omega0 nx: Dy_s(t) = sO_Lx t mod ny
     double rate[3]; // l_i(t) = exp(rate_i t)
@@ -87,8 +99,16 @@ __global__ inline void ctx_kernel(StepCtx* ctx, CtxConst k) {
     const double t = (double)n;
     for (int w = 0; w < 3; ++w) {
         double d = 0.0;
-        if (k.box == 1) {
-            d = fmod(k.sO_Lx * (t + 0.5 * w), (double)k.ny);
+        const double tw = t + 0.5 * w;
+        if (k.box == 1 || k.box == 4) {
+            // shearing box: Dy_s = s Omega0 Lx t; with expansion the faces slide
+            // apart along xi_y at s Omega0 nx l_1/l_2: Dxi_s = s Omega0 nx int_0^t l_1/l_2
+            double I = tw;
+            if (k.box == 4) {
+                const double dr = k.rate[0] - k.rate[1];
+                I = dr == 0.0 ? tw : expm1(dr * tw) / dr;
+            }
+            d = fmod(k.sO_Lx * I, (double)k.ny);
             if (d < 0.0) d += (double)k.ny;
         }
         double fl = floor(d);
@@ -99,14 +119,27 @@ __global__ inline void ctx_kernel(StepCtx* ctx, CtxConst k) {
     }
     double l0[3], lh[3], l1[3];
     for (int a = 0; a < 3; ++a) {
-        const bool ex = k.box == 2;
+        const bool ex = k.box == 2 || k.box == 4;
         l0[a] = ex ? exp(k.rate[a] * t) : 1.0;
         lh[a] = ex ? exp(k.rate[a] * (t + 0.5)) : 1.0;
         l1[a] = ex ? exp(k.rate[a] * (t + 1.0)) : 1.0;
         ctx->inv_lh[a] = 1.0 / lh[a];
         ctx->f_inv_lh[a] = (float)(1.0 / lh[a]);
+        ctx->lh[a] = lh[a];
+        ctx->f_lh[a] = (float)lh[a];
     }
     const double e0 = l0[0] * l0[1] * l0[2], eh = lh[0] * lh[1] * lh[2], e1 = l1[0] * l1[1] * l1[2];
+    ctx->sxe_vf = lh[0] / lh[1];
+    ctx->sxe_l0x = l0[0];
+    ctx->f_sxe_vf = (float)ctx->sxe_vf;
+    ctx->f_sxe_l0x = (float)l0[0];
+    for (int a = 0; a < 3; ++a) {
+        ctx->sxe_pre[a] = e0 / l0[a];
+        ctx->sxe_post[a] = l1[a] / e1;
+        ctx->sxe_sig[a] = lh[a] * lh[a] / eh;
+    }
+    ctx->sxe_rx = (lh[1] / lh[0]) * (lh[1] / lh[0]);
+    ctx->sxe_rz = (lh[1] / lh[2]) * (lh[1] / lh[2]);
     const double FOUR_PI = 12.566370614359172;
     // B^{n+1/2}: B' = ell L^-1 B at t^n, minus (c/2) curl(L E), back with L at n+1/2
     // E^{n+1}:   E' + c curl(L B^{n+1/2}) - 4 pi (ell J'), back with L at n+1

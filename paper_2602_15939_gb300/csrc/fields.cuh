@@ -84,12 +84,20 @@ __global__ void curl_update_kernel(Grid g, const T* __restrict__ in, T* __restri
 // other V-terms are centred and averaged in y onto the component's location;
 // Bx in the By row is the mean of its four neighbours.  Guards of X_n and X_k
 // hold the shearing-periodic images at t^{n+1/2}.
+//
+// The shearing + expanding box sweeps the expanding-frame fields X^ = ell
+// L^{-1} X (Sec. 3.1) with the factors of its coordinates from the step
+// context: curls of (l_a^2 / ell) X^_a, the shear flow and shear term times
+// l_1/l_2, the -V d_x E^_y and -V d_z E^_y terms times (l_2/l_1)^2 and
+// (l_2/l_3)^2, all at t^{n+1/2}.  For the shearing box these are ones.
 template <class T, int G>
 __global__ void ksb_sweep_kernel(Grid g, const T* __restrict__ En, const T* __restrict__ Bn, const T* __restrict__ Ek,
                                  const T* __restrict__ Bk, const T* __restrict__ J, T* __restrict__ Eo, T* __restrict__ Bo,
-                                 double c_, double sO_, double half_nx) {
+                                 double c_, double sO_, double half_nx, const StepCtx* __restrict__ ctx) {
     using GT = GeomT<G>;
-    const T c = T(c_), sO = T(sO_);
+    const T c = T(c_), sO = T(sO_ * ctx->sxe_vf);
+    const T sg0 = T(ctx->sxe_sig[0]), sg1 = T(ctx->sxe_sig[1]), sg2 = T(ctx->sxe_sig[2]);
+    const T rx = T(ctx->sxe_rx), rz = T(ctx->sxe_rz);
     const T FOUR_PI = T(12.566370614359172);
     const long long sx = 1, sy = GT::AY ? g.px : 0, sz = GT::AZ ? (long long)g.px * g.py : 0, cs = g.cstride;
     // launch: cell_grid(nx, ny, nz)
@@ -105,12 +113,12 @@ __global__ void ksb_sweep_kernel(Grid g, const T* __restrict__ En, const T* __re
         const T VN = -sO * (T(i) - T(half_nx));
         const T VH = -sO * ((T(i) + T(0.5)) - T(half_nx));
         // curls (ignorable-axis differences vanish because its stride is 0)
-        T curlEx = (ME(2, sy) - ME(2, 0)) - (ME(1, sz) - ME(1, 0));
-        T curlEy = (ME(0, sz) - ME(0, 0)) - (ME(2, sx) - ME(2, 0));
-        T curlEz = (ME(1, sx) - ME(1, 0)) - (ME(0, sy) - ME(0, 0));
-        T curlBx = (MB(2, 0) - MB(2, -sy)) - (MB(1, 0) - MB(1, -sz));
-        T curlBy = (MB(0, 0) - MB(0, -sz)) - (MB(2, 0) - MB(2, -sx));
-        T curlBz = (MB(1, 0) - MB(1, -sx)) - (MB(0, 0) - MB(0, -sy));
+        T curlEx = sg2 * (ME(2, sy) - ME(2, 0)) - sg1 * (ME(1, sz) - ME(1, 0));
+        T curlEy = sg0 * (ME(0, sz) - ME(0, 0)) - sg2 * (ME(2, sx) - ME(2, 0));
+        T curlEz = sg1 * (ME(1, sx) - ME(1, 0)) - sg0 * (ME(0, sy) - ME(0, 0));
+        T curlBx = sg2 * (MB(2, 0) - MB(2, -sy)) - sg1 * (MB(1, 0) - MB(1, -sz));
+        T curlBy = sg0 * (MB(0, 0) - MB(0, -sz)) - sg2 * (MB(2, 0) - MB(2, -sx));
+        T curlBz = sg1 * (MB(1, 0) - MB(1, -sx)) - sg0 * (MB(0, 0) - MB(0, -sy));
         auto upB = [&](int comp, T v) -> T { return v > T(0) ? MB(comp, 0) - MB(comp, -sy) : MB(comp, sy) - MB(comp, 0); };
         auto upE = [&](int comp, T v) -> T { return v > T(0) ? ME(comp, 0) - ME(comp, -sy) : ME(comp, sy) - ME(comp, 0); };
         T bx4 = T(0.25) * (MB(0, 0) + MB(0, sx) + MB(0, -sy) + MB(0, sx - sy));
@@ -121,9 +129,9 @@ __global__ void ksb_sweep_kernel(Grid g, const T* __restrict__ En, const T* __re
         T divxz = T(0.5) * ((ME(0, 0) - ME(0, -sx)) + (ME(0, sy) - ME(0, sy - sx)) + (ME(2, 0) - ME(2, -sz)) +
                             (ME(2, sy) - ME(2, sy - sz)));
         T dzEy = T(0.5) * ((ME(1, sz) - ME(1, 0)) + (ME(1, sz - sy) - ME(1, -sy)));
-        T FEx = c * curlBx - FOUR_PI * J[c0] + VH * upE(0, -VH) - VH * dxEy;
+        T FEx = c * curlBx - FOUR_PI * J[c0] + VH * upE(0, -VH) - VH * (rx * dxEy);
         T FEy = c * curlBy - FOUR_PI * J[cs + c0] - VN * upE(1, VN) - VN * divxz;
-        T FEz = c * curlBz - FOUR_PI * J[2 * cs + c0] + VN * upE(2, -VN) - VN * dzEy;
+        T FEz = c * curlBz - FOUR_PI * J[2 * cs + c0] + VN * upE(2, -VN) - VN * (rz * dzEy);
         Eo[c0] = En[c0] + FEx;
         Eo[cs + c0] = En[cs + c0] + FEy;
         Eo[2 * cs + c0] = En[2 * cs + c0] + FEz;
@@ -296,7 +304,11 @@ __global__ void fold_x_kernel(Grid g, T* F, const StepCtx* __restrict__ ctx, int
 // interpolation, periodic in y: Jn(j) = (1-f) J(j0) + f J(j0+1), j - d = j0 + f.
 constexpr int ADVECT_ROWS = 8;  // y rows per thread: the column's shift is computed once
 template <class T>
-__global__ void ksb_advect_kernel(Grid g, const T* __restrict__ Jin, T* __restrict__ Jout, double sO, double half_nx) {
+__global__ void ksb_advect_kernel(Grid g, const T* __restrict__ Jin, T* __restrict__ Jout, double sO_, double half_nx,
+                                  const StepCtx* __restrict__ ctx) {
+    // the shearing + expanding box advects along xi_y by v_{s,y} dt / (2 l_2):
+    // the shear times (l_1/l_2)(t^{n+1/2}) (one for the shearing box)
+    const double sO = sO_ * ctx->sxe_vf;
     // launch: cell_grid(nx, ceil(ny / ADVECT_ROWS), 3 * nz)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nx) return;
@@ -321,6 +333,18 @@ __global__ void ksb_advect_kernel(Grid g, const T* __restrict__ Jin, T* __restri
         if (jb >= g.ny) jb -= g.ny;
         Jo[g.idx(i, j, k)] = (T(1) - f) * Jc[g.idx(i, ja, k)] + f * Jc[g.idx(i, jb, k)];
     }
+}
+
+// Component-wise scaling of a padded 3-component field (guards included) by
+// ctx->sxe_pre (which = 0: X^ = ell L^{-1} X at t^n) or ctx->sxe_post (which
+// = 1: back to X = L X^ / ell at t^{n+1}).  Launch: cell_grid(cstride, 1, 3).
+template <class T>
+__global__ void scale3_kernel(T* F, long long cstride, const StepCtx* __restrict__ ctx, int which) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= cstride) return;
+    const int comp = blockIdx.z;
+    const double f = which == 0 ? ctx->sxe_pre[comp] : ctx->sxe_post[comp];
+    F[comp * cstride + q] = T((double)F[comp * cstride + q] * f);
 }
 
 // FP32 current: fixed-point int32 sums -> float, flagging sums that reached

@@ -69,7 +69,8 @@ struct Tiling {
 // reads them from the parameter bank, with no FP64 conversion per particle.
 struct StepPF {
     float c, inv_c, inv_c2, sO, Omega0, half_nx, l_esc, dys_end_f;
-    float Lam[3], im[3], Lt[3], inv_lh[3];
+    float Lam[3], im[3], Lt[3], inv_lh[3], lh[3];
+    float sxe_vf, sxe_l0x;
 };
 
 // The step constant of the path's arithmetic type: FP64 or its FP32 copy.
@@ -95,6 +96,9 @@ struct StepP {
     double keb_im[3];   // 1 / (1 - Lambda_ii)
     double keb_Lt[3];   // (1 + Lambda_ii) / (1 - Lambda_ii)
     double inv_lh[3];   // 1 / l_i(t^{n+1/2})
+    double lh[3];       // l_i(t^{n+1/2})
+    // shearing + expanding box: (l_1/l_2)(t^{n+1/2}) and l_1(t^n)
+    double sxe_vf, sxe_l0x;
     // leaky box
     double l_esc;
     uint32_t esc_thresh;
@@ -547,6 +551,60 @@ __device__ inline void push_keb(T u[3], const T E[3], const T B[3], T qdt2m, T q
     u[0] = up[0] + eps[0]; u[1] = up[1] + eps[1]; u[2] = up[2] + eps[2];
 }
 
+// Shearing + expanding box push: the discrete momentum equation of Sec. 2.2
+// with the expansion term of Sec. 3.2 added,
+//   (I - Lambda - T - S) u+ = (I + Lambda + T + S) u-,
+// T v = v x tt, S v = (S_2 . v) e_y, gbar from the Lambda-corrected cubic
+// gbar^3 - A gbar - C = 0 (A with ((I + Lambda) u-)^2), solved by Newton from
+// the expanding box's Lorentz factor; the 3x3 system by Cramer's rule.  xc:
+// the physical radial coordinate l_1 (xi_x - nx/2) at t^n.
+template <class T>
+__device__ inline void push_sxe(T u[3], const T E[3], const T B[3], T qdt2m, T qdt2mc, T inv_c, T inv_c2, T sO, T Om,
+                                T xc, const T Lam[3]) {
+    T eps[3] = {qdt2m * E[0], qdt2m * E[1], qdt2m * E[2]};
+    T um[3] = {u[0] + eps[0], u[1] + eps[1], u[2] + eps[2]};
+    const T a1 = sO * T(0.5), a2 = sO * xc * inv_c;
+    T lu[3] = {(T(1) + Lam[0]) * um[0], (T(1) + Lam[1]) * um[1], (T(1) + Lam[2]) * um[2]};
+    const T l2 = dot(lu, lu) * inv_c2;
+    const T A = T(1) + l2 + T(2) * a1 * um[0] * um[1] * inv_c2;
+    const T Cc = T(2) * a2 * dot(um, eps) * um[1] * inv_c2;
+    T g = t_sqrt<T>(T(1) + l2);
+    const int NIT = sizeof(T) == 8 ? 8 : 2;
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+        T f = (g * g - A) * g - Cc;
+        T df = T(3) * g * g - A;
+        g -= sizeof(T) == 8 ? f / df : f * t_rcp<T>(df);
+    }
+    const T ig = t_rcp<T>(g), igc = ig * inv_c;
+    const T tt[3] = {qdt2mc * B[0] * ig, qdt2mc * B[1] * ig, qdt2mc * B[2] * ig + Om};
+    const T S2[3] = {a1 + a2 * eps[0] * igc, a2 * eps[1] * igc, a2 * eps[2] * igc};
+    // K = Lambda + T + S: (K v)_r = Lambda_r v_r + (v x tt)_r + [r = y] S_2 . v
+    T K[3][3] = {{Lam[0], tt[2], -tt[1]}, {-tt[2], Lam[1], tt[0]}, {tt[1], -tt[0], Lam[2]}};
+    K[1][0] += S2[0];
+    K[1][1] += S2[1];
+    K[1][2] += S2[2];
+    T M[3][3], r[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        r[i] = um[i] + K[i][0] * um[0] + K[i][1] * um[1] + K[i][2] * um[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) M[i][k] = (i == k ? T(1) : T(0)) - K[i][k];
+    }
+    const T c00 = M[1][1] * M[2][2] - M[1][2] * M[2][1];
+    const T c01 = M[1][2] * M[2][0] - M[1][0] * M[2][2];
+    const T c02 = M[1][0] * M[2][1] - M[1][1] * M[2][0];
+    const T det = M[0][0] * c00 + M[0][1] * c01 + M[0][2] * c02;
+    const T idet = sizeof(T) == 8 ? T(1) / det : t_rcp<T>(det);
+    // Cramer: column k replaced by r
+    const T x0 = r[0] * c00 + M[0][1] * (M[1][2] * r[2] - r[1] * M[2][2]) + M[0][2] * (r[1] * M[2][1] - M[1][1] * r[2]);
+    const T x1 = M[0][0] * (r[1] * M[2][2] - M[1][2] * r[2]) + r[0] * c01 + M[0][2] * (M[1][0] * r[2] - r[1] * M[2][0]);
+    const T x2 = M[0][0] * (M[1][1] * r[2] - r[1] * M[2][1]) + M[0][1] * (r[1] * M[2][0] - M[1][0] * r[2]) + r[0] * c02;
+    u[0] = x0 * idet + eps[0];
+    u[1] = x1 * idet + eps[1];
+    u[2] = x2 * idet + eps[2];
+}
+
 // ---- charge-conserving deposit (Esirkepov) -------------------------------------------
 // The particle moves from x0 = o (offsets in its start cell) to x1 = o + d,
 // |d| < 1 per axis.  With S0, S1 the node shapes on a window of ORD+2 nodes
@@ -890,6 +948,11 @@ __device__ inline void push_particle(Particle<T>& p, const FA& fa, I fidx, const
         const T xc0 = (T(p.ci) - pk<T>(P.half_nx, P.f.half_nx)) + p.o[0];  // exact: integer and half-integer
         push_ksb<T>(p.u, E, B, S.qdt2m, S.qdt2mc, pk<T>(P.inv_c, P.f.inv_c), inv_c2, pk<T>(P.sO, P.f.sO),
                     pk<T>(P.Omega0, P.f.Omega0), xc0);
+    } else if (PUSH == PUSH_SXE) {
+        const T xi0 = (T(p.ci) - pk<T>(P.half_nx, P.f.half_nx)) + p.o[0];
+        const T Lam[3] = {pk<T>(P.Lam[0], P.f.Lam[0]), pk<T>(P.Lam[1], P.f.Lam[1]), pk<T>(P.Lam[2], P.f.Lam[2])};
+        push_sxe<T>(p.u, E, B, S.qdt2m, S.qdt2mc, pk<T>(P.inv_c, P.f.inv_c), inv_c2, pk<T>(P.sO, P.f.sO),
+                    pk<T>(P.Omega0, P.f.Omega0), xi0 * pk<T>(P.sxe_l0x, P.f.sxe_l0x), Lam);
     } else if (PUSH == PUSH_KEB) {
         const T Lam[3] = {pk<T>(P.Lam[0], P.f.Lam[0]), pk<T>(P.Lam[1], P.f.Lam[1]), pk<T>(P.Lam[2], P.f.Lam[2])};
         const T im[3] = {pk<T>(P.keb_im[0], P.f.im[0]), pk<T>(P.keb_im[1], P.f.im[1]), pk<T>(P.keb_im[2], P.f.im[2])};
@@ -900,7 +963,7 @@ __device__ inline void push_particle(Particle<T>& p, const FA& fa, I fidx, const
     }
     T ig = t_rsqrt<T>(T(1) + dot(p.u, p.u) * inv_c2);  // 1 / gamma^{n+1/2}
     d[0] = p.u[0] * ig; d[1] = p.u[1] * ig; d[2] = p.u[2] * ig;
-    if (PUSH == PUSH_KEB) {
+    if (PUSH == PUSH_KEB || PUSH == PUSH_SXE) {
         d[0] *= pk<T>(P.inv_lh[0], P.f.inv_lh[0]);
         d[1] *= pk<T>(P.inv_lh[1], P.f.inv_lh[1]);
         d[2] *= pk<T>(P.inv_lh[2], P.f.inv_lh[2]);
@@ -936,6 +999,23 @@ __device__ inline void move_particle(Particle<T>& p, const T d[3], const StepP& 
             if (d[0] * d[0] + vy * vy + d[2] * d[2] >= c * c) atomicAdd(P.counters + 1, 1ull);
         }
         ny_ -= vs;
+    } else if (PUSH == PUSH_SXE) {
+        // in the expanding coordinates the shear flow moves xi_y at v_{s,y} / l_2:
+        // xi^{n+1}_y = xi'_y - s Omega0 (l_1/l_2)(t^{n+1/2}) (xi'_x + xi^n_x)/2 dt
+        const T c = pk<T>(P.c, P.f.c);
+        const T sO = pk<T>(P.sO, P.f.sO);
+        const T vf = pk<T>(P.sxe_vf, P.f.sxe_vf);
+        const T half_nx = pk<T>(P.half_nx, P.f.half_nx);
+        const T xc0 = (T(p.ci) - half_nx) + p.o[0];
+        const T xc1 = (T(p.ci) - half_nx) + nx_;
+        {
+            // physical velocity u'/gamma' + v_s (d is the xi displacement L^{-1} u'/gamma')
+            const T lx = pk<T>(P.lh[0], P.f.lh[0]), ly = pk<T>(P.lh[1], P.f.lh[1]), lz = pk<T>(P.lh[2], P.f.lh[2]);
+            const T vx = d[0] * lx, vz = d[2] * lz;
+            const T vy = d[1] * ly - sO * xc0 * pk<T>(P.sxe_l0x, P.f.sxe_l0x);
+            if (vx * vx + vy * vy + vz * vz >= c * c) atomicAdd(P.counters + 1, 1ull);
+        }
+        ny_ -= sO * vf * (xc1 + xc0) * T(0.5);
     }
     p.o[0] = nx_; renorm(p.o[0], p.ci);
     if (GT::AY) { p.o[1] = ny_; renorm(p.o[1], p.cj); } else { p.o[1] = T(0.5); }
@@ -943,14 +1023,14 @@ __device__ inline void move_particle(Particle<T>& p, const T d[3], const StepP& 
     // periodic / shearing-periodic wrap
     if (p.ci >= g.nx) {
         p.ci -= g.nx;
-        if (PUSH == PUSH_KSB && GT::AY) {
+        if ((PUSH == PUSH_KSB || PUSH == PUSH_SXE) && GT::AY) {
             p.cj += P.dys_end_i;
             p.o[1] += pk<T>(P.dys_end_f, P.f.dys_end_f);
             renorm(p.o[1], p.cj);
         }
     } else if (p.ci < 0) {
         p.ci += g.nx;
-        if (PUSH == PUSH_KSB && GT::AY) {
+        if ((PUSH == PUSH_KSB || PUSH == PUSH_SXE) && GT::AY) {
             p.cj -= P.dys_end_i;
             p.o[1] -= pk<T>(P.dys_end_f, P.f.dys_end_f);
             renorm(p.o[1], p.cj);
@@ -1012,6 +1092,14 @@ __device__ inline StepP with_ctx(const StepP& P0, const StepCtx* ctx) {
     P.f.inv_lh[0] = ctx->f_inv_lh[0];
     P.f.inv_lh[1] = ctx->f_inv_lh[1];
     P.f.inv_lh[2] = ctx->f_inv_lh[2];
+    for (int a = 0; a < 3; ++a) {
+        P.lh[a] = ctx->lh[a];
+        P.f.lh[a] = ctx->f_lh[a];
+    }
+    P.sxe_vf = ctx->sxe_vf;
+    P.sxe_l0x = ctx->sxe_l0x;
+    P.f.sxe_vf = ctx->f_sxe_vf;
+    P.f.sxe_l0x = ctx->f_sxe_l0x;
     return P;
 }
 

@@ -267,7 +267,8 @@ template <class T, int G> static void fill_guards_t(pic_handle* h, T* F, int ctx
         df = dys - di;
         di %= g.ny;
     }
-    const StepCtx* ctx = (ctx_which >= 0 && h->cfg.box == PIC_BOX_SHEAR) ? h->ctx : nullptr;
+    const bool shearing = h->cfg.box == PIC_BOX_SHEAR || h->cfg.box == PIC_BOX_SHEAR_EXPAND;
+    const StepCtx* ctx = (ctx_which >= 0 && shearing) ? h->ctx : nullptr;
     fill_x_kernel<T, G><<<cell_grid(g.ny, g.nz, 3ll * (g.px - g.nx)), CELL_THREADS, 0, h->stream>>>(
         g, F, 3, di, df, ctx, ctx_which < 0 ? 0 : ctx_which);
     h->prof.launches++;
@@ -310,15 +311,22 @@ template <class T, int G> static void curl_t(pic_handle* h, bool curlE, const vo
 // Host-side shearing shift and expansion factors (diagnostics, set-up fills);
 // the step itself takes them from the device context.
 static double shear_shift(const pic_handle* h, double t) {
-    if (h->cfg.box != PIC_BOX_SHEAR) return 0.0;
-    double ny = (double)h->cfg.ny;
-    double d = std::fmod(h->cfg.s_shear * h->cfg.Omega0 * (double)h->cfg.nx * t, ny);
+    const pic_config& c = h->cfg;
+    if (c.box != PIC_BOX_SHEAR && c.box != PIC_BOX_SHEAR_EXPAND) return 0.0;
+    double I = t;  // shearing + expanding box: int_0^t l_1/l_2 dt'
+    if (c.box == PIC_BOX_SHEAR_EXPAND) {
+        const double dr = c.expand_rate[0] - c.expand_rate[1];
+        I = dr == 0.0 ? t : std::expm1(dr * t) / dr;
+    }
+    double ny = (double)c.ny;
+    double d = std::fmod(c.s_shear * c.Omega0 * (double)c.nx * I, ny);
     if (d < 0) d += ny;
     return d;
 }
 
 static void lvals(const pic_handle* h, double t, double l[3]) {
-    for (int a = 0; a < 3; ++a) l[a] = h->cfg.box == PIC_BOX_EXPAND ? std::exp(h->cfg.expand_rate[a] * t) : 1.0;
+    const bool ex = h->cfg.box == PIC_BOX_EXPAND || h->cfg.box == PIC_BOX_SHEAR_EXPAND;
+    for (int a = 0; a < 3; ++a) l[a] = ex ? std::exp(h->cfg.expand_rate[a] * t) : 1.0;
 }
 
 template <class T, int G> static void fill_all_t(pic_handle* h, double t) {
@@ -331,8 +339,16 @@ template <class T, int G> static void fill_all_t(pic_handle* h, double t) {
 template <class T, int G> static void field_step_t(pic_handle* h) {
     const Grid& g = h->g;
     const double c = h->cfg.c;
-    if (h->cfg.box == PIC_BOX_SHEAR) {
+    if (h->cfg.box == PIC_BOX_SHEAR || h->cfg.box == PIC_BOX_SHEAR_EXPAND) {
         const size_t bytes = (size_t)3 * g.cstride * h->esz;
+        const bool sxe = h->cfg.box == PIC_BOX_SHEAR_EXPAND;
+        const dim3 sgrid = cell_grid(g.cstride, 1, 3);
+        if (sxe) {
+            // the shearing + expanding box sweeps X^ = ell L^{-1} X at t^n
+            scale3_kernel<T><<<sgrid, CELL_THREADS, 0, h->stream>>>((T*)h->E, g.cstride, h->ctx, 0);
+            scale3_kernel<T><<<sgrid, CELL_THREADS, 0, h->stream>>>((T*)h->B, g.cstride, h->ctx, 0);
+            h->prof.launches += 2;
+        }
         // guards of X^n at t^{n+1/2}, then save X^n
         fill_guards_t<T, G>(h, (T*)h->E, 1);
         fill_guards_t<T, G>(h, (T*)h->B, 1);
@@ -347,12 +363,19 @@ template <class T, int G> static void field_step_t(pic_handle* h) {
             T* Bo = (T*)(to_main ? h->B : h->Bc);
             ksb_sweep_kernel<T, G><<<cell_grid(g.nx, g.ny, g.nz), CELL_THREADS, 0, h->stream>>>(g, (const T*)h->Es, (const T*)h->Bs, (const T*)Ek,
                                                                             (const T*)Bk, (const T*)h->Jcur, Eo, Bo, c,
-                                                                            h->cfg.s_shear * h->cfg.Omega0, 0.5 * g.nx);
+                                                                            h->cfg.s_shear * h->cfg.Omega0, 0.5 * g.nx,
+                                                                            h->ctx);
             h->prof.launches++;
             fill_guards_t<T, G>(h, Eo, k == N ? 2 : 1);
             fill_guards_t<T, G>(h, Bo, k == N ? 2 : 1);
             Ek = Eo;
             Bk = Bo;
+        }
+        if (sxe) {
+            // back to X = L X^ / ell at t^{n+1} (guards included: the scaling is per component)
+            scale3_kernel<T><<<sgrid, CELL_THREADS, 0, h->stream>>>((T*)h->E, g.cstride, h->ctx, 1);
+            scale3_kernel<T><<<sgrid, CELL_THREADS, 0, h->stream>>>((T*)h->B, g.cstride, h->ctx, 1);
+            h->prof.launches += 2;
         }
         return;
     }
@@ -394,7 +417,7 @@ template <class T> static long long step_params(pic_handle* h, int b, StepP& P, 
     P.Omega0 = cf.Omega0;
     P.half_nx = 0.5 * g.nx;
     for (int a = 0; a < 3; ++a) {
-        P.Lam[a] = cf.box == PIC_BOX_EXPAND ? -0.5 * cf.expand_rate[a] : 0.0;
+        P.Lam[a] = (cf.box == PIC_BOX_EXPAND || cf.box == PIC_BOX_SHEAR_EXPAND) ? -0.5 * cf.expand_rate[a] : 0.0;
         P.keb_im[a] = 1.0 / (1.0 - P.Lam[a]);
         P.keb_Lt[a] = (1.0 + P.Lam[a]) / (1.0 - P.Lam[a]);
     }
@@ -517,10 +540,10 @@ template <class T, int G> static pic_status post_particle_t(pic_handle* h, const
         h->prof.launches++;
     }
     fold_current_t<T, G>(h, (T*)h->J);
-    if (cf.box == PIC_BOX_SHEAR && GeomT<G>::AY) {
+    if ((cf.box == PIC_BOX_SHEAR || cf.box == PIC_BOX_SHEAR_EXPAND) && GeomT<G>::AY) {
         // J'(x') -> J'(x): advect along y into the second buffer (h->Jcur)
         ksb_advect_kernel<T><<<cell_grid(g.nx, (g.ny + ADVECT_ROWS - 1) / ADVECT_ROWS, 3ll * g.nz), CELL_THREADS, 0,
-                               h->stream>>>(g, (const T*)h->J, (T*)h->Jtmp, cf.s_shear * cf.Omega0, 0.5 * g.nx);
+                               h->stream>>>(g, (const T*)h->J, (T*)h->Jtmp, cf.s_shear * cf.Omega0, 0.5 * g.nx, h->ctx);
         h->prof.launches++;
     }
     field_step_t<T, G>(h);
@@ -1177,7 +1200,7 @@ template <class T, int G> static pic_status diag_t(pic_handle* h, pic_diag* out)
 static pic_status validate(const pic_config* c) {
     pic_handle* h = nullptr;
     if (!c) return fail(h, PIC_ERR_ARG, "config is NULL");
-    if (c->box < 0 || c->box > 3) return fail(h, PIC_ERR_ARG, "box must be 0..3");
+    if (c->box < 0 || c->box > 4) return fail(h, PIC_ERR_ARG, "box must be 0..4");
     if (c->ndim != 2 && c->ndim != 3) return fail(h, PIC_ERR_ARG, "ndim must be 2 or 3");
     if (c->ndim == 2 && c->plane != PIC_PLANE_XY && c->plane != PIC_PLANE_XZ)
         return fail(h, PIC_ERR_ARG, "2D plane must be PIC_PLANE_XY or PIC_PLANE_XZ");
@@ -1193,7 +1216,7 @@ static pic_status validate(const pic_config* c) {
     if (c->precision != PIC_FP32 && c->precision != PIC_FP64) return fail(h, PIC_ERR_ARG, "precision must be FP32 or FP64");
     if (!(c->c > 0) || !(c->c * std::sqrt((double)c->ndim) < 1.0))
         return fail(h, PIC_ERR_ARG, "Courant number c must satisfy 0 < c sqrt(ndim) < 1");
-    if (c->box == PIC_BOX_SHEAR) {
+    if (c->box == PIC_BOX_SHEAR || c->box == PIC_BOX_SHEAR_EXPAND) {
         if (c->fp_iters < 1 || c->fp_iters > 64) return fail(h, PIC_ERR_ARG, "fp_iters must be in 1..64");
         double vmax = std::fabs(c->s_shear * c->Omega0) * 0.5 * c->nx;
         if (c->c + vmax >= 1.0) return fail(h, PIC_ERR_ARG, "c + max shear speed must stay below one cell per step");
@@ -1242,7 +1265,10 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
     h->geom = c.ndim == 3 ? 0 : (c.plane == PIC_PLANE_XY ? 1 : 2);
     h->fp64 = c.precision == PIC_FP64;
     h->esz = h->fp64 ? 8 : 4;
-    h->push = c.box == PIC_BOX_SHEAR ? PUSH_KSB : (c.box == PIC_BOX_EXPAND ? PUSH_KEB : PUSH_BORIS);
+    h->push = c.box == PIC_BOX_SHEAR           ? PUSH_KSB
+              : c.box == PIC_BOX_EXPAND        ? PUSH_KEB
+              : c.box == PIC_BOX_SHEAR_EXPAND ? PUSH_SXE
+                                               : PUSH_BORIS;
     h->esc = c.box == PIC_BOX_LEAKY ? (c.escape_mode == PIC_ESC_DISPLACEMENT ? ESC_DISP
                                        : c.escape_mode == PIC_ESC_PROBABILISTIC ? ESC_PROB
                                                                                  : ESC_NONE)
@@ -1314,10 +1340,10 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
         if (dalloc(h, p, fb) != cudaSuccess) return bail(fail(h, PIC_ERR_OOM, "field allocation failed"));
         cudaMemsetAsync(*p, 0, fb, h->stream);
     }
-    h->Jcur = (c.box == PIC_BOX_SHEAR && AY) ? h->Jtmp : h->J;
+    h->Jcur = ((c.box == PIC_BOX_SHEAR || c.box == PIC_BOX_SHEAR_EXPAND) && AY) ? h->Jtmp : h->J;
     if (dalloc(h, (void**)&h->ctx, sizeof(StepCtx)) != cudaSuccess) return bail(fail(h, PIC_ERR_OOM, "allocation failed"));
     cudaMemsetAsync(h->ctx, 0, sizeof(StepCtx), h->stream);
-    h->cc.box = c.box == PIC_BOX_SHEAR ? 1 : (c.box == PIC_BOX_EXPAND ? 2 : 0);
+    h->cc.box = c.box == PIC_BOX_SHEAR ? 1 : (c.box == PIC_BOX_EXPAND ? 2 : (c.box == PIC_BOX_SHEAR_EXPAND ? 4 : 0));
     h->cc.ny = c.ny;
     h->cc.sO_Lx = c.s_shear * c.Omega0 * (double)c.nx;
     for (int a = 0; a < 3; ++a) h->cc.rate[a] = c.expand_rate[a];
@@ -1328,7 +1354,7 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
             return bail(fail(h, PIC_ERR_OOM, "field allocation failed"));
         cudaMemsetAsync(h->Jint, 0, (size_t)3 * g.cstride * sizeof(int), h->stream);
     }
-    if (c.box == PIC_BOX_SHEAR) {
+    if (c.box == PIC_BOX_SHEAR || c.box == PIC_BOX_SHEAR_EXPAND) {
         void** kb[] = {&h->Es, &h->Bs, &h->Ec, &h->Bc};
         for (void** p : kb) {
             if (dalloc(h, p, fb) != cudaSuccess) return bail(fail(h, PIC_ERR_OOM, "field allocation failed"));
@@ -1746,8 +1772,8 @@ pic_status pic_preload_kernels(int32_t device, int32_t precision) {
     if (precision != PIC_FP32 && precision != PIC_FP64) return fail(nullptr, PIC_ERR_ARG, "bad precision");
     if (cudaSetDevice(device) != cudaSuccess) return fail(nullptr, PIC_ERR_CUDA, "no such CUDA device");
     const bool fp64 = precision == PIC_FP64;
-    const int pushes[5][2] = {{PUSH_BORIS, ESC_NONE}, {PUSH_BORIS, ESC_DISP}, {PUSH_BORIS, ESC_PROB},
-                              {PUSH_KSB, ESC_NONE}, {PUSH_KEB, ESC_NONE}};
+    const int pushes[6][2] = {{PUSH_BORIS, ESC_NONE}, {PUSH_BORIS, ESC_DISP}, {PUSH_BORIS, ESC_PROB},
+                              {PUSH_KSB, ESC_NONE}, {PUSH_KEB, ESC_NONE}, {PUSH_SXE, ESC_NONE}};
     cudaFuncAttributes a;
     for (int geom = 0; geom < 3; ++geom)
         for (int ord = 1; ord <= 2; ++ord)

@@ -96,7 +96,7 @@ extern "C" pic_status pic_run_footprint(const pic_run_spec* s, uint64_t* bytes) 
     const uint64_t px = ((uint64_t)c.nx + 5 + a - 1) / a * a, py = ay ? c.ny + 5 : 1, pz = az ? c.nz + 5 : 1;
     const uint64_t cells = (uint64_t)c.nx * c.ny * c.nz, padded = px * py * pz;
     uint64_t fields = 4;  // E, B, J, J scratch
-    if (c.box == PIC_BOX_SHEAR) fields += 4;
+    if (c.box == PIC_BOX_SHEAR || c.box == PIC_BOX_SHEAR_EXPAND) fields += 4;
     uint64_t total = fields * 3 * padded * es + (fp64 ? 0 : 3 * padded * 4) + 3 * cells * 8;
     int tx, ty, tz;
     tile_shape(c, tx, ty, tz);

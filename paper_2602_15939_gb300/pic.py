@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpic.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "pic.h")
 
 PIC_OK, PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_CUDA, PIC_ERR_TIMEOUT, PIC_ERR_STATE, PIC_ERR_NUMERIC = range(7)
-PIC_BOX_PERIODIC, PIC_BOX_SHEAR, PIC_BOX_EXPAND, PIC_BOX_LEAKY = range(4)
+PIC_BOX_PERIODIC, PIC_BOX_SHEAR, PIC_BOX_EXPAND, PIC_BOX_LEAKY, PIC_BOX_SHEAR_EXPAND = range(5)
 PIC_PLANE_XY, PIC_PLANE_XZ = 0, 1
 PIC_FP32, PIC_FP64 = 0, 1
 PIC_KEB_CLOSED_FORM, PIC_KEB_EXACT = 0, 1

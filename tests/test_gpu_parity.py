@@ -18,6 +18,7 @@ from gpu_harness import Case, compare
 from paper_2602_15939_gb300 import pic as P
 
 BOX_P, BOX_S, BOX_E, BOX_L = P.PIC_BOX_PERIODIC, P.PIC_BOX_SHEAR, P.PIC_BOX_EXPAND, P.PIC_BOX_LEAKY
+BOX_SE = P.PIC_BOX_SHEAR_EXPAND
 XY, XZ = P.PIC_PLANE_XY, P.PIC_PLANE_XZ
 
 CASES = [
@@ -42,6 +43,12 @@ CASES = [
     Case("shear3d_o2_ion25", BOX_S, (16, 12, 8), order=2, s=1.5, Omega0=3e-3, step0=7, masses=(1.0, 25.0)),
     Case("leaky2d_prob_o1_ion25", BOX_L, (32, 24, 1), ndim=2, plane=XY, order=1, ppc=6, esc_mode=2, p_esc=0.05,
          theta_inj=0.5, masses=(1.0, 25.0)),
+    # shearing box that also expands (the combination of Sec. 5): fractional shear shifts at these steps
+    Case("shearexp3d_o2", BOX_SE, (16, 12, 8), order=2, s=1.5, Omega0=3e-3, rate=(1e-3, 2e-3, 5e-4), step0=37),
+    Case("shearexp3d_o1", BOX_SE, (16, 16, 8), order=1, s=1.2, Omega0=2e-3, rate=(0.0, 1e-3, 1e-3), step0=101,
+         fp_iters=3),
+    Case("shearexp2dxy_o2", BOX_SE, (32, 24, 1), ndim=2, plane=XY, order=2, ppc=6, s=1.5, Omega0=4e-3,
+         rate=(2e-3, 1e-3, 0.0), step0=11),
 ]
 
 IDS = [c.name for c in CASES]

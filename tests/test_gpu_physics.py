@@ -197,6 +197,10 @@ def test_leaky_box_relaxes_to_a_steady_state():
     steps, _, esc = leaky[-1]
     mean = npart * p * steps
     assert abs(esc - mean) <= 5 * math.sqrt(mean * (1 - p))
-    assert abs(leaky[-1][1] - e_inj) <= 0.03 * e_inj  # the steady state: (1 - p)^300 ~ 2e-3
+    # the steady state: after 300 steps only (1 - p)^300 (e(0) - e_inj) ~ 0.03 e_inj of
+    # the initial excess is left, and the energy sits within 2% of that remainder
+    tail = (e0 - e_inj) * (1 - p) ** steps
+    assert tail < 0.04 * e_inj
+    assert abs(leaky[-1][1] - (e_inj + tail)) <= 0.02 * e_inj
     for _, ke, esc in closed:
         assert esc == 0 and ke == pytest.approx(e0, rel=0.01)
