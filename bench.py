@@ -354,6 +354,11 @@ def measure(w, args, device, stream, rank, world, headline):
                 "particle_ms_per_variant": [None if v is None else round(v, 4) for v in ms_v]}
     nt_, st_, jc_ = P.pic_kernel_variant_info(tune["chosen"])
     tune.update({"threads_per_cta": nt_, "stable_order": bool(st_), "current_copies": jc_})
+    if not args.variant and not w.fp64 and w.ndim == 3:
+        cands = (2, 3, 4, 6)
+        best_r, ms_r = box.autotune_regroup(cands, 2)
+        tune["regroup"] = {"chosen": best_r, "candidates": list(cands), "ms_per_step": [round(v, 3) for v in ms_r],
+                           "how": "autotuned on whole regroup cycles of untimed steps"}
     box.sync()
     torch.cuda.synchronize()
 

@@ -367,6 +367,20 @@ pic_status pic_set_kernel_variant(pic_handle *h, int32_t k);
 pic_status pic_autotune(pic_handle *h, int32_t trial_steps, int32_t *best, double *ms_per_variant,
                         int64_t *steps_taken);
 
+/* Regroup-interval autotuner (FP32 boxes; FP64 boxes keep 0): for each of
+ * the n candidate intervals (0 = never), run one untimed cycle and then
+ * `cycles` whole cycles of ordinary steps (interval x cycles steps; pairs of
+ * steps for 0), time every kernel of those steps with CUDA events, and keep
+ * the interval with the least device time per step.  The particles' order
+ * decays at a rate set by their speeds, so the best interval depends on the
+ * box.  The trial steps advance the simulation like pic_step (FP32 results do
+ * not depend on the interval).  Outputs (nullable): *best and
+ * ms_per_step[n].  Synchronizes the handle's stream; drops its captured step
+ * graphs.  PIC_ERR_ARG for an FP64 box, n < 1, cycles < 1 or a negative
+ * candidate.  No counterpart in the paper. */
+pic_status pic_autotune_regroup(pic_handle *h, const int32_t *candidates, int32_t n, int32_t cycles, int32_t *best,
+                                double *ms_per_step);
+
 /* ---- batches: many boxes of one kind stepped together --------------------------
  * (no counterpart in the paper; the ensembles of independent boxes the method
  * is run on).  A batch steps n boxes together: each step launches one

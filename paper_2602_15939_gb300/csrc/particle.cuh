@@ -236,6 +236,11 @@ template <int G> struct SmemJ<float, G> {
         const int iv = __float_as_int(fmaf(a, b, 12582912.0f)) - 0x4B400000;
         red_shared(j + 4u * (uint32_t)(comp * SC + idx), iv);
     }
+    // word: component offset comp * SC already added
+    __device__ void add_w(int word, float a, float b) const {
+        const int iv = __float_as_int(fmaf(a, b, 12582912.0f)) - 0x4B400000;
+        red_shared(j + 4u * (uint32_t)word, iv);
+    }
 };
 
 template <int G> struct SmemJ<double, G> {
@@ -891,6 +896,144 @@ template <class T, int G, int ORD> __device__ inline bool crosses(const T o[3], 
     return c;
 }
 
+// Bit a set: the move o -> o + d crosses a boundary on axis a (see deposit_core).
+template <class T, int G, int ORD> __device__ inline int cross_mask(const T o[3], const T d[3]) {
+    using GT = GeomT<G>;
+    int m = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if ((a == 1 && !GT::AY) || (a == 2 && !GT::AZ)) continue;
+        const T x1 = o[a] + d[a];
+        bool c;
+        if (ORD == 1) c = t_floor<T>(x1) != T(0);
+        else c = t_floor<T>(x1 + T(0.5)) != (o[a] >= T(0.5) ? T(1) : T(0));
+        m |= c ? (1 << a) : 0;
+    }
+    return m;
+}
+
+// 3D deposit of a particle that crosses on axis a only (it keeps its nearest
+// node, order 2, or its cell, order 1, on the other two).  Its current lives
+// on the ORD+2 window nodes along a and the ORD+1 core nodes along the other
+// axes: (ORD+1)^3 + 2 ORD (ORD+2)(ORD+1) adds (order 2: 27 + 24 + 24 = 75,
+// against the full window's 144, whose other adds are exact zeros for such a
+// particle).  The axes are taken in the cyclic order (a, a+1, a+2), with the
+// strides and component offsets picked per lane.  Same Esirkepov weights as
+// deposit(): F_bc = S0_b A_c + dS_b Q_c, symmetric in b and c.
+template <class T, int ORD, class JA>
+__device__ inline void deposit_1axis(const JA& ja, int cidx, const T o[3], const T d[3], T qs, int a) {
+    constexpr int NW = ORD + 2, NC = ORD + 1;
+    const int b = a == 2 ? 0 : a + 1, c = a == 0 ? 2 : a - 1;
+    auto pick3 = [](const T* v, int i) -> T { return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]); };
+    auto stride = [](int i) -> int { return i == 0 ? 1 : (i == 1 ? JA::SY : JA::SZ); };
+    const T oa = pick3(o, a), ob = pick3(o, b), oc = pick3(o, c);
+    const T xa1 = oa + pick3(d, a), xb1 = ob + pick3(d, b), xc1 = oc + pick3(d, c);
+    const int sa = stride(a), sb = stride(b), sc = stride(c);
+    // axis a: the window of the full deposit
+    const int wba = window_base<T, ORD>(oa, xa1);
+    T S0a[4], S1a[4], DSa[4], CSa[NW - 1];
+    Shape<T, ORD>::window(oa, wba, S0a);
+    Shape<T, ORD>::window(xa1, wba, S1a);
+    {
+        T run = T(0);
+#pragma unroll
+        for (int m = 0; m < NW; ++m) {
+            DSa[m] = S1a[m] - S0a[m];
+            run += DSa[m];
+            if (m < NW - 1) CSa[m] = -qs * run;
+        }
+    }
+    // axes b and c: the core windows
+    const int wbb = ORD == 1 ? 0 : (ob >= T(0.5) ? 0 : -1);
+    const int wbc = ORD == 1 ? 0 : (oc >= T(0.5) ? 0 : -1);
+    T S0b[NC], DSb[NC], CSb[NC - 1], S0c[NC], DSc[NC], CSc[NC - 1];
+    {
+        T w0[4], w1[4];
+        Shape<T, ORD>::window(ob, wbb, w0);
+        Shape<T, ORD>::window(xb1, wbb, w1);
+        T run = T(0);
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            S0b[m] = w0[m];
+            DSb[m] = w1[m] - w0[m];
+            run += DSb[m];
+            if (m < NC - 1) CSb[m] = -qs * run;
+        }
+        Shape<T, ORD>::window(oc, wbc, w0);
+        Shape<T, ORD>::window(xc1, wbc, w1);
+        run = T(0);
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            S0c[m] = w0[m];
+            DSc[m] = w1[m] - w0[m];
+            run += DSc[m];
+            if (m < NC - 1) CSc[m] = -qs * run;
+        }
+    }
+    const T third = T(1) / T(3);
+    T Aa[NW], Qa[NW], Ab[NC], Qb[NC], Ac[NC], Qc[NC];
+#pragma unroll
+    for (int m = 0; m < NW; ++m) {
+        Aa[m] = S0a[m] + T(0.5) * DSa[m];
+        Qa[m] = T(0.5) * S0a[m] + third * DSa[m];
+    }
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+        Ab[m] = S0b[m] + T(0.5) * DSb[m];
+        Qb[m] = T(0.5) * S0b[m] + third * DSb[m];
+        Ac[m] = S0c[m] + T(0.5) * DSc[m];
+        Qc[m] = T(0.5) * S0c[m] + third * DSc[m];
+    }
+    const int base = cidx + wba * sa + wbb * sb + wbc * sc;
+    const int wa = base + a * JA::SC, wb = base + b * JA::SC, wc = base + c * JA::SC;
+    // The outermost loop of each component stays rolled (instruction cache, as
+    // in deposit()); the values it indexes are picked by selects.
+    // (windows of NC = ORD+1 nodes on b and c, NW = ORD+2 on a)
+    auto pickc = [](const T* v, int i) -> T { return NC == 2 ? (i == 0 ? v[0] : v[NC - 1]) : (i == 0 ? v[0] : (i == 1 ? v[1] : v[NC - 1])); };
+    auto pickw = [](const T* v, int i) -> T {
+        return NW == 3 ? (i == 0 ? v[0] : (i == 1 ? v[1] : v[NW - 1])) : (i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[NW - 1])));
+    };
+    // J_a: running sums along a times F_bc
+#pragma unroll 1
+    for (int m = 0; m < NC; ++m) {
+        const T s0 = pickc(S0b, m), ds = pickc(DSb, m);
+        const int mo = wa + m * sb;
+#pragma unroll
+        for (int n = 0; n < NC; ++n) {
+            const T f = s0 * Ac[n] + ds * Qc[n];
+            const int off = mo + n * sc;
+#pragma unroll
+            for (int l = 0; l < NW - 1; ++l) ja.add_w(off + l * sa, CSa[l], f);
+        }
+    }
+    // J_b: running sums along b times F_ac
+#pragma unroll 1
+    for (int l = 0; l < NW; ++l) {
+        const T s0 = pickw(S0a, l), ds = pickw(DSa, l);
+        const int lo = wb + l * sa;
+#pragma unroll
+        for (int n = 0; n < NC; ++n) {
+            const T f = s0 * Ac[n] + ds * Qc[n];
+            const int off = lo + n * sc;
+#pragma unroll
+            for (int m = 0; m < NC - 1; ++m) ja.add_w(off + m * sb, CSb[m], f);
+        }
+    }
+    // J_c: running sums along c times F_ab
+#pragma unroll 1
+    for (int l = 0; l < NW; ++l) {
+        const T s0 = pickw(S0a, l), ds = pickw(DSa, l);
+        const int lo = wc + l * sa;
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            const T f = s0 * Ab[m] + ds * Qb[m];
+            const int off = lo + m * sb;
+#pragma unroll
+            for (int n = 0; n < NC - 1; ++n) ja.add_w(off + n * sc, CSc[n], f);
+        }
+    }
+}
+
 // ---- one particle ---------------------------------------------------------------------
 
 template <class T> struct Particle {
@@ -1201,16 +1344,25 @@ __device__ __forceinline__ SmemJ<T, G> pick_copy(JWord<T>* sJ, int lane, bool de
     }
 }
 
+// 3D FP32 tiles queue crossing particles in two queues per warp: those that
+// cross on one axis (deposit_1axis) and the rest (the full window).
+template <class T, int G> __host__ __device__ constexpr bool split_queue() { return sizeof(T) == 4 && G == G3D; }
+
 template <class T, int G, int NT, int STABLE, int JC> struct SmemLayout {
     static constexpr int FB = TileDims<G>::FB, JB = TileDims<G>::JB;
     static constexpr int QCAP = 64;  // entries of a warp's crossing-particle queue
+    static constexpr int NQ = split_queue<T, G>() ? 2 : 1;  // queues per warp
     // copy stride in words: a multiple of 32 plus 32/JC (copy k is 32k/JC banks over)
     static constexpr int JCS = JC == 1 ? 3 * JB : ((3 * JB + 31) / 32) * 32 + 32 / JC;
     static constexpr size_t off_B = ((size_t)3 * FB * sizeof(T) + 127) & ~(size_t)127;
     static constexpr size_t off_J = (off_B + (size_t)3 * FB * sizeof(T) + 127) & ~(size_t)127;
+    // queue k of warp w: offsets/moves at off_q + k QBYTES_OD + w QCAP 6 sizeof(T),
+    // cells at off_qc + k QBYTES_C + w QCAP 4
+    static constexpr size_t QBYTES_OD = (size_t)(NT / 32) * QCAP * 6 * sizeof(T);
+    static constexpr size_t QBYTES_C = (size_t)(NT / 32) * QCAP * 4;
     static constexpr size_t off_q = (off_J + (size_t)JC * JCS * sizeof(T) + 15) & ~(size_t)15;
-    static constexpr size_t off_qc = off_q + (size_t)(NT / 32) * QCAP * 6 * sizeof(T);
-    static constexpr size_t off_bar = (off_qc + (size_t)(NT / 32) * QCAP * 4 + 15) & ~(size_t)15;
+    static constexpr size_t off_qc = off_q + NQ * QBYTES_OD;
+    static constexpr size_t off_bar = (off_qc + NQ * QBYTES_C + 15) & ~(size_t)15;
     static constexpr size_t off_wc = off_bar + 16 + 4 * (MAXSP + 2);
     static constexpr size_t bytes = off_wc + (STABLE ? 2 * (NT / 32) * 4 : 0);
 };
@@ -1286,6 +1438,12 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* tmE, const CUtensor
     T* q_od = reinterpret_cast<T*>(smem + L::off_q) + (size_t)warp * 6 * L::QCAP;  // this warp's queue:
     int* q_cell = reinterpret_cast<int*>(smem + L::off_qc) + warp * L::QCAP;        // start offsets, moves, cells
     int qn = 0;                                                                     // entries (warp-uniform)
+    // 3D FP32: a second queue for particles that cross on one axis only (the
+    // axis rides in the cell word's top bits), deposited by deposit_1axis
+    constexpr bool SPLIT = split_queue<T, G>();
+    T* q1_od = reinterpret_cast<T*>(smem + L::off_q + (SPLIT ? L::QBYTES_OD : 0)) + (size_t)warp * 6 * L::QCAP;
+    int* q1_cell = reinterpret_cast<int*>(smem + L::off_qc + (SPLIT ? L::QBYTES_C : 0)) + warp * L::QCAP;
+    int qn1 = 0;
     int* s_wc = reinterpret_cast<int*>(smem + L::off_wc);  // [2][NW] stayer counts (stable variants)
     int wcb = 0;                                            // their buffer for the current chunk
 
@@ -1316,12 +1474,34 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* tmE, const CUtensor
             const JA jq = pick_copy<T, G, JC, L::JCS>(sJ, lane, have, wbase);
             if (have) deposit<T, G, ORD>(jq, ce, oe, de, qs);
         };
+        // the same for the single-axis queue
+        auto queued_deposit1 = [&](int e, bool have) {
+            T oe[3] = {T(0), T(0), T(0)}, de[3] = {T(0), T(0), T(0)};
+            int cw = 0;
+            if (have) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    oe[a] = q1_od[a * L::QCAP + e];
+                    de[a] = q1_od[(3 + a) * L::QCAP + e];
+                }
+                cw = q1_cell[e];
+            }
+            const int ce = cw & 0x0FFFFFFF, ax = (int)((unsigned)cw >> 28);
+            int wbase = ce + window_base<T, ORD>(oe[0], oe[0] + de[0]);
+            if (GT::AY) wbase += window_base<T, ORD>(oe[1], oe[1] + de[1]) * JA::SY;
+            if (GT::AZ) wbase += window_base<T, ORD>(oe[2], oe[2] + de[2]) * JA::SZ;
+            const JA jq = pick_copy<T, G, JC, L::JCS>(sJ, lane, have, wbase);
+            if constexpr (SPLIT) {
+                if (have) deposit_1axis<T, ORD>(jq, ce, oe, de, qs, ax);
+            }
+        };
         for (int i0 = 0; i0 < n; i0 += NT) {
             const int i = i0 + tid;
             const bool valid = i < n;
             Particle<T> p;
             int dest = -1;
-            bool cross = false;
+            bool cross = false, cross1 = false;  // crosses on some axis / on exactly one
+            int cax = 0;                        // that one axis
             int jidx = 0;
             T o0[3], d[3];
             int cbase = 0;  // base word of the core deposit
@@ -1331,7 +1511,14 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* tmE, const CUtensor
                 const int fidx = (p.ci - fox) + (GT::AY ? (p.cj - foy) * FA::SY : 0) + (GT::AZ ? (p.ck - foz) * FA::SZ : 0);
                 jidx = (p.ci - jox) + (GT::AY ? (p.cj - joy) * JA::SY : 0) + (GT::AZ ? (p.ck - joz) * JA::SZ : 0);
                 push_particle<T, G, ORD, PUSH>(p, fa, fidx, S, P, d);
-                cross = crosses<T, G, ORD>(p.o, d);
+                if constexpr (SPLIT) {
+                    const int cm = cross_mask<T, G, ORD>(p.o, d);
+                    cross = cm != 0;
+                    cross1 = cm == 1 || cm == 2 || cm == 4;
+                    cax = cm == 1 ? 0 : (cm == 2 ? 1 : 2);
+                } else {
+                    cross = crosses<T, G, ORD>(p.o, d);
+                }
                 cbase = core_base<T, G, ORD>(jidx, p.o, JA::SY, JA::SZ);
             }
             const JA ja = pick_copy<T, G, JC, L::JCS>(sJ, lane, valid && !cross, cbase);
@@ -1343,8 +1530,22 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* tmE, const CUtensor
             }
             // crossing particles join the warp's queue; their full deposit is
             // made 32 at a time, every lane adding real contributions
-            const unsigned qm = __ballot_sync(0xffffffffu, cross);
-            if (cross) {
+            const bool crossf = cross && !cross1;  // to the full-window queue
+            const unsigned qm = __ballot_sync(0xffffffffu, crossf);
+            if constexpr (SPLIT) {
+                const unsigned q1m = __ballot_sync(0xffffffffu, cross1);
+                if (cross1) {
+                    const int pos = qn1 + __popc(q1m & ((1u << lane) - 1u));
+                    q1_cell[pos] = jidx | (cax << 28);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        q1_od[a * L::QCAP + pos] = o0[a];
+                        q1_od[(3 + a) * L::QCAP + pos] = d[a];
+                    }
+                }
+                qn1 += __popc(q1m);
+            }
+            if (crossf) {
                 const int pos = qn + __popc(qm & ((1u << lane) - 1u));
                 q_cell[pos] = jidx;
 #pragma unroll
@@ -1378,6 +1579,26 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* tmE, const CUtensor
             }
             if (stay) store_particle<T, G>(S.out, base + wb + __popc(m & ((1u << lane) - 1u)), LEAKY, p);
             else if (valid) place_mover<T, G>(p, dest, S, P, LEAKY);
+            if (SPLIT && qn1 >= 32) {
+                __syncwarp();
+                queued_deposit1(lane, true);
+                const int rest = qn1 - 32;
+                int c = 0;
+                T od[6];
+                if (lane < rest) {
+                    c = q1_cell[32 + lane];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) od[k] = q1_od[k * L::QCAP + 32 + lane];
+                }
+                __syncwarp();
+                if (lane < rest) {
+                    q1_cell[lane] = c;
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) q1_od[k * L::QCAP + lane] = od[k];
+                }
+                __syncwarp();
+                qn1 = rest;
+            }
             if (qn >= 32) {
                 __syncwarp();
                 queued_deposit(lane, true);
@@ -1403,6 +1624,11 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* tmE, const CUtensor
         // the species' remaining queue (charge qs)
         __syncwarp();
         if (qn > 0) queued_deposit(lane, lane < qn);  // qn is warp-uniform
+        if (SPLIT && qn1 > 0) {
+            __syncwarp();
+            queued_deposit1(lane, lane < qn1);
+        }
+        qn1 = 0;
         __syncwarp();
         qn = 0;
         if (STABLE && tid == 0) s_cnt[s] = run;

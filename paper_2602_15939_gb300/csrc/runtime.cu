@@ -1822,6 +1822,56 @@ pic_status pic_set_kernel_variant(pic_handle* h, int32_t k) {
     return PIC_OK;
 }
 
+pic_status pic_autotune_regroup(pic_handle* h, const int32_t* candidates, int32_t n, int32_t cycles, int32_t* best,
+                                double* ms_per_step) {
+    if (!h || !candidates || n < 1 || cycles < 1) return fail(h, PIC_ERR_ARG, "bad arguments");
+    if (h->fp64) return fail(h, PIC_ERR_ARG, "FP64 boxes keep regrouping off");
+    for (int i = 0; i < n; ++i)
+        if (candidates[i] < 0) return fail(h, PIC_ERR_ARG, "intervals must be >= 0");
+    cudaSetDevice(h->cfg.device);
+    const bool prof_was = h->prof.on;
+    const int start = h->regroup_every;
+    prof_resolve(h);
+    const double ms0[3] = {h->prof.ms[0], h->prof.ms[1], h->prof.ms[2]};
+    const long long l0 = h->prof.launches, pl0 = h->prof.particle_launches, ps0 = h->prof.particle_steps;
+    pic_status st = PIC_OK;
+    int bi = -1;
+    double bms = 0.0;
+    for (int i = 0; i < n && st == PIC_OK; ++i) {
+        st = pic_set_regroup_interval(h, candidates[i]);
+        if (st != PIC_OK) break;
+        const int cyc = candidates[i] > 0 ? candidates[i] : 2;
+        h->prof.on = false;
+        st = pic_step(h, cyc);  // one untimed cycle: the order settles into this interval's rhythm
+        if (st != PIC_OK) break;
+        prof_resolve(h);
+        const double before = h->prof.ms[0] + h->prof.ms[1] + h->prof.ms[2];
+        h->prof.on = true;
+        st = pic_step(h, cyc * cycles);
+        prof_resolve(h);
+        const double per = (h->prof.ms[0] + h->prof.ms[1] + h->prof.ms[2] - before) / (cyc * cycles);
+        if (ms_per_step) ms_per_step[i] = per;
+        if (bi < 0 || per < bms) {
+            bi = i;
+            bms = per;
+        }
+    }
+    h->prof.ms[0] = ms0[0];
+    h->prof.ms[1] = ms0[1];
+    h->prof.ms[2] = ms0[2];
+    h->prof.launches = l0;
+    h->prof.particle_launches = pl0;
+    h->prof.particle_steps = ps0;
+    h->prof.on = prof_was;
+    if (st != PIC_OK || bi < 0) {
+        pic_set_regroup_interval(h, start);
+        return st != PIC_OK ? st : fail(h, PIC_ERR_STATE, "no interval was timed");
+    }
+    st = pic_set_regroup_interval(h, candidates[bi]);
+    if (st == PIC_OK && best) *best = candidates[bi];
+    return st;
+}
+
 pic_status pic_autotune(pic_handle* h, int32_t trial_steps, int32_t* best, double* ms_per_variant,
                         int64_t* steps_taken) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");

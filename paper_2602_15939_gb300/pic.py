@@ -125,6 +125,8 @@ _SIGS = {
     "pic_get_kernel_variant": (C.c_int, [_H, C.POINTER(C.c_int32)]),
     "pic_set_kernel_variant": (C.c_int, [_H, C.c_int32]),
     "pic_take_result": (C.c_int, [_H, C.c_uint64, C.POINTER(_H)]),
+    "pic_autotune_regroup": (C.c_int, [_H, C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_double)]),
     "pic_batch_create": (C.c_int, [C.POINTER(_H), C.c_int32, C.POINTER(_H)]),
     "pic_batch_step": (C.c_int, [_H, C.c_int32]),
     "pic_batch_set_regroup_interval": (C.c_int, [_H, C.c_int32]),
@@ -370,6 +372,17 @@ def pic_autotune(h, trial_steps: int = 4):
     return best.value, [v if v >= 0 else None for v in ms], taken.value
 
 
+def pic_autotune_regroup(h, candidates=(2, 3, 4, 6), cycles: int = 2):
+    """Time whole regroup cycles for each candidate interval and keep the
+    fastest: returns (best interval, ms per step per candidate)."""
+    n = len(candidates)
+    arr = (C.c_int32 * n)(*candidates)
+    ms = (C.c_double * n)()
+    best = C.c_int32()
+    _check(h, lib().pic_autotune_regroup(h, arr, n, cycles, C.byref(best), ms))
+    return best.value, list(ms)
+
+
 class Batch:
     """Boxes of one kind stepped together (pic_batch_*): one persistent
     particle kernel per step over all their tiles, graph-replayed."""
@@ -489,6 +502,10 @@ class Box:
     def autotune(self, trial_steps=4):
         """Pick the fastest particle-kernel variant on live steps; see pic_autotune."""
         return pic_autotune(self.h, trial_steps)
+
+    def autotune_regroup(self, candidates=(2, 3, 4, 6), cycles=2):
+        """Pick the fastest regroup interval on live steps; see pic_autotune_regroup."""
+        return pic_autotune_regroup(self.h, candidates, cycles)
 
     def step(self, n=1):
         pic_step(self.h, n)
