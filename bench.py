@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--kernel-only", action="store_true", help="warmup + timed steps only (for profiler runs)")
     ap.add_argument("--batch-legs-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--seed", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--tile", type=int, default=0,
+                    help="2D FP32 particle tile side (16 or 32); 0 = autotune with the variant")
     ap.add_argument("--variant", type=int, default=0,
                     help="particle-kernel variant (1-based); 0 = autotune on the box after warm-up")
     return ap.parse_args()
@@ -128,16 +130,18 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def stored_traffic(workload, variant):
-    """DRAM bytes per launch of the particle kernel (launch variant `variant`)
-    at the workload's full size, from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+def stored_traffic(workload, variant, tile=None):
+    """DRAM bytes per launch of the particle kernel (launch variant `variant`,
+    and for 2D boxes the tile side) at the workload's full size, from the
+    committed ncu summary, if it was taken on the current kernel source; else
+    None."""
     p = os.path.join(ROOT, "profiles", f"tile_kernel_{workload}.md")
     if not os.path.exists(p):
         return None
     txt = open(p).read()
+    key = f"v{variant}" + (f",t{tile}" if tile else "")
     m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
-    m_b = re.search(r"dram_bytes_per_launch_full_size\[v%d\]:\s*([0-9.eE+]+)" % variant, txt)
+    m_b = re.search(r"dram_bytes_per_launch_full_size\[%s\]:\s*([0-9.eE+]+)" % re.escape(key), txt)
     if not m_hash or not m_b or m_hash.group(1) != kernel_source_hash():
         return None
     return float(m_b.group(1))
@@ -344,10 +348,17 @@ def measure(w, args, device, stream, rank, world, headline):
 
     box = setup_box(w, device, stream.cuda_stream, seed=replica_seed(rank))
     npart = w.n_particles
+    if args.tile and w.ndim == 2:
+        box.set_tile(args.tile)
     box.step(args.warmup)
     if args.variant:
         P.pic_set_kernel_variant(box.h, args.variant)
         tune = {"chosen": args.variant, "how": "forced"}
+    elif w.ndim == 2 and not w.fp64 and not args.tile:
+        side, ms_side = box.autotune_tile(4 if headline or w.n_particles > 1e8 else 2)
+        tune = {"chosen": P.pic_get_kernel_variant(box.h),
+                "how": "tile shape, then launch variant per shape, autotuned on untimed steps",
+                "tile_ms_per_step": {"16": round(ms_side[0], 4), "32": round(ms_side[1], 4)}}
     else:
         best, ms_v, taken = box.autotune(4 if headline or w.n_particles > 1e8 else 2)
         tune = {"chosen": best, "how": f"autotuned on {taken} untimed steps",
@@ -399,7 +410,9 @@ def measure(w, args, device, stream, rank, world, headline):
     bm = bytes_model(w, regroup)
     peak, peak_kind = measured_peaks()
     achieved = bm["kernel_bytes_per_launch"] / (particle_ms / 1e3) / 1e9
-    traffic = stored_traffic(w.name, tune["chosen"])
+    tile = box.tile()
+    tune["tile"] = list(tile)
+    traffic = stored_traffic(w.name, tune["chosen"], tile[0] if w.ndim == 2 else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)",
                 "kernel": "tile_kernel (fused gather+push+deposit+tile sort)",

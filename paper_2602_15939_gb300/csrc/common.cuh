@@ -16,8 +16,14 @@ namespace pic {
 constexpr int GL = 2;  // low guard cells
 constexpr int GR = 3;  // high guard cells (deposits reach node n+2)
 
-// geometry kinds: which axes are active
-enum Geom : int { G3D = 0, G2XY = 1, G2XZ = 2 };
+// geometry kinds: which axes are active.  G2XY_W and G2XZ_W are the 2D
+// planes again, with 32 x 32-cell particle tiles instead of 16 x 16 (a
+// template geometry: the grid and field code is that of the plane).
+enum Geom : int { G3D = 0, G2XY = 1, G2XZ = 2, G2XY_W = 3, G2XZ_W = 4 };
+constexpr int N_TGEOM = 5;
+__host__ __device__ constexpr int plane_of(int G) { return G == G2XY_W ? G2XY : (G == G2XZ_W ? G2XZ : G); }
+// particle tile side in cells (per active axis) of a template geometry
+__host__ __device__ constexpr int tile_side(int G) { return G == G3D ? 8 : ((G == G2XY_W || G == G2XZ_W) ? 32 : 16); }
 // particle pusher kinds
 enum Push : int { PUSH_BORIS = 0, PUSH_KSB = 1, PUSH_KEB = 2, PUSH_SXE = 3 /* shearing + expanding */ };
 // escape kinds (leaky box)
@@ -35,10 +41,11 @@ enum : int {
 };
 
 template <int G> struct GeomT {
+    static constexpr int P = plane_of(G);
     static constexpr bool AX = true;
-    static constexpr bool AY = (G != G2XZ);
-    static constexpr bool AZ = (G != G2XY);
-    static constexpr int IGN = (G == G2XY) ? 2 : ((G == G2XZ) ? 1 : -1);  // ignorable axis
+    static constexpr bool AY = (P != G2XZ);
+    static constexpr bool AZ = (P != G2XY);
+    static constexpr int IGN = (P == G2XY) ? 2 : ((P == G2XZ) ? 1 : -1);  // ignorable axis
 };
 
 // Padded grid geometry (element offsets).  cell (i,j,k) -> index
@@ -91,8 +98,15 @@ struct CtxConst {
     double c;
 };
 
+__device__ inline void ctx_update(StepCtx* ctx, const CtxConst& k);
+
 __global__ inline void ctx_kernel(StepCtx* ctx, CtxConst k) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    ctx_update(ctx, k);
+}
+
+// Fill the context of the step that starts now (one thread).
+__device__ inline void ctx_update(StepCtx* ctx, const CtxConst& k) {
     const long long n = ctx->next_step;
     ctx->step = n;
     ctx->next_step = n + 1;
@@ -164,15 +178,16 @@ __global__ inline void ctx_kernel(StepCtx* ctx, CtxConst k) {
 // 3D: i in bits 0..10, j in 11..21, k in 22..31 (nx, ny <= 2048, nz <= 1024).
 // 2D: first active axis in bits 0..15, second in 16..31 (<= 65536 cells each).
 template <int G> struct CellPack {
+    static constexpr int P = plane_of(G);
     __host__ __device__ static int pack(int i, int j, int k) {
-        if (G == G3D) return (int)((unsigned)i | ((unsigned)j << 11) | ((unsigned)k << 22));
-        if (G == G2XY) return (int)((unsigned)i | ((unsigned)j << 16));
+        if (P == G3D) return (int)((unsigned)i | ((unsigned)j << 11) | ((unsigned)k << 22));
+        if (P == G2XY) return (int)((unsigned)i | ((unsigned)j << 16));
         return (int)((unsigned)i | ((unsigned)k << 16));
     }
     __host__ __device__ static void unpack(int c, int& i, int& j, int& k) {
         unsigned u = (unsigned)c;
-        if (G == G3D) { i = u & 2047u; j = (u >> 11) & 2047u; k = u >> 22; }
-        else if (G == G2XY) { i = u & 65535u; j = u >> 16; k = 0; }
+        if (P == G3D) { i = u & 2047u; j = (u >> 11) & 2047u; k = u >> 22; }
+        else if (P == G2XY) { i = u & 65535u; j = u >> 16; k = 0; }
         else { i = u & 65535u; k = u >> 16; j = 0; }
     }
 };

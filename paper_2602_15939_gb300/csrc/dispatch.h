@@ -1,7 +1,7 @@
 // dispatch.h -- host-side lookup of the templated particle kernels.  Each
 // instantiation unit (inst_<prec>_g<geom>.cu) compiles the tile and loose
-// kernels of one precision and geometry for both shape orders and every
-// (pusher, escape) pair a box uses.
+// kernels of one precision and template geometry for both shape orders and
+// every (pusher, escape) pair a box uses.
 #pragma once
 
 namespace pic {
@@ -15,14 +15,20 @@ struct KernelSet {
 KernelSet lookup_f32_g0(int ord, int push, int esc);
 KernelSet lookup_f32_g1(int ord, int push, int esc);
 KernelSet lookup_f32_g2(int ord, int push, int esc);
+KernelSet lookup_f32_g3(int ord, int push, int esc);
+KernelSet lookup_f32_g4(int ord, int push, int esc);
 KernelSet lookup_f64_g0(int ord, int push, int esc);
 KernelSet lookup_f64_g1(int ord, int push, int esc);
 KernelSet lookup_f64_g2(int ord, int push, int esc);
 
+// geom: the template geometry (Geom: 3 and 4 are the 2D planes with 32 x 32
+// tiles, FP32 only)
 inline KernelSet lookup_kernels(bool fp64, int geom, int ord, int push, int esc) {
     if (!fp64) {
         if (geom == 0) return lookup_f32_g0(ord, push, esc);
         if (geom == 1) return lookup_f32_g1(ord, push, esc);
+        if (geom == 3) return lookup_f32_g3(ord, push, esc);
+        if (geom == 4) return lookup_f32_g4(ord, push, esc);
         return lookup_f32_g2(ord, push, esc);
     }
     if (geom == 0) return lookup_f64_g0(ord, push, esc);

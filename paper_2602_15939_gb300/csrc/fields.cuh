@@ -24,15 +24,12 @@ inline dim3 cell_grid(long long nfast, long long ny, long long nz) {
 // differences.  Standard Yee: alpha = 1, sigma = 1; expanding box: the
 // transforms X' = ell L^-1 X folded into alpha, beta, gam, sigma (Sec. 3.2).
 template <class T, int G, bool CURL_E>
-__global__ void curl_update_kernel(Grid g, const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ J,
-                                   const StepCtx* __restrict__ ctx, int which) {
+__device__ __forceinline__ void curl_update_body(const Grid& g, const T* __restrict__ in, T* __restrict__ out,
+                                                 const T* __restrict__ J, const StepCtx* __restrict__ ctx, int which,
+                                                 int i, int j, int k) {
     using GT = GeomT<G>;
     const Coef3 cf = ctx->curl[which];
-    // launch: cell_grid(nx, ny, nz)
     {
-        const int i = blockIdx.x * blockDim.x + threadIdx.x;
-        if (i >= g.nx) return;
-        const int j = blockIdx.y, k = blockIdx.z;
         long long c0 = g.idx(i, j, k);
         const long long sx = 1, sy = g.px, sz = (long long)g.px * g.py, cs = g.cstride;
         const T* X = in;
@@ -70,6 +67,15 @@ __global__ void curl_update_kernel(Grid g, const T* __restrict__ in, T* __restri
             out[c * cs + c0] = v;
         }
     }
+}
+
+template <class T, int G, bool CURL_E>
+__global__ void curl_update_kernel(Grid g, const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ J,
+                                   const StepCtx* __restrict__ ctx, int which) {
+    // launch: cell_grid(nx, ny, nz)
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nx) return;
+    curl_update_body<T, G, CURL_E>(g, in, out, J, ctx, which, i, blockIdx.y, blockIdx.z);
 }
 
 // ---- shearing-box implicit-midpoint sweep ---------------------------------------------
@@ -148,19 +154,11 @@ __global__ void ksb_sweep_kernel(Grid g, const T* __restrict__ En, const T* __re
 // (i + nx, j - dys)), then y over all padded x, then z over all padded x, y.
 // The shift is (dys_i, dys_f), or ctx->dys_*[which] when ctx is given.
 template <class T, int G>
-__global__ void fill_x_kernel(Grid g, T* F, int ncomp, int dys_i, double dys_f, const StepCtx* __restrict__ ctx, int which) {
+__device__ __forceinline__ void fill_x_body(const Grid& g, T* F, int dys_i, double dys_f, int j, int k, int zs) {
     using GT = GeomT<G>;
-    if (ctx) {
-        dys_i = ctx->dys_i[which];
-        dys_f = ctx->dys_f[which];
-    }
     const int nguard = g.px - g.nx;  // gx low + the rest high
-    // launch: cell_grid(ny, nz, ncomp * nguard)
     {
-        const int j = blockIdx.x * blockDim.x + threadIdx.x;
-        if (j >= g.ny) return;
-        const int k = blockIdx.y;
-        const int comp = blockIdx.z / nguard, gi = blockIdx.z - comp * nguard;
+        const int comp = zs / nguard, gi = zs - comp * nguard;
         int i = gi < g.gx ? gi - g.gx : g.nx + (gi - g.gx);  // physical ghost index
         int w = i < 0 ? -1 : 1;
         int is = i - w * g.nx;
@@ -183,36 +181,55 @@ __global__ void fill_x_kernel(Grid g, T* F, int ncomp, int dys_i, double dys_f, 
     }
 }
 
-template <class T>
-__global__ void fill_y_kernel(Grid g, T* F, int ncomp) {
-    const int nguard = g.py - g.ny;
-    // launch: cell_grid(px, nz, ncomp * nguard)
-    {
-        const int pi = blockIdx.x * blockDim.x + threadIdx.x;
-        if (pi >= g.px) return;
-        const int k = blockIdx.y;
-        const int comp = blockIdx.z / nguard, gj = blockIdx.z - comp * nguard;
-        int j = gj < g.gy ? gj - g.gy : g.ny + (gj - g.gy);
-        int js = j < 0 ? j + g.ny : j - g.ny;
-        T* Fc = F + (long long)comp * g.cstride;
-        long long row = (long long)(k + g.gz) * g.py;
-        Fc[(row + j + g.gy) * g.px + pi] = Fc[(row + js + g.gy) * g.px + pi];
+template <class T, int G>
+__global__ void fill_x_kernel(Grid g, T* F, int ncomp, int dys_i, double dys_f, const StepCtx* __restrict__ ctx, int which) {
+    if (ctx) {
+        dys_i = ctx->dys_i[which];
+        dys_f = ctx->dys_f[which];
     }
+    // launch: cell_grid(ny, nz, ncomp * nguard)
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.ny) return;
+    fill_x_body<T, G>(g, F, dys_i, dys_f, j, blockIdx.y, blockIdx.z);
 }
 
 template <class T>
-__global__ void fill_z_kernel(Grid g, T* F, int ncomp) {
-    const int nguard = g.pz - g.nz;
-    const long long plane = (long long)g.px * g.py;
-    // launch: cell_grid(px, py, ncomp * nguard)
+__device__ __forceinline__ void fill_y_body(const Grid& g, T* F, int pi, int k, int zs) {
+    const int nguard = g.py - g.ny;
+    const int comp = zs / nguard, gj = zs - comp * nguard;
+    int j = gj < g.gy ? gj - g.gy : g.ny + (gj - g.gy);
+    int js = j < 0 ? j + g.ny : j - g.ny;
+    T* Fc = F + (long long)comp * g.cstride;
+    long long row = (long long)(k + g.gz) * g.py;
+    Fc[(row + j + g.gy) * g.px + pi] = Fc[(row + js + g.gy) * g.px + pi];
+}
+
+template <class T>
+__global__ void fill_y_kernel(Grid g, T* F, int ncomp) {
+    // launch: cell_grid(px, nz, ncomp * nguard)
     const int pi = blockIdx.x * blockDim.x + threadIdx.x;
     if (pi >= g.px) return;
-    const long long pp = (long long)blockIdx.y * g.px + pi;
-    const int comp = blockIdx.z / nguard, gk = blockIdx.z - comp * nguard;
+    fill_y_body<T>(g, F, pi, blockIdx.y, blockIdx.z);
+}
+
+template <class T>
+__device__ __forceinline__ void fill_z_body(const Grid& g, T* F, int pi, int pj, int zs) {
+    const int nguard = g.pz - g.nz;
+    const long long plane = (long long)g.px * g.py;
+    const long long pp = (long long)pj * g.px + pi;
+    const int comp = zs / nguard, gk = zs - comp * nguard;
     int k = gk < g.gz ? gk - g.gz : g.nz + (gk - g.gz);
     int ks = k < 0 ? k + g.nz : k - g.nz;
     T* Fc = F + (long long)comp * g.cstride;
     Fc[(long long)(k + g.gz) * plane + pp] = Fc[(long long)(ks + g.gz) * plane + pp];
+}
+
+template <class T>
+__global__ void fill_z_kernel(Grid g, T* F, int ncomp) {
+    // launch: cell_grid(px, py, ncomp * nguard)
+    const int pi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pi >= g.px) return;
+    fill_z_body<T>(g, F, pi, blockIdx.y, blockIdx.z);
 }
 
 // ---- current fold (adjoint of the fill) ------------------------------------------------
@@ -221,15 +238,12 @@ __global__ void fill_z_kernel(Grid g, T* F, int ncomp) {
 // t^{n+1/2}: a guard value at (i >= nx, j) belongs at (i - nx, j + dys), split
 // (1 - f, f) between rows floor and floor + 1; at (i < 0, j) at (i + nx, j - dys).
 template <class T>
-__global__ void fold_z_kernel(Grid g, T* F) {
+__device__ __forceinline__ void fold_z_body(const Grid& g, T* F, int pi, int pj, int zs) {
     const long long plane = (long long)g.px * g.py;
     const int band = g.pz - g.nz;  // receiving interior planes: k in [0, gzh) and [nz - gz, nz)
     const int gzh = g.pz - g.gz - g.nz;  // high guards
-    // launch: cell_grid(px, py, 3 * band)
-    const int pi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pi >= g.px) return;
-    const long long pp = (long long)blockIdx.y * g.px + pi;
-    const int comp = blockIdx.z / band, b = blockIdx.z - comp * band;
+    const long long pp = (long long)pj * g.px + pi;
+    const int comp = zs / band, b = zs - comp * band;
     T* Fc = F + (long long)comp * g.cstride;
     int k;  // receiving interior plane
     T add = T(0);
@@ -244,15 +258,19 @@ __global__ void fold_z_kernel(Grid g, T* F) {
 }
 
 template <class T>
-__global__ void fold_y_kernel(Grid g, T* F) {
+__global__ void fold_z_kernel(Grid g, T* F) {
+    // launch: cell_grid(px, py, 3 * band)
+    const int pi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pi >= g.px) return;
+    fold_z_body<T>(g, F, pi, blockIdx.y, blockIdx.z);
+}
+
+template <class T>
+__device__ __forceinline__ void fold_y_body(const Grid& g, T* F, int pi, int k, int zs) {
     const int band = g.py - g.ny;
     const int gyh = g.py - g.gy - g.ny;
-    // launch: cell_grid(px, nz, 3 * band)
     {
-        const int pi = blockIdx.x * blockDim.x + threadIdx.x;
-        if (pi >= g.px) return;
-        const int k = blockIdx.y;
-        const int comp = blockIdx.z / band, b = blockIdx.z - comp * band;
+        const int comp = zs / band, b = zs - comp * band;
         T* Fc = F + (long long)comp * g.cstride;
         long long row = (long long)(k + g.gz) * g.py;
         int j;
@@ -263,20 +281,25 @@ __global__ void fold_y_kernel(Grid g, T* F) {
     }
 }
 
+template <class T>
+__global__ void fold_y_kernel(Grid g, T* F) {
+    // launch: cell_grid(px, nz, 3 * band)
+    const int pi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pi >= g.px) return;
+    fold_y_body<T>(g, F, pi, blockIdx.y, blockIdx.z);
+}
+
 template <class T, int G>
-__global__ void fold_x_kernel(Grid g, T* F, const StepCtx* __restrict__ ctx, int which) {
+__device__ __forceinline__ void fold_x_body(const Grid& g, T* F, const StepCtx* __restrict__ ctx, int which, int j, int k,
+                                            int zs) {
     using GT = GeomT<G>;
     const int dys_i = ctx->dys_i[which];
     const double dys_f = ctx->dys_f[which];
     const int band = g.px - g.nx;
     const int gxh = g.px - g.gx - g.nx;
     const bool sh = GT::AY && (dys_i != 0 || dys_f != 0.0);
-    // launch: cell_grid(ny, nz, 3 * band)
     {
-        const int j = blockIdx.x * blockDim.x + threadIdx.x;
-        if (j >= g.ny) return;
-        const int k = blockIdx.y;
-        const int comp = blockIdx.z / band, b = blockIdx.z - comp * band;
+        const int comp = zs / band, b = zs - comp * band;
         T* Fc = F + (long long)comp * g.cstride;
         int i, is, w;  // receiving interior column, source ghost column, side
         if (b < gxh) { i = b; is = g.nx + b; w = 1; }
@@ -297,6 +320,14 @@ __global__ void fold_x_kernel(Grid g, T* F, const StepCtx* __restrict__ ctx, int
         }
         Fc[g.idx(i, j, k)] += add;
     }
+}
+
+template <class T, int G>
+__global__ void fold_x_kernel(Grid g, T* F, const StepCtx* __restrict__ ctx, int which) {
+    // launch: cell_grid(ny, nz, 3 * band)
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.ny) return;
+    fold_x_body<T, G>(g, F, ctx, which, j, blockIdx.y, blockIdx.z);
 }
 
 // Shearing box: advect J' along y by v_{s,y} dt / 2 = -s Omega0 x dt / 2 per x
@@ -356,6 +387,133 @@ __global__ void fixed_to_float_kernel(long long n, const int* __restrict__ src, 
         if (v > (1 << 30) || v < -(1 << 30)) atomicOr(err, ERRB_J_RANGE);
         dst[q] = (float)((double)v * unit);
     }
+}
+
+// ---- batched grid kernels -----------------------------------------------------------------
+// The grid work of many boxes of one kind in one launch each: box b's
+// blocks are blockIdx.z in [zoff[b], zoff[b+1]) (its slabs along the launch's
+// z index), x and y cover the largest box and blocks beyond a box's own
+// extent return.  The bodies are the single-box kernels', so results are the
+// same bit for bit.  Descriptors and offset tables live in device memory
+// (fixed for the life of a batch).
+template <class T> struct FieldBox {
+    Grid g;
+    T* E;
+    T* B;
+    T* J;         // the current the field update reads (the folded one)
+    int* Jint;    // FP32: the fixed-point current (null in FP64)
+    StepCtx* ctx;
+    int* err;
+    double fx_unit;
+    CtxConst cc;
+};
+
+__device__ __forceinline__ int box_of_z(const int* __restrict__ zoff, int n, int z) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (zoff[mid] <= z) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Start of a step for every box: the step context and the current reset.
+// Launch: grid (any, n); block row b serves box b.
+template <class T>
+__global__ void multi_pre_kernel(const FieldBox<T>* __restrict__ fb, int n) {
+    const int b = blockIdx.y;
+    if (b >= n) return;
+    const FieldBox<T>& f = fb[b];
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctx_update(f.ctx, f.cc);
+    const long long m = 3ll * f.g.cstride;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < m; q += (long long)gridDim.x * blockDim.x) {
+        if (sizeof(T) == 4) f.Jint[q] = 0;
+        else f.J[q] = T(0);
+    }
+}
+
+// FP32 current: fixed point -> float for every box.  Launch: grid (any, n).
+__global__ inline void multi_fixed_to_float_kernel(const FieldBox<float>* __restrict__ fb, int n) {
+    const int b = blockIdx.y;
+    if (b >= n) return;
+    const FieldBox<float>& f = fb[b];
+    const long long m = 3ll * f.g.cstride;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < m; q += (long long)gridDim.x * blockDim.x) {
+        const int v = f.Jint[q];
+        if (v > (1 << 30) || v < -(1 << 30)) atomicOr(f.err, ERRB_J_RANGE);
+        f.J[q] = (float)((double)v * f.fx_unit);
+    }
+}
+
+// which field: 0 E, 1 B, 2 J
+template <class T> __device__ __forceinline__ T* field_of(const FieldBox<T>& f, int which) {
+    return which == 0 ? f.E : (which == 1 ? f.B : f.J);
+}
+
+template <class T, int G, bool CURL_E>
+__global__ void multi_curl_kernel(const FieldBox<T>* __restrict__ fb, const int* __restrict__ zoff, int n, int which) {
+    const int b = box_of_z(zoff, n, blockIdx.z);
+    const FieldBox<T>& f = fb[b];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z - zoff[b];
+    if (i >= f.g.nx || j >= f.g.ny) return;
+    curl_update_body<T, G, CURL_E>(f.g, CURL_E ? f.E : f.B, CURL_E ? f.B : f.E, CURL_E ? nullptr : f.J, f.ctx, which, i, j,
+                                   k);
+}
+
+// guard fills of field `which` (no shear shift: the batched path serves the
+// unsheared kinds)
+template <class T, int G>
+__global__ void multi_fill_x_kernel(const FieldBox<T>* __restrict__ fb, const int* __restrict__ zoff, int n, int which) {
+    const int b = box_of_z(zoff, n, blockIdx.z);
+    const FieldBox<T>& f = fb[b];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (j >= f.g.ny || k >= f.g.nz) return;
+    fill_x_body<T, G>(f.g, field_of(f, which), 0, 0.0, j, k, blockIdx.z - zoff[b]);
+}
+
+template <class T>
+__global__ void multi_fill_y_kernel(const FieldBox<T>* __restrict__ fb, const int* __restrict__ zoff, int n, int which) {
+    const int b = box_of_z(zoff, n, blockIdx.z);
+    const FieldBox<T>& f = fb[b];
+    const int pi = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (pi >= f.g.px || k >= f.g.nz) return;
+    fill_y_body<T>(f.g, field_of(f, which), pi, k, blockIdx.z - zoff[b]);
+}
+
+template <class T>
+__global__ void multi_fill_z_kernel(const FieldBox<T>* __restrict__ fb, const int* __restrict__ zoff, int n, int which) {
+    const int b = box_of_z(zoff, n, blockIdx.z);
+    const FieldBox<T>& f = fb[b];
+    const int pi = blockIdx.x * blockDim.x + threadIdx.x, pj = blockIdx.y;
+    if (pi >= f.g.px || pj >= f.g.py) return;
+    fill_z_body<T>(f.g, field_of(f, which), pi, pj, blockIdx.z - zoff[b]);
+}
+
+template <class T>
+__global__ void multi_fold_z_kernel(const FieldBox<T>* __restrict__ fb, const int* __restrict__ zoff, int n) {
+    const int b = box_of_z(zoff, n, blockIdx.z);
+    const FieldBox<T>& f = fb[b];
+    const int pi = blockIdx.x * blockDim.x + threadIdx.x, pj = blockIdx.y;
+    if (pi >= f.g.px || pj >= f.g.py) return;
+    fold_z_body<T>(f.g, f.J, pi, pj, blockIdx.z - zoff[b]);
+}
+
+template <class T>
+__global__ void multi_fold_y_kernel(const FieldBox<T>* __restrict__ fb, const int* __restrict__ zoff, int n) {
+    const int b = box_of_z(zoff, n, blockIdx.z);
+    const FieldBox<T>& f = fb[b];
+    const int pi = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (pi >= f.g.px || k >= f.g.nz) return;
+    fold_y_body<T>(f.g, f.J, pi, k, blockIdx.z - zoff[b]);
+}
+
+template <class T, int G>
+__global__ void multi_fold_x_kernel(const FieldBox<T>* __restrict__ fb, const int* __restrict__ zoff, int n) {
+    const int b = box_of_z(zoff, n, blockIdx.z);
+    const FieldBox<T>& f = fb[b];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (j >= f.g.ny || k >= f.g.nz) return;
+    fold_x_body<T, G>(f.g, f.J, f.ctx, 1, j, k, blockIdx.z - zoff[b]);
 }
 
 // ---- host <-> padded layout -----------------------------------------------------------

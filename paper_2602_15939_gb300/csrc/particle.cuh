@@ -178,9 +178,9 @@ template <class T> struct Shape<T, 2> {
 // arrays (loose particles) use runtime strides.
 
 template <int G> struct TileDims {
-    static constexpr int TX = (G == G3D) ? 8 : 16;
-    static constexpr int TY = (G == G3D) ? 8 : (G == G2XY ? 16 : 1);
-    static constexpr int TZ = (G == G3D) ? 8 : (G == G2XZ ? 16 : 1);
+    static constexpr int TX = tile_side(G);
+    static constexpr int TY = GeomT<G>::AY ? tile_side(G) : 1;
+    static constexpr int TZ = GeomT<G>::AZ ? tile_side(G) : 1;
     static constexpr int BX = TX + 4;
     static constexpr int BY = GeomT<G>::AY ? TY + 4 : 1;
     static constexpr int BZ = GeomT<G>::AZ ? TZ + 4 : 1;

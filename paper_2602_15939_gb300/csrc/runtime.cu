@@ -83,25 +83,32 @@ template <class T, int G> static size_t tile_smem_bytes_t(int v) {
     }
 }
 
-static size_t tile_smem_bytes(bool fp64, int geom, int v) {
-    if (fp64) return geom == 0 ? tile_smem_bytes_t<double, 0>(v) : geom == 1 ? tile_smem_bytes_t<double, 1>(v)
-                                                                              : tile_smem_bytes_t<double, 2>(v);
-    return geom == 0 ? tile_smem_bytes_t<float, 0>(v) : geom == 1 ? tile_smem_bytes_t<float, 1>(v)
-                                                                   : tile_smem_bytes_t<float, 2>(v);
+// tg: template geometry (Geom; the 32 x 32-tile planes are FP32 only)
+static size_t tile_smem_bytes(bool fp64, int tg, int v) {
+    if (fp64) return tg == 0 ? tile_smem_bytes_t<double, 0>(v) : tg == 1 ? tile_smem_bytes_t<double, 1>(v)
+                                                                          : tile_smem_bytes_t<double, 2>(v);
+    switch (tg) {
+        case 0: return tile_smem_bytes_t<float, 0>(v);
+        case 1: return tile_smem_bytes_t<float, 1>(v);
+        case 2: return tile_smem_bytes_t<float, 2>(v);
+        case 3: return tile_smem_bytes_t<float, 3>(v);
+        default: return tile_smem_bytes_t<float, 4>(v);
+    }
 }
 
 // Variant used when the configuration leaves the choice to the library
 // (pic_autotune refines it for a given box).
-static int default_variant(bool fp64, int geom) { return default_tile_variant(fp64, geom); }
+static int default_variant(bool fp64, int tg) { return default_tile_variant(fp64, tg); }
 
 // Steps between regroups of the particles by cell (0: never).  FP64 boxes do
 // not regroup: the order of their current's floating-point adds would then
 // vary from run to run.
-static int default_regroup_interval(bool fp64, int geom) { return fp64 ? 0 : (geom == 0 ? 3 : 0); }
+static int default_regroup_interval(bool fp64, int tg) { return fp64 ? 0 : (tg == G3D ? 3 : 0); }
 
 struct pic_handle {
     pic_config cfg;
     int geom = 0;  // 0 3D, 1 2D-XY, 2 2D-XZ
+    int tg = 0;    // template geometry of the particle kernels: geom, or G2XY_W / G2XZ_W (2D, 32 x 32 tiles)
     bool fp64 = false;
     size_t esz = 4;
     Grid g;
@@ -509,9 +516,8 @@ static pic_status pre_particle(pic_handle* h) {
 // Rest of a step after the tile kernel: loose particles, counter bookkeeping,
 // the current's conversion and guard fold, the field update; then the buffers
 // flip and the step count advances.
-template <class T, int G> static pic_status post_particle_t(pic_handle* h, const StepP& P, const SpecPack<T>& SP) {
+template <class T, int G> static pic_status post_particles_t(pic_handle* h, const StepP& P, const SpecPack<T>& SP) {
     const Grid& g = h->g;
-    const pic_config& cf = h->cfg;
     const int b = h->buf, o = 1 - b;
     if (P.nsp > 0) {
         prof_begin(h);
@@ -533,6 +539,15 @@ template <class T, int G> static pic_status post_particle_t(pic_handle* h, const
         }
         prof_end(h, 1);
     }
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
+// The grid part of the rest of a step: the current's conversion and guard
+// fold, the shearing boxes' J' advection, the field update.
+template <class T, int G> static pic_status post_fields_t(pic_handle* h, const StepP& P) {
+    const Grid& g = h->g;
+    const pic_config& cf = h->cfg;
     prof_begin(h);
     if (!h->fp64) {
         fixed_to_float_kernel<<<grid_blocks(3ll * g.cstride), NTHR, 0, h->stream>>>(3ll * g.cstride, h->Jint, (float*)h->J,
@@ -549,8 +564,20 @@ template <class T, int G> static pic_status post_particle_t(pic_handle* h, const
     field_step_t<T, G>(h);
     prof_end(h, 2);
     CK(cudaGetLastError());
-    h->buf = o;
+    return PIC_OK;
+}
+
+// The step is done: the particle buffers flip and the step count advances.
+static void finish_step(pic_handle* h) {
+    h->buf = 1 - h->buf;
     h->step += 1;
+}
+
+template <class T, int G> static pic_status post_particle_t(pic_handle* h, const StepP& P, const SpecPack<T>& SP) {
+    pic_status st = post_particles_t<T, G>(h, P, SP);
+    if (st == PIC_OK) st = post_fields_t<T, G>(h, P);
+    if (st != PIC_OK) return st;
+    finish_step(h);
     return PIC_OK;
 }
 
@@ -1116,12 +1143,14 @@ template <class T, int G> static pic_status maxwellian_t(pic_handle* h, int spec
 // ---- dispatch by precision / geometry --------------------------------------------------------
 
 #define DISPATCH(h, FN, ...)                                                       \
-    ((h)->fp64 ? ((h)->geom == 0   ? FN<double, 0>(__VA_ARGS__)                  \
-                  : (h)->geom == 1 ? FN<double, 1>(__VA_ARGS__)                  \
-                                   : FN<double, 2>(__VA_ARGS__))                 \
-               : ((h)->geom == 0   ? FN<float, 0>(__VA_ARGS__)                   \
-                  : (h)->geom == 1 ? FN<float, 1>(__VA_ARGS__)                   \
-                                   : FN<float, 2>(__VA_ARGS__)))
+    ((h)->fp64 ? ((h)->tg == 0   ? FN<double, 0>(__VA_ARGS__)                    \
+                  : (h)->tg == 1 ? FN<double, 1>(__VA_ARGS__)                    \
+                                 : FN<double, 2>(__VA_ARGS__))                   \
+               : ((h)->tg == 0   ? FN<float, 0>(__VA_ARGS__)                     \
+                  : (h)->tg == 1 ? FN<float, 1>(__VA_ARGS__)                     \
+                  : (h)->tg == 2 ? FN<float, 2>(__VA_ARGS__)                     \
+                  : (h)->tg == 3 ? FN<float, 3>(__VA_ARGS__)                     \
+                                 : FN<float, 4>(__VA_ARGS__)))
 
 template <class T, int G> static pic_status set_fields_t(pic_handle* h, const double* E, const double* B) {
     const Grid& g = h->g;
@@ -1248,6 +1277,29 @@ int pic_abi_version(void) { return PIC_ABI_VERSION; }
 
 const char* pic_last_error(pic_handle* h) { return h ? h->last_error.c_str() : g_init_error.c_str(); }
 
+// Tiling of a handle from its template geometry (h->tg) and grid: the tile
+// extents are those the particle kernels of h->tg are compiled for.
+static void set_tiling(pic_handle* h) {
+    const pic_config& c = h->cfg;
+    const bool AY = h->geom != 2, AZ = h->geom != 1;
+    const int side = tile_side(h->tg);
+    Tiling& tl = h->tl;
+    tl.tx = side;
+    tl.ty = AY ? side : 1;
+    tl.tz = AZ ? side : 1;
+    tl.ntx = (c.nx + tl.tx - 1) / tl.tx;
+    tl.nty = (c.ny + tl.ty - 1) / tl.ty;
+    tl.ntz = (c.nz + tl.tz - 1) / tl.tz;
+    tl.ntiles = tl.ntx * tl.nty * tl.ntz;
+    tl.xalign = (int)(16 / h->esz);
+    tl.bx = tl.tx + 4;
+    tl.by = AY ? tl.ty + 4 : 1;
+    tl.bz = AZ ? tl.tz + 4 : 1;
+    tl.jx = tl.tx + 5;
+    tl.jy = AY ? tl.ty + 5 : 1;
+    tl.jz = AZ ? tl.tz + 5 : 1;
+}
+
 pic_status pic_init(const pic_config* cfg, pic_handle** out) {
     if (!out) return fail(nullptr, PIC_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -1282,42 +1334,34 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
     g.py = AY ? c.ny + GL + GR : 1;
     g.pz = AZ ? c.nz + GL + GR : 1;
     g.cstride = (long long)g.px * g.py * g.pz;
-    Tiling& tl = h->tl;
-    // tile shape is fixed per geometry (compile-time strides of the shared boxes)
-    const int dtx = h->geom == 0 ? 8 : 16;
-    const int dty = h->geom == 0 ? 8 : (h->geom == 1 ? 16 : 1);
-    const int dtz = h->geom == 0 ? 8 : (h->geom == 2 ? 16 : 1);
-    if ((c.tile[0] && c.tile[0] != dtx) || (c.tile[1] && AY && c.tile[1] != dty) || (c.tile[2] && AZ && c.tile[2] != dtz)) {
-        delete h;
-        return fail(nullptr, PIC_ERR_ARG, "tile must be 0 (automatic) or %dx%dx%d for this geometry", dtx, dty, dtz);
-    }
-    tl.tx = dtx;
-    tl.ty = dty;
-    tl.tz = dtz;
-    tl.ntx = (c.nx + tl.tx - 1) / tl.tx;
-    tl.nty = (c.ny + tl.ty - 1) / tl.ty;
-    tl.ntz = (c.nz + tl.tz - 1) / tl.tz;
-    tl.ntiles = tl.ntx * tl.nty * tl.ntz;
-    tl.xalign = A;
-    tl.bx = tl.tx + 4;
-    tl.by = AY ? tl.ty + 4 : 1;
-    tl.bz = AZ ? tl.tz + 4 : 1;
-    tl.jx = tl.tx + 5;
-    tl.jy = AY ? tl.ty + 5 : 1;
-    tl.jz = AZ ? tl.tz + 5 : 1;
+    // particle tiles: 8^3 cells in 3D; 16^2 cells in 2D, or 32^2 (FP32) on request
     {
-        int v = c.kernel_variant > 0 ? (int)c.kernel_variant - 1 : default_variant(h->fp64, h->geom);
+        const int t0 = c.tile[0], t1 = AY ? c.tile[1] : c.tile[2];
+        const int want = t0 ? t0 : t1;
+        const bool ok3 = h->geom == 0 && (t0 == 0 || t0 == 8) && (c.tile[1] == 0 || c.tile[1] == 8) &&
+                         (c.tile[2] == 0 || c.tile[2] == 8);
+        const bool ok2 = h->geom != 0 && (want == 0 || want == 16 || (want == 32 && !h->fp64)) && (t1 == 0 || t1 == want);
+        if (!(h->geom == 0 ? ok3 : ok2)) {
+            delete h;
+            return fail(nullptr, PIC_ERR_ARG, "tile must be 0 (automatic) or %s", h->geom == 0 ? "8x8x8 in 3D"
+                        : "16x16, or 32x32 (FP32), on the active plane in 2D");
+        }
+        h->tg = (h->geom != 0 && want == 32) ? (h->geom == 1 ? G2XY_W : G2XZ_W) : h->geom;
+    }
+    set_tiling(h);
+    {
+        int v = c.kernel_variant > 0 ? (int)c.kernel_variant - 1 : default_variant(h->fp64, h->tg);
         if (c.kernel_variant == 0)
             if (const char* e = getenv("PIC_KERNEL_VARIANT")) v = atoi(e) - 1;
-        if (v < 0 || v >= N_TILE_VARIANTS || tile_smem_bytes(h->fp64, h->geom, v) > MAX_SMEM) {
+        if (v < 0 || v >= N_TILE_VARIANTS || tile_smem_bytes(h->fp64, h->tg, v) > MAX_SMEM) {
             delete h;
             return fail(nullptr, PIC_ERR_ARG, "particle-kernel variant %d does not fit this configuration", v + 1);
         }
         h->tile_variant = v;
         h->tile_threads = TILE_VARIANTS[v].nt;
-        h->smem_bytes = tile_smem_bytes(h->fp64, h->geom, v);
+        h->smem_bytes = tile_smem_bytes(h->fp64, h->tg, v);
     }
-    h->ks = lookup_kernels(h->fp64, h->geom, c.shape_order, h->push, h->esc);
+    h->ks = lookup_kernels(h->fp64, h->tg, c.shape_order, h->push, h->esc);
     h->tile_fn = h->ks.tile[h->tile_variant];
 
     auto bail = [&](pic_status s) {
@@ -1333,7 +1377,7 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
     if (cudaFuncSetAttribute(h->tile_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_bytes) != cudaSuccess)
         return bail(fail(h, PIC_ERR_CUDA, "cannot set %zu bytes of dynamic shared memory", h->smem_bytes));
     if (DISPATCH(h, regroup_attr_t, h) != PIC_OK) return bail(PIC_ERR_CUDA);
-    h->regroup_every = default_regroup_interval(h->fp64, h->geom);
+    h->regroup_every = default_regroup_interval(h->fp64, h->tg);
     const size_t fb = (size_t)3 * g.cstride * h->esz;
     void** bufs[] = {&h->E, &h->B, &h->J, &h->Jtmp};
     for (void** p : bufs) {
@@ -1775,10 +1819,10 @@ pic_status pic_preload_kernels(int32_t device, int32_t precision) {
     const int pushes[6][2] = {{PUSH_BORIS, ESC_NONE}, {PUSH_BORIS, ESC_DISP}, {PUSH_BORIS, ESC_PROB},
                               {PUSH_KSB, ESC_NONE}, {PUSH_KEB, ESC_NONE}, {PUSH_SXE, ESC_NONE}};
     cudaFuncAttributes a;
-    for (int geom = 0; geom < 3; ++geom)
+    for (int tg = 0; tg < (fp64 ? 3 : N_TGEOM); ++tg)
         for (int ord = 1; ord <= 2; ++ord)
             for (const auto& pe : pushes) {
-                const KernelSet ks = lookup_kernels(fp64, geom, ord, pe[0], pe[1]);
+                const KernelSet ks = lookup_kernels(fp64, tg, ord, pe[0], pe[1]);
                 for (const void* f : ks.tile)
                     if (cudaFuncGetAttributes(&a, f) != cudaSuccess) return fail(nullptr, PIC_ERR_CUDA, "kernel load failed");
                 if (cudaFuncGetAttributes(&a, ks.loose) != cudaSuccess || cudaFuncGetAttributes(&a, ks.batch) != cudaSuccess)
@@ -1809,7 +1853,7 @@ pic_status pic_set_kernel_variant(pic_handle* h, int32_t k) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
     if (k < 1 || k > N_TILE_VARIANTS) return fail(h, PIC_ERR_ARG, "kernel variant %d out of range", (int)k);
     const int v = k - 1;
-    const size_t smem = tile_smem_bytes(h->fp64, h->geom, v);
+    const size_t smem = tile_smem_bytes(h->fp64, h->tg, v);
     if (smem > MAX_SMEM) return fail(h, PIC_ERR_ARG, "kernel variant %d needs %zu bytes of shared memory", (int)k, smem);
     cudaSetDevice(h->cfg.device);
     if (cudaFuncSetAttribute(h->ks.tile[v], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -1872,6 +1916,144 @@ pic_status pic_autotune_regroup(pic_handle* h, const int32_t* candidates, int32_
     return st;
 }
 
+// Switch a handle to the particle tiles of template geometry tg (2D FP32:
+// 16 x 16 or 32 x 32 cells).  Every species is read out into flat device
+// arrays (position = cell + offset in FP64, which holds the FP32 cell and
+// offset exactly, so the round trip changes no particle), its arrays are
+// freed and it is loaded again under the new tiling.  The kernels, shared
+// memory attributes and field tensor maps follow the new tiles.  If the new
+// layout cannot be made, the old one is made again from the same copies.
+static pic_status switch_tiling(pic_handle* h, int tg) {
+    h->tg = tg;
+    set_tiling(h);
+    int v = h->tile_variant;
+    if (tile_smem_bytes(h->fp64, tg, v) > MAX_SMEM) v = default_variant(h->fp64, tg);
+    h->ks = lookup_kernels(h->fp64, tg, h->cfg.shape_order, h->push, h->esc);
+    h->tile_variant = v;
+    h->tile_threads = TILE_VARIANTS[v].nt;
+    h->smem_bytes = tile_smem_bytes(h->fp64, tg, v);
+    h->tile_fn = h->ks.tile[v];
+    if (cudaFuncSetAttribute(h->tile_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_bytes) != cudaSuccess)
+        return fail(h, PIC_ERR_CUDA, "cannot set %zu bytes of dynamic shared memory", h->smem_bytes);
+    if (DISPATCH(h, regroup_attr_t, h) != PIC_OK) return PIC_ERR_CUDA;
+    if (encode_field_map(h, &h->tmE, h->E) != PIC_OK || encode_field_map(h, &h->tmB, h->B) != PIC_OK) return PIC_ERR_CUDA;
+    return PIC_OK;
+}
+
+static pic_status retile(pic_handle* h, int tg) {
+    if (tg == h->tg) return PIC_OK;
+    if (h->batched) return fail(h, PIC_ERR_STATE, "the box is stepped by a batch");
+    CK(cudaStreamSynchronize(h->stream));
+    struct Flat {
+        double* x = nullptr;
+        double* u = nullptr;
+        uint32_t* id = nullptr;
+        double* dr = nullptr;
+        long long n = 0;
+        bool on = false;
+    };
+    Flat f[PIC_MAX_SPECIES];
+    const bool hd = h->esc == ESC_DISP;
+    auto free_flat = [&]() {
+        for (Flat& q : f) {
+            dfree(h, q.x);
+            dfree(h, q.u);
+            dfree(h, q.id);
+            dfree(h, q.dr);
+            q = Flat();
+        }
+    };
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
+        DevSpecies& d = h->sp[s];
+        if (!d.loaded) continue;
+        Flat& q = f[s];
+        q.n = d.n;
+        q.on = true;
+        const size_t m = (size_t)std::max(1ll, d.n);
+        if (dalloc(h, (void**)&q.x, sizeof(double) * 3 * m) != cudaSuccess ||
+            dalloc(h, (void**)&q.u, sizeof(double) * 3 * m) != cudaSuccess ||
+            dalloc(h, (void**)&q.id, sizeof(uint32_t) * m) != cudaSuccess ||
+            (hd && dalloc(h, (void**)&q.dr, sizeof(double) * 3 * m) != cudaSuccess)) {
+            cudaGetLastError();
+            free_flat();
+            return fail(h, PIC_ERR_OOM, "re-tiling: no room for a flat copy of the particles (the tiling is kept)");
+        }
+        const pic_status st = DISPATCH(h, compact_t, h, s, q.x, q.u, q.id, q.dr);
+        if (st != PIC_OK) {
+            free_flat();
+            return st;
+        }
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    // the per-tile counters are sized by the tile count: drop them with the arrays
+    auto drop_species = [&]() {
+        for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
+            if (!f[s].on) continue;
+            DevSpecies& d = h->sp[s];
+            for (int b = 0; b < 2; ++b) {
+                for (int i = 0; i < 11; ++i) {
+                    dfree(h, d.arr[b][i]);
+                    dfree(h, d.larr[b][i]);
+                    d.arr[b][i] = d.larr[b][i] = nullptr;
+                }
+                dfree(h, d.stay[b]);
+                dfree(h, d.arrv[b]);
+                d.stay[b] = d.arrv[b] = nullptr;
+            }
+            d.loaded = false;
+        }
+    };
+    auto load_all = [&]() -> pic_status {
+        for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
+            if (!f[s].on) continue;
+            const pic_status st = DISPATCH(h, load_t, h, s, f[s].n, f[s].x, f[s].u, f[s].id, f[s].dr);
+            if (st != PIC_OK) return st;
+        }
+        return PIC_OK;
+    };
+    const int old_tg = h->tg;
+    const int old_variant = h->tile_variant;
+    drop_species();
+    h->buf = 0;
+    pic_status st = switch_tiling(h, tg);
+    if (st == PIC_OK) st = load_all();
+    if (st != PIC_OK) {
+        const std::string why = h->last_error;
+        drop_species();
+        h->tile_variant = old_variant;
+        pic_status back = switch_tiling(h, old_tg);
+        if (back == PIC_OK) back = load_all();
+        free_flat();
+        if (back != PIC_OK) return fail(h, PIC_ERR_STATE, "re-tiling failed (%s) and the old tiling could not be restored", why.c_str());
+        return fail(h, st, "re-tiling failed (the old tiling is restored): %s", why.c_str());
+    }
+    free_flat();
+    for (int k = 0; k < 2; ++k) h->occ_pending[k] = false;
+    CK(cudaMemsetAsync(h->occ_dev, 0, sizeof(int) * 2 * PIC_MAX_SPECIES, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return PIC_OK;
+}
+
+pic_status pic_get_tile(pic_handle* h, int32_t tile[3]) {
+    if (!h || !tile) return fail(h, PIC_ERR_ARG, "NULL argument");
+    tile[0] = h->tl.tx;
+    tile[1] = h->tl.ty;
+    tile[2] = h->tl.tz;
+    return PIC_OK;
+}
+
+pic_status pic_set_tile(pic_handle* h, int32_t side) {
+    if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    if (h->geom == 0) {
+        if (side != 8) return fail(h, PIC_ERR_ARG, "3D tiles are 8x8x8");
+        return PIC_OK;
+    }
+    if (side != 16 && !(side == 32 && !h->fp64)) return fail(h, PIC_ERR_ARG, "2D tiles are 16x16, or 32x32 in FP32");
+    cudaSetDevice(h->cfg.device);
+    return retile(h, side == 32 ? (h->geom == 1 ? G2XY_W : G2XZ_W) : h->geom);
+}
+
 pic_status pic_autotune(pic_handle* h, int32_t trial_steps, int32_t* best, double* ms_per_variant,
                         int64_t* steps_taken) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
@@ -1885,7 +2067,7 @@ pic_status pic_autotune(pic_handle* h, int32_t trial_steps, int32_t* best, doubl
     for (int v = 0; v < N_TILE_VARIANTS; ++v) {
         ms[v] = 0.0;
         launches[v] = 0;
-        fits[v] = tile_smem_bytes(h->fp64, h->geom, v) <= MAX_SMEM;
+        fits[v] = tile_smem_bytes(h->fp64, h->tg, v) <= MAX_SMEM;
     }
     long long taken = 0;
     // two interleaved rounds, so that every variant sees particles in a
@@ -1939,6 +2121,62 @@ pic_status pic_autotune(pic_handle* h, int32_t trial_steps, int32_t* best, doubl
     return PIC_OK;
 }
 
+pic_status pic_autotune_tile(pic_handle* h, int32_t trial_steps, int32_t* best_side, double* ms_per_side) {
+    if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
+    if (trial_steps < 1) return fail(h, PIC_ERR_ARG, "trial_steps must be >= 1");
+    if (h->geom == 0 || h->fp64) return fail(h, PIC_ERR_ARG, "the tile shape is tuned for 2D FP32 boxes only");
+    cudaSetDevice(h->cfg.device);
+    const int sides[2] = {16, 32};
+    const int start_side = h->tl.tx;
+    const bool prof_was = h->prof.on;
+    prof_resolve(h);
+    const double ms0[3] = {h->prof.ms[0], h->prof.ms[1], h->prof.ms[2]};
+    const long long l0 = h->prof.launches, pl0 = h->prof.particle_launches, ps0 = h->prof.particle_steps;
+    double per[2] = {-1.0, -1.0};
+    int var[2] = {0, 0};
+    pic_status st = PIC_OK;
+    for (int k = 0; k < 2 && st == PIC_OK; ++k) {
+        st = pic_set_tile(h, sides[k]);
+        if (st != PIC_OK) break;
+        // the best launch variant for these tiles, then whole steps with it
+        int32_t bv = 0;
+        st = pic_autotune(h, trial_steps, &bv, nullptr, nullptr);
+        if (st != PIC_OK) break;
+        var[k] = bv;
+        h->prof.on = false;
+        st = pic_step(h, 1);
+        if (st != PIC_OK) break;
+        prof_resolve(h);
+        const double before = h->prof.ms[0] + h->prof.ms[1] + h->prof.ms[2];
+        h->prof.on = true;
+        st = pic_step(h, trial_steps);
+        prof_resolve(h);
+        per[k] = (h->prof.ms[0] + h->prof.ms[1] + h->prof.ms[2] - before) / trial_steps;
+    }
+    h->prof.ms[0] = ms0[0];
+    h->prof.ms[1] = ms0[1];
+    h->prof.ms[2] = ms0[2];
+    h->prof.launches = l0;
+    h->prof.particle_launches = pl0;
+    h->prof.particle_steps = ps0;
+    h->prof.on = prof_was;
+    if (st != PIC_OK) {
+        const std::string why = h->last_error;
+        pic_set_tile(h, start_side);
+        return fail(h, st, "%s", why.c_str());
+    }
+    const int b = per[1] >= 0.0 && per[1] < per[0] ? 1 : 0;
+    st = pic_set_tile(h, sides[b]);
+    if (st == PIC_OK && var[b] > 0) st = pic_set_kernel_variant(h, var[b]);
+    if (st != PIC_OK) return st;
+    if (best_side) *best_side = sides[b];
+    if (ms_per_side) {
+        ms_per_side[0] = per[0];
+        ms_per_side[1] = per[1];
+    }
+    return PIC_OK;
+}
+
 pic_status pic_reset_profile(pic_handle* h) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
     prof_resolve(h);
@@ -1960,7 +2198,7 @@ struct pic_batch {
     std::vector<cudaEvent_t> ev;     // fork / join events: one per side stream, plus the fork
     int device = 0;
     bool fp64 = false;
-    int geom = 0;
+    int tg = 0;  // the members' template geometry
     const void* kern = nullptr;
     int nt = 256;
     size_t smem = 0;
@@ -1971,6 +2209,13 @@ struct pic_batch {
     std::vector<int> nwork[2];
     int* counters = nullptr;  // work counters, one per launch
     int phase = 0;
+    // unsheared kinds: every box's grid work in one batched launch per kernel
+    // (descriptors and z-offset tables in device memory, fixed for the batch)
+    bool multi = false;
+    void* ftab = nullptr;
+    size_t zoff_bytes = 0;  // byte offset of the four z-offset tables in ftab
+    int ztot[4] = {0, 0, 0, 0};  // slabs per table: cells, x guards, y guards, z guards
+    int mx_nx = 0, mx_ny = 0, mx_nz = 0, mx_px = 0, mx_py = 0;
     int regroup_every = 0;  // regroup every box by cell every this many steps (0: never)
     int since_regroup = 0;
     bool graphs_on = true;
@@ -2021,7 +2266,81 @@ template <class T, int G> pic_status batch_build_t(pic_batch* B) {
             B->args[ph].push_back(std::move(img));
         }
     }
+    // batched grid work for the kinds without a shear (their field step is
+    // the leapfrog; the shearing kinds keep one branch per box)
+    const int kind = B->box[0]->cfg.box;
+    if (kind != PIC_BOX_SHEAR && kind != PIC_BOX_SHEAR_EXPAND) {
+        std::vector<FieldBox<T>> fb(n);
+        std::vector<int> z(4 * (n + 1), 0);
+        for (int i = 0; i < n; ++i) {
+            pic_handle* h = B->box[i];
+            StepP P;
+            SpecPack<T> SP;
+            step_params<T>(h, h->buf, P, SP);
+            FieldBox<T>& f = fb[i];
+            f.g = h->g;
+            f.E = (T*)h->E;
+            f.B = (T*)h->B;
+            f.J = (T*)h->Jcur;
+            f.Jint = h->Jint;
+            f.ctx = h->ctx;
+            f.err = h->err;
+            f.fx_unit = P.fx_unit;
+            f.cc = h->cc;
+            const Grid& g = h->g;
+            const int ext[4] = {g.nz, 3 * (g.px - g.nx), 3 * (g.py - g.ny), 3 * (g.pz - g.nz)};
+            for (int t = 0; t < 4; ++t) z[t * (n + 1) + i + 1] = z[t * (n + 1) + i] + ext[t];
+            B->mx_nx = std::max(B->mx_nx, g.nx);
+            B->mx_ny = std::max(B->mx_ny, g.ny);
+            B->mx_nz = std::max(B->mx_nz, g.nz);
+            B->mx_px = std::max(B->mx_px, g.px);
+            B->mx_py = std::max(B->mx_py, g.py);
+        }
+        for (int t = 0; t < 4; ++t) B->ztot[t] = z[t * (n + 1) + n];
+        if (B->ztot[0] < 65536 && B->ztot[1] < 65536 && B->ztot[2] < 65536 && B->ztot[3] < 65536) {
+            B->zoff_bytes = (sizeof(FieldBox<T>) * n + 15) & ~(size_t)15;
+            const size_t bytes = B->zoff_bytes + sizeof(int) * z.size();
+            if (cudaMalloc(&B->ftab, bytes) != cudaSuccess) return batch_fail(PIC_ERR_OOM, "pic_batch_create: allocation failed");
+            if (cudaMemcpy(B->ftab, fb.data(), sizeof(FieldBox<T>) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy((char*)B->ftab + B->zoff_bytes, z.data(), sizeof(int) * z.size(), cudaMemcpyHostToDevice) !=
+                    cudaSuccess)
+                return batch_fail(PIC_ERR_CUDA, "pic_batch_create: table upload failed");
+            B->multi = true;
+        }
+    }
     return PIC_OK;
+}
+
+// The grid work of a step for every box of an unsheared batch, in batched
+// launches on the batch's stream: the current's conversion and guard fold,
+// then the leapfrog (B half, E full, B half) with its guard fills.
+template <class T, int G> static void multi_fields_t(pic_batch* B) {
+    using GT = GeomT<G>;
+    const int n = (int)B->box.size();
+    const FieldBox<T>* fb = (const FieldBox<T>*)B->ftab;
+    const int* z = (const int*)((const char*)B->ftab + B->zoff_bytes);
+    const int* zc = z;                  // cells
+    const int* zx = z + (n + 1);        // x guards
+    const int* zy = z + 2 * (n + 1);    // y guards
+    const int* zz = z + 3 * (n + 1);    // z guards
+    cudaStream_t s = B->stream;
+    if (sizeof(T) == 4)
+        multi_fixed_to_float_kernel<<<dim3(64, n), NTHR, 0, s>>>((const FieldBox<float>*)fb, n);
+    if (GT::AZ) multi_fold_z_kernel<T><<<cell_grid(B->mx_px, B->mx_py, B->ztot[3]), CELL_THREADS, 0, s>>>(fb, zz, n);
+    if (GT::AY) multi_fold_y_kernel<T><<<cell_grid(B->mx_px, B->mx_nz, B->ztot[2]), CELL_THREADS, 0, s>>>(fb, zy, n);
+    multi_fold_x_kernel<T, G><<<cell_grid(B->mx_ny, B->mx_nz, B->ztot[1]), CELL_THREADS, 0, s>>>(fb, zx, n);
+    auto fills = [&](int which) {
+        multi_fill_x_kernel<T, G><<<cell_grid(B->mx_ny, B->mx_nz, B->ztot[1]), CELL_THREADS, 0, s>>>(fb, zx, n, which);
+        if (GT::AY) multi_fill_y_kernel<T><<<cell_grid(B->mx_px, B->mx_nz, B->ztot[2]), CELL_THREADS, 0, s>>>(fb, zy, n, which);
+        if (GT::AZ) multi_fill_z_kernel<T><<<cell_grid(B->mx_px, B->mx_py, B->ztot[3]), CELL_THREADS, 0, s>>>(fb, zz, n, which);
+    };
+    const dim3 cg = cell_grid(B->mx_nx, B->mx_ny, B->ztot[0]);
+    multi_curl_kernel<T, G, true><<<cg, CELL_THREADS, 0, s>>>(fb, zc, n, 0);
+    fills(1);
+    multi_curl_kernel<T, G, false><<<cg, CELL_THREADS, 0, s>>>(fb, zc, n, 1);
+    fills(0);
+    multi_curl_kernel<T, G, true><<<cg, CELL_THREADS, 0, s>>>(fb, zc, n, 2);
+    fills(1);
 }
 
 // Fork: every side stream waits for the batch stream; join: the reverse.
@@ -2052,13 +2371,28 @@ template <class T, int G> pic_status batch_step_t(pic_batch* B) {
     }
     B->since_regroup += 1;
     const int ph = B->phase;
-    pic_status st = batch_fork(B);
-    for (size_t i = 0; i < B->box.size() && st == PIC_OK; ++i) {
-        if (regroup) st = regroup_t<T, G>(B->box[i]);
-        if (st == PIC_OK) st = pre_particle(B->box[i]);
+    pic_status st = PIC_OK;
+    if (B->multi) {
+        // regroups per box (branches), then every box's step context and
+        // current reset in one launch
+        if (regroup) {
+            st = batch_fork(B);
+            for (size_t i = 0; i < B->box.size() && st == PIC_OK; ++i) st = regroup_t<T, G>(B->box[i]);
+            if (st == PIC_OK) st = batch_join(B);
+            if (st != PIC_OK) return st;
+        }
+        multi_pre_kernel<T><<<dim3(64, (unsigned)B->box.size()), NTHR, 0, B->stream>>>((const FieldBox<T>*)B->ftab,
+                                                                                    (int)B->box.size());
+        if (cudaGetLastError() != cudaSuccess) return batch_fail(PIC_ERR_CUDA, "batched step start failed");
+    } else {
+        st = batch_fork(B);
+        for (size_t i = 0; i < B->box.size() && st == PIC_OK; ++i) {
+            if (regroup) st = regroup_t<T, G>(B->box[i]);
+            if (st == PIC_OK) st = pre_particle(B->box[i]);
+        }
+        if (st == PIC_OK) st = batch_join(B);
+        if (st != PIC_OK) return st;
     }
-    if (st == PIC_OK) st = batch_join(B);
-    if (st != PIC_OK) return st;
     // one launch per group of boxes, the groups side by side
     const size_t ng = B->args[ph].size();
     if (cudaMemsetAsync(B->counters, 0, sizeof(int) * ng, B->stream) != cudaSuccess)
@@ -2076,21 +2410,28 @@ template <class T, int G> pic_status batch_step_t(pic_batch* B) {
     for (size_t i = 0; i < B->box.size() && st == PIC_OK; ++i) {
         const A_t* A = reinterpret_cast<const A_t*>(B->args[ph][i / A_t::MAXB].data());
         const BoxDesc<T>& D = A->box[i % A_t::MAXB];
-        st = post_particle_t<T, G>(B->box[i], D.P0, D.SP);
+        st = B->multi ? post_particles_t<T, G>(B->box[i], D.P0, D.SP) : post_particle_t<T, G>(B->box[i], D.P0, D.SP);
     }
     if (st == PIC_OK) st = batch_join(B);
     if (st != PIC_OK) return st;
+    if (B->multi) {
+        multi_fields_t<T, G>(B);
+        if (cudaGetLastError() != cudaSuccess) return batch_fail(PIC_ERR_CUDA, "batched field step failed");
+        for (pic_handle* h : B->box) finish_step(h);
+    }
     B->phase ^= 1;
     return PIC_OK;
 }
 
 #define BDISPATCH(B, FN, ...)                                                      \
-    ((B)->fp64 ? ((B)->geom == 0   ? FN<double, 0>(__VA_ARGS__)                  \
-                  : (B)->geom == 1 ? FN<double, 1>(__VA_ARGS__)                  \
-                                   : FN<double, 2>(__VA_ARGS__))                 \
-               : ((B)->geom == 0   ? FN<float, 0>(__VA_ARGS__)                   \
-                  : (B)->geom == 1 ? FN<float, 1>(__VA_ARGS__)                   \
-                                   : FN<float, 2>(__VA_ARGS__)))
+    ((B)->fp64 ? ((B)->tg == 0   ? FN<double, 0>(__VA_ARGS__)                    \
+                  : (B)->tg == 1 ? FN<double, 1>(__VA_ARGS__)                    \
+                                 : FN<double, 2>(__VA_ARGS__))                   \
+               : ((B)->tg == 0   ? FN<float, 0>(__VA_ARGS__)                     \
+                  : (B)->tg == 1 ? FN<float, 1>(__VA_ARGS__)                     \
+                  : (B)->tg == 2 ? FN<float, 2>(__VA_ARGS__)                     \
+                  : (B)->tg == 3 ? FN<float, 3>(__VA_ARGS__)                     \
+                                 : FN<float, 4>(__VA_ARGS__)))
 
 void batch_drop_graphs(pic_batch* B) {
     for (int p = 0; p < 2; ++p) {
@@ -2159,6 +2500,7 @@ void batch_release(pic_batch* B) {
     }
     batch_drop_graphs(B);
     if (B->counters) cudaFree(B->counters);
+    if (B->ftab) cudaFree(B->ftab);
     for (cudaEvent_t e : B->ev)
         if (e) cudaEventDestroy(e);
     for (cudaStream_t s : B->side)
@@ -2182,10 +2524,10 @@ pic_status pic_batch_create(pic_handle* const* boxes, int32_t n, pic_batch** out
         if (h->batched) return batch_fail(PIC_ERR_STATE, "pic_batch_create: a box is already in a batch");
         for (int j = 0; j < i; ++j)
             if (boxes[j] == h) return batch_fail(PIC_ERR_ARG, "pic_batch_create: a box appears twice");
-        if (h->cfg.device != h0->cfg.device || h->fp64 != h0->fp64 || h->geom != h0->geom ||
+        if (h->cfg.device != h0->cfg.device || h->fp64 != h0->fp64 || h->tg != h0->tg ||
             h->cfg.shape_order != h0->cfg.shape_order || h->push != h0->push || h->esc != h0->esc)
             return batch_fail(PIC_ERR_ARG,
-                              "pic_batch_create: boxes differ in device, precision, geometry, shape order or box type");
+                              "pic_batch_create: boxes differ in device, precision, geometry, tile shape, shape order or box type");
         bool any = false;
         for (int s = 0; s < PIC_MAX_SPECIES; ++s) any |= h->sp[s].loaded;
         if (!any) return batch_fail(PIC_ERR_STATE, "pic_batch_create: a box has no particles");
@@ -2194,11 +2536,11 @@ pic_status pic_batch_create(pic_handle* const* boxes, int32_t n, pic_batch** out
     pic_batch* B = new pic_batch();
     B->device = h0->cfg.device;
     B->fp64 = h0->fp64;
-    B->geom = h0->geom;
+    B->tg = h0->tg;
     B->kern = h0->ks.batch;
-    const int v = batch_tile_variant(B->fp64, B->geom);
+    const int v = batch_tile_variant(B->fp64, B->tg);
     B->nt = TILE_VARIANTS[v].nt;
-    B->smem = tile_smem_bytes(B->fp64, B->geom, v);
+    B->smem = tile_smem_bytes(B->fp64, B->tg, v);
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B->device);
     if (cudaFuncSetAttribute(B->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem) != cudaSuccess ||
@@ -2207,7 +2549,7 @@ pic_status pic_batch_create(pic_handle* const* boxes, int32_t n, pic_batch** out
         return batch_fail(PIC_ERR_CUDA, "pic_batch_create: the batched kernel cannot be launched");
     }
     B->max_grid = sms * per_sm;
-    B->regroup_every = default_regroup_interval(B->fp64, B->geom);
+    B->regroup_every = default_regroup_interval(B->fp64, B->tg);
     // every box's queued work ends before the batch takes over
     for (int i = 0; i < n; ++i) cudaStreamSynchronize(boxes[i]->stream);
     int K = std::min(n, 16);  // parallel branches for the boxes' own kernels

@@ -125,6 +125,9 @@ _SIGS = {
     "pic_get_kernel_variant": (C.c_int, [_H, C.POINTER(C.c_int32)]),
     "pic_set_kernel_variant": (C.c_int, [_H, C.c_int32]),
     "pic_take_result": (C.c_int, [_H, C.c_uint64, C.POINTER(_H)]),
+    "pic_get_tile": (C.c_int, [_H, C.POINTER(C.c_int32)]),
+    "pic_set_tile": (C.c_int, [_H, C.c_int32]),
+    "pic_autotune_tile": (C.c_int, [_H, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "pic_autotune_regroup": (C.c_int, [_H, C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.POINTER(C.c_int32),
                                        C.POINTER(C.c_double)]),
     "pic_batch_create": (C.c_int, [C.POINTER(_H), C.c_int32, C.POINTER(_H)]),
@@ -383,6 +386,27 @@ def pic_autotune_regroup(h, candidates=(2, 3, 4, 6), cycles: int = 2):
     return best.value, list(ms)
 
 
+def pic_get_tile(h):
+    """The particle tile in cells per axis (1 on an ignorable axis)."""
+    t = (C.c_int32 * 3)()
+    _check(h, lib().pic_get_tile(h, t))
+    return tuple(t)
+
+
+def pic_set_tile(h, side: int):
+    """Re-lay the particles out in side x side tiles (2D: 16, or 32 in FP32)."""
+    _check(h, lib().pic_set_tile(h, side))
+
+
+def pic_autotune_tile(h, trial_steps: int = 4):
+    """Time 16 x 16 and 32 x 32 tiles (2D FP32), each with its best launch
+    variant, and keep the faster: returns (best side, ms per step for 16, 32)."""
+    best = C.c_int32()
+    ms = (C.c_double * 2)()
+    _check(h, lib().pic_autotune_tile(h, trial_steps, C.byref(best), ms))
+    return best.value, (ms[0], ms[1])
+
+
 class Batch:
     """Boxes of one kind stepped together (pic_batch_*): one persistent
     particle kernel per step over all their tiles, graph-replayed."""
@@ -506,6 +530,16 @@ class Box:
     def autotune_regroup(self, candidates=(2, 3, 4, 6), cycles=2):
         """Pick the fastest regroup interval on live steps; see pic_autotune_regroup."""
         return pic_autotune_regroup(self.h, candidates, cycles)
+
+    def tile(self):
+        return pic_get_tile(self.h)
+
+    def set_tile(self, side: int):
+        pic_set_tile(self.h, side)
+
+    def autotune_tile(self, trial_steps=4):
+        """Pick 16 x 16 or 32 x 32 particle tiles on live steps (2D FP32); see pic_autotune_tile."""
+        return pic_autotune_tile(self.h, trial_steps)
 
     def step(self, n=1):
         pic_step(self.h, n)

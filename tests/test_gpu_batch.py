@@ -1,8 +1,10 @@
 """Batches (pic_batch_*): boxes of one kind but different grids, parameters
 and particle counts, stepped together by one persistent particle kernel per
-step under graph replay, give exactly the results of stepping each box on
-its own (FP32 bit for bit; FP64 to rounding, its current being summed with
-double atomics), and one of them matches the FP64 oracle like any box."""
+step under graph replay (and, for the unsheared kinds, with every box's grid
+work in one launch per grid kernel), give exactly the results of stepping
+each box on its own (FP32 bit for bit; FP64 to rounding, its current being
+summed with double atomics), and one of them matches the FP64 oracle like
+any box."""
 import dataclasses
 
 import numpy as np
@@ -22,6 +24,15 @@ LEAKY = [
     Case("l0", BOX_L, (32, 24, 1), ndim=2, plane=P.PIC_PLANE_XY, order=2, ppc=6, esc_mode=2, p_esc=0.05, theta_inj=1.0),
     Case("l1", BOX_L, (48, 32, 1), ndim=2, plane=P.PIC_PLANE_XY, order=2, ppc=4, esc_mode=2, p_esc=0.02, theta_inj=0.3,
          seed=3),
+]
+PERIODIC = [
+    Case("p0", BOX_P, (16, 12, 8), order=1, ppc=3),
+    Case("p1", BOX_P, (12, 20, 16), order=1, ppc=4, seed=6, uth=0.25),
+]
+PERIODIC_XZ = [
+    Case("q0", BOX_P, (32, 1, 24), ndim=2, plane=P.PIC_PLANE_XZ, order=1, ppc=5),
+    Case("q1", BOX_P, (24, 1, 40), ndim=2, plane=P.PIC_PLANE_XZ, order=1, ppc=3, seed=8, uth=0.3),
+    Case("q2", BOX_P, (8, 1, 8), ndim=2, plane=P.PIC_PLANE_XZ, order=1, ppc=7, seed=2),
 ]
 SHEAR = [
     Case("s0", BOX_S, (16, 12, 8), order=2, s=1.5, Omega0=3e-3, step0=37),
@@ -92,7 +103,8 @@ def assert_same(a, b, exact, tol=1e-12):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("cases", [EXPAND, LEAKY, SHEAR], ids=["expand3d", "leaky2d", "shear3d"])
+@pytest.mark.parametrize("cases", [EXPAND, LEAKY, SHEAR, PERIODIC, PERIODIC_XZ],
+                         ids=["expand3d", "leaky2d", "shear3d", "periodic3d_o1", "periodic2dxz_o1"])
 def test_fp32_batch_equals_boxes_alone(cases):
     n = 5  # two graph-replayed pairs and one plain step
     got = run_batched(cases, n, False, chunks=[2, 3])

@@ -1,0 +1,186 @@
+"""Particle tile shapes (2D FP32: 16 x 16 or 32 x 32 cells).  The tile only
+decides where a particle is stored and which CTA moves it, so a box on 32 x 32
+tiles matches the oracle like any box, and gives bit for bit the FP32 results
+of the same box on 16 x 16 tiles (its current is an integer sum, exact in any
+order); so does a box switched between the two shapes mid-run (pic_set_tile)
+or by the tile autotuner, and a batch of 32 x 32-tile boxes."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from gpu_harness import Case, compare, inputs
+from paper_2602_15939_gb300 import pic as P
+
+BOX_P, BOX_S, BOX_E, BOX_L = P.PIC_BOX_PERIODIC, P.PIC_BOX_SHEAR, P.PIC_BOX_EXPAND, P.PIC_BOX_LEAKY
+XY, XZ = P.PIC_PLANE_XY, P.PIC_PLANE_XZ
+
+# grids that are not multiples of 32: ragged tiles on the high sides
+WIDE = [
+    Case("leaky2d_prob_o1", BOX_L, (72, 40, 1), ndim=2, plane=XY, order=1, ppc=6, esc_mode=2, p_esc=0.05,
+         theta_inj=1.0, tile=(32, 32, 0)),
+    Case("leaky2d_disp_o2", BOX_L, (40, 72, 1), ndim=2, plane=XY, order=2, ppc=5, esc_mode=1, l_esc=0.35,
+         theta_inj=0.2, tile=(32, 32, 0)),
+    Case("periodic2dxz_o2", BOX_P, (40, 1, 36), ndim=2, plane=XZ, order=2, ppc=6, tile=(32, 0, 32)),
+    Case("expand2dxy_o1", BOX_E, (48, 33, 1), ndim=2, plane=XY, order=1, ppc=6, rate=(2e-3, 1e-3, 0.0), step0=50,
+         tile=(32, 32, 0)),
+    Case("shear2dxz_o1", BOX_S, (64, 1, 40), ndim=2, plane=XZ, order=1, ppc=6, s=1.5, Omega0=4e-3, step0=11,
+         tile=(32, 0, 32)),
+]
+IDS = [c.name for c in WIDE]
+
+
+def narrow(case):
+    return dataclasses.replace(case, tile=(0, 0, 0))
+
+
+def load(case):
+    sp, E, B = inputs(case)
+    box = P.Box(case.gpu_config(False))
+    box.set_fields(E, B)
+    for i, d in enumerate(sp):
+        box.load(i, d["q"], d["m"], d["x"], d["u"], d["id"])
+    box.set_step(case.step0)
+    return box, len(sp)
+
+
+def state(box, nsp, with_dr):
+    parts = []
+    for i in range(nsp):
+        x, u, ids, dr = box.particles(i, want_dr=with_dr)
+        o = np.argsort(ids)
+        parts.append((x[o], u[o], ids[o], None if dr is None else dr[o]))
+    return parts, box.fields(), box.diagnostics()
+
+
+def assert_identical(a, b):
+    (pa, fa, da), (pb, fb, db) = a, b
+    assert da.step == db.step and da.error_word == 0 and db.error_word == 0
+    assert da.escaped_total == db.escaped_total
+    for (xa, ua, ia, ra), (xb, ub, ib, rb) in zip(pa, pb):
+        assert np.array_equal(ia, ib)
+        assert np.array_equal(xa, xb) and np.array_equal(ua, ub)
+        if ra is not None:
+            assert np.array_equal(ra, rb)
+    for x, y in zip(fa, fb):
+        assert np.array_equal(x, y)
+
+
+def run(case, plan):
+    """Step a box through `plan`: ints are step counts, ("tile", s) switches
+    the tile side, ("tune", k) runs the tile autotuner with k trial steps."""
+    box, nsp = load(case)
+    try:
+        for item in plan:
+            if isinstance(item, int):
+                box.step(item)
+            elif item[0] == "tile":
+                box.set_tile(item[1])
+            else:
+                best, ms = box.autotune_tile(item[1])
+                assert best in (16, 32) and box.tile()[0] == best
+                assert ms[0] > 0 and ms[1] > 0
+        return state(box, nsp, case.esc_mode == 1), box.tile()
+    finally:
+        box.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", WIDE, ids=IDS)
+def test_wide_tiles_match_oracle(case):
+    r = compare(case, 1, fp64=False)
+    assert r["error_word"] == 0, r
+    assert r["u"] <= 1e-6 and r["x"] <= 2e-6, r
+    assert r["E"] <= 1e-6 and r["B"] <= 1e-6 and r["J"] <= 1e-6, r
+    assert r["escaped_gpu"] == r["escaped_oracle"], r
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", WIDE, ids=IDS)
+def test_wide_tiles_equal_narrow_tiles(case):
+    (a, ta), (b, tb) = run(case, [6]), run(narrow(case), [6])
+    side = 32
+    assert ta == (side, 1 if case.plane == XZ else side, side if case.plane == XZ else 1)
+    assert tb[0] == 16
+    assert_identical(a, b)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", [WIDE[0], WIDE[1], WIDE[2]], ids=IDS[:3])
+def test_switching_tiles_mid_run_changes_nothing(case):
+    c = narrow(case)
+    got, t = run(c, [2, ("tile", 32), 3, ("tile", 16), 2, ("tile", 32), 1])
+    assert t[0] == 32
+    want, _ = run(c, [8])
+    assert_identical(got, want)
+
+
+@pytest.mark.gpu
+def test_tile_autotuner_keeps_the_simulation():
+    c = narrow(WIDE[0])
+    box, nsp = load(c)
+    try:
+        best, ms = box.autotune_tile(2)
+        assert best in (16, 32) and box.tile()[0] == best
+        box.step(1)
+        got = state(box, nsp, False)
+    finally:
+        box.close()
+    steps = got[2].step - c.step0
+    want, _ = run(c, [int(steps)])
+    assert_identical(got, want)
+
+
+@pytest.mark.gpu
+def test_batch_of_wide_tile_boxes_equals_boxes_alone():
+    cases = [WIDE[0], dataclasses.replace(WIDE[0], name="l1", n=(64, 64, 1), seed=4, ppc=4),
+             dataclasses.replace(WIDE[0], name="l2", n=(33, 97, 1), seed=7, p_esc=0.02)]
+    loaded = [load(c) for c in cases]
+    try:
+        with P.Batch([b for b, _ in loaded]) as bt:
+            bt.step(2)
+            bt.step(3)
+            bt.sync()
+        got = [state(b, n, False) for b, n in loaded]
+    finally:
+        for b, _ in loaded:
+            b.close()
+    for c, g in zip(cases, got):
+        want, _ = run(c, [5])
+        assert_identical(g, want)
+
+
+@pytest.mark.gpu
+def test_tile_shape_errors():
+    c = WIDE[0]
+    with pytest.raises(P.PicError) as e:  # 32 x 32 tiles are FP32 only
+        P.Box(c.gpu_config(True))
+    assert e.value.status == P.PIC_ERR_ARG
+    for bad in ((24, 24, 0), (32, 16, 0), (16, 32, 0)):
+        with pytest.raises(P.PicError) as e:
+            P.Box(dataclasses.replace(c, tile=bad).gpu_config(False))
+        assert e.value.status == P.PIC_ERR_ARG
+    box = P.Box(narrow(c).gpu_config(False))
+    try:
+        with pytest.raises(P.PicError):
+            box.set_tile(24)
+        with pytest.raises(P.PicError):
+            box.set_tile(8)
+    finally:
+        box.close()
+    box3 = P.Box(Case("p3", BOX_P, (8, 8, 8)).gpu_config(False))
+    try:
+        assert box3.tile() == (8, 8, 8)
+        with pytest.raises(P.PicError):
+            box3.set_tile(16)
+        with pytest.raises(P.PicError):
+            box3.autotune_tile(1)
+    finally:
+        box3.close()
+    boxes = [load(c)[0], load(narrow(c))[0]]
+    try:
+        with pytest.raises(P.PicError):  # a batch's members share the tile shape
+            P.Batch(boxes)
+    finally:
+        for b in boxes:
+            b.close()
