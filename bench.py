@@ -66,6 +66,7 @@ def parse():
                     help="prefix of the full-range served-ensemble stream that is timed")
     ap.add_argument("--kernel-only", action="store_true", help="warmup + timed steps only (for profiler runs)")
     ap.add_argument("--batch-legs-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--serving-only", type=int, default=-1, help=argparse.SUPPRESS)
     ap.add_argument("--seed", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--tile", type=int, default=0,
                     help="2D FP32 particle tile side (16 or 32); 0 = autotune with the variant")
@@ -508,6 +509,8 @@ def run_gb300(args):
 
     if not args.no_serving and not args.kernel_only:
         line["serving"] = run_serving(local, seed=rank, runs=args.serve_runs)
+        line["serving_min_batch_" + str(0 if SERVE_MIN_BATCH else 2)] = run_serving(
+            local, seed=rank, runs=args.serve_runs, min_batch=0 if SERVE_MIN_BATCH else 2)
         line["serving_full_range"] = run_serving(local, seed=rank, runs=args.full_serve_runs, full=True)
         line["batched_ensemble"] = batch_legs_subprocess(local, rank)
 
@@ -520,7 +523,12 @@ def run_gb300(args):
     return 0
 
 
-def run_serving(device, seed=0, runs=64, full=False):
+# Served runs of one kind are stepped as batches of at least this many runs
+# (pic_server_set_batching; 0 = every run on its own stream).
+SERVE_MIN_BATCH = 2
+
+
+def run_serving(device, seed=0, runs=64, full=False, min_batch=SERVE_MIN_BATCH):
     """The served-ensemble workload through libpic's continuous-batching
     server: a Poisson stream of independent shearing / expanding / leaky runs
     (2D and 3D, FP32).  full=False: a bounded sample (reduced grids and step
@@ -544,7 +552,7 @@ def run_serving(device, seed=0, runs=64, full=False):
     runs_l = W.served_ensemble(runs, seed=seed, full=full, mean_gap_s=gap)
     specs = [W.run_spec_of(r) for r in runs_l]
     work = sum(2 * r["ppc"] * r["n"][0] * r["n"][1] * r["n"][2] * r["steps"] for r in runs_l)
-    srv = P.Server(device=device, hbm_budget_bytes=96 << 30, max_active=32, steps_per_round=10)
+    srv = P.Server(device=device, hbm_budget_bytes=96 << 30, max_active=32, steps_per_round=10, min_batch=min_batch)
     tickets = []
     t0 = time.perf_counter()
 
@@ -572,7 +580,8 @@ def run_serving(device, seed=0, runs=64, full=False):
                   "8-32 ppc/species; 20-100 steps; FP32")
     return {"runs": len(runs_l), "runs_per_s": len(runs_l) / wall, "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "particle_steps_per_s": work / wall,
-            "peak_active": int(info.peak_active), "wall_s": wall, "sample": sample}
+            "peak_active": int(info.peak_active), "wall_s": wall, "sample": sample,
+            "min_batch": min_batch, "cohorts_formed": int(info.cohorts_formed)}
 
 
 def run_batch_leg(device, steps=20, seed=0, nbox=16, sizes=(32, 48, 64)):
@@ -743,6 +752,19 @@ def main():
         libbuild.build()
         out = {"medium": run_batch_leg(0, seed=args.seed),
                "small": run_batch_leg(0, seed=args.seed, nbox=64, sizes=(16, 24, 32))}
+        print(json.dumps(out), flush=True)
+        return 0
+    if args.serving_only >= 0:
+        import torch
+
+        torch.cuda.set_device(0)
+        from paper_2602_15939_gb300 import build as libbuild
+
+        libbuild.build()
+        out = {"sample": run_serving(0, seed=args.seed, runs=args.serve_runs, min_batch=args.serving_only)}
+        if args.full_serve_runs > 0:
+            out["full_range"] = run_serving(0, seed=args.seed, runs=args.full_serve_runs, full=True,
+                                            min_batch=args.serving_only)
         print(json.dumps(out), flush=True)
         return 0
     if args.impl == "reference":

@@ -461,7 +461,7 @@ typedef struct pic_server_info {
     int64_t completed;
     uint64_t bytes_in_use, peak_bytes;
     int32_t peak_active;
-    int32_t reserved;
+    int32_t cohorts_formed;  /* batches formed from active runs so far (pic_server_set_batching) */
 } pic_server_info;
 
 typedef struct pic_server pic_server;
@@ -480,6 +480,20 @@ int pic_admission_count(uint64_t budget, uint64_t in_use, int active, int max_ac
  * once, advancing each active run steps_per_round steps per round. */
 pic_status pic_server_create(int device, uint64_t hbm_budget_bytes, int max_active,
                              int steps_per_round, pic_server **out);
+
+/* Batching of served runs: min_batch = 0 (the default) steps every active
+ * run on its own stream; min_batch >= 2 groups idle active runs of one kind
+ * (precision, geometry and tile shape, shape order, box type and escape
+ * rule) that have at least 4 x steps_per_round steps left, at least
+ * min_batch of them, into a cohort stepped as one pic_batch (no graph
+ * capture: a cohort may not live long enough to repay one).
+ * A cohort advances by chunks of at most steps_per_round steps and no more
+ * than its shortest remaining run; when a member is done the cohort is
+ * dissolved after its queued chunks complete, the finished runs retire and
+ * the others are regrouped with the idle runs of their kind.  Results are
+ * those of each run stepped alone (FP32: bit-identical).  PIC_ERR_ARG for
+ * min_batch < 0 or 1.  Takes effect from the worker's next round. */
+pic_status pic_server_set_batching(pic_server *s, int min_batch);
 
 /* Queue a run (the spec is copied); *ticket identifies it. */
 pic_status pic_submit(pic_server *s, const pic_run_spec *spec, uint64_t *ticket);

@@ -2209,13 +2209,28 @@ struct pic_batch {
     std::vector<int> nwork[2];
     int* counters = nullptr;  // work counters, one per launch
     int phase = 0;
-    // unsheared kinds: every box's grid work in one batched launch per kernel
-    // (descriptors and z-offset tables in device memory, fixed for the batch)
+    // Unsheared kinds (multi): the boxes are split into lanes.  A lane is a
+    // chain of batched launches on its own side stream: its boxes' step
+    // contexts, one persistent particle kernel over their tiles, their loose
+    // particles, and their grid work in one launch per field kernel.  The
+    // lanes are forked from the batch stream at the start of a cycle of steps
+    // and joined at its end, so one lane's field work and the tail of its
+    // particle kernel overlap the other lanes' particle kernels.
+    struct FieldTab {
+        void* dev = nullptr;    // FieldBox[n], then four z-offset tables of n + 1 ints
+        size_t zoff_bytes = 0;  // byte offset of the z-offset tables
+        int n = 0;
+        int ztot[4] = {0, 0, 0, 0};  // slabs per table: cells, x guards, y guards, z guards
+        int mx_nx = 0, mx_ny = 0, mx_nz = 0, mx_px = 0, mx_py = 0;
+    };
+    struct Lane {
+        std::vector<int> idx;  // the lane's boxes (indices into box)
+        std::vector<unsigned char> args[2];
+        int nwork[2] = {0, 0};
+        FieldTab ft;
+    };
     bool multi = false;
-    void* ftab = nullptr;
-    size_t zoff_bytes = 0;  // byte offset of the four z-offset tables in ftab
-    int ztot[4] = {0, 0, 0, 0};  // slabs per table: cells, x guards, y guards, z guards
-    int mx_nx = 0, mx_ny = 0, mx_nz = 0, mx_px = 0, mx_py = 0;
+    std::vector<Lane> lanes;
     int regroup_every = 0;  // regroup every box by cell every this many steps (0: never)
     int since_regroup = 0;
     bool graphs_on = true;
@@ -2233,108 +2248,151 @@ pic_status batch_fail(pic_status st, const char* msg) {
     return st;
 }
 
+// A batch's own device memory (work counters, field tables) comes from the
+// library's stream-ordered pool on the batch stream: cudaMalloc and cudaFree
+// would synchronise the device, stalling every other box and served run.
+static cudaError_t balloc(pic_batch* B, void** p, size_t bytes) {
+    cudaMemPool_t pool = lib_pool(B->device);
+    if (!pool) return cudaMalloc(p, bytes);
+    return cudaMallocFromPoolAsync(p, bytes, pool, B->stream);
+}
+
+static void bfree(pic_batch* B, void* p) {
+    if (!p) return;
+    if (lib_pool(B->device)) cudaFreeAsync(p, B->stream);
+    else cudaFree(p);
+}
+
+// Descriptor images of the batched particle kernel for boxes `idx` (at most
+// MAXB): one per phase, the box's buffers at that parity.
+template <class T> static void batch_images(pic_batch* B, const std::vector<int>& idx, int* counter,
+                                           std::vector<unsigned char> img[2], int nwork[2]) {
+    using A_t = BatchArgs<T>;
+    for (int ph = 0; ph < 2; ++ph) {
+        img[ph].assign(sizeof(A_t), 0);
+        A_t* A = reinterpret_cast<A_t*>(img[ph].data());
+        const int k = (int)idx.size();
+        A->nbox = k;
+        A->next = counter;
+        A->first[0] = 0;
+        for (int j = 0; j < k; ++j) {
+            pic_handle* h = B->box[idx[j]];
+            BoxDesc<T>& D = A->box[j];
+            D.tmE = h->tmE;
+            D.tmB = h->tmB;
+            D.g = h->g;
+            D.tl = h->tl;
+            step_params<T>(h, ph == 0 ? h->buf : 1 - h->buf, D.P0, D.SP);
+            D.J = h->fp64 ? (JWord<T>*)h->J : (JWord<T>*)(void*)h->Jint;
+            D.ctx = h->ctx;
+            A->first[j + 1] = A->first[j] + h->tl.ntiles;
+        }
+        nwork[ph] = A->first[k];
+    }
+}
+
+// Field descriptors and z-offset tables of boxes `idx`, uploaded to the device.
+template <class T> static pic_status field_table(pic_batch* B, const std::vector<int>& idx, pic_batch::FieldTab& ft) {
+    const int n = (int)idx.size();
+    std::vector<FieldBox<T>> fb(n);
+    std::vector<int> z(4 * (n + 1), 0);
+    for (int i = 0; i < n; ++i) {
+        pic_handle* h = B->box[idx[i]];
+        StepP P;
+        SpecPack<T> SP;
+        step_params<T>(h, h->buf, P, SP);
+        FieldBox<T>& f = fb[i];
+        f.g = h->g;
+        f.E = (T*)h->E;
+        f.B = (T*)h->B;
+        f.J = (T*)h->Jcur;
+        f.Jint = h->Jint;
+        f.ctx = h->ctx;
+        f.err = h->err;
+        f.fx_unit = P.fx_unit;
+        f.cc = h->cc;
+        const Grid& g = h->g;
+        const int ext[4] = {g.nz, 3 * (g.px - g.nx), 3 * (g.py - g.ny), 3 * (g.pz - g.nz)};
+        for (int t = 0; t < 4; ++t) z[t * (n + 1) + i + 1] = z[t * (n + 1) + i] + ext[t];
+        ft.mx_nx = std::max(ft.mx_nx, g.nx);
+        ft.mx_ny = std::max(ft.mx_ny, g.ny);
+        ft.mx_nz = std::max(ft.mx_nz, g.nz);
+        ft.mx_px = std::max(ft.mx_px, g.px);
+        ft.mx_py = std::max(ft.mx_py, g.py);
+    }
+    ft.n = n;
+    for (int t = 0; t < 4; ++t) ft.ztot[t] = z[t * (n + 1) + n];
+    ft.zoff_bytes = (sizeof(FieldBox<T>) * n + 15) & ~(size_t)15;
+    if (balloc(B, &ft.dev, ft.zoff_bytes + sizeof(int) * z.size()) != cudaSuccess)
+        return batch_fail(PIC_ERR_OOM, "pic_batch_create: allocation failed");
+    // pageable sources: each copy has left the host buffer when the call returns
+    if (cudaMemcpyAsync(ft.dev, fb.data(), sizeof(FieldBox<T>) * n, cudaMemcpyHostToDevice, B->stream) != cudaSuccess ||
+        cudaMemcpyAsync((char*)ft.dev + ft.zoff_bytes, z.data(), sizeof(int) * z.size(), cudaMemcpyHostToDevice,
+                        B->stream) != cudaSuccess)
+        return batch_fail(PIC_ERR_CUDA, "pic_batch_create: table upload failed");
+    return PIC_OK;
+}
+
 template <class T, int G> pic_status batch_build_t(pic_batch* B) {
     using A_t = BatchArgs<T>;
     const int n = (int)B->box.size();
     B->args_bytes = sizeof(A_t);
+    if (B->multi) {
+        const int L = (int)B->lanes.size();
+        if (balloc(B, (void**)&B->counters, sizeof(int) * L) != cudaSuccess)
+            return batch_fail(PIC_ERR_OOM, "pic_batch_create: allocation failed");
+        for (int l = 0; l < L; ++l) {
+            pic_batch::Lane& ln = B->lanes[l];
+            batch_images<T>(B, ln.idx, B->counters + l, ln.args, ln.nwork);
+            const pic_status st = field_table<T>(B, ln.idx, ln.ft);
+            if (st != PIC_OK) return st;
+        }
+        return PIC_OK;
+    }
     const int ngroups = (n + A_t::MAXB - 1) / A_t::MAXB;
-    if (cudaMalloc(&B->counters, sizeof(int) * ngroups) != cudaSuccess)
+    if (balloc(B, (void**)&B->counters, sizeof(int) * ngroups) != cudaSuccess)
         return batch_fail(PIC_ERR_OOM, "pic_batch_create: allocation failed");
     for (int ph = 0; ph < 2; ++ph) {
         B->args[ph].clear();
         B->nwork[ph].clear();
-        for (int g0 = 0; g0 < n; g0 += A_t::MAXB) {
-            const int k = std::min(A_t::MAXB, n - g0);
-            std::vector<unsigned char> img(sizeof(A_t), 0);
-            A_t* A = reinterpret_cast<A_t*>(img.data());
-            A->nbox = k;
-            A->next = B->counters + g0 / A_t::MAXB;
-            A->first[0] = 0;
-            for (int j = 0; j < k; ++j) {
-                pic_handle* h = B->box[g0 + j];
-                BoxDesc<T>& D = A->box[j];
-                D.tmE = h->tmE;
-                D.tmB = h->tmB;
-                D.g = h->g;
-                D.tl = h->tl;
-                step_params<T>(h, ph == 0 ? h->buf : 1 - h->buf, D.P0, D.SP);
-                D.J = h->fp64 ? (JWord<T>*)h->J : (JWord<T>*)(void*)h->Jint;
-                D.ctx = h->ctx;
-                A->first[j + 1] = A->first[j] + h->tl.ntiles;
-            }
-            B->nwork[ph].push_back(A->first[k]);
-            B->args[ph].push_back(std::move(img));
-        }
     }
-    // batched grid work for the kinds without a shear (their field step is
-    // the leapfrog; the shearing kinds keep one branch per box)
-    const int kind = B->box[0]->cfg.box;
-    if (kind != PIC_BOX_SHEAR && kind != PIC_BOX_SHEAR_EXPAND) {
-        std::vector<FieldBox<T>> fb(n);
-        std::vector<int> z(4 * (n + 1), 0);
-        for (int i = 0; i < n; ++i) {
-            pic_handle* h = B->box[i];
-            StepP P;
-            SpecPack<T> SP;
-            step_params<T>(h, h->buf, P, SP);
-            FieldBox<T>& f = fb[i];
-            f.g = h->g;
-            f.E = (T*)h->E;
-            f.B = (T*)h->B;
-            f.J = (T*)h->Jcur;
-            f.Jint = h->Jint;
-            f.ctx = h->ctx;
-            f.err = h->err;
-            f.fx_unit = P.fx_unit;
-            f.cc = h->cc;
-            const Grid& g = h->g;
-            const int ext[4] = {g.nz, 3 * (g.px - g.nx), 3 * (g.py - g.ny), 3 * (g.pz - g.nz)};
-            for (int t = 0; t < 4; ++t) z[t * (n + 1) + i + 1] = z[t * (n + 1) + i] + ext[t];
-            B->mx_nx = std::max(B->mx_nx, g.nx);
-            B->mx_ny = std::max(B->mx_ny, g.ny);
-            B->mx_nz = std::max(B->mx_nz, g.nz);
-            B->mx_px = std::max(B->mx_px, g.px);
-            B->mx_py = std::max(B->mx_py, g.py);
-        }
-        for (int t = 0; t < 4; ++t) B->ztot[t] = z[t * (n + 1) + n];
-        if (B->ztot[0] < 65536 && B->ztot[1] < 65536 && B->ztot[2] < 65536 && B->ztot[3] < 65536) {
-            B->zoff_bytes = (sizeof(FieldBox<T>) * n + 15) & ~(size_t)15;
-            const size_t bytes = B->zoff_bytes + sizeof(int) * z.size();
-            if (cudaMalloc(&B->ftab, bytes) != cudaSuccess) return batch_fail(PIC_ERR_OOM, "pic_batch_create: allocation failed");
-            if (cudaMemcpy(B->ftab, fb.data(), sizeof(FieldBox<T>) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
-                cudaMemcpy((char*)B->ftab + B->zoff_bytes, z.data(), sizeof(int) * z.size(), cudaMemcpyHostToDevice) !=
-                    cudaSuccess)
-                return batch_fail(PIC_ERR_CUDA, "pic_batch_create: table upload failed");
-            B->multi = true;
+    for (int g0 = 0; g0 < n; g0 += A_t::MAXB) {
+        std::vector<int> idx;
+        for (int j = g0; j < std::min(n, g0 + A_t::MAXB); ++j) idx.push_back(j);
+        std::vector<unsigned char> img[2];
+        int nw[2];
+        batch_images<T>(B, idx, B->counters + g0 / A_t::MAXB, img, nw);
+        for (int ph = 0; ph < 2; ++ph) {
+            B->args[ph].push_back(std::move(img[ph]));
+            B->nwork[ph].push_back(nw[ph]);
         }
     }
     return PIC_OK;
 }
 
-// The grid work of a step for every box of an unsheared batch, in batched
-// launches on the batch's stream: the current's conversion and guard fold,
-// then the leapfrog (B half, E full, B half) with its guard fills.
-template <class T, int G> static void multi_fields_t(pic_batch* B) {
+// The grid work of a step for the boxes of a field table, in batched
+// launches on stream s: the current's conversion and guard fold, then the
+// leapfrog (B half, E full, B half) with its guard fills.
+template <class T, int G> static void multi_fields_t(const pic_batch::FieldTab& ft, cudaStream_t s) {
     using GT = GeomT<G>;
-    const int n = (int)B->box.size();
-    const FieldBox<T>* fb = (const FieldBox<T>*)B->ftab;
-    const int* z = (const int*)((const char*)B->ftab + B->zoff_bytes);
+    const int n = ft.n;
+    const FieldBox<T>* fb = (const FieldBox<T>*)ft.dev;
+    const int* z = (const int*)((const char*)ft.dev + ft.zoff_bytes);
     const int* zc = z;                  // cells
     const int* zx = z + (n + 1);        // x guards
     const int* zy = z + 2 * (n + 1);    // y guards
     const int* zz = z + 3 * (n + 1);    // z guards
-    cudaStream_t s = B->stream;
     if (sizeof(T) == 4)
         multi_fixed_to_float_kernel<<<dim3(64, n), NTHR, 0, s>>>((const FieldBox<float>*)fb, n);
-    if (GT::AZ) multi_fold_z_kernel<T><<<cell_grid(B->mx_px, B->mx_py, B->ztot[3]), CELL_THREADS, 0, s>>>(fb, zz, n);
-    if (GT::AY) multi_fold_y_kernel<T><<<cell_grid(B->mx_px, B->mx_nz, B->ztot[2]), CELL_THREADS, 0, s>>>(fb, zy, n);
-    multi_fold_x_kernel<T, G><<<cell_grid(B->mx_ny, B->mx_nz, B->ztot[1]), CELL_THREADS, 0, s>>>(fb, zx, n);
+    if (GT::AZ) multi_fold_z_kernel<T><<<cell_grid(ft.mx_px, ft.mx_py, ft.ztot[3]), CELL_THREADS, 0, s>>>(fb, zz, n);
+    if (GT::AY) multi_fold_y_kernel<T><<<cell_grid(ft.mx_px, ft.mx_nz, ft.ztot[2]), CELL_THREADS, 0, s>>>(fb, zy, n);
+    multi_fold_x_kernel<T, G><<<cell_grid(ft.mx_ny, ft.mx_nz, ft.ztot[1]), CELL_THREADS, 0, s>>>(fb, zx, n);
     auto fills = [&](int which) {
-        multi_fill_x_kernel<T, G><<<cell_grid(B->mx_ny, B->mx_nz, B->ztot[1]), CELL_THREADS, 0, s>>>(fb, zx, n, which);
-        if (GT::AY) multi_fill_y_kernel<T><<<cell_grid(B->mx_px, B->mx_nz, B->ztot[2]), CELL_THREADS, 0, s>>>(fb, zy, n, which);
-        if (GT::AZ) multi_fill_z_kernel<T><<<cell_grid(B->mx_px, B->mx_py, B->ztot[3]), CELL_THREADS, 0, s>>>(fb, zz, n, which);
+        multi_fill_x_kernel<T, G><<<cell_grid(ft.mx_ny, ft.mx_nz, ft.ztot[1]), CELL_THREADS, 0, s>>>(fb, zx, n, which);
+        if (GT::AY) multi_fill_y_kernel<T><<<cell_grid(ft.mx_px, ft.mx_nz, ft.ztot[2]), CELL_THREADS, 0, s>>>(fb, zy, n, which);
+        if (GT::AZ) multi_fill_z_kernel<T><<<cell_grid(ft.mx_px, ft.mx_py, ft.ztot[3]), CELL_THREADS, 0, s>>>(fb, zz, n, which);
     };
-    const dim3 cg = cell_grid(B->mx_nx, B->mx_ny, B->ztot[0]);
+    const dim3 cg = cell_grid(ft.mx_nx, ft.mx_ny, ft.ztot[0]);
     multi_curl_kernel<T, G, true><<<cg, CELL_THREADS, 0, s>>>(fb, zc, n, 0);
     fills(1);
     multi_curl_kernel<T, G, false><<<cg, CELL_THREADS, 0, s>>>(fb, zc, n, 1);
@@ -2373,18 +2431,34 @@ template <class T, int G> pic_status batch_step_t(pic_batch* B) {
     const int ph = B->phase;
     pic_status st = PIC_OK;
     if (B->multi) {
-        // regroups per box (branches), then every box's step context and
-        // current reset in one launch
-        if (regroup) {
-            st = batch_fork(B);
-            for (size_t i = 0; i < B->box.size() && st == PIC_OK; ++i) st = regroup_t<T, G>(B->box[i]);
-            if (st == PIC_OK) st = batch_join(B);
-            if (st != PIC_OK) return st;
+        // each lane on its own stream (forked by the caller): regroups, step
+        // contexts and current resets, the particle kernel, loose particles,
+        // the grid work
+        for (size_t l = 0; l < B->lanes.size(); ++l) {
+            pic_batch::Lane& ln = B->lanes[l];
+            cudaStream_t s = B->side[l];
+            for (int i : ln.idx)
+                if (regroup && (st = regroup_t<T, G>(B->box[i])) != PIC_OK) return st;
+            multi_pre_kernel<T><<<dim3(64, (unsigned)ln.ft.n), NTHR, 0, s>>>((const FieldBox<T>*)ln.ft.dev, ln.ft.n);
+            if (cudaMemsetAsync(B->counters + l, 0, sizeof(int), s) != cudaSuccess)
+                return batch_fail(PIC_ERR_CUDA, "work counter reset failed");
+            const int grid = std::max(1, std::min(ln.nwork[ph], B->max_grid));
+            void* a[] = {ln.args[ph].data()};
+            if (cudaLaunchKernel(B->kern, dim3(grid), dim3(B->nt), a, B->smem, s) != cudaSuccess)
+                return batch_fail(PIC_ERR_CUDA, "batched particle kernel launch failed");
+            const A_t* A = reinterpret_cast<const A_t*>(ln.args[ph].data());
+            for (size_t j = 0; j < ln.idx.size(); ++j) {
+                st = post_particles_t<T, G>(B->box[ln.idx[j]], A->box[j].P0, A->box[j].SP);
+                if (st != PIC_OK) return st;
+            }
+            multi_fields_t<T, G>(ln.ft, s);
+            if (cudaGetLastError() != cudaSuccess) return batch_fail(PIC_ERR_CUDA, "batched step failed");
+            for (int i : ln.idx) finish_step(B->box[i]);
         }
-        multi_pre_kernel<T><<<dim3(64, (unsigned)B->box.size()), NTHR, 0, B->stream>>>((const FieldBox<T>*)B->ftab,
-                                                                                    (int)B->box.size());
-        if (cudaGetLastError() != cudaSuccess) return batch_fail(PIC_ERR_CUDA, "batched step start failed");
-    } else {
+        B->phase ^= 1;
+        return PIC_OK;
+    }
+    {
         st = batch_fork(B);
         for (size_t i = 0; i < B->box.size() && st == PIC_OK; ++i) {
             if (regroup) st = regroup_t<T, G>(B->box[i]);
@@ -2410,15 +2484,10 @@ template <class T, int G> pic_status batch_step_t(pic_batch* B) {
     for (size_t i = 0; i < B->box.size() && st == PIC_OK; ++i) {
         const A_t* A = reinterpret_cast<const A_t*>(B->args[ph][i / A_t::MAXB].data());
         const BoxDesc<T>& D = A->box[i % A_t::MAXB];
-        st = B->multi ? post_particles_t<T, G>(B->box[i], D.P0, D.SP) : post_particle_t<T, G>(B->box[i], D.P0, D.SP);
+        st = post_particle_t<T, G>(B->box[i], D.P0, D.SP);
     }
     if (st == PIC_OK) st = batch_join(B);
     if (st != PIC_OK) return st;
-    if (B->multi) {
-        multi_fields_t<T, G>(B);
-        if (cudaGetLastError() != cudaSuccess) return batch_fail(PIC_ERR_CUDA, "batched field step failed");
-        for (pic_handle* h : B->box) finish_step(h);
-    }
     B->phase ^= 1;
     return PIC_OK;
 }
@@ -2443,6 +2512,10 @@ void batch_drop_graphs(pic_batch* B) {
 
 // Steps per captured batch graph: a regroup and the steps up to the next
 // one, or a pair of steps.
+// Lanes of an unsheared batch (more where one launch cannot hold a lane's
+// boxes, fewer for fewer boxes).
+constexpr int BATCH_LANES = 2;
+
 int batch_cycle(const pic_batch* B) { return B->regroup_every > 0 ? B->regroup_every : 2; }
 
 // Capture one cycle of steps from the current phase (with the regroup due,
@@ -2464,8 +2537,9 @@ pic_status batch_capture(pic_batch* B) {
         B->graphs_on = false;
         return PIC_OK;
     }
-    pic_status st = PIC_OK;
+    pic_status st = B->multi ? batch_fork(B) : PIC_OK;
     for (int k = 0; k < batch_cycle(B) && st == PIC_OK; ++k) st = BDISPATCH(B, batch_step_t, B);
+    if (st == PIC_OK && B->multi) st = batch_join(B);
     cudaError_t e = cudaStreamEndCapture(B->stream, &graph);
     B->phase = ph0;
     B->since_regroup = r0;
@@ -2499,8 +2573,8 @@ void batch_release(pic_batch* B) {
         B->box[i]->batched = false;
     }
     batch_drop_graphs(B);
-    if (B->counters) cudaFree(B->counters);
-    if (B->ftab) cudaFree(B->ftab);
+    bfree(B, B->counters);
+    for (pic_batch::Lane& ln : B->lanes) bfree(B, ln.ft.dev);
     for (cudaEvent_t e : B->ev)
         if (e) cudaEventDestroy(e);
     for (cudaStream_t s : B->side)
@@ -2552,8 +2626,30 @@ pic_status pic_batch_create(pic_handle* const* boxes, int32_t n, pic_batch** out
     B->regroup_every = default_regroup_interval(B->fp64, B->tg);
     // every box's queued work ends before the batch takes over
     for (int i = 0; i < n; ++i) cudaStreamSynchronize(boxes[i]->stream);
-    int K = std::min(n, 16);  // parallel branches for the boxes' own kernels
-    if (const char* e = getenv("PIC_BATCH_STREAMS")) K = std::max(1, std::min(n, atoi(e)));
+    // unsheared kinds run in lanes, when the batched grid launches' z extents
+    // (summed over a lane's boxes) stay within the grid limit
+    {
+        const int kind = h0->cfg.box;
+        B->multi = kind != PIC_BOX_SHEAR && kind != PIC_BOX_SHEAR_EXPAND;
+        long long zs[4] = {0, 0, 0, 0};
+        for (int i = 0; i < n; ++i) {
+            const Grid& g = boxes[i]->g;
+            zs[0] += g.nz;
+            zs[1] += 3ll * (g.px - g.nx);
+            zs[2] += 3ll * (g.py - g.ny);
+            zs[3] += 3ll * (g.pz - g.nz);
+        }
+        for (long long z : zs)
+            if (z >= 65536) B->multi = false;
+        if (const char* e = getenv("PIC_BATCH_NO_LANES")) B->multi = B->multi && atoi(e) == 0;
+    }
+    const int maxb = B->fp64 ? BatchArgs<double>::MAXB : BatchArgs<float>::MAXB;
+    int nlanes = BATCH_LANES;
+    if (const char* e = getenv("PIC_BATCH_LANES")) nlanes = std::max(1, atoi(e));
+    nlanes = std::min(n, std::max(nlanes, (n + maxb - 1) / maxb));
+    int K = B->multi ? nlanes : std::min(n, 16);  // side streams: the lanes, or parallel branches for the boxes' own kernels
+    if (!B->multi)
+        if (const char* e = getenv("PIC_BATCH_STREAMS")) K = std::max(1, std::min(n, atoi(e)));
     bool ok = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) == cudaSuccess;
     B->side.assign(K, nullptr);
     B->ev.assign(K + 1, nullptr);
@@ -2577,9 +2673,37 @@ pic_status pic_batch_create(pic_handle* const* boxes, int32_t n, pic_batch** out
         batch_release(B);
         return batch_fail(PIC_ERR_CUDA, "pic_batch_create: stream or event creation failed");
     }
-    for (int i = 0; i < n; ++i) {
-        B->box[i]->stream = B->side[i % K];
-        B->box[i]->batched = true;
+    if (B->multi) {
+        // lanes balanced by particle count (heaviest box first to the lightest
+        // lane with room); each lane keeps the heaviest-tiles-first order
+        std::vector<long long> np(n, 0), load(K, 0);
+        for (int i = 0; i < n; ++i)
+            for (int s = 0; s < PIC_MAX_SPECIES; ++s)
+                if (B->box[i]->sp[s].loaded) np[i] += B->box[i]->sp[s].n;
+        std::vector<int> by(n);
+        for (int i = 0; i < n; ++i) by[i] = i;
+        std::stable_sort(by.begin(), by.end(), [&](int a, int b) { return np[a] > np[b]; });
+        std::vector<int> lane_of(n, 0);
+        B->lanes.assign(K, pic_batch::Lane());
+        std::vector<int> cnt(K, 0);
+        for (int i : by) {
+            int best = -1;
+            for (int l = 0; l < K; ++l)
+                if (cnt[l] < maxb && (best < 0 || load[l] < load[best])) best = l;
+            lane_of[i] = best;
+            load[best] += np[i];
+            cnt[best] += 1;
+        }
+        for (int i = 0; i < n; ++i) B->lanes[lane_of[i]].idx.push_back(i);
+        for (int i = 0; i < n; ++i) {
+            B->box[i]->stream = B->side[lane_of[i]];
+            B->box[i]->batched = true;
+        }
+    } else {
+        for (int i = 0; i < n; ++i) {
+            B->box[i]->stream = B->side[i % K];
+            B->box[i]->batched = true;
+        }
     }
     pic_status st = BDISPATCH(B, batch_build_t, B);
     if (st != PIC_OK) {
@@ -2589,6 +2713,17 @@ pic_status pic_batch_create(pic_handle* const* boxes, int32_t n, pic_batch** out
     if (const char* e = getenv("PIC_NO_GRAPHS")) B->graphs_on = atoi(e) == 0;
     *out = B;
     return PIC_OK;
+}
+
+// The stream a batch's work is ordered on (for the server's completion events).
+cudaStream_t pic_internal_batch_stream(pic_batch* B) { return B ? B->stream : nullptr; }
+
+// Graph capture of a batch's step cycles on (1) or off (0): short-lived
+// batches (the server's cohorts) may not step long enough to repay a capture.
+void pic_internal_batch_graphs(pic_batch* B, int on) {
+    if (!B) return;
+    if (!on) batch_drop_graphs(B);
+    B->graphs_on = on != 0;
 }
 
 pic_status pic_batch_step(pic_batch* B, int32_t nsteps) {
@@ -2619,7 +2754,9 @@ pic_status pic_batch_step(pic_batch* B, int32_t nsteps) {
                 continue;
             }
         }
-        pic_status st = BDISPATCH(B, batch_step_t, B);
+        pic_status st = B->multi ? batch_fork(B) : PIC_OK;
+        if (st == PIC_OK) st = BDISPATCH(B, batch_step_t, B);
+        if (st == PIC_OK && B->multi) st = batch_join(B);
         if (st != PIC_OK) return st;
         nsteps -= 1;
     }

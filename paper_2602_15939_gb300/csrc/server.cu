@@ -9,12 +9,22 @@
 // chunks in flight per run), and retires finished runs: final diagnostics,
 // time from submission to result, handle destroyed, memory returned to the
 // budget -- which lets the next queued runs in while others keep stepping.
+//
+// With batching on (pic_server_set_batching), idle active runs of one kind
+// (precision, geometry and tile shape, shape order, box type) with at least
+// four rounds of steps left are grouped into cohorts of at least `min_batch`
+// runs, each stepped as one pic_batch
+// (one persistent particle kernel and batched grid work per step).  A cohort
+// advances by chunks no longer than its shortest remaining run; when a member
+// is done, the cohort is dissolved after its chunks complete, the finished
+// runs retire, and the others are regrouped with the idle runs of their kind.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -26,10 +36,14 @@
 #include "../../include/pic.h"
 
 extern "C" void pic_internal_set_global_error(const char* msg);
+extern "C" cudaStream_t pic_internal_batch_stream(pic_batch* b);
+extern "C" void pic_internal_batch_graphs(pic_batch* b, int on);
 
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+struct Cohort;
 
 struct Run {
     uint64_t ticket = 0;
@@ -46,6 +60,17 @@ struct Run {
     pic_diag diag{};
     double latency_s = 0.0;
     bool kept = false;  // the finished box is held for pic_take_result
+    Cohort* co = nullptr;  // the cohort stepping this run, if any
+    bool hold = false;     // queue no new chunk: the run is draining to join a cohort
+    bool alone = false;    // a cohort could not be made with this run: it steps alone
+    bool fresh = true;     // admitted and not yet stepped
+};
+
+struct Cohort {
+    pic_batch* b = nullptr;
+    std::vector<Run*> runs;
+    std::deque<cudaEvent_t> inflight;
+    bool failed = false;
 };
 
 }  // namespace
@@ -64,6 +89,11 @@ struct pic_server {
     uint64_t bytes_in_use = 0;
     uint64_t peak_bytes = 0;
     int starting = 0;  // admitted runs being set up (neither queued nor active)
+    int min_batch = 0;  // 0: no cohorts; else the fewest runs of one kind stepped as a batch
+    bool cohort_graphs = false;  // capture cohorts' step cycles in graphs
+    int cohort_policy = 0;  // 0: regroup idle runs (draining them); 1: group only runs admitted together
+    int64_t cohorts_formed = 0;
+    std::vector<Cohort*> cohorts;  // worker thread only
     int64_t completed = 0;
     int peak_active = 0;
     bool stop = false;
@@ -224,18 +254,109 @@ static void worker_main(pic_server* S) {
             S->peak_active = std::max(S->peak_active, (int)S->active.size());
         }
         std::vector<Run*> act;
+        int min_batch = 0;
         {
             std::lock_guard<std::mutex> lock(S->mu);
             act = S->active;
+            min_batch = S->min_batch;
         }
-        // one round: keep up to two chunks of steps queued per active run
-        for (Run* r : act) {
+        for (Run* r : act)
             while (!r->inflight.empty() && cudaEventQuery(r->inflight.front()) == cudaSuccess) {
                 cudaEventDestroy(r->inflight.front());
                 r->inflight.pop_front();
             }
+        // cohorts: drop completed chunks; dissolve those with a finished (or
+        // failed) member once their chunks are done
+        for (size_t c = 0; c < S->cohorts.size();) {
+            Cohort* co = S->cohorts[c];
+            while (!co->inflight.empty() && cudaEventQuery(co->inflight.front()) == cudaSuccess) {
+                cudaEventDestroy(co->inflight.front());
+                co->inflight.pop_front();
+            }
+            bool end = co->failed;
+            for (Run* r : co->runs) end |= r->remaining <= 0;
+            if (end && co->inflight.empty()) {
+                if (pic_batch_destroy(co->b) != PIC_OK)
+                    for (Run* r : co->runs) {
+                        r->error = pic_last_error(nullptr);
+                        r->remaining = -1;
+                    }
+                for (Run* r : co->runs) r->co = nullptr;
+                delete co;
+                S->cohorts.erase(S->cohorts.begin() + c);
+            } else {
+                ++c;
+            }
+        }
+        // new cohorts from runs of one kind with several rounds left (a
+        // cohort's set-up must be repaid): once there are min_batch of them,
+        // they get no new chunks of their own, and when all are idle they are
+        // grouped
+        for (Run* r : act) r->hold = false;
+        if (min_batch > 0) {
+            std::map<std::vector<int>, std::vector<Run*>> kinds;
+            const int64_t min_left = 4ll * S->steps_per_round;
+            for (Run* r : act) {
+                if (r->co || r->alone || r->remaining < min_left) continue;
+                if (S->cohort_policy == 1 && !r->fresh) continue;
+                const pic_config& c = r->spec.cfg;
+                const int t = c.ndim == 3 ? 0 : (c.tile[0] ? c.tile[0] : (c.plane == PIC_PLANE_XY ? c.tile[1] : c.tile[2]));
+                kinds[{c.precision, c.ndim, c.plane, t, c.shape_order, c.box, c.box == PIC_BOX_LEAKY ? c.escape_mode : 0}]
+                    .push_back(r);
+            }
+            for (auto& kv : kinds) {
+                std::vector<Run*>& rs = kv.second;
+                if ((int)rs.size() < min_batch) continue;
+                bool idle = true;
+                for (Run* r : rs) idle = idle && r->inflight.empty();
+                if (S->cohort_policy == 1) idle = true;  // fresh runs have nothing in flight
+                if (!idle) {
+                    for (Run* r : rs) r->hold = true;
+                    continue;
+                }
+                std::vector<pic_handle*> hs;
+                for (Run* r : rs) hs.push_back(r->h);
+                pic_batch* b = nullptr;
+                if (pic_batch_create(hs.data(), (int)hs.size(), &b) != PIC_OK) {
+                    for (Run* r : rs) r->alone = true;
+                    continue;
+                }
+                pic_internal_batch_graphs(b, S->cohort_graphs ? 1 : 0);
+                for (Run* r : rs) r->fresh = false;
+                Cohort* co = new Cohort();
+                co->b = b;
+                co->runs = rs;
+                for (Run* r : rs) r->co = co;
+                S->cohorts.push_back(co);
+                S->cohorts_formed += 1;
+            }
+        }
+        // one round: keep up to two chunks of steps queued per cohort and per lone run
+        for (Cohort* co : S->cohorts) {
+            int64_t k = S->steps_per_round;
+            for (Run* r : co->runs) k = std::min(k, r->remaining);
+            if (co->failed || k <= 0 || co->inflight.size() >= 2) continue;
+            if (pic_batch_step(co->b, (int)k) != PIC_OK) {
+                const std::string why = pic_last_error(nullptr);
+                for (Run* r : co->runs) r->error = why;
+                co->failed = true;
+                continue;
+            }
+            for (Run* r : co->runs) r->remaining -= k;
+            cudaEvent_t e;
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+            cudaEventRecord(e, pic_internal_batch_stream(co->b));
+            co->inflight.push_back(e);
+        }
+        for (Cohort* co : S->cohorts)
+            if (co->failed)
+                for (Run* r : co->runs)
+                    if (r->remaining >= 0) r->remaining = -1;
+        for (Run* r : act) {
+            if (r->co || r->hold) continue;
             if (r->remaining > 0 && r->inflight.size() < 2) {
                 const int k = (int)std::min<int64_t>(r->remaining, S->steps_per_round);
+                r->fresh = false;
                 pic_status st = pic_step(r->h, k);
                 if (st != PIC_OK) {
                     r->error = pic_last_error(r->h);
@@ -249,9 +370,10 @@ static void worker_main(pic_server* S) {
                 r->inflight.push_back(e);
             }
         }
-        // retire runs whose last chunk has completed
+        // retire runs (out of any cohort) whose last chunk has completed
         std::vector<Run*> finished;
         for (Run* r : act) {
+            if (r->co) continue;
             if (r->remaining < 0 || (r->remaining == 0 && (r->inflight.empty() || cudaEventQuery(r->inflight.back()) == cudaSuccess)))
                 finished.push_back(r);
         }
@@ -289,8 +411,20 @@ extern "C" pic_status pic_server_create(int device, uint64_t hbm_budget_bytes, i
     S->budget = hbm_budget_bytes;
     S->max_active = max_active;
     S->steps_per_round = steps_per_round;
+    if (const char* e = getenv("PIC_SERVER_COHORT_GRAPHS")) S->cohort_graphs = atoi(e) != 0;
+    if (const char* e = getenv("PIC_SERVER_COHORT_POLICY")) S->cohort_policy = atoi(e);
     S->worker = std::thread(worker_main, S);
     *out = S;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_server_set_batching(pic_server* S, int min_batch) {
+    if (!S || min_batch < 0 || min_batch == 1) {
+        pic_internal_set_global_error("pic_server_set_batching: min_batch must be 0 (off) or >= 2");
+        return PIC_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->min_batch = min_batch;
     return PIC_OK;
 }
 
@@ -391,6 +525,7 @@ extern "C" pic_status pic_server_stats(pic_server* S, pic_server_info* out) {
     out->bytes_in_use = S->bytes_in_use;
     out->peak_bytes = S->peak_bytes;
     out->peak_active = S->peak_active;
+    out->cohorts_formed = (int32_t)std::min<int64_t>(S->cohorts_formed, INT32_MAX);
     return PIC_OK;
 }
 

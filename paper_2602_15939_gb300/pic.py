@@ -80,7 +80,7 @@ class pic_run_spec(C.Structure):
 class pic_server_info(C.Structure):
     _fields_ = [("queued", C.c_int32), ("active", C.c_int32), ("completed", C.c_int64),
                 ("bytes_in_use", C.c_uint64), ("peak_bytes", C.c_uint64), ("peak_active", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("cohorts_formed", C.c_int32)]
 
 
 _lib = None
@@ -146,6 +146,7 @@ _SIGS = {
     "pic_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_double]),
     "pic_server_stats": (C.c_int, [C.c_void_p, C.POINTER(pic_server_info)]),
     "pic_server_destroy": (C.c_int, [C.c_void_p]),
+    "pic_server_set_batching": (C.c_int, [C.c_void_p, C.c_int]),
 }
 
 
@@ -601,11 +602,18 @@ def pic_admission_count(budget, in_use, active, max_active, queued_bytes) -> int
 class Server:
     """Continuous-batching run server (libpic's pic_server_*)."""
 
-    def __init__(self, device=0, hbm_budget_bytes=64 << 30, max_active=64, steps_per_round=8):
+    def __init__(self, device=0, hbm_budget_bytes=64 << 30, max_active=64, steps_per_round=8, min_batch=0):
         h = C.c_void_p()
         _check(None, lib().pic_server_create(device, hbm_budget_bytes, max_active, steps_per_round, C.byref(h)))
         self.h = h
         self._specs = {}
+        if min_batch:
+            self.set_batching(min_batch)
+
+    def set_batching(self, min_batch: int):
+        """Step idle active runs of one kind as batches of at least min_batch
+        runs (0: off); see pic_server_set_batching."""
+        _check(None, lib().pic_server_set_batching(self.h, min_batch))
 
     def submit(self, spec: pic_run_spec) -> int:
         t = C.c_uint64()

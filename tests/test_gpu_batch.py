@@ -192,3 +192,15 @@ def test_batch_rejects_mixed_kinds():
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("lanes", [1, 2, 5])
+def test_lane_counts_give_the_same_results(lanes, monkeypatch):
+    """Unsheared batches run their boxes in lanes (chains of batched launches
+    on streams of their own); any lane count gives the boxes-alone results."""
+    monkeypatch.setenv("PIC_BATCH_LANES", str(lanes))
+    cases = [dataclasses.replace(EXPAND[k % 3], name=f"x{k}", seed=200 + k, ppc=2 + k % 4) for k in range(7)]
+    got = run_batched(cases, 7, False, chunks=[1, 6])
+    for c, g in zip(cases, got):
+        assert_same(g, run_alone(c, 7, False), exact=True)

@@ -193,3 +193,68 @@ def test_a_served_run_matches_the_oracle():
     for a, r in ((E, st.E), (B, st.B), (J, st.J)):
         floor = jref if a is J else 4 * np.pi * jref
         assert np.abs(a - r).max() <= 2e-6 * max(np.abs(r).max(), floor)
+
+
+def _kinds_mix():
+    """Three runs each of three kinds, with different grids, loads and step
+    counts, so that cohorts form, dissolve as their shortest runs finish and
+    regroup."""
+    XY, XZ = P.PIC_PLANE_XY, P.PIC_PLANE_XZ
+    specs = []
+    for k, (n, steps) in enumerate(((16, 12), (24, 20), (16, 27))):
+        specs.append(P.make_run_spec(P.make_config(box=P.PIC_BOX_EXPAND, nx=n, ny=n, nz=n, order=2,
+                                                   precision=P.PIC_FP32, rate=(0, 1e-3, 1e-3)), steps, 6 + k, 0.05,
+                                     q=(-0.05, 0.05), B0=(0.2, 0.2, 0), load_seed=20 + k))
+        specs.append(P.make_run_spec(P.make_config(box=P.PIC_BOX_LEAKY, ndim=2, plane=XY, nx=2 * n, ny=2 * n, nz=1,
+                                                   order=1, precision=P.PIC_FP32,
+                                                   escape_mode=P.PIC_ESC_PROBABILISTIC, p_esc=0.02, theta_inj=1.0,
+                                                   seed=30 + k), steps + 3, 8, 1.0, q=(-0.05, 0.05),
+                                     B0=(0, 0, 0.2), load_seed=30 + k))
+        specs.append(P.make_run_spec(P.make_config(box=P.PIC_BOX_SHEAR, ndim=2, plane=XZ, nx=2 * n, ny=1, nz=2 * n,
+                                                   order=1, precision=P.PIC_FP32, s=1.5, Omega0=2e-3), steps + 1,
+                                     8, 0.1, q=(-0.05, 0.05), B0=(0, 0, 0.3), load_seed=40 + k))
+    return specs
+
+
+@pytest.mark.gpu
+def test_batched_serving_equals_the_runs_stepped_alone():
+    """With batching on, idle runs of one kind are stepped as batches
+    (cohorts); every served run's final particles and fields still equal the
+    same run stepped alone, bit for bit."""
+    specs = _kinds_mix()
+    for s in specs:
+        s.keep_state = 1
+    # cohorts take runs with at least 4 x steps_per_round = 8 steps left
+    with P.Server(hbm_budget_bytes=1 << 36, max_active=16, steps_per_round=2, min_batch=2) as srv:
+        tickets = [srv.submit(s) for s in specs]
+        srv.wait(0, 300)
+        assert srv.stats().cohorts_formed >= 3
+        served = []
+        for t, s in zip(tickets, specs):
+            d, _ = srv.poll(t)
+            assert d.step == s.nsteps
+            b = srv.take(t)
+            served.append(_state(b, s.nspecies))
+            b.close()
+    for s, (sp_s, f_s) in zip(specs, served):
+        box = _alone(s)
+        box.step(s.nsteps)
+        sp_a, f_a = _state(box, s.nspecies)
+        box.close()
+        for (xs, us, is_, ds), (xa, ua, ia, da) in zip(sp_s, sp_a):
+            np.testing.assert_array_equal(is_, ia)
+            np.testing.assert_array_equal(xs, xa)
+            np.testing.assert_array_equal(us, ua)
+            np.testing.assert_array_equal(ds, da)
+        for a, b in zip(f_s, f_a):
+            np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.gpu
+def test_batching_argument_checks():
+    with P.Server(hbm_budget_bytes=1 << 30, max_active=2) as srv:
+        for bad in (-1, 1):
+            with pytest.raises(P.PicError):
+                srv.set_batching(bad)
+        srv.set_batching(0)
+        srv.set_batching(4)
