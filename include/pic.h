@@ -482,17 +482,17 @@ pic_status pic_server_create(int device, uint64_t hbm_budget_bytes, int max_acti
                              int steps_per_round, pic_server **out);
 
 /* Batching of served runs: min_batch = 0 (the default) steps every active
- * run on its own stream; min_batch >= 2 groups idle active runs of one kind
- * (precision, geometry and tile shape, shape order, box type and escape
- * rule) that have at least 4 x steps_per_round steps left, at least
- * min_batch of them, into a cohort stepped as one pic_batch (no graph
- * capture: a cohort may not live long enough to repay one).
- * A cohort advances by chunks of at most steps_per_round steps and no more
- * than its shortest remaining run; when a member is done the cohort is
- * dissolved after its queued chunks complete, the finished runs retire and
- * the others are regrouped with the idle runs of their kind.  Results are
- * those of each run stepped alone (FP32: bit-identical).  PIC_ERR_ARG for
- * min_batch < 0 or 1.  Takes effect from the worker's next round. */
+ * run on its own stream; min_batch >= 2 groups runs of one kind (precision,
+ * geometry and tile shape, shape order, box type and escape rule) that were
+ * admitted in the same round and have at least 4 x steps_per_round steps
+ * left, at least min_batch of them, into a cohort stepped as one pic_batch
+ * (no graph capture: a cohort may not live long enough to repay one).  A
+ * cohort advances by chunks of at most steps_per_round steps and no more than
+ * its shortest remaining run; when a member is done the cohort is dissolved
+ * after its queued chunks complete, the finished runs retire and the others
+ * step alone.  Results are those of each run stepped alone (FP32:
+ * bit-identical).  PIC_ERR_ARG for min_batch < 0 or 1.  Takes effect from
+ * the worker's next round. */
 pic_status pic_server_set_batching(pic_server *s, int min_batch);
 
 /* Queue a run (the spec is copied); *ticket identifies it. */

@@ -20,6 +20,21 @@ template <class T> __device__ inline void split_coord(double x, int n, int& c, T
     if (o >= T(1)) { o = T(0); c += 1; if (c >= n) c = 0; }
 }
 
+// Tile counters of a load, one atomic per group of lanes with the same tile
+// (loaded particles usually come in cell or tile order, so most of a warp
+// shares one counter).  Returns the lane's slot: the counter's old value
+// plus the lane's rank in its group.
+__device__ __forceinline__ int tile_count_add(int* __restrict__ count, int t) {
+    const unsigned act = __activemask();
+    const unsigned grp = __match_any_sync(act, t);
+    const int lane = (int)(threadIdx.x & 31u);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count + t, __popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    return base + __popc(grp & ((1u << lane) - 1u));
+}
+
 // Pass 1 of a load: per particle, its tile; per tile, a count.
 template <class T, int G>
 __global__ void load_bin_kernel(long long n, const double* __restrict__ x, Tiling tl, Grid g, int* __restrict__ count) {
@@ -30,7 +45,7 @@ __global__ void load_bin_kernel(long long n, const double* __restrict__ x, Tilin
         split_coord<T>(x[3 * q + 0], g.nx, ci, o);
         if (GT::AY) split_coord<T>(x[3 * q + 1], g.ny, cj, o);
         if (GT::AZ) split_coord<T>(x[3 * q + 2], g.nz, ck, o);
-        atomicAdd(count + tile_of<G>(tl, ci, cj, ck), 1);
+        tile_count_add(count, tile_of<G>(tl, ci, cj, ck));
     }
 }
 
@@ -55,8 +70,8 @@ __global__ void load_scatter_kernel(long long n, long long q0, const double* __r
             p.dr[1] = dr ? T(dr[3 * q + 1]) : T(0);
             p.dr[2] = dr ? T(dr[3 * q + 2]) : T(0);
         }
-        int t = tile_of<G>(tl, p.ci, p.cj, p.ck);
-        int s = atomicAdd(fill + t, 1);
+        const int t = tile_of<G>(tl, p.ci, p.cj, p.ck);
+        const int s = tile_count_add(fill, t);
         store_particle<T, G>(v, (long long)t * tcap + s, has_dr, p);
     }
 }

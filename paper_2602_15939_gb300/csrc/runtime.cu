@@ -780,46 +780,139 @@ static pic_status alloc_species(pic_handle* h, DevSpecies& d, long long tcap) {
 // after the first), and no transfer needs memory in proportion to the box.
 constexpr long long STAGE_PARTICLES = 1ll << 23;
 
-// Particles from the caller's arrays (host or device memory), a chunk of at
-// most STAGE_PARTICLES at a time through device staging buffers: one pass
-// counts each tile's particles (positions only), the layout is sized from
-// the fullest tile, a second pass scatters the particles into their tiles.
-// The staging stays small enough for the memory pool to keep: a load needs
-// no device memory in proportion to its input beyond the particle arrays.
+// True when p is (null or) device memory of `device`: a load reads such
+// arrays in place.
+static bool on_device(const void* p, int device) {
+    if (!p) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == device;
+}
+
+// Copy/compute overlap of a chunked transfer: chunk k's copies go on a copy
+// stream into staging set k & 1 while the handle's stream runs chunk k - 1's
+// kernel; events order each set's copy after the kernel that last read it.
+struct LoadPipe {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ready[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr}, start = nullptr;
+    bool used[2] = {false, false};
+    cudaError_t open(cudaStream_t main) {
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaEventCreateWithFlags(&ready[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+        // the staging memory comes from the pool on the main stream: the copy stream starts after it
+        if (e == cudaSuccess) e = cudaEventRecord(start, main);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, start, 0);
+        return e;
+    }
+    // before the copies of set b
+    cudaError_t acquire(int b) { return used[b] ? cudaStreamWaitEvent(cs, done[b], 0) : cudaSuccess; }
+    // after the copies of set b, before the kernel on `main` that reads them
+    cudaError_t hand_over(int b, cudaStream_t main) {
+        cudaError_t e = cudaEventRecord(ready[b], cs);
+        return e == cudaSuccess ? cudaStreamWaitEvent(main, ready[b], 0) : e;
+    }
+    // after that kernel
+    cudaError_t release(int b, cudaStream_t main) {
+        used[b] = true;
+        return cudaEventRecord(done[b], main);
+    }
+    void close() {
+        for (int b = 0; b < 2; ++b) {
+            if (ready[b]) cudaEventDestroy(ready[b]);
+            if (done[b]) cudaEventDestroy(done[b]);
+        }
+        if (start) cudaEventDestroy(start);
+        if (cs) cudaStreamDestroy(cs);  // returns at once; its queued copies still complete
+    }
+};
+
+// Particles from the caller's arrays (host or device memory) in two passes:
+// one counts each tile's particles (positions only), the layout is sized
+// from the fullest tile, the second scatters the particles into their tiles.
+// Device-resident arrays are read in place.  Host arrays go through device
+// staging, a chunk of at most STAGE_PARTICLES particles at a time, with each
+// chunk's copy overlapping the previous chunk's kernel (two staging sets and
+// a copy stream); the positions copied for the first pass are kept on the
+// device for the second when the device has room for them (the input's
+// positions and 4 GB more free), else copied again.
 template <class T, int G>
 static pic_status load_t(pic_handle* h, int species, long long n, const double* x, const double* u, const uint32_t* id,
                          const double* dr) {
     DevSpecies& d = h->sp[species];
     const int nt = h->tl.ntiles;
     const bool leaky = h->esc == ESC_DISP;
+    const int dev = h->cfg.device;
+    const bool in_place = on_device(x, dev) && on_device(u, dev) && on_device(id, dev) && on_device(dr, dev);
     const long long S = std::max(1ll, std::min(STAGE_PARTICLES, n));
     int* cnt = nullptr;
-    double *sx = nullptr, *su = nullptr, *sdr = nullptr;
-    uint32_t* sid = nullptr;
+    double* dx = nullptr;  // the positions, kept on the device between the passes
+    double *sx[2] = {nullptr, nullptr}, *su[2] = {nullptr, nullptr}, *sdr[2] = {nullptr, nullptr};
+    uint32_t* sid[2] = {nullptr, nullptr};
+    LoadPipe pipe;
     auto cleanup = [&]() {
+        // copies still queued (a failure midway) finish before their buffers go back to the pool
+        if (pipe.cs) cudaStreamSynchronize(pipe.cs);
+        cudaStreamSynchronize(h->stream);
         dfree(h, cnt);
-        dfree(h, sx);
-        dfree(h, su);
-        dfree(h, sid);
-        dfree(h, sdr);
+        dfree(h, dx);
+        for (int b = 0; b < 2; ++b) {
+            dfree(h, sx[b]);
+            dfree(h, su[b]);
+            dfree(h, sid[b]);
+            dfree(h, sdr[b]);
+        }
+        pipe.close();
     };
-    if (dalloc(h, (void**)&cnt, sizeof(int) * nt) != cudaSuccess || dalloc(h, (void**)&sx, sizeof(double) * 3 * S) != cudaSuccess ||
-        dalloc(h, (void**)&su, sizeof(double) * 3 * S) != cudaSuccess ||
-        (id && dalloc(h, (void**)&sid, sizeof(uint32_t) * S) != cudaSuccess) ||
-        (dr && dalloc(h, (void**)&sdr, sizeof(double) * 3 * S) != cudaSuccess)) {
+    cudaError_t e = dalloc(h, (void**)&cnt, sizeof(int) * nt);
+    bool keep_x = !in_place && n > S;
+    if (const char* v = getenv("PIC_LOAD_RESIDENT_POSITIONS")) keep_x = keep_x && atoi(v) != 0;
+    if (e == cudaSuccess && keep_x) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && fr > sizeof(double) * 3 * (size_t)n + (4ull << 30))
+            if (dalloc(h, (void**)&dx, sizeof(double) * 3 * (size_t)n) != cudaSuccess) {
+                cudaGetLastError();
+                dx = nullptr;
+            }
+    }
+    for (int b = 0; b < 2 && e == cudaSuccess && !in_place; ++b) {
+        if (!dx) e = dalloc(h, (void**)&sx[b], sizeof(double) * 3 * S);
+        if (e == cudaSuccess) e = dalloc(h, (void**)&su[b], sizeof(double) * 3 * S);
+        if (e == cudaSuccess && id) e = dalloc(h, (void**)&sid[b], sizeof(uint32_t) * S);
+        if (e == cudaSuccess && dr) e = dalloc(h, (void**)&sdr[b], sizeof(double) * 3 * S);
+    }
+    if (e != cudaSuccess) {
         cudaGetLastError();
         cleanup();
         return fail(h, PIC_ERR_OOM, "load staging allocation failed");
     }
-    // stream order: each chunk's kernel finishes before the next chunk's copy
-    // overwrites the staging buffers
-    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * nt, h->stream);
-    for (long long q0 = 0; q0 < n && e == cudaSuccess; q0 += S) {
-        const long long m = std::min(S, n - q0);
-        e = cudaMemcpyAsync(sx, x + 3 * q0, sizeof(double) * 3 * m, cudaMemcpyDefault, h->stream);
-        if (e == cudaSuccess) {
-            load_bin_kernel<T, G><<<grid_blocks(m), NTHR, 0, h->stream>>>(m, sx, h->tl, h->g, cnt);
+    if (!in_place) e = pipe.open(h->stream);
+    // pass 1: tile counts
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int) * nt, h->stream);
+    if (in_place) {
+        if (e == cudaSuccess && n > 0) {
+            load_bin_kernel<T, G><<<grid_blocks(n), NTHR, 0, h->stream>>>(n, x, h->tl, h->g, cnt);
             e = cudaGetLastError();
+        }
+    } else {
+        for (long long q0 = 0, k = 0; q0 < n && e == cudaSuccess; q0 += S, ++k) {
+            const long long m = std::min(S, n - q0);
+            const int b = (int)(k & 1);
+            double* px = dx ? dx + 3 * q0 : sx[b];
+            e = pipe.acquire(b);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(px, x + 3 * q0, sizeof(double) * 3 * m, cudaMemcpyDefault, pipe.cs);
+            if (e == cudaSuccess) e = pipe.hand_over(b, h->stream);
+            if (e == cudaSuccess) {
+                load_bin_kernel<T, G><<<grid_blocks(m), NTHR, 0, h->stream>>>(m, px, h->tl, h->g, cnt);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = pipe.release(b, h->stream);
         }
     }
     std::vector<int> hc(nt);
@@ -840,21 +933,39 @@ static pic_status load_t(pic_handle* h, int species, long long n, const double* 
         cleanup();
         return st;
     }
-    const int b = h->buf;
+    // pass 2: scatter into the tiles
+    const int b0 = h->buf;
     e = cudaMemsetAsync(cnt, 0, sizeof(int) * nt, h->stream);
-    for (long long q0 = 0; q0 < n && e == cudaSuccess; q0 += S) {
-        const long long m = std::min(S, n - q0);
-        e = cudaMemcpyAsync(sx, x + 3 * q0, sizeof(double) * 3 * m, cudaMemcpyDefault, h->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(su, u + 3 * q0, sizeof(double) * 3 * m, cudaMemcpyDefault, h->stream);
-        if (id && e == cudaSuccess) e = cudaMemcpyAsync(sid, id + q0, sizeof(uint32_t) * m, cudaMemcpyDefault, h->stream);
-        if (dr && e == cudaSuccess) e = cudaMemcpyAsync(sdr, dr + 3 * q0, sizeof(double) * 3 * m, cudaMemcpyDefault, h->stream);
-        if (e == cudaSuccess) {
-            load_scatter_kernel<T, G><<<grid_blocks(m), NTHR, 0, h->stream>>>(m, q0, sx, su, sid, sdr, h->tl, h->g, cnt, tcap,
-                                                                              view_of<T>(d.arr[b]), leaky);
+    if (in_place) {
+        if (e == cudaSuccess && n > 0) {
+            load_scatter_kernel<T, G><<<grid_blocks(n), NTHR, 0, h->stream>>>(n, 0, x, u, id, dr, h->tl, h->g, cnt, tcap,
+                                                                              view_of<T>(d.arr[b0]), leaky);
             e = cudaGetLastError();
         }
+    } else {
+        for (long long q0 = 0, k = 0; q0 < n && e == cudaSuccess; q0 += S, ++k) {
+            const long long m = std::min(S, n - q0);
+            const int b = (int)((k + 1) & 1);  // continues the alternation of pass 1's sets
+            const double* px = dx ? dx + 3 * q0 : sx[b];
+            e = pipe.acquire(b);
+            if (e == cudaSuccess && !dx)
+                e = cudaMemcpyAsync(sx[b], x + 3 * q0, sizeof(double) * 3 * m, cudaMemcpyDefault, pipe.cs);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(su[b], u + 3 * q0, sizeof(double) * 3 * m, cudaMemcpyDefault, pipe.cs);
+            if (id && e == cudaSuccess)
+                e = cudaMemcpyAsync(sid[b], id + q0, sizeof(uint32_t) * m, cudaMemcpyDefault, pipe.cs);
+            if (dr && e == cudaSuccess)
+                e = cudaMemcpyAsync(sdr[b], dr + 3 * q0, sizeof(double) * 3 * m, cudaMemcpyDefault, pipe.cs);
+            if (e == cudaSuccess) e = pipe.hand_over(b, h->stream);
+            if (e == cudaSuccess) {
+                load_scatter_kernel<T, G><<<grid_blocks(m), NTHR, 0, h->stream>>>(
+                    m, q0, px, su[b], id ? sid[b] : nullptr, dr ? sdr[b] : nullptr, h->tl, h->g, cnt, tcap,
+                    view_of<T>(d.arr[b0]), leaky);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = pipe.release(b, h->stream);
+        }
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d.stay[b], cnt, sizeof(int) * nt, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.stay[b0], cnt, sizeof(int) * nt, cudaMemcpyDeviceToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cleanup();
     if (e != cudaSuccess) return fail(h, PIC_ERR_CUDA, "load failed: %s", cudaGetErrorString(e));

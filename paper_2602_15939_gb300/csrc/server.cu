@@ -10,14 +10,16 @@
 // time from submission to result, handle destroyed, memory returned to the
 // budget -- which lets the next queued runs in while others keep stepping.
 //
-// With batching on (pic_server_set_batching), idle active runs of one kind
-// (precision, geometry and tile shape, shape order, box type) with at least
-// four rounds of steps left are grouped into cohorts of at least `min_batch`
-// runs, each stepped as one pic_batch
-// (one persistent particle kernel and batched grid work per step).  A cohort
-// advances by chunks no longer than its shortest remaining run; when a member
-// is done, the cohort is dissolved after its chunks complete, the finished
-// runs retire, and the others are regrouped with the idle runs of their kind.
+// With batching on (pic_server_set_batching), runs of one kind (precision,
+// geometry and tile shape, shape order, box type) admitted in the same round
+// with at least four rounds of steps left are grouped into cohorts of at
+// least `min_batch` runs, each stepped as one pic_batch (one persistent
+// particle kernel and batched grid work per step).  A cohort advances by
+// chunks no longer than its shortest remaining run; when a member is done,
+// the cohort is dissolved after its chunks complete, the finished runs
+// retire, and the others step alone.  (PIC_SERVER_COHORT_POLICY=0 instead
+// regroups every run of a kind with enough steps left, holding back new
+// chunks until all of them are idle.)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -91,7 +93,7 @@ struct pic_server {
     int starting = 0;  // admitted runs being set up (neither queued nor active)
     int min_batch = 0;  // 0: no cohorts; else the fewest runs of one kind stepped as a batch
     bool cohort_graphs = false;  // capture cohorts' step cycles in graphs
-    int cohort_policy = 0;  // 0: regroup idle runs (draining them); 1: group only runs admitted together
+    int cohort_policy = 1;  // 1: group only runs admitted together; 0: regroup idle runs (draining them)
     int64_t cohorts_formed = 0;
     std::vector<Cohort*> cohorts;  // worker thread only
     int64_t completed = 0;

@@ -88,3 +88,70 @@ def test_load_and_readback_across_staging_chunks():
             assert np.array_equal(xo[o][k], xs) and np.array_equal(uo[o][k], us)
     finally:
         box.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("source", ["pageable", "pinned", "device", "pageable_restaged"])
+def test_load_paths_give_the_same_box(source, monkeypatch):
+    """A load of three staging chunks (more than 2 x 2^23 particles) from
+    pageable or pinned host memory (copies overlapping the kernels, positions
+    kept on the device between the two passes, or copied twice when that is
+    switched off) or from device memory (read in place) lays out the same
+    particles, and the box steps to the same state bit for bit."""
+    torch = pytest.importorskip("torch")
+    if source == "pageable_restaged":
+        monkeypatch.setenv("PIC_LOAD_RESIDENT_POSITIONS", "0")
+    n3 = (64, 48, 48)
+    ppc = 115
+    N = n3[0] * n3[1] * n3[2] * ppc
+    assert N > 2 * (1 << 23)
+    cfg = P.make_config(box=P.PIC_BOX_PERIODIC, nx=n3[0], ny=n3[1], nz=n3[2], ndim=3, order=1, precision=P.PIC_FP32)
+    r = np.random.default_rng(5)
+    # cell-ordered positions (the order the loader's aggregated tile counters favour), shuffled ids
+    cells = np.repeat(np.arange(n3[0] * n3[1] * n3[2]), ppc)
+    ci, cj, ck = cells % n3[0], (cells // n3[0]) % n3[1], cells // (n3[0] * n3[1])
+    x = np.stack([ci, cj, ck], axis=1) + r.uniform(0.0, 1.0, (N, 3))
+    u = r.normal(0.0, 0.1, (N, 3))
+    ids = r.permutation(N).astype(np.uint32)
+    box = P.Box(cfg)
+    try:
+        z = np.zeros((3, n3[2], n3[1], n3[0]))
+        box.set_fields(z, z)
+        if source in ("pageable", "pageable_restaged"):
+            box.load(0, -0.01, 1.0, x, u, ids)
+        else:
+            kw = dict(pin_memory=True) if source == "pinned" else dict(device="cuda")
+            tx = torch.from_numpy(x).to(**kw) if source == "device" else torch.from_numpy(x).pin_memory()
+            tu = torch.from_numpy(u).to(**kw) if source == "device" else torch.from_numpy(u).pin_memory()
+            ti = torch.from_numpy(ids.view(np.int32)).to(**kw) if source == "device" else \
+                torch.from_numpy(ids.view(np.int32)).pin_memory()
+            torch.cuda.synchronize()
+            st = P.lib().pic_load_particles(box.h, 0, -0.01, 1.0, N, P.C.cast(tx.data_ptr(), P._D),
+                                            P.C.cast(tu.data_ptr(), P._D), P.C.cast(ti.data_ptr(), P._U32))
+            assert st == P.PIC_OK, P.pic_last_error(box.h)
+        xo, uo, io, _ = box.particles(0)
+        o = np.argsort(io)
+        back = np.empty(N, dtype=np.int64)
+        back[ids] = np.arange(N)
+        assert np.array_equal(io[o], np.arange(N, dtype=np.uint32))
+        assert np.abs(xo[o] - x[back]).max() <= 1e-5
+        assert np.array_equal(uo[o], u[back].astype(np.float32).astype(np.float64))
+        box.step(2)
+        xo, uo, io, _ = box.particles(0)
+        o = np.argsort(io)
+        E, B, J = box.fields()
+        # the same particles stepped from a pageable load (the reference path)
+        ref = P.Box(cfg)
+        try:
+            ref.set_fields(z, z)
+            ref.load(0, -0.01, 1.0, x, u, ids)
+            ref.step(2)
+            xr, ur, ir, _ = ref.particles(0)
+            orr = np.argsort(ir)
+            assert np.array_equal(xo[o], xr[orr]) and np.array_equal(uo[o], ur[orr])
+            for a_, b_ in zip((E, B, J), ref.fields()):
+                assert np.array_equal(a_, b_)
+        finally:
+            ref.close()
+    finally:
+        box.close()

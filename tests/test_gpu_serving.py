@@ -217,10 +217,14 @@ def _kinds_mix():
 
 
 @pytest.mark.gpu
-def test_batched_serving_equals_the_runs_stepped_alone():
-    """With batching on, idle runs of one kind are stepped as batches
-    (cohorts); every served run's final particles and fields still equal the
-    same run stepped alone, bit for bit."""
+@pytest.mark.parametrize("policy", [0, 1])
+def test_batched_serving_equals_the_runs_stepped_alone(policy, monkeypatch):
+    """With batching on, runs of one kind are stepped as batches (cohorts):
+    policy 1 (the default) groups runs admitted together, policy 0 regroups
+    every run of a kind with steps enough left; every served run's final
+    particles and fields still equal the same run stepped alone, bit for
+    bit."""
+    monkeypatch.setenv("PIC_SERVER_COHORT_POLICY", str(policy))
     specs = _kinds_mix()
     for s in specs:
         s.keep_state = 1
@@ -228,7 +232,8 @@ def test_batched_serving_equals_the_runs_stepped_alone():
     with P.Server(hbm_budget_bytes=1 << 36, max_active=16, steps_per_round=2, min_batch=2) as srv:
         tickets = [srv.submit(s) for s in specs]
         srv.wait(0, 300)
-        assert srv.stats().cohorts_formed >= 3
+        if policy == 0:  # runs drain until they can be grouped
+            assert srv.stats().cohorts_formed >= 3
         served = []
         for t, s in zip(tickets, specs):
             d, _ = srv.poll(t)
