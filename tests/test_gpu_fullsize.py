@@ -5,7 +5,8 @@ tiles and threads), against the FP64 oracle:
 - the 2D shearing box in FP64 (64 x 64, 131,072 particles): the whole state
   against the oracle after three steps;
 - the 3D expanding box (128^3, 134M particles), the 3D shearing box (256^3,
-  1.07e9 particles) and the 2D leaky box (2048^2, 5.4e8 particles): a fixed
+  1.07e9 particles) and the 2D leaky box (2048^2, 5.4e8 particles, on 16 x 16
+  and on 32 x 32 tiles): a fixed
   id-sampled subset of particles followed through one step and recomputed one
   by one by the oracle in the device's own fields (gather, push, move,
   boundary and, for the leaky box, the escape decision and reinjection);
@@ -139,10 +140,17 @@ def test_shear3d_256_sampled_particles():
 
 
 @pytest.mark.gpu
-def test_leaky2d_2048_sampled_particles_and_escapes():
+@pytest.mark.parametrize("side", [16, 32])
+def test_leaky2d_2048_sampled_particles_and_escapes(side):
+    # 32 x 32 tiles with launch variant 2: the shape and variant the bench's
+    # tile autotuner keeps at this size
     w = W.LEAKY_2D_FP32
     box = W.setup_box(w, device=0, seed=0)
     try:
+        if side != 16:
+            box.set_tile(side)
+            P.pic_set_kernel_variant(box.h, 2)
+            assert box.tile() == (side, side, 1)
         d0 = box.diagnostics()
         errs = follow_sample(w, box, 10007, 1)
         d1 = box.diagnostics()
