@@ -723,9 +723,12 @@ def run_e2e(w, device, stream, steps, rank):
         P._check(box.h, lib.pic_load_particles(box.h, s, q, 1.0, len(tx), P.C.cast(tx.data_ptr(), P._D),
                                                P.C.cast(tu.data_ptr(), P._D), P.C.cast(ti.data_ptr(), P._U32)))
     box.set_uniform_fields((0.0, 0.0, 0.0), w.b0())
+    box.sync()
+    t1 = time.perf_counter()
     for _ in range(steps):
         box.step(1)
         box.diagnostics()
+    t2 = time.perf_counter()
     got = 0
     for s, (ox, ou, oi) in enumerate(outs):
         n_out = P.C.c_int64()
@@ -734,12 +737,14 @@ def run_e2e(w, device, stream, steps, rank):
                                                       None, P.C.byref(n_out)))
         got += min(n_out.value, nsamp)
     box.sync()
-    dt = time.perf_counter() - t0
+    t3 = time.perf_counter()
+    dt = t3 - t0
     box.close()
     h2d = sum(tx.numel() * 8 + tu.numel() * 8 + ti.numel() * 4 for _, tx, tu, ti in pinned)
     d2h = got * (8 * 6 + 4) + steps * P.C.sizeof(P.pic_diag)
     return {"value": npart * steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
             "d2h_bytes_per_step": d2h / steps, "steps": steps, "seconds": dt,
+            "phases_s": {"load_and_fields": t1 - t0, "steps_with_diagnostics": t2 - t1, "sampled_readback": t3 - t2},
             "includes": "pic_load_particles of the whole state from pinned host memory, per step pic_step + "
                         "pic_diagnostics, final pic_get_particles_sampled (1 in 256 ids)"}
 
