@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--serving-only", type=int, default=-1, help=argparse.SUPPRESS)
     ap.add_argument("--seed", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--tile", type=int, default=0,
-                    help="2D FP32 particle tile side (16 or 32); 0 = autotune with the variant")
+                    help="2D particle tile side (8, 16, or 32 in FP32); 0 = autotune with the variant")
     ap.add_argument("--variant", type=int, default=0,
                     help="particle-kernel variant (1-based); 0 = autotune on the box after warm-up")
     return ap.parse_args()
@@ -355,11 +355,12 @@ def measure(w, args, device, stream, rank, world, headline):
     if args.variant:
         P.pic_set_kernel_variant(box.h, args.variant)
         tune = {"chosen": args.variant, "how": "forced"}
-    elif w.ndim == 2 and not w.fp64 and not args.tile:
+    elif w.ndim == 2 and not args.tile:
         side, ms_side = box.autotune_tile(4 if headline or w.n_particles > 1e8 else 2)
         tune = {"chosen": P.pic_get_kernel_variant(box.h),
                 "how": "tile shape, then launch variant per shape, autotuned on untimed steps",
-                "tile_ms_per_step": {"16": round(ms_side[0], 4), "32": round(ms_side[1], 4)}}
+                "tile_ms_per_step": {str(k): (None if v is None else round(v, 4))
+                                     for k, v in zip((8, 16, 32), ms_side)}}
     else:
         best, ms_v, taken = box.autotune(4 if headline or w.n_particles > 1e8 else 2)
         tune = {"chosen": best, "how": f"autotuned on {taken} untimed steps",

@@ -97,9 +97,9 @@ typedef struct pic_config {
     int32_t escape_mode;  /* leaky box: PIC_ESC_* */
     int32_t escape_dims;  /* leaky displacement test over (x,y) [2] or (x,y,z) [3] */
     int32_t tile[3];      /* particle tile in cells per axis; 0 = automatic.  3D: 8x8x8.
-                             2D: 16x16 (the automatic choice) or, FP32 only, 32x32 on the
-                             active plane (the ignorable axis' entry is not read); other
-                             shapes are PIC_ERR_ARG.  See pic_autotune_tile. */
+                             2D: 16x16 (the automatic choice), 8x8 or, FP32 only, 32x32 on
+                             the active plane (the ignorable axis' entry is not read);
+                             other shapes are PIC_ERR_ARG.  See pic_autotune_tile. */
     int32_t device;       /* CUDA device ordinal the handle lives on */
     uint32_t seed;        /* key word of the Philox streams (escape, reinjection, loading) */
     uint32_t kernel_variant; /* particle-kernel launch shape: 0 = automatic (the tuned choice
@@ -371,8 +371,8 @@ pic_status pic_autotune(pic_handle *h, int32_t trial_steps, int32_t *best, doubl
                         int64_t *steps_taken);
 
 /* Particle tiles (no counterpart in the paper).  pic_get_tile: the tile in
- * cells per axis (1 on the ignorable axis).  pic_set_tile (2D: side 16, or 32
- * in FP32; 3D: 8): re-lay the particles out in side x side tiles.  Every
+ * cells per axis (1 on the ignorable axis).  pic_set_tile (2D: side 8, 16, or
+ * 32 in FP32; 3D: 8): re-lay the particles out in side x side tiles.  Every
  * species is read out into flat device arrays (cell + offset in FP64, which
  * holds FP32 state exactly), its arrays are freed and it is loaded again
  * under the new tiling, so the particles and every later result are
@@ -381,12 +381,13 @@ pic_status pic_autotune(pic_handle *h, int32_t trial_steps, int32_t *best, doubl
  * largest species); PIC_ERR_OOM leaves the tiling as it was, PIC_ERR_STATE
  * for a batched box.  Synchronizes the handle's stream; drops its captured
  * step graphs.
- * pic_autotune_tile (2D FP32 boxes; PIC_ERR_ARG otherwise): for 16x16 and
- * then 32x32 tiles, switch to them, run pic_autotune(trial_steps) for their
- * best launch variant, then one untimed and trial_steps timed ordinary steps
- * (all kernels, CUDA events); keep the tiles and variant with the least time
- * per step.  The trial steps advance the simulation like pic_step.  Outputs
- * (nullable): *best_side and ms_per_side[2] (16, 32). */
+ * pic_autotune_tile (2D boxes; PIC_ERR_ARG in 3D): for 8x8, 16x16 and (FP32)
+ * 32x32 tiles in turn, switch to them, run pic_autotune(trial_steps) for
+ * their best launch variant, then one untimed and trial_steps timed ordinary
+ * steps (all kernels, CUDA events); keep the tiles and variant with the least
+ * time per step.  The trial steps advance the simulation like pic_step.
+ * Outputs (nullable): *best_side and ms_per_side[3] (8, 16, 32; -1 for a side
+ * not tried). */
 pic_status pic_get_tile(pic_handle *h, int32_t tile[3]);
 pic_status pic_set_tile(pic_handle *h, int32_t side);
 pic_status pic_autotune_tile(pic_handle *h, int32_t trial_steps, int32_t *best_side, double *ms_per_side);

@@ -16,14 +16,27 @@ namespace pic {
 constexpr int GL = 2;  // low guard cells
 constexpr int GR = 3;  // high guard cells (deposits reach node n+2)
 
-// geometry kinds: which axes are active.  G2XY_W and G2XZ_W are the 2D
-// planes again, with 32 x 32-cell particle tiles instead of 16 x 16 (a
-// template geometry: the grid and field code is that of the plane).
-enum Geom : int { G3D = 0, G2XY = 1, G2XZ = 2, G2XY_W = 3, G2XZ_W = 4 };
-constexpr int N_TGEOM = 5;
-__host__ __device__ constexpr int plane_of(int G) { return G == G2XY_W ? G2XY : (G == G2XZ_W ? G2XZ : G); }
+// geometry kinds: which axes are active.  G2XY_W / G2XZ_W and G2XY_S /
+// G2XZ_S are the 2D planes again, with 32 x 32- and 8 x 8-cell particle
+// tiles instead of 16 x 16 (template geometries: the grid and field code is
+// that of the plane).
+enum Geom : int { G3D = 0, G2XY = 1, G2XZ = 2, G2XY_W = 3, G2XZ_W = 4, G2XY_S = 5, G2XZ_S = 6 };
+constexpr int N_TGEOM = 7;
+__host__ __device__ constexpr int plane_of(int G) {
+    return (G == G2XY_W || G == G2XY_S) ? G2XY : ((G == G2XZ_W || G == G2XZ_S) ? G2XZ : G);
+}
 // particle tile side in cells (per active axis) of a template geometry
-__host__ __device__ constexpr int tile_side(int G) { return G == G3D ? 8 : ((G == G2XY_W || G == G2XZ_W) ? 32 : 16); }
+__host__ __device__ constexpr int tile_side(int G) {
+    return (G == G3D || G == G2XY_S || G == G2XZ_S) ? 8 : ((G == G2XY_W || G == G2XZ_W) ? 32 : 16);
+}
+// the template geometry of a geometry (G3D, G2XY, G2XZ) with tiles of `side` cells
+__host__ __device__ constexpr int tgeom_of(int geom, int side) {
+    return geom == G3D ? G3D
+           : side == 32 ? (geom == G2XY ? G2XY_W : G2XZ_W)
+           : side == 8 ? (geom == G2XY ? G2XY_S : G2XZ_S) : geom;
+}
+// template geometries with kernels for a precision (32 x 32 tiles: FP32 only)
+__host__ __device__ constexpr bool tgeom_built(int tg, bool fp64) { return !(fp64 && (tg == G2XY_W || tg == G2XZ_W)); }
 // particle pusher kinds
 enum Push : int { PUSH_BORIS = 0, PUSH_KSB = 1, PUSH_KEB = 2, PUSH_SXE = 3 /* shearing + expanding */ };
 // escape kinds (leaky box)

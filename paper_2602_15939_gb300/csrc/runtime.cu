@@ -85,14 +85,23 @@ template <class T, int G> static size_t tile_smem_bytes_t(int v) {
 
 // tg: template geometry (Geom; the 32 x 32-tile planes are FP32 only)
 static size_t tile_smem_bytes(bool fp64, int tg, int v) {
-    if (fp64) return tg == 0 ? tile_smem_bytes_t<double, 0>(v) : tg == 1 ? tile_smem_bytes_t<double, 1>(v)
-                                                                          : tile_smem_bytes_t<double, 2>(v);
+    if (fp64) {
+        switch (tg) {
+            case 0: return tile_smem_bytes_t<double, 0>(v);
+            case 1: return tile_smem_bytes_t<double, 1>(v);
+            case 5: return tile_smem_bytes_t<double, 5>(v);
+            case 6: return tile_smem_bytes_t<double, 6>(v);
+            default: return tile_smem_bytes_t<double, 2>(v);
+        }
+    }
     switch (tg) {
         case 0: return tile_smem_bytes_t<float, 0>(v);
         case 1: return tile_smem_bytes_t<float, 1>(v);
         case 2: return tile_smem_bytes_t<float, 2>(v);
         case 3: return tile_smem_bytes_t<float, 3>(v);
-        default: return tile_smem_bytes_t<float, 4>(v);
+        case 4: return tile_smem_bytes_t<float, 4>(v);
+        case 5: return tile_smem_bytes_t<float, 5>(v);
+        default: return tile_smem_bytes_t<float, 6>(v);
     }
 }
 
@@ -108,7 +117,7 @@ static int default_regroup_interval(bool fp64, int tg) { return fp64 ? 0 : (tg =
 struct pic_handle {
     pic_config cfg;
     int geom = 0;  // 0 3D, 1 2D-XY, 2 2D-XZ
-    int tg = 0;    // template geometry of the particle kernels: geom, or G2XY_W / G2XZ_W (2D, 32 x 32 tiles)
+    int tg = 0;    // template geometry of the particle kernels: geom, or a 2D plane with 32 x 32 or 8 x 8 tiles
     bool fp64 = false;
     size_t esz = 4;
     Grid g;
@@ -1253,15 +1262,21 @@ template <class T, int G> static pic_status maxwellian_t(pic_handle* h, int spec
 
 // ---- dispatch by precision / geometry --------------------------------------------------------
 
-#define DISPATCH(h, FN, ...)                                                       \
-    ((h)->fp64 ? ((h)->tg == 0   ? FN<double, 0>(__VA_ARGS__)                    \
-                  : (h)->tg == 1 ? FN<double, 1>(__VA_ARGS__)                    \
-                                 : FN<double, 2>(__VA_ARGS__))                   \
-               : ((h)->tg == 0   ? FN<float, 0>(__VA_ARGS__)                     \
-                  : (h)->tg == 1 ? FN<float, 1>(__VA_ARGS__)                     \
-                  : (h)->tg == 2 ? FN<float, 2>(__VA_ARGS__)                     \
-                  : (h)->tg == 3 ? FN<float, 3>(__VA_ARGS__)                     \
-                                 : FN<float, 4>(__VA_ARGS__)))
+#define DISPATCH(h, FN, ...) TG_DISPATCH((h)->fp64, (h)->tg, FN, __VA_ARGS__)
+// by precision and template geometry (no FP64 kernels for 32 x 32 tiles)
+#define TG_DISPATCH(fp64, tg, FN, ...)                                              \
+    ((fp64) ? ((tg) == 0   ? FN<double, 0>(__VA_ARGS__)                             \
+               : (tg) == 1 ? FN<double, 1>(__VA_ARGS__)                             \
+               : (tg) == 5 ? FN<double, 5>(__VA_ARGS__)                             \
+               : (tg) == 6 ? FN<double, 6>(__VA_ARGS__)                             \
+                           : FN<double, 2>(__VA_ARGS__))                            \
+            : ((tg) == 0   ? FN<float, 0>(__VA_ARGS__)                              \
+               : (tg) == 1 ? FN<float, 1>(__VA_ARGS__)                              \
+               : (tg) == 2 ? FN<float, 2>(__VA_ARGS__)                              \
+               : (tg) == 3 ? FN<float, 3>(__VA_ARGS__)                              \
+               : (tg) == 4 ? FN<float, 4>(__VA_ARGS__)                              \
+               : (tg) == 5 ? FN<float, 5>(__VA_ARGS__)                              \
+                           : FN<float, 6>(__VA_ARGS__)))
 
 template <class T, int G> static pic_status set_fields_t(pic_handle* h, const double* E, const double* B) {
     const Grid& g = h->g;
@@ -1445,19 +1460,20 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
     g.py = AY ? c.ny + GL + GR : 1;
     g.pz = AZ ? c.nz + GL + GR : 1;
     g.cstride = (long long)g.px * g.py * g.pz;
-    // particle tiles: 8^3 cells in 3D; 16^2 cells in 2D, or 32^2 (FP32) on request
+    // particle tiles: 8^3 cells in 3D; 16^2 cells in 2D, or 8^2 or 32^2 (FP32) on request
     {
         const int t0 = c.tile[0], t1 = AY ? c.tile[1] : c.tile[2];
         const int want = t0 ? t0 : t1;
         const bool ok3 = h->geom == 0 && (t0 == 0 || t0 == 8) && (c.tile[1] == 0 || c.tile[1] == 8) &&
                          (c.tile[2] == 0 || c.tile[2] == 8);
-        const bool ok2 = h->geom != 0 && (want == 0 || want == 16 || (want == 32 && !h->fp64)) && (t1 == 0 || t1 == want);
+        const bool ok2 = h->geom != 0 && (want == 0 || want == 8 || want == 16 || (want == 32 && !h->fp64)) &&
+                         (t1 == 0 || t1 == want);
         if (!(h->geom == 0 ? ok3 : ok2)) {
             delete h;
             return fail(nullptr, PIC_ERR_ARG, "tile must be 0 (automatic) or %s", h->geom == 0 ? "8x8x8 in 3D"
-                        : "16x16, or 32x32 (FP32), on the active plane in 2D");
+                        : "8x8, 16x16, or 32x32 (FP32), on the active plane in 2D");
         }
-        h->tg = (h->geom != 0 && want == 32) ? (h->geom == 1 ? G2XY_W : G2XZ_W) : h->geom;
+        h->tg = tgeom_of(h->geom, want ? want : 16);
     }
     set_tiling(h);
     {
@@ -1565,6 +1581,12 @@ pic_status pic_destroy(pic_handle* h) {
         }
     snap_give(h->occ_host);
     if (h->ctx) dfree(h, h->ctx);
+    // hand the freed memory beyond what the pool keeps back now, not at some
+    // later synchronisation of another box's work
+    if (cudaMemPool_t pool = lib_pool(h->cfg.device)) {
+        if (h->stream) cudaStreamSynchronize(h->stream);
+        cudaMemPoolTrimTo(pool, POOL_KEEP);
+    }
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return PIC_OK;
@@ -1930,8 +1952,8 @@ pic_status pic_preload_kernels(int32_t device, int32_t precision) {
     const int pushes[6][2] = {{PUSH_BORIS, ESC_NONE}, {PUSH_BORIS, ESC_DISP}, {PUSH_BORIS, ESC_PROB},
                               {PUSH_KSB, ESC_NONE}, {PUSH_KEB, ESC_NONE}, {PUSH_SXE, ESC_NONE}};
     cudaFuncAttributes a;
-    for (int tg = 0; tg < (fp64 ? 3 : N_TGEOM); ++tg)
-        for (int ord = 1; ord <= 2; ++ord)
+    for (int tg = 0; tg < N_TGEOM; ++tg)
+        for (int ord = 1; ord <= 2 && tgeom_built(tg, fp64); ++ord)
             for (const auto& pe : pushes) {
                 const KernelSet ks = lookup_kernels(fp64, tg, ord, pe[0], pe[1]);
                 for (const void* f : ks.tile)
@@ -2160,9 +2182,10 @@ pic_status pic_set_tile(pic_handle* h, int32_t side) {
         if (side != 8) return fail(h, PIC_ERR_ARG, "3D tiles are 8x8x8");
         return PIC_OK;
     }
-    if (side != 16 && !(side == 32 && !h->fp64)) return fail(h, PIC_ERR_ARG, "2D tiles are 16x16, or 32x32 in FP32");
+    if (side != 8 && side != 16 && !(side == 32 && !h->fp64))
+        return fail(h, PIC_ERR_ARG, "2D tiles are 8x8, 16x16, or 32x32 in FP32");
     cudaSetDevice(h->cfg.device);
-    return retile(h, side == 32 ? (h->geom == 1 ? G2XY_W : G2XZ_W) : h->geom);
+    return retile(h, tgeom_of(h->geom, side));
 }
 
 pic_status pic_autotune(pic_handle* h, int32_t trial_steps, int32_t* best, double* ms_per_variant,
@@ -2235,18 +2258,19 @@ pic_status pic_autotune(pic_handle* h, int32_t trial_steps, int32_t* best, doubl
 pic_status pic_autotune_tile(pic_handle* h, int32_t trial_steps, int32_t* best_side, double* ms_per_side) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
     if (trial_steps < 1) return fail(h, PIC_ERR_ARG, "trial_steps must be >= 1");
-    if (h->geom == 0 || h->fp64) return fail(h, PIC_ERR_ARG, "the tile shape is tuned for 2D FP32 boxes only");
+    if (h->geom == 0) return fail(h, PIC_ERR_ARG, "the tile shape is tuned for 2D boxes only");
     cudaSetDevice(h->cfg.device);
-    const int sides[2] = {16, 32};
+    const int sides[3] = {8, 16, 32};
+    const int nsides = h->fp64 ? 2 : 3;  // no FP64 kernels for 32 x 32 tiles
     const int start_side = h->tl.tx;
     const bool prof_was = h->prof.on;
     prof_resolve(h);
     const double ms0[3] = {h->prof.ms[0], h->prof.ms[1], h->prof.ms[2]};
     const long long l0 = h->prof.launches, pl0 = h->prof.particle_launches, ps0 = h->prof.particle_steps;
-    double per[2] = {-1.0, -1.0};
-    int var[2] = {0, 0};
+    double per[3] = {-1.0, -1.0, -1.0};
+    int var[3] = {0, 0, 0};
     pic_status st = PIC_OK;
-    for (int k = 0; k < 2 && st == PIC_OK; ++k) {
+    for (int k = 0; k < nsides && st == PIC_OK; ++k) {
         st = pic_set_tile(h, sides[k]);
         if (st != PIC_OK) break;
         // the best launch variant for these tiles, then whole steps with it
@@ -2276,15 +2300,15 @@ pic_status pic_autotune_tile(pic_handle* h, int32_t trial_steps, int32_t* best_s
         pic_set_tile(h, start_side);
         return fail(h, st, "%s", why.c_str());
     }
-    const int b = per[1] >= 0.0 && per[1] < per[0] ? 1 : 0;
+    int b = 0;
+    for (int k = 1; k < nsides; ++k)
+        if (per[k] >= 0.0 && per[k] < per[b]) b = k;
     st = pic_set_tile(h, sides[b]);
     if (st == PIC_OK && var[b] > 0) st = pic_set_kernel_variant(h, var[b]);
     if (st != PIC_OK) return st;
     if (best_side) *best_side = sides[b];
-    if (ms_per_side) {
-        ms_per_side[0] = per[0];
-        ms_per_side[1] = per[1];
-    }
+    if (ms_per_side)
+        for (int k = 0; k < 3; ++k) ms_per_side[k] = per[k];
     return PIC_OK;
 }
 
@@ -2603,15 +2627,7 @@ template <class T, int G> pic_status batch_step_t(pic_batch* B) {
     return PIC_OK;
 }
 
-#define BDISPATCH(B, FN, ...)                                                      \
-    ((B)->fp64 ? ((B)->tg == 0   ? FN<double, 0>(__VA_ARGS__)                    \
-                  : (B)->tg == 1 ? FN<double, 1>(__VA_ARGS__)                    \
-                                 : FN<double, 2>(__VA_ARGS__))                   \
-               : ((B)->tg == 0   ? FN<float, 0>(__VA_ARGS__)                     \
-                  : (B)->tg == 1 ? FN<float, 1>(__VA_ARGS__)                     \
-                  : (B)->tg == 2 ? FN<float, 2>(__VA_ARGS__)                     \
-                  : (B)->tg == 3 ? FN<float, 3>(__VA_ARGS__)                     \
-                                 : FN<float, 4>(__VA_ARGS__)))
+#define BDISPATCH(B, FN, ...) TG_DISPATCH((B)->fp64, (B)->tg, FN, __VA_ARGS__)
 
 void batch_drop_graphs(pic_batch* B) {
     for (int p = 0; p < 2; ++p) {

@@ -106,9 +106,9 @@ struct pic_server {
 
 static void tile_shape(const pic_config& c, int& tx, int& ty, int& tz) {
     const int geom = c.ndim == 3 ? 0 : (c.plane == PIC_PLANE_XY ? 1 : 2);
-    // 2D: 16 x 16 unless the configuration asks for 32 x 32 tiles
+    // 2D: 16 x 16 unless the configuration asks for 8 x 8 or 32 x 32 tiles
     const int req = geom == 0 ? 0 : (c.tile[0] ? c.tile[0] : (geom == 1 ? c.tile[1] : c.tile[2]));
-    const int side = geom == 0 ? 8 : (req == 32 ? 32 : 16);
+    const int side = geom == 0 ? 8 : ((req == 32 || req == 8) ? req : 16);
     tx = side;
     ty = geom == 2 ? 1 : side;
     tz = geom == 1 ? 1 : side;

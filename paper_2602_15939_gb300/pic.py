@@ -395,17 +395,18 @@ def pic_get_tile(h):
 
 
 def pic_set_tile(h, side: int):
-    """Re-lay the particles out in side x side tiles (2D: 16, or 32 in FP32)."""
+    """Re-lay the particles out in side x side tiles (2D: 8, 16, or 32 in FP32)."""
     _check(h, lib().pic_set_tile(h, side))
 
 
 def pic_autotune_tile(h, trial_steps: int = 4):
-    """Time 16 x 16 and 32 x 32 tiles (2D FP32), each with its best launch
-    variant, and keep the faster: returns (best side, ms per step for 16, 32)."""
+    """Time 8 x 8, 16 x 16 and (FP32) 32 x 32 tiles of a 2D box, each with its
+    best launch variant, and keep the fastest: returns (best side, ms per step
+    for 8, 16, 32; None for a side not tried)."""
     best = C.c_int32()
-    ms = (C.c_double * 2)()
+    ms = (C.c_double * 3)()
     _check(h, lib().pic_autotune_tile(h, trial_steps, C.byref(best), ms))
-    return best.value, (ms[0], ms[1])
+    return best.value, tuple(v if v >= 0 else None for v in ms)
 
 
 class Batch:
@@ -539,7 +540,7 @@ class Box:
         pic_set_tile(self.h, side)
 
     def autotune_tile(self, trial_steps=4):
-        """Pick 16 x 16 or 32 x 32 particle tiles on live steps (2D FP32); see pic_autotune_tile."""
+        """Pick 8 x 8, 16 x 16 or 32 x 32 particle tiles on live steps (2D); see pic_autotune_tile."""
         return pic_autotune_tile(self.h, trial_steps)
 
     def step(self, n=1):

@@ -1,9 +1,9 @@
-"""Particle tile shapes (2D FP32: 16 x 16 or 32 x 32 cells).  The tile only
-decides where a particle is stored and which CTA moves it, so a box on 32 x 32
-tiles matches the oracle like any box, and gives bit for bit the FP32 results
-of the same box on 16 x 16 tiles (its current is an integer sum, exact in any
-order); so does a box switched between the two shapes mid-run (pic_set_tile)
-or by the tile autotuner, and a batch of 32 x 32-tile boxes."""
+"""Particle tile shapes (2D: 8 x 8, 16 x 16 or, in FP32, 32 x 32 cells).  The
+tile only decides where a particle is stored and which CTA moves it, so a box
+on 8 x 8 or 32 x 32 tiles matches the oracle like any box, and gives bit for
+bit the FP32 results of the same box on 16 x 16 tiles (its current is an
+integer sum, exact in any order); so does a box switched between shapes
+mid-run (pic_set_tile) or by the tile autotuner, and a batch of such boxes."""
 import dataclasses
 
 import numpy as np
@@ -34,9 +34,13 @@ def narrow(case):
     return dataclasses.replace(case, tile=(0, 0, 0))
 
 
-def load(case):
+def with_side(case, side):
+    return dataclasses.replace(case, tile=(side, 0, side) if case.plane == XZ else (side, side, 0))
+
+
+def load(case, fp64=False):
     sp, E, B = inputs(case)
-    box = P.Box(case.gpu_config(False))
+    box = P.Box(case.gpu_config(fp64))
     box.set_fields(E, B)
     for i, d in enumerate(sp):
         box.load(i, d["q"], d["m"], d["x"], d["u"], d["id"])
@@ -78,17 +82,18 @@ def run(case, plan):
                 box.set_tile(item[1])
             else:
                 best, ms = box.autotune_tile(item[1])
-                assert best in (16, 32) and box.tile()[0] == best
-                assert ms[0] > 0 and ms[1] > 0
+                assert best in (8, 16, 32) and box.tile()[0] == best
+                assert all(v > 0 for v in ms)
         return state(box, nsp, case.esc_mode == 1), box.tile()
     finally:
         box.close()
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("side", [8, 32])
 @pytest.mark.parametrize("case", WIDE, ids=IDS)
-def test_wide_tiles_match_oracle(case):
-    r = compare(case, 1, fp64=False)
+def test_tile_shapes_match_oracle(case, side):
+    r = compare(with_side(case, side), 1, fp64=False)
     assert r["error_word"] == 0, r
     assert r["u"] <= 1e-6 and r["x"] <= 2e-6, r
     assert r["E"] <= 1e-6 and r["B"] <= 1e-6 and r["J"] <= 1e-6, r
@@ -97,9 +102,19 @@ def test_wide_tiles_match_oracle(case):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("case", WIDE, ids=IDS)
-def test_wide_tiles_equal_narrow_tiles(case):
-    (a, ta), (b, tb) = run(case, [6]), run(narrow(case), [6])
-    side = 32
+def test_small_tiles_match_oracle_fp64(case):
+    r = compare(with_side(case, 8), 1, fp64=True)
+    assert r["error_word"] == 0, r
+    assert r["u"] <= 1e-12 and r["x"] <= 1e-11, r
+    assert r["E"] <= 1e-12 and r["B"] <= 1e-12 and r["J"] <= 1e-12, r
+    assert r["escaped_gpu"] == r["escaped_oracle"], r
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("side", [8, 32])
+@pytest.mark.parametrize("case", WIDE, ids=IDS)
+def test_tile_shapes_equal_16x16_tiles(case, side):
+    (a, ta), (b, tb) = run(with_side(case, side), [6]), run(narrow(case), [6])
     assert ta == (side, 1 if case.plane == XZ else side, side if case.plane == XZ else 1)
     assert tb[0] == 16
     assert_identical(a, b)
@@ -109,9 +124,9 @@ def test_wide_tiles_equal_narrow_tiles(case):
 @pytest.mark.parametrize("case", [WIDE[0], WIDE[1], WIDE[2]], ids=IDS[:3])
 def test_switching_tiles_mid_run_changes_nothing(case):
     c = narrow(case)
-    got, t = run(c, [2, ("tile", 32), 3, ("tile", 16), 2, ("tile", 32), 1])
+    got, t = run(c, [2, ("tile", 32), 3, ("tile", 8), 2, ("tile", 16), 1, ("tile", 32), 1])
     assert t[0] == 32
-    want, _ = run(c, [8])
+    want, _ = run(c, [9])
     assert_identical(got, want)
 
 
@@ -121,7 +136,8 @@ def test_tile_autotuner_keeps_the_simulation():
     box, nsp = load(c)
     try:
         best, ms = box.autotune_tile(2)
-        assert best in (16, 32) and box.tile()[0] == best
+        assert best in (8, 16, 32) and box.tile()[0] == best
+        assert all(v > 0 for v in ms)
         box.step(1)
         got = state(box, nsp, False)
     finally:
@@ -162,12 +178,19 @@ def test_tile_shape_errors():
         assert e.value.status == P.PIC_ERR_ARG
     box = P.Box(narrow(c).gpu_config(False))
     try:
-        with pytest.raises(P.PicError):
-            box.set_tile(24)
-        with pytest.raises(P.PicError):
-            box.set_tile(8)
+        for bad in (24, 4, 64):
+            with pytest.raises(P.PicError):
+                box.set_tile(bad)
     finally:
         box.close()
+    box64 = P.Box(narrow(c).gpu_config(True))
+    try:
+        with pytest.raises(P.PicError):  # no FP64 kernels for 32 x 32 tiles
+            box64.set_tile(32)
+        box64.set_tile(8)
+        assert box64.tile() == (8, 8, 1)
+    finally:
+        box64.close()
     box3 = P.Box(Case("p3", BOX_P, (8, 8, 8)).gpu_config(False))
     try:
         assert box3.tile() == (8, 8, 8)
@@ -184,3 +207,15 @@ def test_tile_shape_errors():
     finally:
         for b in boxes:
             b.close()
+
+
+@pytest.mark.gpu
+def test_fp64_tile_autotuner_tries_8_and_16():
+    c = narrow(WIDE[2])
+    box, nsp = load(c, fp64=True)
+    try:
+        best, ms = box.autotune_tile(1)
+        assert best in (8, 16) and box.tile()[0] == best
+        assert ms[0] > 0 and ms[1] > 0 and ms[2] is None
+    finally:
+        box.close()
