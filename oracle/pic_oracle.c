@@ -1076,22 +1076,30 @@ void ora_advance_particle(const ora_params *p, const double *E, const double *B,
         wrap_coord(&x1[0], p->nx);
         wrap_coord(&x1[1], p->ny);
         wrap_coord(&x1[2], p->nz);
-        if (p->box == ORA_BOX_LEAKY && p->esc_mode != ORA_ESC_NONE) {
-            /* Sec. 4.1: end-of-step escape test and reinjection */
-            int esc;
-            if (p->esc_mode == ORA_ESC_DISPLACEMENT) {
-                for (int a = 0; a < 3; ++a) dr[a] += u[a] / g;
-                double mx = fabs(dr[0]) > fabs(dr[1]) ? fabs(dr[0]) : fabs(dr[1]);
-                if (p->esc_dims == 3 && fabs(dr[2]) > mx) mx = fabs(dr[2]);
-                esc = mx >= p->l_esc;
-            } else {
-                esc = ora_escape_draw(id, p->seed, n, p->p_esc);
-            }
-            if (esc) {
-                ora_sample_mj(id, p->seed, n, p->theta_inj, p->c, u);
-                if (dr) dr[0] = dr[1] = dr[2] = 0.0;
-                loc->escaped++;
-            }
+        if (p->box == ORA_BOX_LEAKY && p->esc_mode == ORA_ESC_DISPLACEMENT) {
+            /* Sec. 4.1: the displacement since the last (re)injection */
+            for (int a = 0; a < 3; ++a) dr[a] += u[a] / g;
+        }
+    }
+    if (p->esc_mode == ORA_ESC_PROBABILISTIC || (p->box == ORA_BOX_LEAKY && p->esc_mode == ORA_ESC_DISPLACEMENT)) {
+        /* Sec. 4.1: end-of-step escape test and reinjection.  The displacement
+         * rule is the leaky box's; the probabilistic rule runs in every box
+         * (the leaky box combined with the others, Sec. 5), where the
+         * reinjected momentum replaces the momentum variable that box
+         * evolves (the peculiar u' of the shearing box, the comoving u of
+         * the expanding box) and the position is kept. */
+        int esc;
+        if (p->esc_mode == ORA_ESC_DISPLACEMENT) {
+            double mx = fabs(dr[0]) > fabs(dr[1]) ? fabs(dr[0]) : fabs(dr[1]);
+            if (p->esc_dims == 3 && fabs(dr[2]) > mx) mx = fabs(dr[2]);
+            esc = mx >= p->l_esc;
+        } else {
+            esc = ora_escape_draw(id, p->seed, n, p->p_esc);
+        }
+        if (esc) {
+            ora_sample_mj(id, p->seed, n, p->theta_inj, p->c, u);
+            if (dr) dr[0] = dr[1] = dr[2] = 0.0;
+            loc->escaped++;
         }
     }
     x[0] = x1[0];

@@ -39,7 +39,7 @@ typedef struct {
     int32_t box;            /* ORA_BOX_* */
     int32_t fp_iters;       /* shearing box: fixed-point sweeps of the Maxwell solve */
     int32_t keb_exact;      /* expanding box: 0 = closed-form modified Boris, 1 = 3x3 solve */
-    int32_t esc_mode;       /* leaky box: ORA_ESC_* */
+    int32_t esc_mode;       /* ORA_ESC_*: the displacement rule in the leaky box; the probabilistic rule in any box */
     int32_t esc_dims;       /* 2: max(|dx|,|dy|); 3: max over x,y,z */
     uint32_t seed;          /* low word of the Philox key */
     double c;

@@ -171,6 +171,69 @@ def test_leaky_probabilistic_survival_is_binomial():
     assert abs(surv - N * pr) < 5 * math.sqrt(N * pr * (1 - pr))
 
 
+OTHER_BOXES = [
+    dict(box=O.BOX_SHEAR, s=1.5, Omega0=3e-3),
+    dict(box=O.BOX_EXPAND, rate=(0.0, 1e-3, 2e-3)),
+    dict(box=O.BOX_SHEAR_EXPAND, s=1.2, Omega0=2e-3, rate=(1e-3, 2e-3, 5e-4)),
+]
+
+
+@pytest.mark.parametrize("kw", OTHER_BOXES, ids=["shear", "expand", "shear_expand"])
+def test_probabilistic_escape_in_other_boxes_follows_the_move(kw):
+    """The leaky box's probabilistic escape combined with the shearing,
+    expanding and combined boxes (Sec. 5): it acts at the end of the step.
+    With p = 1 every particle escapes: its position and the step's current
+    and fields are those of the step without escape (the move and deposit
+    came first), and its momentum is the Maxwell-Juettner draw keyed on (id,
+    seed, step).  With p = 0 nothing changes."""
+    n = (6, 5, 4)
+    p_none = O.make_params(*n, C, order=2, seed=4, **kw)
+    sp = plasma(n, 3, seed=2, uth=0.15)
+    r = np.random.default_rng(1)
+    E = r.normal(0, 0.01, (3, n[2], n[1], n[0]))
+    B = r.normal(0, 0.01, (3, n[2], n[1], n[0])) + np.array([0, 0, 0.2])[:, None, None, None]
+    ref = O.State(p_none, E, B, sp, step=7)
+    ref.step(1)
+    for p_esc in (0.0, 1.0):
+        p = O.make_params(*n, C, order=2, seed=4, esc_mode=O.ESC_PROBABILISTIC, p_esc=p_esc, theta_inj=0.3, **kw)
+        st = O.State(p, E, B, sp, step=7)
+        info = st.step(1)
+        for a, b in zip(st.species, ref.species):
+            assert np.array_equal(a["x"], b["x"])
+            if p_esc == 0.0:
+                assert np.array_equal(a["u"], b["u"])
+            else:
+                want = np.array([O.sample_mj(int(i), 4, 7, 0.3, C)[0] for i in a["id"]])
+                np.testing.assert_array_equal(a["u"], want)
+        assert np.array_equal(st.E, ref.E) and np.array_equal(st.B, ref.B) and np.array_equal(st.J, ref.J)
+        assert info["escaped"] == (0 if p_esc == 0.0 else sum(len(d["id"]) for d in sp))
+
+
+@pytest.mark.parametrize("kw", OTHER_BOXES, ids=["shear", "expand", "shear_expand"])
+def test_probabilistic_escape_in_other_boxes_is_binomial(kw):
+    """Survival of uncharged test particles under escape at p per step, in
+    the shearing, expanding and combined boxes: a particle never reinjected
+    has exactly the momentum of the same particle stepped without escape;
+    their number after n steps is binomial(N, (1 - p)^n), checked at 5
+    sigma."""
+    n = (4, 4, 3)
+    N = 6000
+    p_esc = 0.03
+    r = np.random.default_rng(3)
+    sp = [{"q": 0.0, "m": 1.0, "x": r.uniform(0, 1, (N, 3)) * np.array(n, dtype=float),
+           "u": r.normal(0, 0.1, (N, 3)), "id": np.arange(N)}]
+    z = np.zeros((3, n[2], n[1], n[0]))
+    steps = 30
+    ref = O.State(O.make_params(*n, C, order=1, seed=8, **kw), z, z, sp)
+    ref.step(steps)
+    st = O.State(O.make_params(*n, C, order=1, seed=8, esc_mode=O.ESC_PROBABILISTIC, p_esc=p_esc, theta_inj=0.2,
+                               **kw), z, z, sp)
+    st.step(steps)
+    surv = np.all(st.species[0]["u"] == ref.species[0]["u"], axis=1).sum()
+    pr = (1 - p_esc) ** steps
+    assert abs(surv - N * pr) < 5 * math.sqrt(N * pr * (1 - pr))
+
+
 def test_threaded_step_equals_the_plain_loop():
     """The timed CPU baseline runs the oracle's particle loop on several
     threads (per-thread currents added in thread order): the same step as the
