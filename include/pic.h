@@ -94,7 +94,11 @@ typedef struct pic_config {
                              solve (Sec. 2.2); counts of 3, 4, 7, 8, ... are stable */
     int32_t keb_push;     /* expanding box: PIC_KEB_CLOSED_FORM (the operator of Sec. 3.2)
                              or PIC_KEB_EXACT (direct 3x3 solve of its defining equation) */
-    int32_t escape_mode;  /* leaky box: PIC_ESC_* */
+    int32_t escape_mode;  /* PIC_ESC_*: the leaky box's escape and reinjection (Sec. 4.1).
+                             PIC_ESC_PROBABILISTIC also runs in the shearing, expanding
+                             and combined boxes (the reinjected momentum replaces the
+                             momentum that box evolves; positions are kept);
+                             PIC_ESC_DISPLACEMENT there is PIC_ERR_ARG */
     int32_t escape_dims;  /* leaky displacement test over (x,y) [2] or (x,y,z) [3] */
     int32_t tile[3];      /* particle tile in cells per axis; 0 = automatic.  3D: 8x8x8.
                              2D: 16x16 (the automatic choice), 8x8 or, FP32 only, 32x32 on

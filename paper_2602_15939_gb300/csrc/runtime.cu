@@ -1376,12 +1376,14 @@ static pic_status validate(const pic_config* c) {
         double vmax = std::fabs(c->s_shear * c->Omega0) * 0.5 * c->nx;
         if (c->c + vmax >= 1.0) return fail(h, PIC_ERR_ARG, "c + max shear speed must stay below one cell per step");
     }
+    if (c->escape_mode < 0 || c->escape_mode > 2) return fail(h, PIC_ERR_ARG, "escape_mode must be 0..2");
+    if (c->escape_mode == PIC_ESC_DISPLACEMENT && c->box != PIC_BOX_LEAKY)
+        return fail(h, PIC_ERR_ARG, "the displacement escape rule is the leaky box's; other boxes take the probabilistic one");
     if (c->box == PIC_BOX_LEAKY) {
-        if (c->escape_mode < 0 || c->escape_mode > 2) return fail(h, PIC_ERR_ARG, "escape_mode must be 0..2");
         if (c->escape_mode == PIC_ESC_DISPLACEMENT && !(c->l_esc > 0)) return fail(h, PIC_ERR_ARG, "l_esc must be > 0");
         if (c->escape_dims != 2 && c->escape_dims != 3) return fail(h, PIC_ERR_ARG, "escape_dims must be 2 or 3");
-        if (c->escape_mode != PIC_ESC_NONE && !(c->theta_inj > 0)) return fail(h, PIC_ERR_ARG, "theta_inj must be > 0");
     }
+    if (c->escape_mode != PIC_ESC_NONE && !(c->theta_inj > 0)) return fail(h, PIC_ERR_ARG, "theta_inj must be > 0");
     for (int a = 0; a < 3; ++a)
         if (c->tile[a] < 0) return fail(h, PIC_ERR_ARG, "tile sizes must be >= 0");
     return PIC_OK;
@@ -1447,10 +1449,10 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
               : c.box == PIC_BOX_EXPAND        ? PUSH_KEB
               : c.box == PIC_BOX_SHEAR_EXPAND ? PUSH_SXE
                                                : PUSH_BORIS;
-    h->esc = c.box == PIC_BOX_LEAKY ? (c.escape_mode == PIC_ESC_DISPLACEMENT ? ESC_DISP
-                                       : c.escape_mode == PIC_ESC_PROBABILISTIC ? ESC_PROB
-                                                                                 : ESC_NONE)
-                                    : ESC_NONE;
+    // escape: the displacement rule in the leaky box, the probabilistic rule in any box
+    h->esc = c.escape_mode == PIC_ESC_PROBABILISTIC                              ? ESC_PROB
+             : (c.box == PIC_BOX_LEAKY && c.escape_mode == PIC_ESC_DISPLACEMENT) ? ESC_DISP
+                                                                                 : ESC_NONE;
     const bool AY = h->geom != 2, AZ = h->geom != 1;
     const int A = (int)(16 / h->esz);  // TMA x quantum
     Grid& g = h->g;
@@ -1949,8 +1951,9 @@ pic_status pic_preload_kernels(int32_t device, int32_t precision) {
     if (precision != PIC_FP32 && precision != PIC_FP64) return fail(nullptr, PIC_ERR_ARG, "bad precision");
     if (cudaSetDevice(device) != cudaSuccess) return fail(nullptr, PIC_ERR_CUDA, "no such CUDA device");
     const bool fp64 = precision == PIC_FP64;
-    const int pushes[6][2] = {{PUSH_BORIS, ESC_NONE}, {PUSH_BORIS, ESC_DISP}, {PUSH_BORIS, ESC_PROB},
-                              {PUSH_KSB, ESC_NONE}, {PUSH_KEB, ESC_NONE}, {PUSH_SXE, ESC_NONE}};
+    const int pushes[9][2] = {{PUSH_BORIS, ESC_NONE}, {PUSH_BORIS, ESC_DISP}, {PUSH_BORIS, ESC_PROB},
+                              {PUSH_KSB, ESC_NONE},   {PUSH_KEB, ESC_NONE},   {PUSH_SXE, ESC_NONE},
+                              {PUSH_KSB, ESC_PROB},   {PUSH_KEB, ESC_PROB},   {PUSH_SXE, ESC_PROB}};
     cudaFuncAttributes a;
     for (int tg = 0; tg < N_TGEOM; ++tg)
         for (int ord = 1; ord <= 2 && tgeom_built(tg, fp64); ++ord)

@@ -303,7 +303,7 @@ static void worker_main(pic_server* S) {
                 if (S->cohort_policy == 1 && !r->fresh) continue;
                 const pic_config& c = r->spec.cfg;
                 const int t = c.ndim == 3 ? 0 : (c.tile[0] ? c.tile[0] : (c.plane == PIC_PLANE_XY ? c.tile[1] : c.tile[2]));
-                kinds[{c.precision, c.ndim, c.plane, t, c.shape_order, c.box, c.box == PIC_BOX_LEAKY ? c.escape_mode : 0}]
+                kinds[{c.precision, c.ndim, c.plane, t, c.shape_order, c.box, c.escape_mode}]
                     .push_back(r);
             }
             for (auto& kv : kinds) {

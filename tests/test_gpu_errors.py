@@ -64,3 +64,18 @@ def test_fixed_point_current_beyond_range_is_reported_and_handle_recovers():
         np.testing.assert_array_equal(ig[og], iw[ow])
         np.testing.assert_array_equal(xg[og], xw[ow])
         np.testing.assert_array_equal(ug[og], uw[ow])
+
+
+@pytest.mark.gpu
+def test_displacement_escape_is_the_leaky_boxs_only():
+    """The probabilistic escape runs in every box; the displacement rule is
+    defined for the leaky box alone, so other boxes refuse it."""
+    for box in (P.PIC_BOX_SHEAR, P.PIC_BOX_EXPAND, P.PIC_BOX_SHEAR_EXPAND, P.PIC_BOX_PERIODIC):
+        cfg = P.make_config(box=box, nx=8, ny=8, nz=8, order=1, precision=P.PIC_FP32, s=1.5, Omega0=1e-3,
+                            escape_mode=P.PIC_ESC_DISPLACEMENT, l_esc=2.0, theta_inj=0.2)
+        with pytest.raises(P.PicError) as e:
+            P.Box(cfg)
+        assert e.value.status == P.PIC_ERR_ARG
+        cfg.escape_mode = P.PIC_ESC_PROBABILISTIC
+        cfg.p_esc = 0.01
+        P.Box(cfg).close()

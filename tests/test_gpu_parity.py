@@ -49,6 +49,15 @@ CASES = [
          fp_iters=3),
     Case("shearexp2dxy_o2", BOX_SE, (32, 24, 1), ndim=2, plane=XY, order=2, ppc=6, s=1.5, Omega0=4e-3,
          rate=(2e-3, 1e-3, 0.0), step0=11),
+    # the leaky box's probabilistic escape combined with the other boxes (Sec. 4.1 with Sec. 5)
+    Case("shear3d_o2_esc", BOX_S, (16, 12, 8), order=2, s=1.5, Omega0=3e-3, step0=37, esc_mode=2, p_esc=0.05,
+         theta_inj=0.3),
+    Case("shear2dxz_o1_esc", BOX_S, (32, 1, 24), ndim=2, plane=XZ, order=1, ppc=6, s=1.5, Omega0=4e-3, step0=11,
+         esc_mode=2, p_esc=0.05, theta_inj=0.5),
+    Case("expand3d_o2_esc", BOX_E, (16, 12, 8), order=2, rate=(0.0, 1e-3, 1e-3), step0=20, esc_mode=2, p_esc=0.05,
+         theta_inj=0.2),
+    Case("shearexp3d_o1_esc", BOX_SE, (16, 16, 8), order=1, s=1.2, Omega0=2e-3, rate=(0.0, 1e-3, 1e-3),
+         step0=101, fp_iters=3, esc_mode=2, p_esc=0.05, theta_inj=0.3),
 ]
 
 IDS = [c.name for c in CASES]
