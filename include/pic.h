@@ -100,10 +100,14 @@ typedef struct pic_config {
                              momentum that box evolves; positions are kept);
                              PIC_ESC_DISPLACEMENT there is PIC_ERR_ARG */
     int32_t escape_dims;  /* leaky displacement test over (x,y) [2] or (x,y,z) [3] */
-    int32_t tile[3];      /* particle tile in cells per axis; 0 = automatic.  3D: 8x8x8.
-                             2D: 16x16 (the automatic choice), 8x8 or, FP32 only, 32x32 on
-                             the active plane (the ignorable axis' entry is not read);
-                             other shapes are PIC_ERR_ARG.  See pic_autotune_tile. */
+    int32_t tile[3];      /* particle tile in cells per axis; 0 = automatic.  3D: 4x4x4 or
+                             8x8x8.  2D: 8x8, 16x16 or, FP32 only, 32x32 on the active
+                             plane (the ignorable axis' entry is not read); other shapes
+                             are PIC_ERR_ARG.  Automatic: in 3D 4x4x4 when 8x8x8 tiles
+                             would be fewer than two per SM, else 8x8x8; in 2D 8x8 when
+                             16x16 tiles would be fewer than two per SM, 32x32 (FP32) when
+                             those are still eight per SM, else 16x16.  See
+                             pic_autotune_tile. */
     int32_t device;       /* CUDA device ordinal the handle lives on */
     uint32_t seed;        /* key word of the Philox streams (escape, reinjection, loading) */
     uint32_t kernel_variant; /* particle-kernel launch shape: 0 = automatic (the tuned choice
@@ -376,7 +380,7 @@ pic_status pic_autotune(pic_handle *h, int32_t trial_steps, int32_t *best, doubl
 
 /* Particle tiles (no counterpart in the paper).  pic_get_tile: the tile in
  * cells per axis (1 on the ignorable axis).  pic_set_tile (2D: side 8, 16, or
- * 32 in FP32; 3D: 8): re-lay the particles out in side x side tiles.  Every
+ * 32 in FP32; 3D: 4 or 8): re-lay the particles out in tiles of that side.  Every
  * species is read out into flat device arrays (cell + offset in FP64, which
  * holds FP32 state exactly), its arrays are freed and it is loaded again
  * under the new tiling, so the particles and every later result are
@@ -385,13 +389,13 @@ pic_status pic_autotune(pic_handle *h, int32_t trial_steps, int32_t *best, doubl
  * largest species); PIC_ERR_OOM leaves the tiling as it was, PIC_ERR_STATE
  * for a batched box.  Synchronizes the handle's stream; drops its captured
  * step graphs.
- * pic_autotune_tile (2D boxes; PIC_ERR_ARG in 3D): for 8x8, 16x16 and (FP32)
- * 32x32 tiles in turn, switch to them, run pic_autotune(trial_steps) for
- * their best launch variant, then one untimed and trial_steps timed ordinary
- * steps (all kernels, CUDA events); keep the tiles and variant with the least
- * time per step.  The trial steps advance the simulation like pic_step.
- * Outputs (nullable): *best_side and ms_per_side[3] (8, 16, 32; -1 for a side
- * not tried). */
+ * pic_autotune_tile: for each tile shape (2D: 8x8, 16x16 and, FP32, 32x32;
+ * 3D: 4x4x4 and 8x8x8) in turn, switch to it, run pic_autotune(trial_steps)
+ * for its best launch variant, then one untimed and trial_steps timed
+ * ordinary steps (all kernels, CUDA events); keep the tiles and variant with
+ * the least time per step.  The trial steps advance the simulation like
+ * pic_step.  Outputs (nullable): *best_side and ms_per_side[3] (2D: sides 8,
+ * 16, 32; 3D: 4, 8; -1 for a side not tried). */
 pic_status pic_get_tile(pic_handle *h, int32_t tile[3]);
 pic_status pic_set_tile(pic_handle *h, int32_t side);
 pic_status pic_autotune_tile(pic_handle *h, int32_t trial_steps, int32_t *best_side, double *ms_per_side);
@@ -420,7 +424,9 @@ pic_status pic_autotune_regroup(pic_handle *h, const int32_t *candidates, int32_
  * steps up to the next, or a pair of steps) is captured in one CUDA graph and
  * replayed.  The boxes must share device, precision, geometry (3D, 2D x-y, 2D
  * x-z), shape order and box type; they may differ in grid, parameters, species
- * and particle counts.  They must be loaded before pic_batch_create and stay
+ * and particle counts.  Members run on the plain tiles of their geometry
+ * (8x8x8, 16x16): members on other tile shapes are first re-laid out
+ * (pic_set_tile).  They must be loaded before pic_batch_create and stay
  * owned by the caller; until pic_batch_destroy they are stepped only through
  * the batch (pic_step on a member is PIC_ERR_STATE), may be read back after
  * pic_batch_synchronize, and must not be destroyed.  The particle kernel of a

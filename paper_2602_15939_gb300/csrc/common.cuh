@@ -18,20 +18,21 @@ constexpr int GR = 3;  // high guard cells (deposits reach node n+2)
 
 // geometry kinds: which axes are active.  G2XY_W / G2XZ_W and G2XY_S /
 // G2XZ_S are the 2D planes again, with 32 x 32- and 8 x 8-cell particle
-// tiles instead of 16 x 16 (template geometries: the grid and field code is
-// that of the plane).
-enum Geom : int { G3D = 0, G2XY = 1, G2XZ = 2, G2XY_W = 3, G2XZ_W = 4, G2XY_S = 5, G2XZ_S = 6 };
-constexpr int N_TGEOM = 7;
+// tiles instead of 16 x 16, and G3D_S is 3D with 4 x 4 x 4 tiles instead of
+// 8 x 8 x 8 (template geometries: the grid and field code is that of the
+// plain geometry).
+enum Geom : int { G3D = 0, G2XY = 1, G2XZ = 2, G2XY_W = 3, G2XZ_W = 4, G2XY_S = 5, G2XZ_S = 6, G3D_S = 7 };
+constexpr int N_TGEOM = 8;
 __host__ __device__ constexpr int plane_of(int G) {
-    return (G == G2XY_W || G == G2XY_S) ? G2XY : ((G == G2XZ_W || G == G2XZ_S) ? G2XZ : G);
+    return (G == G2XY_W || G == G2XY_S) ? G2XY : ((G == G2XZ_W || G == G2XZ_S) ? G2XZ : (G == G3D_S ? G3D : G));
 }
 // particle tile side in cells (per active axis) of a template geometry
 __host__ __device__ constexpr int tile_side(int G) {
-    return (G == G3D || G == G2XY_S || G == G2XZ_S) ? 8 : ((G == G2XY_W || G == G2XZ_W) ? 32 : 16);
+    return G == G3D_S ? 4 : ((G == G3D || G == G2XY_S || G == G2XZ_S) ? 8 : ((G == G2XY_W || G == G2XZ_W) ? 32 : 16));
 }
 // the template geometry of a geometry (G3D, G2XY, G2XZ) with tiles of `side` cells
 __host__ __device__ constexpr int tgeom_of(int geom, int side) {
-    return geom == G3D ? G3D
+    return geom == G3D ? (side == 4 ? G3D_S : G3D)
            : side == 32 ? (geom == G2XY ? G2XY_W : G2XZ_W)
            : side == 8 ? (geom == G2XY ? G2XY_S : G2XZ_S) : geom;
 }

@@ -1300,7 +1300,7 @@ constexpr TileVariant TILE_VARIANTS[N_TILE_VARIANTS] = {{256, 0, 1}, {512, 0, 1}
 // with one otherwise), and the one batched launches use (the same: for a
 // batch of 16 3D FP32 boxes the four-copy variant also beat two copies at
 // 256 threads, 1.31e10 against 1.24e10 particle-steps/s).
-constexpr int default_tile_variant(bool fp64, int geom) { return (!fp64 && geom == 0) ? 6 : 1; }
+constexpr int default_tile_variant(bool fp64, int geom) { return (!fp64 && plane_of(geom) == G3D) ? 6 : 1; }
 constexpr int batch_tile_variant(bool fp64, int geom) { return default_tile_variant(fp64, geom); }
 
 // Dynamic shared memory: E box, B box (each 128-byte aligned, the TMA
@@ -1346,7 +1346,7 @@ __device__ __forceinline__ SmemJ<T, G> pick_copy(JWord<T>* sJ, int lane, bool de
 
 // 3D FP32 tiles queue crossing particles in two queues per warp: those that
 // cross on one axis (deposit_1axis) and the rest (the full window).
-template <class T, int G> __host__ __device__ constexpr bool split_queue() { return sizeof(T) == 4 && G == G3D; }
+template <class T, int G> __host__ __device__ constexpr bool split_queue() { return sizeof(T) == 4 && plane_of(G) == G3D; }
 
 template <class T, int G, int NT, int STABLE, int JC> struct SmemLayout {
     static constexpr int FB = TileDims<G>::FB, JB = TileDims<G>::JB;

@@ -409,27 +409,14 @@ __global__ void kinetic_kernel(Tiling tl, PView<T> v, const int* __restrict__ st
                                double* __restrict__ partial) {
     // gamma - 1 = (u/c)^2 / (gamma + 1) per particle in the particles' own
     // precision (no cancellation; FP64 division and square root per particle
-    // would cost far more than the pass's memory traffic on this part).  FP64
-    // particles are summed in FP64.  FP32 particles are summed per thread in
-    // FP32 with Kahan's compensation (the running error term carries the
-    // rounding of every add, so the partial sum is good to about one FP32
-    // rounding of the total, with no FP64 add per particle, which this part
-    // issues at a small fraction of the FP32 rate), each thread's sum then in
-    // FP64; m c^2 is applied once per block
+    // would cost far more than the pass's memory traffic on this part), summed
+    // in FP64; m c^2 is applied once per block
     __shared__ double red[32];
-    T sum = T(0), comp = T(0);
+    double acc = 0.0;
     const T ic2 = T(1.0 / (c * c));
-    auto add = [&](T ux, T uy, T uz) {
+    auto term = [&](T ux, T uy, T uz) {
         const T u2 = (ux * ux + uy * uy + uz * uz) * ic2;
-        const T term = u2 / (t_sqrt<T>(T(1) + u2) + T(1));
-        if (sizeof(T) == 8) {
-            sum += term;
-        } else {
-            const T y = term - comp;
-            const T s1 = sum + y;
-            comp = (s1 - sum) - y;
-            sum = s1;
-        }
+        return (double)(u2 / (t_sqrt<T>(T(1) + u2) + T(1)));
     };
     for (int t = blockIdx.x; t < tl.ntiles + 1; t += gridDim.x) {
         if (t < tl.ntiles) {
@@ -437,15 +424,14 @@ __global__ void kinetic_kernel(Tiling tl, PView<T> v, const int* __restrict__ st
             const long long base = (long long)t * tcap;
             for (int i = threadIdx.x; i < nst + nar; i += blockDim.x) {
                 long long slot = i < nst ? base + i : base + tcap - nar + (i - nst);
-                add(v.u[0][slot], v.u[1][slot], v.u[2][slot]);
+                acc += term(v.u[0][slot], v.u[1][slot], v.u[2][slot]);
             }
         } else {
             long long n = *lcount;
             if (n > lcap) n = lcap;
-            for (long long i = threadIdx.x; i < n; i += blockDim.x) add(lv.u[0][i], lv.u[1][i], lv.u[2][i]);
+            for (long long i = threadIdx.x; i < n; i += blockDim.x) acc += term(lv.u[0][i], lv.u[1][i], lv.u[2][i]);
         }
     }
-    double acc = (double)sum - (double)comp;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();

@@ -91,6 +91,7 @@ static size_t tile_smem_bytes(bool fp64, int tg, int v) {
             case 1: return tile_smem_bytes_t<double, 1>(v);
             case 5: return tile_smem_bytes_t<double, 5>(v);
             case 6: return tile_smem_bytes_t<double, 6>(v);
+            case 7: return tile_smem_bytes_t<double, 7>(v);
             default: return tile_smem_bytes_t<double, 2>(v);
         }
     }
@@ -101,7 +102,8 @@ static size_t tile_smem_bytes(bool fp64, int tg, int v) {
         case 3: return tile_smem_bytes_t<float, 3>(v);
         case 4: return tile_smem_bytes_t<float, 4>(v);
         case 5: return tile_smem_bytes_t<float, 5>(v);
-        default: return tile_smem_bytes_t<float, 6>(v);
+        case 6: return tile_smem_bytes_t<float, 6>(v);
+        default: return tile_smem_bytes_t<float, 7>(v);
     }
 }
 
@@ -112,7 +114,7 @@ static int default_variant(bool fp64, int tg) { return default_tile_variant(fp64
 // Steps between regroups of the particles by cell (0: never).  FP64 boxes do
 // not regroup: the order of their current's floating-point adds would then
 // vary from run to run.
-static int default_regroup_interval(bool fp64, int tg) { return fp64 ? 0 : (tg == G3D ? 3 : 0); }
+static int default_regroup_interval(bool fp64, int tg) { return fp64 ? 0 : (plane_of(tg) == G3D ? 3 : 0); }
 
 struct pic_handle {
     pic_config cfg;
@@ -1269,6 +1271,7 @@ template <class T, int G> static pic_status maxwellian_t(pic_handle* h, int spec
                : (tg) == 1 ? FN<double, 1>(__VA_ARGS__)                             \
                : (tg) == 5 ? FN<double, 5>(__VA_ARGS__)                             \
                : (tg) == 6 ? FN<double, 6>(__VA_ARGS__)                             \
+               : (tg) == 7 ? FN<double, 7>(__VA_ARGS__)                             \
                            : FN<double, 2>(__VA_ARGS__))                            \
             : ((tg) == 0   ? FN<float, 0>(__VA_ARGS__)                              \
                : (tg) == 1 ? FN<float, 1>(__VA_ARGS__)                              \
@@ -1276,7 +1279,8 @@ template <class T, int G> static pic_status maxwellian_t(pic_handle* h, int spec
                : (tg) == 3 ? FN<float, 3>(__VA_ARGS__)                              \
                : (tg) == 4 ? FN<float, 4>(__VA_ARGS__)                              \
                : (tg) == 5 ? FN<float, 5>(__VA_ARGS__)                              \
-                           : FN<float, 6>(__VA_ARGS__)))
+               : (tg) == 6 ? FN<float, 6>(__VA_ARGS__)                              \
+                           : FN<float, 7>(__VA_ARGS__)))
 
 template <class T, int G> static pic_status set_fields_t(pic_handle* h, const double* E, const double* B) {
     const Grid& g = h->g;
@@ -1405,6 +1409,29 @@ int pic_abi_version(void) { return PIC_ABI_VERSION; }
 
 const char* pic_last_error(pic_handle* h) { return h ? h->last_error.c_str() : g_init_error.c_str(); }
 
+// The 2D tile side pic_init picks when the configuration leaves it open: 8
+// when 16 x 16 tiles would give fewer than two per SM (a small box's
+// particle kernel then runs on a few SMs), 32 (FP32) when 32 x 32 tiles still
+// give eight per SM (the larger tiles amortise staging and barriers), else
+// 16.  pic_autotune_tile measures instead.
+static int auto_tile_side(const pic_config& c, bool fp64) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 152;
+    }
+    if (c.ndim == 3) {
+        // 4 x 4 x 4 tiles when 8 x 8 x 8 ones would be fewer than two per SM
+        const long long t8 = ((c.nx + 7ll) / 8) * ((c.ny + 7ll) / 8) * ((c.nz + 7ll) / 8);
+        return t8 < 2ll * sms ? 4 : 8;
+    }
+    const long long a = c.nx, b = c.plane == PIC_PLANE_XY ? c.ny : c.nz;
+    auto tiles = [&](long long s) { return ((a + s - 1) / s) * ((b + s - 1) / s); };
+    if (tiles(16) < 2ll * sms) return 8;
+    if (!fp64 && tiles(32) >= 8ll * sms) return 32;
+    return 16;
+}
+
 // Tiling of a handle from its template geometry (h->tg) and grid: the tile
 // extents are those the particle kernels of h->tg are compiled for.
 static void set_tiling(pic_handle* h) {
@@ -1466,16 +1493,18 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
     {
         const int t0 = c.tile[0], t1 = AY ? c.tile[1] : c.tile[2];
         const int want = t0 ? t0 : t1;
-        const bool ok3 = h->geom == 0 && (t0 == 0 || t0 == 8) && (c.tile[1] == 0 || c.tile[1] == 8) &&
-                         (c.tile[2] == 0 || c.tile[2] == 8);
+        const int w3 = c.tile[0] ? c.tile[0] : (c.tile[1] ? c.tile[1] : c.tile[2]);
+        const bool ok3 = h->geom == 0 && (w3 == 0 || w3 == 4 || w3 == 8) && (c.tile[0] == 0 || c.tile[0] == w3) &&
+                         (c.tile[1] == 0 || c.tile[1] == w3) && (c.tile[2] == 0 || c.tile[2] == w3);
         const bool ok2 = h->geom != 0 && (want == 0 || want == 8 || want == 16 || (want == 32 && !h->fp64)) &&
                          (t1 == 0 || t1 == want);
         if (!(h->geom == 0 ? ok3 : ok2)) {
             delete h;
-            return fail(nullptr, PIC_ERR_ARG, "tile must be 0 (automatic) or %s", h->geom == 0 ? "8x8x8 in 3D"
+            return fail(nullptr, PIC_ERR_ARG, "tile must be 0 (automatic) or %s", h->geom == 0 ? "4x4x4 or 8x8x8 in 3D"
                         : "8x8, 16x16, or 32x32 (FP32), on the active plane in 2D");
         }
-        h->tg = tgeom_of(h->geom, want ? want : 16);
+        const int side = h->geom == 0 ? w3 : want;
+        h->tg = tgeom_of(h->geom, side ? side : auto_tile_side(c, h->fp64));
     }
     set_tiling(h);
     {
@@ -2181,11 +2210,8 @@ pic_status pic_get_tile(pic_handle* h, int32_t tile[3]) {
 
 pic_status pic_set_tile(pic_handle* h, int32_t side) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
-    if (h->geom == 0) {
-        if (side != 8) return fail(h, PIC_ERR_ARG, "3D tiles are 8x8x8");
-        return PIC_OK;
-    }
-    if (side != 8 && side != 16 && !(side == 32 && !h->fp64))
+    if (h->geom == 0 && side != 4 && side != 8) return fail(h, PIC_ERR_ARG, "3D tiles are 4x4x4 or 8x8x8");
+    if (h->geom != 0 && side != 8 && side != 16 && !(side == 32 && !h->fp64))
         return fail(h, PIC_ERR_ARG, "2D tiles are 8x8, 16x16, or 32x32 in FP32");
     cudaSetDevice(h->cfg.device);
     return retile(h, tgeom_of(h->geom, side));
@@ -2261,10 +2287,15 @@ pic_status pic_autotune(pic_handle* h, int32_t trial_steps, int32_t* best, doubl
 pic_status pic_autotune_tile(pic_handle* h, int32_t trial_steps, int32_t* best_side, double* ms_per_side) {
     if (!h) return fail(h, PIC_ERR_ARG, "handle is NULL");
     if (trial_steps < 1) return fail(h, PIC_ERR_ARG, "trial_steps must be >= 1");
-    if (h->geom == 0) return fail(h, PIC_ERR_ARG, "the tile shape is tuned for 2D boxes only");
     cudaSetDevice(h->cfg.device);
-    const int sides[3] = {8, 16, 32};
-    const int nsides = h->fp64 ? 2 : 3;  // no FP64 kernels for 32 x 32 tiles
+    // 3D: 4 and 8; 2D: 8, 16 and (no FP64 kernels for 32 x 32 tiles) 32
+    int sides[3] = {8, 16, 32};
+    int nsides = h->fp64 ? 2 : 3;
+    if (h->geom == 0) {
+        sides[0] = 4;
+        sides[1] = 8;
+        nsides = 2;
+    }
     const int start_side = h->tl.tx;
     const bool prof_was = h->prof.on;
     prof_resolve(h);
@@ -2728,15 +2759,26 @@ pic_status pic_batch_create(pic_handle* const* boxes, int32_t n, pic_batch** out
         if (h->batched) return batch_fail(PIC_ERR_STATE, "pic_batch_create: a box is already in a batch");
         for (int j = 0; j < i; ++j)
             if (boxes[j] == h) return batch_fail(PIC_ERR_ARG, "pic_batch_create: a box appears twice");
-        if (h->cfg.device != h0->cfg.device || h->fp64 != h0->fp64 || h->tg != h0->tg ||
+        if (h->cfg.device != h0->cfg.device || h->fp64 != h0->fp64 || h->geom != h0->geom ||
             h->cfg.shape_order != h0->cfg.shape_order || h->push != h0->push || h->esc != h0->esc)
             return batch_fail(PIC_ERR_ARG,
-                              "pic_batch_create: boxes differ in device, precision, geometry, tile shape, shape order or box type");
+                              "pic_batch_create: boxes differ in device, precision, geometry, shape order or box type");
         bool any = false;
         for (int s = 0; s < PIC_MAX_SPECIES; ++s) any |= h->sp[s].loaded;
         if (!any) return batch_fail(PIC_ERR_STATE, "pic_batch_create: a box has no particles");
     }
     cudaSetDevice(h0->cfg.device);
+    // one persistent kernel serves every member, so they share a tile shape:
+    // the plain tiles of their geometry (8^3, 16^2).  The batch's many boxes
+    // fill the GPU, so a small box's automatic smaller tiles (chosen for a box
+    // running alone) would only add per-tile work; members on another shape
+    // are re-laid out.
+    {
+        const int plain = tgeom_of(h0->geom, h0->geom == 0 ? 8 : 16);
+        for (int i = 0; i < n; ++i)
+            if (boxes[i]->tg != plain && retile(boxes[i], plain) != PIC_OK)
+                return batch_fail(PIC_ERR_STATE, "pic_batch_create: a member could not take the batch's tile shape");
+    }
     pic_batch* B = new pic_batch();
     B->device = h0->cfg.device;
     B->fp64 = h0->fp64;

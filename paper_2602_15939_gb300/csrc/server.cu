@@ -104,11 +104,23 @@ struct pic_server {
 
 // ---- footprint and admission (host arithmetic only) ------------------------------------------
 
+// The tile pic_init will use: the configuration's, or its automatic choice
+// (estimated for a 152-SM device).
 static void tile_shape(const pic_config& c, int& tx, int& ty, int& tz) {
     const int geom = c.ndim == 3 ? 0 : (c.plane == PIC_PLANE_XY ? 1 : 2);
-    // 2D: 16 x 16 unless the configuration asks for 8 x 8 or 32 x 32 tiles
-    const int req = geom == 0 ? 0 : (c.tile[0] ? c.tile[0] : (geom == 1 ? c.tile[1] : c.tile[2]));
-    const int side = geom == 0 ? 8 : ((req == 32 || req == 8) ? req : 16);
+    const int req = c.tile[0] ? c.tile[0] : (geom == 2 ? c.tile[2] : (c.tile[1] ? c.tile[1] : c.tile[2]));
+    const long long sms = 152;
+    int side = req;
+    if (!side) {
+        if (geom == 0) {
+            const long long t8 = ((c.nx + 7ll) / 8) * ((c.ny + 7ll) / 8) * ((c.nz + 7ll) / 8);
+            side = t8 < 2 * sms ? 4 : 8;
+        } else {
+            const long long a = c.nx, b = geom == 1 ? c.ny : c.nz;
+            auto tiles = [&](long long s) { return ((a + s - 1) / s) * ((b + s - 1) / s); };
+            side = tiles(16) < 2 * sms ? 8 : ((c.precision != PIC_FP64 && tiles(32) >= 8 * sms) ? 32 : 16);
+        }
+    }
     tx = side;
     ty = geom == 2 ? 1 : side;
     tz = geom == 1 ? 1 : side;

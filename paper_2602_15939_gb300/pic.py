@@ -395,18 +395,20 @@ def pic_get_tile(h):
 
 
 def pic_set_tile(h, side: int):
-    """Re-lay the particles out in side x side tiles (2D: 8, 16, or 32 in FP32)."""
+    """Re-lay the particles out in tiles of `side` cells per axis (2D: 8, 16,
+    or 32 in FP32; 3D: 4 or 8)."""
     _check(h, lib().pic_set_tile(h, side))
 
 
 def pic_autotune_tile(h, trial_steps: int = 4):
-    """Time 8 x 8, 16 x 16 and (FP32) 32 x 32 tiles of a 2D box, each with its
-    best launch variant, and keep the fastest: returns (best side, ms per step
-    for 8, 16, 32; None for a side not tried)."""
+    """Time the tile shapes of a box (2D: 8 x 8, 16 x 16 and, FP32, 32 x 32;
+    3D: 4^3 and 8^3), each with its best launch variant, and keep the
+    fastest: returns (best side, {side: ms per step})."""
     best = C.c_int32()
     ms = (C.c_double * 3)()
     _check(h, lib().pic_autotune_tile(h, trial_steps, C.byref(best), ms))
-    return best.value, tuple(v if v >= 0 else None for v in ms)
+    sides = (4, 8) if pic_get_tile(h)[2] > 1 and pic_get_tile(h)[1] > 1 else (8, 16, 32)
+    return best.value, {s: ms[k] for k, s in enumerate(sides) if ms[k] >= 0}
 
 
 class Batch:
@@ -540,7 +542,7 @@ class Box:
         pic_set_tile(self.h, side)
 
     def autotune_tile(self, trial_steps=4):
-        """Pick 8 x 8, 16 x 16 or 32 x 32 particle tiles on live steps (2D); see pic_autotune_tile."""
+        """Pick the particle tile shape on live steps; see pic_autotune_tile."""
         return pic_autotune_tile(self.h, trial_steps)
 
     def step(self, n=1):

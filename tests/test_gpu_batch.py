@@ -204,3 +204,27 @@ def test_lane_counts_give_the_same_results(lanes, monkeypatch):
     got = run_batched(cases, 7, False, chunks=[1, 6])
     for c, g in zip(cases, got):
         assert_same(g, run_alone(c, 7, False), exact=True)
+
+
+@pytest.mark.gpu
+def test_members_on_different_automatic_tiles_are_batched():
+    """Small boxes take 4^3 tiles automatically and large ones 8^3; a batch
+    runs its members on the plain 8^3 tiles (re-laid out) and still gives the
+    boxes-alone results (which do not depend on the tile shape)."""
+    cases = [dataclasses.replace(EXPAND[2], name="s16", n=(16, 16, 16), ppc=2, seed=31),
+             dataclasses.replace(EXPAND[2], name="s64", n=(64, 64, 64), ppc=1, seed=32)]
+    loaded = [load(c, False) for c in cases]
+    try:
+        tiles = [b.tile() for b, _ in loaded]
+        with P.Batch([b for b, _ in loaded]) as bt:
+            bt.step(4)
+            bt.sync()
+        assert all(b.tile() == (8, 8, 8) for b, _ in loaded)
+        got = [state(b, n) for b, n in loaded]
+    finally:
+        for b, _ in loaded:
+            b.close()
+    if tiles[0] != tiles[1]:  # the automatic choice differed (the usual case on a 152-SM part)
+        assert tiles[0] == (4, 4, 4)
+    for c, g in zip(cases, got):
+        assert_same(g, run_alone(c, 4, False), exact=True)

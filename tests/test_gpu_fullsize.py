@@ -147,10 +147,9 @@ def test_leaky2d_2048_sampled_particles_and_escapes(side):
     w = W.LEAKY_2D_FP32
     box = W.setup_box(w, device=0, seed=0)
     try:
-        if side != 16:
-            box.set_tile(side)
-            P.pic_set_kernel_variant(box.h, 2)
-            assert box.tile() == (side, side, 1)
+        box.set_tile(side)
+        P.pic_set_kernel_variant(box.h, 2)
+        assert box.tile() == (side, side, 1)
         d0 = box.diagnostics()
         errs = follow_sample(w, box, 10007, 1)
         d1 = box.diagnostics()

@@ -150,7 +150,7 @@ def test_regroup_edge_cases_empty_tiles_and_oversized_tiles():
         assert np.array_equal(x, y)
     # (b) one 8^3 tile holding more slots than the in-shared-memory sort takes
     # (tcap >= 65536): the regroup copies that species in order instead
-    cfg = P.make_config(box=BOX_P, nx=8, ny=8, nz=8, ndim=3, order=1, precision=P.PIC_FP32)
+    cfg = P.make_config(box=BOX_P, nx=8, ny=8, nz=8, ndim=3, order=1, precision=P.PIC_FP32, tile=(8, 8, 8))
     N = 512 * 130
     r = np.random.default_rng(5)
     sp = [dict(q=-0.01, m=1.0, x=r.uniform(0, 8, (N, 3)), u=r.normal(0, 0.05, (N, 3)),

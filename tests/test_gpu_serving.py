@@ -52,7 +52,7 @@ def test_results_alone_equal_results_in_the_mix():
         tickets = []
         for s in specs:
             tickets.append(srv.submit(s))
-            time.sleep(0.005)  # arrivals while others are stepping
+            time.sleep(0.001)  # arrivals while others are stepping
         srv.wait(0, 300)
         info = srv.stats()
         mixed = [srv.poll(t) for t in tickets]

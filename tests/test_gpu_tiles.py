@@ -1,4 +1,5 @@
-"""Particle tile shapes (2D: 8 x 8, 16 x 16 or, in FP32, 32 x 32 cells).  The
+"""Particle tile shapes (2D: 8 x 8, 16 x 16 or, in FP32, 32 x 32 cells; 3D:
+4 x 4 x 4 or 8 x 8 x 8).  The
 tile only decides where a particle is stored and which CTA moves it, so a box
 on 8 x 8 or 32 x 32 tiles matches the oracle like any box, and gives bit for
 bit the FP32 results of the same box on 16 x 16 tiles (its current is an
@@ -13,6 +14,7 @@ from gpu_harness import Case, compare, inputs
 from paper_2602_15939_gb300 import pic as P
 
 BOX_P, BOX_S, BOX_E, BOX_L = P.PIC_BOX_PERIODIC, P.PIC_BOX_SHEAR, P.PIC_BOX_EXPAND, P.PIC_BOX_LEAKY
+BOX_SE = P.PIC_BOX_SHEAR_EXPAND
 XY, XZ = P.PIC_PLANE_XY, P.PIC_PLANE_XZ
 
 # grids that are not multiples of 32: ragged tiles on the high sides
@@ -30,12 +32,12 @@ WIDE = [
 IDS = [c.name for c in WIDE]
 
 
-def narrow(case):
-    return dataclasses.replace(case, tile=(0, 0, 0))
-
-
 def with_side(case, side):
     return dataclasses.replace(case, tile=(side, 0, side) if case.plane == XZ else (side, side, 0))
+
+
+def narrow(case):
+    return with_side(case, 16)
 
 
 def load(case, fp64=False):
@@ -83,7 +85,7 @@ def run(case, plan):
             else:
                 best, ms = box.autotune_tile(item[1])
                 assert best in (8, 16, 32) and box.tile()[0] == best
-                assert all(v > 0 for v in ms)
+                assert sorted(ms) == [8, 16, 32] and all(v > 0 for v in ms.values())
         return state(box, nsp, case.esc_mode == 1), box.tile()
     finally:
         box.close()
@@ -137,7 +139,7 @@ def test_tile_autotuner_keeps_the_simulation():
     try:
         best, ms = box.autotune_tile(2)
         assert best in (8, 16, 32) and box.tile()[0] == best
-        assert all(v > 0 for v in ms)
+        assert sorted(ms) == [8, 16, 32] and all(v > 0 for v in ms.values())
         box.step(1)
         got = state(box, nsp, False)
     finally:
@@ -191,19 +193,24 @@ def test_tile_shape_errors():
         assert box64.tile() == (8, 8, 1)
     finally:
         box64.close()
-    box3 = P.Box(Case("p3", BOX_P, (8, 8, 8)).gpu_config(False))
+    box3 = P.Box(Case("p3", BOX_P, (8, 8, 8), tile=(8, 8, 8)).gpu_config(False))
     try:
         assert box3.tile() == (8, 8, 8)
-        with pytest.raises(P.PicError):
-            box3.set_tile(16)
-        with pytest.raises(P.PicError):
-            box3.autotune_tile(1)
+        for bad in (16, 2, 32):
+            with pytest.raises(P.PicError):
+                box3.set_tile(bad)
+        box3.set_tile(4)
+        assert box3.tile() == (4, 4, 4)
     finally:
         box3.close()
+    for bad in ((4, 8, 8), (8, 8, 16), (16, 16, 16)):
+        with pytest.raises(P.PicError):
+            P.Box(Case("p3", BOX_P, (8, 8, 8), tile=bad).gpu_config(False))
     boxes = [load(c)[0], load(narrow(c))[0]]
     try:
-        with pytest.raises(P.PicError):  # a batch's members share the tile shape
-            P.Batch(boxes)
+        with P.Batch(boxes) as bt:  # a batch's members run on the plain tiles
+            bt.sync()
+            assert boxes[0].tile() == boxes[1].tile() == (16, 16, 1)
     finally:
         for b in boxes:
             b.close()
@@ -216,6 +223,74 @@ def test_fp64_tile_autotuner_tries_8_and_16():
     try:
         best, ms = box.autotune_tile(1)
         assert best in (8, 16) and box.tile()[0] == best
-        assert ms[0] > 0 and ms[1] > 0 and ms[2] is None
+        assert sorted(ms) == [8, 16] and all(v > 0 for v in ms.values())
     finally:
         box.close()
+
+
+@pytest.mark.gpu
+def test_automatic_tile_side_follows_the_box_size():
+    """With the tile left open, pic_init takes 8 x 8 tiles when 16 x 16 ones
+    would leave fewer than two per SM, 32 x 32 (FP32) when those still give
+    eight per SM, else 16 x 16; 3D boxes keep 8 x 8 x 8."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for n, fp64, want in (((64, 64, 1), False, 8), ((64, 64, 1), True, 8), ((512, 512, 1), False, 16),
+                          ((2048, 2048, 1), False, 32), ((2048, 2048, 1), True, 16), ((64, 1, 2048), False, 16)):
+        plane = XZ if n[1] == 1 else XY
+        tiles16 = -(-n[0] // 16) * -(-(n[2] if plane == XZ else n[1]) // 16)
+        tiles32 = -(-n[0] // 32) * -(-(n[2] if plane == XZ else n[1]) // 32)
+        expect = 8 if tiles16 < 2 * sms else (32 if not fp64 and tiles32 >= 8 * sms else 16)
+        assert expect == want or sms != 152
+        cfg = P.make_config(box=BOX_P, nx=n[0], ny=n[1], nz=n[2], ndim=2, plane=plane, order=1,
+                            precision=P.PIC_FP64 if fp64 else P.PIC_FP32)
+        box = P.Box(cfg)
+        try:
+            t = box.tile()
+            assert t[0] == expect and (t[2] if plane == XZ else t[1]) == expect
+        finally:
+            box.close()
+    # 3D: 4^3 tiles when 8^3 ones would be fewer than two per SM
+    for n, want in (((16, 16, 16), 4 if 8 < 2 * sms else 8), ((64, 64, 64), 8 if 512 >= 2 * sms else 4)):
+        box = P.Box(P.make_config(box=BOX_P, nx=n[0], ny=n[1], nz=n[2], order=1, precision=P.PIC_FP32))
+        try:
+            assert box.tile() == (want,) * 3
+        finally:
+            box.close()
+
+
+CUBES = [
+    Case("expand3d_o2", BOX_E, (16, 12, 8), order=2, rate=(0.0, 1e-3, 1e-3), step0=20, ppc=4),
+    Case("shear3d_o2", BOX_S, (16, 12, 8), order=2, s=1.5, Omega0=3e-3, step0=37, ppc=4),
+    Case("leaky3d_disp_o1", BOX_L, (12, 10, 9), order=1, esc_mode=1, esc_dims=3, l_esc=0.3, theta_inj=0.3, ppc=4),
+    Case("shearexp3d_o1_esc", BOX_SE, (16, 16, 8), order=1, s=1.2, Omega0=2e-3, rate=(0.0, 1e-3, 1e-3),
+         step0=101, fp_iters=3, esc_mode=2, p_esc=0.05, theta_inj=0.3, ppc=4),
+]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("fp64", [False, True], ids=["fp32", "fp64"])
+@pytest.mark.parametrize("case", CUBES, ids=[c.name for c in CUBES])
+def test_small_3d_tiles_match_oracle(case, fp64):
+    """4 x 4 x 4 tiles (small 3D boxes) against the oracle, on grids that are
+    not multiples of the tile."""
+    r = compare(dataclasses.replace(case, tile=(4, 4, 4)), 1, fp64=fp64)
+    tol, tx = (1e-12, 1e-11) if fp64 else (1e-6, 2e-6)
+    assert r["error_word"] == 0, r
+    assert r["u"] <= tol and r["x"] <= tx, r
+    assert r["E"] <= tol and r["B"] <= tol and r["J"] <= tol, r
+    assert r["escaped_gpu"] == r["escaped_oracle"], r
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", CUBES, ids=[c.name for c in CUBES])
+def test_small_3d_tiles_equal_8x8x8_tiles(case):
+    """FP32 on 4^3 tiles equals FP32 on 8^3 tiles bit for bit over six steps
+    (regrouping every 3), and so does a box switched between the two."""
+    a, ta = run(dataclasses.replace(case, tile=(4, 4, 4)), [6])
+    b, tb = run(dataclasses.replace(case, tile=(8, 8, 8)), [6])
+    c, tc = run(dataclasses.replace(case, tile=(8, 8, 8)), [2, ("tile", 4), 3, ("tile", 8), 1])
+    assert ta == (4, 4, 4) and tb == (8, 8, 8) and tc == (8, 8, 8)
+    assert_identical(a, b)
+    assert_identical(c, b)
