@@ -359,8 +359,7 @@ def measure(w, args, device, stream, rank, world, headline):
         side, ms_side = box.autotune_tile(4 if headline or w.n_particles > 1e8 else 2)
         tune = {"chosen": P.pic_get_kernel_variant(box.h),
                 "how": "tile shape, then launch variant per shape, autotuned on untimed steps",
-                "tile_ms_per_step": {str(k): (None if v is None else round(v, 4))
-                                     for k, v in zip((8, 16, 32), ms_side)}}
+                "tile_ms_per_step": {str(k): round(v, 4) for k, v in ms_side.items()}}
     else:
         best, ms_v, taken = box.autotune(4 if headline or w.n_particles > 1e8 else 2)
         tune = {"chosen": best, "how": f"autotuned on {taken} untimed steps",
