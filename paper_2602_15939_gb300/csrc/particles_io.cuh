@@ -420,11 +420,26 @@ __global__ void kinetic_kernel(Tiling tl, PView<T> v, const int* __restrict__ st
     };
     for (int t = blockIdx.x; t < tl.ntiles + 1; t += gridDim.x) {
         if (t < tl.ntiles) {
-            const int nst = stay[t], nar = arr[t];
+            const int nst = stay[t], nar = arr[t], n = nst + nar;
             const long long base = (long long)t * tcap;
-            for (int i = threadIdx.x; i < nst + nar; i += blockDim.x) {
-                long long slot = i < nst ? base + i : base + tcap - nar + (i - nst);
-                acc += term(v.u[0][slot], v.u[1][slot], v.u[2][slot]);
+            auto slot = [&](int i) -> long long { return i < nst ? base + i : base + tcap - nar + (i - nst); };
+            // four particles per thread at a time: enough loads in flight to stream u at HBM speed
+            constexpr int K = 4;
+            for (int i0 = threadIdx.x; i0 < n; i0 += K * blockDim.x) {
+                T ux[K], uy[K], uz[K];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int i = i0 + k * blockDim.x;
+                    if (i < n) {
+                        const long long sl = slot(i);
+                        ux[k] = v.u[0][sl];
+                        uy[k] = v.u[1][sl];
+                        uz[k] = v.u[2][sl];
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    if (i0 + k * blockDim.x < n) acc += term(ux[k], uy[k], uz[k]);
             }
         } else {
             long long n = *lcount;

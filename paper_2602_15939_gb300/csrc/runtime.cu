@@ -1566,7 +1566,7 @@ pic_status pic_init(const pic_config* cfg, pic_handle** out) {
     h->stage_elems = (size_t)3 * c.nx * c.ny * c.nz;
     if (dalloc(h, (void**)&h->stage, sizeof(double) * h->stage_elems) != cudaSuccess)
         return bail(fail(h, PIC_ERR_OOM, "staging allocation failed"));
-    h->partial_blocks = 152 * 4;
+    h->partial_blocks = 152 * 8;
     if (dalloc(h, (void**)&h->partial, sizeof(double) * (h->partial_blocks * 3 + 8)) != cudaSuccess)
         return bail(fail(h, PIC_ERR_OOM, "allocation failed"));
     if (dalloc(h, (void**)&h->err, sizeof(int)) != cudaSuccess || dalloc(h, (void**)&h->counters, 2 * sizeof(unsigned long long)) != cudaSuccess)
