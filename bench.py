@@ -685,8 +685,9 @@ def run_e2e(w, device, stream, steps, rank):
     (pic_step + pic_diagnostics read-back), then read an id-sampled subset of
     the final particles (1 in 256) back into pinned memory; all inside the
     timed region.  The host state is generated chunk by chunk straight into
-    the pinned buffers; the leg is skipped (and says so) when those buffers
-    would take more than a third of the host's available memory."""
+    the pinned buffers; the leg is skipped (and says so) when those buffers,
+    times the ranks sharing this host, would take more than a third of the
+    host's available memory."""
     import numpy as np
     import torch
 
@@ -695,10 +696,11 @@ def run_e2e(w, device, stream, steps, rank):
 
     npart = w.n_particles
     need = npart * (8 * 6 + 4)
+    local_ranks = int(os.environ.get("LOCAL_WORLD_SIZE", os.environ.get("WORLD_SIZE", "1")))
     avail = host_mem_available()
-    if avail and need > avail / 3:
-        return {"skipped": f"host memory: the pinned state needs {need / 2**30:.1f} GiB, "
-                           f"available {avail / 2**30:.1f} GiB"}
+    if avail and need * local_ranks > avail / 3:
+        return {"skipped": f"host memory: the pinned state needs {need / 2**30:.1f} GiB per rank on "
+                           f"{local_ranks} rank(s), available {avail / 2**30:.1f} GiB"}
     per_species = npart // 2
     pinned = []
     for s in range(2):
