@@ -232,6 +232,75 @@ __global__ void fill_z_kernel(Grid g, T* F, int ncomp) {
     fill_z_body<T>(g, F, pi, blockIdx.y, blockIdx.z);
 }
 
+// One-pass guard fill of the three components of F for boxes without a
+// shear shift: every guard point takes the interior value at its periodic
+// image in all axes at once, so the x, y and z guards need no ordering and
+// one launch does what the three axis passes do (the same values: a copy).
+// Guard points are enumerated in three regions: the z-guard planes (all
+// padded x, y), then the y-guard rows of interior planes (all padded x),
+// then the x-guard columns of interior rows.
+template <class T, int G>
+__device__ __forceinline__ void fill_all_point(const Grid& g, T* F, long long q) {
+    using GT = GeomT<G>;
+    const long long nzr = GT::AZ ? (long long)(g.pz - g.nz) * g.py * g.px : 0;
+    const long long nyr = GT::AY ? (long long)g.nz * (g.py - g.ny) * g.px : 0;
+    const long long nxr = (long long)g.nz * g.ny * (g.px - g.nx);
+    const long long per = nzr + nyr + nxr;
+    const int comp = (int)(q / per);
+    long long r = q - comp * per;
+    int pi, pj, pk;  // padded coordinates of the guard point
+    if (r < nzr) {
+        const long long plane = (long long)g.py * g.px;
+        const int b = (int)(r / plane);
+        const long long rr = r - b * plane;
+        pk = b < g.gz ? b : g.nz + b;  // low guards, then high guards after the interior
+        pj = (int)(rr / g.px);
+        pi = (int)(rr - (long long)pj * g.px);
+    } else if ((r -= nzr) < nyr) {
+        const long long row = (long long)(g.py - g.ny) * g.px;
+        pk = (int)(r / row) + g.gz;
+        const long long rr = r - (long long)(pk - g.gz) * row;
+        const int b = (int)(rr / g.px);
+        pj = b < g.gy ? b : g.ny + b;
+        pi = (int)(rr - (long long)b * g.px);
+    } else {
+        r -= nyr;
+        const int nxg = g.px - g.nx;
+        const long long col = (long long)g.ny * nxg;
+        pk = (int)(r / col) + g.gz;
+        const long long rr = r - (long long)(pk - g.gz) * col;
+        pj = (int)(rr / nxg) + g.gy;
+        const int b = (int)(rr - (long long)(pj - g.gy) * nxg);
+        pi = b < g.gx ? b : g.nx + b;
+    }
+    // physical coordinates and their periodic images
+    auto img = [](int p, int lo, int n) {
+        int v = p - lo;
+        v %= n;
+        if (v < 0) v += n;
+        return v + lo;
+    };
+    const int si = img(pi, g.gx, g.nx);
+    const int sj = GT::AY ? img(pj, g.gy, g.ny) : pj;
+    const int sk = GT::AZ ? img(pk, g.gz, g.nz) : pk;
+    T* Fc = F + (long long)comp * g.cstride;
+    Fc[((long long)pk * g.py + pj) * g.px + pi] = Fc[((long long)sk * g.py + sj) * g.px + si];
+}
+
+template <class T, int G> __host__ __device__ inline long long fill_all_count(const Grid& g) {
+    using GT = GeomT<G>;
+    const long long nzr = GT::AZ ? (long long)(g.pz - g.nz) * g.py * g.px : 0;
+    const long long nyr = GT::AY ? (long long)g.nz * (g.py - g.ny) * g.px : 0;
+    return 3 * (nzr + nyr + (long long)g.nz * g.ny * (g.px - g.nx));
+}
+
+template <class T, int G>
+__global__ void fill_all_kernel(Grid g, T* F) {
+    const long long n = fill_all_count<T, G>(g);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        fill_all_point<T, G>(g, F, q);
+}
+
 // ---- current fold (adjoint of the fill) ------------------------------------------------
 // Pull form: each interior point near a boundary adds the guard values that
 // map onto it.  Order z, y (over all padded x), then x with the shear shift at
@@ -460,33 +529,17 @@ __global__ void multi_curl_kernel(const FieldBox<T>* __restrict__ fb, const int*
                                    k);
 }
 
-// guard fills of field `which` (no shear shift: the batched path serves the
-// unsheared kinds)
+// One-pass guard fill (fill_all_point) of field `which` for every box.
+// Launch: grid (any, n); block row b serves box b.
 template <class T, int G>
-__global__ void multi_fill_x_kernel(const FieldBox<T>* __restrict__ fb, const int* __restrict__ zoff, int n, int which) {
-    const int b = box_of_z(zoff, n, blockIdx.z);
+__global__ void multi_fill_all_kernel(const FieldBox<T>* __restrict__ fb, int n, int which) {
+    const int b = blockIdx.y;
+    if (b >= n) return;
     const FieldBox<T>& f = fb[b];
-    const int j = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
-    if (j >= f.g.ny || k >= f.g.nz) return;
-    fill_x_body<T, G>(f.g, field_of(f, which), 0, 0.0, j, k, blockIdx.z - zoff[b]);
-}
-
-template <class T>
-__global__ void multi_fill_y_kernel(const FieldBox<T>* __restrict__ fb, const int* __restrict__ zoff, int n, int which) {
-    const int b = box_of_z(zoff, n, blockIdx.z);
-    const FieldBox<T>& f = fb[b];
-    const int pi = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
-    if (pi >= f.g.px || k >= f.g.nz) return;
-    fill_y_body<T>(f.g, field_of(f, which), pi, k, blockIdx.z - zoff[b]);
-}
-
-template <class T>
-__global__ void multi_fill_z_kernel(const FieldBox<T>* __restrict__ fb, const int* __restrict__ zoff, int n, int which) {
-    const int b = box_of_z(zoff, n, blockIdx.z);
-    const FieldBox<T>& f = fb[b];
-    const int pi = blockIdx.x * blockDim.x + threadIdx.x, pj = blockIdx.y;
-    if (pi >= f.g.px || pj >= f.g.py) return;
-    fill_z_body<T>(f.g, field_of(f, which), pi, pj, blockIdx.z - zoff[b]);
+    const long long m = fill_all_count<T, G>(f.g);
+    T* F = field_of(f, which);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < m; q += (long long)gridDim.x * blockDim.x)
+        fill_all_point<T, G>(f.g, F, q);
 }
 
 template <class T>

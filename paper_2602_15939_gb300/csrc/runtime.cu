@@ -397,13 +397,18 @@ template <class T, int G> static void field_step_t(pic_handle* h) {
         }
         return;
     }
-    // standard / expanding leapfrog: coefficients of the three curl updates in the context
+    // standard / expanding leapfrog: coefficients of the three curl updates in
+    // the context; no shear shift, so each guard fill is one pass
+    auto fill = [&](T* F) {
+        fill_all_kernel<T, G><<<grid_blocks(fill_all_count<T, G>(g)), NTHR, 0, h->stream>>>(g, F);
+        h->prof.launches++;
+    };
     curl_t<T, G>(h, true, h->E, h->B, nullptr, 0);
-    fill_guards_t<T, G>(h, (T*)h->B, -1);
+    fill((T*)h->B);
     curl_t<T, G>(h, false, h->B, h->E, h->Jcur, 1);
-    fill_guards_t<T, G>(h, (T*)h->E, -1);
+    fill((T*)h->E);
     curl_t<T, G>(h, true, h->E, h->B, nullptr, 2);
-    fill_guards_t<T, G>(h, (T*)h->B, -1);
+    fill((T*)h->B);
 }
 
 template <class T> static PView<T> view_of(void* const a[11]) {
@@ -2556,11 +2561,7 @@ template <class T, int G> static void multi_fields_t(const pic_batch::FieldTab& 
     if (GT::AZ) multi_fold_z_kernel<T><<<cell_grid(ft.mx_px, ft.mx_py, ft.ztot[3]), CELL_THREADS, 0, s>>>(fb, zz, n);
     if (GT::AY) multi_fold_y_kernel<T><<<cell_grid(ft.mx_px, ft.mx_nz, ft.ztot[2]), CELL_THREADS, 0, s>>>(fb, zy, n);
     multi_fold_x_kernel<T, G><<<cell_grid(ft.mx_ny, ft.mx_nz, ft.ztot[1]), CELL_THREADS, 0, s>>>(fb, zx, n);
-    auto fills = [&](int which) {
-        multi_fill_x_kernel<T, G><<<cell_grid(ft.mx_ny, ft.mx_nz, ft.ztot[1]), CELL_THREADS, 0, s>>>(fb, zx, n, which);
-        if (GT::AY) multi_fill_y_kernel<T><<<cell_grid(ft.mx_px, ft.mx_nz, ft.ztot[2]), CELL_THREADS, 0, s>>>(fb, zy, n, which);
-        if (GT::AZ) multi_fill_z_kernel<T><<<cell_grid(ft.mx_px, ft.mx_py, ft.ztot[3]), CELL_THREADS, 0, s>>>(fb, zz, n, which);
-    };
+    auto fills = [&](int which) { multi_fill_all_kernel<T, G><<<dim3(64, n), NTHR, 0, s>>>(fb, n, which); };
     const dim3 cg = cell_grid(ft.mx_nx, ft.mx_ny, ft.ztot[0]);
     multi_curl_kernel<T, G, true><<<cg, CELL_THREADS, 0, s>>>(fb, zc, n, 0);
     fills(1);
