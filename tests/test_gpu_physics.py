@@ -151,8 +151,20 @@ def _mj_mean_gamma_minus_one(theta):
     return kve(1, x) / kve(2, x) + 3.0 * theta - 1.0
 
 
+LEAKY_KINDS = {
+    "leaky": dict(box=P.PIC_BOX_LEAKY, plane=P.PIC_PLANE_XY),
+    # the leaky box combined with the others (probabilistic escape): slow shear and expansion, so that over
+    # the 300 steps the box's own energy change stays well inside the 2% tolerance
+    "shear": dict(box=P.PIC_BOX_SHEAR, plane=P.PIC_PLANE_XZ, s=1.5, Omega0=2e-5),
+    "expand": dict(box=P.PIC_BOX_EXPAND, plane=P.PIC_PLANE_XY, rate=(1e-6, 1e-6, 0.0)),
+    "shear_expand": dict(box=P.PIC_BOX_SHEAR_EXPAND, plane=P.PIC_PLANE_XY, s=1.5, Omega0=2e-5,
+                         rate=(1e-6, 1e-6, 0.0)),
+}
+
+
 @pytest.mark.gpu
-def test_leaky_box_relaxes_to_a_steady_state():
+@pytest.mark.parametrize("kind", list(LEAKY_KINDS))
+def test_leaky_box_relaxes_to_a_steady_state(kind):
     """Leaky box (Sec. 4): particles escape and are replaced at their own
     position by particles drawn from the reinjection law, so the box keeps its
     particle number and its energy content settles where escape balances what
@@ -162,18 +174,23 @@ def test_leaky_box_relaxes_to_a_steady_state():
     e(n) = e_inj + (e(0) - e_inj) (1 - p)^n, e_inj the mean of the reinjection
     law, and the escape count is binomial with mean N p n.  The same box with
     escape off keeps e(0): the drift to the reinjection temperature is the
-    escape's doing.  FP32 particles, FP64 sums."""
-    n, ppc, theta0, theta_inj, p = (64, 64, 1), 32, 1.0, 0.1, 0.02
+    escape's doing.  Also for the escape combined with the shearing, expanding
+    and combined boxes (slow shear and expansion).  FP32 particles, FP64
+    sums."""
+    kw = dict(LEAKY_KINDS[kind])
+    box_type, plane = kw.pop("box"), kw.pop("plane")
+    n = (64, 1, 64) if plane == P.PIC_PLANE_XZ else (64, 64, 1)
+    ppc, theta0, theta_inj, p = 32, 1.0, 0.1, 0.02
     u = W.PairUnits(0.45, 5.0, ppc)
-    npart = 2 * ppc * n[0] * n[1]
+    npart = 2 * ppc * n[0] * n[1] * n[2]
     out = {}
     for mode in (P.PIC_ESC_PROBABILISTIC, P.PIC_ESC_NONE):
-        cfg = P.make_config(box=P.PIC_BOX_LEAKY, ndim=2, plane=P.PIC_PLANE_XY, nx=n[0], ny=n[1], nz=1, order=1,
-                            precision=P.PIC_FP32, escape_mode=mode, p_esc=p, theta_inj=theta_inj, seed=21)
+        cfg = P.make_config(box=box_type, ndim=2, plane=plane, nx=n[0], ny=n[1], nz=n[2], order=1,
+                            precision=P.PIC_FP32, escape_mode=mode, p_esc=p, theta_inj=theta_inj, seed=21, **kw)
         box = P.Box(cfg)
         try:
             box.load_maxwellian(0, -u.q, 1.0, ppc, theta0, seed=1, id_base=0)
-            box.load_maxwellian(1, u.q, 1.0, ppc, theta0, seed=2, id_base=ppc * n[0] * n[1])
+            box.load_maxwellian(1, u.q, 1.0, ppc, theta0, seed=2, id_base=ppc * n[0] * n[1] * n[2])
             box.set_uniform_fields((0.0, 0.0, 0.0), (0.0, 0.0, u.b0_from_sigma(0.1)))
             hist = []
             for k in range(13):
