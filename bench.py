@@ -148,6 +148,34 @@ def stored_traffic(workload, variant, tile=None):
     return float(m_b.group(1))
 
 
+def stored_instructions(workload, variant, tile=None):
+    """Warp instructions per 32 particles of the particle kernel, from the
+    committed ncu summary of the workload, if it was taken on the current
+    kernel source and launch variant (and tile side); else None."""
+    p = os.path.join(ROOT, "profiles", f"tile_kernel_{workload}.md")
+    if not os.path.exists(p) or stored_traffic(workload, variant, tile) is None:
+        return None
+    m = re.search(r"\| warp instructions per 32 particles \| ([0-9.]+) \|", open(p).read())
+    return float(m.group(1)) if m else None
+
+
+def issue_roofline(ipw, npart, launch_ms, sm_mhz):
+    """The particle kernel against its instruction-issue ceiling: one warp
+    instruction per SM sub-partition (4 per SM) per cycle at the sampled SM
+    clock.  The 3D kernels are bound here long before HBM: at full issue they
+    would still move their bytes at a fraction of the copy bandwidth."""
+    if ipw is None or not launch_ms:
+        return None
+    import torch
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    achieved = ipw * npart / 32 / (launch_ms / 1e3)
+    peak = sms * 4 * sm_mhz * 1e6
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp-instructions/s",
+            "frac": achieved / peak, "warp_instructions_per_32_particles": ipw,
+            "peak_is": f"{sms} SMs x 4 schedulers x {sm_mhz:.0f} MHz", "source": "profiles/ (ncu instruction count)"}
+
+
 # ---- algorithmic bytes ------------------------------------------------------------------------
 # The particle state the method itself needs, read once and written once per
 # step: the int32 cell index, the in-cell offsets of the active axes and the
@@ -423,6 +451,11 @@ def measure(w, args, device, stream, rank, world, headline):
                 "step_frac": (npart * bm["step_bytes_per_particle_step"] / (ms / args.steps / 1e3) / 1e9) / peak,
                 "step_bytes_per_particle_step": bm["step_bytes_per_particle_step"],
                 "overhead_bytes_per_particle_step": bm["overhead_bytes_per_particle_step"]}
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    ir = issue_roofline(stored_instructions(w.name, tune["chosen"], tile[0] if w.ndim == 2 else None), npart,
+                        particle_ms, sm_mhz)
+    if ir:
+        roofline["issue"] = ir
     res = {"value": value, "ms_per_step": ms / args.steps, "particles": npart, "steps": args.steps,
            "particle_phase": {"value": npart / (particle_ms / 1e3), "unit": UNIT, "avg_launch_ms": particle_ms},
            "profile_ms_per_step": {"particle": prof.ms_particle / args.steps, "field": prof.ms_field / args.steps,
