@@ -601,3 +601,46 @@ def test_ksb_fixed_point_iteration_polynomial(nsweeps):
         accB += 2 * termB
     np.testing.assert_allclose(E1, accE, atol=1e-12)
     np.testing.assert_allclose(B1, accB, atol=1e-12)
+
+
+@pytest.mark.parametrize("term", ["bx4", "dxEy", "divxz", "dzEy"])
+def test_ksb_rhs_averaged_shear_terms_on_a_sinusoid(term):
+    """The shear terms of Sec. 2.1 that need a field at another component's
+    location (B_x in the B_y row; d_x E'_y, d_x E'_x + d_z E'_z and d_z E'_y
+    in the E'_x, E'_y and E'_z rows) are centred differences averaged over the
+    two neighbouring y rows.  On a product of sinusoids both steps have closed
+    forms: [sin(a + h/2) + sin(a - h/2)] / 2 = cos(h/2) sin(a) and
+    sin(a + h/2) - sin(a - h/2) = 2 sin(h/2) cos(a).  With one field component
+    nonzero the row reduces to that term alone (its curl, current and
+    upwinded terms vanish), so the right-hand side is known exactly; an
+    average over the wrong rows or a difference at the wrong points is not."""
+    n = (16, 12, 8)
+    kx, ky, kz = 2 * math.pi * 2 / n[0], 2 * math.pi / n[1], 2 * math.pi / n[2]
+    sO = 0.01
+    p = O.make_params(*n, C, box=O.BOX_SHEAR, s=1.0, Omega0=sO)
+    i, j, k = grid_coords(n)
+    E = np.zeros((3,) + i.shape)
+    B = np.zeros_like(E)
+    VN = -sO * (i - n[0] / 2)
+    VH = -sO * (i + 0.5 - n[0] / 2)
+    cy = math.cos(ky / 2)
+    if term == "bx4":  # B_x at (i, j+1/2, k+1/2), wanted at B_y's (i+1/2, j, k+1/2)
+        B = field_from(lambda x, y, z, c: (c == 0) * np.sin(kx * x) * np.sin(ky * y), n, B_STAG)
+        comp, F = 1, "B"
+        want = -sO * math.cos(kx / 2) * np.sin(kx * (i + 0.5)) * cy * np.sin(ky * j)
+    elif term == "dxEy":  # E'_y at (i, j+1/2, k), d_x wanted at E'_x's (i+1/2, j, k)
+        E = field_from(lambda x, y, z, c: (c == 1) * np.sin(kx * x) * np.sin(ky * y), n, E_STAG)
+        comp, F = 0, "E"
+        want = -VH * 2 * math.sin(kx / 2) * np.cos(kx * (i + 0.5)) * cy * np.sin(ky * j)
+    elif term == "divxz":  # E'_x at (i+1/2, j, k), d_x wanted at E'_y's (i, j+1/2, k)
+        E = field_from(lambda x, y, z, c: (c == 0) * np.sin(kx * x) * np.sin(ky * y), n, E_STAG)
+        comp, F = 1, "E"
+        want = -VN * 2 * math.sin(kx / 2) * np.cos(kx * i) * cy * np.sin(ky * (j + 0.5))
+    else:  # E'_y at (i, j+1/2, k), d_z wanted at E'_z's (i, j, k+1/2)
+        E = field_from(lambda x, y, z, c: (c == 1) * np.sin(kz * z) * np.sin(ky * y), n, E_STAG)
+        comp, F = 2, "E"
+        want = -VN * 2 * math.sin(kz / 2) * np.cos(kz * (k + 0.5)) * cy * np.sin(ky * j)
+    FE, FB = O.ksb_rhs(p, E, B, np.zeros_like(E), 0.0)
+    got = (FE if F == "E" else FB)[comp]
+    assert np.abs(want).max() > 1e-3
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-15)

@@ -84,3 +84,20 @@ def test_maxwell_juettner_attempts_bounded():
     for theta in (0.01, 0.2, 2.0, 30.0):
         att = [O.sample_mj(i, 1, 0, theta, 1.0)[1] for i in range(3000)]
         assert np.mean(att) < 1.0 / (1.0 / math.sqrt(2)) + 0.05
+
+
+def test_escape_draw_reads_the_documented_stream():
+    """The escape draw is counter-based: Philox4x32-10 keyed on (particle id,
+    seed) with counter (step low word, step high word, the ASCII tag "ESCP",
+    0); the particle escapes when the first output word is below
+    floor(p 2^32).  The generator itself is pinned by the known-answer vectors
+    above; this fixes which counter and which output word the decision uses,
+    the layout both implementations share."""
+    tag = int.from_bytes(b"ESCP", "big")
+    r = np.random.default_rng(5)
+    for _ in range(400):
+        pid, seed = (int(v) for v in r.integers(0, 2**32, 2))
+        step = int(r.integers(0, 2**40))
+        p = float(r.uniform(0.0, 1.0))
+        w = int(O.philox4x32_10([step & 0xFFFFFFFF, step >> 32, tag, 0], [pid, seed])[0])
+        assert O.escape_draw(pid, seed, step, p) == (w < math.floor(p * 2**32))

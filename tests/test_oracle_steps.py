@@ -262,3 +262,173 @@ def test_threaded_step_equals_the_plain_loop():
         np.testing.assert_allclose(da["u"], db["u"], rtol=0, atol=1e-14)
     np.testing.assert_allclose(a.J, b.J, rtol=0, atol=1e-14 * np.abs(a.J).max())
     np.testing.assert_allclose(a.E, b.E, rtol=0, atol=1e-14 * np.abs(a.E).max())
+
+
+@pytest.mark.parametrize("box", [O.BOX_SHEAR, O.BOX_SHEAR_EXPAND])
+def test_superluminal_counter_counts_the_shear_flow(box):
+    """Sec. 2.1: particles move with the effective velocity u'/gamma' + v_s,
+    v_s = -s Omega0 x e_y, which can exceed c far from the box centre.  A
+    particle at rest in the shearing frame with no fields stays at rest (every
+    push term is proportional to u' or E), so the count over one step is the
+    number of particles with s Omega0 |x - nx/2| >= c, x the physical radial
+    coordinate: l_1(t^n) times the expanding coordinate in the combined box."""
+    n = (16, 4, 4)
+    s, Om = 1.5, 0.05
+    step0, rate = 10, 0.02
+    kw = dict(box=box, s=s, Omega0=Om)
+    l1 = 1.0
+    if box == O.BOX_SHEAR_EXPAND:
+        kw["rate"] = (rate, 0.0, 0.0)
+        l1 = math.exp(rate * step0)
+    p = O.make_params(*n, C, order=1, **kw)
+    xi = np.arange(n[0]) + 0.5                  # one particle per x column
+    N = xi.size
+    x = np.stack([xi, np.full(N, 1.5), np.full(N, 2.5)], axis=1)
+    sp = [{"q": 0.05, "m": 1.0, "x": x, "u": np.zeros((N, 3)), "id": np.arange(N)}]
+    z = np.zeros((3, n[2], n[1], n[0]))
+    st = O.State(p, z, z, sp, step=step0)
+    info = st.step(1)
+    speed = s * Om * np.abs(l1 * (xi - n[0] / 2))  # |v_s| of each particle
+    want = int((speed >= C).sum())
+    assert 0 < want < N and np.abs(speed - C).min() > 0.01  # some, not all, and no ties
+    assert info["superluminal"] == want
+    np.testing.assert_array_equal(st.species[0]["u"], 0.0)
+
+
+def _yee_curl(F, forward):
+    """Yee curl of a [3][nz][ny][nx] periodic field: forward differences
+    (E at B locations) or backward ones (B at E locations)."""
+    d = (lambda A, ax: np.roll(A, -1, axis=ax) - A) if forward else (lambda A, ax: A - np.roll(A, 1, axis=ax))
+    return np.stack([d(F[2], 1) - d(F[1], 0), d(F[0], 0) - d(F[2], 2), d(F[1], 2) - d(F[0], 1)])
+
+
+def test_isotropic_expansion_is_yee_in_conformal_time():
+    """Secs. 3.1-3.2 with L = l(t) I: the expanding-frame fields X' = ell L^-1 X
+    = l^2 X obey the vacuum Maxwell equations with c / l in place of c (the
+    conformal time of the expansion).  The transformed leapfrog must then be
+    the textbook Yee leapfrog on E', B' with c / l at the level of each of its
+    three half updates: t^n, t^{n+1/2}, t^{n+1}.  Two whole steps of an
+    expanding box without particles, from step 7."""
+    n = (6, 5, 4)
+    rate, step0 = 0.05, 7
+    p = O.make_params(*n, C, order=1, box=O.BOX_EXPAND, rate=(rate, rate, rate))
+    r = np.random.default_rng(12)
+    E = r.normal(0, 0.1, (3, n[2], n[1], n[0]))
+    B = r.normal(0, 0.1, (3, n[2], n[1], n[0]))
+    st = O.State(p, E, B, [], step=step0)
+    st.step(2)
+    lv = lambda t: math.exp(rate * t)
+    Ep, Bp = lv(step0) ** 2 * E, lv(step0) ** 2 * B
+    for t in (step0, step0 + 1):
+        Bp = Bp - C / (2 * lv(t)) * _yee_curl(Ep, True)
+        Ep = Ep + C / lv(t + 0.5) * _yee_curl(Bp, False)
+        Bp = Bp - C / (2 * lv(t + 1)) * _yee_curl(Ep, True)
+    l2 = lv(step0 + 2) ** 2
+    np.testing.assert_allclose(st.E, Ep / l2, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(st.B, Bp / l2, rtol=0, atol=1e-14)
+
+
+def test_combined_box_current_advection_integer_shift_is_a_roll():
+    """The combined box advects the collected current along xi_y by
+    v_{s,y} dt / (2 l_2) = -s Omega0 (l_1/l_2)(xi_x - nx/2) / 2, with l_1/l_2
+    at t^{n+1/2}.  Choosing s Omega0 so that this is exactly one cell for the
+    J_y column two cells right of the centre makes that column an exact roll
+    (and the mirror column the opposite roll, the centre column unmoved);
+    l_1/l_2 taken at another time level gives a fractional shift instead."""
+    n = (8, 8, 1)
+    t, r0, r1 = 4.0, 0.03, -0.02
+    vf = math.exp((r0 - r1) * (t + 0.5))
+    p = O.make_params(*n, C, box=O.BOX_SHEAR_EXPAND, s=1.0, Omega0=1.0 / vf, rate=(r0, r1, 0.0))
+    r = np.random.default_rng(4)
+    J = r.normal(size=(3, n[2], n[1], n[0]))
+    J0 = J.copy()
+    O.sxe_advect_current(p, J, t)
+    # J_y sits at x = i: the shift of column i is -(i - 4) / 2 * s Omega0 vf = -(i - 4) / 2
+    np.testing.assert_allclose(J[1, :, :, 6], np.roll(J0[1, :, :, 6], -1, axis=1), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(J[1, :, :, 2], np.roll(J0[1, :, :, 2], 1, axis=1), rtol=0, atol=1e-14)
+    np.testing.assert_array_equal(J[1, :, :, 4], J0[1, :, :, 4])
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_displacement_rule_watches_each_axis(dims):
+    """Sec. 4.1: a particle escapes once its displacement since injection
+    reaches l_esc along a watched axis: x and y in 2D, x, y and z in 3D.  With
+    no fields the momenta stay put, so particles moving along one axis at
+    0.25 cells per step have covered 2.0 cells after 8 steps and 2.25 after 9:
+    with l_esc = 2.1 the x and y movers (and in 3D the z mover) escape on the
+    ninth step, a particle at rest never, and escape resets the displacement
+    and replaces the momentum."""
+    n = (16, 16, 16)
+    v = 0.25
+    u0 = v / math.sqrt(1 - (v / C) ** 2)
+    u = np.zeros((4, 3))
+    u[0, 0], u[1, 1], u[2, 2] = u0, -u0, u0
+    x = np.full((4, 3), 8.3)
+    sp = [{"q": 0.0, "m": 1.0, "x": x, "u": u, "id": np.arange(4)}]  # uncharged: no fields arise
+    z = np.zeros((3, n[2], n[1], n[0]))
+    p = O.make_params(*n, C, box=O.BOX_LEAKY, esc_mode=O.ESC_DISPLACEMENT, esc_dims=dims, l_esc=2.1,
+                      theta_inj=0.1, seed=9)
+    st = O.State(p, z, z, sp)
+    counts = [st.step(1)["escaped"] for _ in range(9)]
+    movers = 3 if dims == 3 else 2
+    assert counts == [0] * 8 + [movers]
+    d = st.species[0]
+    gone = [0, 1, 2][:movers]
+    kept = [q for q in range(4) if q not in gone]
+    np.testing.assert_array_equal(d["dr"][gone], 0.0)
+    assert np.all(np.any(d["u"][gone] != u[gone], axis=1))
+    np.testing.assert_array_equal(d["u"][kept], u[kept])
+
+
+@pytest.mark.parametrize("box", [O.BOX_LEAKY, O.BOX_SHEAR, O.BOX_EXPAND, O.BOX_SHEAR_EXPAND])
+def test_probabilistic_escape_uses_the_draws_of_the_step_taken(box):
+    """Sec. 4.1 with the probabilistic rule: in the step n -> n+1 a particle
+    escapes when its escape draw keyed on step n says so, and its momentum is
+    replaced by the reinjection sample keyed on the same step (both draws are
+    pinned above).  Uncharged particles in zero fields keep their momenta
+    otherwise (the shearing and expanding pushes leave u = 0 at rest)."""
+    n = (8, 8, 8)
+    N, step0, p_esc, theta, seed = 400, 6, 0.3, 0.2, 21
+    kw = {}
+    if box in (O.BOX_SHEAR, O.BOX_SHEAR_EXPAND):
+        kw.update(s=1.5, Omega0=1e-3)
+    if box in (O.BOX_EXPAND, O.BOX_SHEAR_EXPAND):
+        kw.update(rate=(0.01, 0.0, -0.01))
+    p = O.make_params(*n, C, box=box, esc_mode=O.ESC_PROBABILISTIC, p_esc=p_esc, theta_inj=theta, seed=seed, **kw)
+    r = np.random.default_rng(2)
+    x = r.uniform(0, 8, (N, 3))
+    ids = np.arange(N) * 7 + 3
+    sp = [{"q": 0.0, "m": 1.0, "x": x, "u": np.zeros((N, 3)), "id": ids}]
+    z = np.zeros((3, n[2], n[1], n[0]))
+    st = O.State(p, z, z, sp, step=step0)
+    info = st.step(1)
+    esc = np.array([O.escape_draw(int(i), seed, step0, p_esc) for i in ids])
+    assert 0 < esc.sum() < N and info["escaped"] == esc.sum()
+    want = np.zeros((N, 3))
+    for q in np.flatnonzero(esc):
+        want[q] = O.sample_mj(int(ids[q]), seed, step0, theta, C)[0]
+    np.testing.assert_array_equal(st.species[0]["u"], want)
+
+
+def test_combined_box_pushes_with_the_physical_radial_coordinate():
+    """The combined box carries xi = L^-1 x (Sec. 3.1), but the shear terms of
+    the push (Sec. 2.2: a2 = s Omega0 x / c) take the physical distance from
+    the box centre, x = l_1(t^n) (xi_x - nx/2).  In uniform fields the gather
+    returns the fields themselves, so one step's momentum is the pinned
+    combined push at that coordinate."""
+    n = (16, 8, 8)
+    rate, step0, s, Om = (0.05, 0.01, -0.02), 10, 1.5, 0.01
+    p = O.make_params(*n, C, box=O.BOX_SHEAR_EXPAND, s=s, Omega0=Om, rate=rate)
+    Eu, Bu = np.array([0.03, -0.05, 0.02]), np.array([0.1, 0.2, -0.3])
+    E = np.broadcast_to(Eu[:, None, None, None], (3, n[2], n[1], n[0])).copy()
+    B = np.broadcast_to(Bu[:, None, None, None], (3, n[2], n[1], n[0])).copy()
+    x0 = np.array([[13.2, 4.1, 3.7], [2.6, 1.5, 6.2]])
+    u0 = np.array([[0.1, 0.2, -0.05], [-0.15, 0.05, 0.1]])
+    sp = [{"q": 0.05, "m": 1.0, "x": x0, "u": u0, "id": np.arange(2)}]
+    st = O.State(p, E, B, sp, step=step0)
+    st.step(1)
+    l1 = math.exp(rate[0] * step0)
+    Lam = [-0.5 * r for r in rate]
+    for q in range(2):
+        want, _ = O.push_sxe(0.05, 1.0, C, s, Om, l1 * (x0[q, 0] - n[0] / 2), Lam, Eu, Bu, u0[q])
+        np.testing.assert_allclose(st.species[0]["u"][q], want, rtol=1e-13, atol=1e-16)
