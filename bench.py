@@ -717,7 +717,8 @@ def run_e2e(w, device, stream, steps, rank):
     particle state (float64 x, u and uint32 ids) from pinned host memory, K x
     (pic_step + pic_diagnostics read-back), then read an id-sampled subset of
     the final particles (1 in 256) back into pinned memory; all inside the
-    timed region.  The host state is generated chunk by chunk straight into
+    timed region, which follows one untimed pass of the same calls (the
+    warm-up, timed apart and reported).  The host state is generated chunk by chunk straight into
     the pinned buffers; the leg is skipped (and says so) when those buffers,
     times the ranks sharing this host, would take more than a third of the
     host's available memory."""
@@ -749,39 +750,51 @@ def run_e2e(w, device, stream, steps, rank):
              torch.empty((nsamp, 3), dtype=torch.float64, pin_memory=True),
              torch.empty((nsamp,), dtype=torch.int32, pin_memory=True)) for _ in range(2)]
     cfg = P.make_config(precision=P.PIC_FP64 if w.fp64 else P.PIC_FP32, device=device, **w.config_kwargs())
-    box = P.Box(cfg)
-    P.pic_set_stream(box.h, stream.cuda_stream)
     lib = P.lib()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for s, (q, tx, tu, ti) in enumerate(pinned):
-        P._check(box.h, lib.pic_load_particles(box.h, s, q, 1.0, len(tx), P.C.cast(tx.data_ptr(), P._D),
-                                               P.C.cast(tu.data_ptr(), P._D), P.C.cast(ti.data_ptr(), P._U32)))
-    box.set_uniform_fields((0.0, 0.0, 0.0), w.b0())
-    box.sync()
-    t1 = time.perf_counter()
-    for _ in range(steps):
-        box.step(1)
-        box.diagnostics()
-    t2 = time.perf_counter()
-    got = 0
-    for s, (ox, ou, oi) in enumerate(outs):
-        n_out = P.C.c_int64()
-        P._check(box.h, lib.pic_get_particles_sampled(box.h, s, modulus, 0, nsamp, P.C.cast(ox.data_ptr(), P._D),
-                                                      P.C.cast(ou.data_ptr(), P._D), P.C.cast(oi.data_ptr(), P._U32),
-                                                      None, P.C.byref(n_out)))
-        got += min(n_out.value, nsamp)
-    box.sync()
-    t3 = time.perf_counter()
-    dt = t3 - t0
-    box.close()
+
+    def one_pass(nsteps):
+        """load, nsteps x (step + diagnostics), sampled read-back: the user's calls"""
+        box = P.Box(cfg)
+        P.pic_set_stream(box.h, stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s, (q, tx, tu, ti) in enumerate(pinned):
+            P._check(box.h, lib.pic_load_particles(box.h, s, q, 1.0, len(tx), P.C.cast(tx.data_ptr(), P._D),
+                                                   P.C.cast(tu.data_ptr(), P._D), P.C.cast(ti.data_ptr(), P._U32)))
+        box.set_uniform_fields((0.0, 0.0, 0.0), w.b0())
+        box.sync()
+        t1 = time.perf_counter()
+        for _ in range(nsteps):
+            box.step(1)
+            box.diagnostics()
+        t2 = time.perf_counter()
+        got = 0
+        for s, (ox, ou, oi) in enumerate(outs):
+            n_out = P.C.c_int64()
+            P._check(box.h, lib.pic_get_particles_sampled(box.h, s, modulus, 0, nsamp, P.C.cast(ox.data_ptr(), P._D),
+                                                          P.C.cast(ou.data_ptr(), P._D),
+                                                          P.C.cast(oi.data_ptr(), P._U32), None, P.C.byref(n_out)))
+            got += min(n_out.value, nsamp)
+        box.sync()
+        t3 = time.perf_counter()
+        box.close()
+        return got, {"load_and_fields": t1 - t0, "steps_with_diagnostics": t2 - t1, "sampled_readback": t3 - t2}
+
+    # one untimed pass of the same calls on the same pinned buffers first: the
+    # first DMA from freshly pinned pages runs several times slower on this
+    # kind of host, a one-time cost per buffer (reported beside the value)
+    warm_steps = min(2, steps)
+    _, first = one_pass(warm_steps)
+    got, phases = one_pass(steps)
+    dt = sum(phases.values())
     h2d = sum(tx.numel() * 8 + tu.numel() * 8 + ti.numel() * 4 for _, tx, tu, ti in pinned)
     d2h = got * (8 * 6 + 4) + steps * P.C.sizeof(P.pic_diag)
     return {"value": npart * steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
-            "d2h_bytes_per_step": d2h / steps, "steps": steps, "seconds": dt,
-            "phases_s": {"load_and_fields": t1 - t0, "steps_with_diagnostics": t2 - t1, "sampled_readback": t3 - t2},
+            "d2h_bytes_per_step": d2h / steps, "steps": steps, "seconds": dt, "phases_s": phases,
             "includes": "pic_load_particles of the whole state from pinned host memory, per step pic_step + "
-                        "pic_diagnostics, final pic_get_particles_sampled (1 in 256 ids)"}
+                        "pic_diagnostics, final pic_get_particles_sampled (1 in 256 ids)",
+            "warmup": {"how": f"one untimed pass of the same calls ({warm_steps} steps) on the same pinned "
+                              "buffers, with its own box", "phases_s": first}}
 
 
 def main():
