@@ -50,3 +50,52 @@ def test_diagnostics_equal_independent_sums(case, fp64):
         u2 = (u ** 2).sum(axis=1) / c**2
         kin = d["m"] * c**2 * (u2 / (np.sqrt(1.0 + u2) + 1.0)).sum()
         np.testing.assert_allclose(diag.kinetic_energy[i], kin, rtol=1e-12 if fp64 else 1e-6, atol=0)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("fp64", [True, False], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("box_kind", [P.PIC_BOX_SHEAR, P.PIC_BOX_SHEAR_EXPAND], ids=["shear", "shear_expand"])
+def test_superluminal_count_matches_oracle_and_closed_form(box_kind, fp64):
+    """The superluminal counter (Sec. 2.1: the effective velocity u'/gamma' +
+    v_s, v_s = -s Omega0 x e_y, can exceed c far from the centre).  Particles
+    at rest in the shearing frame with no fields stay at rest, so each step
+    counts those with s Omega0 |x - nx/2| >= c, x the physical coordinate
+    (l_1(t^n) times the expanding coordinate in the combined box).  The
+    device's total over three steps must equal the oracle's and the closed
+    form."""
+    import oracle as O
+
+    # the library admits shear flows with c + s Omega0 nx/2 < 1 cell per step,
+    # so the edge speed (0.52 here) sits between c and 1 - c
+    n = (16, 8, 8)
+    s, Om, c, step0, rate = 1.5, 0.065 / 1.5, 0.45, 10, 0.01
+    rates = (rate, 0.0, 0.0) if box_kind == P.PIC_BOX_SHEAR_EXPAND else (0.0, 0.0, 0.0)
+    xi = np.arange(n[0]) + 0.5
+    N = xi.size
+    x = np.stack([xi, np.full(N, 1.5), np.full(N, 2.5)], axis=1)
+    u = np.zeros((N, 3))
+    ids = np.arange(N, dtype=np.uint32)
+    z = np.zeros((3, n[2], n[1], n[0]))
+    want = 0
+    for t in range(step0, step0 + 3):
+        l1 = math.exp(rates[0] * t)
+        speed = s * Om * np.abs(l1 * (xi - n[0] / 2))
+        assert np.abs(speed - c).min() > 0.01  # no particle near the threshold
+        want += int((speed >= c).sum())
+    st = O.State(O.make_params(*n, c, box=box_kind, s=s, Omega0=Om, rate=rates), z, z,
+                 [{"q": 0.05, "m": 1.0, "x": x, "u": u, "id": ids}], step=step0)
+    assert st.step(3)["superluminal"] == want
+    cfg = P.make_config(box=box_kind, nx=n[0], ny=n[1], nz=n[2], c=c, order=1,
+                        precision=P.PIC_FP64 if fp64 else P.PIC_FP32, s=s, Omega0=Om, rate=rates)
+    box = P.Box(cfg)
+    try:
+        box.set_fields(z, z)
+        box.load(0, 0.05, 1.0, x, u, ids)
+        box.set_step(step0)
+        box.step(3)
+        diag = box.diagnostics()
+    finally:
+        box.close()
+    assert diag.error_word == 0
+    assert 0 < want < 3 * N
+    assert diag.superluminal_total == want
