@@ -101,3 +101,25 @@ def test_escape_draw_reads_the_documented_stream():
         p = float(r.uniform(0.0, 1.0))
         w = int(O.philox4x32_10([step & 0xFFFFFFFF, step >> 32, tag, 0], [pid, seed])[0])
         assert O.escape_draw(pid, seed, step, p) == (w < math.floor(p * 2**32))
+
+
+def test_reinjection_direction_reads_the_documented_stream():
+    """The direction of a reinjected momentum: mu = cos(polar angle) = 2 U0 - 1
+    and the azimuth phi = 2 pi U1, from the first two words of Philox4x32-10
+    keyed on (particle id, seed) with counter (step low word, step high word,
+    the ASCII tag "DIRC", 0), U = (w + 1/2) / 2^32.  Its law (isotropy) is
+    pinned above; this fixes the layout both implementations share."""
+    tag = int.from_bytes(b"DIRC", "big")
+    r = np.random.default_rng(8)
+    c = 0.45
+    for _ in range(300):
+        pid, seed = (int(v) for v in r.integers(0, 2**32, 2))
+        step = int(r.integers(0, 2**40))
+        u, _ = O.sample_mj(pid, seed, step, float(r.uniform(0.05, 3.0)), c)
+        w = O.philox4x32_10([step & 0xFFFFFFFF, step >> 32, tag, 0], [pid, seed])
+        mu = 2.0 * (int(w[0]) + 0.5) / 2**32 - 1.0
+        phi = 2.0 * math.pi * (int(w[1]) + 0.5) / 2**32
+        st = math.sqrt(1.0 - mu * mu)
+        umag = float(np.linalg.norm(u))
+        want = umag * np.array([st * math.cos(phi), st * math.sin(phi), mu])
+        np.testing.assert_allclose(u, want, rtol=0, atol=1e-12 * umag)
