@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--grid", default=None, help="override the grid, e.g. 64,64,64 (profiling a smaller case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the other-precision legs (FP64 of FP32 configurations, FP32 of FP64 ones)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="headline workload only")
     ap.add_argument("--serve-runs", type=int, default=64)
@@ -99,6 +99,19 @@ def max_over_ranks(x, world, device="cpu"):
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+L2_BYTES = 129 * 2**20  # the GPU's last-level cache
+
+
+def l2_note(w):
+    """Whether the timed steps can run out of L2: the particle state alone
+    (double-buffered, as the layout stores it) against the cache size."""
+    state = 2 * w.n_particles * stored_state_bytes(w)
+    if state > L2_BYTES:
+        return f"inputs larger than L2 ({state / 2**30:.1f} GiB of particle state; no flush needed)"
+    return (f"inputs fit in L2 ({state / 2**20:.0f} MiB of particle state): a small-box rate, "
+            "not an HBM-bound one")
 
 
 def whole_job_rate(units_per_rank, steps, world, ms):
@@ -466,11 +479,12 @@ def measure(w, args, device, stream, rank, world, headline):
     return box, res
 
 
-def measure_fp64(w, args, device, stream, rank):
-    """The plain FP64 method on the same workload: a few graph-replayed steps."""
+def measure_precision(w, args, device, stream, rank, fp64=True):
+    """The same workload in the other precision (FP64 for an FP32
+    configuration, FP32 for an FP64 one): a few graph-replayed steps."""
     import torch
 
-    b64 = setup_box(w, device, stream.cuda_stream, fp64=True, seed=replica_seed(rank))
+    b64 = setup_box(w, device, stream.cuda_stream, fp64=fp64, seed=replica_seed(rank))
     b64.step(2)
     b64.sync()
     k64 = max(2, min(args.steps, 4))
@@ -513,13 +527,13 @@ def run_gb300(args):
                        "field_sweeps": sweeps_of(w),
                        "precision": ("int32 cell + fp64 offsets/momenta" if w.fp64 else
                                      "int32 cell + fp32 offsets/momenta, fp64 shear shift / l(t) / sums"),
-                       "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}",
+                       "l2": l2_note(w), "parallelism": f"replicas x{world}",
                        "kernel_variant": res["kernel_variant"], "regroup_every": res["regroup_every"]},
             "particle_phase": res["particle_phase"], "profile_ms_per_step": res["profile_ms_per_step"],
             "gpu_launches": res["gpu_launches"], "roofline": res["roofline"], "clocks": res["clocks"]}
 
     if not args.no_fp64 and not args.kernel_only:
-        line["fp64"] = measure_fp64(w, args, local, stream, rank)
+        line["fp32" if w.fp64 else "fp64"] = measure_precision(w, args, local, stream, rank, fp64=not w.fp64)
 
     # the other configurations: FP32 (or the configuration's precision) and FP64 each
     if not args.no_extra and not args.kernel_only and not args.grid:
@@ -533,7 +547,14 @@ def run_gb300(args):
             entry = {"workload": name, "grid": list(wx.n), "particles": wx.n_particles,
                      "box": BOX_NAMES.get(wx.box, str(wx.box)), "dtype": "f64" if wx.fp64 else "f32", **rx}
             if not wx.fp64 and not args.no_fp64:
-                entry["fp64"] = measure_fp64(wx, args, local, stream, rank)
+                entry["fp64"] = measure_precision(wx, args, local, stream, rank)
+            elif wx.fp64 and not args.no_fp64:
+                from paper_2602_15939_gb300 import pic as P
+
+                try:
+                    entry["fp32"] = measure_precision(wx, args, local, stream, rank, fp64=False)
+                except P.PicError as e:  # an argument or memory refusal leaves the context usable
+                    entry["fp32"] = {"error": str(e)}
             configs[name] = entry
         line["configs"] = configs
 

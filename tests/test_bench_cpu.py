@@ -102,3 +102,10 @@ def test_stored_traffic_follows_the_kernel_source(monkeypatch):
 def test_whole_job_rate_counts_every_rank():
     assert bench.whole_job_rate(1000, 4, 2, 500.0) == 1000 * 4 * 2 / 0.5
     assert math.isclose(bench.whole_job_rate(2 ** 30, 20, 1, 81.0 * 20), 2 ** 30 / 0.081)
+
+
+def test_l2_note_tells_which_configurations_fit_in_l2():
+    """Timed steps on a state larger than the 129 MB L2 need no flush; the
+    64^2 FP64 box's 12 MiB state stays in L2 and is labelled so."""
+    assert bench.l2_note(W.SUITE["ksb3d_256_fp32"]).startswith("inputs larger than L2 (64.0 GiB")
+    assert bench.l2_note(W.SUITE["ksb2d_64x64_fp64"]).startswith("inputs fit in L2 (12 MiB")
