@@ -74,3 +74,14 @@ def test_kernel_variant_table():
     for bad in (0, n + 1):
         with pytest.raises(P.PicError):
             P.pic_kernel_variant_info(bad)
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with libpic absent, loading the binding and creating a
+    box both raise."""
+    monkeypatch.setattr(P, "LIB_PATH", str(tmp_path / "libpic.so"))
+    monkeypatch.setattr(P, "_lib", None)
+    with pytest.raises(P.LibraryMissing):
+        P.lib()
+    with pytest.raises(P.LibraryMissing):
+        P.Box(P.make_config())
